@@ -1,0 +1,387 @@
+"""Pins of the FP64 oracle to facts other than itself (CPU only).
+
+Each test names what it checks against: a closed form, a printed formula of
+the libMobility paper, a quadrature of the paper's defining integral
+(Eq. stokestomob), an invariant of the mobility, or a library routine."""
+import os
+
+import numpy as np
+import pytest
+
+from rpy_quadrature import rpy_blocks_quadrature
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _rand_unit(rng):
+    v = rng.standard_normal(3)
+    return v / np.linalg.norm(v)
+
+
+def _rotation(rng):
+    q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+    q = q * np.sign(np.diag(r))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+# --------------------------------------------------------------------------
+# Self mobility (Sec. 3.5, SelfMobility: (6 pi eta a)^-1 I)
+# --------------------------------------------------------------------------
+def test_self_mobility_golden(orc):
+    rows = np.loadtxt(os.path.join(GOLDEN, "self_mobility.txt"))
+    rng = np.random.default_rng(0)
+    for eta, a, mu_t, mu_r in rows:
+        F = rng.standard_normal((1, 3))
+        T = rng.standard_normal((1, 3))
+        u, w = orc.mdot(np.zeros((1, 3)), F, T, a, eta, True)
+        np.testing.assert_allclose(u, mu_t * F, rtol=1e-14, atol=0)
+        np.testing.assert_allclose(w, mu_r * T, rtol=1e-14, atol=0)
+
+
+def test_fp64_workload_parameters_give_unit_self_mobility(orc):
+    # eta = 1/(6 pi), a = 1: the paper's formula gives u = F for an isolated sphere.
+    F = np.array([[0.3, -1.7, 2.5]])
+    u, _ = orc.mdot(np.zeros((1, 3)), F, None, 1.0, 1.0 / (6.0 * np.pi), False)
+    np.testing.assert_allclose(u, F, rtol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Pair blocks vs a quadrature of Eq. (stokestomob) with the RPY envelopes
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("s", [0.3, 1.2, 1.9, 2.05, 2.15, 3.0, 6.0])
+def test_pair_blocks_match_envelope_quadrature(orc, s):
+    a, eta = 1.3, 0.7
+    r = s * a
+    uF, uT, wF, wT = orc.pair_blocks([0.0, 0.0, r], a, eta)
+    q = rpy_blocks_quadrature(r, a, eta, order=6, levels=8)
+    tol = 5e-4 if s < 0.5 else 3e-6
+    tt_scale = max(abs(uF[2, 2]), abs(uF[0, 0]))
+    rr_scale = max(abs(wT[2, 2]), abs(wT[0, 0]))
+    assert abs(q["tt_par"] - uF[2, 2]) <= tol * tt_scale
+    assert abs(q["tt_perp"] - uF[0, 0]) <= tol * tt_scale
+    assert abs(q["tt_perp"] - uF[1, 1]) <= tol * tt_scale
+    assert abs(q["g_uT"] - uT[1, 0]) <= tol * abs(uT[1, 0])
+    assert abs(q["g_wF"] - wF[1, 0]) <= tol * abs(wF[1, 0])
+    assert abs(q["rr_par"] - wT[2, 2]) <= tol * rr_scale
+    assert abs(q["rr_perp"] - wT[0, 0]) <= tol * rr_scale
+    # structure along e_z: uF, wT diagonal; uT, wF antisymmetric [e_z]x
+    for B in (uF, wT):
+        assert np.allclose(B, np.diag(np.diag(B)), atol=1e-15 * abs(B).max())
+    for B in (uT, wF):
+        np.testing.assert_allclose(B, B[1, 0] * np.array([[0, -1, 0], [1, 0, 0], [0, 0, 0]]),
+                                   atol=1e-15 * abs(B).max())
+
+
+def test_contact_values_golden(orc):
+    a, eta = 1.0, 1.0
+    uF, uT, wF, wT = orc.pair_blocks([0.0, 0.0, 2.0 * a], a, eta)
+    units = {"uF": 1 / (8 * np.pi * eta * a), "uT": 1 / (8 * np.pi * eta * a ** 2),
+             "wF": 1 / (8 * np.pi * eta * a ** 2), "wT": 1 / (8 * np.pi * eta * a ** 3)}
+    blocks = {"uF": uF, "uT": uT, "wF": wF, "wT": wT}
+    with open(os.path.join(GOLDEN, "rpy_contact.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, comp, val, _unit = line.split(None, 3)
+            B = blocks[name] / units[name]
+            got = {"par": B[2, 2], "perp": B[0, 0], "cross": B[1, 0]}[comp]
+            assert abs(got - float(val)) < 1e-14, (name, comp, got, val)
+
+
+def test_blocks_continuous_at_contact(orc):
+    a, eta = 0.9, 1.4
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        e = _rand_unit(rng)
+        lo = orc.pair_blocks(2 * a * (1 - 1e-13) * e, a, eta)
+        hi = orc.pair_blocks(2 * a * (1 + 1e-13) * e, a, eta)
+        for B0, B1 in zip(lo, hi):
+            np.testing.assert_allclose(B0, B1, atol=1e-11 * abs(B1).max())
+
+
+def test_oseen_limit(orc):
+    a, eta = 1.0, 1.0
+    r = 1e3
+    e = np.array([0.6, 0.0, 0.8])
+    uF, uT, wF, wT = orc.pair_blocks(r * e, a, eta)
+    oseen = (np.eye(3) + np.outer(e, e)) / (8 * np.pi * eta * r)
+    assert np.abs(uF - oseen).max() <= 2e-6 * np.abs(oseen).max()
+
+
+def test_far_field_rotation_is_half_vorticity(orc):
+    """For r > 2a the angular velocity induced by a force is half the
+    vorticity of the translational field, and likewise for torques
+    (kinetic constraint, Eq. kinetic_constraint, with a point-like delta_T
+    in the far field)."""
+    a, eta = 1.0, 1.0
+    rng = np.random.default_rng(5)
+    h = 1e-5
+    for r in (2.6, 4.0, 9.0):
+        d0 = r * _rand_unit(rng)
+        F = rng.standard_normal(3)
+        T = rng.standard_normal(3)
+
+        def field(d, which):
+            uF, uT, _, _ = orc.pair_blocks(d, a, eta)
+            return uF @ F if which == "F" else uT @ T
+
+        for which, blk in (("F", 2), ("T", 3)):
+            J = np.zeros((3, 3))  # J[p, k] = d field_p / d d_k
+            for k in range(3):
+                dp = d0.copy(); dp[k] += h
+                dm = d0.copy(); dm[k] -= h
+                J[:, k] = (field(dp, which) - field(dm, which)) / (2 * h)
+            curl = np.array([J[2, 1] - J[1, 2], J[0, 2] - J[2, 0], J[1, 0] - J[0, 1]])
+            B = orc.pair_blocks(d0, a, eta)[blk]
+            want = B @ (F if which == "F" else T)
+            np.testing.assert_allclose(0.5 * curl, want, atol=1e-7 * np.abs(want).max())
+
+
+def test_translational_block_divergence_free(orc):
+    """div_x (M_uF(x - x_j) F) = 0 in both branches (incompressible flow)."""
+    a, eta = 1.0, 1.0
+    rng = np.random.default_rng(7)
+    h = 1e-6
+    for r in (0.4, 1.1, 1.7, 2.5, 6.0):
+        d0 = r * _rand_unit(rng)
+        F = rng.standard_normal(3)
+        div = 0.0
+        for k in range(3):
+            dp = d0.copy(); dp[k] += h
+            dm = d0.copy(); dm[k] -= h
+            div += ((orc.pair_blocks(dp, a, eta)[0] @ F)[k] - (orc.pair_blocks(dm, a, eta)[0] @ F)[k]) / (2 * h)
+        scale = np.abs(orc.pair_blocks(d0, a, eta)[0]).max() * np.linalg.norm(F) / r
+        assert abs(div) < 1e-7 * scale
+
+
+# --------------------------------------------------------------------------
+# Whole-matrix invariants
+# --------------------------------------------------------------------------
+def _overlapping(rng, n, L):
+    return rng.uniform(-L / 2, L / 2, size=(n, 3))
+
+
+@pytest.mark.parametrize("n,L", [(2, 1.5), (40, 6.0), (200, 14.0)])
+def test_grand_mobility_symmetric_positive_definite(orc, n, L):
+    rng = np.random.default_rng(n)
+    pos = _overlapping(rng, n, L)
+    M = orc.assemble(pos, 1.0, 1.0, True)
+    assert np.abs(M - M.T).max() <= 1e-15 * np.abs(M).max()
+    lam = np.linalg.eigvalsh(M)
+    assert lam.min() > 0.0
+    if n > 2:
+        # a coincident pair (r = 0, i != j) duplicates 6 columns: M stays
+        # positive semi-definite with exactly 6 zero eigenvalues
+        pos[1] = pos[0]
+        M = orc.assemble(pos, 1.0, 1.0, True)
+        lam = np.linalg.eigvalsh(M)
+        tiny = 1e-13 * lam.max()
+        assert lam.min() > -tiny
+        assert np.sum(np.abs(lam) <= tiny) == 6
+        assert lam[6] > 1e-6 * lam.max()
+
+
+def test_translation_rotation_viscosity(orc):
+    rng = np.random.default_rng(11)
+    n = 30
+    pos = _overlapping(rng, n, 8.0)
+    F = rng.standard_normal((n, 3))
+    T = rng.standard_normal((n, 3))
+    a, eta = 1.0, 1.0
+    u, w = orc.mdot(pos, F, T, a, eta, True)
+    u2, w2 = orc.mdot(pos + np.array([3.0, -7.0, 11.0]), F, T, a, eta, True)
+    np.testing.assert_allclose(u2, u, atol=1e-12 * np.abs(u).max())
+    np.testing.assert_allclose(w2, w, atol=1e-12 * np.abs(w).max())
+    R = _rotation(rng)
+    u3, w3 = orc.mdot(pos @ R.T, F @ R.T, T @ R.T, a, eta, True)
+    np.testing.assert_allclose(u3, u @ R.T, atol=1e-12 * np.abs(u).max())
+    np.testing.assert_allclose(w3, w @ R.T, atol=1e-12 * np.abs(w).max())
+    u4, w4 = orc.mdot(pos, F, T, a, 2.5 * eta, True)
+    np.testing.assert_allclose(u4, u / 2.5, rtol=1e-13)
+    np.testing.assert_allclose(w4, w / 2.5, rtol=1e-13)
+
+
+def test_dense_and_direct_sum_agree(orc):
+    rng = np.random.default_rng(13)
+    n = 50
+    pos = _overlapping(rng, n, 9.0)
+    F = rng.standard_normal((n, 3))
+    T = rng.standard_normal((n, 3))
+    M = orc.assemble(pos, 1.0, 1.0, True)
+    y = M @ np.concatenate([F.ravel(), T.ravel()])
+    u, w = orc.mdot(pos, F, T, 1.0, 1.0, True)
+    np.testing.assert_allclose(u.ravel(), y[: 3 * n], atol=1e-13 * np.abs(y).max())
+    np.testing.assert_allclose(w.ravel(), y[3 * n:], atol=1e-13 * np.abs(y).max())
+    rows = [7, 0, 49, 7]
+    ur, wr = orc.mdot(pos, F, T, 1.0, 1.0, True, rows=rows)
+    np.testing.assert_array_equal(ur, u[rows])
+    np.testing.assert_array_equal(wr, w[rows])
+    # translation-only matrix is the uF part
+    M3 = orc.assemble(pos, 1.0, 1.0, False)
+    np.testing.assert_array_equal(M3, M[: 3 * n, : 3 * n])
+
+
+# --------------------------------------------------------------------------
+# Square root (Eq. fdt) and Lanczos (Sec. 3.3)
+# --------------------------------------------------------------------------
+def test_sqrt_exact_matches_schur_sqrtm(orc):
+    import scipy.linalg
+
+    rng = np.random.default_rng(17)
+    pos = _overlapping(rng, 20, 5.0)
+    M = orc.assemble(pos, 1.0, 1.0, True)
+    S = orc.sqrt_exact(M, np.eye(M.shape[0]))
+    np.testing.assert_allclose(S @ S, M, atol=1e-13 * np.abs(M).max())
+    S2 = np.real(scipy.linalg.sqrtm(M))
+    np.testing.assert_allclose(S, S2, atol=1e-10 * np.abs(S).max())
+
+
+def test_tridiagonal_root_matches_dense(orc):
+    rng = np.random.default_rng(19)
+    m = 12
+    alpha = rng.uniform(2.0, 3.0, m)
+    beta = rng.uniform(0.1, 0.6, m - 1)
+    T = np.diag(alpha) + np.diag(beta, 1) + np.diag(beta, -1)
+    e1 = np.zeros(m); e1[0] = 1.0
+    np.testing.assert_allclose(orc.tridiag_sqrt_e1(alpha, beta), orc.sqrt_exact(T, e1), atol=1e-14)
+
+
+def test_lanczos_full_dimension_is_exact(orc):
+    rng = np.random.default_rng(23)
+    pos = _overlapping(rng, 6, 4.0)
+    M = orc.assemble(pos, 1.0, 1.0, True)
+    W = rng.standard_normal(M.shape[0])
+    y, it, conv = orc.lanczos_sqrt(lambda v: M @ v, W, tol=0.0, max_iter=M.shape[0])
+    assert it <= M.shape[0]
+    np.testing.assert_allclose(y, orc.sqrt_exact(M, W), atol=1e-10 * np.linalg.norm(W))
+
+
+def test_lanczos_eigenvector_converges_in_one_step(orc):
+    rng = np.random.default_rng(29)
+    pos = _overlapping(rng, 10, 6.0)
+    M = orc.assemble(pos, 1.0, 1.0, False)
+    lam, Q = np.linalg.eigh(M)
+    W = 3.0 * Q[:, 4]
+    y, it, conv = orc.lanczos_sqrt(lambda v: M @ v, W, tol=1e-12, max_iter=50)
+    assert it == 1 and conv
+    np.testing.assert_allclose(y, np.sqrt(lam[4]) * W, atol=1e-12)
+
+
+def test_lanczos_zero_rhs(orc):
+    y, it, conv = orc.lanczos_sqrt(lambda v: v, np.zeros(9), tol=1e-8)
+    assert it == 0 and conv and not y.any()
+
+
+def test_lanczos_tolerance_controls_error(orc):
+    rng = np.random.default_rng(31)
+    pos = rng.uniform(-8, 8, size=(120, 3))
+    M = orc.assemble(pos, 1.0, 1.0, True)
+    W = rng.standard_normal(M.shape[0])
+    exact = orc.sqrt_exact(M, W)
+    for tol in (1e-4, 1e-8, 1e-11):
+        y, it, conv = orc.lanczos_sqrt(lambda v: M @ v, W, tol=tol, max_iter=300)
+        assert conv
+        err = np.linalg.norm(y - exact) / np.linalg.norm(exact)
+        assert err < 20 * tol, (tol, err, it)
+
+
+def test_fluctuation_dissipation_covariance(orc):
+    """<(M^1/2 W)(M^1/2 W)^T> = M for W ~ N(0, I) (Eq. fdt with 2kT dt = 1)."""
+    rng = np.random.default_rng(37)
+    pos = _overlapping(rng, 3, 3.0)
+    M = orc.assemble(pos, 1.0, 1.0, True)
+    ns = 40000
+    Wm = rng.standard_normal((M.shape[0], ns))
+    Y = orc.sqrt_exact(M, Wm)
+    C = Y @ Y.T / ns
+    # statistical error of each entry ~ sqrt((M_ii M_jj + M_ij^2)/ns)
+    se = np.sqrt((np.outer(np.diag(M), np.diag(M)) + M ** 2) / ns)
+    assert np.all(np.abs(C - M) < 6 * se)
+
+
+def test_fdt_whitening_kolmogorov_smirnov(orc):
+    """Z = M_SVD^{-1/2} M^{1/2} W ~ N(0, I), component-wise KS test (Sec. 4, FDT test),
+    with M^{1/2} W from the Lanczos method."""
+    from scipy.stats import kstest
+
+    rng = np.random.default_rng(41)
+    pos = _overlapping(rng, 4, 3.5)
+    M = orc.assemble(pos, 1.0, 1.0, True)
+    U, s, Vt = np.linalg.svd(M)
+    Minvsqrt = U @ np.diag(1 / np.sqrt(s)) @ Vt
+    ns = 3000
+    Z = np.empty((M.shape[0], ns))
+    for k in range(ns):
+        W = rng.standard_normal(M.shape[0])
+        y, _, conv = orc.lanczos_sqrt(lambda v: M @ v, W, tol=1e-10, max_iter=M.shape[0])
+        Z[:, k] = Minvsqrt @ y
+    pvals = [kstest(Z[c], "norm").pvalue for c in range(M.shape[0])]
+    assert min(pvals) > 1e-4
+    np.testing.assert_allclose(np.cov(Z), np.eye(M.shape[0]), atol=0.12)
+
+
+# --------------------------------------------------------------------------
+# Gradient of L = <[G;H], M(X)[F;T]>
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("angular", [False, True])
+def test_gradient_matches_central_differences(orc, angular):
+    rng = np.random.default_rng(43 + angular)
+    n = 14
+    pos = _overlapping(rng, n, 5.0)
+    F, T, G, H = (rng.standard_normal((n, 3)) for _ in range(4))
+    a, eta = 1.0, 1.0
+
+    def L(p):
+        u, w = orc.mdot(p, F, T, a, eta, angular)
+        return np.sum(G * u) + (np.sum(H * w) if angular else 0.0)
+
+    dX = orc.grad(pos, F, T, G, H, a, eta, angular)
+    h = 1e-6
+    fd = np.zeros_like(pos)
+    for i in range(n):
+        for k in range(3):
+            pp = pos.copy(); pp[i, k] += h
+            pm = pos.copy(); pm[i, k] -= h
+            fd[i, k] = (L(pp) - L(pm)) / (2 * h)
+    np.testing.assert_allclose(dX, fd, atol=2e-7 * np.abs(fd).max())
+    rows = [3, 0, 13]
+    np.testing.assert_array_equal(orc.grad(pos, F, T, G, H, a, eta, angular, rows=rows), dX[rows])
+
+
+def test_force_gradient_is_mobility_product(orc):
+    """dL/dF = (M [G;H])_u and dL/dT = (M [G;H])_w because M is symmetric."""
+    rng = np.random.default_rng(47)
+    n = 25
+    pos = _overlapping(rng, n, 6.0)
+    F, T, G, H = (rng.standard_normal((n, 3)) for _ in range(4))
+    M = orc.assemble(pos, 1.0, 1.0, True)
+    g = np.concatenate([G.ravel(), H.ravel()])
+    grad_f = M.T @ g
+    u, w = orc.mdot(pos, G, H, 1.0, 1.0, True)
+    np.testing.assert_allclose(u.ravel(), grad_f[: 3 * n], atol=1e-13 * np.abs(grad_f).max())
+    np.testing.assert_allclose(w.ravel(), grad_f[3 * n:], atol=1e-13 * np.abs(grad_f).max())
+
+
+# --------------------------------------------------------------------------
+# Philox-4x32-10 and Box-Muller (noise drawn inside the batched BD step)
+# --------------------------------------------------------------------------
+def test_philox_normals_statistics(orc):
+    from scipy.stats import kstest
+
+    n = 200000
+    ctr = np.zeros((n, 4), dtype=np.uint32)
+    ctr[:, 0] = np.arange(n, dtype=np.uint32)
+    ctr[:, 2] = 7
+    out = orc.philox4x32(ctr, np.array([12345, 678], dtype=np.uint32))
+    assert out.dtype == np.uint32
+    # 4n words: roughly uniform bits
+    bits = np.unpackbits(out.view(np.uint8))
+    assert abs(bits.mean() - 0.5) < 5 / np.sqrt(bits.size)
+    z0, z1 = orc.box_muller(out[:, :2])
+    z = np.concatenate([z0, z1])
+    assert kstest(z, "norm").pvalue > 1e-4
+    # distinct keys and counters give distinct streams
+    out2 = orc.philox4x32(ctr, np.array([12346, 678], dtype=np.uint32))
+    assert np.mean(out2 == out) < 1e-3
