@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Throughput of the open-boundary RPY mobility hot path on one GB300.
+
+One step = one pass of the hot path over one suspension:
+  lm_set_positions -> lm_mdot (M [F; T], all four blocks) -> lm_sqrt_mdot
+  (Lanczos M^{1/2} W at the workload's tolerance).
+Metric: RPY pair-interactions per second, counting N^2 ordered pairs for
+every application of M (the product and each Lanczos iteration), inputs
+resident in HBM, L2 flushed (256 MB write) before every step.
+
+Default workload: N = 32768 spheres uniform in a cube at volume fraction
+0.2, a = 1, eta = 1, translation + rotation, FP32 pair arithmetic with
+compensated sums, FP64 Lanczos at tol 1e-5 (seeded synthetic inputs).
+"--workload melt" runs 1024 chains x 512 beads (N = 524288), tol 1e-3.
+
+--impl reference times the FP64 CPU oracle (the only reference that exists:
+the paper ships no code) on the same metric over a bounded row sample.
+Multi-GPU: replicas only (the product does not shard); one process per GPU
+under torchrun, value = pairs of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RPY pair-interactions/s (N^2 ordered pairs per application of M, incl. Lanczos)"
+UNIT = "pair-interactions/s"
+FP32_LANES_PER_SM = 128
+RECIPE_MAX_SM_MHZ = 2070.0
+PAIR_KERNEL_SRC = os.path.join(ROOT, "paper_2510_02135_gb300", "csrc", "pair_kernels.cu")
+
+
+def workload_spec(name: str):
+    from paper_2510_02135_gb300 import inputs as I
+
+    if name == "rpy6":
+        c = I.RPY6_FP32_N32768
+        s = I.cube_suspension(c["seed"], c["n"], c["phi"], c["a"], angular=True, fp32=True)
+        desc = (f"rpy6_fp32_n32768: N={c['n']} spheres uniform in a cube, phi={c['phi']}, a={c['a']}, "
+                f"eta={c['eta']}, forces+torques, FP32 compensated pairs, FP64 Lanczos tol {c['tol']}")
+        return s, c["eta"], c["a"], c["tol"], desc
+    if name == "melt":
+        c = I.MELT_N524288
+        s = I.polymer_melt(c["seed"], c["n_chains"], c["beads"], c["bond"], c["sigma"], c["phi"], c["a"])
+        desc = (f"melt_n524288: {c['n_chains']} chains x {c['beads']} beads, bond {c['bond']}a, "
+                f"angle jitter {c['sigma']} rad, phi={c['phi']}, forces+torques, FP32 compensated pairs, "
+                f"FP64 Lanczos tol {c['tol']}")
+        return s, c["eta"], c["a"], c["tol"], desc
+    raise SystemExit(f"unknown workload {name}")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def oracle_pairs_per_s(pos, F, T, a, eta, budget_s: float):
+    """Time the FP64 oracle direct sum on a row sample sized to ~budget_s."""
+    import oracle
+
+    n = pos.shape[0]
+    rng = np.random.default_rng(0)
+    rows = rng.choice(n, min(n, 32), replace=False)
+    t0 = time.perf_counter()
+    oracle.mdot(pos, F, T, a, eta, T is not None, rows=rows)
+    t = time.perf_counter() - t0
+    nrows = int(min(n, max(32, len(rows) * budget_s / max(t, 1e-6))))
+    rows = rng.choice(n, nrows, replace=False)
+    t0 = time.perf_counter()
+    oracle.mdot(pos, F, T, a, eta, T is not None, rows=rows)
+    t = time.perf_counter() - t0
+    return nrows * n / t, nrows, t, oracle.num_threads()
+
+
+def profile_traffic():
+    """DRAM bytes per pair-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "pair_kernel_rpy6_n32768.txt")
+    if not os.path.exists(path):
+        return None
+    src_hash = hashlib.sha256(open(PAIR_KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != src_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    s, eta, a, tol, desc = workload_spec(args.workload)
+    import oracle
+
+    oracle.build()
+    n = s.pos.shape[0]
+    for _ in range(args.warmup):
+        oracle_pairs_per_s(s.pos, s.F, s.T, a, eta, budget_s=0.5)
+    vals, rows_used, secs = [], 0, 0.0
+    for _ in range(args.steps):
+        v, nr, t, cores = oracle_pairs_per_s(s.pos, s.F, s.T, a, eta, budget_s=args.ref_step_s)
+        vals.append(v)
+        rows_used += nr
+        secs += t
+    value = rows_used * n / secs
+    sample = (f"each step: FP64 oracle direct sum of M [F; T] (all four blocks) for a random sample of rows "
+              f"(~{args.ref_step_s:.0f} s of CPU work, {rows_used // max(1, args.steps)} rows x {n} columns per step)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["rpy6", "melt"], default="rpy6")
+    ap.add_argument("--autotune", action="store_true", help="autotune the pair kernel before timing")
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle CPU work for cpu_baseline")
+    ap.add_argument("--ref-step-s", type=float, default=3.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+
+    import torch
+
+    from paper_2510_02135_gb300 import _build, lm
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    s_, eta, a, tol, desc = workload_spec(args.workload)
+    n = s_.pos.shape[0]
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    pos, F, T, W = dev(s_.pos), dev(s_.F), dev(s_.T), dev(s_.W)
+    lin = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    ang = torch.empty_like(lin)
+    lin2 = torch.empty_like(lin)
+    ang2 = torch.empty_like(lin)
+    solver = lm.lm_create(eta, a, True, lm.LM_FP32C, cuda_stream=torch.cuda.current_stream().cuda_stream)
+    lm.lm_set_positions(solver, pos)
+    if args.autotune:
+        lm.lm_autotune(solver, reps=2)
+    cfg = lm.lm_get_pair_config(solver)
+    iters = []
+
+    def step():
+        lm.lm_set_positions(solver, pos)
+        lm.lm_mdot(solver, F, T, lin, ang)
+        _, _, it = lm.lm_sqrt_mdot(solver, W, tol=tol, max_iter=200, lin_out=lin2, ang_out=ang2)
+        iters.append(it)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    iters.clear()
+    sampler = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    lm.lm_profile_read(solver, reset=True)
+    lm.lm_profile_enable(solver, True)
+    sampler.start()
+    launches0 = lm.lm_launch_count()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall0
+    launches = lm.lm_launch_count() - launches0
+    clocks = sampler.stop()
+    lm.lm_profile_enable(solver, False)
+    prof = lm.lm_profile_read(solver, reset=True)
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    total_ms = float(sum(step_ms))
+    pairs = float(n) * float(n) * float(sum(1 + it for it in iters))
+    if dist is not None:
+        t = torch.tensor([total_ms, pairs], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_ms_max, pairs_all = float(tmax[0]), float(t[1])
+    else:
+        total_ms_max, pairs_all = total_ms, pairs
+    value = pairs_all / (total_ms_max / 1e3)
+
+    # e2e: the same step through host (pinned) buffers, copies inside the timed region
+    pos_h = torch.from_numpy(s_.pos).pin_memory()
+    F_h = torch.from_numpy(s_.F).pin_memory()
+    T_h = torch.from_numpy(s_.T).pin_memory()
+    W_h = torch.from_numpy(s_.W).pin_memory()
+    outs_h = [torch.empty((n, 3), dtype=torch.float32).pin_memory() for _ in range(4)]
+    e2e_steps = max(3, min(args.steps, 10))
+    e2e_iters = []
+
+    def step_host():
+        lm.lm_set_positions(solver, pos_h)
+        lm.lm_mdot(solver, F_h, T_h, outs_h[0], outs_h[1])
+        _, _, it = lm.lm_sqrt_mdot(solver, W_h, tol=tol, max_iter=200, lin_out=outs_h[2], ang_out=outs_h[3])
+        e2e_iters.append(it)
+
+    step_host()
+    e2e_iters.clear()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        step_host()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    e2e_pairs = float(n) * float(n) * float(sum(1 + it for it in e2e_iters))
+    if dist is not None:
+        t = torch.tensor([t_e2e, e2e_pairs], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        t_e2e, e2e_pairs = float(tmax[0]), float(t[1])
+    e2e_value = e2e_pairs / t_e2e
+    h2d = n * 3 * 4 * 3 + W_h.numel() * 8
+    d2h = n * 3 * 4 * 4
+
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * 2 * RECIPE_MAX_SM_MHZ * 1e6 / 1e12
+    achieved = prof["pair_flops"] / (prof["pair_ms"] / 1e3) / 1e12 if prof["pair_ms"] > 0 else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": profile_traffic(),
+                "kernel": "rpy_mdot_kernel (forward pair kernel, FP32, all four blocks)",
+                "flops_per_pair": 86, "pair_launches": prof["pair_launches"],
+                "pair_kernel_ms_avg": prof["pair_ms"] / max(1, prof["pair_launches"]),
+                "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {RECIPE_MAX_SM_MHZ:.0f} MHz "
+                              f"(recipe max SM clock; FP32 FMA peak)"}
+    if clocks and achieved:
+        roofline["frac_at_sampled_clock"] = achieved / (peak * clocks["sm_mhz"] / RECIPE_MAX_SM_MHZ)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "dtype_detail": "FP32 pair arithmetic with compensated (TwoSum) accumulation; FP64 Lanczos vectors",
+            "data": "synthetic (seeded; shapes of the paper's random-cube benchmark)",
+            "config": {"workload": desc, "N": n, "lanczos_iterations_mean": float(np.mean(iters)),
+                       "sqrt_per_s": args.steps / (total_ms_max / 1e3),
+                       "l2": "flushed by a 256 MB device write before every step (outside the step events)",
+                       "pair_config": cfg, "parallelism": f"replicas x{ws}", "wall_s_timed": t_wall},
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps, "api": "lm_set_positions/lm_mdot/lm_sqrt_mdot with pinned host buffers"},
+            "gpu_launches": launches, "clocks": clocks}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, nrows, t, cores = oracle_pairs_per_s(s_.pos, s_.F, s_.T, a, eta, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"FP64 oracle direct sum of M [F; T] for {nrows} random rows x {n} "
+                                          f"columns ({t:.1f} s); the Lanczos cost per pair is the same product"}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

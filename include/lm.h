@@ -1,0 +1,224 @@
+/*
+ * lm.h -- C ABI of the GB300 open-boundary RPY mobility library.
+ *
+ * The operations follow the solver interface of the libMobility paper
+ * (Sec. 3.2): a solver is created for a periodicity ("open" in x, y, z: the
+ * NBody solver of Sec. 3.5), initialised with the viscosity and hydrodynamic
+ * radius, given positions, and then applies the grand mobility M of
+ * Eq. (block_mobility) to forces and torques (Mdot), or its square root to a
+ * Gaussian vector (sqrtMdotW, Sec. 3.3, by the Lanczos method).  divM is zero
+ * for the open geometry (Sec. 2, after Eq. fdt).
+ *
+ * Common conventions
+ *   - Every call returns an lm_status; LM_OK is 0.  No call aborts, throws or
+ *     exits.  On failure lm_last_error() returns a message for the calling
+ *     thread.
+ *   - Arrays are row-major N x 3 (x, y, z per particle).  The element type is
+ *     float for LM_FP32C solvers and double for LM_FP64 solvers, except W and
+ *     the Lanczos state, which are always double.
+ *   - A grand vector (W) is ordered [F-part (3N); T-part (3N)], the ordering of
+ *     Eq. (block_mobility); without angular blocks it has 3N entries.
+ *   - Any array argument may live in device memory or in host memory (pinned
+ *     or pageable).  Host arrays are copied to and from the GPU by the
+ *     library (Sec. 3.2: numpy inputs are moved automatically); device arrays
+ *     are used in place.  The caller keeps ownership of every array it passes.
+ *   - Calls are ordered on the solver's CUDA stream and return before the GPU
+ *     work finishes, except where a host value must be returned (lm_sqrt_mdot:
+ *     the Lanczos iteration count and convergence) or a host output array is
+ *     written; those synchronise the stream.
+ *   - The library owns its scratch memory (packed positions, split partial
+ *     sums, the Krylov basis) and frees it in lm_destroy.
+ */
+#ifndef LM_GB300_H
+#define LM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lm_solver lm_solver; /* opaque, owned by the library */
+
+typedef enum {
+    LM_OK = 0,
+    LM_ERR_INVALID_ARG = 1,          /* bad pointer, size, value or combination */
+    LM_ERR_UNSUPPORTED_GEOMETRY = 2, /* periodicity other than "open" */
+    LM_ERR_STATE = 3,                /* call out of order (e.g. mdot before set_positions) */
+    LM_ERR_NONFINITE = 4,            /* NaN or Inf in positions */
+    LM_ERR_NOT_CONVERGED = 5,        /* Lanczos hit max_iter; outputs hold the last iterate */
+    LM_ERR_TIMEOUT = 6,              /* a bounded device-side wait expired */
+    LM_ERR_OOM = 7,                  /* device allocation failed */
+    LM_ERR_CUDA = 8                  /* any other CUDA runtime error */
+} lm_status;
+
+typedef enum {
+    LM_FP32C = 0, /* FP32 pair arithmetic, compensated (two-float) accumulation */
+    LM_FP64 = 1   /* FP64 throughout */
+} lm_precision;
+
+/*
+ * lm_create -- the solver constructor and `initialize` of Sec. 3.2.
+ *   px, py, pz: periodicity strings; only "open" is accepted in all three
+ *     directions (NBody, Sec. 3.5; Table tab:solver_summary).  Other valid
+ *     names ("periodic", "single_wall", "two_walls") give
+ *     LM_ERR_UNSUPPORTED_GEOMETRY, unknown names LM_ERR_INVALID_ARG.
+ *   viscosity (eta > 0), hydrodynamic_radius (a > 0): the parameters of the
+ *     RPY kernel.
+ *   include_angular: nonzero to accept torques and return angular
+ *     velocities (the 6N grand mobility); zero for forces only (3N).
+ *   cuda_stream: a cudaStream_t, or NULL for the legacy default stream.
+ *   *out receives the solver; it is NULL on failure.
+ */
+lm_status lm_create(lm_solver **out, const char *px, const char *py, const char *pz,
+                    double viscosity, double hydrodynamic_radius, int include_angular,
+                    lm_precision precision, void *cuda_stream);
+
+/* lm_destroy -- frees the solver and all its device memory.  NULL is allowed. */
+lm_status lm_destroy(lm_solver *solver);
+
+/* lm_set_stream -- change the CUDA stream used by later calls. */
+lm_status lm_set_stream(lm_solver *solver, void *cuda_stream);
+
+/*
+ * lm_set_positions -- setPositions of Sec. 3.2.
+ *   pos: N x 3 positions (float for LM_FP32C, double for LM_FP64), host or
+ *     device.  The library copies them into its own packed buffer, so the
+ *     caller may reuse pos immediately after the call returns.
+ *   N >= 1.  Non-finite coordinates give LM_ERR_NONFINITE (this check
+ *   synchronises the stream) and leave the solver without positions.
+ */
+lm_status lm_set_positions(lm_solver *solver, const void *pos, int64_t N);
+
+/*
+ * lm_mdot -- Mdot of Sec. 3.2: [lin; ang] = M(X) [F; T] with the blocks of
+ * Eq. (block_mobility), a direct O(N^2) sum over all ordered pairs including
+ * the self term (NBody, Sec. 3.5).
+ *   forces, torques: N x 3 or NULL (NULL means zero; "one or both").
+ *     torques must be NULL unless include_angular.
+ *   lin_out: N x 3, required.  ang_out: N x 3, required iff include_angular,
+ *     must be NULL otherwise.
+ */
+lm_status lm_mdot(lm_solver *solver, const void *forces, const void *torques, void *lin_out,
+                  void *ang_out);
+
+/*
+ * lm_sqrt_mdot -- sqrtMdotW of Sec. 3.2 by the Krylov/Lanczos method of
+ * Sec. 3.3: [lin; ang] = prefactor * M^{1/2} W.
+ *   W: 3N (or 6N with angular) doubles, host or device; NULL draws W from
+ *     the library's Philox-4x32-10 generator keyed by seed (normals by
+ *     Box-Muller, element e from counter e / 4).
+ *   prefactor: scale applied to the result, e.g. sqrt(2 kT dt) for the
+ *     Brownian term of Eq. (bdhi); 1 gives M^{1/2} W.
+ *   tol: stop when the relative change of successive iterates is below tol
+ *     (checked from the second iteration).  tol >= 0.
+ *   max_iter: iteration cap, 1 <= max_iter (values above the dimension are
+ *     clamped to it).
+ *   iters_out: optional; receives the number of Lanczos iterations.
+ *   Returns LM_ERR_NOT_CONVERGED when max_iter is reached first; the outputs
+ *   then hold the last iterate.  W = 0 gives zero outputs and 0 iterations.
+ *   Synchronises the stream once per iteration (scalar read-back).
+ */
+lm_status lm_sqrt_mdot(lm_solver *solver, const double *W, uint64_t seed, double prefactor,
+                       double tol, int max_iter, void *lin_out, void *ang_out, int *iters_out);
+
+/*
+ * lm_div_m -- divM of Sec. 3.2.  For the open geometry the mobility is
+ * translation invariant and isotropic, so the thermal drift is identically
+ * zero (Sec. 2, discussion after Eq. fdt); the outputs are set to zero.
+ */
+lm_status lm_div_m(lm_solver *solver, void *lin_out, void *ang_out);
+
+/*
+ * lm_mdot_backward -- adjoint of Mdot (not in the paper; the differentiable
+ * form of the product).  For the scalar L = sum_i G_i . lin_i + H_i . ang_i
+ * with [lin; ang] = M(X) [F; T] it writes
+ *   dX = dL/dX (N x 3), dF = dL/dF = (M [G; H])_lin, dT = dL/dT = (M [G; H])_ang,
+ * in one fused pass that recomputes the pair terms (no N^2 storage).
+ *   forces (required), torques (NULL = zero, angular only), grad_lin (G,
+ *   required), grad_ang (H, NULL = zero, angular only).
+ *   dX and dF may be NULL to skip them; dT must be NULL unless angular.
+ *   The gradient of a pair term at r = 0 (coincident particles) is taken
+ *   as zero.
+ */
+lm_status lm_mdot_backward(lm_solver *solver, const void *forces, const void *torques,
+                           const void *grad_lin, const void *grad_ang, void *dX, void *dF,
+                           void *dT);
+
+/*
+ * Pair-kernel launch configuration (chosen by the autotuner or set by hand).
+ *   threads: CTA size (64, 128 or 256); ilp: i-particles per thread (1, 2, 4);
+ *   splits: number of j-range splits (>= 1; 0 = automatic).
+ */
+typedef struct {
+    int threads;
+    int ilp;
+    int splits;
+} lm_pair_config;
+
+/* lm_get_pair_config / lm_set_pair_config -- read or force the launch
+ * configuration used for the solver's current N.  Setting an unsupported
+ * combination gives LM_ERR_INVALID_ARG. */
+lm_status lm_get_pair_config(lm_solver *solver, lm_pair_config *cfg);
+lm_status lm_set_pair_config(lm_solver *solver, const lm_pair_config *cfg);
+
+/*
+ * lm_autotune -- time every supported pair-kernel configuration for the
+ * solver's precision, angular flag and current N (positions must be set),
+ * keep the fastest, and return it in *best (nullable).  reps >= 1 timed
+ * launches per candidate.  Synchronises the stream.
+ */
+lm_status lm_autotune(lm_solver *solver, int reps, lm_pair_config *best);
+
+/* Statistics of the last lm_sqrt_mdot call on this solver. */
+typedef struct {
+    int iterations;       /* Lanczos iterations */
+    int converged;        /* 1 if the tolerance or a breakdown stopped it */
+    double rel_change;    /* last relative change of successive iterates */
+    double norm_w;        /* |W| */
+    int clamped_eigs;     /* tridiagonal eigenvalues clamped from < 0 to 0 */
+} lm_lanczos_stats;
+
+lm_status lm_get_lanczos_stats(lm_solver *solver, lm_lanczos_stats *stats);
+
+/*
+ * Device-time profile of the forward pair kernel.  While enabled, the solver
+ * records a CUDA event pair on its stream around every pair-kernel launch
+ * (the split reduction is not included).  lm_profile_read synchronises the
+ * stream, returns the totals since the last reset, and resets them if reset
+ * is nonzero.
+ */
+typedef struct {
+    int64_t pair_launches;    /* pair-kernel launches recorded */
+    double pair_ms;           /* their summed device time, milliseconds */
+    double pair_interactions; /* ordered pairs evaluated, N^2 per launch */
+    double pair_flops;        /* algorithmic flops: 35 per pair (forces only) or 86 (all blocks) */
+} lm_profile;
+
+lm_status lm_profile_enable(lm_solver *solver, int enable);
+lm_status lm_profile_read(lm_solver *solver, lm_profile *out, int reset);
+
+/* Number of GPU kernel launches the library has issued in this process, over
+ * all solvers (monotone counter; the argument is ignored and may be NULL). */
+int64_t lm_launch_count(lm_solver *solver);
+
+/*
+ * lm_tridiag_sqrt_e1 -- host-only helper (no GPU needed): out = T^{1/2} e1
+ * for the m x m symmetric tridiagonal T with diagonal alpha[0..m-1] and
+ * off-diagonal beta[0..m-2], the last step of the Lanczos square root
+ * (Sec. 3.3).  Eigenvalues below zero from round-off are clamped to zero.
+ * Returns 0, -1 if the QR iteration did not converge, -2 on bad arguments.
+ */
+int lm_tridiag_sqrt_e1(int m, const double *alpha, const double *beta, double *out);
+
+/* Thread-local message for the last non-OK status ("" if none). */
+const char *lm_last_error(void);
+
+/* Library version string. */
+const char *lm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LM_GB300_H */

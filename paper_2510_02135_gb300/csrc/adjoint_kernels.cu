@@ -1,0 +1,380 @@
+// Adjoint of the RPY mobility product (differentiable form of Mdot, Sec. 3.2).
+//
+// For L = sum_i G_i.u_i + H_i.w_i with [u; w] = M(X) [F; T]:
+//   dL/dF = (M [G; H])_u,  dL/dT = (M [G; H])_w      (M is symmetric)
+//   dL/dx_i = sum_j grad_d Phi_ij(d),  d = x_i - x_j, with
+//   Phi_ij = G_i.tt(d)F_j + F_i.tt(d)G_j + H_i.rr(d)T_j + T_i.rr(d)H_j
+//            + g(r) d.(G_i x T_j + H_i x F_j - G_j x T_i - H_j x F_i)
+// (tt, rr even in d; the tr/rt coupling odd, hence the signs).  With
+// tt = A I + B d d^T and rr = ar I + br d d^T (B, br multiply (d.f) d):
+//   grad_d [g.tt f] = (A'/r)(g.f) d + (B'/r)(g.d)(f.d) d + B[(f.d) g + (g.d) f]
+//   grad_d [g(r) d.P] = (g'/r)(d.P) d + g P.
+// One pass over j per i recomputes every pair term; nothing of size N^2 is
+// stored.  The i-side vectors (G_i, F_i, H_i, T_i) multiply sums of scalars
+// or vectors accumulated over a tile, so their products are applied once per
+// tile.  FP32 partial sums are folded per tile with TwoSum, as in the forward
+// kernel.  Units: coefficients in 1/(8 pi eta), applied once per particle.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "lm_internal.cuh"
+
+namespace lmk {
+namespace {
+
+template <typename R> struct V4;
+template <> struct V4<float> { using type = float4; };
+template <> struct V4<double> { using type = lmk::dvec4; };
+
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
+
+template <typename R>
+__device__ __forceinline__ R ld(const void* p, int f64, int64_t idx) {
+    if (p == nullptr) return R(0);
+    return f64 ? (R)(static_cast<const double*>(p)[idx]) : (R)(static_cast<const float*>(p)[idx]);
+}
+
+// Coefficients and their derivatives divided by r.
+template <typename R>
+struct Coef {
+    R A, B, g, ar, br;       // values
+    R Ap, Bp, gp, arp, brp;  // d/dr divided by r
+};
+
+template <typename R, bool ANG>
+__device__ __forceinline__ void far_coef(R r2, const RpyConst<R>& k, Coef<R>& c) {
+    const R invr = rsq(r2);
+    const R invr2 = invr * invr;
+    const R invr3 = invr2 * invr;
+    const R invr5 = invr3 * invr2;
+    const R invr7 = invr5 * invr2;
+    c.A = fma(k.K1, invr3, invr);
+    c.B = fma(-k.K2, invr5, invr3);
+    c.Ap = fma(R(-3) * k.K1, invr5, -invr3);
+    c.Bp = fma(R(5) * k.K2, invr7, R(-3) * invr5);
+    if constexpr (ANG) {
+        c.g = invr3;
+        c.gp = R(-3) * invr5;
+        c.ar = R(-0.5) * invr3;
+        c.arp = R(1.5) * invr5;
+        c.br = R(1.5) * invr5;
+        c.brp = R(-7.5) * invr7;
+    }
+}
+
+// Exact coefficients; returns false at r = 0 (self / coincident pair), where
+// the gradient is taken as zero and only the mobility part contributes.
+template <typename R, bool ANG>
+__device__ __forceinline__ bool exact_coef(R r2, const RpyConst<R>& k, Coef<R>& c) {
+    if (r2 >= k.four_a2) {
+        far_coef<R, ANG>(r2, k, c);
+        return true;
+    }
+    const R invr = (r2 > R(0)) ? rsq(r2) : R(0);
+    const R r = r2 * invr;
+    const R invr3 = invr * invr * invr;
+    c.A = k.nA0 - k.nA1 * r;
+    c.B = k.nB * invr;
+    c.Ap = -k.nA1 * invr;
+    c.Bp = -k.nB * invr3;
+    if constexpr (ANG) {
+        c.g = k.ng0 - k.ng1 * r;
+        c.gp = -k.ng1 * invr;
+        c.ar = k.inv_a3 * (R(1) - k.rr1 * r + k.rr3 * r * r * r);
+        c.arp = k.inv_a3 * (-k.rr1 * invr + R(3) * k.rr3 * r);
+        c.br = k.inv_a3 * (k.rrb0 * invr - k.rrb1 * r);
+        c.brp = k.inv_a3 * (-k.rrb0 * invr3 - k.rrb1 * invr);
+    }
+    if (!(r2 > R(0))) {
+        c.Ap = c.Bp = R(0);
+        if constexpr (ANG) { c.gp = c.arp = c.brp = R(0); }
+        return false;
+    }
+    return true;
+}
+
+template <typename R, bool ANG>
+struct IData {
+    R x, y, z;
+    R F[3], G[3];
+    R T[ANG ? 3 : 1], H[ANG ? 3 : 1];
+};
+
+template <typename R, bool ANG>
+struct AAcc {
+    static constexpr int C = ANG ? 9 : 6;   // dX(3) dF(3) [dT(3)]
+    R p[C], hi[C], lo[C];
+    R sG, sF;                               // scalars multiplying G_i, F_i
+    R sH, sT;                               // scalars multiplying H_i, T_i
+    R gT[3], gF[3], gG[3], gH[3];           // g-weighted sums of j vectors
+};
+
+// One pair.  grad = false skips the gradient (r = 0).
+template <typename R, bool ANG>
+__device__ __forceinline__ void adj_pair(R dx, R dy, R dz, const Coef<R>& c, bool grad,
+                                         const typename V4<R>::type& Fj, const typename V4<R>::type& Gj,
+                                         const typename V4<R>::type& Tj, const typename V4<R>::type& Hj,
+                                         const IData<R, ANG>& I, AAcc<R, ANG>& a) {
+    const R b1 = fma(Fj.x, dx, fma(Fj.y, dy, Fj.z * dz));   // F_j.d
+    const R b2 = fma(Gj.x, dx, fma(Gj.y, dy, Gj.z * dz));   // G_j.d
+    const R Bb2 = c.B * b2;
+    // dF += A G_j + B (G_j.d) d
+    a.p[3] = fma(Bb2, dx, fma(c.A, Gj.x, a.p[3]));
+    a.p[4] = fma(Bb2, dy, fma(c.A, Gj.y, a.p[4]));
+    a.p[5] = fma(Bb2, dz, fma(c.A, Gj.z, a.p[5]));
+    if (grad) {
+        const R a1 = fma(I.G[0], dx, fma(I.G[1], dy, I.G[2] * dz));  // G_i.d
+        const R a2 = fma(I.F[0], dx, fma(I.F[1], dy, I.F[2] * dz));  // F_i.d
+        const R S1 = fma(I.G[0], Fj.x, fma(I.G[1], Fj.y, fma(I.G[2], Fj.z,
+                     fma(I.F[0], Gj.x, fma(I.F[1], Gj.y, I.F[2] * Gj.z)))));
+        const R S2 = fma(a1, b1, a2 * b2);
+        R cd = fma(c.Ap, S1, c.Bp * S2);
+        const R Ba2 = c.B * a2, Ba1 = c.B * a1;
+        a.sG = fma(c.B, b1, a.sG);
+        a.sF += Bb2;
+        if constexpr (ANG) {
+            const R e1 = fma(Tj.x, dx, fma(Tj.y, dy, Tj.z * dz));    // T_j.d
+            const R e2 = fma(Hj.x, dx, fma(Hj.y, dy, Hj.z * dz));    // H_j.d
+            const R c1 = fma(I.H[0], dx, fma(I.H[1], dy, I.H[2] * dz));
+            const R c2 = fma(I.T[0], dx, fma(I.T[1], dy, I.T[2] * dz));
+            const R R1 = fma(I.H[0], Tj.x, fma(I.H[1], Tj.y, fma(I.H[2], Tj.z,
+                         fma(I.T[0], Hj.x, fma(I.T[1], Hj.y, I.T[2] * Hj.z)))));
+            const R R2 = fma(c1, e1, c2 * e2);
+            cd = fma(c.arp, R1, fma(c.brp, R2, cd));
+            // d.P with P = G_i x T_j + H_i x F_j - G_j x T_i - H_j x F_i
+            //   = T_j.(d x G_i) + F_j.(d x H_i) + G_j.(d x T_i) + H_j.(d x F_i)
+            const R dP =
+                Tj.x * (dy * I.G[2] - dz * I.G[1]) + Tj.y * (dz * I.G[0] - dx * I.G[2]) + Tj.z * (dx * I.G[1] - dy * I.G[0]) +
+                Fj.x * (dy * I.H[2] - dz * I.H[1]) + Fj.y * (dz * I.H[0] - dx * I.H[2]) + Fj.z * (dx * I.H[1] - dy * I.H[0]) +
+                Gj.x * (dy * I.T[2] - dz * I.T[1]) + Gj.y * (dz * I.T[0] - dx * I.T[2]) + Gj.z * (dx * I.T[1] - dy * I.T[0]) +
+                Hj.x * (dy * I.F[2] - dz * I.F[1]) + Hj.y * (dz * I.F[0] - dx * I.F[2]) + Hj.z * (dx * I.F[1] - dy * I.F[0]);
+            cd = fma(c.gp, dP, cd);
+            const R bc2 = c.br * c2, bc1 = c.br * c1;
+            a.p[0] = fma(bc2, Hj.x, fma(bc1, Tj.x, a.p[0]));
+            a.p[1] = fma(bc2, Hj.y, fma(bc1, Tj.y, a.p[1]));
+            a.p[2] = fma(bc2, Hj.z, fma(bc1, Tj.z, a.p[2]));
+            a.sH = fma(c.br, e1, a.sH);
+            a.sT = fma(c.br, e2, a.sT);
+            a.gT[0] = fma(c.g, Tj.x, a.gT[0]); a.gT[1] = fma(c.g, Tj.y, a.gT[1]); a.gT[2] = fma(c.g, Tj.z, a.gT[2]);
+            a.gF[0] = fma(c.g, Fj.x, a.gF[0]); a.gF[1] = fma(c.g, Fj.y, a.gF[1]); a.gF[2] = fma(c.g, Fj.z, a.gF[2]);
+            a.gG[0] = fma(c.g, Gj.x, a.gG[0]); a.gG[1] = fma(c.g, Gj.y, a.gG[1]); a.gG[2] = fma(c.g, Gj.z, a.gG[2]);
+            a.gH[0] = fma(c.g, Hj.x, a.gH[0]); a.gH[1] = fma(c.g, Hj.y, a.gH[1]); a.gH[2] = fma(c.g, Hj.z, a.gH[2]);
+        }
+        a.p[0] = fma(cd, dx, fma(Ba2, Gj.x, fma(Ba1, Fj.x, a.p[0])));
+        a.p[1] = fma(cd, dy, fma(Ba2, Gj.y, fma(Ba1, Fj.y, a.p[1])));
+        a.p[2] = fma(cd, dz, fma(Ba2, Gj.z, fma(Ba1, Fj.z, a.p[2])));
+    }
+    if constexpr (ANG) {
+        // dF += g (H_j x d) ; dT += g (G_j x d) + ar H_j + br (H_j.d) d
+        const R e2 = fma(Hj.x, dx, fma(Hj.y, dy, Hj.z * dz));
+        a.p[3] = fma(c.g, Hj.y * dz - Hj.z * dy, a.p[3]);
+        a.p[4] = fma(c.g, Hj.z * dx - Hj.x * dz, a.p[4]);
+        a.p[5] = fma(c.g, Hj.x * dy - Hj.y * dx, a.p[5]);
+        const R be2 = c.br * e2;
+        a.p[6] = fma(be2, dx, fma(c.ar, Hj.x, fma(c.g, Gj.y * dz - Gj.z * dy, a.p[6])));
+        a.p[7] = fma(be2, dy, fma(c.ar, Hj.y, fma(c.g, Gj.z * dx - Gj.x * dz, a.p[7])));
+        a.p[8] = fma(be2, dz, fma(c.ar, Hj.z, fma(c.g, Gj.x * dy - Gj.y * dx, a.p[8])));
+    }
+}
+
+__device__ __forceinline__ void fold(float& hi, float& lo, float& p) {
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (p - bb);
+    hi = s;
+    lo += err;
+    p = 0.0f;
+}
+__device__ __forceinline__ void fold(double& hi, double& lo, double& p) {
+    hi += p;
+    p = 0.0;
+    (void)lo;
+}
+
+// Apply the tile's i-side products to dX and fold.
+template <typename R, bool ANG>
+__device__ __forceinline__ void flush_tile(const IData<R, ANG>& I, AAcc<R, ANG>& a) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) a.p[q] = fma(a.sG, I.G[q], fma(a.sF, I.F[q], a.p[q]));
+    a.sG = a.sF = R(0);
+    if constexpr (ANG) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) a.p[q] = fma(a.sH, I.H[q], fma(a.sT, I.T[q], a.p[q]));
+        a.sH = a.sT = R(0);
+        // + G_i x gT + H_i x gF - gG x T_i - gH x F_i
+        a.p[0] += (I.G[1] * a.gT[2] - I.G[2] * a.gT[1]) + (I.H[1] * a.gF[2] - I.H[2] * a.gF[1]) -
+                  (a.gG[1] * I.T[2] - a.gG[2] * I.T[1]) - (a.gH[1] * I.F[2] - a.gH[2] * I.F[1]);
+        a.p[1] += (I.G[2] * a.gT[0] - I.G[0] * a.gT[2]) + (I.H[2] * a.gF[0] - I.H[0] * a.gF[2]) -
+                  (a.gG[2] * I.T[0] - a.gG[0] * I.T[2]) - (a.gH[2] * I.F[0] - a.gH[0] * I.F[2]);
+        a.p[2] += (I.G[0] * a.gT[1] - I.G[1] * a.gT[0]) + (I.H[0] * a.gF[1] - I.H[1] * a.gF[0]) -
+                  (a.gG[0] * I.T[1] - a.gG[1] * I.T[0]) - (a.gH[0] * I.F[1] - a.gH[1] * I.F[0]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) a.gT[q] = a.gF[q] = a.gG[q] = a.gH[q] = R(0);
+    }
+#pragma unroll
+    for (int c = 0; c < AAcc<R, ANG>::C; ++c) fold(a.hi[c], a.lo[c], a.p[c]);
+}
+
+template <typename R, bool ANG, int NT>
+__global__ void __launch_bounds__(NT) rpy_adjoint_kernel(const typename V4<R>::type* __restrict__ pos4,
+                                                         const void* __restrict__ Fp, const void* __restrict__ Tp,
+                                                         const void* __restrict__ Gp, const void* __restrict__ Hp,
+                                                         int f64, int64_t N, int64_t jchunk, RpyConst<R> k, double c8,
+                                                         void* __restrict__ dX, void* __restrict__ dF,
+                                                         void* __restrict__ dT, double* __restrict__ partials) {
+    using R4 = typename V4<R>::type;
+    constexpr int C = AAcc<R, ANG>::C;
+    __shared__ R4 sp[NT], sF[NT], sG[NT];
+    __shared__ R4 sT[ANG ? NT : 1], sH[ANG ? NT : 1];
+    const int tid = threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * NT + tid;
+    const int64_t jb = (int64_t)blockIdx.y * jchunk;
+    const int64_t je = (jb + jchunk < N) ? (jb + jchunk) : N;
+    const R pad = (R)kPadCoord;
+
+    IData<R, ANG> I;
+    if (i < N) {
+        const R4 p = pos4[i];
+        I.x = p.x; I.y = p.y; I.z = p.z;
+    } else {
+        I.x = I.y = I.z = -pad;
+    }
+    const int64_t ii = (i < N) ? i : 0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        I.F[q] = ld<R>(Fp, f64, 3 * ii + q);
+        I.G[q] = ld<R>(Gp, f64, 3 * ii + q);
+        if constexpr (ANG) {
+            I.T[q] = ld<R>(Tp, f64, 3 * ii + q);
+            I.H[q] = ld<R>(Hp, f64, 3 * ii + q);
+        }
+    }
+    AAcc<R, ANG> a;
+#pragma unroll
+    for (int c = 0; c < C; ++c) a.p[c] = a.hi[c] = a.lo[c] = R(0);
+    a.sG = a.sF = a.sH = a.sT = R(0);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) a.gT[q] = a.gF[q] = a.gG[q] = a.gH[q] = R(0);
+
+    R4 np, nF, nG, nT, nH;
+    auto fetch = [&](int64_t j) {
+        const bool in = j < je;
+        if (in) np = pos4[j]; else { np.x = pad; np.y = pad; np.z = pad; }
+        const int64_t jj = in ? j : 0;
+        const R z = R(0);
+        nF.x = in ? ld<R>(Fp, f64, 3 * jj) : z; nF.y = in ? ld<R>(Fp, f64, 3 * jj + 1) : z; nF.z = in ? ld<R>(Fp, f64, 3 * jj + 2) : z;
+        nG.x = in ? ld<R>(Gp, f64, 3 * jj) : z; nG.y = in ? ld<R>(Gp, f64, 3 * jj + 1) : z; nG.z = in ? ld<R>(Gp, f64, 3 * jj + 2) : z;
+        if constexpr (ANG) {
+            nT.x = in ? ld<R>(Tp, f64, 3 * jj) : z; nT.y = in ? ld<R>(Tp, f64, 3 * jj + 1) : z; nT.z = in ? ld<R>(Tp, f64, 3 * jj + 2) : z;
+            nH.x = in ? ld<R>(Hp, f64, 3 * jj) : z; nH.y = in ? ld<R>(Hp, f64, 3 * jj + 1) : z; nH.z = in ? ld<R>(Hp, f64, 3 * jj + 2) : z;
+        }
+        np.w = nF.w = nG.w = nT.w = nH.w = z;
+    };
+    fetch(jb + tid);
+
+    for (int64_t jt = jb; jt < je; jt += NT) {
+        sp[tid] = np; sF[tid] = nF; sG[tid] = nG;
+        if constexpr (ANG) { sT[tid] = nT; sH[tid] = nH; }
+        __syncthreads();
+        if (jt + NT < je) fetch(jt + NT + tid);
+#pragma unroll 2
+        for (int jj = 0; jj < NT; ++jj) {
+            const R4 pj = sp[jj];
+            const R4 Fj = sF[jj];
+            const R4 Gj = sG[jj];
+            R4 Tj, Hj;
+            if constexpr (ANG) { Tj = sT[jj]; Hj = sH[jj]; } else { Tj = Fj; Hj = Fj; }
+            const R dx = I.x - pj.x, dy = I.y - pj.y, dz = I.z - pj.z;
+            const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
+            Coef<R> c;
+            if (__any_sync(0xffffffffu, r2 < k.four_a2)) {
+                const bool g = exact_coef<R, ANG>(r2, k, c);
+                adj_pair<R, ANG>(dx, dy, dz, c, g, Fj, Gj, Tj, Hj, I, a);
+            } else {
+                far_coef<R, ANG>(r2, k, c);
+                adj_pair<R, ANG>(dx, dy, dz, c, true, Fj, Gj, Tj, Hj, I, a);
+            }
+        }
+        flush_tile<R, ANG>(I, a);
+        __syncthreads();
+    }
+    if (i >= N) return;
+    const bool direct = (gridDim.y == 1);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const double v = (double)a.hi[c] + (double)a.lo[c];
+        if (direct) {
+            void* out = (c < 3) ? dX : (c < 6 ? dF : dT);
+            if (out == nullptr) continue;
+            const int64_t idx = 3 * i + (c % 3);
+            if (f64) static_cast<double*>(out)[idx] = c8 * v;
+            else static_cast<float*>(out)[idx] = (float)(c8 * v);
+        } else {
+            partials[((int64_t)blockIdx.y * C + c) * N + i] = v;
+        }
+    }
+}
+
+__global__ void adj_reduce_kernel(const double* __restrict__ partials, int splits, int C, int64_t N, double c8,
+                                  void* __restrict__ dX, void* __restrict__ dF, void* __restrict__ dT, int f64) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)C * N) return;
+    const int64_t i = e / C;
+    const int c = (int)(e - i * C);
+    void* out = (c < 3) ? dX : (c < 6 ? dF : dT);
+    if (out == nullptr) return;
+    double s = 0.0;
+    for (int k = 0; k < splits; ++k) s += partials[((int64_t)k * C + c) * N + i];
+    const int64_t idx = 3 * i + (c % 3);
+    if (f64) static_cast<double*>(out)[idx] = c8 * s;
+    else static_cast<float*>(out)[idx] = (float)(c8 * s);
+}
+
+int64_t adj_split_plan(int64_t N, int NT, int splits, int64_t* jchunk) {
+    if (splits < 1) splits = 1;
+    const int64_t ntiles = (N + NT - 1) / NT;
+    if (splits > ntiles) splits = (int)ntiles;
+    const int64_t tps = (ntiles + splits - 1) / splits;
+    *jchunk = tps * NT;
+    return (N + *jchunk - 1) / *jchunk;
+}
+
+template <typename R, bool ANG>
+cudaError_t launch_adj_t(const AdjointArgs& a, cudaStream_t s) {
+    constexpr int NT = 128;
+    const int64_t nblk = (a.N + NT - 1) / NT;
+    int64_t jchunk = 0;
+    const int splits = (int)adj_split_plan(a.N, NT, a.splits, &jchunk);
+    if (nblk > 0x7fffffff || splits > 65535) return cudaErrorInvalidConfiguration;
+    if (splits > 1 && a.partials == nullptr) return cudaErrorInvalidValue;
+    const double c8 = 1.0 / (8.0 * 3.14159265358979323846 * a.eta);
+    const RpyConst<R> k = make_rpy_const<R>(a.a);
+    dim3 grid((unsigned)nblk, (unsigned)splits);
+    rpy_adjoint_kernel<R, ANG, NT><<<grid, NT, 0, s>>>(static_cast<const typename V4<R>::type*>(a.pos4), a.F,
+                                                       ANG ? a.T : nullptr, a.G, ANG ? a.H : nullptr, a.fp64, a.N,
+                                                       jchunk, k, c8, a.dX, a.dF, ANG ? a.dT : nullptr, a.partials);
+    cudaError_t err = cudaGetLastError();
+    count_launches(1);
+    if (err != cudaSuccess || splits == 1) return err;
+    constexpr int C = ANG ? 9 : 6;
+    const int64_t tot = (int64_t)C * a.N;
+    adj_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a.partials, splits, C, a.N, c8, a.dX, a.dF,
+                                                                     ANG ? a.dT : nullptr, a.fp64);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int adjoint_partial_components(int angular) { return angular ? 9 : 6; }
+
+cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s) {
+    if (a.N <= 0) return cudaSuccess;
+    if (a.threads != 128) return cudaErrorInvalidConfiguration;
+    if (a.fp64) return a.angular ? launch_adj_t<double, true>(a, s) : launch_adj_t<double, false>(a, s);
+    return a.angular ? launch_adj_t<float, true>(a, s) : launch_adj_t<float, false>(a, s);
+}
+
+}  // namespace lmk

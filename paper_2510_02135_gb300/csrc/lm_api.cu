@@ -1,0 +1,722 @@
+// C ABI of the library (include/lm.h): solver state, argument validation,
+// host/device staging of arrays, launch-configuration choice, the Lanczos
+// driver of lm_sqrt_mdot and the autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lm.h"
+#include "lm_internal.cuh"
+#include "tridiag.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+std::atomic<int64_t> g_launches{0};
+
+lm_status fail(lm_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+lm_status cuda_fail(cudaError_t e, const char* where) {
+    cudaGetLastError();  // clear a sticky launch error where possible
+    if (e == cudaErrorMemoryAllocation) return fail(LM_ERR_OOM, "%s: out of device memory", where);
+    return fail(LM_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define LM_CUDA(call, where)                          \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+struct DBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= cap && p != nullptr) return cudaSuccess;
+        release();
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) { p = nullptr; cap = 0; return e; }
+        cap = bytes;
+        return cudaSuccess;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = (cudaSetDevice(dev) == cudaSuccess);
+        }
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+bool is_device_ptr(const void* p) {
+    if (p == nullptr) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+namespace lmk {
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace lmk
+
+struct lm_solver {
+    int angular = 0;
+    int fp64 = 0;
+    double eta = 1.0, a = 1.0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sm_count = 1;
+
+    int64_t N = 0;
+    bool has_pos = false;
+
+    DBuf pos4;
+    DBuf partials;
+    DBuf in_stage[4];
+    DBuf out_stage[3];
+    DBuf flag;
+    DBuf tune_in, tune_out;
+
+    // Lanczos state
+    DBuf V, w, y, red, scal, zbuf, cbuf, Wbuf;
+    double* pinned = nullptr;  // host scalar read-back
+    size_t pinned_doubles = 0;
+
+    lm_pair_config cfg{128, 4, 1};
+    bool cfg_forced = false;
+    int64_t cfg_N = -1;
+    lm_pair_config adj_cfg{128, 1, 1};
+    int64_t adj_cfg_N = -1;
+
+    lm_lanczos_stats stats{0, 0, 0.0, 0.0, 0};
+
+    // profiling of the pair kernel
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;   // pairs (begin, end)
+    size_t prof_used = 0;               // event pairs in use
+    double prof_pairs = 0.0;
+
+    ~lm_solver() {
+        DBuf* all[] = {&pos4, &partials, &in_stage[0], &in_stage[1], &in_stage[2], &in_stage[3],
+                       &out_stage[0], &out_stage[1], &out_stage[2], &flag, &tune_in, &tune_out,
+                       &V, &w, &y, &red, &scal, &zbuf, &cbuf, &Wbuf};
+        for (DBuf* b : all) b->release();
+        if (pinned) cudaFreeHost(pinned);
+        for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+
+size_t elem_size(const lm_solver* s) { return s->fp64 ? sizeof(double) : sizeof(float); }
+
+// Device view of an input array: device pointers pass through, host arrays
+// are copied into a staging buffer on the solver's stream.
+lm_status stage_in(lm_solver* s, const void* p, size_t bytes, int slot, const void** out) {
+    *out = nullptr;
+    if (p == nullptr) return LM_OK;
+    if (is_device_ptr(p)) { *out = p; return LM_OK; }
+    LM_CUDA(s->in_stage[slot].ensure(bytes), "staging input");
+    LM_CUDA(cudaMemcpyAsync(s->in_stage[slot].p, p, bytes, cudaMemcpyHostToDevice, s->stream), "copy input to device");
+    *out = s->in_stage[slot].p;
+    return LM_OK;
+}
+
+struct OutView {
+    void* user = nullptr;
+    void* dev = nullptr;
+    size_t bytes = 0;
+    bool host = false;
+};
+
+lm_status stage_out(lm_solver* s, void* p, size_t bytes, int slot, OutView* v) {
+    v->user = p;
+    v->bytes = bytes;
+    v->dev = nullptr;
+    v->host = false;
+    if (p == nullptr) return LM_OK;
+    if (is_device_ptr(p)) { v->dev = p; return LM_OK; }
+    LM_CUDA(s->out_stage[slot].ensure(bytes), "staging output");
+    v->dev = s->out_stage[slot].p;
+    v->host = true;
+    return LM_OK;
+}
+
+lm_status finish_out(lm_solver* s, OutView* views, int nv) {
+    bool any = false;
+    for (int k = 0; k < nv; ++k) {
+        if (views[k].host && views[k].user) {
+            LM_CUDA(cudaMemcpyAsync(views[k].user, views[k].dev, views[k].bytes, cudaMemcpyDeviceToHost, s->stream),
+                    "copy output to host");
+            any = true;
+        }
+    }
+    if (any) LM_CUDA(cudaStreamSynchronize(s->stream), "synchronise outputs");
+    return LM_OK;
+}
+
+// Split count minimising (waves x tiles per CTA): keeps all SMs busy when N
+// is small and limits the tail wave when N is large.
+int auto_splits(int64_t N, int threads, int ilp, int slots) {
+    const int64_t nblk = (N + (int64_t)threads * ilp - 1) / ((int64_t)threads * ilp);
+    const int64_t ntiles = (N + threads - 1) / threads;
+    int best = 1;
+    double best_cost = 1e300;
+    for (int s = 1; s <= 64 && s <= ntiles; ++s) {
+        const int64_t tps = (ntiles + s - 1) / s;
+        if (s > 1 && tps < 4) break;
+        const int64_t se = (ntiles + tps - 1) / tps;
+        const int64_t items = nblk * se;
+        const int64_t waves = (items + slots - 1) / std::max(1, slots);
+        const double cost = (double)waves * (double)tps * (1.0 + 0.002 * (double)se);
+        if (cost < best_cost - 1e-9) { best_cost = cost; best = (int)se; }
+    }
+    return best;
+}
+
+lm_pair_config default_config(const lm_solver* s, int64_t N) {
+    lm_pair_config c;
+    c.threads = 128;
+    c.ilp = s->fp64 ? (s->angular ? 1 : 2) : 4;
+    int occ = lmk::mdot_ctas_per_sm(s->fp64, s->angular, c.threads, c.ilp);
+    if (occ < 1) occ = 1;
+    c.splits = auto_splits(N, c.threads, c.ilp, occ * s->sm_count);
+    return c;
+}
+
+void ensure_config(lm_solver* s) {
+    if (s->cfg_N == s->N) return;
+    if (!s->cfg_forced) s->cfg = default_config(s, s->N);
+    s->cfg_N = s->N;
+}
+
+lm_status run_mdot(lm_solver* s, const void* F, const void* T, int in_f64, void* lin, void* ang, int out_f64,
+                   const lm_pair_config& cfg) {
+    lmk::MdotArgs a;
+    a.fp64 = s->fp64;
+    a.angular = s->angular;
+    a.N = s->N;
+    a.pos4 = s->pos4.p;
+    a.F = F;
+    a.T = s->angular ? T : nullptr;
+    a.in_f64 = in_f64;
+    a.lin = lin;
+    a.ang = s->angular ? ang : nullptr;
+    a.out_f64 = out_f64;
+    a.a = s->a;
+    a.eta = s->eta;
+    a.threads = cfg.threads;
+    a.ilp = cfg.ilp;
+    a.splits = cfg.splits;
+    a.partials = nullptr;
+    const int64_t se = lmk::mdot_effective_splits(s->N, cfg.threads, cfg.splits);
+    if (se > 1) {
+        const size_t bytes = (size_t)se * lmk::mdot_partial_components(s->angular) * (size_t)s->N * sizeof(double);
+        LM_CUDA(s->partials.ensure(bytes), "allocating split partial sums");
+        a.partials = s->partials.as<double>();
+    }
+    if (s->prof_on) {
+        while (s->prof_ev.size() < 2 * (s->prof_used + 1)) {
+            cudaEvent_t e;
+            LM_CUDA(cudaEventCreate(&e), "profiling event");
+            s->prof_ev.push_back(e);
+        }
+        a.ev_begin = s->prof_ev[2 * s->prof_used];
+        a.ev_end = s->prof_ev[2 * s->prof_used + 1];
+        s->prof_used += 1;
+        s->prof_pairs += (double)s->N * (double)s->N;
+    }
+    LM_CUDA(lmk::launch_mdot(a, s->stream), "mobility product kernel");
+    return LM_OK;
+}
+
+lm_status check_solver(lm_solver* s, bool need_pos) {
+    if (s == nullptr) return fail(LM_ERR_INVALID_ARG, "solver is NULL");
+    if (need_pos && !s->has_pos) return fail(LM_ERR_STATE, "positions not set (call lm_set_positions first)");
+    return LM_OK;
+}
+
+bool valid_name(const char* p) {
+    return p && (!strcmp(p, "open") || !strcmp(p, "periodic") || !strcmp(p, "single_wall") ||
+                 !strcmp(p, "two_walls"));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lm_last_error(void) { return g_err.c_str(); }
+
+const char* lm_version(void) { return "lm-gb300 0.1 (sm_103a)"; }
+
+int64_t lm_launch_count(lm_solver* solver) {
+    (void)solver;
+    return g_launches.load(std::memory_order_relaxed);
+}
+
+lm_status lm_create(lm_solver** out, const char* px, const char* py, const char* pz, double viscosity,
+                    double hydrodynamic_radius, int include_angular, lm_precision precision, void* cuda_stream) {
+    g_err.clear();
+    if (out == nullptr) return fail(LM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!valid_name(px) || !valid_name(py) || !valid_name(pz))
+        return fail(LM_ERR_INVALID_ARG, "periodicity must be one of open, periodic, single_wall, two_walls");
+    if (strcmp(px, "open") || strcmp(py, "open") || strcmp(pz, "open"))
+        return fail(LM_ERR_UNSUPPORTED_GEOMETRY, "only open boundaries (\"open\", \"open\", \"open\") are supported");
+    if (!(viscosity > 0.0) || !std::isfinite(viscosity)) return fail(LM_ERR_INVALID_ARG, "viscosity must be > 0");
+    if (!(hydrodynamic_radius > 0.0) || !std::isfinite(hydrodynamic_radius))
+        return fail(LM_ERR_INVALID_ARG, "hydrodynamic radius must be > 0");
+    if (precision != LM_FP32C && precision != LM_FP64) return fail(LM_ERR_INVALID_ARG, "unknown precision");
+    lm_solver* s = new (std::nothrow) lm_solver();
+    if (!s) return fail(LM_ERR_OOM, "host allocation failed");
+    s->angular = include_angular ? 1 : 0;
+    s->fp64 = precision == LM_FP64 ? 1 : 0;
+    s->eta = viscosity;
+    s->a = hydrodynamic_radius;
+    s->stream = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device);
+    if (e == cudaSuccess) e = s->flag.ensure(64);
+    if (e == cudaSuccess) {
+        s->pinned_doubles = 64;
+        e = cudaMallocHost(reinterpret_cast<void**>(&s->pinned), s->pinned_doubles * sizeof(double));
+    }
+    if (e != cudaSuccess) {
+        lm_status st = cuda_fail(e, "lm_create");
+        delete s;
+        return st;
+    }
+    *out = s;
+    return LM_OK;
+}
+
+lm_status lm_destroy(lm_solver* solver) {
+    if (solver == nullptr) return LM_OK;
+    DeviceGuard g(solver->device);
+    cudaStreamSynchronize(solver->stream);
+    delete solver;
+    return LM_OK;
+}
+
+lm_status lm_set_stream(lm_solver* solver, void* cuda_stream) {
+    if (lm_status st = check_solver(solver, false)) return st;
+    solver->stream = static_cast<cudaStream_t>(cuda_stream);
+    return LM_OK;
+}
+
+lm_status lm_set_positions(lm_solver* s, const void* pos, int64_t N) {
+    if (lm_status st = check_solver(s, false)) return st;
+    if (pos == nullptr) return fail(LM_ERR_INVALID_ARG, "pos is NULL");
+    if (N < 1) return fail(LM_ERR_INVALID_ARG, "N must be >= 1 (got %lld)", (long long)N);
+    if (N > (int64_t)1 << 31) return fail(LM_ERR_INVALID_ARG, "N too large");
+    DeviceGuard g(s->device);
+    s->has_pos = false;
+    const size_t bytes = (size_t)N * 3 * elem_size(s);
+    const void* dpos = nullptr;
+    if (lm_status st = stage_in(s, pos, bytes, 0, &dpos)) return st;
+    LM_CUDA(s->pos4.ensure((size_t)N * (s->fp64 ? sizeof(lmk::dvec4) : sizeof(float4))), "allocating positions");
+    LM_CUDA(cudaMemsetAsync(s->flag.p, 0, sizeof(int), s->stream), "clearing flag");
+    LM_CUDA(lmk::launch_pack_positions(dpos, s->fp64, N, s->pos4.p, s->fp64, s->flag.as<int>(), s->stream),
+            "packing positions");
+    int bad = 0;
+    LM_CUDA(cudaMemcpyAsync(&s->pinned[0], s->flag.p, sizeof(int), cudaMemcpyDeviceToHost, s->stream),
+            "reading flag");
+    LM_CUDA(cudaStreamSynchronize(s->stream), "set_positions");
+    memcpy(&bad, &s->pinned[0], sizeof(int));
+    if (bad) return fail(LM_ERR_NONFINITE, "positions contain NaN/Inf or |x| > 1e15");
+    s->N = N;
+    s->has_pos = true;
+    return LM_OK;
+}
+
+lm_status lm_mdot(lm_solver* s, const void* forces, const void* torques, void* lin_out, void* ang_out) {
+    if (lm_status st = check_solver(s, true)) return st;
+    if (lin_out == nullptr) return fail(LM_ERR_INVALID_ARG, "lin_out is NULL");
+    if (s->angular && ang_out == nullptr) return fail(LM_ERR_INVALID_ARG, "ang_out is required with angular blocks");
+    if (!s->angular && ang_out != nullptr) return fail(LM_ERR_INVALID_ARG, "ang_out given but include_angular is 0");
+    if (!s->angular && torques != nullptr) return fail(LM_ERR_INVALID_ARG, "torques given but include_angular is 0");
+    DeviceGuard g(s->device);
+    const size_t bytes = (size_t)s->N * 3 * elem_size(s);
+    const void *dF = nullptr, *dT = nullptr;
+    if (lm_status st = stage_in(s, forces, bytes, 1, &dF)) return st;
+    if (lm_status st = stage_in(s, torques, bytes, 2, &dT)) return st;
+    OutView ov[2];
+    if (lm_status st = stage_out(s, lin_out, bytes, 0, &ov[0])) return st;
+    if (lm_status st = stage_out(s, ang_out, bytes, 1, &ov[1])) return st;
+    if (dF == nullptr && dT == nullptr) {
+        LM_CUDA(cudaMemsetAsync(ov[0].dev, 0, bytes, s->stream), "zero output");
+        if (s->angular) LM_CUDA(cudaMemsetAsync(ov[1].dev, 0, bytes, s->stream), "zero output");
+    } else {
+        ensure_config(s);
+        if (lm_status st = run_mdot(s, dF, dT, s->fp64, ov[0].dev, ov[1].dev, s->fp64, s->cfg)) return st;
+    }
+    return finish_out(s, ov, 2);
+}
+
+lm_status lm_div_m(lm_solver* s, void* lin_out, void* ang_out) {
+    if (lm_status st = check_solver(s, true)) return st;
+    if (lin_out == nullptr) return fail(LM_ERR_INVALID_ARG, "lin_out is NULL");
+    if (s->angular && ang_out == nullptr) return fail(LM_ERR_INVALID_ARG, "ang_out is required with angular blocks");
+    if (!s->angular && ang_out != nullptr) return fail(LM_ERR_INVALID_ARG, "ang_out given but include_angular is 0");
+    DeviceGuard g(s->device);
+    const size_t bytes = (size_t)s->N * 3 * elem_size(s);
+    OutView ov[2];
+    if (lm_status st = stage_out(s, lin_out, bytes, 0, &ov[0])) return st;
+    if (lm_status st = stage_out(s, ang_out, bytes, 1, &ov[1])) return st;
+    LM_CUDA(cudaMemsetAsync(ov[0].dev, 0, bytes, s->stream), "zero output");
+    if (s->angular) LM_CUDA(cudaMemsetAsync(ov[1].dev, 0, bytes, s->stream), "zero output");
+    return finish_out(s, ov, 2);
+}
+
+// ---------------------------------------------------------------------------
+// Lanczos square root (Sec. 3.3).  Per iteration k (v_k = row k of V):
+//   w = M v_k;  alpha_k = v_k . w;  w -= alpha_k v_k + beta_{k-1} v_{k-1};
+//   twice: w -= V_k (V_k^T w);  beta_k = |w|;
+//   z_k = |W| f(T_k) e1 (host, implicit QR);  stop if k >= 1 and
+//   |z_k - [z_{k-1}; 0]| / |z_k| < tol, or on breakdown, or at max_iter;
+//   v_{k+1} = w / beta_k.
+// Result: y = V_m z_m, scaled by the prefactor.
+// ---------------------------------------------------------------------------
+lm_status lm_sqrt_mdot(lm_solver* s, const double* W, uint64_t seed, double prefactor, double tol, int max_iter,
+                       void* lin_out, void* ang_out, int* iters_out) {
+    if (lm_status st = check_solver(s, true)) return st;
+    if (lin_out == nullptr) return fail(LM_ERR_INVALID_ARG, "lin_out is NULL");
+    if (s->angular && ang_out == nullptr) return fail(LM_ERR_INVALID_ARG, "ang_out is required with angular blocks");
+    if (!s->angular && ang_out != nullptr) return fail(LM_ERR_INVALID_ARG, "ang_out given but include_angular is 0");
+    if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(LM_ERR_INVALID_ARG, "tol must be finite and >= 0");
+    if (max_iter < 1) return fail(LM_ERR_INVALID_ARG, "max_iter must be >= 1");
+    if (!std::isfinite(prefactor)) return fail(LM_ERR_INVALID_ARG, "prefactor must be finite");
+    DeviceGuard g(s->device);
+    if (iters_out) *iters_out = 0;
+    s->stats = lm_lanczos_stats{0, 0, 0.0, 0.0, 0};
+
+    const int64_t N = s->N;
+    const int64_t n = (s->angular ? 6 : 3) * N;
+    const int m_max = (int)std::min<int64_t>(max_iter, n);
+    const size_t out_bytes = (size_t)N * 3 * elem_size(s);
+    OutView ov[2];
+    if (lm_status st = stage_out(s, lin_out, out_bytes, 0, &ov[0])) return st;
+    if (lm_status st = stage_out(s, ang_out, out_bytes, 1, &ov[1])) return st;
+
+    ensure_config(s);
+    LM_CUDA(s->V.ensure((size_t)m_max * n * sizeof(double)), "allocating Krylov basis");
+    LM_CUDA(s->w.ensure((size_t)n * sizeof(double)), "allocating Lanczos vector");
+    LM_CUDA(s->y.ensure((size_t)n * sizeof(double)), "allocating Lanczos vector");
+    LM_CUDA(s->red.ensure(lmk::lz_red_doubles(n, m_max) * sizeof(double)), "allocating reduction scratch");
+    LM_CUDA(s->scal.ensure((size_t)(4 * (m_max + 2)) * sizeof(double)), "allocating scalars");
+    LM_CUDA(s->zbuf.ensure((size_t)m_max * sizeof(double)), "allocating coefficients");
+    LM_CUDA(s->cbuf.ensure((size_t)m_max * sizeof(double)), "allocating coefficients");
+    double* V = s->V.as<double>();
+    double* w = s->w.as<double>();
+    double* scal = s->scal.as<double>();
+    double* red = s->red.as<double>();
+    double* cb = s->cbuf.as<double>();
+    double* wn = scal + 4 * (m_max + 1);  // |W|, |W|^2
+
+    // W: user array (host or device) or Philox normals
+    const double* dW = nullptr;
+    if (W == nullptr) {
+        LM_CUDA(s->Wbuf.ensure((size_t)n * sizeof(double)), "allocating noise");
+        LM_CUDA(lmk::lz_philox_normals(seed, 0, s->Wbuf.as<double>(), n, s->stream), "noise generator");
+        dW = s->Wbuf.as<double>();
+    } else {
+        const void* p = nullptr;
+        if (lm_status st = stage_in(s, W, (size_t)n * sizeof(double), 3, &p)) return st;
+        dW = static_cast<const double*>(p);
+    }
+    LM_CUDA(lmk::lz_norm(dW, n, red, wn, s->stream), "norm of W");
+    LM_CUDA(cudaMemcpyAsync(s->pinned, wn, sizeof(double), cudaMemcpyDeviceToHost, s->stream), "read |W|");
+    LM_CUDA(cudaStreamSynchronize(s->stream), "lanczos");
+    const double normW = s->pinned[0];
+    s->stats.norm_w = normW;
+    if (!std::isfinite(normW)) return fail(LM_ERR_INVALID_ARG, "W contains NaN or Inf");
+    if (normW == 0.0) {
+        LM_CUDA(cudaMemsetAsync(ov[0].dev, 0, out_bytes, s->stream), "zero output");
+        if (s->angular) LM_CUDA(cudaMemsetAsync(ov[1].dev, 0, out_bytes, s->stream), "zero output");
+        s->stats.converged = 1;
+        return finish_out(s, ov, 2);
+    }
+    LM_CUDA(lmk::lz_scale(dW, wn, V, n, s->stream), "normalise W");
+
+    std::vector<double> alpha, beta, z, zprev, work;
+    alpha.reserve(m_max);
+    beta.reserve(m_max);
+    const double brk_rel = s->fp64 ? 1e-13 : 1e-7;
+    bool converged = false;
+    double rel = 0.0;
+    int clamped = 0;
+    int k = 0;
+    for (k = 0; k < m_max; ++k) {
+        double* vk = V + (int64_t)k * n;
+        if (lm_status st = run_mdot(s, vk, vk + 3 * N, 1, w, w + 3 * N, 1, s->cfg)) return st;
+        LM_CUDA(lmk::lz_dot(vk, w, n, red, scal + 4 * k, s->stream), "alpha");
+        LM_CUDA(lmk::lz_axpy2(w, vk, scal + 4 * k, k > 0 ? vk - n : nullptr, k > 0 ? scal + 4 * (k - 1) + 1 : nullptr,
+                              n, s->stream),
+                "three-term update");
+        for (int pass = 0; pass < 2; ++pass) {
+            LM_CUDA(lmk::lz_multidot(V, k + 1, w, n, red, cb, s->stream), "reorthogonalisation");
+            LM_CUDA(lmk::lz_sub_vc(V, k + 1, cb, w, n, s->stream), "reorthogonalisation");
+        }
+        LM_CUDA(lmk::lz_norm(w, n, red, scal + 4 * k + 1, s->stream), "beta");
+        LM_CUDA(cudaMemcpyAsync(s->pinned, scal + 4 * k, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream),
+                "read alpha, beta");
+        LM_CUDA(cudaStreamSynchronize(s->stream), "lanczos iteration");
+        const double a_k = s->pinned[0];
+        const double b_k = s->pinned[1];
+        if (!std::isfinite(a_k) || !std::isfinite(b_k))
+            return fail(LM_ERR_CUDA, "Lanczos produced a non-finite coefficient at iteration %d", k + 1);
+        alpha.push_back(a_k);
+        const int m = k + 1;
+        z.assign(m, 0.0);
+        work.assign((size_t)m * m + 2 * m, 0.0);
+        int ncl = 0;
+        if (lmk::tridiag_sqrt_e1(m, alpha.data(), beta.data(), work.data(), z.data(), &ncl) != 0)
+            return fail(LM_ERR_NOT_CONVERGED, "tridiagonal eigensolver did not converge");
+        clamped = ncl;
+        for (double& v : z) v *= normW;
+        if (k >= 1) {
+            double dn = 0.0, zn = 0.0;
+            for (int i = 0; i < m; ++i) {
+                const double d = z[i] - (i < m - 1 ? zprev[i] : 0.0);
+                dn += d * d;
+                zn += z[i] * z[i];
+            }
+            rel = (zn > 0.0) ? std::sqrt(dn / zn) : 0.0;
+            if (rel < tol) { converged = true; break; }
+        }
+        double amax = 0.0;
+        for (double v : alpha) amax = std::max(amax, std::fabs(v));
+        if (b_k <= brk_rel * amax) { converged = true; break; }
+        if (k + 1 == m_max) break;
+        beta.push_back(b_k);
+        LM_CUDA(lmk::lz_scale(w, scal + 4 * k + 1, V + (int64_t)(k + 1) * n, n, s->stream), "next basis vector");
+        zprev = z;
+    }
+    const int m = std::min(k + 1, m_max);
+    LM_CUDA(cudaMemcpyAsync(s->zbuf.p, z.data(), (size_t)m * sizeof(double), cudaMemcpyHostToDevice, s->stream),
+            "coefficients to device");
+    LM_CUDA(lmk::lz_combine(V, m, s->zbuf.as<double>(), s->y.as<double>(), n, s->stream), "combine basis");
+    LM_CUDA(lmk::lz_store(s->y.as<double>(), prefactor, N, s->angular, ov[0].dev, ov[1].dev, s->fp64, s->stream),
+            "store result");
+    // z lives in host memory read by the copy above: wait before it goes out of scope
+    LM_CUDA(cudaStreamSynchronize(s->stream), "lanczos result");
+    s->stats.iterations = m;
+    s->stats.converged = converged ? 1 : 0;
+    s->stats.rel_change = rel;
+    s->stats.clamped_eigs = clamped;
+    if (iters_out) *iters_out = m;
+    if (lm_status st = finish_out(s, ov, 2)) return st;
+    if (!converged)
+        return fail(LM_ERR_NOT_CONVERGED, "Lanczos did not reach tol %.3g in %d iterations (last change %.3g)", tol,
+                    m, rel);
+    return LM_OK;
+}
+
+lm_status lm_get_lanczos_stats(lm_solver* s, lm_lanczos_stats* stats) {
+    if (lm_status st = check_solver(s, false)) return st;
+    if (stats == nullptr) return fail(LM_ERR_INVALID_ARG, "stats is NULL");
+    *stats = s->stats;
+    return LM_OK;
+}
+
+lm_status lm_mdot_backward(lm_solver* s, const void* forces, const void* torques, const void* grad_lin,
+                           const void* grad_ang, void* dX, void* dF, void* dT) {
+    if (lm_status st = check_solver(s, true)) return st;
+    if (forces == nullptr || grad_lin == nullptr) return fail(LM_ERR_INVALID_ARG, "forces and grad_lin are required");
+    if (!s->angular && (torques != nullptr || grad_ang != nullptr || dT != nullptr))
+        return fail(LM_ERR_INVALID_ARG, "torque arguments given but include_angular is 0");
+    DeviceGuard g(s->device);
+    const size_t bytes = (size_t)s->N * 3 * elem_size(s);
+    const void *pF = nullptr, *pT = nullptr, *pG = nullptr, *pH = nullptr;
+    if (lm_status st = stage_in(s, forces, bytes, 0, &pF)) return st;
+    if (lm_status st = stage_in(s, torques, bytes, 1, &pT)) return st;
+    if (lm_status st = stage_in(s, grad_lin, bytes, 2, &pG)) return st;
+    if (lm_status st = stage_in(s, grad_ang, bytes, 3, &pH)) return st;
+    OutView ov[3];
+    if (lm_status st = stage_out(s, dX, bytes, 0, &ov[0])) return st;
+    if (lm_status st = stage_out(s, dF, bytes, 1, &ov[1])) return st;
+    if (lm_status st = stage_out(s, dT, bytes, 2, &ov[2])) return st;
+    if (dX == nullptr && dF == nullptr && dT == nullptr) return LM_OK;
+    if (s->adj_cfg_N != s->N) {
+        lm_pair_config c{128, 1, 1};
+        int slots = 4 * s->sm_count;
+        c.splits = auto_splits(s->N, c.threads, 1, slots);
+        s->adj_cfg = c;
+        s->adj_cfg_N = s->N;
+    }
+    lmk::AdjointArgs a;
+    a.fp64 = s->fp64;
+    a.angular = s->angular;
+    a.N = s->N;
+    a.pos4 = s->pos4.p;
+    a.F = pF; a.T = pT; a.G = pG; a.H = pH;
+    a.dX = ov[0].dev; a.dF = ov[1].dev; a.dT = ov[2].dev;
+    a.a = s->a;
+    a.eta = s->eta;
+    a.threads = s->adj_cfg.threads;
+    a.splits = s->adj_cfg.splits;
+    a.partials = nullptr;
+    const int64_t se = lmk::mdot_effective_splits(s->N, a.threads, a.splits);
+    if (se > 1) {
+        const size_t pb = (size_t)se * lmk::adjoint_partial_components(s->angular) * (size_t)s->N * sizeof(double);
+        LM_CUDA(s->partials.ensure(pb), "allocating split partial sums");
+        a.partials = s->partials.as<double>();
+    }
+    LM_CUDA(lmk::launch_adjoint(a, s->stream), "adjoint kernel");
+    return finish_out(s, ov, 3);
+}
+
+lm_status lm_get_pair_config(lm_solver* s, lm_pair_config* cfg) {
+    if (lm_status st = check_solver(s, true)) return st;
+    if (cfg == nullptr) return fail(LM_ERR_INVALID_ARG, "cfg is NULL");
+    ensure_config(s);
+    *cfg = s->cfg;
+    return LM_OK;
+}
+
+lm_status lm_set_pair_config(lm_solver* s, const lm_pair_config* cfg) {
+    if (lm_status st = check_solver(s, false)) return st;
+    if (cfg == nullptr) return fail(LM_ERR_INVALID_ARG, "cfg is NULL");
+    if (!lmk::mdot_config_supported(s->fp64, s->angular, cfg->threads, cfg->ilp) || cfg->splits < 0)
+        return fail(LM_ERR_INVALID_ARG, "unsupported pair configuration (threads %d, ilp %d, splits %d)", cfg->threads,
+                    cfg->ilp, cfg->splits);
+    s->cfg = *cfg;
+    if (s->cfg.splits == 0) {
+        int occ = std::max(1, lmk::mdot_ctas_per_sm(s->fp64, s->angular, cfg->threads, cfg->ilp));
+        s->cfg.splits = s->has_pos ? auto_splits(s->N, cfg->threads, cfg->ilp, occ * s->sm_count) : 1;
+    }
+    s->cfg_forced = true;
+    s->cfg_N = s->has_pos ? s->N : -1;
+    return LM_OK;
+}
+
+lm_status lm_autotune(lm_solver* s, int reps, lm_pair_config* best) {
+    if (lm_status st = check_solver(s, true)) return st;
+    if (reps < 1) return fail(LM_ERR_INVALID_ARG, "reps must be >= 1");
+    DeviceGuard g(s->device);
+    const int64_t N = s->N;
+    const size_t bytes = (size_t)N * 3 * elem_size(s);
+    LM_CUDA(s->tune_in.ensure(2 * bytes), "autotune buffers");
+    LM_CUDA(s->tune_out.ensure(2 * bytes), "autotune buffers");
+    LM_CUDA(cudaMemsetAsync(s->tune_in.p, 0, 2 * bytes, s->stream), "autotune buffers");
+    char* fin = s->tune_in.as<char>();
+    char* fout = s->tune_out.as<char>();
+    std::vector<lm_pair_config> cands;
+    const int threads_opts[2] = {128, 256};
+    const int ilp_opts[3] = {1, 2, 4};
+    for (int t : threads_opts) {
+        for (int il : ilp_opts) {
+            if (!lmk::mdot_config_supported(s->fp64, s->angular, t, il)) continue;
+            const int occ = lmk::mdot_ctas_per_sm(s->fp64, s->angular, t, il);
+            if (occ < 1) continue;
+            const int sa = auto_splits(N, t, il, occ * s->sm_count);
+            int opts[3] = {sa, std::max(1, sa / 2), sa * 2};
+            for (int k = 0; k < 3; ++k) {
+                if (k > 0 && opts[k] == sa) continue;
+                if (k == 2 && opts[2] == opts[1]) continue;
+                cands.push_back(lm_pair_config{t, il, opts[k]});
+            }
+        }
+    }
+    cudaEvent_t e0, e1;
+    LM_CUDA(cudaEventCreate(&e0), "autotune events");
+    LM_CUDA(cudaEventCreate(&e1), "autotune events");
+    float best_ms = 1e30f;
+    lm_pair_config best_cfg = default_config(s, N);
+    lm_status result = LM_OK;
+    for (const lm_pair_config& c : cands) {
+        // warm-up
+        if ((result = run_mdot(s, fin, fin + bytes, s->fp64, fout, fout + bytes, s->fp64, c)) != LM_OK) break;
+        cudaEventRecord(e0, s->stream);
+        for (int r = 0; r < reps; ++r)
+            if ((result = run_mdot(s, fin, fin + bytes, s->fp64, fout, fout + bytes, s->fp64, c)) != LM_OK) break;
+        if (result != LM_OK) break;
+        cudaEventRecord(e1, s->stream);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) { result = cuda_fail(e, "autotune"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best_cfg = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (result != LM_OK) return result;
+    s->cfg = best_cfg;
+    s->cfg_forced = true;
+    s->cfg_N = N;
+    if (best) *best = best_cfg;
+    return LM_OK;
+}
+
+lm_status lm_profile_enable(lm_solver* s, int enable) {
+    if (lm_status st = check_solver(s, false)) return st;
+    s->prof_on = enable != 0;
+    return LM_OK;
+}
+
+lm_status lm_profile_read(lm_solver* s, lm_profile* out, int reset) {
+    if (lm_status st = check_solver(s, false)) return st;
+    if (out == nullptr) return fail(LM_ERR_INVALID_ARG, "out is NULL");
+    DeviceGuard g(s->device);
+    LM_CUDA(cudaStreamSynchronize(s->stream), "profile read");
+    double ms = 0.0;
+    for (size_t k = 0; k < s->prof_used; ++k) {
+        float t = 0.f;
+        LM_CUDA(cudaEventElapsedTime(&t, s->prof_ev[2 * k], s->prof_ev[2 * k + 1]), "profile read");
+        ms += t;
+    }
+    out->pair_launches = (int64_t)s->prof_used;
+    out->pair_ms = ms;
+    out->pair_interactions = s->prof_pairs;
+    out->pair_flops = s->prof_pairs * (s->angular ? lmk::kFlopsPerPair6N : lmk::kFlopsPerPairTT);
+    if (reset) {
+        s->prof_used = 0;
+        s->prof_pairs = 0.0;
+    }
+    return LM_OK;
+}
+
+// Host-only helper exposed for testing the tridiagonal step on the CPU:
+// out = f(T) e1, f = sqrt, for T = tridiag(beta, alpha, beta) of size m.
+int lm_tridiag_sqrt_e1(int m, const double* alpha, const double* beta, double* out) {
+    if (m < 1 || !alpha || !out || (m > 1 && !beta)) return -2;
+    std::vector<double> work((size_t)m * m + 2 * m);
+    int cl = 0;
+    return lmk::tridiag_sqrt_e1(m, alpha, beta, work.data(), out, &cl);
+}
+
+}  // extern "C"

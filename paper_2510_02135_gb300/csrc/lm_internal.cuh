@@ -1,0 +1,150 @@
+// Internal interfaces between the library's translation units.
+// Kernels live in pair_kernels.cu, adjoint_kernels.cu, lanczos_kernels.cu and
+// batch_kernels.cu; the C ABI and the solver state live in lm_api.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace lmk {
+
+// Packed FP64 position / vector slot (x, y, z, pad), 32-byte aligned.
+struct __align__(32) dvec4 {
+    double x, y, z, w;
+};
+
+// Kernel launches issued by the library (all solvers, all threads).
+void count_launches(int n);
+
+// Algorithmic work per ordered pair (far-field formula, FMA = 2 flops),
+// frozen for the roofline figures: translation only, and all four blocks.
+constexpr double kFlopsPerPairTT = 35.0;
+constexpr double kFlopsPerPair6N = 86.0;
+
+// Constants of the RPY pair blocks for radius a, in units of 1/(8 pi eta).
+// Far field (r >= 2a), d = x_i - x_j, F the force and T the torque on j:
+//   u_i += A F + B (d.F) d + g (T x d)
+//   w_i += g (F x d) + ar T + br (d.T) d
+//   A = 1/r + K1/r^3, B = 1/r^3 - K2/r^5, g = 1/r^3, ar = -1/(2 r^3), br = 3/(2 r^5)
+// Overlap (r < 2a), s = r / a:
+//   A = (4/(3a)) (1 - 9 s / 32),        B = 1 / (8 a^2 r)
+//   g = (1/(2 a^3)) (1 - 3 s / 8),
+//   ar = (1/a^3) (1 - 27 s/32 + 5 s^3/64),  br = (1/a^3) (9/(32 a r) - 3 r/(64 a^3))
+// The results are multiplied by 1/(8 pi eta) once per particle.
+template <typename R>
+struct RpyConst {
+    R four_a2;  // (2a)^2
+    R K1;       // 2a^2/3
+    R K2;       // 2a^2
+    R nA0;      // 4/(3a)
+    R nA1;      // 3/(8a^2)
+    R nB;       // 1/(8a^2)
+    R ng0;      // 1/(2a^3)
+    R ng1;      // 3/(16a^4)
+    R inv_a3;   // 1/a^3
+    R rr1;      // 27/(32a)
+    R rr3;      // 5/(64a^3)
+    R rrb0;     // 9/(32a)
+    R rrb1;     // 3/(64a^3)
+};
+
+template <typename R>
+inline RpyConst<R> make_rpy_const(double a) {
+    RpyConst<R> k;
+    k.four_a2 = (R)(4.0 * a * a);
+    k.K1 = (R)(2.0 * a * a / 3.0);
+    k.K2 = (R)(2.0 * a * a);
+    k.nA0 = (R)(4.0 / (3.0 * a));
+    k.nA1 = (R)(3.0 / (8.0 * a * a));
+    k.nB = (R)(1.0 / (8.0 * a * a));
+    k.ng0 = (R)(1.0 / (2.0 * a * a * a));
+    k.ng1 = (R)(3.0 / (16.0 * a * a * a * a));
+    k.inv_a3 = (R)(1.0 / (a * a * a));
+    k.rr1 = (R)(27.0 / (32.0 * a));
+    k.rr3 = (R)(5.0 / (64.0 * a * a * a));
+    k.rrb0 = (R)(9.0 / (32.0 * a));
+    k.rrb1 = (R)(3.0 / (64.0 * a * a * a));
+    return k;
+}
+
+// Positions are packed as (x, y, z, 0) float4 (FP32C) or double4 (FP64).
+// Padding coordinate for unused tile slots: far from any admissible particle.
+constexpr double kPadCoord = 1.0e18;
+constexpr double kMaxAbsCoord = 1.0e15;
+
+// One mobility product on the packed positions.
+struct MdotArgs {
+    int fp64;              // 0: FP32 pairs with compensated sums, 1: FP64
+    int angular;           // 0: 3N (forces only), 1: 6N
+    int64_t N;
+    const void* pos4;      // packed positions
+    const void* F;         // N x 3 (nullable = zero)
+    const void* T;         // N x 3 (nullable = zero; ignored without angular)
+    int in_f64;            // element type of F, T
+    void* lin;             // N x 3
+    void* ang;             // N x 3 (angular only)
+    int out_f64;           // element type of lin, ang
+    double a, eta;
+    int threads, ilp, splits;
+    double* partials;      // splits * (3 or 6) * N doubles when splits > 1
+    cudaEvent_t ev_begin = nullptr;   // recorded right before / after the pair
+    cudaEvent_t ev_end = nullptr;     // kernel when non-null (profiling)
+};
+
+// Backward (adjoint) product.
+struct AdjointArgs {
+    int fp64;
+    int angular;
+    int64_t N;
+    const void* pos4;
+    const void* F; const void* T;     // forward inputs
+    const void* G; const void* H;     // cotangents of lin, ang
+    void* dX; void* dF; void* dT;     // outputs (nullable dX / dF)
+    double a, eta;
+    int threads, splits;
+    double* partials;                 // splits * (3 + 3 or 6) * N doubles when splits > 1
+};
+
+// Launch-configuration tables (pair_kernels.cu / adjoint_kernels.cu).
+bool mdot_config_supported(int fp64, int angular, int threads, int ilp);
+int mdot_ctas_per_sm(int fp64, int angular, int threads, int ilp);
+// Number of j-splits actually launched for a requested split count.
+int64_t mdot_effective_splits(int64_t N, int threads, int splits);
+int mdot_partial_components(int angular);
+cudaError_t launch_mdot(const MdotArgs& a, cudaStream_t s);
+cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s);
+int adjoint_partial_components(int angular);
+
+// Pack N x 3 positions into (x, y, z, 0) and flag non-finite or too large
+// coordinates in *bad (device int, set to 1).
+cudaError_t launch_pack_positions(const void* pos, int in_f64, int64_t N, void* pos4, int out_f64,
+                                  int* bad, cudaStream_t s);
+
+// Lanczos vector kernels (lanczos_kernels.cu).  All vectors are FP64 of
+// length n; the basis V is row-major (row j = v_j, stride n).  Reductions are
+// two-stage and deterministic; `red` is scratch of lz_red_doubles(n, m).
+size_t lz_red_doubles(int64_t n, int m);
+cudaError_t lz_dot(const double* x, const double* y, int64_t n, double* red, double* out, cudaStream_t s);
+// out[0] = |x|, out[1] = |x|^2
+cudaError_t lz_norm(const double* x, int64_t n, double* red, double* out, cudaStream_t s);
+// w -= alpha[0] vk + beta[0] vkm1   (vkm1 / beta nullable)
+cudaError_t lz_axpy2(double* w, const double* vk, const double* alpha, const double* vkm1,
+                     const double* beta, int64_t n, cudaStream_t s);
+// c[j] = v_j . w for j < m
+cudaError_t lz_multidot(const double* V, int m, const double* w, int64_t n, double* red, double* c,
+                        cudaStream_t s);
+// w -= sum_j c[j] v_j
+cudaError_t lz_sub_vc(const double* V, int m, const double* c, double* w, int64_t n, cudaStream_t s);
+// y = x / nrm[0]
+cudaError_t lz_scale(const double* x, const double* nrm, double* y, int64_t n, cudaStream_t s);
+// y = sum_j z[j] v_j
+cudaError_t lz_combine(const double* V, int m, const double* z, double* y, int64_t n, cudaStream_t s);
+// lin / ang (float or double) = scale * y, lin from y[0, 3N), ang from y[3N, 6N)
+cudaError_t lz_store(const double* y, double scale, int64_t N, int angular, void* lin, void* ang, int out_f64,
+                     cudaStream_t s);
+// W from Philox-4x32-10: element e is normal number (e % 4) of block q = e / 4,
+// counter (q low, q high, stream low, stream high), key (seed low, seed high),
+// two Box-Muller pairs from the words (0, 1) and (2, 3).
+cudaError_t lz_philox_normals(uint64_t seed, uint64_t stream, double* W, int64_t n, cudaStream_t s);
+
+}  // namespace lmk

@@ -1,0 +1,407 @@
+"""Python binding of the C ABI in ``include/lm.h`` (ctypes; marshalling only).
+
+Every function keeps the name of the C entry point it calls.  Arrays may be
+torch tensors (CUDA or CPU) or numpy arrays; their data pointers are passed
+as they are, and the library copies host arrays to and from the GPU itself
+(libMobility paper, Sec. 3.2).  Outputs are allocated with the same kind
+(device tensor, host tensor or numpy array) as the first array argument.
+Calls on CUDA tensors run on torch's current stream.
+
+All arithmetic happens in the CUDA library; if the shared object is missing
+this module raises instead of computing anything itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblm_gb300.so")
+
+LM_OK = 0
+LM_ERR_INVALID_ARG = 1
+LM_ERR_UNSUPPORTED_GEOMETRY = 2
+LM_ERR_STATE = 3
+LM_ERR_NONFINITE = 4
+LM_ERR_NOT_CONVERGED = 5
+LM_ERR_TIMEOUT = 6
+LM_ERR_OOM = 7
+LM_ERR_CUDA = 8
+LM_FP32C = 0
+LM_FP64 = 1
+
+_STATUS_NAMES = {0: "LM_OK", 1: "LM_ERR_INVALID_ARG", 2: "LM_ERR_UNSUPPORTED_GEOMETRY", 3: "LM_ERR_STATE",
+                 4: "LM_ERR_NONFINITE", 5: "LM_ERR_NOT_CONVERGED", 6: "LM_ERR_TIMEOUT", 7: "LM_ERR_OOM",
+                 8: "LM_ERR_CUDA"}
+
+
+class LmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class lm_pair_config(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int), ("ilp", ctypes.c_int), ("splits", ctypes.c_int)]
+
+
+class lm_lanczos_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("rel_change", ctypes.c_double),
+                ("norm_w", ctypes.c_double), ("clamped_eigs", ctypes.c_int)]
+
+
+class lm_profile(ctypes.Structure):
+    _fields_ = [("pair_launches", ctypes.c_int64), ("pair_ms", ctypes.c_double),
+                ("pair_interactions", ctypes.c_double), ("pair_flops", ctypes.c_double)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def lib():
+    """Load the shared library (built by ``_build.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2510_02135_gb300._build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        st = ctypes.c_int
+        L.lm_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, _vp]
+        L.lm_create.restype = st
+        L.lm_destroy.argtypes = [_vp]
+        L.lm_destroy.restype = st
+        L.lm_set_stream.argtypes = [_vp, _vp]
+        L.lm_set_stream.restype = st
+        L.lm_set_positions.argtypes = [_vp, _vp, ctypes.c_int64]
+        L.lm_set_positions.restype = st
+        L.lm_mdot.argtypes = [_vp, _vp, _vp, _vp, _vp]
+        L.lm_mdot.restype = st
+        L.lm_sqrt_mdot.argtypes = [_vp, _vp, ctypes.c_uint64, ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp,
+                                   _vp, ctypes.POINTER(ctypes.c_int)]
+        L.lm_sqrt_mdot.restype = st
+        L.lm_div_m.argtypes = [_vp, _vp, _vp]
+        L.lm_div_m.restype = st
+        L.lm_mdot_backward.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.lm_mdot_backward.restype = st
+        L.lm_get_pair_config.argtypes = [_vp, ctypes.POINTER(lm_pair_config)]
+        L.lm_get_pair_config.restype = st
+        L.lm_set_pair_config.argtypes = [_vp, ctypes.POINTER(lm_pair_config)]
+        L.lm_set_pair_config.restype = st
+        L.lm_autotune.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(lm_pair_config)]
+        L.lm_autotune.restype = st
+        L.lm_get_lanczos_stats.argtypes = [_vp, ctypes.POINTER(lm_lanczos_stats)]
+        L.lm_get_lanczos_stats.restype = st
+        L.lm_profile_enable.argtypes = [_vp, ctypes.c_int]
+        L.lm_profile_enable.restype = st
+        L.lm_profile_read.argtypes = [_vp, ctypes.POINTER(lm_profile), ctypes.c_int]
+        L.lm_profile_read.restype = st
+        L.lm_launch_count.argtypes = [_vp]
+        L.lm_launch_count.restype = ctypes.c_int64
+        L.lm_last_error.argtypes = []
+        L.lm_last_error.restype = ctypes.c_char_p
+        L.lm_version.argtypes = []
+        L.lm_version.restype = ctypes.c_char_p
+        L.lm_tridiag_sqrt_e1.argtypes = [ctypes.c_int, _vp, _vp, _vp]
+        L.lm_tridiag_sqrt_e1.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != LM_OK:
+        raise LmError(status, lib().lm_last_error().decode(errors="replace"))
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _is_tensor(x) -> bool:
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        return False
+    return isinstance(x, torch.Tensor)
+
+
+def _ptr(x, dtype_f64: bool, n_elems: int | None, name: str):
+    """Data pointer of a contiguous array of the solver's dtype (or None)."""
+    if x is None:
+        return None
+    if _is_tensor(x):
+        torch = _torch()
+        want = torch.float64 if dtype_f64 else torch.float32
+        if x.dtype != want:
+            raise TypeError(f"{name}: expected {want}, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError(f"{name}: tensor must be contiguous")
+        if n_elems is not None and x.numel() != n_elems:
+            raise ValueError(f"{name}: expected {n_elems} elements, got {x.numel()}")
+        return x.data_ptr()
+    a = x
+    if not isinstance(a, np.ndarray):
+        raise TypeError(f"{name}: expected a torch tensor or numpy array")
+    want = np.float64 if dtype_f64 else np.float32
+    if a.dtype != want:
+        raise TypeError(f"{name}: expected {np.dtype(want)}, got {a.dtype}")
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"{name}: array must be C-contiguous")
+    if n_elems is not None and a.size != n_elems:
+        raise ValueError(f"{name}: expected {n_elems} elements, got {a.size}")
+    return a.ctypes.data
+
+
+def _like(ref, shape, f64: bool):
+    """Allocate an output of the same kind as ``ref``."""
+    if _is_tensor(ref):
+        torch = _torch()
+        return torch.empty(shape, dtype=torch.float64 if f64 else torch.float32, device=ref.device)
+    return np.empty(shape, dtype=np.float64 if f64 else np.float32)
+
+
+def _current_stream(*arrays):
+    for a in arrays:
+        if _is_tensor(a) and a.is_cuda:
+            torch = _torch()
+            return torch.cuda.current_stream(a.device).cuda_stream
+    return None
+
+
+class Solver:
+    """Handle of an ``lm_solver``; freed with ``lm_destroy`` when collected."""
+
+    def __init__(self, handle: int, eta: float, a: float, angular: bool, precision: int):
+        self.handle = ctypes.c_void_p(handle)
+        self.eta = eta
+        self.a = a
+        self.angular = bool(angular)
+        self.precision = precision
+        self.f64 = precision == LM_FP64
+        self.N = 0
+        self._stream = None
+
+    def _sync_stream(self, *arrays):
+        s = _current_stream(*arrays)
+        if s is not None and s != self._stream:
+            _check(lib().lm_set_stream(self.handle, s))
+            self._stream = s
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.lm_destroy(h)
+            self.handle = None
+
+
+def lm_create(viscosity: float, hydrodynamic_radius: float, include_angular: bool = False,
+              precision: int = LM_FP32C, periodicity=("open", "open", "open"), cuda_stream: int | None = None
+              ) -> Solver:
+    h = ctypes.c_void_p()
+    px, py, pz = (p.encode() for p in periodicity)
+    _check(lib().lm_create(ctypes.byref(h), px, py, pz, float(viscosity), float(hydrodynamic_radius),
+                           int(bool(include_angular)), int(precision), cuda_stream))
+    s = Solver(h.value, viscosity, hydrodynamic_radius, include_angular, precision)
+    s._stream = cuda_stream
+    return s
+
+
+def lm_set_positions(s: Solver, pos) -> None:
+    n = (pos.numel() if _is_tensor(pos) else np.asarray(pos).size) // 3
+    s._sync_stream(pos)
+    _check(lib().lm_set_positions(s.handle, _ptr(pos, s.f64, 3 * n, "pos"), n))
+    s.N = n
+
+
+def lm_mdot(s: Solver, forces=None, torques=None, lin_out=None, ang_out=None):
+    """[lin; ang] = M [F; T].  Returns (lin, ang); ang is None without angular blocks."""
+    ref = forces if forces is not None else torques
+    if lin_out is None:
+        if ref is None:
+            raise ValueError("give forces, torques or lin_out")
+        lin_out = _like(ref, (s.N, 3), s.f64)
+    if s.angular and ang_out is None:
+        ang_out = _like(ref if ref is not None else lin_out, (s.N, 3), s.f64)
+    s._sync_stream(forces, torques, lin_out, ang_out)
+    n3 = 3 * s.N
+    _check(lib().lm_mdot(s.handle, _ptr(forces, s.f64, n3, "forces"), _ptr(torques, s.f64, n3, "torques"),
+                         _ptr(lin_out, s.f64, n3, "lin_out"), _ptr(ang_out, s.f64, n3, "ang_out")))
+    return lin_out, ang_out
+
+
+def lm_sqrt_mdot(s: Solver, W=None, seed: int = 0, prefactor: float = 1.0, tol: float = 1e-5,
+                 max_iter: int = 200, lin_out=None, ang_out=None, like=None, raise_not_converged: bool = True):
+    """[lin; ang] = prefactor * M^{1/2} W (Lanczos).  Returns (lin, ang, iterations)."""
+    ref = W if W is not None else (lin_out if lin_out is not None else like)
+    if ref is None:
+        raise ValueError("give W, lin_out or like= to choose where outputs live")
+    if lin_out is None:
+        lin_out = _like(ref, (s.N, 3), s.f64)
+    if s.angular and ang_out is None:
+        ang_out = _like(ref, (s.N, 3), s.f64)
+    s._sync_stream(W, lin_out, ang_out)
+    n3 = 3 * s.N
+    it = ctypes.c_int(0)
+    wptr = _ptr(W, True, (6 if s.angular else 3) * s.N, "W")
+    st = lib().lm_sqrt_mdot(s.handle, wptr, int(seed), float(prefactor), float(tol), int(max_iter),
+                            _ptr(lin_out, s.f64, n3, "lin_out"), _ptr(ang_out, s.f64, n3, "ang_out"),
+                            ctypes.byref(it))
+    if st != LM_OK and (raise_not_converged or st != LM_ERR_NOT_CONVERGED):
+        _check(st)
+    return lin_out, ang_out, it.value
+
+
+def lm_div_m(s: Solver, like):
+    lin = _like(like, (s.N, 3), s.f64)
+    ang = _like(like, (s.N, 3), s.f64) if s.angular else None
+    s._sync_stream(lin, ang)
+    n3 = 3 * s.N
+    _check(lib().lm_div_m(s.handle, _ptr(lin, s.f64, n3, "lin"), _ptr(ang, s.f64, n3, "ang")))
+    return lin, ang
+
+
+def lm_mdot_backward(s: Solver, forces, torques, grad_lin, grad_ang, need_dX: bool = True, need_dF: bool = True):
+    """Adjoint of lm_mdot.  Returns (dX, dF, dT)."""
+    dX = _like(forces, (s.N, 3), s.f64) if need_dX else None
+    dF = _like(forces, (s.N, 3), s.f64) if need_dF else None
+    dT = _like(forces, (s.N, 3), s.f64) if (s.angular and need_dF) else None
+    s._sync_stream(forces, torques, grad_lin, grad_ang, dX, dF, dT)
+    n3 = 3 * s.N
+    _check(lib().lm_mdot_backward(s.handle, _ptr(forces, s.f64, n3, "forces"), _ptr(torques, s.f64, n3, "torques"),
+                                  _ptr(grad_lin, s.f64, n3, "grad_lin"), _ptr(grad_ang, s.f64, n3, "grad_ang"),
+                                  _ptr(dX, s.f64, n3, "dX"), _ptr(dF, s.f64, n3, "dF"), _ptr(dT, s.f64, n3, "dT")))
+    return dX, dF, dT
+
+
+def lm_get_pair_config(s: Solver) -> dict:
+    c = lm_pair_config()
+    _check(lib().lm_get_pair_config(s.handle, ctypes.byref(c)))
+    return {"threads": c.threads, "ilp": c.ilp, "splits": c.splits}
+
+
+def lm_set_pair_config(s: Solver, threads: int, ilp: int, splits: int = 0) -> None:
+    c = lm_pair_config(threads, ilp, splits)
+    _check(lib().lm_set_pair_config(s.handle, ctypes.byref(c)))
+
+
+def lm_autotune(s: Solver, reps: int = 3) -> dict:
+    c = lm_pair_config()
+    _check(lib().lm_autotune(s.handle, int(reps), ctypes.byref(c)))
+    return {"threads": c.threads, "ilp": c.ilp, "splits": c.splits}
+
+
+def lm_get_lanczos_stats(s: Solver) -> dict:
+    st = lm_lanczos_stats()
+    _check(lib().lm_get_lanczos_stats(s.handle, ctypes.byref(st)))
+    return {"iterations": st.iterations, "converged": bool(st.converged), "rel_change": st.rel_change,
+            "norm_w": st.norm_w, "clamped_eigs": st.clamped_eigs}
+
+
+def lm_profile_enable(s: Solver, enable: bool = True) -> None:
+    _check(lib().lm_profile_enable(s.handle, int(bool(enable))))
+
+
+def lm_profile_read(s: Solver, reset: bool = True) -> dict:
+    p = lm_profile()
+    _check(lib().lm_profile_read(s.handle, ctypes.byref(p), int(bool(reset))))
+    return {"pair_launches": p.pair_launches, "pair_ms": p.pair_ms, "pair_interactions": p.pair_interactions,
+            "pair_flops": p.pair_flops}
+
+
+def lm_launch_count() -> int:
+    return int(lib().lm_launch_count(None))
+
+
+def lm_version() -> str:
+    return lib().lm_version().decode()
+
+
+def lm_tridiag_sqrt_e1(alpha, beta) -> np.ndarray:
+    """Host helper: T^{1/2} e1 for the symmetric tridiagonal T (no GPU)."""
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    out = np.zeros(a.size)
+    rc = lib().lm_tridiag_sqrt_e1(a.size, a.ctypes.data, b.ctypes.data if b.size else None, out.ctypes.data)
+    if rc != 0:
+        raise LmError(LM_ERR_NOT_CONVERGED if rc == -1 else LM_ERR_INVALID_ARG, "tridiagonal square root failed")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Autograd: (X, F, T) -> (u, w) with the fused adjoint as backward.
+# ---------------------------------------------------------------------------
+def _make_function():
+    torch = _torch()
+
+    class MobilityFn(torch.autograd.Function):
+        """u, w = M(X) [F; T] with gradients through X, F and T (lm_mdot / lm_mdot_backward)."""
+
+        @staticmethod
+        def forward(ctx, solver: Solver, X, F, T):
+            X = X.contiguous()
+            F = F.contiguous()
+            T = T.contiguous() if T is not None else None
+            lm_set_positions(solver, X)
+            u, w = lm_mdot(solver, F, T)
+            ctx.solver = solver
+            ctx.save_for_backward(X, F, T if T is not None else F)
+            ctx.has_T = T is not None
+            return (u, w) if solver.angular else (u, torch.zeros(0, device=u.device, dtype=u.dtype))
+
+        @staticmethod
+        def backward(ctx, gu, gw):
+            X, F, T = ctx.saved_tensors
+            s = ctx.solver
+            T = T if ctx.has_T else None
+            lm_set_positions(s, X)
+            gu = gu.contiguous()
+            gw = gw.contiguous() if (s.angular and gw is not None and gw.numel()) else None
+            dX, dF, dT = lm_mdot_backward(s, F, T, gu, gw, need_dX=ctx.needs_input_grad[1],
+                                          need_dF=ctx.needs_input_grad[2] or ctx.needs_input_grad[3])
+            return None, dX, dF, (dT if ctx.has_T else None)
+
+    return MobilityFn
+
+
+_MobilityFn = None
+
+
+def mobility(solver: Solver, X, F, T=None):
+    """Differentiable u, w = M(X) [F; T] on torch tensors (w is None without angular blocks)."""
+    global _MobilityFn
+    if _MobilityFn is None:
+        _MobilityFn = _make_function()
+    u, w = _MobilityFn.apply(solver, X, F, T)
+    return u, (w if solver.angular else None)
+
+
+@dataclass
+class NBody:
+    """The paper's solver interface (Sec. 3.2) over the C ABI: open boundaries."""
+
+    viscosity: float
+    hydrodynamicRadius: float
+    includeAngular: bool = False
+    precision: int = LM_FP32C
+
+    def __post_init__(self):
+        self.solver = lm_create(self.viscosity, self.hydrodynamicRadius, self.includeAngular, self.precision)
+
+    def setPositions(self, pos):
+        lm_set_positions(self.solver, pos)
+
+    def Mdot(self, forces=None, torques=None):
+        return lm_mdot(self.solver, forces, torques)
+
+    def sqrtMdotW(self, W=None, seed=0, prefactor=1.0, tol=1e-5, max_iter=200, like=None):
+        lin, ang, _ = lm_sqrt_mdot(self.solver, W, seed, prefactor, tol, max_iter, like=like)
+        return lin, ang
+
+    def divM(self, like):
+        return lm_div_m(self.solver, like)

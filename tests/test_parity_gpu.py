@@ -1,0 +1,342 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
+
+Tolerances (relative L2 error per output block, |y - y_ref| / |y_ref|):
+  * FP64 path: 1e-12 for M [F; T] (the stated target); the adjoint 1e-11.
+  * FP32 compensated path: 1e-5 for M [F; T] per block (the stated target),
+    with the max-abs error below 1e-4 x RMS(y_ref); the adjoint 1e-5.
+  * Lanczos: against the oracle's Lanczos at the same W and tol, and
+    against the exact eigen-root within 20 x tol (the stopping rule bounds the
+    change of successive iterates, not the error).
+Inputs come from the seeded generators; FP32 workloads use the same
+FP32-rounded values on both sides."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_2510_02135_gb300 import inputs as I  # noqa: E402
+from paper_2510_02135_gb300 import lm  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2510_02135_gb300 import _build
+
+    _build.build()
+
+
+def dev(x):
+    return None if x is None else torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(t):
+    return None if t is None else t.detach().cpu().numpy().astype(np.float64)
+
+
+def rel(y, ref):
+    y = np.asarray(y, dtype=np.float64).ravel()
+    ref = np.asarray(ref, dtype=np.float64).ravel()
+    n = np.linalg.norm(ref)
+    return np.linalg.norm(y - ref) / (n if n > 0 else 1.0)
+
+
+def maxabs_over_rms(y, ref):
+    y = np.asarray(y, dtype=np.float64).ravel()
+    ref = np.asarray(ref, dtype=np.float64).ravel()
+    rms = np.sqrt(np.mean(ref ** 2))
+    return np.abs(y - ref).max() / (rms if rms > 0 else 1.0)
+
+
+def make(eta, a, angular, fp64, pos):
+    s = lm.lm_create(eta, a, angular, lm.LM_FP64 if fp64 else lm.LM_FP32C)
+    lm.lm_set_positions(s, dev(pos))
+    return s
+
+
+def gpu_mdot(s, F, T):
+    u, w = lm.lm_mdot(s, dev(F), dev(T) if s.angular else None,
+                      lin_out=torch.empty((s.N, 3), dtype=torch.float64 if s.f64 else torch.float32, device="cuda"),
+                      ang_out=(torch.empty((s.N, 3), dtype=torch.float64 if s.f64 else torch.float32,
+                                           device="cuda") if s.angular else None))
+    torch.cuda.synchronize()
+    return host(u), host(w)
+
+
+# ---------------------------------------------------------------------------
+# M [F; T]
+# ---------------------------------------------------------------------------
+def test_mdot_fp64_translational_n1024(orc):
+    c = I.RPY_FP64_N1024
+    s_ = I.cube_suspension(c["seed"], c["n"], c["phi"], c["a"], angular=False, fp32=False)
+    s = make(c["eta"], c["a"], False, True, s_.pos)
+    u, _ = gpu_mdot(s, s_.F, None)
+    ur, _ = orc.mdot(s_.pos, s_.F, None, c["a"], c["eta"], False)
+    assert rel(u, ur) <= 1e-12
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_mdot_blocks_match_oracle(orc, fp64):
+    n = 2500  # 19 tiles of 128 and a ragged tail of 68
+    a, eta = 1.0, 1.0
+    s_ = I.cube_suspension(77, n, 0.2, a, angular=True, fp32=not fp64)
+    s = make(eta, a, True, fp64, s_.pos)
+    tol = 1e-12 if fp64 else 1e-5
+    zero = np.zeros_like(s_.F)
+    for name, F, T in (("F", s_.F, zero), ("T", zero, s_.T), ("FT", s_.F, s_.T)):
+        u, w = gpu_mdot(s, F, T)
+        ur, wr = orc.mdot(s_.pos, F, T, a, eta, True)
+        assert rel(u, ur) <= tol, (name, "u", rel(u, ur))
+        assert rel(w, wr) <= tol, (name, "w", rel(w, wr))
+        if not fp64:
+            assert maxabs_over_rms(u, ur) <= 1e-4, (name, maxabs_over_rms(u, ur))
+            assert maxabs_over_rms(w, wr) <= 1e-4, (name, maxabs_over_rms(w, wr))
+
+
+@pytest.mark.parametrize("fp64,angular", [(False, False), (False, True), (True, False), (True, True)])
+def test_mdot_launch_configs_agree(orc, fp64, angular):
+    n = 1100
+    s_ = I.cube_suspension(5, n, 0.15, 1.0, angular=angular, fp32=not fp64)
+    s = make(1.0, 1.0, angular, fp64, s_.pos)
+    ur, wr = orc.mdot(s_.pos, s_.F, s_.T, 1.0, 1.0, angular)
+    tol = 1e-12 if fp64 else 1e-5
+    for threads in (128, 256):
+        for ilp in (1, 2, 4):
+            for splits in (1, 3, 9):
+                lm.lm_set_pair_config(s, threads, ilp, splits)
+                u, w = gpu_mdot(s, s_.F, s_.T)
+                assert rel(u, ur) <= tol, (threads, ilp, splits, rel(u, ur))
+                if angular:
+                    assert rel(w, wr) <= tol, (threads, ilp, splits, rel(w, wr))
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_mdot_edge_cases(orc, fp64):
+    dt = np.float64 if fp64 else np.float32
+    a, eta = 1.3, 0.7
+    rng = np.random.default_rng(3)
+    tol = 1e-12 if fp64 else 1e-6
+    # N = 1: the self mobilities (6 pi eta a)^-1 and (8 pi eta a^3)^-1
+    pos = np.zeros((1, 3), dt) + dt(5.0)
+    F = rng.standard_normal((1, 3)).astype(dt)
+    T = rng.standard_normal((1, 3)).astype(dt)
+    s = make(eta, a, True, fp64, pos)
+    u, w = gpu_mdot(s, F, T)
+    np.testing.assert_allclose(u, F / (6 * np.pi * eta * a), rtol=tol)
+    np.testing.assert_allclose(w, T / (8 * np.pi * eta * a ** 3), rtol=tol)
+    # overlapping pair, coincident pair, pair at exactly 2a, and a ragged N
+    for pos in (np.array([[0, 0, 0], [0.7, 0.2, -0.1]], dt),
+                np.array([[1, 2, 3], [1, 2, 3], [4, 2, 3]], dt),
+                np.array([[0, 0, 0], [2 * a, 0, 0]], dt),
+                rng.uniform(-4, 4, size=(129, 3)).astype(dt),
+                rng.uniform(-4, 4, size=(257, 3)).astype(dt)):
+        n = pos.shape[0]
+        F = rng.standard_normal((n, 3)).astype(dt)
+        T = rng.standard_normal((n, 3)).astype(dt)
+        s = make(eta, a, True, fp64, pos)
+        u, w = gpu_mdot(s, F, T)
+        ur, wr = orc.mdot(pos, F, T, a, eta, True)
+        assert rel(u, ur) <= tol and rel(w, wr) <= tol, (n, rel(u, ur), rel(w, wr))
+        # forces only, torques only, neither
+        u1, w1 = lm.lm_mdot(s, dev(F), None)
+        ur1, wr1 = orc.mdot(pos, F, None, a, eta, True)
+        assert rel(host(u1), ur1) <= tol and rel(host(w1), wr1) <= tol
+        u2, w2 = lm.lm_mdot(s, None, dev(T))
+        ur2, wr2 = orc.mdot(pos, np.zeros_like(F), T, a, eta, True)
+        assert rel(host(u2), ur2) <= tol and rel(host(w2), wr2) <= tol
+        lin = torch.full((n, 3), 7.0, dtype=torch.float64 if fp64 else torch.float32, device="cuda")
+        ang = torch.full((n, 3), 7.0, dtype=lin.dtype, device="cuda")
+        lm.lm_mdot(s, None, None, lin, ang)
+        assert not lin.any() and not ang.any()
+
+
+def test_mdot_rpy6_n32768_sampled_rows(orc):
+    """Full-size 6N FP32 workload (N = 32768, phi = 0.2) in the benchmark's
+    launch configuration; 256 sampled rows against the oracle, per block."""
+    c = I.RPY6_FP32_N32768
+    s_ = I.cube_suspension(c["seed"], c["n"], c["phi"], c["a"], angular=True, fp32=True)
+    s = make(c["eta"], c["a"], True, False, s_.pos)
+    rows = np.random.default_rng(0).choice(c["n"], 256, replace=False)
+    zero = np.zeros_like(s_.F)
+    for name, F, T in (("F", s_.F, zero), ("T", zero, s_.T), ("FT", s_.F, s_.T)):
+        u, w = gpu_mdot(s, F, T)
+        ur, wr = orc.mdot(s_.pos, F, T, c["a"], c["eta"], True, rows=rows)
+        assert rel(u[rows], ur) <= 1e-5, (name, rel(u[rows], ur))
+        assert rel(w[rows], wr) <= 1e-5, (name, rel(w[rows], wr))
+        assert np.isfinite(u).all() and np.isfinite(w).all()
+
+
+def test_mdot_melt_n524288_sampled_rows(orc):
+    """Largest workload: 1024 chains x 512 beads, 6N, FP32; 48 sampled rows."""
+    c = I.MELT_N524288
+    m = I.polymer_melt(c["seed"], c["n_chains"], c["beads"], c["bond"], c["sigma"], c["phi"], c["a"])
+    s = make(c["eta"], c["a"], True, False, m.pos)
+    u, w = gpu_mdot(s, m.F, m.T)
+    rows = np.random.default_rng(1).choice(m.pos.shape[0], 48, replace=False)
+    ur, wr = orc.mdot(m.pos, m.F, m.T, c["a"], c["eta"], True, rows=rows)
+    assert rel(u[rows], ur) <= 1e-5, rel(u[rows], ur)
+    assert rel(w[rows], wr) <= 1e-5, rel(w[rows], wr)
+    assert np.isfinite(u).all() and np.isfinite(w).all()
+
+
+def test_host_arrays_are_copied_by_the_library(orc):
+    n = 700
+    s_ = I.cube_suspension(9, n, 0.1, 1.0, angular=True, fp32=True)
+    s = lm.lm_create(1.0, 1.0, True, lm.LM_FP32C)
+    lm.lm_set_positions(s, s_.pos)  # numpy (pageable host memory)
+    u_h, w_h = lm.lm_mdot(s, s_.F, s_.T)
+    assert isinstance(u_h, np.ndarray)
+    pin = torch.from_numpy(s_.F).pin_memory()
+    pinT = torch.from_numpy(s_.T).pin_memory()
+    u_p, w_p = lm.lm_mdot(s, pin, pinT)
+    assert not u_p.is_cuda
+    u_d, w_d = lm.lm_mdot(s, dev(s_.F), dev(s_.T))
+    np.testing.assert_array_equal(u_h, host(u_d))
+    np.testing.assert_array_equal(u_p.numpy(), host(u_d))
+    np.testing.assert_array_equal(w_h, host(w_d))
+
+
+# ---------------------------------------------------------------------------
+# Lanczos M^{1/2} W
+# ---------------------------------------------------------------------------
+def test_sqrt_fp64_n1024_matches_eigen_root(orc):
+    c = I.RPY_FP64_N1024
+    s_ = I.cube_suspension(c["seed"], c["n"], c["phi"], c["a"], angular=False, fp32=False)
+    s = make(c["eta"], c["a"], False, True, s_.pos)
+    y, _, it = lm.lm_sqrt_mdot(s, dev(s_.W), tol=c["tol"], max_iter=200)
+    y = host(y).ravel()
+    M = orc.assemble(s_.pos, c["a"], c["eta"], False)
+    exact = orc.sqrt_exact(M, s_.W)
+    assert rel(y, exact) <= 20 * c["tol"], (rel(y, exact), it)
+    yo, ito, conv = orc.lanczos_sqrt(lambda v: M @ v, s_.W, tol=c["tol"], max_iter=200)
+    assert conv and abs(ito - it) <= 1
+    if ito == it:
+        assert rel(y, yo) <= 1e-10, rel(y, yo)
+    st = lm.lm_get_lanczos_stats(s)
+    assert st["converged"] and st["iterations"] == it
+    # prefactor scales linearly
+    y2, _, _ = lm.lm_sqrt_mdot(s, dev(s_.W), prefactor=-0.25, tol=c["tol"], max_iter=200)
+    np.testing.assert_allclose(host(y2).ravel(), -0.25 * y, rtol=1e-14, atol=1e-300)
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_sqrt_rpy6_small_matches_oracle(orc, fp64):
+    n = 600
+    a, eta = 1.0, 1.0
+    s_ = I.cube_suspension(12, n, 0.2, a, angular=True, fp32=not fp64)
+    s = make(eta, a, True, fp64, s_.pos)
+    tol = 1e-5
+    lin, ang, it = lm.lm_sqrt_mdot(s, dev(s_.W), tol=tol, max_iter=300)
+    y = np.concatenate([host(lin).ravel(), host(ang).ravel()])
+    M = orc.assemble(s_.pos, a, eta, True)
+    exact = orc.sqrt_exact(M, s_.W)
+    assert rel(y, exact) <= 20 * tol, rel(y, exact)
+    yo, ito, conv = orc.lanczos_sqrt(lambda v: M @ v, s_.W, tol=tol, max_iter=300)
+    if ito == it:
+        assert rel(y, yo) <= (1e-10 if fp64 else 1e-5), rel(y, yo)
+
+
+def test_sqrt_philox_noise_matches_oracle_generator(orc):
+    n = 300
+    s_ = I.cube_suspension(21, n, 0.1, 1.0, angular=True, fp32=False)
+    s = make(1.0, 1.0, True, True, s_.pos)
+    seed = 0x1234_5678_9ABC
+    lin, ang, it = lm.lm_sqrt_mdot(s, None, seed=seed, tol=1e-10, max_iter=300, like=dev(s_.F))
+    y = np.concatenate([host(lin).ravel(), host(ang).ravel()])
+    ntot = 6 * n
+    q = np.arange((ntot + 3) // 4, dtype=np.uint64)
+    ctr = np.zeros((q.size, 4), dtype=np.uint32)
+    ctr[:, 0] = (q & 0xFFFFFFFF).astype(np.uint32)
+    ctr[:, 1] = (q >> 32).astype(np.uint32)
+    words = orc.philox4x32(ctr, np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32))
+    z0, z1 = orc.box_muller(words[:, 0:2])
+    z2, z3 = orc.box_muller(words[:, 2:4])
+    W = np.stack([z0, z1, z2, z3], axis=1).ravel()[:ntot]
+    # the library's generator reproduces the oracle's W (to Box-Muller rounding)
+    lin_b, ang_b, _ = lm.lm_sqrt_mdot(s, dev(W), tol=1e-10, max_iter=300)
+    yb = np.concatenate([host(lin_b).ravel(), host(ang_b).ravel()])
+    assert rel(y, yb) <= 1e-13, rel(y, yb)
+    M = orc.assemble(s_.pos, 1.0, 1.0, True)
+    assert rel(y, orc.sqrt_exact(M, W)) <= 1e-8
+
+
+def test_sqrt_rpy6_n32768_norm_identity(orc):
+    """Full-size Lanczos (N = 32768, 6N, FP32, tol 1e-5): |M^1/2 W|^2 = W^T M W,
+    with W^T M W from the oracle's direct sum."""
+    c = I.RPY6_FP32_N32768
+    s_ = I.cube_suspension(c["seed"], c["n"], c["phi"], c["a"], angular=True, fp32=True)
+    s = make(c["eta"], c["a"], True, False, s_.pos)
+    lin, ang, it = lm.lm_sqrt_mdot(s, dev(s_.W), tol=c["tol"], max_iter=200)
+    y = np.concatenate([host(lin).ravel(), host(ang).ravel()])
+    n = c["n"]
+    u, w = orc.mdot(s_.pos, s_.W[: 3 * n].reshape(n, 3), s_.W[3 * n:].reshape(n, 3), c["a"], c["eta"], True)
+    wmw = float(s_.W @ np.concatenate([u.ravel(), w.ravel()]))
+    assert abs(y @ y - wmw) / wmw <= 1e-4, (y @ y, wmw, it)
+    st = lm.lm_get_lanczos_stats(s)
+    assert st["converged"] and 2 <= it < 200
+
+
+def test_sqrt_error_paths(orc):
+    n = 200
+    s_ = I.cube_suspension(4, n, 0.2, 1.0, angular=False, fp32=False)
+    s = make(1.0, 1.0, False, True, s_.pos)
+    with pytest.raises(lm.LmError) as e:
+        lm.lm_sqrt_mdot(s, dev(s_.W), tol=1e-14, max_iter=2)
+    assert e.value.status == lm.LM_ERR_NOT_CONVERGED
+    y, _, it = lm.lm_sqrt_mdot(s, dev(s_.W), tol=1e-14, max_iter=2, raise_not_converged=False)
+    assert it == 2 and torch.isfinite(y).all()
+    y0, _, it0 = lm.lm_sqrt_mdot(s, dev(np.zeros(3 * n)), tol=1e-6)
+    assert it0 == 0 and not y0.any()
+    # an eigenvector of M converges in one iteration
+    M = orc.assemble(s_.pos, 1.0, 1.0, False)
+    lam, Q = np.linalg.eigh(M)
+    W = Q[:, 10] * 2.0
+    y1, _, it1 = lm.lm_sqrt_mdot(s, dev(W), tol=1e-10, max_iter=50)
+    assert it1 == 1
+    np.testing.assert_allclose(host(y1).ravel(), np.sqrt(lam[10]) * W, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Errors and call order
+# ---------------------------------------------------------------------------
+def test_call_order_and_argument_errors():
+    s = lm.lm_create(1.0, 1.0, False, lm.LM_FP32C)
+    F = torch.zeros((4, 3), dtype=torch.float32, device="cuda")
+    with pytest.raises(lm.LmError) as e:
+        lm.lm_mdot(s, F, None, lin_out=torch.empty_like(F))
+    assert e.value.status == lm.LM_ERR_STATE
+    bad = torch.zeros((4, 3), dtype=torch.float32, device="cuda")
+    bad[2, 1] = float("nan")
+    with pytest.raises(lm.LmError) as e:
+        lm.lm_set_positions(s, bad)
+    assert e.value.status == lm.LM_ERR_NONFINITE
+    bad[2, 1] = float("inf")
+    with pytest.raises(lm.LmError):
+        lm.lm_set_positions(s, bad)
+    lm.lm_set_positions(s, torch.rand((4, 3), device="cuda"))
+    with pytest.raises(lm.LmError) as e:
+        lm.lm_mdot(s, F, F)  # torques without angular blocks
+    assert e.value.status == lm.LM_ERR_INVALID_ARG
+    with pytest.raises(lm.LmError) as e:
+        lm.lm_sqrt_mdot(s, torch.zeros(12, dtype=torch.float64, device="cuda"), tol=-1.0)
+    assert e.value.status == lm.LM_ERR_INVALID_ARG
+    with pytest.raises(lm.LmError) as e:
+        lm.lm_set_pair_config(s, 96, 3, 1)
+    assert e.value.status == lm.LM_ERR_INVALID_ARG
+    z, _ = lm.lm_div_m(s, F)
+    assert not z.any()
+
+
+def test_autotune_keeps_results(orc):
+    n = 3000
+    s_ = I.cube_suspension(31, n, 0.1, 1.0, angular=False, fp32=True)
+    s = make(1.0, 1.0, False, False, s_.pos)
+    cfg = lm.lm_autotune(s, reps=2)
+    assert cfg["threads"] in (128, 256) and cfg["ilp"] in (1, 2, 4) and cfg["splits"] >= 1
+    assert lm.lm_get_pair_config(s) == cfg
+    u, _ = gpu_mdot(s, s_.F, None)
+    ur, _ = orc.mdot(s_.pos, s_.F, None, 1.0, 1.0, False)
+    assert rel(u, ur) <= 1e-5
