@@ -285,3 +285,46 @@ def box_muller(u32_pair):
     u2 = w[..., 1] / 4294967296.0
     rad = np.sqrt(-2.0 * np.log(u1))
     return rad * np.cos(2.0 * np.pi * u2), rad * np.sin(2.0 * np.pi * u2)
+
+
+def philox_normals(seed: int, stream: int, n: int) -> np.ndarray:
+    """n standard normals from Philox-4x32-10: element e is normal (e % 4) of
+    block q = e // 4, counter (q low, q high, stream low, stream high), key
+    (seed low, seed high); normals 0, 1 from words (0, 1), 2, 3 from (2, 3)."""
+    nq = (n + 3) // 4
+    q = np.arange(nq, dtype=np.uint64)
+    ctr = np.zeros((nq, 4), dtype=np.uint32)
+    ctr[:, 0] = (q & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    ctr[:, 1] = (q >> np.uint64(32)).astype(np.uint32)
+    ctr[:, 2] = np.uint32(stream & 0xFFFFFFFF)
+    ctr[:, 3] = np.uint32((stream >> 32) & 0xFFFFFFFF)
+    key = np.array([seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF], dtype=np.uint32)
+    w = philox4x32(ctr, key)
+    z0, z1 = box_muller(w[:, 0:2])
+    z2, z3 = box_muller(w[:, 2:4])
+    return np.stack([z0, z1, z2, z3], axis=1).ravel()[:n]
+
+
+def bd_noise_stream(system: int, step: int) -> int:
+    """Philox stream of the Brownian noise of one system at one step."""
+    return (int(step) << 32) | int(system)
+
+
+def em_step(pos, a: float, eta: float, kT: float, dt: float, k_trap: float, W, tol: float,
+            max_iter: int = 200, exact_sqrt: bool = False):
+    """One Euler-Maruyama step of Eq. (bdhi) for an open system (drift term 0):
+    X' = X + dt M F + sqrt(2 kT dt) M^{1/2} W with the harmonic trap
+    F = -k_trap X (centre at the origin), forces only.
+    Returns (X', iterations)."""
+    pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+    n = pos.shape[0]
+    F = -k_trap * pos
+    u, _ = mdot(pos, F, None, a, eta, False)
+    if exact_sqrt:
+        M = assemble(pos, a, eta, False)
+        y = sqrt_exact(M, W)
+        it = 0
+    else:
+        y, it, _ = lanczos_sqrt(lambda v: mdot(pos, v.reshape(n, 3), None, a, eta, False)[0].ravel(), W, tol,
+                                max_iter)
+    return pos + dt * u + np.sqrt(2.0 * kT * dt) * y.reshape(n, 3), it

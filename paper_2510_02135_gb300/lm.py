@@ -229,7 +229,7 @@ def lm_mdot(s: Solver, forces=None, torques=None, lin_out=None, ang_out=None):
     if s.angular and ang_out is None:
         ang_out = _like(ref if ref is not None else lin_out, (s.N, 3), s.f64)
     s._sync_stream(forces, torques, lin_out, ang_out)
-    n3 = 3 * s.N
+    n3 = 3 * s.N if s.N else None  # size unknown until positions are set
     _check(lib().lm_mdot(s.handle, _ptr(forces, s.f64, n3, "forces"), _ptr(torques, s.f64, n3, "torques"),
                          _ptr(lin_out, s.f64, n3, "lin_out"), _ptr(ang_out, s.f64, n3, "ang_out")))
     return lin_out, ang_out
@@ -246,9 +246,9 @@ def lm_sqrt_mdot(s: Solver, W=None, seed: int = 0, prefactor: float = 1.0, tol: 
     if s.angular and ang_out is None:
         ang_out = _like(ref, (s.N, 3), s.f64)
     s._sync_stream(W, lin_out, ang_out)
-    n3 = 3 * s.N
+    n3 = 3 * s.N if s.N else None  # size unknown until positions are set
     it = ctypes.c_int(0)
-    wptr = _ptr(W, True, (6 if s.angular else 3) * s.N, "W")
+    wptr = _ptr(W, True, (6 if s.angular else 3) * s.N if s.N else None, "W")
     st = lib().lm_sqrt_mdot(s.handle, wptr, int(seed), float(prefactor), float(tol), int(max_iter),
                             _ptr(lin_out, s.f64, n3, "lin_out"), _ptr(ang_out, s.f64, n3, "ang_out"),
                             ctypes.byref(it))
@@ -261,7 +261,7 @@ def lm_div_m(s: Solver, like):
     lin = _like(like, (s.N, 3), s.f64)
     ang = _like(like, (s.N, 3), s.f64) if s.angular else None
     s._sync_stream(lin, ang)
-    n3 = 3 * s.N
+    n3 = 3 * s.N if s.N else None  # size unknown until positions are set
     _check(lib().lm_div_m(s.handle, _ptr(lin, s.f64, n3, "lin"), _ptr(ang, s.f64, n3, "ang")))
     return lin, ang
 
@@ -272,7 +272,7 @@ def lm_mdot_backward(s: Solver, forces, torques, grad_lin, grad_ang, need_dX: bo
     dF = _like(forces, (s.N, 3), s.f64) if need_dF else None
     dT = _like(forces, (s.N, 3), s.f64) if (s.angular and need_dF) else None
     s._sync_stream(forces, torques, grad_lin, grad_ang, dX, dF, dT)
-    n3 = 3 * s.N
+    n3 = 3 * s.N if s.N else None  # size unknown until positions are set
     _check(lib().lm_mdot_backward(s.handle, _ptr(forces, s.f64, n3, "forces"), _ptr(torques, s.f64, n3, "torques"),
                                   _ptr(grad_lin, s.f64, n3, "grad_lin"), _ptr(grad_ang, s.f64, n3, "grad_ang"),
                                   _ptr(dX, s.f64, n3, "dX"), _ptr(dF, s.f64, n3, "dF"), _ptr(dT, s.f64, n3, "dT")))
