@@ -211,6 +211,39 @@ int64_t lm_launch_count(lm_solver *solver);
  */
 int lm_tridiag_sqrt_e1(int m, const double *alpha, const double *beta, double *out);
 
+/*
+ * lm_mdot_noalloc -- the FP32 (compensated) mobility product for callers that
+ * cannot let a library allocate device memory.  The paper has no counterpart:
+ * its solvers own their buffers.  Such callers are applications whose
+ * device memory all belongs to their own pool or caching allocator (where a
+ * foreign cudaMalloc can fail or fragment it), latency-critical loops that
+ * cannot take the implicit device synchronisation of cudaMalloc / cudaFree,
+ * and hosts that forbid allocation inside plugins.
+ *
+ * It computes what lm_mdot computes for an LM_FP32C solver with the given
+ * viscosity, radius and angular flag, with no solver object: no cudaMalloc,
+ * cudaFree, pinned or library allocation, and no stream synchronisation.
+ *   pos, forces, torques, lin_out, ang_out: device arrays, N x 3 float, with
+ *     the lm_mdot conventions (forces / torques NULL = zero; torques and
+ *     ang_out only with include_angular, ang_out then required).  Host arrays
+ *     are rejected with LM_ERR_INVALID_ARG (copying them would need buffers).
+ *   1 <= N <= LM_NOALLOC_MAX_N, else LM_ERR_INVALID_ARG.
+ *   Positions are not checked for NaN/Inf (the check needs a read-back).
+ *   cuda_stream: the stream to run on (NULL = legacy default stream).
+ * Scratch: a fixed device array of LM_NOALLOC_SCRATCH_BYTES inside the
+ * library (packed positions and split partial sums), held by every GPU that
+ * loads the library until the process exits.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  All calls
+ * share the array: calls whose GPU work overlaps (e.g. on unordered streams)
+ * race on it and give wrong results.
+ */
+#define LM_NOALLOC_MAX_N 32768
+#define LM_NOALLOC_SCRATCH_BYTES (16u << 20)
+lm_status lm_mdot_noalloc(const float *pos, const float *forces, const float *torques, int64_t N,
+                          double viscosity, double hydrodynamic_radius, int include_angular,
+                          float *lin_out, float *ang_out, void *cuda_stream);
+
 /* Thread-local message for the last non-OK status ("" if none). */
 const char *lm_last_error(void);
 

@@ -91,6 +91,7 @@ bool is_device_ptr(const void* p) {
 
 namespace lmk {
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void set_last_error(const char* msg) { g_err = msg; }
 }  // namespace lmk
 
 struct lm_solver {
@@ -189,9 +190,11 @@ lm_status finish_out(lm_solver* s, OutView* views, int nv) {
     return LM_OK;
 }
 
+}  // namespace
+
 // Split count minimising (waves x tiles per CTA): keeps all SMs busy when N
 // is small and limits the tail wave when N is large.
-int auto_splits(int64_t N, int threads, int ilp, int slots) {
+int lmk::auto_splits(int64_t N, int threads, int ilp, int slots) {
     const int64_t nblk = (N + (int64_t)threads * ilp - 1) / ((int64_t)threads * ilp);
     const int64_t ntiles = (N + threads - 1) / threads;
     int best = 1;
@@ -207,6 +210,9 @@ int auto_splits(int64_t N, int threads, int ilp, int slots) {
     }
     return best;
 }
+
+namespace {
+using lmk::auto_splits;
 
 lm_pair_config default_config(const lm_solver* s, int64_t N) {
     lm_pair_config c;

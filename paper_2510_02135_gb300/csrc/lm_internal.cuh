@@ -15,6 +15,8 @@ struct __align__(32) dvec4 {
 
 // Kernel launches issued by the library (all solvers, all threads).
 void count_launches(int n);
+// Message returned by lm_last_error() on the calling thread.
+void set_last_error(const char* msg);
 
 // Algorithmic work per ordered pair (far-field formula, FMA = 2 flops),
 // frozen for the roofline figures: translation only, and all four blocks.
@@ -108,6 +110,8 @@ struct AdjointArgs {
 // Launch-configuration tables (pair_kernels.cu / adjoint_kernels.cu).
 bool mdot_config_supported(int fp64, int angular, int threads, int ilp);
 int mdot_ctas_per_sm(int fp64, int angular, int threads, int ilp);
+// Default j-split count for `slots` concurrently resident CTAs (lm_api.cu).
+int auto_splits(int64_t N, int threads, int ilp, int slots);
 // Number of j-splits actually launched for a requested split count.
 int64_t mdot_effective_splits(int64_t N, int threads, int splits);
 int mdot_partial_components(int angular);

@@ -106,6 +106,9 @@ def lib():
         L.lm_last_error.restype = ctypes.c_char_p
         L.lm_version.argtypes = []
         L.lm_version.restype = ctypes.c_char_p
+        L.lm_mdot_noalloc.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                      _vp, _vp, _vp]
+        L.lm_mdot_noalloc.restype = st
         L.lm_tridiag_sqrt_e1.argtypes = [ctypes.c_int, _vp, _vp, _vp]
         L.lm_tridiag_sqrt_e1.restype = ctypes.c_int
         _lib = L
@@ -277,6 +280,27 @@ def lm_mdot_backward(s: Solver, forces, torques, grad_lin, grad_ang, need_dX: bo
                                   _ptr(grad_lin, s.f64, n3, "grad_lin"), _ptr(grad_ang, s.f64, n3, "grad_ang"),
                                   _ptr(dX, s.f64, n3, "dX"), _ptr(dF, s.f64, n3, "dF"), _ptr(dT, s.f64, n3, "dT")))
     return dX, dF, dT
+
+
+LM_NOALLOC_MAX_N = 32768
+LM_NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def lm_mdot_noalloc(pos, forces, torques, viscosity: float, hydrodynamic_radius: float,
+                    include_angular: bool, lin_out, ang_out=None, cuda_stream=None) -> None:
+    """FP32 mobility product that allocates no device memory (all arrays on
+    the device, N <= LM_NOALLOC_MAX_N).  For callers that cannot let the
+    library allocate: see lm_mdot_noalloc in include/lm.h.  Runs on
+    ``cuda_stream`` (default: torch's current stream of lin_out's device)."""
+    n = lin_out.numel() // 3
+    if cuda_stream is None:
+        cuda_stream = _current_stream(lin_out)
+    n3 = 3 * n
+    _check(lib().lm_mdot_noalloc(_ptr(pos, False, n3, "pos"), _ptr(forces, False, n3, "forces"),
+                                 _ptr(torques, False, n3, "torques"), n, float(viscosity),
+                                 float(hydrodynamic_radius), int(bool(include_angular)),
+                                 _ptr(lin_out, False, n3, "lin_out"), _ptr(ang_out, False, n3, "ang_out"),
+                                 cuda_stream))
 
 
 def lm_get_pair_config(s: Solver) -> dict:
