@@ -147,8 +147,9 @@ lm_status lm_mdot_backward(lm_solver *solver, const void *forces, const void *to
 
 /*
  * Pair-kernel launch configuration (chosen by the autotuner or set by hand).
- *   threads: CTA size (64, 128 or 256); ilp: i-particles per thread (1, 2, 4);
- *   splits: number of j-range splits (>= 1; 0 = automatic).
+ *   threads: CTA size (128 or 256); ilp: i-particles per thread (1, 2, 4, 8
+ *   for LM_FP32C; 1, 2 for LM_FP64); splits: number of j-range splits
+ *   (>= 1; 0 = automatic).
  */
 typedef struct {
     int threads;
@@ -210,6 +211,102 @@ int64_t lm_launch_count(lm_solver *solver);
  * Returns 0, -1 if the QR iteration did not converge, -2 on bad arguments.
  */
 int lm_tridiag_sqrt_e1(int m, const double *alpha, const double *beta, double *out);
+
+/*
+ * ---------------------------------------------------------------------------
+ * Batches of independent open-boundary suspensions (uneven sizes).
+ * The Brownian dynamics of Eq. (bdhi) with the default Euler-Maruyama step
+ * (Sec. 3.2, LangevinVelocities) for many small systems at once: every call
+ * below runs as ONE persistent cooperative kernel launch over all systems
+ * (the thermal drift is zero in the open geometry, Sec. 2).  Pairs in FP32
+ * with compensated sums, Lanczos vectors in FP64, translational blocks only.
+ * Systems are concatenated: system s owns particles [offsets[s],
+ * offsets[s+1]) of every N_total x 3 array.
+ * ---------------------------------------------------------------------------
+ */
+typedef struct lm_batch lm_batch;
+
+/*
+ * lm_batch_create -- S >= 1 systems; offsets: host array of S+1 int64 with
+ * offsets[0] = 0 and offsets[s+1] - offsets[s] in [1, 65536].
+ * max_iter (1..128): Lanczos iteration cap per system and step; it sizes the
+ * Krylov storage, max_iter x 3 N_total doubles.
+ */
+lm_status lm_batch_create(lm_batch **out, int64_t S, const int64_t *offsets, double viscosity,
+                          double hydrodynamic_radius, int max_iter, void *cuda_stream);
+lm_status lm_batch_destroy(lm_batch *batch);
+
+/* Positions of all systems, N_total x 3 float (host or device); copied. */
+lm_status lm_batch_set_positions(lm_batch *batch, const float *pos);
+/* Current positions (after lm_batch_bd_run), N_total x 3 float. */
+lm_status lm_batch_get_positions(lm_batch *batch, float *pos_out);
+
+/* lin = M_s F_s for every system s (Mdot per system), N_total x 3 float. */
+lm_status lm_batch_mdot(lm_batch *batch, const float *forces, float *lin_out);
+
+/*
+ * lm_batch_sqrt_mdot -- lin = prefactor * M_s^{1/2} W_s for every system, by
+ * the Lanczos method of Sec. 3.3 with the stopping rule of lm_sqrt_mdot,
+ * applied per system.  W: 3 N_total doubles (host or device), or NULL to
+ * draw system s's noise from Philox-4x32-10 with key seed and stream s
+ * (element e of the system is normal e mod 4 of counter block e / 4).
+ * iters_out: optional host array of S ints (iterations per system).
+ * Returns LM_ERR_NOT_CONVERGED if some system reached max_iter.
+ */
+lm_status lm_batch_sqrt_mdot(lm_batch *batch, const double *W, uint64_t seed, double prefactor,
+                             double tol, float *lin_out, int *iters_out);
+
+/*
+ * lm_batch_bd_run -- nsteps Euler-Maruyama steps of Eq. (bdhi) for every
+ * system, with harmonic confining forces F = -k_trap x (trap centre at the
+ * origin, no torques):
+ *   x <- x + dt M F + sqrt(2 kT dt) M^{1/2} W,
+ * W of system s at step t from Philox-4x32-10 with key seed and stream
+ * (t << 32) | s, t counted from step0 (so that runs can be continued).
+ * All steps run in one persistent cooperative launch; with use_graph != 0
+ * that launch is captured into a CUDA graph and the graph is launched.
+ * Positions stay on the device (lm_batch_get_positions reads them).
+ * iters_out: optional host array of S ints (total Lanczos iterations per
+ * system over the run).  Device-side waits are bounded; if one expires the
+ * call returns LM_ERR_TIMEOUT.  Synchronises the stream.
+ */
+lm_status lm_batch_bd_run(lm_batch *batch, double kT, double dt, double k_trap, int nsteps,
+                          int64_t step0, uint64_t seed, double tol, int use_graph, int *iters_out);
+
+/*
+ * Pair tiling of the batched launches: threads per CTA (64 or 128) and
+ * i-particles per thread (1 or 2); picked by lm_batch_autotune (timing a
+ * product over all systems) or set by hand.
+ */
+lm_status lm_batch_set_tiling(lm_batch *batch, int threads, int ilp);
+lm_status lm_batch_autotune(lm_batch *batch, int *threads_out, int *ilp_out);
+
+/*
+ * Phase timeline of a batched run (profiling).  While enabled, the
+ * persistent kernel records the device global timer (ns) at the start of the
+ * first step and after every phase of that step: [start, A1, A2, then per
+ * Lanczos iteration B, C2, C3, C4, C5, then D].  lm_batch_profile_read copies
+ * up to n stamps of the last run into out and the number recorded into
+ * *count.
+ */
+lm_status lm_batch_profile_enable(lm_batch *batch, int enable);
+lm_status lm_batch_profile_read(lm_batch *batch, uint64_t *out, int n, int *count);
+
+/*
+ * lm_batch_timeout_selftest -- check of the bounded device-side waits (no
+ * paper counterpart): launches a kernel whose grid barrier waits for one CTA
+ * more than it has, so every wait runs out after about spin_cycles clock
+ * cycles (1e3..1e8).  Returns LM_ERR_TIMEOUT when the timeout path works.
+ */
+lm_status lm_batch_timeout_selftest(long long spin_cycles);
+
+/*
+ * lm_philox_normals -- the library's noise generator on the device: n
+ * standard normals, element e = normal (e mod 4) of Philox-4x32-10 counter
+ * block (e/4 low, e/4 high, stream low, stream high) with key (seed low,
+ * seed high), Box-Muller in FP64.  out: n doubles, device memory.
+ */
+lm_status lm_philox_normals(uint64_t seed, uint64_t stream, double *out, int64_t n, void *cuda_stream);
 
 /*
  * lm_mdot_noalloc -- the FP32 (compensated) mobility product for callers that

@@ -1,0 +1,664 @@
+// Batched Brownian dynamics of many independent open-boundary suspensions in
+// one persistent cooperative launch (libMobility paper, Eq. bdhi with the
+// Euler-Maruyama step of Sec. 3.2; Lanczos square root of Sec. 3.3; the drift
+// term is zero in the open geometry, Sec. 2).
+//
+// One BD step, every system s at once:
+//   A1  chunks   W_s (Philox) -> V_s[0], |W_s|^2 partials, F_s = -k x_s
+//   A2  chunks   v_0 = W_s / |W_s|
+//   for k = 0, 1, ...                       (systems drop out as they converge)
+//     B   items    w = M_s v_k   (k = 0: also u = M_s F_s, a second right-hand
+//                  side sharing the pair coefficients); v_k = w_{k-1} / beta_{k-1}
+//                  is formed while loading (and stored for the own rows);
+//                  partial v_k . w per item
+//     C2  chunks   alpha_k; w -= alpha_k v_k + beta_{k-1} v_{k-1}; dots V_s^T w
+//     C3  chunks   w -= V_s c; dots V_s^T w            (second Gram-Schmidt pass)
+//     C4  chunks   w -= V_s c'; |w|^2 partials
+//     C5  systems  beta_k; z_k = |W| f(T_k) e1 (implicit QR, FP64); stopping rule
+//   D   chunks   y = V_s z; x += dt u + sqrt(2 kT dt) y
+// Phases are separated by a grid barrier whose waits are bounded in clock
+// cycles: an expired wait sets an error flag and every CTA returns.
+// Items are (system, block of NT*NI particles) in decreasing system size,
+// handed out through a ticket counter; chunks are kBatchChunk vector elements
+// of one system, assigned round-robin.  Every reduction is a fixed-order sum
+// of per-item or per-chunk partials, so results do not depend on timing.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "lm_internal.cuh"
+#include "tridiag.cuh"
+
+namespace lmk {
+namespace {
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Phase end times of the first step (CTA 0, thread 0), for profiling.
+__device__ __forceinline__ void stamp(const BatchParams& P, int step, int& slot) {
+    if (P.timeline != nullptr && step == 0 && blockIdx.x == 0 && threadIdx.x == 0 && slot < P.timeline_len)
+        P.timeline[slot] = global_ns();
+    ++slot;
+}
+
+// Grid barrier with a bounded wait.  Returns false if the run must stop.
+__device__ bool grid_sync(const BatchParams& P) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = P.bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(P.bar, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(P.bar, 0u);
+            __threadfence();
+            atomicAdd(P.bar + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g) {
+                if (*(volatile int*)P.err != kBatchOk) break;
+                if (clock64() - t0 > P.spin_limit) {
+                    atomicCAS(P.err, kBatchOk, kBatchTimeout);
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int*)P.err == kBatchOk;
+}
+
+// Philox-4x32-10 (Salmon et al., SC'11) and FP64 Box-Muller, as in the
+// single-system generator.
+__device__ __forceinline__ void philox(uint32_t c[4], uint32_t k0, uint32_t k1) {
+    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+        const uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+        if (r < 9) { k0 += W0; k1 += W1; }
+    }
+}
+
+__device__ __forceinline__ void normals4(uint64_t seed, uint64_t stream, uint64_t q, double z[4]) {
+    uint32_t c[4] = {(uint32_t)(q & 0xffffffffu), (uint32_t)(q >> 32), (uint32_t)(stream & 0xffffffffu),
+                     (uint32_t)(stream >> 32)};
+    philox(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const double u1 = ((double)c[2 * p] + 1.0) * (1.0 / 4294967296.0);
+        const double u2 = (double)c[2 * p + 1] * (1.0 / 4294967296.0);
+        const double rad = sqrt(-2.0 * log(u1));
+        double sn, cs;
+        sincospi(2.0 * u2, &sn, &cs);
+        z[2 * p] = rad * cs;
+        z[2 * p + 1] = rad * sn;
+    }
+}
+
+__device__ __forceinline__ double* basis(const BatchParams& P, int s, int j) {
+    const int64_t o = P.off[s];
+    return P.V + (int64_t)P.m_max * 3 * o + (int64_t)j * 3 * (P.off[s + 1] - o);
+}
+
+// ---------------------------------------------------------------------------
+// Phase B: pair products for one item (system s, particles [i0, i0 + NT*NI)).
+// Right-hand side A: F_in (float, mdot mode) or a double vector times scaleA;
+// right-hand side B (NRHS = 2): the forces Fbuf (float).
+// ---------------------------------------------------------------------------
+template <int NT, int NI, int NRHS>
+__device__ void pair_item(const BatchParams& P, int s, int i0, const float* srcA_f, const double* srcA_d,
+                          double scaleA, double* outA_d, float* outA_f, double* outB, double* Vrow_store,
+                          double* part_slot, float4* sp, float4* sa, float4* sb, double* sred) {
+    const int tid = threadIdx.x;
+    const int64_t o = P.off[s];
+    const int Ns = (int)(P.off[s + 1] - o);
+    const float pad = (float)kPadCoord;
+    const RpyConst<float>& k = P.k;
+    float xi[NI], yi[NI], zi[NI];
+    float pA[NI][3], hA[NI][3], lA[NI][3];
+    float pB[NRHS == 2 ? NI : 1][3], hB[NRHS == 2 ? NI : 1][3], lB[NRHS == 2 ? NI : 1][3];
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+        const int i = i0 + q * NT + tid;
+        if (i < Ns) {
+            const float4 p = P.pos4[o + i];
+            xi[q] = p.x; yi[q] = p.y; zi[q] = p.z;
+        } else {
+            xi[q] = yi[q] = zi[q] = -pad;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            pA[q][c] = hA[q][c] = lA[q][c] = 0.f;
+            if (NRHS == 2) pB[q][c] = hB[q][c] = lB[q][c] = 0.f;
+        }
+    }
+    for (int jt = 0; jt < Ns; jt += NT) {
+        const int j = jt + tid;
+        __syncthreads();
+        if (j < Ns) {
+            sp[tid] = P.pos4[o + j];
+            float4 a;
+            if (srcA_f) {
+                a.x = srcA_f[3 * (o + j)]; a.y = srcA_f[3 * (o + j) + 1]; a.z = srcA_f[3 * (o + j) + 2];
+            } else {
+                a.x = (float)(srcA_d[3 * (o + j)] * scaleA);
+                a.y = (float)(srcA_d[3 * (o + j) + 1] * scaleA);
+                a.z = (float)(srcA_d[3 * (o + j) + 2] * scaleA);
+            }
+            a.w = 0.f;
+            sa[tid] = a;
+            if (NRHS == 2) sb[tid] = make_float4(P.Fbuf[3 * (o + j)], P.Fbuf[3 * (o + j) + 1], P.Fbuf[3 * (o + j) + 2], 0.f);
+        } else {
+            sp[tid] = make_float4(pad, pad, pad, 0.f);
+            sa[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (NRHS == 2) sb[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+        for (int jj = 0; jj < NT; ++jj) {
+            const float4 pj = sp[jj];
+            const float4 fa = sa[jj];
+            float4 fb = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (NRHS == 2) fb = sb[jj];
+            float dx[NI], dy[NI], dz[NI], r2[NI];
+            float mn = 0.f;
+#pragma unroll
+            for (int q = 0; q < NI; ++q) {
+                dx[q] = xi[q] - pj.x; dy[q] = yi[q] - pj.y; dz[q] = zi[q] - pj.z;
+                r2[q] = fmaf(dx[q], dx[q], fmaf(dy[q], dy[q], dz[q] * dz[q]));
+                mn = (q == 0) ? r2[q] : fminf(mn, r2[q]);
+            }
+            const bool near = __any_sync(0xffffffffu, mn < k.four_a2);
+#pragma unroll
+            for (int q = 0; q < NI; ++q) {
+                float A, B;
+                if (near && r2[q] < k.four_a2) {
+                    const float invr = (r2[q] > 0.f) ? rsqrtf(r2[q]) : 0.f;
+                    const float r = r2[q] * invr;
+                    A = k.nA0 - k.nA1 * r;
+                    B = k.nB * invr;
+                } else {
+                    const float invr = rsqrtf(r2[q]);
+                    const float invr2 = invr * invr;
+                    const float invr3 = invr2 * invr;
+                    A = fmaf(k.K1, invr3, invr);
+                    B = fmaf(-k.K2, invr3 * invr2, invr3);
+                }
+                const float sa_ = B * fmaf(dx[q], fa.x, fmaf(dy[q], fa.y, dz[q] * fa.z));
+                pA[q][0] = fmaf(sa_, dx[q], fmaf(A, fa.x, pA[q][0]));
+                pA[q][1] = fmaf(sa_, dy[q], fmaf(A, fa.y, pA[q][1]));
+                pA[q][2] = fmaf(sa_, dz[q], fmaf(A, fa.z, pA[q][2]));
+                if (NRHS == 2) {
+                    const float sb_ = B * fmaf(dx[q], fb.x, fmaf(dy[q], fb.y, dz[q] * fb.z));
+                    pB[q][0] = fmaf(sb_, dx[q], fmaf(A, fb.x, pB[q][0]));
+                    pB[q][1] = fmaf(sb_, dy[q], fmaf(A, fb.y, pB[q][1]));
+                    pB[q][2] = fmaf(sb_, dz[q], fmaf(A, fb.z, pB[q][2]));
+                }
+            }
+        }
+        // TwoSum fold of the tile partials
+#pragma unroll
+        for (int q = 0; q < NI; ++q) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float sm = hA[q][c] + pA[q][c], bb = sm - hA[q][c];
+                lA[q][c] += (hA[q][c] - (sm - bb)) + (pA[q][c] - bb);
+                hA[q][c] = sm; pA[q][c] = 0.f;
+                if (NRHS == 2) {
+                    sm = hB[q][c] + pB[q][c]; bb = sm - hB[q][c];
+                    lB[q][c] += (hB[q][c] - (sm - bb)) + (pB[q][c] - bb);
+                    hB[q][c] = sm; pB[q][c] = 0.f;
+                }
+            }
+        }
+    }
+    // outputs and the partial v_k . w of this item
+    double dot = 0.0;
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+        const int i = i0 + q * NT + tid;
+        if (i >= Ns) continue;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int64_t g = 3 * (o + i) + c;
+            const double wv = P.c8 * ((double)hA[q][c] + (double)lA[q][c]);
+            if (outA_f) outA_f[g] = (float)wv;
+            if (outA_d) {
+                outA_d[g] = wv;
+                const double vk = srcA_d[g] * scaleA;
+                if (Vrow_store) Vrow_store[3 * i + c] = vk;
+                dot = fma(vk, wv, dot);
+            }
+            if (NRHS == 2) outB[g] = P.c8 * ((double)hB[q][c] + (double)lB[q][c]);
+        }
+    }
+    if (part_slot) {
+        dot = warp_sum_d(dot);
+        if ((tid & 31) == 0) sred[tid >> 5] = dot;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < NT / 32; ++w) t += sred[w];
+            *part_slot = t;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Vector phases on one chunk (system s, elements [e0, e1) of the system).
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ void chunk_dots(const BatchParams& P, int s, int e0, int e1, const double* w, int nrows,
+                           double* part_out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int j = wid; j < nrows; j += NT / 32) {
+        const double* v = basis(P, s, j);
+        double acc = 0.0;
+        for (int e = e0 + lane; e < e1; e += 32) acc = fma(v[e], w[e], acc);
+        acc = warp_sum_d(acc);
+        if (lane == 0) part_out[j] = acc;
+    }
+}
+
+template <int NT>
+__device__ void chunk_sum_coeffs(const BatchParams& P, int s, const double* part, int nrows, double* cvec) {
+    const int cb = P.chunk_range[2 * s], ce = P.chunk_range[2 * s + 1];
+    for (int j = threadIdx.x; j < nrows; j += NT) {
+        double t = 0.0;
+        for (int c = cb; c < ce; ++c) t += part[(int64_t)c * (P.m_max + 1) + j];
+        cvec[j] = t;
+    }
+    __syncthreads();
+}
+
+template <int NT, int NI>
+__global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
+    __shared__ float4 sp[NT], sa[NT], sb[NT];
+    __shared__ double sred[NT / 32];
+    __shared__ double cvec[129];
+    __shared__ unsigned long long s_ticket;
+    const int tid = threadIdx.x;
+    const int G = gridDim.x;
+    const int per_item = NT * NI;
+    unsigned long long base = 0;
+
+    // dynamic item loop: calls fn(t) for items t handed out by the ticket counter
+    auto for_items = [&](auto&& fn) {
+        while (true) {
+            if (tid == 0) s_ticket = atomicAdd(P.ticket, 1ull);
+            __syncthreads();
+            const unsigned long long t = s_ticket;
+            __syncthreads();
+            if (t - base >= (unsigned long long)P.n_items) break;
+            fn((int)(t - base));
+        }
+        base += (unsigned long long)P.n_items + (unsigned long long)G;
+    };
+
+    if (P.mode == kBatchMdot) {
+        for_items([&](int t) {
+            const int s = P.items[2 * t], i0 = P.items[2 * t + 1];
+            pair_item<NT, NI, 1>(P, s, i0, P.F_in, nullptr, 1.0, nullptr, P.lin_out, nullptr, nullptr, nullptr, sp,
+                                 sa, sb, sred);
+        });
+        (void)per_item;
+        return;
+    }
+
+    const int nsteps = (P.mode == kBatchBD) ? P.nsteps : 1;
+    const double sq = sqrt(2.0 * P.kT * P.dt);
+    const int M1 = P.m_max + 1;
+    double* partA = P.part_chunk;
+    double* partB = P.part_chunk + (int64_t)P.n_chunks * M1;
+
+    for (int step = 0; step < nsteps; ++step) {
+        const uint64_t gstep = (uint64_t)(P.step0 + step);
+        int slot = 0;
+        stamp(P, step, slot);
+        // ---- A1: noise, forces, |W|^2 partials
+        if (blockIdx.x == 0)
+            for (int k = tid; k <= P.m_max; k += NT) P.nact[k] = 0;
+        for (int c = blockIdx.x; c < P.n_chunks; c += G) {
+            const int s = P.chunks[2 * c], e0 = P.chunks[2 * c + 1];
+            const int64_t o = P.off[s];
+            const int ns = 3 * (int)(P.off[s + 1] - o);
+            const int e1 = min(e0 + kBatchChunk, ns);
+            double* v0 = basis(P, s, 0);
+            double acc = 0.0;
+            if (P.W_in != nullptr) {
+                for (int e = e0 + tid; e < e1; e += NT) {
+                    const double wv = P.W_in[3 * o + e];
+                    v0[e] = wv;
+                    acc = fma(wv, wv, acc);
+                }
+            } else {
+                const uint64_t stream = (P.mode == kBatchBD) ? ((gstep << 32) | (uint64_t)s) : (uint64_t)s;
+                for (int q = e0 / 4 + tid; 4 * q < e1; q += NT) {
+                    double zz[4];
+                    normals4(P.seed, stream, (uint64_t)q, zz);
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int e = 4 * q + t;
+                        if (e < e1) { v0[e] = zz[t]; acc = fma(zz[t], zz[t], acc); }
+                    }
+                }
+            }
+            if (P.mode == kBatchBD)
+                for (int e = e0 + tid; e < e1; e += NT) P.Fbuf[3 * o + e] = (float)(-P.k_trap * P.x64[3 * o + e]);
+            acc = warp_sum_d(acc);
+            if ((tid & 31) == 0) sred[tid >> 5] = acc;
+            __syncthreads();
+            if (tid == 0) {
+                double t = 0.0;
+                for (int w = 0; w < NT / 32; ++w) t += sred[w];
+                partA[(int64_t)c * M1] = t;
+                if (e0 == 0) { P.active[s] = 1; P.msys[s] = 0; }
+            }
+            __syncthreads();
+        }
+        if (!grid_sync(P)) return;
+        stamp(P, step, slot);
+        // ---- A2: normalise
+        for (int c = blockIdx.x; c < P.n_chunks; c += G) {
+            const int s = P.chunks[2 * c], e0 = P.chunks[2 * c + 1];
+            const int ns = 3 * (int)(P.off[s + 1] - P.off[s]);
+            const int e1 = min(e0 + kBatchChunk, ns);
+            chunk_sum_coeffs<NT>(P, s, partA, 1, cvec);
+            const double nw = sqrt(cvec[0]);
+            if (e0 == 0 && tid == 0) {
+                P.normW[s] = nw;
+                if (!(nw > 0.0)) P.active[s] = 0;   // W = 0: zero output, no iterations
+            }
+            if (nw > 0.0) {
+                double* v0 = basis(P, s, 0);
+                const double inv = 1.0 / nw;
+                for (int e = e0 + tid; e < e1; e += NT) v0[e] *= inv;
+            }
+            __syncthreads();
+        }
+        if (!grid_sync(P)) return;
+        stamp(P, step, slot);
+        // ---- Lanczos iterations
+        for (int k = 0; k < P.m_max; ++k) {
+            double* wcur = (k & 1) ? P.w1 : P.w0;
+            double* wprev = (k & 1) ? P.w0 : P.w1;
+            // B: products
+            for_items([&](int t) {
+                const int s = P.items[2 * t], i0 = P.items[2 * t + 1];
+                if (!P.active[s]) return;
+                const int64_t o = P.off[s];
+                if (k == 0) {
+                    const double* v0 = basis(P, s, 0) - 3 * o;  // indexed by global element
+                    if (P.mode == kBatchBD)
+                        pair_item<NT, NI, 2>(P, s, i0, nullptr, v0, 1.0, wcur, nullptr, P.u, nullptr,
+                                             &P.part_item[t], sp, sa, sb, sred);
+                    else
+                        pair_item<NT, NI, 1>(P, s, i0, nullptr, v0, 1.0, wcur, nullptr, nullptr, nullptr,
+                                             &P.part_item[t], sp, sa, sb, sred);
+                } else {
+                    const double invb = 1.0 / P.beta[s * P.m_max + k - 1];
+                    pair_item<NT, NI, 1>(P, s, i0, nullptr, wprev, invb, wcur, nullptr, nullptr, basis(P, s, k),
+                                         &P.part_item[t], sp, sa, sb, sred);
+                }
+            });
+            if (!grid_sync(P)) return;
+            stamp(P, step, slot);
+            // C2: alpha, three-term update, first Gram-Schmidt dots
+            for (int c = blockIdx.x; c < P.n_chunks; c += G) {
+                const int s = P.chunks[2 * c], e0 = P.chunks[2 * c + 1];
+                if (!P.active[s]) continue;
+                const int64_t o = P.off[s];
+                const int ns = 3 * (int)(P.off[s + 1] - o);
+                const int e1 = min(e0 + kBatchChunk, ns);
+                double alpha = 0.0;
+                for (int t = P.item_range[2 * s]; t < P.item_range[2 * s + 1]; ++t) alpha += P.part_item[t];
+                if (e0 == 0 && tid == 0) P.alpha[s * P.m_max + k] = alpha;
+                const double bprev = (k > 0) ? P.beta[s * P.m_max + k - 1] : 0.0;
+                const double* vk = basis(P, s, k);
+                const double* vkm1 = (k > 0) ? basis(P, s, k - 1) : vk;
+                double* w = wcur + 3 * o;
+                for (int e = e0 + tid; e < e1; e += NT) w[e] -= alpha * vk[e] + bprev * vkm1[e];
+                __syncthreads();
+                chunk_dots<NT>(P, s, e0, e1, w, k + 1, partA + (int64_t)c * M1);
+                __syncthreads();
+            }
+            if (!grid_sync(P)) return;
+            stamp(P, step, slot);
+            // C3, C4: subtract projections; dots again / norm
+            for (int pass = 0; pass < 2; ++pass) {
+                const double* pin = pass == 0 ? partA : partB;
+                double* pout = pass == 0 ? partB : partA;
+                for (int c = blockIdx.x; c < P.n_chunks; c += G) {
+                    const int s = P.chunks[2 * c], e0 = P.chunks[2 * c + 1];
+                    if (!P.active[s]) continue;
+                    const int64_t o = P.off[s];
+                    const int ns = 3 * (int)(P.off[s + 1] - o);
+                    const int e1 = min(e0 + kBatchChunk, ns);
+                    chunk_sum_coeffs<NT>(P, s, pin, k + 1, cvec);
+                    double* w = wcur + 3 * o;
+                    const double* V0 = basis(P, s, 0);
+                    double nrm = 0.0;
+                    for (int e = e0 + tid; e < e1; e += NT) {
+                        double acc = w[e];
+                        for (int j = 0; j <= k; ++j) acc -= cvec[j] * V0[(int64_t)j * ns + e];
+                        w[e] = acc;
+                        nrm = fma(acc, acc, nrm);
+                    }
+                    __syncthreads();
+                    if (pass == 0) {
+                        chunk_dots<NT>(P, s, e0, e1, w, k + 1, pout + (int64_t)c * M1);
+                    } else {
+                        nrm = warp_sum_d(nrm);
+                        if ((tid & 31) == 0) sred[tid >> 5] = nrm;
+                        __syncthreads();
+                        if (tid == 0) {
+                            double t = 0.0;
+                            for (int ww = 0; ww < NT / 32; ++ww) t += sred[ww];
+                            pout[(int64_t)c * M1] = t;
+                        }
+                    }
+                    __syncthreads();
+                }
+                if (!grid_sync(P)) return;
+                stamp(P, step, slot);
+            }
+            // C5: beta, tridiagonal square root, stopping rule (one thread per system)
+            for (int s = blockIdx.x; s < P.S; s += G) {
+                if (tid != 0 || !P.active[s]) continue;
+                double b2 = 0.0;
+                for (int c = P.chunk_range[2 * s]; c < P.chunk_range[2 * s + 1]; ++c) b2 += partA[(int64_t)c * M1];
+                const double b = sqrt(b2);
+                double* al = P.alpha + s * P.m_max;
+                double* be = P.beta + s * P.m_max;
+                be[k] = b;
+                const int m = k + 1;
+                double* zs = P.z + s * P.m_max;
+                double* zp = P.zprev + s * P.m_max;
+                int ncl = 0;
+                const int rc = tridiag_sqrt_e1(m, al, be, P.td + (int64_t)s * 2 * P.m_max,
+                                               P.td + (int64_t)s * 2 * P.m_max + P.m_max,
+                                               P.trk + (int64_t)s * P.max_rot, P.trc + (int64_t)s * P.max_rot,
+                                               P.trs + (int64_t)s * P.max_rot, P.max_rot, zs, &ncl);
+                if (rc != 0) atomicCAS(P.err, kBatchOk, kBatchTridiag);
+                const double nw = P.normW[s];
+                for (int i = 0; i < m; ++i) zs[i] *= nw;
+                bool stop = false;
+                double rel = 0.0;
+                if (k >= 1) {
+                    double dn = 0.0, zn = 0.0;
+                    for (int i = 0; i < m; ++i) {
+                        const double dd = zs[i] - (i < m - 1 ? zp[i] : 0.0);
+                        dn += dd * dd;
+                        zn += zs[i] * zs[i];
+                    }
+                    rel = (zn > 0.0) ? sqrt(dn / zn) : 0.0;
+                    P.rel[s] = rel;
+                    if (rel < P.tol) stop = true;
+                }
+                if (!stop) {
+                    double amax = 0.0;
+                    for (int i = 0; i < m; ++i) amax = fmax(amax, fabs(al[i]));
+                    if (b <= P.brk_rel * amax) stop = true;
+                }
+                if (!stop && m == P.m_max) { stop = true; P.notconv[s] = 1; }
+                if (stop) {
+                    P.active[s] = 0;
+                    P.msys[s] = m;
+                    P.itsum[s] += m;
+                } else {
+                    for (int i = 0; i < m; ++i) zp[i] = zs[i];
+                    atomicAdd(&P.nact[k + 1], 1);
+                }
+            }
+            if (!grid_sync(P)) return;
+            stamp(P, step, slot);
+            if (*(volatile int*)&P.nact[k + 1] == 0) break;
+        }
+        // ---- D: combine and update
+        for (int c = blockIdx.x; c < P.n_chunks; c += G) {
+            const int s = P.chunks[2 * c], e0 = P.chunks[2 * c + 1];
+            const int64_t o = P.off[s];
+            const int ns = 3 * (int)(P.off[s + 1] - o);
+            const int e1 = min(e0 + kBatchChunk, ns);
+            const int m = P.msys[s];
+            for (int j = tid; j < m; j += NT) cvec[j] = P.z[s * P.m_max + j];
+            __syncthreads();
+            const double* V0 = basis(P, s, 0);
+            for (int e = e0 + tid; e < e1; e += NT) {
+                double y = 0.0;
+                for (int j = 0; j < m; ++j) y = fma(cvec[j], V0[(int64_t)j * ns + e], y);
+                if (P.mode == kBatchBD) {
+                    const double xn = P.x64[3 * o + e] + P.dt * P.u[3 * o + e] + sq * y;
+                    P.x64[3 * o + e] = xn;
+                    float* pf = reinterpret_cast<float*>(P.pos4 + o + e / 3);
+                    pf[e % 3] = (float)xn;
+                } else {
+                    P.lin_out[3 * o + e] = (float)(P.prefactor * y);
+                }
+            }
+            __syncthreads();
+        }
+        if (!grid_sync(P)) return;
+        stamp(P, step, slot);
+    }
+}
+
+__global__ void batch_pack_kernel(const float* __restrict__ pos, int64_t N, float4* __restrict__ pos4,
+                                  double* __restrict__ x64, int* __restrict__ bad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+    const float m = (float)kMaxAbsCoord;
+    if (!(fabsf(x) <= m && fabsf(y) <= m && fabsf(z) <= m)) atomicExch(bad, 1);
+    pos4[i] = make_float4(x, y, z, 0.f);
+    x64[3 * i] = x; x64[3 * i + 1] = y; x64[3 * i + 2] = z;
+}
+
+__global__ void batch_unpack_kernel(const double* __restrict__ x64, int64_t n, float* __restrict__ out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) out[e] = (float)x64[e];
+}
+
+// Every CTA waits at a barrier that expects one CTA more than the grid has.
+__global__ void timeout_probe_kernel(BatchParams P) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = P.bar + 1;
+        const unsigned g = *gen;
+        atomicAdd(P.bar, 1u);   // never reaches gridDim.x + 1
+        const long long t0 = clock64();
+        while (*gen == g) {
+            if (clock64() - t0 > P.spin_limit) {
+                atomicCAS(P.err, kBatchOk, kBatchTimeout);
+                break;
+            }
+            __nanosleep(100);
+        }
+    }
+    __syncthreads();
+}
+
+template <int NT, int NI>
+cudaError_t launch_nt(const BatchParams& p, int grid, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, batch_kernel<NT, NI>, p);
+}
+
+template <int NT, int NI>
+int occ_nt() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel<NT, NI>, NT, 0) != cudaSuccess) return 0;
+    return n;
+}
+
+}  // namespace
+
+bool batch_tiling_supported(int threads, int ilp) {
+    return (threads == 64 || threads == 128) && (ilp == 1 || ilp == 2);
+}
+
+int batch_ctas_per_sm(int threads, int ilp) {
+    if (threads == 64 && ilp == 1) return occ_nt<64, 1>();
+    if (threads == 64 && ilp == 2) return occ_nt<64, 2>();
+    if (threads == 128 && ilp == 1) return occ_nt<128, 1>();
+    if (threads == 128 && ilp == 2) return occ_nt<128, 2>();
+    return 0;
+}
+
+cudaError_t launch_batch(const BatchParams& p, int threads, int ilp, int grid, cudaStream_t s) {
+    cudaError_t e = cudaErrorInvalidConfiguration;
+    if (threads == 64 && ilp == 1) e = launch_nt<64, 1>(p, grid, s);
+    else if (threads == 64 && ilp == 2) e = launch_nt<64, 2>(p, grid, s);
+    else if (threads == 128 && ilp == 1) e = launch_nt<128, 1>(p, grid, s);
+    else if (threads == 128 && ilp == 2) e = launch_nt<128, 2>(p, grid, s);
+    count_launches(1);
+    return e;
+}
+
+cudaError_t launch_batch_pack(const float* pos, int64_t N, float4* pos4, double* x64, int* bad, cudaStream_t s) {
+    batch_pack_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(pos, N, pos4, x64, bad);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_unpack(const double* x64, int64_t N, float* out, cudaStream_t s) {
+    batch_unpack_kernel<<<(unsigned)((3 * N + 255) / 256), 256, 0, s>>>(x64, 3 * N, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_timeout_probe(unsigned* bar, int* err, long long spin_limit, int grid, cudaStream_t s) {
+    BatchParams p = {};
+    p.bar = bar;
+    p.err = err;
+    p.spin_limit = spin_limit;
+    timeout_probe_kernel<<<grid, 32, 0, s>>>(p);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace lmk

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <memory>
 #include <vector>
 
 #include "../../include/lm.h"
@@ -87,6 +88,28 @@ bool is_device_ptr(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+struct LanczosHost {
+    std::vector<double> alpha, beta, z, zprev, d, e, rc, rs;
+    std::vector<int> rk;
+    int solve(int m, double normW, int* clamped) {
+        z.assign(m, 0.0);
+        d.resize(m);
+        e.resize(m);
+        size_t max_rot = (size_t)4 * m * m + 64;
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            if (rk.size() < max_rot) { rk.resize(max_rot); rc.resize(max_rot); rs.resize(max_rot); }
+            const int r = lmk::tridiag_sqrt_e1(m, alpha.data(), beta.data(), d.data(), e.data(), rk.data(),
+                                               rc.data(), rs.data(), (int)max_rot, z.data(), clamped);
+            if (r != -2) {
+                for (double& v : z) v *= normW;
+                return r;
+            }
+            max_rot = (size_t)30 * m * m + 64;
+        }
+        return -2;
+    }
+};
+
 }  // namespace
 
 namespace lmk {
@@ -125,6 +148,10 @@ struct lm_solver {
 
     lm_lanczos_stats stats{0, 0, 0.0, 0.0, 0};
 
+    // Lanczos host state and per-iteration events
+    LanczosHost lz_host;
+    std::vector<cudaEvent_t> lz_ev;
+
     // profiling of the pair kernel
     bool prof_on = false;
     std::vector<cudaEvent_t> prof_ev;   // pairs (begin, end)
@@ -138,6 +165,7 @@ struct lm_solver {
         for (DBuf* b : all) b->release();
         if (pinned) cudaFreeHost(pinned);
         for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
+        for (cudaEvent_t e : lz_ev) cudaEventDestroy(e);
     }
 };
 
@@ -412,11 +440,41 @@ lm_status lm_div_m(lm_solver* s, void* lin_out, void* ang_out) {
 // Lanczos square root (Sec. 3.3).  Per iteration k (v_k = row k of V):
 //   w = M v_k;  alpha_k = v_k . w;  w -= alpha_k v_k + beta_{k-1} v_{k-1};
 //   twice: w -= V_k (V_k^T w);  beta_k = |w|;
-//   z_k = |W| f(T_k) e1 (host, implicit QR);  stop if k >= 1 and
+//   z_k = |W| f(T_k) e1 (host);  stop if k >= 1 and
 //   |z_k - [z_{k-1}; 0]| / |z_k| < tol, or on breakdown, or at max_iter;
 //   v_{k+1} = w / beta_k.
 // Result: y = V_m z_m, scaled by the prefactor.
+// The GPU runs one iteration ahead of the host: iteration k+1 is enqueued
+// (it needs only device data) before the host reads alpha_k, beta_k and
+// decides whether to stop at k, so the read-back and the tridiagonal step
+// overlap the next product.  The speculative iteration is skipped when the
+// geometric trend of the relative changes predicts a stop at k.
 // ---------------------------------------------------------------------------
+namespace {
+
+lm_status enqueue_lanczos_iteration(lm_solver* s, int k, int64_t n, double* V, double* w, double* scal, double* red,
+                                    double* cb, cudaEvent_t ev) {
+    const int64_t N = s->N;
+    double* vk = V + (int64_t)k * n;
+    if (k > 0) LM_CUDA(lmk::lz_scale(w, scal + 4 * (k - 1) + 1, vk, n, s->stream), "next basis vector");
+    if (lm_status st = run_mdot(s, vk, vk + 3 * N, 1, w, w + 3 * N, 1, s->cfg)) return st;
+    LM_CUDA(lmk::lz_dot(vk, w, n, red, scal + 4 * k, s->stream), "alpha");
+    LM_CUDA(lmk::lz_axpy2(w, vk, scal + 4 * k, k > 0 ? vk - n : nullptr, k > 0 ? scal + 4 * (k - 1) + 1 : nullptr, n,
+                          s->stream),
+            "three-term update");
+    for (int pass = 0; pass < 2; ++pass) {
+        LM_CUDA(lmk::lz_multidot(V, k + 1, w, n, red, cb, s->stream), "reorthogonalisation");
+        LM_CUDA(lmk::lz_sub_vc(V, k + 1, cb, w, n, s->stream), "reorthogonalisation");
+    }
+    LM_CUDA(lmk::lz_norm(w, n, red, scal + 4 * k + 1, s->stream), "beta");
+    LM_CUDA(cudaMemcpyAsync(s->pinned + 4 * k, scal + 4 * k, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream),
+            "read alpha, beta");
+    LM_CUDA(cudaEventRecord(ev, s->stream), "iteration event");
+    return LM_OK;
+}
+
+}  // namespace
+
 lm_status lm_sqrt_mdot(lm_solver* s, const double* W, uint64_t seed, double prefactor, double tol, int max_iter,
                        void* lin_out, void* ang_out, int* iters_out) {
     if (lm_status st = check_solver(s, true)) return st;
@@ -439,19 +497,33 @@ lm_status lm_sqrt_mdot(lm_solver* s, const double* W, uint64_t seed, double pref
     if (lm_status st = stage_out(s, ang_out, out_bytes, 1, &ov[1])) return st;
 
     ensure_config(s);
-    LM_CUDA(s->V.ensure((size_t)m_max * n * sizeof(double)), "allocating Krylov basis");
+    // one spare basis row for the speculative iteration
+    LM_CUDA(s->V.ensure((size_t)(m_max + 1) * n * sizeof(double)), "allocating Krylov basis");
     LM_CUDA(s->w.ensure((size_t)n * sizeof(double)), "allocating Lanczos vector");
     LM_CUDA(s->y.ensure((size_t)n * sizeof(double)), "allocating Lanczos vector");
-    LM_CUDA(s->red.ensure(lmk::lz_red_doubles(n, m_max) * sizeof(double)), "allocating reduction scratch");
-    LM_CUDA(s->scal.ensure((size_t)(4 * (m_max + 2)) * sizeof(double)), "allocating scalars");
+    LM_CUDA(s->red.ensure(lmk::lz_red_doubles(n, m_max + 1) * sizeof(double)), "allocating reduction scratch");
+    LM_CUDA(s->scal.ensure((size_t)(4 * (m_max + 3)) * sizeof(double)), "allocating scalars");
     LM_CUDA(s->zbuf.ensure((size_t)m_max * sizeof(double)), "allocating coefficients");
-    LM_CUDA(s->cbuf.ensure((size_t)m_max * sizeof(double)), "allocating coefficients");
+    LM_CUDA(s->cbuf.ensure((size_t)(m_max + 1) * sizeof(double)), "allocating coefficients");
+    if (s->pinned_doubles < (size_t)(4 * (m_max + 3))) {
+        cudaFreeHost(s->pinned);
+        s->pinned = nullptr;
+        s->pinned_doubles = 0;
+        LM_CUDA(cudaMallocHost(reinterpret_cast<void**>(&s->pinned), (size_t)(4 * (m_max + 3)) * sizeof(double)),
+                "allocating pinned scalars");
+        s->pinned_doubles = (size_t)(4 * (m_max + 3));
+    }
+    while (s->lz_ev.size() < (size_t)(m_max + 1)) {
+        cudaEvent_t e;
+        LM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "lanczos event");
+        s->lz_ev.push_back(e);
+    }
     double* V = s->V.as<double>();
     double* w = s->w.as<double>();
     double* scal = s->scal.as<double>();
     double* red = s->red.as<double>();
     double* cb = s->cbuf.as<double>();
-    double* wn = scal + 4 * (m_max + 1);  // |W|, |W|^2
+    double* wn = scal + 4 * (m_max + 2);  // |W|, |W|^2
 
     // W: user array (host or device) or Philox normals
     const double* dW = nullptr;
@@ -465,9 +537,12 @@ lm_status lm_sqrt_mdot(lm_solver* s, const double* W, uint64_t seed, double pref
         dW = static_cast<const double*>(p);
     }
     LM_CUDA(lmk::lz_norm(dW, n, red, wn, s->stream), "norm of W");
-    LM_CUDA(cudaMemcpyAsync(s->pinned, wn, sizeof(double), cudaMemcpyDeviceToHost, s->stream), "read |W|");
-    LM_CUDA(cudaStreamSynchronize(s->stream), "lanczos");
-    const double normW = s->pinned[0];
+    LM_CUDA(lmk::lz_scale(dW, wn, V, n, s->stream), "normalise W");
+    LM_CUDA(cudaMemcpyAsync(s->pinned + 4 * (m_max + 2), wn, sizeof(double), cudaMemcpyDeviceToHost, s->stream),
+            "read |W|");
+    if (lm_status st = enqueue_lanczos_iteration(s, 0, n, V, w, scal, red, cb, s->lz_ev[0])) return st;
+    LM_CUDA(cudaEventSynchronize(s->lz_ev[0]), "lanczos");
+    const double normW = s->pinned[4 * (m_max + 2)];
     s->stats.norm_w = normW;
     if (!std::isfinite(normW)) return fail(LM_ERR_INVALID_ARG, "W contains NaN or Inf");
     if (normW == 0.0) {
@@ -476,69 +551,66 @@ lm_status lm_sqrt_mdot(lm_solver* s, const double* W, uint64_t seed, double pref
         s->stats.converged = 1;
         return finish_out(s, ov, 2);
     }
-    LM_CUDA(lmk::lz_scale(dW, wn, V, n, s->stream), "normalise W");
 
-    std::vector<double> alpha, beta, z, zprev, work;
-    alpha.reserve(m_max);
-    beta.reserve(m_max);
+    LanczosHost& H = s->lz_host;
+    H.alpha.clear();
+    H.beta.clear();
+    H.zprev.clear();
     const double brk_rel = s->fp64 ? 1e-13 : 1e-7;
     bool converged = false;
-    double rel = 0.0;
+    double rel = 0.0, rel_prev = 0.0;
     int clamped = 0;
     int k = 0;
     for (k = 0; k < m_max; ++k) {
-        double* vk = V + (int64_t)k * n;
-        if (lm_status st = run_mdot(s, vk, vk + 3 * N, 1, w, w + 3 * N, 1, s->cfg)) return st;
-        LM_CUDA(lmk::lz_dot(vk, w, n, red, scal + 4 * k, s->stream), "alpha");
-        LM_CUDA(lmk::lz_axpy2(w, vk, scal + 4 * k, k > 0 ? vk - n : nullptr, k > 0 ? scal + 4 * (k - 1) + 1 : nullptr,
-                              n, s->stream),
-                "three-term update");
-        for (int pass = 0; pass < 2; ++pass) {
-            LM_CUDA(lmk::lz_multidot(V, k + 1, w, n, red, cb, s->stream), "reorthogonalisation");
-            LM_CUDA(lmk::lz_sub_vc(V, k + 1, cb, w, n, s->stream), "reorthogonalisation");
+        // speculative enqueue of iteration k+1 unless a stop at k is predicted
+        bool predicted_stop = false;
+        if (k >= 2 && rel_prev > 0.0 && rel > 0.0) predicted_stop = (rel * rel / rel_prev) < 2.0 * tol;
+        if (k + 1 < m_max && !predicted_stop && k > 0) {
+            if (lm_status st = enqueue_lanczos_iteration(s, k + 1, n, V, w, scal, red, cb, s->lz_ev[k + 1])) return st;
         }
-        LM_CUDA(lmk::lz_norm(w, n, red, scal + 4 * k + 1, s->stream), "beta");
-        LM_CUDA(cudaMemcpyAsync(s->pinned, scal + 4 * k, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream),
-                "read alpha, beta");
-        LM_CUDA(cudaStreamSynchronize(s->stream), "lanczos iteration");
-        const double a_k = s->pinned[0];
-        const double b_k = s->pinned[1];
+        LM_CUDA(cudaEventSynchronize(s->lz_ev[k]), "lanczos iteration");
+        const double a_k = s->pinned[4 * k];
+        const double b_k = s->pinned[4 * k + 1];
         if (!std::isfinite(a_k) || !std::isfinite(b_k))
             return fail(LM_ERR_CUDA, "Lanczos produced a non-finite coefficient at iteration %d", k + 1);
-        alpha.push_back(a_k);
+        H.alpha.push_back(a_k);
         const int m = k + 1;
-        z.assign(m, 0.0);
-        work.assign((size_t)m * m + 2 * m, 0.0);
         int ncl = 0;
-        if (lmk::tridiag_sqrt_e1(m, alpha.data(), beta.data(), work.data(), z.data(), &ncl) != 0)
-            return fail(LM_ERR_NOT_CONVERGED, "tridiagonal eigensolver did not converge");
+        if (H.solve(m, normW, &ncl) != 0) return fail(LM_ERR_NOT_CONVERGED, "tridiagonal eigensolver did not converge");
         clamped = ncl;
-        for (double& v : z) v *= normW;
+        bool stop = false;
         if (k >= 1) {
             double dn = 0.0, zn = 0.0;
             for (int i = 0; i < m; ++i) {
-                const double d = z[i] - (i < m - 1 ? zprev[i] : 0.0);
-                dn += d * d;
-                zn += z[i] * z[i];
+                const double dd = H.z[i] - (i < m - 1 ? H.zprev[i] : 0.0);
+                dn += dd * dd;
+                zn += H.z[i] * H.z[i];
             }
+            rel_prev = rel;
             rel = (zn > 0.0) ? std::sqrt(dn / zn) : 0.0;
-            if (rel < tol) { converged = true; break; }
+            if (rel < tol) { converged = true; stop = true; }
         }
-        double amax = 0.0;
-        for (double v : alpha) amax = std::max(amax, std::fabs(v));
-        if (b_k <= brk_rel * amax) { converged = true; break; }
-        if (k + 1 == m_max) break;
-        beta.push_back(b_k);
-        LM_CUDA(lmk::lz_scale(w, scal + 4 * k + 1, V + (int64_t)(k + 1) * n, n, s->stream), "next basis vector");
-        zprev = z;
+        if (!stop) {
+            double amax = 0.0;
+            for (double v : H.alpha) amax = std::max(amax, std::fabs(v));
+            if (b_k <= brk_rel * amax) { converged = true; stop = true; }
+        }
+        if (!stop && k + 1 == m_max) stop = true;
+        if (stop) break;
+        H.beta.push_back(b_k);
+        H.zprev = H.z;
+        // iteration k+1 not enqueued yet (first iteration, or a predicted stop that did not happen)
+        if (k == 0 || predicted_stop) {
+            if (lm_status st = enqueue_lanczos_iteration(s, k + 1, n, V, w, scal, red, cb, s->lz_ev[k + 1])) return st;
+        }
     }
     const int m = std::min(k + 1, m_max);
-    LM_CUDA(cudaMemcpyAsync(s->zbuf.p, z.data(), (size_t)m * sizeof(double), cudaMemcpyHostToDevice, s->stream),
+    LM_CUDA(cudaMemcpyAsync(s->zbuf.p, H.z.data(), (size_t)m * sizeof(double), cudaMemcpyHostToDevice, s->stream),
             "coefficients to device");
     LM_CUDA(lmk::lz_combine(V, m, s->zbuf.as<double>(), s->y.as<double>(), n, s->stream), "combine basis");
     LM_CUDA(lmk::lz_store(s->y.as<double>(), prefactor, N, s->angular, ov[0].dev, ov[1].dev, s->fp64, s->stream),
             "store result");
-    // z lives in host memory read by the copy above: wait before it goes out of scope
+    // z lives in host memory read by the copy above: wait before it changes
     LM_CUDA(cudaStreamSynchronize(s->stream), "lanczos result");
     s->stats.iterations = m;
     s->stats.converged = converged ? 1 : 0;
@@ -643,7 +715,7 @@ lm_status lm_autotune(lm_solver* s, int reps, lm_pair_config* best) {
     char* fout = s->tune_out.as<char>();
     std::vector<lm_pair_config> cands;
     const int threads_opts[2] = {128, 256};
-    const int ilp_opts[3] = {1, 2, 4};
+    const int ilp_opts[4] = {1, 2, 4, 8};
     for (int t : threads_opts) {
         for (int il : ilp_opts) {
             if (!lmk::mdot_config_supported(s->fp64, s->angular, t, il)) continue;
@@ -720,9 +792,489 @@ lm_status lm_profile_read(lm_solver* s, lm_profile* out, int reset) {
 // out = f(T) e1, f = sqrt, for T = tridiag(beta, alpha, beta) of size m.
 int lm_tridiag_sqrt_e1(int m, const double* alpha, const double* beta, double* out) {
     if (m < 1 || !alpha || !out || (m > 1 && !beta)) return -2;
-    std::vector<double> work((size_t)m * m + 2 * m);
+    LanczosHost H;
+    H.alpha.assign(alpha, alpha + m);
+    H.beta.assign(beta ? beta : alpha, beta ? beta + (m - 1) : alpha);
     int cl = 0;
-    return lmk::tridiag_sqrt_e1(m, alpha, beta, work.data(), out, &cl);
+    const int r = H.solve(m, 1.0, &cl);
+    if (r == 0)
+        for (int i = 0; i < m; ++i) out[i] = H.z[i];
+    return r == -2 ? -1 : r;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// Batched systems (lm_batch_*): host side of the persistent kernel.
+// ===========================================================================
+struct lm_batch {
+    int S = 0;
+    int64_t Ntot = 0;
+    int m_max = 64;
+    cudaStream_t stream = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    int device = 0, sms = 1;
+    double eta = 1.0, a = 1.0;
+    std::vector<int64_t> off_h;
+    DBuf off, pos4, x64, Fbuf, u, w0, w1, V, alpha, beta, z, zprev, normW, rel, active, msys, itsum, notconv, nact;
+    DBuf items, item_range, chunks, chunk_range, part_item, part_chunk, td, trk, trc, trs, bar, ticket, err, flag;
+    DBuf in_stage, out_stage, W_stage;
+    int n_items = 0, n_chunks = 0, max_rot = 0;
+    int threads = 128, ilp = 1;
+    bool has_pos = false;
+    int* pinned = nullptr;
+    bool prof_on = false;
+    DBuf timeline;
+    int timeline_len = 0;
+    ~lm_batch() {
+        timeline.release();
+        DBuf* all[] = {&off, &pos4, &x64, &Fbuf, &u, &w0, &w1, &V, &alpha, &beta, &z, &zprev, &normW, &rel,
+                       &active, &msys, &itsum, &notconv, &nact, &items, &item_range, &chunks, &chunk_range,
+                       &part_item, &part_chunk, &td, &trk, &trc, &trs, &bar, &ticket, &err, &flag, &in_stage,
+                       &out_stage, &W_stage};
+        for (DBuf* b : all) b->release();
+        if (pinned) cudaFreeHost(pinned);
+        if (graph_stream) cudaStreamDestroy(graph_stream);
+    }
+};
+
+namespace {
+
+// Work items: systems in decreasing size, each cut into blocks of
+// threads * ilp particles.
+lm_status batch_build_items(lm_batch* b) {
+    const int per = b->threads * b->ilp;
+    std::vector<int> order(b->S);
+    for (int s = 0; s < b->S; ++s) order[s] = s;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return (b->off_h[x + 1] - b->off_h[x]) > (b->off_h[y + 1] - b->off_h[y]);
+    });
+    std::vector<int> items, range(2 * b->S);
+    for (int s : order) {
+        const int64_t n = b->off_h[s + 1] - b->off_h[s];
+        range[2 * s] = (int)(items.size() / 2);
+        for (int64_t i0 = 0; i0 < n; i0 += per) { items.push_back(s); items.push_back((int)i0); }
+        range[2 * s + 1] = (int)(items.size() / 2);
+    }
+    b->n_items = (int)(items.size() / 2);
+    LM_CUDA(b->items.ensure(items.size() * sizeof(int)), "batch items");
+    LM_CUDA(b->item_range.ensure(range.size() * sizeof(int)), "batch items");
+    LM_CUDA(b->part_item.ensure((size_t)b->n_items * sizeof(double)), "batch items");
+    LM_CUDA(cudaMemcpy(b->items.p, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice), "batch items");
+    LM_CUDA(cudaMemcpy(b->item_range.p, range.data(), range.size() * sizeof(int), cudaMemcpyHostToDevice),
+            "batch items");
+    return LM_OK;
+}
+
+int batch_grid(const lm_batch* b) {
+    const int occ = lmk::batch_ctas_per_sm(b->threads, b->ilp);
+    return std::max(1, occ) * b->sms;
+}
+
+lmk::BatchParams batch_params(lm_batch* b, int mode) {
+    lmk::BatchParams p = {};
+    p.S = b->S;
+    p.m_max = b->m_max;
+    p.mode = mode;
+    p.nsteps = 1;
+    p.Ntot = b->Ntot;
+    p.off = b->off.as<int64_t>();
+    p.pos4 = b->pos4.as<float4>();
+    p.x64 = b->x64.as<double>();
+    p.Fbuf = b->Fbuf.as<float>();
+    p.u = b->u.as<double>();
+    p.w0 = b->w0.as<double>();
+    p.w1 = b->w1.as<double>();
+    p.V = b->V.as<double>();
+    p.alpha = b->alpha.as<double>();
+    p.beta = b->beta.as<double>();
+    p.z = b->z.as<double>();
+    p.zprev = b->zprev.as<double>();
+    p.normW = b->normW.as<double>();
+    p.rel = b->rel.as<double>();
+    p.active = b->active.as<int>();
+    p.msys = b->msys.as<int>();
+    p.itsum = b->itsum.as<int>();
+    p.notconv = b->notconv.as<int>();
+    p.nact = b->nact.as<int>();
+    p.items = b->items.as<int>();
+    p.n_items = b->n_items;
+    p.item_range = b->item_range.as<int>();
+    p.chunks = b->chunks.as<int>();
+    p.n_chunks = b->n_chunks;
+    p.chunk_range = b->chunk_range.as<int>();
+    p.part_item = b->part_item.as<double>();
+    p.part_chunk = b->part_chunk.as<double>();
+    p.td = b->td.as<double>();
+    p.trk = b->trk.as<int>();
+    p.trc = b->trc.as<double>();
+    p.trs = b->trs.as<double>();
+    p.max_rot = b->max_rot;
+    p.bar = b->bar.as<unsigned>();
+    p.ticket = b->ticket.as<unsigned long long>();
+    p.err = b->err.as<int>();
+    p.spin_limit = 4000000000LL;  // ~2 s at 2 GHz: far above any phase
+    p.k = lmk::make_rpy_const<float>(b->a);
+    p.c8 = 1.0 / (8.0 * 3.14159265358979323846 * b->eta);
+    p.brk_rel = 1e-7;
+    p.prefactor = 1.0;
+    if (b->prof_on && b->timeline.p) {
+        p.timeline = b->timeline.as<unsigned long long>();
+        p.timeline_len = b->timeline_len;
+    }
+    return p;
+}
+
+// Reset the per-call device state and run the persistent kernel (directly or
+// captured in a CUDA graph on the batch's own stream); waits for it.
+lm_status batch_run(lm_batch* b, const lmk::BatchParams& p, bool use_graph) {
+    const int grid = batch_grid(b);
+    cudaStream_t st = b->stream;
+    if (use_graph) {
+        LM_CUDA(cudaStreamSynchronize(b->stream), "batch run");
+        if (!b->graph_stream)
+            LM_CUDA(cudaStreamCreateWithFlags(&b->graph_stream, cudaStreamNonBlocking), "batch graph stream");
+        st = b->graph_stream;
+        LM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "batch graph capture");
+    }
+    cudaError_t e = cudaMemsetAsync(b->bar.p, 0, 2 * sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ticket.p, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->err.p, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->itsum.p, 0, (size_t)b->S * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->notconv.p, 0, (size_t)b->S * sizeof(int), st);
+    if (e == cudaSuccess) e = lmk::launch_batch(p, b->threads, b->ilp, grid, st);
+    if (use_graph) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(st, &g);
+        if (e == cudaSuccess) e = e2;
+        cudaGraphExec_t ex = nullptr;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(ex, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (ex) cudaGraphExecDestroy(ex);
+        if (g) cudaGraphDestroy(g);
+    } else if (e == cudaSuccess) {
+        e = cudaStreamSynchronize(st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "batched kernel");
+    int errv = 0;
+    LM_CUDA(cudaMemcpy(&errv, b->err.p, sizeof(int), cudaMemcpyDeviceToHost), "batched kernel status");
+    if (errv == lmk::kBatchTimeout) return fail(LM_ERR_TIMEOUT, "a device-side barrier wait expired");
+    if (errv == lmk::kBatchTridiag) return fail(LM_ERR_CUDA, "tridiagonal eigensolver failed on the device");
+    return LM_OK;
+}
+
+lm_status check_batch(lm_batch* b, bool need_pos) {
+    if (b == nullptr) return fail(LM_ERR_INVALID_ARG, "batch is NULL");
+    if (need_pos && !b->has_pos) return fail(LM_ERR_STATE, "positions not set (call lm_batch_set_positions first)");
+    return LM_OK;
+}
+
+lm_status batch_stage_in(lm_batch* b, const void* p, size_t bytes, DBuf& buf, const void** out) {
+    *out = nullptr;
+    if (!p) return LM_OK;
+    if (is_device_ptr(p)) { *out = p; return LM_OK; }
+    LM_CUDA(buf.ensure(bytes), "staging input");
+    LM_CUDA(cudaMemcpyAsync(buf.p, p, bytes, cudaMemcpyHostToDevice, b->stream), "copy input");
+    *out = buf.p;
+    return LM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lm_status lm_batch_create(lm_batch** out, int64_t S, const int64_t* offsets, double viscosity,
+                          double hydrodynamic_radius, int max_iter, void* cuda_stream) {
+    g_err.clear();
+    if (!out) return fail(LM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (S < 1 || S > (1 << 20)) return fail(LM_ERR_INVALID_ARG, "S must be in [1, 2^20]");
+    if (!offsets) return fail(LM_ERR_INVALID_ARG, "offsets is NULL");
+    if (offsets[0] != 0) return fail(LM_ERR_INVALID_ARG, "offsets[0] must be 0");
+    for (int64_t s = 0; s < S; ++s) {
+        const int64_t n = offsets[s + 1] - offsets[s];
+        if (n < 1 || n > 65536) return fail(LM_ERR_INVALID_ARG, "system %lld has %lld particles (1..65536 allowed)",
+                                            (long long)s, (long long)n);
+    }
+    if (!(viscosity > 0.0) || !(hydrodynamic_radius > 0.0))
+        return fail(LM_ERR_INVALID_ARG, "viscosity and radius must be > 0");
+    if (max_iter < 1 || max_iter > 128) return fail(LM_ERR_INVALID_ARG, "max_iter must be in [1, 128]");
+    lm_batch* b = new (std::nothrow) lm_batch();
+    if (!b) return fail(LM_ERR_OOM, "host allocation failed");
+    std::unique_ptr<lm_batch> guard(b);
+    b->S = (int)S;
+    b->off_h.assign(offsets, offsets + S + 1);
+    b->Ntot = offsets[S];
+    b->m_max = max_iter;
+    b->eta = viscosity;
+    b->a = hydrodynamic_radius;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    LM_CUDA(cudaGetDevice(&b->device), "lm_batch_create");
+    LM_CUDA(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device), "lm_batch_create");
+    int coop = 0;
+    LM_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, b->device), "lm_batch_create");
+    if (!coop) return fail(LM_ERR_CUDA, "device does not support cooperative launches");
+    const int64_t n3 = 3 * b->Ntot;
+    const size_t S_ = (size_t)S, M = (size_t)b->m_max;
+    // chunks
+    std::vector<int> chunks, crange(2 * S_);
+    for (int64_t s = 0; s < S; ++s) {
+        const int64_t ns = 3 * (offsets[s + 1] - offsets[s]);
+        crange[2 * s] = (int)(chunks.size() / 2);
+        for (int64_t e0 = 0; e0 < ns; e0 += lmk::kBatchChunk) { chunks.push_back((int)s); chunks.push_back((int)e0); }
+        crange[2 * s + 1] = (int)(chunks.size() / 2);
+    }
+    b->n_chunks = (int)(chunks.size() / 2);
+    b->max_rot = (int)(4 * M * M + 64);
+    struct { DBuf* buf; size_t bytes; } allocs[] = {
+        {&b->off, (S_ + 1) * sizeof(int64_t)}, {&b->pos4, (size_t)b->Ntot * sizeof(float4)},
+        {&b->x64, (size_t)n3 * sizeof(double)}, {&b->Fbuf, (size_t)n3 * sizeof(float)},
+        {&b->u, (size_t)n3 * sizeof(double)}, {&b->w0, (size_t)n3 * sizeof(double)},
+        {&b->w1, (size_t)n3 * sizeof(double)}, {&b->V, M * (size_t)n3 * sizeof(double)},
+        {&b->alpha, S_ * M * sizeof(double)}, {&b->beta, S_ * M * sizeof(double)},
+        {&b->z, S_ * M * sizeof(double)}, {&b->zprev, S_ * M * sizeof(double)},
+        {&b->normW, S_ * sizeof(double)}, {&b->rel, S_ * sizeof(double)}, {&b->active, S_ * sizeof(int)},
+        {&b->msys, S_ * sizeof(int)}, {&b->itsum, S_ * sizeof(int)}, {&b->notconv, S_ * sizeof(int)},
+        {&b->nact, (M + 1) * sizeof(int)}, {&b->chunks, chunks.size() * sizeof(int)},
+        {&b->chunk_range, crange.size() * sizeof(int)},
+        {&b->part_chunk, 2 * (size_t)b->n_chunks * (M + 1) * sizeof(double)},
+        {&b->td, S_ * 2 * M * sizeof(double)}, {&b->trk, S_ * (size_t)b->max_rot * sizeof(int)},
+        {&b->trc, S_ * (size_t)b->max_rot * sizeof(double)}, {&b->trs, S_ * (size_t)b->max_rot * sizeof(double)},
+        {&b->bar, 4 * sizeof(unsigned)}, {&b->ticket, sizeof(unsigned long long)}, {&b->err, sizeof(int)},
+        {&b->flag, sizeof(int)}};
+    for (auto& al : allocs) LM_CUDA(al.buf->ensure(al.bytes), "allocating batch buffers");
+    LM_CUDA(cudaMemcpy(b->off.p, offsets, (S_ + 1) * sizeof(int64_t), cudaMemcpyHostToDevice), "batch offsets");
+    LM_CUDA(cudaMemcpy(b->chunks.p, chunks.data(), chunks.size() * sizeof(int), cudaMemcpyHostToDevice), "chunks");
+    LM_CUDA(cudaMemcpy(b->chunk_range.p, crange.data(), crange.size() * sizeof(int), cudaMemcpyHostToDevice),
+            "chunks");
+    LM_CUDA(cudaMemset(b->bar.p, 0, 4 * sizeof(unsigned)), "batch barrier");
+    if (lm_status st = batch_build_items(b)) return st;
+    LM_CUDA(cudaMallocHost(reinterpret_cast<void**>(&b->pinned), 2 * S_ * sizeof(int)), "batch pinned");
+    *out = guard.release();
+    return LM_OK;
+}
+
+lm_status lm_batch_destroy(lm_batch* b) {
+    if (!b) return LM_OK;
+    DeviceGuard g(b->device);
+    cudaStreamSynchronize(b->stream);
+    delete b;
+    return LM_OK;
+}
+
+lm_status lm_batch_set_positions(lm_batch* b, const float* pos) {
+    if (lm_status st = check_batch(b, false)) return st;
+    if (!pos) return fail(LM_ERR_INVALID_ARG, "pos is NULL");
+    DeviceGuard g(b->device);
+    b->has_pos = false;
+    const void* d = nullptr;
+    if (lm_status st = batch_stage_in(b, pos, (size_t)b->Ntot * 3 * sizeof(float), b->in_stage, &d)) return st;
+    LM_CUDA(cudaMemsetAsync(b->flag.p, 0, sizeof(int), b->stream), "batch positions");
+    LM_CUDA(lmk::launch_batch_pack(static_cast<const float*>(d), b->Ntot, b->pos4.as<float4>(), b->x64.as<double>(),
+                                   b->flag.as<int>(), b->stream),
+            "batch positions");
+    LM_CUDA(cudaMemcpyAsync(b->pinned, b->flag.p, sizeof(int), cudaMemcpyDeviceToHost, b->stream), "batch positions");
+    LM_CUDA(cudaStreamSynchronize(b->stream), "batch positions");
+    if (b->pinned[0]) return fail(LM_ERR_NONFINITE, "positions contain NaN/Inf or |x| > 1e15");
+    b->has_pos = true;
+    return LM_OK;
+}
+
+lm_status lm_batch_get_positions(lm_batch* b, float* pos_out) {
+    if (lm_status st = check_batch(b, true)) return st;
+    if (!pos_out) return fail(LM_ERR_INVALID_ARG, "pos_out is NULL");
+    DeviceGuard g(b->device);
+    const size_t bytes = (size_t)b->Ntot * 3 * sizeof(float);
+    const bool host = !is_device_ptr(pos_out);
+    float* d = pos_out;
+    if (host) {
+        LM_CUDA(b->out_stage.ensure(bytes), "staging output");
+        d = b->out_stage.as<float>();
+    }
+    LM_CUDA(lmk::launch_batch_unpack(b->x64.as<double>(), b->Ntot, d, b->stream), "batch positions");
+    if (host) LM_CUDA(cudaMemcpyAsync(pos_out, d, bytes, cudaMemcpyDeviceToHost, b->stream), "batch positions");
+    LM_CUDA(cudaStreamSynchronize(b->stream), "batch positions");
+    return LM_OK;
+}
+
+lm_status lm_batch_mdot(lm_batch* b, const float* forces, float* lin_out) {
+    if (lm_status st = check_batch(b, true)) return st;
+    if (!forces || !lin_out) return fail(LM_ERR_INVALID_ARG, "forces and lin_out are required");
+    DeviceGuard g(b->device);
+    const size_t bytes = (size_t)b->Ntot * 3 * sizeof(float);
+    const void* dF = nullptr;
+    if (lm_status st = batch_stage_in(b, forces, bytes, b->in_stage, &dF)) return st;
+    const bool host = !is_device_ptr(lin_out);
+    float* dout = lin_out;
+    if (host) {
+        LM_CUDA(b->out_stage.ensure(bytes), "staging output");
+        dout = b->out_stage.as<float>();
+    }
+    lmk::BatchParams p = batch_params(b, lmk::kBatchMdot);
+    p.F_in = static_cast<const float*>(dF);
+    p.lin_out = dout;
+    if (lm_status st = batch_run(b, p, false)) return st;
+    if (host) LM_CUDA(cudaMemcpy(lin_out, dout, bytes, cudaMemcpyDeviceToHost), "copy output");
+    return LM_OK;
+}
+
+lm_status lm_batch_sqrt_mdot(lm_batch* b, const double* W, uint64_t seed, double prefactor, double tol,
+                             float* lin_out, int* iters_out) {
+    if (lm_status st = check_batch(b, true)) return st;
+    if (!lin_out) return fail(LM_ERR_INVALID_ARG, "lin_out is NULL");
+    if (!(tol >= 0.0) || !std::isfinite(prefactor)) return fail(LM_ERR_INVALID_ARG, "bad tol or prefactor");
+    DeviceGuard g(b->device);
+    const size_t bytes = (size_t)b->Ntot * 3 * sizeof(float);
+    const void* dW = nullptr;
+    if (lm_status st = batch_stage_in(b, W, (size_t)b->Ntot * 3 * sizeof(double), b->W_stage, &dW)) return st;
+    const bool host = !is_device_ptr(lin_out);
+    float* dout = lin_out;
+    if (host) {
+        LM_CUDA(b->out_stage.ensure(bytes), "staging output");
+        dout = b->out_stage.as<float>();
+    }
+    lmk::BatchParams p = batch_params(b, lmk::kBatchSqrt);
+    p.W_in = static_cast<const double*>(dW);
+    p.seed = seed;
+    p.tol = tol;
+    p.prefactor = prefactor;
+    p.lin_out = dout;
+    if (lm_status st = batch_run(b, p, false)) return st;
+    if (host) LM_CUDA(cudaMemcpy(lin_out, dout, bytes, cudaMemcpyDeviceToHost), "copy output");
+    std::vector<int> nc(b->S), its(b->S);
+    LM_CUDA(cudaMemcpy(its.data(), b->itsum.p, b->S * sizeof(int), cudaMemcpyDeviceToHost), "iterations");
+    LM_CUDA(cudaMemcpy(nc.data(), b->notconv.p, b->S * sizeof(int), cudaMemcpyDeviceToHost), "iterations");
+    if (iters_out) std::copy(its.begin(), its.end(), iters_out);
+    for (int v : nc)
+        if (v) return fail(LM_ERR_NOT_CONVERGED, "some systems reached max_iter before tol %.3g", tol);
+    return LM_OK;
+}
+
+lm_status lm_batch_bd_run(lm_batch* b, double kT, double dt, double k_trap, int nsteps, int64_t step0,
+                          uint64_t seed, double tol, int use_graph, int* iters_out) {
+    if (lm_status st = check_batch(b, true)) return st;
+    if (nsteps < 1 || !(kT >= 0.0) || !(dt >= 0.0) || !std::isfinite(k_trap) || !(tol >= 0.0) || step0 < 0)
+        return fail(LM_ERR_INVALID_ARG, "bad Brownian-dynamics parameters");
+    DeviceGuard g(b->device);
+    lmk::BatchParams p = batch_params(b, lmk::kBatchBD);
+    p.nsteps = nsteps;
+    p.step0 = step0;
+    p.kT = kT;
+    p.dt = dt;
+    p.k_trap = k_trap;
+    p.tol = tol;
+    p.seed = seed;
+    if (lm_status st = batch_run(b, p, use_graph != 0)) return st;
+    if (iters_out)
+        LM_CUDA(cudaMemcpy(iters_out, b->itsum.p, b->S * sizeof(int), cudaMemcpyDeviceToHost), "iterations");
+    std::vector<int> nc(b->S);
+    LM_CUDA(cudaMemcpy(nc.data(), b->notconv.p, b->S * sizeof(int), cudaMemcpyDeviceToHost), "iterations");
+    for (int v : nc)
+        if (v) return fail(LM_ERR_NOT_CONVERGED, "some systems reached max_iter before tol %.3g", tol);
+    return LM_OK;
+}
+
+lm_status lm_batch_set_tiling(lm_batch* b, int threads, int ilp) {
+    if (lm_status st = check_batch(b, false)) return st;
+    if (!lmk::batch_tiling_supported(threads, ilp))
+        return fail(LM_ERR_INVALID_ARG, "unsupported batch tiling (threads %d, ilp %d)", threads, ilp);
+    DeviceGuard g(b->device);
+    b->threads = threads;
+    b->ilp = ilp;
+    return batch_build_items(b);
+}
+
+lm_status lm_batch_autotune(lm_batch* b, int* threads_out, int* ilp_out) {
+    if (lm_status st = check_batch(b, true)) return st;
+    DeviceGuard g(b->device);
+    const size_t bytes = (size_t)b->Ntot * 3 * sizeof(float);
+    LM_CUDA(b->in_stage.ensure(bytes), "autotune buffers");
+    LM_CUDA(b->out_stage.ensure(bytes), "autotune buffers");
+    LM_CUDA(cudaMemsetAsync(b->in_stage.p, 0, bytes, b->stream), "autotune buffers");
+    const int opts[4][2] = {{64, 1}, {64, 2}, {128, 1}, {128, 2}};
+    float best = 1e30f;
+    int bt = b->threads, bi = b->ilp;
+    cudaEvent_t e0, e1;
+    LM_CUDA(cudaEventCreate(&e0), "autotune");
+    LM_CUDA(cudaEventCreate(&e1), "autotune");
+    lm_status result = LM_OK;
+    for (auto& o : opts) {
+        if ((result = lm_batch_set_tiling(b, o[0], o[1])) != LM_OK) break;
+        lmk::BatchParams p = batch_params(b, lmk::kBatchMdot);
+        p.F_in = b->in_stage.as<float>();
+        p.lin_out = b->out_stage.as<float>();
+        if ((result = batch_run(b, p, false)) != LM_OK) break;  // warm-up
+        cudaEventRecord(e0, b->stream);
+        for (int r = 0; r < 3 && result == LM_OK; ++r) result = batch_run(b, p, false);
+        cudaEventRecord(e1, b->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (result == LM_OK && ms < best) { best = ms; bt = o[0]; bi = o[1]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (result != LM_OK) return result;
+    if (lm_status st = lm_batch_set_tiling(b, bt, bi)) return st;
+    if (threads_out) *threads_out = bt;
+    if (ilp_out) *ilp_out = bi;
+    return LM_OK;
+}
+
+lm_status lm_batch_profile_enable(lm_batch* b, int enable) {
+    if (lm_status st = check_batch(b, false)) return st;
+    DeviceGuard g(b->device);
+    b->prof_on = enable != 0;
+    if (b->prof_on) {
+        b->timeline_len = 4 + 5 * b->m_max;
+        LM_CUDA(b->timeline.ensure((size_t)b->timeline_len * sizeof(unsigned long long)), "batch timeline");
+        LM_CUDA(cudaMemset(b->timeline.p, 0, (size_t)b->timeline_len * sizeof(unsigned long long)), "timeline");
+    }
+    return LM_OK;
+}
+
+lm_status lm_batch_profile_read(lm_batch* b, uint64_t* out, int n, int* count) {
+    if (lm_status st = check_batch(b, false)) return st;
+    if (!out || n < 0) return fail(LM_ERR_INVALID_ARG, "bad output array");
+    DeviceGuard g(b->device);
+    std::vector<unsigned long long> t(b->timeline_len);
+    if (b->timeline.p && b->timeline_len)
+        LM_CUDA(cudaMemcpy(t.data(), b->timeline.p, t.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost),
+                "timeline");
+    int c = 0;
+    while (c < (int)t.size() && t[c] != 0) ++c;
+    for (int i = 0; i < std::min(c, n); ++i) out[i] = t[i];
+    if (count) *count = c;
+    return LM_OK;
+}
+
+lm_status lm_philox_normals(uint64_t seed, uint64_t stream, double* out, int64_t n, void* cuda_stream) {
+    if (!out || n < 0) return fail(LM_ERR_INVALID_ARG, "out must be a device array and n >= 0");
+    if (!is_device_ptr(out)) return fail(LM_ERR_INVALID_ARG, "out must be device memory");
+    if (n == 0) return LM_OK;
+    LM_CUDA(lmk::lz_philox_normals(seed, stream, out, n, static_cast<cudaStream_t>(cuda_stream)), "noise generator");
+    return LM_OK;
+}
+
+// Test hook for the bounded waits of the persistent kernel: a barrier that can
+// never complete must end with LM_ERR_TIMEOUT after about spin_cycles cycles.
+lm_status lm_batch_timeout_selftest(long long spin_cycles) {
+    if (spin_cycles < 1000 || spin_cycles > 100000000LL)
+        return fail(LM_ERR_INVALID_ARG, "spin_cycles must be in [1e3, 1e8]");
+    DBuf bar, err;
+    LM_CUDA(bar.ensure(4 * sizeof(unsigned)), "selftest");
+    LM_CUDA(err.ensure(sizeof(int)), "selftest");
+    LM_CUDA(cudaMemset(bar.p, 0, 4 * sizeof(unsigned)), "selftest");
+    LM_CUDA(cudaMemset(err.p, 0, sizeof(int)), "selftest");
+    LM_CUDA(lmk::launch_batch_timeout_probe(bar.as<unsigned>(), err.as<int>(), spin_cycles, 4, nullptr), "selftest");
+    LM_CUDA(cudaDeviceSynchronize(), "selftest");
+    int e = 0;
+    LM_CUDA(cudaMemcpy(&e, err.p, sizeof(int), cudaMemcpyDeviceToHost), "selftest");
+    bar.release();
+    err.release();
+    if (e == lmk::kBatchTimeout) return fail(LM_ERR_TIMEOUT, "barrier wait expired as intended");
+    return fail(LM_ERR_CUDA, "timeout probe did not report a timeout");
 }
 
 }  // extern "C"

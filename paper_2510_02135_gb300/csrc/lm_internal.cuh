@@ -151,4 +151,76 @@ cudaError_t lz_store(const double* y, double scale, int64_t N, int angular, void
 // two Box-Muller pairs from the words (0, 1) and (2, 3).
 cudaError_t lz_philox_normals(uint64_t seed, uint64_t stream, double* W, int64_t n, cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Batched persistent kernel (batch_kernels.cu) over S concatenated systems.
+// ---------------------------------------------------------------------------
+enum BatchMode { kBatchBD = 0, kBatchMdot = 1, kBatchSqrt = 2 };
+enum BatchError { kBatchOk = 0, kBatchTimeout = 1, kBatchTridiag = 2 };
+constexpr int kBatchChunk = 1024;      // elements per vector-phase work unit
+
+struct BatchParams {
+    int S, m_max, mode, nsteps;
+    int64_t Ntot;                      // particles over all systems
+    int64_t step0;
+    const int64_t* off;                // S + 1 particle offsets
+    float4* pos4;                      // Ntot packed FP32 positions for the pair kernel
+    double* x64;                       // 3 Ntot FP64 positions (the BD state)
+    float* Fbuf;                       // 3 Ntot forces of the step
+    double* u;                         // 3 Ntot drift product M F
+    double* w0;                        // 3 Ntot Lanczos residual, even iterations
+    double* w1;                        // 3 Ntot Lanczos residual, odd iterations
+    double* V;                         // Krylov bases: system s at V + m_max * 3 off[s], row j stride 3 N_s
+    double* alpha;                     // S x m_max
+    double* beta;                      // S x m_max
+    double* z;                         // S x m_max: |W| f(T_k) e1 of the latest iteration
+    double* zprev;                     // S x m_max
+    double* normW;                     // S
+    double* rel;                       // S: last relative change
+    int* active;                       // S: 1 while iterating in the current step
+    int* msys;                         // S: iterations used in the current step
+    int* itsum;                        // S: iterations summed over the call
+    int* notconv;                      // S: 1 if max_iter was reached in some step
+    int* nact;                         // m_max + 1 counters of systems still active
+    const int* items;                  // n_items x (system, first particle)
+    int n_items;
+    const int* item_range;             // S x (first item, end item)
+    const int* chunks;                 // n_chunks x (system, first element)
+    int n_chunks;
+    const int* chunk_range;            // S x (first chunk, end chunk)
+    double* part_item;                 // n_items partial dots
+    double* part_chunk;                // 2 x n_chunks x (m_max + 1) partial dots
+    double* td;                        // S x 2 m_max tridiagonal scratch
+    int* trk;                          // S x max_rot rotation indices
+    double* trc;                       // S x max_rot rotation cosines
+    double* trs;                       // S x max_rot rotation sines
+    int max_rot;
+    unsigned* bar;                     // grid barrier: count, generation
+    unsigned long long* ticket;        // dynamic work counter
+    int* err;                          // BatchError
+    long long spin_limit;              // clock cycles a barrier may wait
+    RpyConst<float> k;
+    double c8;                         // 1 / (8 pi eta)
+    double kT, dt, k_trap, tol, brk_rel, prefactor;
+    uint64_t seed;
+    const float* F_in;                 // kBatchMdot input
+    float* lin_out;                    // kBatchMdot / kBatchSqrt output
+    const double* W_in;                // kBatchSqrt noise (nullable: Philox)
+    unsigned long long* timeline;      // nullable: phase end times (ns) of the first step
+    int timeline_len;
+};
+
+// Launch the persistent kernel (cooperative) with `threads` x `ilp` tiling.
+cudaError_t launch_batch(const BatchParams& p, int threads, int ilp, int grid, cudaStream_t s);
+// CTAs of the persistent kernel that can be co-resident per SM.
+int batch_ctas_per_sm(int threads, int ilp);
+bool batch_tiling_supported(int threads, int ilp);
+// Pack N x 3 float positions into pos4 and x64.
+cudaError_t launch_batch_pack(const float* pos, int64_t N, float4* pos4, double* x64, int* bad, cudaStream_t s);
+// out (N x 3 float) = x64
+cudaError_t launch_batch_unpack(const double* x64, int64_t N, float* out, cudaStream_t s);
+// A kernel whose barrier waits for one CTA more than it launches: every
+// wait runs out after spin_limit cycles and *err becomes kBatchTimeout.
+cudaError_t launch_batch_timeout_probe(unsigned* bar, int* err, long long spin_limit, int grid,
+                                       cudaStream_t s);
+
 }  // namespace lmk

@@ -65,12 +65,12 @@ __device__ __forceinline__ void exact_coeffs(R r2, const RpyConst<R>& k, R& A, R
     }
 }
 
-// Accumulators of one i-particle.
+// Current-tile partial sums of one i-particle (registers).  The running
+// sums across tiles live in shared memory (FP32: a TwoSum (hi, lo) pair per
+// component; FP64: a plain sum), read and written once per tile.
 template <typename R, bool ANG>
 struct Acc {
-    R p[ANG ? 6 : 3];    // current-tile partial
-    R hi[ANG ? 6 : 3];   // compensated running sum (FP32 only)
-    R lo[ANG ? 6 : 3];
+    R p[ANG ? 6 : 3];
 };
 
 // Far-field pair: u += A F + B (d.F) d + g (T x d) ; w += g (F x d - T/2) + br (d.T) d
@@ -135,19 +135,27 @@ __device__ __forceinline__ void pair_exact(R dx, R dy, R dz, R r2, const typenam
     }
 }
 
-// Knuth TwoSum fold of the tile partial into (hi, lo).
-__device__ __forceinline__ void fold(float& hi, float& lo, float& p) {
-    const float s = hi + p;
-    const float bb = s - hi;
-    const float err = (hi - (s - bb)) + (p - bb);
-    hi = s;
-    lo += err;
+// Knuth TwoSum fold of the tile partial p into the shared (hi, lo) pair.
+__device__ __forceinline__ void fold(float* hi, float* lo, float& p) {
+    const float h = *hi;
+    const float s = h + p;
+    const float bb = s - h;
+    const float err = (h - (s - bb)) + (p - bb);
+    *hi = s;
+    *lo += err;
     p = 0.0f;
 }
-__device__ __forceinline__ void fold(double& hi, double& lo, double& p) {
-    hi += p;
+__device__ __forceinline__ void fold(double* hi, double* lo, double& p) {
+    *hi += p;
     p = 0.0;
     (void)lo;
+}
+
+// Dynamic shared memory for the running sums: C x NI x NT values of R
+// (FP32 adds the same again for the low parts).
+template <typename R, bool ANG, int NT, int NI>
+constexpr size_t running_sum_bytes() {
+    return (size_t)(ANG ? 6 : 3) * NI * NT * sizeof(R) * (sizeof(R) == 4 ? 2 : 1);
 }
 
 template <typename R, bool ANG, int NT, int NI>
@@ -161,6 +169,9 @@ __global__ void __launch_bounds__(NT) rpy_mdot_kernel(const typename V4<R>::type
     __shared__ R4 sp[NT];
     __shared__ R4 sf[NT];
     __shared__ R4 sh[ANG ? NT : 1];
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    R* s_hi = reinterpret_cast<R*>(dyn_smem);              // [c][q][tid]
+    R* s_lo = s_hi + (sizeof(R) == 4 ? C * NI * NT : 0);     // FP32 only
 
     const int tid = threadIdx.x;
     const int64_t i0 = (int64_t)blockIdx.x * (NT * NI);
@@ -180,7 +191,11 @@ __global__ void __launch_bounds__(NT) rpy_mdot_kernel(const typename V4<R>::type
             xi[q] = -pad; yi[q] = -pad; zi[q] = -pad;
         }
 #pragma unroll
-        for (int c = 0; c < C; ++c) { acc[q].p[c] = R(0); acc[q].hi[c] = R(0); acc[q].lo[c] = R(0); }
+        for (int c = 0; c < C; ++c) {
+            acc[q].p[c] = R(0);
+            s_hi[(c * NI + q) * NT + tid] = R(0);
+            if (sizeof(R) == 4) s_lo[(c * NI + q) * NT + tid] = R(0);
+        }
     }
 
     // register prefetch of this thread's j in the first tile
@@ -239,7 +254,10 @@ __global__ void __launch_bounds__(NT) rpy_mdot_kernel(const typename V4<R>::type
 #pragma unroll
         for (int q = 0; q < NI; ++q) {
 #pragma unroll
-            for (int c = 0; c < C; ++c) fold(acc[q].hi[c], acc[q].lo[c], acc[q].p[c]);
+            for (int c = 0; c < C; ++c) {
+                const int o = (c * NI + q) * NT + tid;
+                fold(&s_hi[o], &s_lo[o], acc[q].p[c]);
+            }
         }
         __syncthreads();
     }
@@ -251,7 +269,8 @@ __global__ void __launch_bounds__(NT) rpy_mdot_kernel(const typename V4<R>::type
         if (i >= N) continue;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            const double v = (double)acc[q].hi[c] + (double)acc[q].lo[c];
+            const int o = (c * NI + q) * NT + tid;
+            const double v = (double)s_hi[o] + (sizeof(R) == 4 ? (double)s_lo[o] : 0.0);
             if (direct) {
                 void* out = (c < 3) ? lin : ang;
                 const int64_t idx = 3 * i + (c % 3);
@@ -300,8 +319,16 @@ cudaError_t launch_t(const MdotArgs& a, cudaStream_t s) {
     const RpyConst<R> k = make_rpy_const<R>(a.a);
     dim3 grid((unsigned)nblk, (unsigned)splits);
     if (splits > 1 && a.partials == nullptr) return cudaErrorInvalidValue;
+    constexpr size_t dyn = running_sum_bytes<R, ANG, NT, NI>();
+    static bool attr_set = false;  // per instantiation; the attribute is process-wide
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(rpy_mdot_kernel<R, ANG, NT, NI>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
     if (a.ev_begin) cudaEventRecord(a.ev_begin, s);
-    rpy_mdot_kernel<R, ANG, NT, NI><<<grid, NT, 0, s>>>(
+    rpy_mdot_kernel<R, ANG, NT, NI><<<grid, NT, dyn, s>>>(
         static_cast<const typename V4<R>::type*>(a.pos4), a.F, ANG ? a.T : nullptr, a.in_f64, a.N, jchunk, k, c8,
         a.lin, a.ang, a.out_f64, a.partials);
     cudaError_t err = cudaGetLastError();
@@ -316,14 +343,25 @@ cudaError_t launch_t(const MdotArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Instantiated configurations: FP32 threads {128, 256} x ilp {1, 2, 4, 8};
+// FP64 (parity path) threads {128, 256} x ilp {1, 2}.
+template <typename R>
+constexpr bool ilp_ok(int ilp) {
+    return sizeof(R) == 4 ? (ilp == 1 || ilp == 2 || ilp == 4 || ilp == 8) : (ilp == 1 || ilp == 2);
+}
+
 template <typename R, bool ANG>
 cudaError_t launch_r(const MdotArgs& a, cudaStream_t s) {
     if (a.threads == 128 && a.ilp == 1) return launch_t<R, ANG, 128, 1>(a, s);
     if (a.threads == 128 && a.ilp == 2) return launch_t<R, ANG, 128, 2>(a, s);
-    if (a.threads == 128 && a.ilp == 4) return launch_t<R, ANG, 128, 4>(a, s);
     if (a.threads == 256 && a.ilp == 1) return launch_t<R, ANG, 256, 1>(a, s);
     if (a.threads == 256 && a.ilp == 2) return launch_t<R, ANG, 256, 2>(a, s);
-    if (a.threads == 256 && a.ilp == 4) return launch_t<R, ANG, 256, 4>(a, s);
+    if constexpr (sizeof(R) == 4) {
+        if (a.threads == 128 && a.ilp == 4) return launch_t<R, ANG, 128, 4>(a, s);
+        if (a.threads == 128 && a.ilp == 8) return launch_t<R, ANG, 128, 8>(a, s);
+        if (a.threads == 256 && a.ilp == 4) return launch_t<R, ANG, 256, 4>(a, s);
+        if (a.threads == 256 && a.ilp == 8) return launch_t<R, ANG, 256, 8>(a, s);
+    }
     return cudaErrorInvalidConfiguration;
 }
 
@@ -331,10 +369,19 @@ template <typename R, bool ANG>
 int occupancy_r(int threads, int ilp) {
     int n = 0;
     cudaError_t e = cudaErrorInvalidConfiguration;
-#define LM_OCC(NT, NI)                                                                                 \
-    if (threads == NT && ilp == NI)                                                                    \
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rpy_mdot_kernel<R, ANG, NT, NI>, NT, 0);
-    LM_OCC(128, 1) LM_OCC(128, 2) LM_OCC(128, 4) LM_OCC(256, 1) LM_OCC(256, 2) LM_OCC(256, 4)
+#define LM_OCC(NT, NI)                                                                             \
+    if (threads == NT && ilp == NI) {                                                              \
+        constexpr size_t dyn = running_sum_bytes<R, ANG, NT, NI>();                                \
+        e = cudaFuncSetAttribute(rpy_mdot_kernel<R, ANG, NT, NI>,                                  \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);           \
+        if (e == cudaSuccess)                                                                      \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rpy_mdot_kernel<R, ANG, NT, NI>, \
+                                                              NT, dyn);                            \
+    }
+    LM_OCC(128, 1) LM_OCC(128, 2) LM_OCC(256, 1) LM_OCC(256, 2)
+    if constexpr (sizeof(R) == 4) {
+        LM_OCC(128, 4) LM_OCC(128, 8) LM_OCC(256, 4) LM_OCC(256, 8)
+    }
 #undef LM_OCC
     return e == cudaSuccess ? n : 0;
 }
@@ -352,8 +399,8 @@ int mdot_ctas_per_sm(int fp64, int angular, int threads, int ilp) {
 }
 
 bool mdot_config_supported(int fp64, int angular, int threads, int ilp) {
-    (void)fp64; (void)angular;
-    return (threads == 128 || threads == 256) && (ilp == 1 || ilp == 2 || ilp == 4);
+    (void)angular;
+    return (threads == 128 || threads == 256) && (fp64 ? ilp_ok<double>(ilp) : ilp_ok<float>(ilp));
 }
 
 int mdot_partial_components(int angular) { return angular ? 6 : 3; }

@@ -1,8 +1,12 @@
 // f(T) e1 with f = sqrt for a small symmetric tridiagonal T, the last step
 // of the Krylov square root M^{1/2} W ~ |W| V_m T_m^{1/2} e1 (libMobility
-// paper, Sec. 3.3).  Eigen-decomposition by implicit symmetric QR steps with
+// paper, Sec. 3.3).  Eigenvalues by implicit symmetric QR steps with
 // Wilkinson shifts and bulge chasing (Golub & Van Loan, "Matrix
-// Computations", Sec. 8.3), written for host and device.
+// Computations", Sec. 8.3).  The eigenvector matrix Q is the product of the
+// Givens rotations of all QR steps, Q = J_1 J_2 ... J_K; instead of forming it
+// (O(m^3)), the rotations are recorded and applied to two vectors:
+//   r = Q^T e1 = J_K^T ... J_1^T e1,   z = Q (f(Lambda) r) = J_1 ... J_K (f(Lambda) r),
+// which costs O(K) = O(m^2).  Host and device.
 #pragma once
 
 #include <cmath>
@@ -14,14 +18,14 @@
 
 namespace lmk {
 
-// d[0..m-1] diagonal, e[0..m-2] off-diagonal (destroyed); Q is m x m
-// row-major and receives the eigenvectors in its columns; on return d holds
-// the eigenvalues.  Returns 0, or -1 if 30 m QR steps did not converge.
-__host__ __device__ inline int tridiag_eig(int m, double* d, double* e, double* Q) {
+// d[0..m-1] diagonal, e[0..m-2] off-diagonal (both destroyed; d receives the
+// eigenvalues).  Rotation t acts on (rk[t], rk[t]+1) with (rc[t], rs[t]).
+// Returns 0; -1 if 30 m QR steps did not converge; -2 if more than max_rot
+// rotations were needed.
+__host__ __device__ inline int tridiag_qr_rotations(int m, double* d, double* e, int* rk, double* rc, double* rs,
+                                                    int max_rot, int* nrot) {
     const double eps = 2.220446049250313e-16;
-    for (int r = 0; r < m; ++r)
-        for (int c = 0; c < m; ++c) Q[r * m + c] = (r == c) ? 1.0 : 0.0;
-    int steps = 0;
+    int steps = 0, nr = 0;
     int hi = m - 1;
     while (hi > 0) {
         if (fabs(e[hi - 1]) <= eps * (fabs(d[hi - 1]) + fabs(d[hi]))) {
@@ -32,19 +36,24 @@ __host__ __device__ inline int tridiag_eig(int m, double* d, double* e, double* 
         int lo = hi - 1;
         while (lo > 0 && fabs(e[lo - 1]) > eps * (fabs(d[lo - 1]) + fabs(d[lo]))) --lo;
         if (lo > 0) e[lo - 1] = 0.0;
-        if (++steps > 30 * m) return -1;
+        if (++steps > 30 * m) { *nrot = nr; return -1; }
         // Wilkinson shift: eigenvalue of the trailing 2x2 closer to d[hi]
         const double delta = 0.5 * (d[hi - 1] - d[hi]);
         const double bb = e[hi - 1];
-        const double den = delta + copysign(hypot(delta, bb), delta);
+        const double den = delta + copysign(sqrt(delta * delta + bb * bb), delta);
         const double mu = d[hi] - bb * bb / den;
         double x = d[lo] - mu;
         double z = e[lo];
         for (int k = lo; k < hi; ++k) {
-            // rotation J = [[c, -s], [s, c]] with J^T [x; z] = [r; 0]
-            const double r = hypot(x, z);
+            // rotation J = [[c, -s], [s, c]] on (k, k+1) with J^T [x; z] = [r; 0]
+            // entries of T are of the order of the mobility: no over/underflow in x^2 + z^2
+            const double r = sqrt(x * x + z * z);
             double c = 1.0, s = 0.0;
-            if (r > 0.0) { c = x / r; s = z / r; }
+            if (r > 0.0) {
+                const double inv = 1.0 / r;
+                c = x * inv;
+                s = z * inv;
+            }
             if (k > lo) e[k - 1] = r;
             const double ak = d[k], ak1 = d[k + 1], bk = e[k];
             d[k] = c * c * ak + 2.0 * c * s * bk + s * s * ak1;
@@ -55,36 +64,51 @@ __host__ __device__ inline int tridiag_eig(int m, double* d, double* e, double* 
                 z = s * e[k + 1];
                 e[k + 1] = c * e[k + 1];
             }
-            for (int rr = 0; rr < m; ++rr) {
-                const double q0 = Q[rr * m + k], q1 = Q[rr * m + k + 1];
-                Q[rr * m + k] = c * q0 + s * q1;
-                Q[rr * m + k + 1] = -s * q0 + c * q1;
-            }
+            if (nr >= max_rot) { *nrot = nr; return -2; }
+            rk[nr] = k; rc[nr] = c; rs[nr] = s;
+            ++nr;
         }
     }
+    *nrot = nr;
     return 0;
 }
 
-// out = f(T) e1, f = sqrt, with eigenvalues below zero (round-off) clamped
-// to zero; *clamped counts them.  work needs m*m + 2m doubles.
-__host__ __device__ inline int tridiag_sqrt_e1(int m, const double* alpha, const double* beta, double* work,
-                                               double* out, int* clamped) {
-    double* Q = work;
-    double* d = work + m * m;
-    double* e = d + m;
+// out = f(T) e1, f = sqrt, eigenvalues below zero (round-off) clamped to 0
+// and counted in *clamped.  d, e: m doubles of scratch each; rk, rc, rs:
+// max_rot entries of scratch.
+__host__ __device__ inline int tridiag_sqrt_e1(int m, const double* alpha, const double* beta, double* d, double* e,
+                                               int* rk, double* rc, double* rs, int max_rot, double* out,
+                                               int* clamped) {
     for (int i = 0; i < m; ++i) d[i] = alpha[i];
     for (int i = 0; i + 1 < m; ++i) e[i] = beta[i];
-    const int rc = tridiag_eig(m, d, e, Q);
+    int nr = 0;
+    const int rc_ = tridiag_qr_rotations(m, d, e, rk, rc, rs, max_rot, &nr);
+    if (rc_ != 0) return rc_;
+    // r = Q^T e1
+    for (int i = 0; i < m; ++i) out[i] = (i == 0) ? 1.0 : 0.0;
+    for (int t = 0; t < nr; ++t) {
+        const int k = rk[t];
+        const double c = rc[t], s = rs[t];
+        const double a = out[k], b = out[k + 1];
+        out[k] = c * a + s * b;
+        out[k + 1] = -s * a + c * b;
+    }
     int nclamp = 0;
-    for (int r = 0; r < m; ++r) out[r] = 0.0;
     for (int i = 0; i < m; ++i) {
         double lam = d[i];
         if (lam < 0.0) { lam = 0.0; ++nclamp; }
-        const double w = sqrt(lam) * Q[0 * m + i];
-        for (int r = 0; r < m; ++r) out[r] += w * Q[r * m + i];
+        out[i] *= sqrt(lam);
+    }
+    // z = Q v
+    for (int t = nr - 1; t >= 0; --t) {
+        const int k = rk[t];
+        const double c = rc[t], s = rs[t];
+        const double a = out[k], b = out[k + 1];
+        out[k] = c * a - s * b;
+        out[k + 1] = s * a + c * b;
     }
     if (clamped) *clamped = nclamp;
-    return rc;
+    return 0;
 }
 
 }  // namespace lmk

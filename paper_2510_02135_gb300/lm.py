@@ -109,6 +109,34 @@ def lib():
         L.lm_mdot_noalloc.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                       _vp, _vp, _vp]
         L.lm_mdot_noalloc.restype = st
+        L.lm_batch_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int64, _vp, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int, _vp]
+        L.lm_batch_create.restype = st
+        L.lm_batch_destroy.argtypes = [_vp]
+        L.lm_batch_destroy.restype = st
+        L.lm_batch_set_positions.argtypes = [_vp, _vp]
+        L.lm_batch_set_positions.restype = st
+        L.lm_batch_get_positions.argtypes = [_vp, _vp]
+        L.lm_batch_get_positions.restype = st
+        L.lm_batch_mdot.argtypes = [_vp, _vp, _vp]
+        L.lm_batch_mdot.restype = st
+        L.lm_batch_sqrt_mdot.argtypes = [_vp, _vp, ctypes.c_uint64, ctypes.c_double, ctypes.c_double, _vp, _vp]
+        L.lm_batch_sqrt_mdot.restype = st
+        L.lm_batch_bd_run.argtypes = [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                      ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int, _vp]
+        L.lm_batch_bd_run.restype = st
+        L.lm_batch_set_tiling.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+        L.lm_batch_set_tiling.restype = st
+        L.lm_batch_autotune.argtypes = [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.lm_batch_autotune.restype = st
+        L.lm_batch_profile_enable.argtypes = [_vp, ctypes.c_int]
+        L.lm_batch_profile_enable.restype = st
+        L.lm_batch_profile_read.argtypes = [_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        L.lm_batch_profile_read.restype = st
+        L.lm_batch_timeout_selftest.argtypes = [ctypes.c_longlong]
+        L.lm_batch_timeout_selftest.restype = st
+        L.lm_philox_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint64, _vp, ctypes.c_int64, _vp]
+        L.lm_philox_normals.restype = st
         L.lm_tridiag_sqrt_e1.argtypes = [ctypes.c_int, _vp, _vp, _vp]
         L.lm_tridiag_sqrt_e1.restype = ctypes.c_int
         _lib = L
@@ -301,6 +329,112 @@ def lm_mdot_noalloc(pos, forces, torques, viscosity: float, hydrodynamic_radius:
                                  float(hydrodynamic_radius), int(bool(include_angular)),
                                  _ptr(lin_out, False, n3, "lin_out"), _ptr(ang_out, False, n3, "ang_out"),
                                  cuda_stream))
+
+
+class Batch:
+    """Handle of an ``lm_batch`` (systems concatenated by ``offsets``)."""
+
+    def __init__(self, handle: int, offsets, eta: float, a: float, max_iter: int):
+        self.handle = ctypes.c_void_p(handle)
+        self.offsets = np.asarray(offsets, dtype=np.int64)
+        self.S = self.offsets.size - 1
+        self.Ntot = int(self.offsets[-1])
+        self.eta = eta
+        self.a = a
+        self.max_iter = max_iter
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.lm_batch_destroy(h)
+            self.handle = None
+
+
+def lm_batch_create(offsets, viscosity: float, hydrodynamic_radius: float, max_iter: int = 64,
+                    cuda_stream: int | None = None) -> Batch:
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    h = ctypes.c_void_p()
+    _check(lib().lm_batch_create(ctypes.byref(h), off.size - 1, off.ctypes.data, float(viscosity),
+                                 float(hydrodynamic_radius), int(max_iter), cuda_stream))
+    return Batch(h.value, off, viscosity, hydrodynamic_radius, max_iter)
+
+
+def lm_batch_set_positions(b: Batch, pos) -> None:
+    _check(lib().lm_batch_set_positions(b.handle, _ptr(pos, False, 3 * b.Ntot, "pos")))
+
+
+def lm_batch_get_positions(b: Batch, out=None, like=None):
+    if out is None:
+        out = _like(like if like is not None else np.empty(0, np.float32), (b.Ntot, 3), False)
+    _check(lib().lm_batch_get_positions(b.handle, _ptr(out, False, 3 * b.Ntot, "pos_out")))
+    return out
+
+
+def lm_batch_mdot(b: Batch, forces, lin_out=None):
+    if lin_out is None:
+        lin_out = _like(forces, (b.Ntot, 3), False)
+    _check(lib().lm_batch_mdot(b.handle, _ptr(forces, False, 3 * b.Ntot, "forces"),
+                               _ptr(lin_out, False, 3 * b.Ntot, "lin_out")))
+    return lin_out
+
+
+def lm_batch_sqrt_mdot(b: Batch, W=None, seed: int = 0, prefactor: float = 1.0, tol: float = 1e-4, lin_out=None,
+                       like=None, raise_not_converged: bool = True):
+    """Returns (lin, iterations per system)."""
+    ref = W if W is not None else (lin_out if lin_out is not None else like)
+    if lin_out is None:
+        lin_out = _like(ref, (b.Ntot, 3), False)
+    its = np.zeros(b.S, dtype=np.int32)
+    st = lib().lm_batch_sqrt_mdot(b.handle, _ptr(W, True, 3 * b.Ntot, "W"), int(seed), float(prefactor), float(tol),
+                                  _ptr(lin_out, False, 3 * b.Ntot, "lin_out"), its.ctypes.data)
+    if st != LM_OK and (raise_not_converged or st != LM_ERR_NOT_CONVERGED):
+        _check(st)
+    return lin_out, its
+
+
+def lm_batch_bd_run(b: Batch, kT: float, dt: float, k_trap: float, nsteps: int, step0: int = 0, seed: int = 0,
+                    tol: float = 1e-4, use_graph: bool = True, raise_not_converged: bool = True):
+    """nsteps Euler-Maruyama steps in one persistent launch.  Returns iterations per system."""
+    its = np.zeros(b.S, dtype=np.int32)
+    st = lib().lm_batch_bd_run(b.handle, float(kT), float(dt), float(k_trap), int(nsteps), int(step0), int(seed),
+                               float(tol), int(bool(use_graph)), its.ctypes.data)
+    if st != LM_OK and (raise_not_converged or st != LM_ERR_NOT_CONVERGED):
+        _check(st)
+    return its
+
+
+def lm_batch_set_tiling(b: Batch, threads: int, ilp: int) -> None:
+    _check(lib().lm_batch_set_tiling(b.handle, int(threads), int(ilp)))
+
+
+def lm_batch_autotune(b: Batch) -> dict:
+    t, i = ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib().lm_batch_autotune(b.handle, ctypes.byref(t), ctypes.byref(i)))
+    return {"threads": t.value, "ilp": i.value}
+
+
+def lm_batch_profile_enable(b: Batch, enable: bool = True) -> None:
+    _check(lib().lm_batch_profile_enable(b.handle, int(bool(enable))))
+
+
+def lm_batch_profile_read(b: Batch) -> np.ndarray:
+    """Phase end times (ns) of the first step of the last run (see include/lm.h)."""
+    out = np.zeros(4 + 5 * b.max_iter, dtype=np.uint64)
+    c = ctypes.c_int(0)
+    _check(lib().lm_batch_profile_read(b.handle, out.ctypes.data, out.size, ctypes.byref(c)))
+    return out[: c.value]
+
+
+def lm_batch_timeout_selftest(spin_cycles: int = 2_000_000) -> int:
+    """Returns the status of the bounded-wait self test (LM_ERR_TIMEOUT when it works)."""
+    return int(lib().lm_batch_timeout_selftest(int(spin_cycles)))
+
+
+def lm_philox_normals(seed: int, stream: int, out, cuda_stream=None) -> None:
+    """Fill the device tensor ``out`` (float64) with the library's Philox normals."""
+    if cuda_stream is None:
+        cuda_stream = _current_stream(out)
+    _check(lib().lm_philox_normals(int(seed), int(stream), _ptr(out, True, None, "out"), out.numel(), cuda_stream))
 
 
 def lm_get_pair_config(s: Solver) -> dict:

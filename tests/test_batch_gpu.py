@@ -1,0 +1,196 @@
+"""GPU parity of the batched persistent kernel (lm_batch_*) and its noise
+generator, against the FP64 oracle and against the single-system API.
+
+Batched Euler-Maruyama step (Eq. bdhi, open geometry, drift 0):
+  x' = x + dt M F + sqrt(2 kT dt) M^{1/2} W,   F = -k x,
+with W of system s at step t drawn from Philox-4x32-10 (key seed, stream
+(t << 32) | s); the oracle draws the same numbers from its own
+implementation of the generator."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2510_02135_gb300 import inputs as I  # noqa: E402
+from paper_2510_02135_gb300 import lm  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2510_02135_gb300 import _build
+
+    _build.build()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def rel(y, r):
+    y = np.asarray(y, np.float64).ravel()
+    r = np.asarray(r, np.float64).ravel()
+    return np.linalg.norm(y - r) / max(np.linalg.norm(r), 1e-300)
+
+
+def small_batch(seed=7, S=6, nmin=20, nmax=700):
+    return I.batch_suspensions(seed, S=S, nmin=nmin, nmax=nmax)
+
+
+def test_philox_normals_match_oracle(orc):
+    for seed, stream, n in ((0, 0, 1000), (123456789012345, (7 << 32) | 3, 4099)):
+        out = torch.empty(n, dtype=torch.float64, device="cuda")
+        lm.lm_philox_normals(seed, stream, out)
+        torch.cuda.synchronize()
+        ref = orc.philox_normals(seed, stream, n)
+        np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=1e-13)
+
+
+def test_batch_mdot_matches_oracle(orc):
+    b_ = small_batch()
+    rng = np.random.default_rng(1)
+    F = rng.standard_normal((b_.pos.shape[0], 3)).astype(np.float32)
+    b = lm.lm_batch_create(b_.offsets, 1.0, 1.0)
+    lm.lm_batch_set_positions(b, dev(b_.pos))
+    for threads, ilp in ((128, 1), (64, 2), (128, 2), (64, 1)):
+        lm.lm_batch_set_tiling(b, threads, ilp)
+        u = lm.lm_batch_mdot(b, dev(F)).cpu().numpy()
+        for s in range(b.S):
+            o0, o1 = b_.offsets[s], b_.offsets[s + 1]
+            ur, _ = orc.mdot(b_.pos[o0:o1], F[o0:o1], None, 1.0, 1.0, False)
+            assert rel(u[o0:o1], ur) <= 1e-5, (threads, ilp, s, rel(u[o0:o1], ur))
+
+
+def test_batch_sqrt_matches_oracle(orc):
+    b_ = small_batch(seed=9)
+    n = b_.pos.shape[0]
+    W = np.random.default_rng(2).standard_normal(3 * n)
+    b = lm.lm_batch_create(b_.offsets, 1.0, 1.0, max_iter=100)
+    lm.lm_batch_set_positions(b, dev(b_.pos))
+    tol = 1e-6
+    y, its = lm.lm_batch_sqrt_mdot(b, dev(W), tol=tol, prefactor=0.5)
+    y = y.cpu().numpy()
+    for s in range(b.S):
+        o0, o1 = b_.offsets[s], b_.offsets[s + 1]
+        M = orc.assemble(b_.pos[o0:o1], 1.0, 1.0, False)
+        ws = W[3 * o0:3 * o1]
+        exact = 0.5 * orc.sqrt_exact(M, ws)
+        assert rel(y[o0:o1], exact) <= 20 * tol, (s, rel(y[o0:o1], exact), its[s])
+        yo, ito, conv = orc.lanczos_sqrt(lambda v: M @ v, ws, tol=tol, max_iter=100)
+        assert abs(int(its[s]) - ito) <= 1, (s, its[s], ito)
+
+
+def test_batch_sqrt_philox_equals_explicit_noise(orc):
+    b_ = small_batch(seed=11)
+    n = b_.pos.shape[0]
+    b = lm.lm_batch_create(b_.offsets, 1.0, 1.0)
+    lm.lm_batch_set_positions(b, dev(b_.pos))
+    seed = 99
+    y1, it1 = lm.lm_batch_sqrt_mdot(b, None, seed=seed, tol=1e-5, like=dev(b_.pos))
+    W = np.concatenate([orc.philox_normals(seed, s, 3 * int(b_.sizes[s])) for s in range(b.S)])
+    y2, it2 = lm.lm_batch_sqrt_mdot(b, dev(W), tol=1e-5)
+    np.testing.assert_array_equal(it1, it2)
+    assert rel(y1.cpu().numpy(), y2.cpu().numpy()) <= 1e-12
+
+
+def test_batch_sqrt_matches_single_system_api(orc):
+    b_ = small_batch(seed=13, S=4)
+    n = b_.pos.shape[0]
+    W = np.random.default_rng(3).standard_normal(3 * n)
+    b = lm.lm_batch_create(b_.offsets, 1.0, 1.0)
+    lm.lm_batch_set_positions(b, dev(b_.pos))
+    y, its = lm.lm_batch_sqrt_mdot(b, dev(W), tol=1e-6)
+    y = y.cpu().numpy()
+    for s in range(b.S):
+        o0, o1 = b_.offsets[s], b_.offsets[s + 1]
+        sv = lm.lm_create(1.0, 1.0, False, lm.LM_FP32C)
+        lm.lm_set_positions(sv, dev(b_.pos[o0:o1]))
+        ys, _, it = lm.lm_sqrt_mdot(sv, dev(W[3 * o0:3 * o1]), tol=1e-6, max_iter=64)
+        assert abs(it - int(its[s])) <= 1
+        assert rel(y[o0:o1], ys.cpu().numpy()) <= 1e-5
+
+
+def test_batch_bd_one_step_matches_oracle(orc):
+    b_ = small_batch(seed=17, S=5, nmin=30, nmax=400)
+    b = lm.lm_batch_create(b_.offsets, 1.0, 1.0, max_iter=100)
+    lm.lm_batch_set_positions(b, dev(b_.pos))
+    kT, dt, k, seed, tol = 1.0, 1e-3, 1.0, 4242, 1e-8
+    its = lm.lm_batch_bd_run(b, kT, dt, k, 1, step0=0, seed=seed, tol=tol, use_graph=True)
+    x1 = lm.lm_batch_get_positions(b, like=dev(b_.pos)).cpu().numpy()
+    for s in range(b.S):
+        o0, o1 = b_.offsets[s], b_.offsets[s + 1]
+        x0 = b_.pos[o0:o1].astype(np.float64)
+        W = orc.philox_normals(seed, orc.bd_noise_stream(s, 0), 3 * (o1 - o0))
+        xr, itr = orc.em_step(x0, 1.0, 1.0, kT, dt, k, W, tol)
+        # compare displacements; x1 is rounded to FP32 on read-back
+        d_gpu = x1[o0:o1] - x0
+        d_ref = xr - x0
+        atol = 2 * np.abs(x0).max() * 2 ** -24
+        assert np.abs(d_gpu - d_ref).max() <= 1e-5 * np.abs(d_ref).max() + atol, s
+        assert abs(int(its[s]) - itr) <= 1
+
+
+def test_batch_bd_graph_direct_and_resume_agree():
+    b_ = small_batch(seed=19, S=7, nmin=16, nmax=300)
+    args = dict(kT=1.0, dt=1e-3, k_trap=1.0, seed=5, tol=1e-4)
+    res = []
+    for mode in ("graph4", "direct4", "resume2+2"):
+        b = lm.lm_batch_create(b_.offsets, 1.0, 1.0)
+        lm.lm_batch_set_positions(b, dev(b_.pos))
+        if mode == "graph4":
+            lm.lm_batch_bd_run(b, nsteps=4, use_graph=True, **args)
+        elif mode == "direct4":
+            lm.lm_batch_bd_run(b, nsteps=4, use_graph=False, **args)
+        else:
+            lm.lm_batch_bd_run(b, nsteps=2, step0=0, use_graph=True, **args)
+            lm.lm_batch_bd_run(b, nsteps=2, step0=2, use_graph=False, **args)
+        res.append(lm.lm_batch_get_positions(b, like=dev(b_.pos)).cpu().numpy())
+    np.testing.assert_array_equal(res[0], res[1])
+    np.testing.assert_array_equal(res[0], res[2])
+    assert np.abs(res[0] - b_.pos).max() > 0
+
+
+def test_batch_trap_statistics_single_particles():
+    """Isolated spheres in the trap: x' = (1 - k mu dt) x + sqrt(2 kT mu dt) xi with
+    mu = 1/(6 pi eta a); the displacement variance after one step is 2 kT mu dt."""
+    S = 4000
+    offsets = np.arange(S + 1, dtype=np.int64)
+    pos = np.zeros((S, 3), np.float32)
+    b = lm.lm_batch_create(offsets, 1.0, 1.0, max_iter=8)
+    lm.lm_batch_set_positions(b, dev(pos))
+    lm.lm_batch_bd_run(b, 1.0, 1e-2, 1.0, 1, seed=3, tol=1e-10)
+    x = lm.lm_batch_get_positions(b, like=dev(pos)).cpu().numpy().astype(np.float64)
+    var = 2 * 1.0 * (1 / (6 * np.pi)) * 1e-2
+    assert abs(x.var() / var - 1) < 0.05
+    assert abs(x.mean()) < 5 * np.sqrt(var / x.size)
+
+
+def test_batch_errors_and_timeout_selftest():
+    with pytest.raises(lm.LmError) as e:
+        lm.lm_batch_create(np.array([0, 0], np.int64), 1.0, 1.0)
+    assert e.value.status == lm.LM_ERR_INVALID_ARG
+    b = lm.lm_batch_create(np.array([0, 5, 9], np.int64), 1.0, 1.0)
+    with pytest.raises(lm.LmError) as e:
+        lm.lm_batch_bd_run(b, 1.0, 1e-3, 1.0, 1)
+    assert e.value.status == lm.LM_ERR_STATE
+    with pytest.raises(lm.LmError):
+        lm.lm_batch_set_tiling(b, 96, 3)
+    assert lm.lm_batch_timeout_selftest(2_000_000) == lm.LM_ERR_TIMEOUT
+    # the context stays usable after the expired waits
+    lm.lm_batch_set_positions(b, dev(np.random.default_rng(0).uniform(-3, 3, (9, 3)).astype(np.float32)))
+    lm.lm_batch_bd_run(b, 1.0, 1e-3, 1.0, 2)
+
+
+def test_batch_autotune_keeps_results(orc):
+    b_ = small_batch(seed=23)
+    F = np.random.default_rng(4).standard_normal((b_.pos.shape[0], 3)).astype(np.float32)
+    b = lm.lm_batch_create(b_.offsets, 1.0, 1.0)
+    lm.lm_batch_set_positions(b, dev(b_.pos))
+    t = lm.lm_batch_autotune(b)
+    assert (t["threads"], t["ilp"]) in ((64, 1), (64, 2), (128, 1), (128, 2))
+    u = lm.lm_batch_mdot(b, dev(F)).cpu().numpy()
+    o0, o1 = b_.offsets[0], b_.offsets[1]
+    ur, _ = orc.mdot(b_.pos[o0:o1], F[o0:o1], None, 1.0, 1.0, False)
+    assert rel(u[o0:o1], ur) <= 1e-5

@@ -104,7 +104,7 @@ def test_mdot_launch_configs_agree(orc, fp64, angular):
     ur, wr = orc.mdot(s_.pos, s_.F, s_.T, 1.0, 1.0, angular)
     tol = 1e-12 if fp64 else 1e-5
     for threads in (128, 256):
-        for ilp in (1, 2, 4):
+        for ilp in ((1, 2) if fp64 else (1, 2, 4, 8)):
             for splits in (1, 3, 9):
                 lm.lm_set_pair_config(s, threads, ilp, splits)
                 u, w = gpu_mdot(s, s_.F, s_.T)
@@ -335,7 +335,7 @@ def test_autotune_keeps_results(orc):
     s_ = I.cube_suspension(31, n, 0.1, 1.0, angular=False, fp32=True)
     s = make(1.0, 1.0, False, False, s_.pos)
     cfg = lm.lm_autotune(s, reps=2)
-    assert cfg["threads"] in (128, 256) and cfg["ilp"] in (1, 2, 4) and cfg["splits"] >= 1
+    assert cfg["threads"] in (128, 256) and cfg["ilp"] in (1, 2, 4, 8) and cfg["splits"] >= 1
     assert lm.lm_get_pair_config(s) == cfg
     u, _ = gpu_mdot(s, s_.F, None)
     ur, _ = orc.mdot(s_.pos, s_.F, None, 1.0, 1.0, False)
