@@ -7,19 +7,24 @@
 //   A1  chunks   W_s (Philox) -> V_s[0], |W_s|^2 partials, F_s = -k x_s
 //   A2  chunks   v_0 = W_s / |W_s|
 //   for k = 0, 1, ...                       (systems drop out as they converge)
-//     B   items    w = M_s v_k   (k = 0: also u = M_s F_s, a second right-hand
-//                  side sharing the pair coefficients); v_k = w_{k-1} / beta_{k-1}
-//                  is formed while loading (and stored for the own rows);
-//                  partial v_k . w per item
-//     C2  chunks   alpha_k; w -= alpha_k v_k + beta_{k-1} v_{k-1}; dots V_s^T w
+//     B   items    partial products of w = M_s v_k over one j-part (k = 0: also
+//                  u = M_s F_s, a second right-hand side sharing the pair
+//                  coefficients); v_k = w_{k-1} / beta_{k-1} is formed while
+//                  loading (and stored for the own rows); partial v_k . w
+//     C2  chunks   w = sum of the j-parts; alpha_k = sum of the item partials;
+//                  w -= alpha_k v_k + beta_{k-1} v_{k-1}; dots V_s^T w
 //     C3  chunks   w -= V_s c; dots V_s^T w            (second Gram-Schmidt pass)
 //     C4  chunks   w -= V_s c'; |w|^2 partials
 //     C5  systems  beta_k; z_k = |W| f(T_k) e1 (implicit QR, FP64); stopping rule
+//                  (in BD runs the solve and the relative-change test start at
+//                  the previous step's iteration count minus 3)
 //   D   chunks   y = V_s z; x += dt u + sqrt(2 kT dt) y
 // Phases are separated by a grid barrier whose waits are bounded in clock
 // cycles: an expired wait sets an error flag and every CTA returns.
-// Items are (system, block of NT*NI particles) in decreasing system size,
-// handed out through a ticket counter; chunks are kBatchChunk vector elements
+// Items are (system, block of NT*NI particles, j-part of kBatchJPart) in
+// decreasing system size, handed out through a ticket counter, so that the
+// largest systems are cut into several short items; chunks are kBatchChunk
+// vector elements
 // of one system, assigned round-robin.  Every reduction is a fixed-order sum
 // of per-item or per-chunk partials, so results do not depend on timing.
 #include <cuda_runtime.h>
@@ -121,8 +126,8 @@ __device__ __forceinline__ double* basis(const BatchParams& P, int s, int j) {
 // right-hand side B (NRHS = 2): the forces Fbuf (float).
 // ---------------------------------------------------------------------------
 template <int NT, int NI, int NRHS>
-__device__ void pair_item(const BatchParams& P, int s, int i0, const float* srcA_f, const double* srcA_d,
-                          double scaleA, double* outA_d, float* outA_f, double* outB, double* Vrow_store,
+__device__ void pair_item(const BatchParams& P, int s, int i0, int jb, int je, const float* srcA_f,
+                          const double* srcA_d, double scaleA, double* outA_d, double* outB, double* Vrow_store,
                           double* part_slot, float4* sp, float4* sa, float4* sb, double* sred) {
     const int tid = threadIdx.x;
     const int64_t o = P.off[s];
@@ -147,10 +152,10 @@ __device__ void pair_item(const BatchParams& P, int s, int i0, const float* srcA
             if (NRHS == 2) pB[q][c] = hB[q][c] = lB[q][c] = 0.f;
         }
     }
-    for (int jt = 0; jt < Ns; jt += NT) {
+    for (int jt = jb; jt < je; jt += NT) {
         const int j = jt + tid;
         __syncthreads();
-        if (j < Ns) {
+        if (j < je) {
             sp[tid] = P.pos4[o + j];
             float4 a;
             if (srcA_f) {
@@ -236,14 +241,13 @@ __device__ void pair_item(const BatchParams& P, int s, int i0, const float* srcA
         for (int c = 0; c < 3; ++c) {
             const int64_t g = 3 * (o + i) + c;
             const double wv = P.c8 * ((double)hA[q][c] + (double)lA[q][c]);
-            if (outA_f) outA_f[g] = (float)wv;
-            if (outA_d) {
-                outA_d[g] = wv;
+            outA_d[3 * i + c] = wv;
+            if (part_slot) {
                 const double vk = srcA_d[g] * scaleA;
                 if (Vrow_store) Vrow_store[3 * i + c] = vk;
                 dot = fma(vk, wv, dot);
             }
-            if (NRHS == 2) outB[g] = P.c8 * ((double)hB[q][c] + (double)lB[q][c]);
+            if (NRHS == 2) outB[3 * i + c] = P.c8 * ((double)hB[q][c] + (double)lB[q][c]);
         }
     }
     if (part_slot) {
@@ -291,6 +295,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
     __shared__ float4 sp[NT], sa[NT], sb[NT];
     __shared__ double sred[NT / 32];
     __shared__ double cvec[129];
+    __shared__ double tri_d[128], tri_e[128], tri_z[128];   // C5 scratch (thread 0)
     __shared__ unsigned long long s_ticket;
     const int tid = threadIdx.x;
     const int G = gridDim.x;
@@ -310,12 +315,43 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
         base += (unsigned long long)P.n_items + (unsigned long long)G;
     };
 
+    // item t: system, first particle, j-part [jp * kBatchJPart, ...)
+    auto item_args = [&](int t, int& s, int& i0, int& jp, int& jb, int& je, double*& wout, double*& uout) {
+        s = P.items[3 * t];
+        i0 = P.items[3 * t + 1];
+        jp = P.items[3 * t + 2];
+        const int ns = (int)(P.off[s + 1] - P.off[s]);
+        jb = jp * kBatchJPart;
+        je = min(jb + kBatchJPart, ns);
+        wout = P.wsplit + P.woff[s] + (int64_t)jp * 3 * ns;
+        uout = P.usplit + P.woff[s] + (int64_t)jp * 3 * ns;
+    };
+    // sum of the j-part partials of system s at element e
+    auto sum_parts = [&](const double* split, int s, int e) {
+        const int ns = (int)(P.off[s + 1] - P.off[s]);
+        const int parts = (ns + kBatchJPart - 1) / kBatchJPart;
+        const double* b = split + P.woff[s];
+        double t = 0.0;
+        for (int p = 0; p < parts; ++p) t += b[(int64_t)p * 3 * ns + e];
+        return t;
+    };
+
     if (P.mode == kBatchMdot) {
         for_items([&](int t) {
-            const int s = P.items[2 * t], i0 = P.items[2 * t + 1];
-            pair_item<NT, NI, 1>(P, s, i0, P.F_in, nullptr, 1.0, nullptr, P.lin_out, nullptr, nullptr, nullptr, sp,
-                                 sa, sb, sred);
+            int s, i0, jp, jb, je;
+            double *wout, *uout;
+            item_args(t, s, i0, jp, jb, je, wout, uout);
+            pair_item<NT, NI, 1>(P, s, i0, jb, je, P.F_in, nullptr, 1.0, wout, nullptr, nullptr, nullptr, sp, sa, sb,
+                                 sred);
         });
+        if (!grid_sync(P)) return;
+        for (int c = blockIdx.x; c < P.n_chunks; c += G) {
+            const int s = P.chunks[2 * c], e0 = P.chunks[2 * c + 1];
+            const int64_t o = P.off[s];
+            const int ns3 = 3 * (int)(P.off[s + 1] - o);
+            const int e1 = min(e0 + kBatchChunk, ns3);
+            for (int e = e0 + tid; e < e1; e += NT) P.lin_out[3 * o + e] = (float)sum_parts(P.wsplit, s, e);
+        }
         (void)per_item;
         return;
     }
@@ -399,21 +435,23 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
             double* wprev = (k & 1) ? P.w0 : P.w1;
             // B: products
             for_items([&](int t) {
-                const int s = P.items[2 * t], i0 = P.items[2 * t + 1];
+                int s, i0, jp, jb, je;
+                double *wout, *uout;
+                item_args(t, s, i0, jp, jb, je, wout, uout);
                 if (!P.active[s]) return;
                 const int64_t o = P.off[s];
                 if (k == 0) {
                     const double* v0 = basis(P, s, 0) - 3 * o;  // indexed by global element
                     if (P.mode == kBatchBD)
-                        pair_item<NT, NI, 2>(P, s, i0, nullptr, v0, 1.0, wcur, nullptr, P.u, nullptr,
+                        pair_item<NT, NI, 2>(P, s, i0, jb, je, nullptr, v0, 1.0, wout, uout, nullptr,
                                              &P.part_item[t], sp, sa, sb, sred);
                     else
-                        pair_item<NT, NI, 1>(P, s, i0, nullptr, v0, 1.0, wcur, nullptr, nullptr, nullptr,
+                        pair_item<NT, NI, 1>(P, s, i0, jb, je, nullptr, v0, 1.0, wout, nullptr, nullptr,
                                              &P.part_item[t], sp, sa, sb, sred);
                 } else {
                     const double invb = 1.0 / P.beta[s * P.m_max + k - 1];
-                    pair_item<NT, NI, 1>(P, s, i0, nullptr, wprev, invb, wcur, nullptr, nullptr, basis(P, s, k),
-                                         &P.part_item[t], sp, sa, sb, sred);
+                    pair_item<NT, NI, 1>(P, s, i0, jb, je, nullptr, wprev, invb, wout, nullptr,
+                                         jp == 0 ? basis(P, s, k) : nullptr, &P.part_item[t], sp, sa, sb, sred);
                 }
             });
             if (!grid_sync(P)) return;
@@ -432,7 +470,10 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                 const double* vk = basis(P, s, k);
                 const double* vkm1 = (k > 0) ? basis(P, s, k - 1) : vk;
                 double* w = wcur + 3 * o;
-                for (int e = e0 + tid; e < e1; e += NT) w[e] -= alpha * vk[e] + bprev * vkm1[e];
+                for (int e = e0 + tid; e < e1; e += NT) {
+                    w[e] = sum_parts(P.wsplit, s, e) - (alpha * vk[e] + bprev * vkm1[e]);
+                    if (k == 0 && P.mode == kBatchBD) P.u[3 * o + e] = sum_parts(P.usplit, s, e);
+                }
                 __syncthreads();
                 chunk_dots<NT>(P, s, e0, e1, w, k + 1, partA + (int64_t)c * M1);
                 __syncthreads();
@@ -477,7 +518,11 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                 if (!grid_sync(P)) return;
                 stamp(P, step, slot);
             }
-            // C5: beta, tridiagonal square root, stopping rule (one thread per system)
+            // C5: beta, tridiagonal square root, stopping rule (one thread per system).
+            // Warm start (BD mode): the tridiagonal solve and the relative-change
+            // test begin at k0 = kprev - 3, two iterations before the first test,
+            // since iteration counts change little from one step to the next;
+            // breakdown and max_iter are tested at every iteration.
             for (int s = blockIdx.x; s < P.S; s += G) {
                 if (tid != 0 || !P.active[s]) continue;
                 double b2 = 0.0;
@@ -487,41 +532,44 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                 double* be = P.beta + s * P.m_max;
                 be[k] = b;
                 const int m = k + 1;
+                double amax = 0.0;
+                for (int i = 0; i < m; ++i) amax = fmax(amax, fabs(al[i]));
+                const bool breakdown = b <= P.brk_rel * amax;
+                const bool last = (m == P.m_max);
+                const int k0 = (P.warm_start && P.kprev[s] > 0) ? max(0, P.kprev[s] - 3) : 0;
                 double* zs = P.z + s * P.m_max;
                 double* zp = P.zprev + s * P.m_max;
-                int ncl = 0;
-                const int rc = tridiag_sqrt_e1(m, al, be, P.td + (int64_t)s * 2 * P.m_max,
-                                               P.td + (int64_t)s * 2 * P.m_max + P.m_max,
-                                               P.trk + (int64_t)s * P.max_rot, P.trc + (int64_t)s * P.max_rot,
-                                               P.trs + (int64_t)s * P.max_rot, P.max_rot, zs, &ncl);
-                if (rc != 0) atomicCAS(P.err, kBatchOk, kBatchTridiag);
-                const double nw = P.normW[s];
-                for (int i = 0; i < m; ++i) zs[i] *= nw;
                 bool stop = false;
-                double rel = 0.0;
-                if (k >= 1) {
-                    double dn = 0.0, zn = 0.0;
-                    for (int i = 0; i < m; ++i) {
-                        const double dd = zs[i] - (i < m - 1 ? zp[i] : 0.0);
-                        dn += dd * dd;
-                        zn += zs[i] * zs[i];
+                if (k >= k0 || breakdown || last) {
+                    int ncl = 0;
+                    const int rc = tridiag_sqrt_e1(m, al, be, tri_d, tri_e, P.trk + (int64_t)s * P.max_rot,
+                                                   P.trc + (int64_t)s * P.max_rot, P.trs + (int64_t)s * P.max_rot,
+                                                   P.max_rot, tri_z, &ncl);
+                    if (rc != 0) atomicCAS(P.err, kBatchOk, kBatchTridiag);
+                    const double nw = P.normW[s];
+                    for (int i = 0; i < m; ++i) zs[i] = tri_z[i] * nw;
+                    if (k >= 1 && k >= k0 + 1) {
+                        double dn = 0.0, zn = 0.0;
+                        for (int i = 0; i < m; ++i) {
+                            const double dd = zs[i] - (i < m - 1 ? zp[i] : 0.0);
+                            dn += dd * dd;
+                            zn += zs[i] * zs[i];
+                        }
+                        const double rel = (zn > 0.0) ? sqrt(dn / zn) : 0.0;
+                        P.rel[s] = rel;
+                        if (rel < P.tol) stop = true;
                     }
-                    rel = (zn > 0.0) ? sqrt(dn / zn) : 0.0;
-                    P.rel[s] = rel;
-                    if (rel < P.tol) stop = true;
+                    if (breakdown) stop = true;
+                    if (!stop && last) { stop = true; P.notconv[s] = 1; }
+                    if (!stop)
+                        for (int i = 0; i < m; ++i) zp[i] = zs[i];
                 }
-                if (!stop) {
-                    double amax = 0.0;
-                    for (int i = 0; i < m; ++i) amax = fmax(amax, fabs(al[i]));
-                    if (b <= P.brk_rel * amax) stop = true;
-                }
-                if (!stop && m == P.m_max) { stop = true; P.notconv[s] = 1; }
                 if (stop) {
                     P.active[s] = 0;
                     P.msys[s] = m;
                     P.itsum[s] += m;
+                    P.kprev[s] = m;
                 } else {
-                    for (int i = 0; i < m; ++i) zp[i] = zs[i];
                     atomicAdd(&P.nact[k + 1], 1);
                 }
             }

@@ -817,6 +817,7 @@ struct lm_batch {
     double eta = 1.0, a = 1.0;
     std::vector<int64_t> off_h;
     DBuf off, pos4, x64, Fbuf, u, w0, w1, V, alpha, beta, z, zprev, normW, rel, active, msys, itsum, notconv, nact;
+    DBuf kprev, wsplit, usplit, woff;
     DBuf items, item_range, chunks, chunk_range, part_item, part_chunk, td, trk, trc, trs, bar, ticket, err, flag;
     DBuf in_stage, out_stage, W_stage;
     int n_items = 0, n_chunks = 0, max_rot = 0;
@@ -828,6 +829,10 @@ struct lm_batch {
     int timeline_len = 0;
     ~lm_batch() {
         timeline.release();
+        kprev.release();
+        wsplit.release();
+        usplit.release();
+        woff.release();
         DBuf* all[] = {&off, &pos4, &x64, &Fbuf, &u, &w0, &w1, &V, &alpha, &beta, &z, &zprev, &normW, &rel,
                        &active, &msys, &itsum, &notconv, &nact, &items, &item_range, &chunks, &chunk_range,
                        &part_item, &part_chunk, &td, &trk, &trc, &trs, &bar, &ticket, &err, &flag, &in_stage,
@@ -852,11 +857,16 @@ lm_status batch_build_items(lm_batch* b) {
     std::vector<int> items, range(2 * b->S);
     for (int s : order) {
         const int64_t n = b->off_h[s + 1] - b->off_h[s];
-        range[2 * s] = (int)(items.size() / 2);
-        for (int64_t i0 = 0; i0 < n; i0 += per) { items.push_back(s); items.push_back((int)i0); }
-        range[2 * s + 1] = (int)(items.size() / 2);
+        range[2 * s] = (int)(items.size() / 3);
+        for (int64_t jp = 0; jp * lmk::kBatchJPart < n; ++jp)
+            for (int64_t i0 = 0; i0 < n; i0 += per) {
+                items.push_back(s);
+                items.push_back((int)i0);
+                items.push_back((int)jp);
+            }
+        range[2 * s + 1] = (int)(items.size() / 3);
     }
-    b->n_items = (int)(items.size() / 2);
+    b->n_items = (int)(items.size() / 3);
     LM_CUDA(b->items.ensure(items.size() * sizeof(int)), "batch items");
     LM_CUDA(b->item_range.ensure(range.size() * sizeof(int)), "batch items");
     LM_CUDA(b->part_item.ensure((size_t)b->n_items * sizeof(double)), "batch items");
@@ -896,6 +906,11 @@ lmk::BatchParams batch_params(lm_batch* b, int mode) {
     p.msys = b->msys.as<int>();
     p.itsum = b->itsum.as<int>();
     p.notconv = b->notconv.as<int>();
+    p.kprev = b->kprev.as<int>();
+    p.wsplit = b->wsplit.as<double>();
+    p.usplit = b->usplit.as<double>();
+    p.woff = b->woff.as<int64_t>();
+    p.warm_start = (mode == lmk::kBatchBD) ? 1 : 0;
     p.nact = b->nact.as<int>();
     p.items = b->items.as<int>();
     p.n_items = b->n_items;
@@ -1026,6 +1041,13 @@ lm_status lm_batch_create(lm_batch** out, int64_t S, const int64_t* offsets, dou
         crange[2 * s + 1] = (int)(chunks.size() / 2);
     }
     b->n_chunks = (int)(chunks.size() / 2);
+    std::vector<int64_t> woff(S_);
+    int64_t wtot = 0;
+    for (int64_t s = 0; s < S; ++s) {
+        const int64_t n = offsets[s + 1] - offsets[s];
+        woff[s] = wtot;
+        wtot += ((n + lmk::kBatchJPart - 1) / lmk::kBatchJPart) * 3 * n;
+    }
     b->max_rot = (int)(4 * M * M + 64);
     struct { DBuf* buf; size_t bytes; } allocs[] = {
         {&b->off, (S_ + 1) * sizeof(int64_t)}, {&b->pos4, (size_t)b->Ntot * sizeof(float4)},
@@ -1042,13 +1064,16 @@ lm_status lm_batch_create(lm_batch** out, int64_t S, const int64_t* offsets, dou
         {&b->td, S_ * 2 * M * sizeof(double)}, {&b->trk, S_ * (size_t)b->max_rot * sizeof(int)},
         {&b->trc, S_ * (size_t)b->max_rot * sizeof(double)}, {&b->trs, S_ * (size_t)b->max_rot * sizeof(double)},
         {&b->bar, 4 * sizeof(unsigned)}, {&b->ticket, sizeof(unsigned long long)}, {&b->err, sizeof(int)},
-        {&b->flag, sizeof(int)}};
+        {&b->flag, sizeof(int)}, {&b->kprev, S_ * sizeof(int)}, {&b->woff, S_ * sizeof(int64_t)},
+        {&b->wsplit, (size_t)wtot * sizeof(double)}, {&b->usplit, (size_t)wtot * sizeof(double)}};
     for (auto& al : allocs) LM_CUDA(al.buf->ensure(al.bytes), "allocating batch buffers");
     LM_CUDA(cudaMemcpy(b->off.p, offsets, (S_ + 1) * sizeof(int64_t), cudaMemcpyHostToDevice), "batch offsets");
     LM_CUDA(cudaMemcpy(b->chunks.p, chunks.data(), chunks.size() * sizeof(int), cudaMemcpyHostToDevice), "chunks");
     LM_CUDA(cudaMemcpy(b->chunk_range.p, crange.data(), crange.size() * sizeof(int), cudaMemcpyHostToDevice),
             "chunks");
     LM_CUDA(cudaMemset(b->bar.p, 0, 4 * sizeof(unsigned)), "batch barrier");
+    LM_CUDA(cudaMemset(b->kprev.p, 0, S_ * sizeof(int)), "batch history");
+    LM_CUDA(cudaMemcpy(b->woff.p, woff.data(), S_ * sizeof(int64_t), cudaMemcpyHostToDevice), "batch offsets");
     if (lm_status st = batch_build_items(b)) return st;
     LM_CUDA(cudaMallocHost(reinterpret_cast<void**>(&b->pinned), 2 * S_ * sizeof(int)), "batch pinned");
     *out = guard.release();

@@ -156,7 +156,8 @@ cudaError_t lz_philox_normals(uint64_t seed, uint64_t stream, double* W, int64_t
 // ---------------------------------------------------------------------------
 enum BatchMode { kBatchBD = 0, kBatchMdot = 1, kBatchSqrt = 2 };
 enum BatchError { kBatchOk = 0, kBatchTimeout = 1, kBatchTridiag = 2 };
-constexpr int kBatchChunk = 1024;      // elements per vector-phase work unit
+constexpr int kBatchChunk = 256;       // elements per vector-phase work unit
+constexpr int kBatchJPart = 1024;      // j-range of one product work item
 
 struct BatchParams {
     int S, m_max, mode, nsteps;
@@ -180,8 +181,13 @@ struct BatchParams {
     int* msys;                         // S: iterations used in the current step
     int* itsum;                        // S: iterations summed over the call
     int* notconv;                      // S: 1 if max_iter was reached in some step
+    int* kprev;                        // S: iterations of the previous BD step (0 = none)
+    int warm_start;                    // 1: start the stopping test near kprev (BD mode)
     int* nact;                         // m_max + 1 counters of systems still active
-    const int* items;                  // n_items x (system, first particle)
+    double* wsplit;                    // per-system j-part partial products of w (or F for mdot)
+    double* usplit;                    // per-system j-part partial products of u = M F
+    const int64_t* woff;               // S: offset of system s in wsplit / usplit (parts x 3 N_s)
+    const int* items;                  // n_items x (system, first particle, j-part)
     int n_items;
     const int* item_range;             // S x (first item, end item)
     const int* chunks;                 // n_chunks x (system, first element)

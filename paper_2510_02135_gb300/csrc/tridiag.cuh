@@ -18,6 +18,24 @@
 
 namespace lmk {
 
+// 1 / sqrt(t) for t > 0.  On the device FP64 square root and division are
+// long dependent sequences, so the rotation uses Newton-Raphson iteration for
+// the reciprocal square root, y <- y (3 - t y^2) / 2, from the FP32 estimate:
+// two steps take the ~2^-22 relative error of the seed below FP64 rounding
+// (quadratic convergence).  Outside the FP32 range, and on the host, it is
+// the plain quotient.
+__host__ __device__ inline double inv_sqrt(double t) {
+#ifdef __CUDA_ARCH__
+    if (t > 1e-36 && t < 1e36) {
+        double y = (double)rsqrtf((float)t);
+        y = y * fma(-0.5 * t, y * y, 1.5);
+        y = y * fma(-0.5 * t, y * y, 1.5);
+        return y;
+    }
+#endif
+    return 1.0 / sqrt(t);
+}
+
 // d[0..m-1] diagonal, e[0..m-2] off-diagonal (both destroyed; d receives the
 // eigenvalues).  Rotation t acts on (rk[t], rk[t]+1) with (rc[t], rs[t]).
 // Returns 0; -1 if 30 m QR steps did not converge; -2 if more than max_rot
@@ -47,12 +65,13 @@ __host__ __device__ inline int tridiag_qr_rotations(int m, double* d, double* e,
         for (int k = lo; k < hi; ++k) {
             // rotation J = [[c, -s], [s, c]] on (k, k+1) with J^T [x; z] = [r; 0]
             // entries of T are of the order of the mobility: no over/underflow in x^2 + z^2
-            const double r = sqrt(x * x + z * z);
-            double c = 1.0, s = 0.0;
-            if (r > 0.0) {
-                const double inv = 1.0 / r;
+            const double t2 = x * x + z * z;
+            double c = 1.0, s = 0.0, r = 0.0;
+            if (t2 > 0.0) {
+                const double inv = inv_sqrt(t2);
                 c = x * inv;
                 s = z * inv;
+                r = t2 * inv;
             }
             if (k > lo) e[k - 1] = r;
             const double ak = d[k], ak1 = d[k + 1], bk = e[k];
