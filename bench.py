@@ -190,8 +190,8 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["rpy6", "melt"], default="rpy6")
-    ap.add_argument("--autotune", action="store_true", help="autotune the pair kernel before timing")
+    ap.add_argument("--workload", choices=["rpy6", "melt", "adjoint", "bd256"], default="rpy6")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default pair-kernel configuration")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle CPU work for cpu_baseline")
     ap.add_argument("--ref-step-s", type=float, default=3.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -201,6 +201,10 @@ def main():
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, ws, rank)
+    if args.workload == "adjoint":
+        return run_adjoint(args, ws, rank, local)
+    if args.workload == "bd256":
+        return run_bd(args, ws, rank, local)
 
     import torch
 
@@ -223,7 +227,7 @@ def main():
     ang2 = torch.empty_like(lin)
     solver = lm.lm_create(eta, a, True, lm.LM_FP32C, cuda_stream=torch.cuda.current_stream().cuda_stream)
     lm.lm_set_positions(solver, pos)
-    if args.autotune:
+    if not args.no_autotune:
         lm.lm_autotune(solver, reps=2)
     cfg = lm.lm_get_pair_config(solver)
     iters = []
@@ -341,6 +345,203 @@ def main():
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"FP64 oracle direct sum of M [F; T] for {nrows} random rows x {n} "
                                           f"columns ({t:.1f} s); the Lanczos cost per pair is the same product"}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def _dist_init(ws, local):
+    import torch
+
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+        return dist
+    return None
+
+
+def _reduce(dist, t_ms, units):
+    """(max time over ranks, sum of units over ranks)."""
+    if dist is None:
+        return t_ms, units
+    import torch
+
+    t = torch.tensor([t_ms, units], dtype=torch.float64, device="cuda")
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
+def run_adjoint(args, ws, rank, local):
+    """Forward product and fused adjoint (L = <G, M(X) F>) at N = 65536,
+    translation only, FP32: one step = lm_set_positions + lm_mdot +
+    lm_mdot_backward (dL/dX and dL/dF); pairs counted N^2 per launch."""
+    import torch
+
+    from paper_2510_02135_gb300 import _build, inputs as I, lm
+
+    dist = _dist_init(ws, local)
+    _build.build()
+    c = I.ADJOINT_N65536
+    s_ = I.cube_suspension(c["seed"], c["n"], c["phi"], c["a"], angular=False, fp32=True)
+    n = c["n"]
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    pos, F, G = dev(s_.pos), dev(s_.F), dev(s_.G)
+    u = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    solver = lm.lm_create(c["eta"], c["a"], False, lm.LM_FP32C, cuda_stream=torch.cuda.current_stream().cuda_stream)
+    lm.lm_set_positions(solver, pos)
+    if not args.no_autotune:
+        lm.lm_autotune(solver, reps=2)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+
+    def step(e=None):
+        lm.lm_set_positions(solver, pos)
+        if e:
+            e[0].record(stream)
+        lm.lm_mdot(solver, F, None, u, None)
+        if e:
+            e[1].record(stream)
+        lm.lm_mdot_backward(solver, F, None, G, None)
+        if e:
+            e[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = lm.lm_launch_count()
+    for k in range(args.steps):
+        flush.zero_()
+        step(ev[k])
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    launches = lm.lm_launch_count() - launches0
+    fwd = [e[0].elapsed_time(e[1]) for e in ev]
+    bwd = [e[1].elapsed_time(e[2]) for e in ev]
+    total = float(sum(fwd) + sum(bwd))
+    tmax, pairs = _reduce(dist, total, 2.0 * n * n * args.steps)
+    props = torch.cuda.get_device_properties(local)
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * RECIPE_MAX_SM_MHZ * 1e6 / 1e12
+    fwd_ms = float(np.mean(fwd))
+    achieved = 35.0 * n * n / (fwd_ms / 1e3) / 1e12
+    line = {"metric": METRIC, "value": pairs / (tmax / 1e3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+            "config": {"workload": f"adjoint_n65536: N={n}, phi={c['phi']}, translation only, FP32 compensated; "
+                                   f"step = lm_mdot + lm_mdot_backward (dX, dF)",
+                       "forward_ms": fwd_ms, "backward_ms": float(np.mean(bwd)),
+                       "backward_over_forward": float(np.mean(bwd)) / fwd_ms,
+                       "pair_config": lm.lm_get_pair_config(solver),
+                       "l2": "flushed by a 256 MB device write before every step"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "rpy_mdot_kernel (forward, translation, 35 flops/pair)"},
+            "gpu_launches": launches, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_bd(args, ws, rank, local):
+    """Batched Brownian dynamics: 256 suspensions (N log-uniform in [64, 4096],
+    phi uniform in [0.05, 0.3]), 10 Euler-Maruyama steps per bench step in one
+    persistent cooperative launch captured in a CUDA graph, Lanczos tol 1e-4.
+    Pairs counted: sum_s N_s^2 per Lanczos iteration of system s.  Also times
+    one BD step done with per-system library calls, for the speed-up factor."""
+    import torch
+
+    from paper_2510_02135_gb300 import _build, inputs as I, lm
+
+    dist = _dist_init(ws, local)
+    _build.build()
+    c = I.BATCH_BD_256
+    b_ = I.batch_suspensions(c["seed"], c["S"], c["nmin"], c["nmax"], c["phi_lo"], c["phi_hi"], c["a"])
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    b = lm.lm_batch_create(b_.offsets, c["eta"], c["a"], max_iter=64,
+                           cuda_stream=torch.cuda.current_stream().cuda_stream)
+    lm.lm_batch_set_positions(b, dev(b_.pos))
+    tiling = lm.lm_batch_autotune(b) if not args.no_autotune else {"threads": 128, "ilp": 1}
+    nsub = 10
+    sizes2 = b_.sizes.astype(np.float64) ** 2
+    step_no = [0]
+
+    def step():
+        its = lm.lm_batch_bd_run(b, c["kT"], c["dt"], c["k_trap"], nsub, step0=step_no[0], seed=c["seed"],
+                                 tol=c["tol"], use_graph=True)
+        step_no[0] += nsub
+        return its
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = lm.lm_launch_count()
+    t0 = time.perf_counter()
+    pairs = 0.0
+    iters = []
+    for _ in range(args.steps):
+        its = step()
+        pairs += float((sizes2 * its).sum())
+        iters.append(its.sum() / (b.S * nsub))
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t = (time.perf_counter() - t0) * 1e3
+    clocks = sampler.stop()
+    launches = lm.lm_launch_count() - launches0
+    tmax, pairs_all = _reduce(dist, t, pairs)
+    # one BD step with per-system calls (same noise streams and tolerance)
+    t_loop = None
+    if rank == 0:
+        x = lm.lm_batch_get_positions(b, like=dev(b_.pos))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        sq = float(np.sqrt(2 * c["kT"] * c["dt"]))
+        for s in range(b.S):
+            o0, o1 = int(b_.offsets[s]), int(b_.offsets[s + 1])
+            sv = lm.lm_create(c["eta"], c["a"], False, lm.LM_FP32C)
+            xs = x[o0:o1].contiguous()
+            lm.lm_set_positions(sv, xs)
+            uu, _ = lm.lm_mdot(sv, (-c["k_trap"]) * xs, None)
+            W = torch.empty(3 * (o1 - o0), dtype=torch.float64, device="cuda")
+            lm.lm_philox_normals(c["seed"], (step_no[0] << 32) | s, W)
+            y, _, _ = lm.lm_sqrt_mdot(sv, W, tol=c["tol"], max_iter=64, prefactor=sq)
+            x[o0:o1] = xs + c["dt"] * uu + y
+        torch.cuda.synchronize()
+        t_loop = time.perf_counter() - t1
+    ms_bd_step = tmax / (args.steps * nsub)
+    line = {"metric": METRIC, "value": pairs_all / (tmax / 1e3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "dtype_detail": "FP32 pairs (compensated), FP64 Lanczos",
+            "data": "synthetic (seeded)",
+            "config": {"workload": "bd256: 256 systems, N log-uniform [64, 4096], phi U(0.05, 0.3), a=1, eta=1, "
+                                   "kT=1, dt=1e-3, k=1, tol 1e-4; one bench step = 10 EM steps in one graph launch",
+                       "N_total": int(b.Ntot), "ms_per_bd_step": ms_bd_step,
+                       "lanczos_iterations_mean": float(np.mean(iters)), "tiling": tiling,
+                       "per_system_calls_ms_per_bd_step": None if t_loop is None else 1e3 * t_loop,
+                       "speedup_vs_per_system_calls": None if t_loop is None else 1e3 * t_loop / ms_bd_step},
+            "gpu_launches": launches, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:

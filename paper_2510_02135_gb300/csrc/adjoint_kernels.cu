@@ -105,7 +105,7 @@ struct IData {
 template <typename R, bool ANG>
 struct AAcc {
     static constexpr int C = ANG ? 9 : 6;   // dX(3) dF(3) [dT(3)]
-    R p[C], hi[C], lo[C];
+    R p[C];                                 // current-tile partials (running sums in shared memory)
     R sG, sF;                               // scalars multiplying G_i, F_i
     R sH, sT;                               // scalars multiplying H_i, T_i
     R gT[3], gF[3], gG[3], gH[3];           // g-weighted sums of j vectors
@@ -179,23 +179,25 @@ __device__ __forceinline__ void adj_pair(R dx, R dy, R dz, const Coef<R>& c, boo
     }
 }
 
-__device__ __forceinline__ void fold(float& hi, float& lo, float& p) {
-    const float s = hi + p;
-    const float bb = s - hi;
-    const float err = (hi - (s - bb)) + (p - bb);
-    hi = s;
-    lo += err;
+__device__ __forceinline__ void fold(float* hi, float* lo, float& p) {
+    const float h = *hi;
+    const float s = h + p;
+    const float bb = s - h;
+    const float err = (h - (s - bb)) + (p - bb);
+    *hi = s;
+    *lo += err;
     p = 0.0f;
 }
-__device__ __forceinline__ void fold(double& hi, double& lo, double& p) {
-    hi += p;
+__device__ __forceinline__ void fold(double* hi, double* lo, double& p) {
+    *hi += p;
     p = 0.0;
     (void)lo;
 }
 
-// Apply the tile's i-side products to dX and fold.
-template <typename R, bool ANG>
-__device__ __forceinline__ void flush_tile(const IData<R, ANG>& I, AAcc<R, ANG>& a) {
+// Apply the tile's i-side products to dX and fold into the running sums
+// (shared memory, [c][q][tid]).
+template <typename R, bool ANG, int NT, int NI>
+__device__ __forceinline__ void flush_tile(const IData<R, ANG>& I, AAcc<R, ANG>& a, R* s_hi, R* s_lo, int q) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) a.p[q] = fma(a.sG, I.G[q], fma(a.sF, I.F[q], a.p[q]));
     a.sG = a.sF = R(0);
@@ -214,10 +216,18 @@ __device__ __forceinline__ void flush_tile(const IData<R, ANG>& I, AAcc<R, ANG>&
         for (int q = 0; q < 3; ++q) a.gT[q] = a.gF[q] = a.gG[q] = a.gH[q] = R(0);
     }
 #pragma unroll
-    for (int c = 0; c < AAcc<R, ANG>::C; ++c) fold(a.hi[c], a.lo[c], a.p[c]);
+    for (int c = 0; c < AAcc<R, ANG>::C; ++c) {
+        const int o = (c * NI + q) * NT + threadIdx.x;
+        fold(&s_hi[o], &s_lo[o], a.p[c]);
+    }
 }
 
-template <typename R, bool ANG, int NT>
+template <typename R, bool ANG, int NT, int NI>
+constexpr size_t adj_running_bytes() {
+    return (size_t)(ANG ? 9 : 6) * NI * NT * sizeof(R) * (sizeof(R) == 4 ? 2 : 1);
+}
+
+template <typename R, bool ANG, int NT, int NI>
 __global__ void __launch_bounds__(NT) rpy_adjoint_kernel(const typename V4<R>::type* __restrict__ pos4,
                                                          const void* __restrict__ Fp, const void* __restrict__ Tp,
                                                          const void* __restrict__ Gp, const void* __restrict__ Hp,
@@ -228,35 +238,46 @@ __global__ void __launch_bounds__(NT) rpy_adjoint_kernel(const typename V4<R>::t
     constexpr int C = AAcc<R, ANG>::C;
     __shared__ R4 sp[NT], sF[NT], sG[NT];
     __shared__ R4 sT[ANG ? NT : 1], sH[ANG ? NT : 1];
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    R* s_hi = reinterpret_cast<R*>(dyn_smem);
+    R* s_lo = s_hi + (sizeof(R) == 4 ? C * NI * NT : 0);
     const int tid = threadIdx.x;
-    const int64_t i = (int64_t)blockIdx.x * NT + tid;
+    const int64_t i0 = (int64_t)blockIdx.x * (NT * NI);
     const int64_t jb = (int64_t)blockIdx.y * jchunk;
     const int64_t je = (jb + jchunk < N) ? (jb + jchunk) : N;
     const R pad = (R)kPadCoord;
 
-    IData<R, ANG> I;
-    if (i < N) {
-        const R4 p = pos4[i];
-        I.x = p.x; I.y = p.y; I.z = p.z;
-    } else {
-        I.x = I.y = I.z = -pad;
-    }
-    const int64_t ii = (i < N) ? i : 0;
+    IData<R, ANG> I[NI];
+    AAcc<R, ANG> a[NI];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        I.F[q] = ld<R>(Fp, f64, 3 * ii + q);
-        I.G[q] = ld<R>(Gp, f64, 3 * ii + q);
-        if constexpr (ANG) {
-            I.T[q] = ld<R>(Tp, f64, 3 * ii + q);
-            I.H[q] = ld<R>(Hp, f64, 3 * ii + q);
+    for (int q = 0; q < NI; ++q) {
+        const int64_t i = i0 + (int64_t)q * NT + tid;
+        if (i < N) {
+            const R4 p = pos4[i];
+            I[q].x = p.x; I[q].y = p.y; I[q].z = p.z;
+        } else {
+            I[q].x = I[q].y = I[q].z = -pad;
         }
+        const int64_t ii = (i < N) ? i : 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            I[q].F[c] = ld<R>(Fp, f64, 3 * ii + c);
+            I[q].G[c] = ld<R>(Gp, f64, 3 * ii + c);
+            if constexpr (ANG) {
+                I[q].T[c] = ld<R>(Tp, f64, 3 * ii + c);
+                I[q].H[c] = ld<R>(Hp, f64, 3 * ii + c);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            a[q].p[c] = R(0);
+            s_hi[(c * NI + q) * NT + tid] = R(0);
+            if (sizeof(R) == 4) s_lo[(c * NI + q) * NT + tid] = R(0);
+        }
+        a[q].sG = a[q].sF = a[q].sH = a[q].sT = R(0);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a[q].gT[c] = a[q].gF[c] = a[q].gG[c] = a[q].gH[c] = R(0);
     }
-    AAcc<R, ANG> a;
-#pragma unroll
-    for (int c = 0; c < C; ++c) a.p[c] = a.hi[c] = a.lo[c] = R(0);
-    a.sG = a.sF = a.sH = a.sT = R(0);
-#pragma unroll
-    for (int q = 0; q < 3; ++q) a.gT[q] = a.gF[q] = a.gG[q] = a.gH[q] = R(0);
 
     R4 np, nF, nG, nT, nH;
     auto fetch = [&](int64_t j) {
@@ -286,33 +307,52 @@ __global__ void __launch_bounds__(NT) rpy_adjoint_kernel(const typename V4<R>::t
             const R4 Gj = sG[jj];
             R4 Tj, Hj;
             if constexpr (ANG) { Tj = sT[jj]; Hj = sH[jj]; } else { Tj = Fj; Hj = Fj; }
-            const R dx = I.x - pj.x, dy = I.y - pj.y, dz = I.z - pj.z;
-            const R r2 = fma(dx, dx, fma(dy, dy, dz * dz));
-            Coef<R> c;
-            if (__any_sync(0xffffffffu, r2 < k.four_a2)) {
-                const bool g = exact_coef<R, ANG>(r2, k, c);
-                adj_pair<R, ANG>(dx, dy, dz, c, g, Fj, Gj, Tj, Hj, I, a);
+            R dx[NI], dy[NI], dz[NI], r2[NI];
+            R mn = R(0);
+#pragma unroll
+            for (int q = 0; q < NI; ++q) {
+                dx[q] = I[q].x - pj.x; dy[q] = I[q].y - pj.y; dz[q] = I[q].z - pj.z;
+                r2[q] = fma(dx[q], dx[q], fma(dy[q], dy[q], dz[q] * dz[q]));
+                mn = (q == 0) ? r2[q] : fmin(mn, r2[q]);
+            }
+            if (__any_sync(0xffffffffu, mn < k.four_a2)) {
+#pragma unroll
+                for (int q = 0; q < NI; ++q) {
+                    Coef<R> c;
+                    const bool g = exact_coef<R, ANG>(r2[q], k, c);
+                    adj_pair<R, ANG>(dx[q], dy[q], dz[q], c, g, Fj, Gj, Tj, Hj, I[q], a[q]);
+                }
             } else {
-                far_coef<R, ANG>(r2, k, c);
-                adj_pair<R, ANG>(dx, dy, dz, c, true, Fj, Gj, Tj, Hj, I, a);
+#pragma unroll
+                for (int q = 0; q < NI; ++q) {
+                    Coef<R> c;
+                    far_coef<R, ANG>(r2[q], k, c);
+                    adj_pair<R, ANG>(dx[q], dy[q], dz[q], c, true, Fj, Gj, Tj, Hj, I[q], a[q]);
+                }
             }
         }
-        flush_tile<R, ANG>(I, a);
+#pragma unroll
+        for (int q = 0; q < NI; ++q) flush_tile<R, ANG, NT, NI>(I[q], a[q], s_hi, s_lo, q);
         __syncthreads();
     }
-    if (i >= N) return;
     const bool direct = (gridDim.y == 1);
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-        const double v = (double)a.hi[c] + (double)a.lo[c];
-        if (direct) {
-            void* out = (c < 3) ? dX : (c < 6 ? dF : dT);
-            if (out == nullptr) continue;
-            const int64_t idx = 3 * i + (c % 3);
-            if (f64) static_cast<double*>(out)[idx] = c8 * v;
-            else static_cast<float*>(out)[idx] = (float)(c8 * v);
-        } else {
-            partials[((int64_t)blockIdx.y * C + c) * N + i] = v;
+    for (int q = 0; q < NI; ++q) {
+        const int64_t i = i0 + (int64_t)q * NT + tid;
+        if (i >= N) continue;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int o = (c * NI + q) * NT + tid;
+            const double v = (double)s_hi[o] + (sizeof(R) == 4 ? (double)s_lo[o] : 0.0);
+            if (direct) {
+                void* out = (c < 3) ? dX : (c < 6 ? dF : dT);
+                if (out == nullptr) continue;
+                const int64_t idx = 3 * i + (c % 3);
+                if (f64) static_cast<double*>(out)[idx] = c8 * v;
+                else static_cast<float*>(out)[idx] = (float)(c8 * v);
+            } else {
+                partials[((int64_t)blockIdx.y * C + c) * N + i] = v;
+            }
         }
     }
 }
@@ -341,10 +381,10 @@ int64_t adj_split_plan(int64_t N, int NT, int splits, int64_t* jchunk) {
     return (N + *jchunk - 1) / *jchunk;
 }
 
-template <typename R, bool ANG>
+template <typename R, bool ANG, int NI>
 cudaError_t launch_adj_t(const AdjointArgs& a, cudaStream_t s) {
     constexpr int NT = 128;
-    const int64_t nblk = (a.N + NT - 1) / NT;
+    const int64_t nblk = (a.N + NT * NI - 1) / (NT * NI);
     int64_t jchunk = 0;
     const int splits = (int)adj_split_plan(a.N, NT, a.splits, &jchunk);
     if (nblk > 0x7fffffff || splits > 65535) return cudaErrorInvalidConfiguration;
@@ -352,7 +392,15 @@ cudaError_t launch_adj_t(const AdjointArgs& a, cudaStream_t s) {
     const double c8 = 1.0 / (8.0 * 3.14159265358979323846 * a.eta);
     const RpyConst<R> k = make_rpy_const<R>(a.a);
     dim3 grid((unsigned)nblk, (unsigned)splits);
-    rpy_adjoint_kernel<R, ANG, NT><<<grid, NT, 0, s>>>(static_cast<const typename V4<R>::type*>(a.pos4), a.F,
+    constexpr size_t dyn = adj_running_bytes<R, ANG, NT, NI>();
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(rpy_adjoint_kernel<R, ANG, NT, NI>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    rpy_adjoint_kernel<R, ANG, NT, NI><<<grid, NT, dyn, s>>>(static_cast<const typename V4<R>::type*>(a.pos4), a.F,
                                                        ANG ? a.T : nullptr, a.G, ANG ? a.H : nullptr, a.fp64, a.N,
                                                        jchunk, k, c8, a.dX, a.dF, ANG ? a.dT : nullptr, a.partials);
     cudaError_t err = cudaGetLastError();
@@ -370,11 +418,34 @@ cudaError_t launch_adj_t(const AdjointArgs& a, cudaStream_t s) {
 
 int adjoint_partial_components(int angular) { return angular ? 9 : 6; }
 
+// i-particles per thread: FP32 translation 4, FP32 with angular blocks 2,
+// FP64 1 (register budget of the heavier angular and FP64 adjoints).
+int adjoint_ilp(int fp64, int angular) { return fp64 ? 1 : (angular ? 2 : 4); }
+
 cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s) {
     if (a.N <= 0) return cudaSuccess;
     if (a.threads != 128) return cudaErrorInvalidConfiguration;
-    if (a.fp64) return a.angular ? launch_adj_t<double, true>(a, s) : launch_adj_t<double, false>(a, s);
-    return a.angular ? launch_adj_t<float, true>(a, s) : launch_adj_t<float, false>(a, s);
+    if (a.fp64) return a.angular ? launch_adj_t<double, true, 1>(a, s) : launch_adj_t<double, false, 1>(a, s);
+    return a.angular ? launch_adj_t<float, true, 2>(a, s) : launch_adj_t<float, false, 4>(a, s);
+}
+
+int adjoint_ctas_per_sm(int fp64, int angular) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidConfiguration;
+#define LM_AOCC(R, ANG, NI)                                                                       \
+    {                                                                                             \
+        constexpr size_t dyn = adj_running_bytes<R, ANG, 128, NI>();                              \
+        e = cudaFuncSetAttribute(rpy_adjoint_kernel<R, ANG, 128, NI>,                             \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);          \
+        if (e == cudaSuccess)                                                                     \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rpy_adjoint_kernel<R, ANG, 128, NI>, 128, dyn); \
+    }
+    if (fp64 && angular) LM_AOCC(double, true, 1)
+    else if (fp64) LM_AOCC(double, false, 1)
+    else if (angular) LM_AOCC(float, true, 2)
+    else LM_AOCC(float, false, 4)
+#undef LM_AOCC
+    return e == cudaSuccess ? n : 0;
 }
 
 }  // namespace lmk

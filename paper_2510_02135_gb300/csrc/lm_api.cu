@@ -650,9 +650,9 @@ lm_status lm_mdot_backward(lm_solver* s, const void* forces, const void* torques
     if (lm_status st = stage_out(s, dT, bytes, 2, &ov[2])) return st;
     if (dX == nullptr && dF == nullptr && dT == nullptr) return LM_OK;
     if (s->adj_cfg_N != s->N) {
-        lm_pair_config c{128, 1, 1};
-        int slots = 4 * s->sm_count;
-        c.splits = auto_splits(s->N, c.threads, 1, slots);
+        lm_pair_config c{128, lmk::adjoint_ilp(s->fp64, s->angular), 1};
+        const int occ = std::max(1, lmk::adjoint_ctas_per_sm(s->fp64, s->angular));
+        c.splits = auto_splits(s->N, c.threads, c.ilp, occ * s->sm_count);
         s->adj_cfg = c;
         s->adj_cfg_N = s->N;
     }
@@ -722,11 +722,11 @@ lm_status lm_autotune(lm_solver* s, int reps, lm_pair_config* best) {
             const int occ = lmk::mdot_ctas_per_sm(s->fp64, s->angular, t, il);
             if (occ < 1) continue;
             const int sa = auto_splits(N, t, il, occ * s->sm_count);
-            int opts[3] = {sa, std::max(1, sa / 2), sa * 2};
-            for (int k = 0; k < 3; ++k) {
-                if (k > 0 && opts[k] == sa) continue;
-                if (k == 2 && opts[2] == opts[1]) continue;
-                cands.push_back(lm_pair_config{t, il, opts[k]});
+            const int opts[4] = {sa, std::max(1, sa / 2), std::max(1, (3 * sa) / 2), sa * 2};
+            for (int k = 0; k < 4; ++k) {
+                bool dup = false;
+                for (int q = 0; q < k; ++q) dup = dup || (opts[q] == opts[k]);
+                if (!dup) cands.push_back(lm_pair_config{t, il, opts[k]});
             }
         }
     }

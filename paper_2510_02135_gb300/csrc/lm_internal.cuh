@@ -118,6 +118,8 @@ int mdot_partial_components(int angular);
 cudaError_t launch_mdot(const MdotArgs& a, cudaStream_t s);
 cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s);
 int adjoint_partial_components(int angular);
+int adjoint_ilp(int fp64, int angular);
+int adjoint_ctas_per_sm(int fp64, int angular);
 
 // Pack N x 3 positions into (x, y, z, 0) and flag non-finite or too large
 // coordinates in *bad (device int, set to 1).

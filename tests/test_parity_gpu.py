@@ -155,10 +155,12 @@ def test_mdot_edge_cases(orc, fp64):
 
 def test_mdot_rpy6_n32768_sampled_rows(orc):
     """Full-size 6N FP32 workload (N = 32768, phi = 0.2) in the benchmark's
-    launch configuration; 256 sampled rows against the oracle, per block."""
+    launch configuration (autotuned, as bench.py does); 256 sampled rows
+    against the oracle, per block."""
     c = I.RPY6_FP32_N32768
     s_ = I.cube_suspension(c["seed"], c["n"], c["phi"], c["a"], angular=True, fp32=True)
     s = make(c["eta"], c["a"], True, False, s_.pos)
+    lm.lm_autotune(s, reps=2)
     rows = np.random.default_rng(0).choice(c["n"], 256, replace=False)
     zero = np.zeros_like(s_.F)
     for name, F, T in (("F", s_.F, zero), ("T", zero, s_.T), ("FT", s_.F, s_.T)):
