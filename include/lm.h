@@ -266,9 +266,10 @@ lm_status lm_batch_sqrt_mdot(lm_batch *batch, const double *W, uint64_t seed, do
  * All steps run in one persistent cooperative launch; with use_graph != 0
  * that launch is captured into a CUDA graph and the graph is launched.
  * The stopping rule is that of lm_sqrt_mdot per system, except that the
- * relative-change test (and the tridiagonal solve it needs) starts at the
- * iteration count the system needed in its previous step minus 3: counts
- * change little from step to step, and each test costs an FP64 eigen-solve.
+ * relative-change test is first made one iteration before the count the
+ * system needed in its previous step (its tridiagonal solves start one
+ * iteration earlier still): counts change little from step to step, and each
+ * test costs an FP64 eigen-solve.
  * Breakdown and max_iter are tested at every iteration.
  * Positions stay on the device (lm_batch_get_positions reads them).
  * iters_out: optional host array of S ints (total Lanczos iterations per

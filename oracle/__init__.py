@@ -193,7 +193,11 @@ def lanczos_sqrt(matvec, W, tol: float, max_iter: int = 200, breakdown: float = 
       w   = M v_k
       alpha_k = v_k . w
       w  -= alpha_k v_k + beta_{k-1} v_{k-1}
-      w  -= V_k (V_k^T w), done twice (full reorthogonalisation)
+      h0  = |w|;  w -= V_k (V_k^T w);  h1 = |w|     (full reorthogonalisation)
+      if h1 < h0 / sqrt(2):  w -= V_k (V_k^T w)      (second pass only after
+                                                       cancellation: the DGKS
+                                                       criterion of Daniel,
+                                                       Gragg, Kaufman & Stewart 1976)
       beta_k = |w|
       z_k = |W| f(T_k) e1 with f = sqrt,  y_k = V_k z_k
       stop when k >= 2 and |z_k - [z_{k-1}; 0]| / |z_k| < tol   (converged)
@@ -221,7 +225,10 @@ def lanczos_sqrt(matvec, W, tol: float, max_iter: int = 200, breakdown: float = 
         w -= a_k * V[k]
         if k > 0:
             w -= beta[k - 1] * V[k - 1]
-        for _ in range(2):
+        h0 = float(np.linalg.norm(w))
+        w -= V[: k + 1].T @ (V[: k + 1] @ w)
+        h1 = float(np.linalg.norm(w))
+        if h1 < h0 / np.sqrt(2.0):
             w -= V[: k + 1].T @ (V[: k + 1] @ w)
         b_k = float(np.linalg.norm(w))
         alpha.append(a_k)

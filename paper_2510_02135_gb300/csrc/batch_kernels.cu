@@ -13,11 +13,12 @@
 //                  loading (and stored for the own rows); partial v_k . w
 //     C2  chunks   w = sum of the j-parts; alpha_k = sum of the item partials;
 //                  w -= alpha_k v_k + beta_{k-1} v_{k-1}; dots V_s^T w
-//     C3  chunks   w -= V_s c; dots V_s^T w            (second Gram-Schmidt pass)
-//     C4  chunks   w -= V_s c'; |w|^2 partials
+//     C3  chunks   w -= V_s c; dots V_s^T w; |w|^2 before and after the pass
+//     C4  chunks   w -= V_s c' only if |w| fell below 1/sqrt(2) of its value
+//                  before C3 (DGKS); |w|^2 partials
 //     C5  systems  beta_k; z_k = |W| f(T_k) e1 (implicit QR, FP64); stopping rule
-//                  (in BD runs the solve and the relative-change test start at
-//                  the previous step's iteration count minus 3)
+//                  (in BD runs the relative-change test is first made one
+//                  iteration before the count of the system's previous step)
 //   D   chunks   y = V_s z; x += dt u + sqrt(2 kT dt) y
 // Phases are separated by a grid barrier whose waits are bounded in clock
 // cycles: an expired wait sets an error flag and every CTA returns.
@@ -470,17 +471,30 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                 const double* vk = basis(P, s, k);
                 const double* vkm1 = (k > 0) ? basis(P, s, k - 1) : vk;
                 double* w = wcur + 3 * o;
+                double h0 = 0.0;
                 for (int e = e0 + tid; e < e1; e += NT) {
-                    w[e] = sum_parts(P.wsplit, s, e) - (alpha * vk[e] + bprev * vkm1[e]);
+                    const double we = sum_parts(P.wsplit, s, e) - (alpha * vk[e] + bprev * vkm1[e]);
+                    w[e] = we;
+                    h0 = fma(we, we, h0);
                     if (k == 0 && P.mode == kBatchBD) P.u[3 * o + e] = sum_parts(P.usplit, s, e);
                 }
+                // |w|^2 before the Gram-Schmidt pass, in the spare last slot
+                h0 = warp_sum_d(h0);
+                if ((tid & 31) == 0) sred[tid >> 5] = h0;
                 __syncthreads();
+                if (tid == 0) {
+                    double t = 0.0;
+                    for (int ww = 0; ww < NT / 32; ++ww) t += sred[ww];
+                    partA[(int64_t)c * M1 + P.m_max] = t;
+                }
                 chunk_dots<NT>(P, s, e0, e1, w, k + 1, partA + (int64_t)c * M1);
                 __syncthreads();
             }
             if (!grid_sync(P)) return;
             stamp(P, step, slot);
-            // C3, C4: subtract projections; dots again / norm
+            // C3: first Gram-Schmidt pass; dots for a second pass and |w|^2 after.
+            // C4: second pass only if |w| dropped below |w_before| / sqrt(2)
+            //     (DGKS criterion); |w|^2 partials for beta.
             for (int pass = 0; pass < 2; ++pass) {
                 const double* pin = pass == 0 ? partA : partB;
                 double* pout = pass == 0 ? partB : partA;
@@ -490,39 +504,49 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                     const int64_t o = P.off[s];
                     const int ns = 3 * (int)(P.off[s + 1] - o);
                     const int e1 = min(e0 + kBatchChunk, ns);
-                    chunk_sum_coeffs<NT>(P, s, pin, k + 1, cvec);
+                    bool apply = true;
+                    if (pass == 1) {
+                        double h0 = 0.0, h1 = 0.0;
+                        for (int cc = P.chunk_range[2 * s]; cc < P.chunk_range[2 * s + 1]; ++cc) {
+                            h0 += partA[(int64_t)cc * M1 + P.m_max];
+                            h1 += partB[(int64_t)cc * M1 + P.m_max];
+                        }
+                        apply = h1 < 0.5 * h0;   // squared norms: |w1| < |w0| / sqrt(2)
+                    }
                     double* w = wcur + 3 * o;
                     const double* V0 = basis(P, s, 0);
                     double nrm = 0.0;
+                    if (apply) chunk_sum_coeffs<NT>(P, s, pin, k + 1, cvec);
                     for (int e = e0 + tid; e < e1; e += NT) {
                         double acc = w[e];
-                        for (int j = 0; j <= k; ++j) acc -= cvec[j] * V0[(int64_t)j * ns + e];
+                        if (apply)
+                            for (int j = 0; j <= k; ++j) acc -= cvec[j] * V0[(int64_t)j * ns + e];
                         w[e] = acc;
                         nrm = fma(acc, acc, nrm);
                     }
                     __syncthreads();
-                    if (pass == 0) {
-                        chunk_dots<NT>(P, s, e0, e1, w, k + 1, pout + (int64_t)c * M1);
-                    } else {
-                        nrm = warp_sum_d(nrm);
-                        if ((tid & 31) == 0) sred[tid >> 5] = nrm;
-                        __syncthreads();
-                        if (tid == 0) {
-                            double t = 0.0;
-                            for (int ww = 0; ww < NT / 32; ++ww) t += sred[ww];
-                            pout[(int64_t)c * M1] = t;
-                        }
+                    nrm = warp_sum_d(nrm);
+                    if ((tid & 31) == 0) sred[tid >> 5] = nrm;
+                    __syncthreads();
+                    if (tid == 0) {
+                        double t = 0.0;
+                        for (int ww = 0; ww < NT / 32; ++ww) t += sred[ww];
+                        pout[(int64_t)c * M1 + (pass == 0 ? P.m_max : 0)] = t;
                     }
+                    if (pass == 0) chunk_dots<NT>(P, s, e0, e1, w, k + 1, pout + (int64_t)c * M1);
                     __syncthreads();
                 }
                 if (!grid_sync(P)) return;
                 stamp(P, step, slot);
             }
             // C5: beta, tridiagonal square root, stopping rule (one thread per system).
-            // Warm start (BD mode): the tridiagonal solve and the relative-change
-            // test begin at k0 = kprev - 3, two iterations before the first test,
-            // since iteration counts change little from one step to the next;
-            // breakdown and max_iter are tested at every iteration.
+            // Warm start (BD mode): with kprev the iteration count of the system's
+            // previous step, the tridiagonal solve begins at (0-based) iteration
+            // k0 = kprev - 3 and the relative-change test one iteration later, at
+            // the count kprev - 1 (one below the previous count, so that counts
+            // can also fall from step to step), since counts change little from
+            // one step to the next; breakdown and max_iter are tested at every
+            // iteration.
             for (int s = blockIdx.x; s < P.S; s += G) {
                 if (tid != 0 || !P.active[s]) continue;
                 double b2 = 0.0;

@@ -73,8 +73,15 @@ __global__ void axpy2_kernel(double* __restrict__ w, const double* __restrict__ 
 
 // Multi-dot: block b owns the chunk [b*cs, min(n, (b+1)*cs)); warp q handles
 // rows j = q, q + 8, ...; red[j * nb + b] = partial dot.
+// DGKS test for the second Gram-Schmidt pass: h = [h0, h0^2, h1, h1^2], the
+// norms before and after the first pass; the pass runs only if h1 < h0 / sqrt(2).
+__device__ __forceinline__ bool second_pass_needed(const double* h) {
+    return h == nullptr || h[2] < h[0] * 0.70710678118654752440;
+}
+
 __global__ void multidot_stage1(const double* __restrict__ V, int m, const double* __restrict__ w, int64_t n,
-                                int64_t cs, double* __restrict__ red) {
+                                int64_t cs, double* __restrict__ red, const double* __restrict__ cond) {
+    if (!second_pass_needed(cond)) return;
     const int64_t e0 = (int64_t)blockIdx.x * cs;
     const int64_t e1 = (e0 + cs < n) ? (e0 + cs) : n;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -87,7 +94,9 @@ __global__ void multidot_stage1(const double* __restrict__ V, int m, const doubl
     }
 }
 
-__global__ void multidot_stage2(const double* __restrict__ red, int m, int nb, double* __restrict__ c) {
+__global__ void multidot_stage2(const double* __restrict__ red, int m, int nb, double* __restrict__ c,
+                                const double* __restrict__ cond) {
+    if (!second_pass_needed(cond)) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int j = blockIdx.x * (kThreads / 32) + wid; j < m; j += gridDim.x * (kThreads / 32)) {
         double acc = 0.0;
@@ -99,7 +108,9 @@ __global__ void multidot_stage2(const double* __restrict__ red, int m, int nb, d
 
 // w[e] (+)= sign * sum_j c[j] V[j][e]; accumulate = 0 overwrites (y = V^T z).
 __global__ void combine_kernel(const double* __restrict__ V, int m, const double* __restrict__ c,
-                               double* __restrict__ w, int64_t n, int accumulate, double sign) {
+                               double* __restrict__ w, int64_t n, int accumulate, double sign,
+                               const double* __restrict__ cond) {
+    if (!second_pass_needed(cond)) return;
     __shared__ double cs[256];
     for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e - threadIdx.x < n;
          e += (int64_t)gridDim.x * kThreads) {
@@ -216,18 +227,19 @@ cudaError_t lz_axpy2(double* w, const double* vk, const double* alpha, const dou
 }
 
 cudaError_t lz_multidot(const double* V, int m, const double* w, int64_t n, double* red, double* c,
-                        cudaStream_t s) {
+                        cudaStream_t s, const double* cond) {
     int nb = 0;
     const int64_t cs = md_chunk(n, &nb);
-    multidot_stage1<<<nb, kThreads, 0, s>>>(V, m, w, n, cs, red);
+    multidot_stage1<<<nb, kThreads, 0, s>>>(V, m, w, n, cs, red, cond);
     const int g2 = (m + (kThreads / 32) - 1) / (kThreads / 32);
-    multidot_stage2<<<g2, kThreads, 0, s>>>(red, m, nb, c);
+    multidot_stage2<<<g2, kThreads, 0, s>>>(red, m, nb, c, cond);
     count_launches(2);
     return cudaGetLastError();
 }
 
-cudaError_t lz_sub_vc(const double* V, int m, const double* c, double* w, int64_t n, cudaStream_t s) {
-    combine_kernel<<<blocks_for(n, 1), kThreads, 0, s>>>(V, m, c, w, n, 1, -1.0);
+cudaError_t lz_sub_vc(const double* V, int m, const double* c, double* w, int64_t n, cudaStream_t s,
+                      const double* cond) {
+    combine_kernel<<<blocks_for(n, 1), kThreads, 0, s>>>(V, m, c, w, n, 1, -1.0, cond);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -239,7 +251,7 @@ cudaError_t lz_scale(const double* x, const double* nrm, double* y, int64_t n, c
 }
 
 cudaError_t lz_combine(const double* V, int m, const double* z, double* y, int64_t n, cudaStream_t s) {
-    combine_kernel<<<blocks_for(n, 1), kThreads, 0, s>>>(V, m, z, y, n, 0, 1.0);
+    combine_kernel<<<blocks_for(n, 1), kThreads, 0, s>>>(V, m, z, y, n, 0, 1.0, nullptr);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -439,7 +439,8 @@ lm_status lm_div_m(lm_solver* s, void* lin_out, void* ang_out) {
 // ---------------------------------------------------------------------------
 // Lanczos square root (Sec. 3.3).  Per iteration k (v_k = row k of V):
 //   w = M v_k;  alpha_k = v_k . w;  w -= alpha_k v_k + beta_{k-1} v_{k-1};
-//   twice: w -= V_k (V_k^T w);  beta_k = |w|;
+//   h0 = |w|; w -= V_k (V_k^T w); h1 = |w|; if h1 < h0 / sqrt(2): again (DGKS);
+//   beta_k = |w|;
 //   z_k = |W| f(T_k) e1 (host);  stop if k >= 1 and
 //   |z_k - [z_{k-1}; 0]| / |z_k| < tol, or on breakdown, or at max_iter;
 //   v_{k+1} = w / beta_k.
@@ -452,22 +453,29 @@ lm_status lm_div_m(lm_solver* s, void* lin_out, void* ang_out) {
 // ---------------------------------------------------------------------------
 namespace {
 
+// Device scalars per iteration k at scal + kScal * k:
+//   [alpha, beta, beta^2, -, h0, h0^2, h1, h1^2]
+constexpr int kScal = 8;
+
 lm_status enqueue_lanczos_iteration(lm_solver* s, int k, int64_t n, double* V, double* w, double* scal, double* red,
                                     double* cb, cudaEvent_t ev) {
     const int64_t N = s->N;
     double* vk = V + (int64_t)k * n;
-    if (k > 0) LM_CUDA(lmk::lz_scale(w, scal + 4 * (k - 1) + 1, vk, n, s->stream), "next basis vector");
+    double* sk = scal + kScal * k;
+    if (k > 0) LM_CUDA(lmk::lz_scale(w, sk - kScal + 1, vk, n, s->stream), "next basis vector");
     if (lm_status st = run_mdot(s, vk, vk + 3 * N, 1, w, w + 3 * N, 1, s->cfg)) return st;
-    LM_CUDA(lmk::lz_dot(vk, w, n, red, scal + 4 * k, s->stream), "alpha");
-    LM_CUDA(lmk::lz_axpy2(w, vk, scal + 4 * k, k > 0 ? vk - n : nullptr, k > 0 ? scal + 4 * (k - 1) + 1 : nullptr, n,
-                          s->stream),
+    LM_CUDA(lmk::lz_dot(vk, w, n, red, sk, s->stream), "alpha");
+    LM_CUDA(lmk::lz_axpy2(w, vk, sk, k > 0 ? vk - n : nullptr, k > 0 ? sk - kScal + 1 : nullptr, n, s->stream),
             "three-term update");
-    for (int pass = 0; pass < 2; ++pass) {
-        LM_CUDA(lmk::lz_multidot(V, k + 1, w, n, red, cb, s->stream), "reorthogonalisation");
-        LM_CUDA(lmk::lz_sub_vc(V, k + 1, cb, w, n, s->stream), "reorthogonalisation");
-    }
-    LM_CUDA(lmk::lz_norm(w, n, red, scal + 4 * k + 1, s->stream), "beta");
-    LM_CUDA(cudaMemcpyAsync(s->pinned + 4 * k, scal + 4 * k, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream),
+    // full reorthogonalisation: one Gram-Schmidt pass, a second one only after cancellation (DGKS)
+    LM_CUDA(lmk::lz_norm(w, n, red, sk + 4, s->stream), "reorthogonalisation");
+    LM_CUDA(lmk::lz_multidot(V, k + 1, w, n, red, cb, s->stream), "reorthogonalisation");
+    LM_CUDA(lmk::lz_sub_vc(V, k + 1, cb, w, n, s->stream), "reorthogonalisation");
+    LM_CUDA(lmk::lz_norm(w, n, red, sk + 6, s->stream), "reorthogonalisation");
+    LM_CUDA(lmk::lz_multidot(V, k + 1, w, n, red, cb, s->stream, sk + 4), "reorthogonalisation");
+    LM_CUDA(lmk::lz_sub_vc(V, k + 1, cb, w, n, s->stream, sk + 4), "reorthogonalisation");
+    LM_CUDA(lmk::lz_norm(w, n, red, sk + 1, s->stream), "beta");
+    LM_CUDA(cudaMemcpyAsync(s->pinned + kScal * k, sk, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream),
             "read alpha, beta");
     LM_CUDA(cudaEventRecord(ev, s->stream), "iteration event");
     return LM_OK;
@@ -502,16 +510,16 @@ lm_status lm_sqrt_mdot(lm_solver* s, const double* W, uint64_t seed, double pref
     LM_CUDA(s->w.ensure((size_t)n * sizeof(double)), "allocating Lanczos vector");
     LM_CUDA(s->y.ensure((size_t)n * sizeof(double)), "allocating Lanczos vector");
     LM_CUDA(s->red.ensure(lmk::lz_red_doubles(n, m_max + 1) * sizeof(double)), "allocating reduction scratch");
-    LM_CUDA(s->scal.ensure((size_t)(4 * (m_max + 3)) * sizeof(double)), "allocating scalars");
+    LM_CUDA(s->scal.ensure((size_t)(kScal * (m_max + 3)) * sizeof(double)), "allocating scalars");
     LM_CUDA(s->zbuf.ensure((size_t)m_max * sizeof(double)), "allocating coefficients");
     LM_CUDA(s->cbuf.ensure((size_t)(m_max + 1) * sizeof(double)), "allocating coefficients");
-    if (s->pinned_doubles < (size_t)(4 * (m_max + 3))) {
+    if (s->pinned_doubles < (size_t)(kScal * (m_max + 3))) {
         cudaFreeHost(s->pinned);
         s->pinned = nullptr;
         s->pinned_doubles = 0;
-        LM_CUDA(cudaMallocHost(reinterpret_cast<void**>(&s->pinned), (size_t)(4 * (m_max + 3)) * sizeof(double)),
+        LM_CUDA(cudaMallocHost(reinterpret_cast<void**>(&s->pinned), (size_t)(kScal * (m_max + 3)) * sizeof(double)),
                 "allocating pinned scalars");
-        s->pinned_doubles = (size_t)(4 * (m_max + 3));
+        s->pinned_doubles = (size_t)(kScal * (m_max + 3));
     }
     while (s->lz_ev.size() < (size_t)(m_max + 1)) {
         cudaEvent_t e;
@@ -523,7 +531,7 @@ lm_status lm_sqrt_mdot(lm_solver* s, const double* W, uint64_t seed, double pref
     double* scal = s->scal.as<double>();
     double* red = s->red.as<double>();
     double* cb = s->cbuf.as<double>();
-    double* wn = scal + 4 * (m_max + 2);  // |W|, |W|^2
+    double* wn = scal + kScal * (m_max + 2);  // |W|, |W|^2
 
     // W: user array (host or device) or Philox normals
     const double* dW = nullptr;
@@ -538,11 +546,11 @@ lm_status lm_sqrt_mdot(lm_solver* s, const double* W, uint64_t seed, double pref
     }
     LM_CUDA(lmk::lz_norm(dW, n, red, wn, s->stream), "norm of W");
     LM_CUDA(lmk::lz_scale(dW, wn, V, n, s->stream), "normalise W");
-    LM_CUDA(cudaMemcpyAsync(s->pinned + 4 * (m_max + 2), wn, sizeof(double), cudaMemcpyDeviceToHost, s->stream),
+    LM_CUDA(cudaMemcpyAsync(s->pinned + kScal * (m_max + 2), wn, sizeof(double), cudaMemcpyDeviceToHost, s->stream),
             "read |W|");
     if (lm_status st = enqueue_lanczos_iteration(s, 0, n, V, w, scal, red, cb, s->lz_ev[0])) return st;
     LM_CUDA(cudaEventSynchronize(s->lz_ev[0]), "lanczos");
-    const double normW = s->pinned[4 * (m_max + 2)];
+    const double normW = s->pinned[kScal * (m_max + 2)];
     s->stats.norm_w = normW;
     if (!std::isfinite(normW)) return fail(LM_ERR_INVALID_ARG, "W contains NaN or Inf");
     if (normW == 0.0) {
@@ -569,8 +577,8 @@ lm_status lm_sqrt_mdot(lm_solver* s, const double* W, uint64_t seed, double pref
             if (lm_status st = enqueue_lanczos_iteration(s, k + 1, n, V, w, scal, red, cb, s->lz_ev[k + 1])) return st;
         }
         LM_CUDA(cudaEventSynchronize(s->lz_ev[k]), "lanczos iteration");
-        const double a_k = s->pinned[4 * k];
-        const double b_k = s->pinned[4 * k + 1];
+        const double a_k = s->pinned[kScal * k];
+        const double b_k = s->pinned[kScal * k + 1];
         if (!std::isfinite(a_k) || !std::isfinite(b_k))
             return fail(LM_ERR_CUDA, "Lanczos produced a non-finite coefficient at iteration %d", k + 1);
         H.alpha.push_back(a_k);

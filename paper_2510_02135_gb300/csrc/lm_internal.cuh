@@ -136,11 +136,13 @@ cudaError_t lz_norm(const double* x, int64_t n, double* red, double* out, cudaSt
 // w -= alpha[0] vk + beta[0] vkm1   (vkm1 / beta nullable)
 cudaError_t lz_axpy2(double* w, const double* vk, const double* alpha, const double* vkm1,
                      const double* beta, int64_t n, cudaStream_t s);
-// c[j] = v_j . w for j < m
+// c[j] = v_j . w for j < m.  With cond = [h0, h0^2, h1, h1^2] (device) the
+// kernels do nothing unless h1 < h0 / sqrt(2) (DGKS second-pass test).
 cudaError_t lz_multidot(const double* V, int m, const double* w, int64_t n, double* red, double* c,
-                        cudaStream_t s);
-// w -= sum_j c[j] v_j
-cudaError_t lz_sub_vc(const double* V, int m, const double* c, double* w, int64_t n, cudaStream_t s);
+                        cudaStream_t s, const double* cond = nullptr);
+// w -= sum_j c[j] v_j  (same optional condition)
+cudaError_t lz_sub_vc(const double* V, int m, const double* c, double* w, int64_t n, cudaStream_t s,
+                      const double* cond = nullptr);
 // y = x / nrm[0]
 cudaError_t lz_scale(const double* x, const double* nrm, double* y, int64_t n, cudaStream_t s);
 // y = sum_j z[j] v_j

@@ -40,19 +40,30 @@ __host__ __device__ inline double inv_sqrt(double t) {
 // eigenvalues).  Rotation t acts on (rk[t], rk[t]+1) with (rc[t], rs[t]).
 // Returns 0; -1 if 30 m QR steps did not converge; -2 if more than max_rot
 // rotations were needed.
+// Deflation test |e| <= eps (|d1| + |d2|).  On the device the comparison is
+// made in FP32 (a dependent FP64 compare costs ~130 cycles there); it only
+// decides when an off-diagonal entry is negligible, and the FP32 operands
+// differ from the FP64 ones by one rounding, far below the threshold's scale.
+__host__ __device__ inline bool negligible(double e, double d1, double d2) {
+#ifdef __CUDA_ARCH__
+    return fabsf((float)e) <= 2.220446049250313e-16f * (fabsf((float)d1) + fabsf((float)d2));
+#else
+    return fabs(e) <= 2.220446049250313e-16 * (fabs(d1) + fabs(d2));
+#endif
+}
+
 __host__ __device__ inline int tridiag_qr_rotations(int m, double* d, double* e, int* rk, double* rc, double* rs,
                                                     int max_rot, int* nrot) {
-    const double eps = 2.220446049250313e-16;
     int steps = 0, nr = 0;
     int hi = m - 1;
     while (hi > 0) {
-        if (fabs(e[hi - 1]) <= eps * (fabs(d[hi - 1]) + fabs(d[hi]))) {
+        if (negligible(e[hi - 1], d[hi - 1], d[hi])) {
             e[hi - 1] = 0.0;
             --hi;
             continue;
         }
         int lo = hi - 1;
-        while (lo > 0 && fabs(e[lo - 1]) > eps * (fabs(d[lo - 1]) + fabs(d[lo]))) --lo;
+        while (lo > 0 && !negligible(e[lo - 1], d[lo - 1], d[lo])) --lo;
         if (lo > 0) e[lo - 1] = 0.0;
         if (++steps > 30 * m) { *nrot = nr; return -1; }
         // Wilkinson shift: eigenvalue of the trailing 2x2 closer to d[hi]
