@@ -291,7 +291,8 @@ lm_status lm_batch_autotune(lm_batch *batch, int *threads_out, int *ilp_out);
  * Phase timeline of a batched run (profiling).  While enabled, the
  * persistent kernel records the device global timer (ns) at the start of the
  * first step and after every phase of that step: [start, A1, A2, then per
- * Lanczos iteration B, C2, C3, C4, C5, then D].  lm_batch_profile_read copies
+ * Lanczos iteration B, C2, C3, C4, C5, then the wait for the last
+ * tridiagonal results, then D].  lm_batch_profile_read copies
  * up to n stamps of the last run into out and the number recorded into
  * *count.
  */

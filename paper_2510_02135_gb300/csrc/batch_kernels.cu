@@ -65,7 +65,7 @@ __device__ bool grid_sync(const BatchParams& P) {
         const unsigned g = *gen;
         __threadfence();
         const unsigned arrived = atomicAdd(P.bar, 1u);
-        if (arrived == gridDim.x - 1) {
+        if (arrived == (unsigned)P.n_main - 1) {
             atomicExch(P.bar, 0u);
             __threadfence();
             atomicAdd(P.bar + 1, 1u);
@@ -291,15 +291,229 @@ __device__ void chunk_sum_coeffs(const BatchParams& P, int s, const double* part
     __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Asynchronous tridiagonal solves.  The main CTAs post a request (step,
+// system, k) once beta_k is known and keep iterating; the warps of the solver
+// CTAs take the posted requests, up to 32 at a time (one per lane), compute
+// |W| f(T_{k+1}) e1 with T_{k+1} = tridiag(beta_0..k-1, alpha_0..k,
+// beta_0..k-1) in FP64 and publish it in the system's result ring under a
+// tag; the main CTAs apply the stopping rule in iteration order as results
+// arrive.  Requests of an earlier step are dropped.  Every wait is bounded by
+// spin_limit clock cycles without progress of the other side.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long res_tag(uint64_t gstep, int k) {
+    return (unsigned long long)gstep * 128ull + (unsigned long long)k + 1ull;
+}
+
+__device__ __forceinline__ size_t res_index(const BatchParams& P, int s, uint64_t gstep, int k) {
+    return ((size_t)s * 2 + (size_t)(gstep & 1)) * (size_t)P.R + (size_t)(k % P.R);
+}
+
+__device__ __forceinline__ unsigned long long vload(const unsigned long long* p) {
+    return *(const volatile unsigned long long*)p;
+}
+
+// Post request (gstep, s, k).  Returns false on a timeout.
+__device__ bool post_request(const BatchParams& P, uint64_t gstep, int s, int k) {
+    atomicAdd(&P.inflight[gstep & 1], 1);
+    __threadfence();   // alpha / beta of the request visible before it is posted
+    const unsigned long long idx = atomicAdd(&P.q_ctr[1], 1ull);
+    const int slot = (int)(idx % (unsigned long long)P.q_cap);
+    if (idx >= (unsigned long long)P.q_cap) {
+        // the slot's previous request must have been read
+        const unsigned long long want = idx - (unsigned long long)P.q_cap + 1ull;
+        long long t0 = clock64();
+        unsigned long long seen = vload(&P.q_ctr[2]);
+        while (vload(&P.q_ack[slot]) != want) {
+            if (*(volatile int*)P.err != kBatchOk) return false;
+            const unsigned long long now = vload(&P.q_ctr[2]);
+            if (now != seen) { seen = now; t0 = clock64(); }
+            if (clock64() - t0 > P.spin_limit) { atomicCAS(P.err, kBatchOk, kBatchTimeout); return false; }
+            __nanosleep(200);
+        }
+    }
+    P.q_req[slot] = (long long)((gstep << 28) | ((uint64_t)s << 7) | (uint64_t)k);
+    __threadfence();
+    atomicExch(&P.q_seq[slot], idx + 1ull);
+    return true;
+}
+
+// Solve the request of ticket idx (one lane).  Returns false on an error.
+__device__ bool serve_request(const BatchParams& P, unsigned long long idx, double* d, double* e, double* z, int* rk,
+                              double* rc, double* rs) {
+    const int slot = (int)(idx % (unsigned long long)P.q_cap);
+    const long long t0 = clock64();
+    while (vload(&P.q_seq[slot]) != idx + 1ull) {   // the poster is between its two writes
+        if (clock64() - t0 > P.spin_limit) { atomicCAS(P.err, kBatchOk, kBatchTimeout); return false; }
+        __nanosleep(100);
+    }
+    __threadfence();
+    const uint64_t req = (uint64_t)*(volatile long long*)&P.q_req[slot];
+    __threadfence();
+    atomicExch(&P.q_ack[slot], idx + 1ull);
+    const uint64_t gstep = req >> 28;
+    const int s = (int)((req >> 7) & ((1u << 21) - 1));
+    const int k = (int)(req & 127);
+    bool ok = true;
+    if ((long long)gstep == *(volatile long long*)P.cur_step) {
+        const int m = k + 1;
+        int ncl = 0;
+        const int rcode = tridiag_sqrt_e1<32>(m, P.alpha + (size_t)s * P.m_max, P.beta + (size_t)s * P.m_max, d, e,
+                                             rk, rc, rs, P.max_rot, z, &ncl);
+        // a request that became stale during the solve may have read the next
+        // step's coefficients: its result and status are dropped
+        if ((long long)gstep == *(volatile long long*)P.cur_step) {
+            if (rcode != 0) {
+                atomicCAS(P.err, kBatchOk, kBatchTridiag);
+                ok = false;
+            } else {
+                const size_t ri = res_index(P, s, gstep, k);
+                double* zr = P.zres + ri * P.m_max;
+                const double nw = __ldcg(P.normW + s);
+                for (int i = 0; i < m; ++i) zr[i] = z[32 * i] * nw;
+                __threadfence();
+                atomicExch(&P.zdone[ri], res_tag(gstep, k));
+            }
+        }
+    }
+    __threadfence();
+    atomicSub(&P.inflight[gstep & 1], 1);
+    atomicAdd(&P.q_ctr[2], 1ull);
+    return ok;
+}
+
+__device__ void solver_loop(const BatchParams& P) {
+    const int lane = threadIdx.x & 31;
+    const int wid = ((blockIdx.x - P.n_main) * blockDim.x + threadIdx.x) >> 5;
+    const size_t M32 = (size_t)P.m_max * 32;
+    double* d = P.sv_w + (size_t)wid * 3 * M32 + lane;
+    double* e = d + M32;
+    double* z = e + M32;
+    const size_t R32 = (size_t)P.max_rot * 32;
+    int* rk = P.trk + (size_t)wid * R32 + lane;
+    double* rc = P.trc + (size_t)wid * R32 + lane;
+    double* rs = P.trs + (size_t)wid * R32 + lane;
+    // idle wait: bounded by spin_limit cycles without any sign of progress of
+    // the main CTAs (barrier generation, item tickets, posted requests)
+    unsigned hb_bar = 0;
+    unsigned long long hb_ticket = 0, hb_tail = 0;
+    long long t0 = clock64();
+    while (true) {
+        unsigned long long first = 0;
+        int n = 0, quit = 0;
+        if (lane == 0) {
+            const unsigned long long h = vload(&P.q_ctr[0]);
+            const unsigned long long t = vload(&P.q_ctr[1]);
+            if (t > h) {
+                const int want = (int)min(32ull, t - h);
+                if (atomicCAS(&P.q_ctr[0], h, h + (unsigned long long)want) == h) { n = want; first = h; }
+            }
+            if (n == 0) {
+                if (*(volatile int*)P.main_done || *(volatile int*)P.err != kBatchOk) {
+                    quit = 1;
+                } else {
+                    const unsigned b = *(volatile unsigned*)(P.bar + 1);
+                    const unsigned long long tk = vload(P.ticket);
+                    if (b != hb_bar || tk != hb_ticket || t != hb_tail) {
+                        hb_bar = b; hb_ticket = tk; hb_tail = t;
+                        t0 = clock64();
+                    } else if (clock64() - t0 > P.spin_limit) {
+                        atomicCAS(P.err, kBatchOk, kBatchTimeout);
+                        quit = 1;
+                    }
+                }
+            }
+        }
+        n = __shfl_sync(0xffffffffu, n, 0);
+        quit = __shfl_sync(0xffffffffu, quit, 0);
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (quit) return;
+        if (n == 0) {
+            __nanosleep(256);
+            continue;
+        }
+        if (lane < n) serve_request(P, first + (unsigned long long)lane, d, e, z, rk, rc, rs);
+        __syncwarp();
+        if (lane == 0) t0 = clock64();
+    }
+}
+
+// Stopping rule of one system on the results that have arrived, in iteration
+// order (thread 0 of the system's CTA).  Returns true when the system stops.
+__device__ bool evaluate_results(const BatchParams& P, int s, uint64_t gstep, int upto) {
+    const int k0 = P.k0s[s];
+    while (P.next_check[s] <= upto) {
+        const int j = P.next_check[s];
+        if (j < k0) { P.next_check[s] = j + 1; continue; }
+        const size_t rj = res_index(P, s, gstep, j);
+        if (vload(&P.zdone[rj]) != res_tag(gstep, j)) return false;   // not there yet
+        __threadfence();
+        const double* zj = P.zres + rj * P.m_max;
+        const int m = j + 1;
+        bool stop = false;
+        if (j >= 1 && j >= k0 + 1) {
+            const double* zp = P.zres + res_index(P, s, gstep, j - 1) * P.m_max;
+            double dn = 0.0, zn = 0.0;
+            for (int i = 0; i < m; ++i) {
+                const double zi = __ldcg(zj + i);
+                const double dd = zi - (i < m - 1 ? __ldcg(zp + i) : 0.0);
+                dn += dd * dd;
+                zn += zi * zi;
+            }
+            const double rel = (zn > 0.0) ? sqrt(dn / zn) : 0.0;
+            P.rel[s] = rel;
+            if (rel < P.tol) stop = true;
+        }
+        if (!stop && P.state[s] >= 2 && j == P.last_k[s]) {
+            stop = true;
+            if (P.state[s] == 2) P.notconv[s] = 1;   // max_iter reached; a breakdown is converged
+        }
+        if (stop) {
+            double* zf = P.z + (size_t)s * P.m_max;
+            for (int i = 0; i < m; ++i) zf[i] = __ldcg(zj + i);
+            P.msys[s] = m;
+            P.itsum[s] += m;
+            P.kprev[s] = m;
+            P.state[s] = 0;
+            P.active[s] = 0;
+            return true;
+        }
+        P.next_check[s] = j + 1;
+    }
+    return false;
+}
+
+// Evaluate the results of system s until it stops or fewer than `gap`
+// iterations up to `upto` remain unevaluated (gap = 0: all of them).  The wait
+// is bounded by spin_limit cycles without a finished request.  Returns false
+// on a timeout or an error.
+__device__ bool wait_results(const BatchParams& P, int s, uint64_t gstep, int upto, int gap) {
+    long long t0 = clock64();
+    unsigned long long seen = vload(&P.q_ctr[2]);
+    while (P.state[s] != 0 && upto - P.next_check[s] >= gap) {
+        if (evaluate_results(P, s, gstep, upto)) break;
+        if (upto - P.next_check[s] < gap) break;
+        if (*(volatile int*)P.err != kBatchOk) return false;
+        const unsigned long long now = vload(&P.q_ctr[2]);
+        if (now != seen) { seen = now; t0 = clock64(); }
+        if (clock64() - t0 > P.spin_limit) { atomicCAS(P.err, kBatchOk, kBatchTimeout); return false; }
+        __nanosleep(200);
+    }
+    return true;
+}
+
 template <int NT, int NI>
 __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
+    if (blockIdx.x >= P.n_main) {
+        solver_loop(P);
+        return;
+    }
     __shared__ float4 sp[NT], sa[NT], sb[NT];
     __shared__ double sred[NT / 32];
     __shared__ double cvec[129];
-    __shared__ double tri_d[128], tri_e[128], tri_z[128];   // C5 scratch (thread 0)
     __shared__ unsigned long long s_ticket;
     const int tid = threadIdx.x;
-    const int G = gridDim.x;
+    const int G = P.n_main;
     const int per_item = NT * NI;
     unsigned long long base = 0;
 
@@ -346,6 +560,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                                  sred);
         });
         if (!grid_sync(P)) return;
+        if (blockIdx.x == 0 && tid == 0) atomicExch(P.main_done, 1);
         for (int c = blockIdx.x; c < P.n_chunks; c += G) {
             const int s = P.chunks[2 * c], e0 = P.chunks[2 * c + 1];
             const int64_t o = P.off[s];
@@ -368,8 +583,22 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
         int slot = 0;
         stamp(P, step, slot);
         // ---- A1: noise, forces, |W|^2 partials
-        if (blockIdx.x == 0)
+        if (blockIdx.x == 0) {
             for (int k = tid; k <= P.m_max; k += NT) P.nact[k] = 0;
+            if (tid == 0) {
+                atomicExch((unsigned long long*)P.cur_step, (unsigned long long)gstep);
+                // requests of two steps ago (same result-ring parity) all finished:
+                // no stale result can land in a slot of this step
+                long long t0 = clock64();
+                unsigned long long seen = vload(&P.q_ctr[2]);
+                while (*(volatile int*)&P.inflight[gstep & 1] != 0) {
+                    const unsigned long long now = vload(&P.q_ctr[2]);
+                    if (now != seen) { seen = now; t0 = clock64(); }
+                    if (clock64() - t0 > P.spin_limit) { atomicCAS(P.err, kBatchOk, kBatchTimeout); break; }
+                    __nanosleep(200);
+                }
+            }
+        }
         for (int c = blockIdx.x; c < P.n_chunks; c += G) {
             const int s = P.chunks[2 * c], e0 = P.chunks[2 * c + 1];
             const int64_t o = P.off[s];
@@ -404,7 +633,14 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                 double t = 0.0;
                 for (int w = 0; w < NT / 32; ++w) t += sred[w];
                 partA[(int64_t)c * M1] = t;
-                if (e0 == 0) { P.active[s] = 1; P.msys[s] = 0; }
+                if (e0 == 0) {
+                    P.active[s] = 1;
+                    P.state[s] = 1;
+                    P.msys[s] = 0;
+                    P.next_check[s] = 0;
+                    P.last_k[s] = -1;
+                    P.k0s[s] = (P.warm_start && P.kprev[s] > 0) ? max(0, P.kprev[s] - 3) : 0;
+                }
             }
             __syncthreads();
         }
@@ -419,7 +655,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
             const double nw = sqrt(cvec[0]);
             if (e0 == 0 && tid == 0) {
                 P.normW[s] = nw;
-                if (!(nw > 0.0)) P.active[s] = 0;   // W = 0: zero output, no iterations
+                if (!(nw > 0.0)) { P.active[s] = 0; P.state[s] = 0; }   // W = 0: zero output, no iterations
             }
             if (nw > 0.0) {
                 double* v0 = basis(P, s, 0);
@@ -539,68 +775,54 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                 if (!grid_sync(P)) return;
                 stamp(P, step, slot);
             }
-            // C5: beta, tridiagonal square root, stopping rule (one thread per system).
-            // Warm start (BD mode): with kprev the iteration count of the system's
-            // previous step, the tridiagonal solve begins at (0-based) iteration
-            // k0 = kprev - 3 and the relative-change test one iteration later, at
-            // the count kprev - 1 (one below the previous count, so that counts
-            // can also fall from step to step), since counts change little from
-            // one step to the next; breakdown and max_iter are tested at every
-            // iteration.
+            // C5: beta_k, solve request, stopping rule on the results that have
+            // arrived (one thread per system).  Warm start (BD mode): with kprev
+            // the iteration count of the system's previous step, solves begin at
+            // (0-based) iteration k0 = kprev - 3 and the relative-change test one
+            // iteration later, at the count kprev - 1 (one below the previous
+            // count, so that counts can also fall), since counts change little
+            // from one step to the next; breakdown and max_iter end the iteration
+            // at once.  A system keeps iterating while its results are pending;
+            // iterations past its stopping point are discarded.
             for (int s = blockIdx.x; s < P.S; s += G) {
-                if (tid != 0 || !P.active[s]) continue;
+                if (tid != 0 || P.state[s] != 1) continue;
                 double b2 = 0.0;
                 for (int c = P.chunk_range[2 * s]; c < P.chunk_range[2 * s + 1]; ++c) b2 += partA[(int64_t)c * M1];
                 const double b = sqrt(b2);
-                double* al = P.alpha + s * P.m_max;
-                double* be = P.beta + s * P.m_max;
-                be[k] = b;
+                const double* al = P.alpha + s * P.m_max;
+                P.beta[s * P.m_max + k] = b;
                 const int m = k + 1;
                 double amax = 0.0;
                 for (int i = 0; i < m; ++i) amax = fmax(amax, fabs(al[i]));
                 const bool breakdown = b <= P.brk_rel * amax;
                 const bool last = (m == P.m_max);
-                const int k0 = (P.warm_start && P.kprev[s] > 0) ? max(0, P.kprev[s] - 3) : 0;
-                double* zs = P.z + s * P.m_max;
-                double* zp = P.zprev + s * P.m_max;
-                bool stop = false;
-                if (k >= k0 || breakdown || last) {
-                    int ncl = 0;
-                    const int rc = tridiag_sqrt_e1(m, al, be, tri_d, tri_e, P.trk + (int64_t)s * P.max_rot,
-                                                   P.trc + (int64_t)s * P.max_rot, P.trs + (int64_t)s * P.max_rot,
-                                                   P.max_rot, tri_z, &ncl);
-                    if (rc != 0) atomicCAS(P.err, kBatchOk, kBatchTridiag);
-                    const double nw = P.normW[s];
-                    for (int i = 0; i < m; ++i) zs[i] = tri_z[i] * nw;
-                    if (k >= 1 && k >= k0 + 1) {
-                        double dn = 0.0, zn = 0.0;
-                        for (int i = 0; i < m; ++i) {
-                            const double dd = zs[i] - (i < m - 1 ? zp[i] : 0.0);
-                            dn += dd * dd;
-                            zn += zs[i] * zs[i];
-                        }
-                        const double rel = (zn > 0.0) ? sqrt(dn / zn) : 0.0;
-                        P.rel[s] = rel;
-                        if (rel < P.tol) stop = true;
-                    }
-                    if (breakdown) stop = true;
-                    if (!stop && last) { stop = true; P.notconv[s] = 1; }
-                    if (!stop)
-                        for (int i = 0; i < m; ++i) zp[i] = zs[i];
+                // at most R - 2 iterations ahead of the stopping test (result ring)
+                if (!wait_results(P, s, gstep, k - 1, P.R - 3)) break;
+                if (P.state[s] != 1) continue;
+                if (k >= P.k0s[s] || breakdown || last) {
+                    if (k < P.k0s[s]) P.k0s[s] = k;   // first solve forced by breakdown / max_iter
+                    if (!post_request(P, gstep, s, k)) break;
                 }
-                if (stop) {
+                if (breakdown || last) {
+                    P.state[s] = breakdown ? 3 : 2;
+                    P.last_k[s] = k;
                     P.active[s] = 0;
-                    P.msys[s] = m;
-                    P.itsum[s] += m;
-                    P.kprev[s] = m;
                 } else {
-                    atomicAdd(&P.nact[k + 1], 1);
+                    evaluate_results(P, s, gstep, k);
+                    if (P.state[s] == 1) atomicAdd(&P.nact[k + 1], 1);
                 }
             }
             if (!grid_sync(P)) return;
             stamp(P, step, slot);
             if (*(volatile int*)&P.nact[k + 1] == 0) break;
         }
+        // ---- wait for the last results of every system
+        for (int s = blockIdx.x; s < P.S; s += G) {
+            if (tid != 0 || P.state[s] == 0) continue;
+            if (!wait_results(P, s, gstep, P.last_k[s], 0)) break;
+        }
+        if (!grid_sync(P)) return;
+        stamp(P, step, slot);
         // ---- D: combine and update
         for (int c = blockIdx.x; c < P.n_chunks; c += G) {
             const int s = P.chunks[2 * c], e0 = P.chunks[2 * c + 1];
@@ -628,6 +850,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
         if (!grid_sync(P)) return;
         stamp(P, step, slot);
     }
+    if (blockIdx.x == 0 && tid == 0) atomicExch(P.main_done, 1);
 }
 
 __global__ void batch_pack_kernel(const float* __restrict__ pos, int64_t N, float4* __restrict__ pos4,

@@ -826,8 +826,11 @@ struct lm_batch {
     std::vector<int64_t> off_h;
     DBuf off, pos4, x64, Fbuf, u, w0, w1, V, alpha, beta, z, zprev, normW, rel, active, msys, itsum, notconv, nact;
     DBuf kprev, wsplit, usplit, woff;
-    DBuf items, item_range, chunks, chunk_range, part_item, part_chunk, td, trk, trc, trs, bar, ticket, err, flag;
+    DBuf items, item_range, chunks, chunk_range, part_item, part_chunk, trk, trc, trs, bar, ticket, err, flag;
     DBuf in_stage, out_stage, W_stage;
+    // asynchronous tridiagonal solves
+    DBuf sv_w, q_req, q_seq, q_ack, q_ctr, inflight, zres, zdone, state, next_check, last_k, k0s, main_done, cur_step;
+    int solver_lanes = 0, q_cap = 0, R = 32;
     int n_items = 0, n_chunks = 0, max_rot = 0;
     int threads = 128, ilp = 1;
     bool has_pos = false;
@@ -843,8 +846,9 @@ struct lm_batch {
         woff.release();
         DBuf* all[] = {&off, &pos4, &x64, &Fbuf, &u, &w0, &w1, &V, &alpha, &beta, &z, &zprev, &normW, &rel,
                        &active, &msys, &itsum, &notconv, &nact, &items, &item_range, &chunks, &chunk_range,
-                       &part_item, &part_chunk, &td, &trk, &trc, &trs, &bar, &ticket, &err, &flag, &in_stage,
-                       &out_stage, &W_stage};
+                       &part_item, &part_chunk, &trk, &trc, &trs, &bar, &ticket, &err, &flag, &in_stage,
+                       &out_stage, &W_stage, &sv_w, &q_req, &q_seq, &q_ack, &q_ctr, &inflight, &zres, &zdone,
+                       &state, &next_check, &last_k, &k0s, &main_done, &cur_step};
         for (DBuf* b : all) b->release();
         if (pinned) cudaFreeHost(pinned);
         if (graph_stream) cudaStreamDestroy(graph_stream);
@@ -889,6 +893,9 @@ int batch_grid(const lm_batch* b) {
     return std::max(1, occ) * b->sms;
 }
 
+// Solver CTAs at the end of the cooperative grid (whole CTAs of solver lanes).
+int batch_solver_ctas(const lm_batch* b) { return (b->solver_lanes + b->threads - 1) / b->threads; }
+
 lmk::BatchParams batch_params(lm_batch* b, int mode) {
     lmk::BatchParams p = {};
     p.S = b->S;
@@ -928,11 +935,27 @@ lmk::BatchParams batch_params(lm_batch* b, int mode) {
     p.chunk_range = b->chunk_range.as<int>();
     p.part_item = b->part_item.as<double>();
     p.part_chunk = b->part_chunk.as<double>();
-    p.td = b->td.as<double>();
+    p.n_main = batch_grid(b) - batch_solver_ctas(b);
+    p.sv_w = b->sv_w.as<double>();
     p.trk = b->trk.as<int>();
     p.trc = b->trc.as<double>();
     p.trs = b->trs.as<double>();
     p.max_rot = b->max_rot;
+    p.q_req = b->q_req.as<long long>();
+    p.q_seq = b->q_seq.as<unsigned long long>();
+    p.q_ack = b->q_ack.as<unsigned long long>();
+    p.q_ctr = b->q_ctr.as<unsigned long long>();
+    p.q_cap = b->q_cap;
+    p.inflight = b->inflight.as<int>();
+    p.zres = b->zres.as<double>();
+    p.zdone = b->zdone.as<unsigned long long>();
+    p.R = b->R;
+    p.state = b->state.as<int>();
+    p.next_check = b->next_check.as<int>();
+    p.last_k = b->last_k.as<int>();
+    p.k0s = b->k0s.as<int>();
+    p.main_done = b->main_done.as<int>();
+    p.cur_step = b->cur_step.as<long long>();
     p.bar = b->bar.as<unsigned>();
     p.ticket = b->ticket.as<unsigned long long>();
     p.err = b->err.as<int>();
@@ -960,8 +983,19 @@ lm_status batch_run(lm_batch* b, const lmk::BatchParams& p, bool use_graph) {
         st = b->graph_stream;
         LM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "batch graph capture");
     }
+    if (p.n_main < 1) return fail(LM_ERR_CUDA, "cooperative grid of %d CTAs leaves no main CTA", grid);
     cudaError_t e = cudaMemsetAsync(b->bar.p, 0, 2 * sizeof(unsigned), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->ticket.p, 0, sizeof(unsigned long long), st);
+    // request ring, counters and result tags start empty in every launch
+    const size_t S_ = (size_t)b->S;
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->q_seq.p, 0, (size_t)b->q_cap * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->q_ack.p, 0, (size_t)b->q_cap * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->q_ctr.p, 0, 4 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->inflight.p, 0, 2 * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->zdone.p, 0, S_ * 2 * b->R * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->state.p, 0, S_ * sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->main_done.p, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->cur_step.p, 0xff, sizeof(long long), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->err.p, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->itsum.p, 0, (size_t)b->S * sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->notconv.p, 0, (size_t)b->S * sizeof(int), st);
@@ -1057,6 +1091,13 @@ lm_status lm_batch_create(lm_batch** out, int64_t S, const int64_t* offsets, dou
         wtot += ((n + lmk::kBatchJPart - 1) / lmk::kBatchJPart) * 3 * n;
     }
     b->max_rot = (int)(4 * M * M + 64);
+    // solver lanes: about four requests in flight per system, at most 1024
+    // lanes and about 512 MB of solver scratch
+    const size_t lane_bytes = 3 * M * sizeof(double) + (size_t)b->max_rot * (sizeof(int) + 2 * sizeof(double));
+    size_t lanes = std::min<size_t>(1024, std::max<size_t>(128, (4 * S_ + 127) / 128 * 128));
+    while (lanes > 128 && lanes * lane_bytes > ((size_t)512 << 20)) lanes /= 2;
+    b->solver_lanes = (int)lanes;
+    b->q_cap = 16384;
     struct { DBuf* buf; size_t bytes; } allocs[] = {
         {&b->off, (S_ + 1) * sizeof(int64_t)}, {&b->pos4, (size_t)b->Ntot * sizeof(float4)},
         {&b->x64, (size_t)n3 * sizeof(double)}, {&b->Fbuf, (size_t)n3 * sizeof(float)},
@@ -1069,8 +1110,14 @@ lm_status lm_batch_create(lm_batch** out, int64_t S, const int64_t* offsets, dou
         {&b->nact, (M + 1) * sizeof(int)}, {&b->chunks, chunks.size() * sizeof(int)},
         {&b->chunk_range, crange.size() * sizeof(int)},
         {&b->part_chunk, 2 * (size_t)b->n_chunks * (M + 1) * sizeof(double)},
-        {&b->td, S_ * 2 * M * sizeof(double)}, {&b->trk, S_ * (size_t)b->max_rot * sizeof(int)},
-        {&b->trc, S_ * (size_t)b->max_rot * sizeof(double)}, {&b->trs, S_ * (size_t)b->max_rot * sizeof(double)},
+        {&b->sv_w, lanes * 3 * M * sizeof(double)}, {&b->trk, lanes * (size_t)b->max_rot * sizeof(int)},
+        {&b->trc, lanes * (size_t)b->max_rot * sizeof(double)}, {&b->trs, lanes * (size_t)b->max_rot * sizeof(double)},
+        {&b->q_req, (size_t)b->q_cap * sizeof(long long)}, {&b->q_seq, (size_t)b->q_cap * sizeof(unsigned long long)},
+        {&b->q_ack, (size_t)b->q_cap * sizeof(unsigned long long)}, {&b->q_ctr, 4 * sizeof(unsigned long long)},
+        {&b->inflight, 2 * sizeof(int)}, {&b->zres, S_ * 2 * (size_t)b->R * M * sizeof(double)},
+        {&b->zdone, S_ * 2 * (size_t)b->R * sizeof(unsigned long long)}, {&b->state, S_ * sizeof(int)},
+        {&b->next_check, S_ * sizeof(int)}, {&b->last_k, S_ * sizeof(int)}, {&b->k0s, S_ * sizeof(int)},
+        {&b->main_done, sizeof(int)}, {&b->cur_step, sizeof(long long)},
         {&b->bar, 4 * sizeof(unsigned)}, {&b->ticket, sizeof(unsigned long long)}, {&b->err, sizeof(int)},
         {&b->flag, sizeof(int)}, {&b->kprev, S_ * sizeof(int)}, {&b->woff, S_ * sizeof(int64_t)},
         {&b->wsplit, (size_t)wtot * sizeof(double)}, {&b->usplit, (size_t)wtot * sizeof(double)}};
@@ -1260,7 +1307,7 @@ lm_status lm_batch_profile_enable(lm_batch* b, int enable) {
     DeviceGuard g(b->device);
     b->prof_on = enable != 0;
     if (b->prof_on) {
-        b->timeline_len = 4 + 5 * b->m_max;
+        b->timeline_len = 5 + 5 * b->m_max;
         LM_CUDA(b->timeline.ensure((size_t)b->timeline_len * sizeof(unsigned long long)), "batch timeline");
         LM_CUDA(cudaMemset(b->timeline.p, 0, (size_t)b->timeline_len * sizeof(unsigned long long)), "timeline");
     }

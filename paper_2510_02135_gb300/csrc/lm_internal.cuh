@@ -199,11 +199,31 @@ struct BatchParams {
     const int* chunk_range;            // S x (first chunk, end chunk)
     double* part_item;                 // n_items partial dots
     double* part_chunk;                // 2 x n_chunks x (m_max + 1) partial dots
-    double* td;                        // S x 2 m_max tridiagonal scratch
-    int* trk;                          // S x max_rot rotation indices
-    double* trc;                       // S x max_rot rotation cosines
-    double* trs;                       // S x max_rot rotation sines
+    // Asynchronous tridiagonal solves.  CTAs [n_main, gridDim.x) are solver
+    // CTAs: each of their warps solves up to 32 requests side by side, one per
+    // lane, in lane-interleaved scratch (element i of lane l at [32 i + l]).
+    int n_main;                        // CTAs that run the phases and the grid barrier
+    double* sv_w;                      // per solver warp: d, e, z (3 x m_max x 32 doubles)
+    int* trk;                          // per solver warp: max_rot x 32 rotation indices
+    double* trc;                       // per solver warp: max_rot x 32 rotation cosines
+    double* trs;                       // per solver warp: max_rot x 32 rotation sines
     int max_rot;
+    long long* q_req;                  // request ring: (step << 28) | (system << 7) | k
+    unsigned long long* q_seq;         // ticket + 1 once the slot holds that ticket's request
+    unsigned long long* q_ack;         // ticket + 1 once a solver has read that ticket's request
+    unsigned long long* q_ctr;         // [0] next ticket to take, [1] next ticket to post, [2] requests done
+    int q_cap;
+    int* inflight;                     // [step parity]: requests posted and not yet done
+    double* zres;                      // S x 2 (step parity) x R x m_max results |W| f(T_k) e1
+    unsigned long long* zdone;         // S x 2 x R tags: step * 128 + k + 1
+    int R;
+    int* state;                        // S: 1 iterating, 2 / 3 waiting for the last result
+                                       //    (max_iter / breakdown), 0 done
+    int* next_check;                   // S: next iteration whose stopping test is due
+    int* last_k;                       // S: last iteration (states 2, 3)
+    int* k0s;                          // S: first iteration with a solve in this step
+    int* main_done;                    // set when no more requests can come
+    long long* cur_step;               // step the main CTAs are in (solvers drop older requests)
     unsigned* bar;                     // grid barrier: count, generation
     unsigned long long* ticket;        // dynamic work counter
     int* err;                          // BatchError

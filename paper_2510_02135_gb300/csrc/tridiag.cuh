@@ -36,10 +36,22 @@ __host__ __device__ inline double inv_sqrt(double t) {
     return 1.0 / sqrt(t);
 }
 
+// Load of a coefficient that another CTA may have written (on the device
+// through L2, bypassing the SM's L1).
+__host__ __device__ inline double load_coef(const double* p) {
+#ifdef __CUDA_ARCH__
+    return __ldcg(p);
+#else
+    return *p;
+#endif
+}
+
 // d[0..m-1] diagonal, e[0..m-2] off-diagonal (both destroyed; d receives the
 // eigenvalues).  Rotation t acts on (rk[t], rk[t]+1) with (rc[t], rs[t]).
 // Returns 0; -1 if 30 m QR steps did not converge; -2 if more than max_rot
-// rotations were needed.
+// rotations were needed.  Element i of every array is at [i * ST]: ST = 1 for
+// a plain array, ST = 32 for the lane-interleaved scratch of a warp whose 32
+// lanes solve 32 systems side by side (coalesced accesses).
 // Deflation test |e| <= eps (|d1| + |d2|).  On the device the comparison is
 // made in FP32 (a dependent FP64 compare costs ~130 cycles there); it only
 // decides when an off-diagonal entry is negligible, and the FP32 operands
@@ -52,27 +64,28 @@ __host__ __device__ inline bool negligible(double e, double d1, double d2) {
 #endif
 }
 
+template <int ST = 1>
 __host__ __device__ inline int tridiag_qr_rotations(int m, double* d, double* e, int* rk, double* rc, double* rs,
                                                     int max_rot, int* nrot) {
     int steps = 0, nr = 0;
     int hi = m - 1;
     while (hi > 0) {
-        if (negligible(e[hi - 1], d[hi - 1], d[hi])) {
-            e[hi - 1] = 0.0;
+        if (negligible(e[(hi - 1) * ST], d[(hi - 1) * ST], d[hi * ST])) {
+            e[(hi - 1) * ST] = 0.0;
             --hi;
             continue;
         }
         int lo = hi - 1;
-        while (lo > 0 && !negligible(e[lo - 1], d[lo - 1], d[lo])) --lo;
-        if (lo > 0) e[lo - 1] = 0.0;
+        while (lo > 0 && !negligible(e[(lo - 1) * ST], d[(lo - 1) * ST], d[lo * ST])) --lo;
+        if (lo > 0) e[(lo - 1) * ST] = 0.0;
         if (++steps > 30 * m) { *nrot = nr; return -1; }
         // Wilkinson shift: eigenvalue of the trailing 2x2 closer to d[hi]
-        const double delta = 0.5 * (d[hi - 1] - d[hi]);
-        const double bb = e[hi - 1];
+        const double delta = 0.5 * (d[(hi - 1) * ST] - d[hi * ST]);
+        const double bb = e[(hi - 1) * ST];
         const double den = delta + copysign(sqrt(delta * delta + bb * bb), delta);
-        const double mu = d[hi] - bb * bb / den;
-        double x = d[lo] - mu;
-        double z = e[lo];
+        const double mu = d[hi * ST] - bb * bb / den;
+        double x = d[lo * ST] - mu;
+        double z = e[lo * ST];
         for (int k = lo; k < hi; ++k) {
             // rotation J = [[c, -s], [s, c]] on (k, k+1) with J^T [x; z] = [r; 0]
             // entries of T are of the order of the mobility: no over/underflow in x^2 + z^2
@@ -84,18 +97,18 @@ __host__ __device__ inline int tridiag_qr_rotations(int m, double* d, double* e,
                 s = z * inv;
                 r = t2 * inv;
             }
-            if (k > lo) e[k - 1] = r;
-            const double ak = d[k], ak1 = d[k + 1], bk = e[k];
-            d[k] = c * c * ak + 2.0 * c * s * bk + s * s * ak1;
-            d[k + 1] = s * s * ak - 2.0 * c * s * bk + c * c * ak1;
-            e[k] = c * s * (ak1 - ak) + (c * c - s * s) * bk;
+            if (k > lo) e[(k - 1) * ST] = r;
+            const double ak = d[k * ST], ak1 = d[(k + 1) * ST], bk = e[k * ST];
+            d[k * ST] = c * c * ak + 2.0 * c * s * bk + s * s * ak1;
+            d[(k + 1) * ST] = s * s * ak - 2.0 * c * s * bk + c * c * ak1;
+            e[k * ST] = c * s * (ak1 - ak) + (c * c - s * s) * bk;
             if (k < hi - 1) {
-                x = e[k];
-                z = s * e[k + 1];
-                e[k + 1] = c * e[k + 1];
+                x = e[k * ST];
+                z = s * e[(k + 1) * ST];
+                e[(k + 1) * ST] = c * e[(k + 1) * ST];
             }
             if (nr >= max_rot) { *nrot = nr; return -2; }
-            rk[nr] = k; rc[nr] = c; rs[nr] = s;
+            rk[nr * ST] = k; rc[nr * ST] = c; rs[nr * ST] = s;
             ++nr;
         }
     }
@@ -106,36 +119,38 @@ __host__ __device__ inline int tridiag_qr_rotations(int m, double* d, double* e,
 // out = f(T) e1, f = sqrt, eigenvalues below zero (round-off) clamped to 0
 // and counted in *clamped.  d, e: m doubles of scratch each; rk, rc, rs:
 // max_rot entries of scratch.
+// alpha, beta: plain arrays (stride 1); d, e, rk, rc, rs, out: stride ST.
+template <int ST = 1>
 __host__ __device__ inline int tridiag_sqrt_e1(int m, const double* alpha, const double* beta, double* d, double* e,
                                                int* rk, double* rc, double* rs, int max_rot, double* out,
                                                int* clamped) {
-    for (int i = 0; i < m; ++i) d[i] = alpha[i];
-    for (int i = 0; i + 1 < m; ++i) e[i] = beta[i];
+    for (int i = 0; i < m; ++i) d[i * ST] = load_coef(alpha + i);
+    for (int i = 0; i + 1 < m; ++i) e[i * ST] = load_coef(beta + i);
     int nr = 0;
-    const int rc_ = tridiag_qr_rotations(m, d, e, rk, rc, rs, max_rot, &nr);
+    const int rc_ = tridiag_qr_rotations<ST>(m, d, e, rk, rc, rs, max_rot, &nr);
     if (rc_ != 0) return rc_;
     // r = Q^T e1
-    for (int i = 0; i < m; ++i) out[i] = (i == 0) ? 1.0 : 0.0;
+    for (int i = 0; i < m; ++i) out[i * ST] = (i == 0) ? 1.0 : 0.0;
     for (int t = 0; t < nr; ++t) {
-        const int k = rk[t];
-        const double c = rc[t], s = rs[t];
-        const double a = out[k], b = out[k + 1];
-        out[k] = c * a + s * b;
-        out[k + 1] = -s * a + c * b;
+        const int k = rk[t * ST];
+        const double c = rc[t * ST], s = rs[t * ST];
+        const double a = out[k * ST], b = out[(k + 1) * ST];
+        out[k * ST] = c * a + s * b;
+        out[(k + 1) * ST] = -s * a + c * b;
     }
     int nclamp = 0;
     for (int i = 0; i < m; ++i) {
-        double lam = d[i];
+        double lam = d[i * ST];
         if (lam < 0.0) { lam = 0.0; ++nclamp; }
-        out[i] *= sqrt(lam);
+        out[i * ST] *= sqrt(lam);
     }
     // z = Q v
     for (int t = nr - 1; t >= 0; --t) {
-        const int k = rk[t];
-        const double c = rc[t], s = rs[t];
-        const double a = out[k], b = out[k + 1];
-        out[k] = c * a - s * b;
-        out[k + 1] = s * a + c * b;
+        const int k = rk[t * ST];
+        const double c = rc[t * ST], s = rs[t * ST];
+        const double a = out[k * ST], b = out[(k + 1) * ST];
+        out[k * ST] = c * a - s * b;
+        out[(k + 1) * ST] = s * a + c * b;
     }
     if (clamped) *clamped = nclamp;
     return 0;

@@ -419,7 +419,7 @@ def lm_batch_profile_enable(b: Batch, enable: bool = True) -> None:
 
 def lm_batch_profile_read(b: Batch) -> np.ndarray:
     """Phase end times (ns) of the first step of the last run (see include/lm.h)."""
-    out = np.zeros(4 + 5 * b.max_iter, dtype=np.uint64)
+    out = np.zeros(5 + 5 * b.max_iter, dtype=np.uint64)
     c = ctypes.c_int(0)
     _check(lib().lm_batch_profile_read(b.handle, out.ctypes.data, out.size, ctypes.byref(c)))
     return out[: c.value]
