@@ -290,7 +290,7 @@ lm_status lm_batch_autotune(lm_batch *batch, int *threads_out, int *ilp_out);
 /*
  * Phase timeline of a batched run (profiling).  While enabled, the
  * persistent kernel records the device global timer (ns) at the start of the
- * first step and after every phase of that step: [start, A1, A2, then per
+ * last step of the run and after every phase of that step: [start, A1, A2, then per
  * Lanczos iteration B, C2, C3, C4, C5, then the wait for the last
  * tridiagonal results, then D].  lm_batch_profile_read copies
  * up to n stamps of the last run into out and the number recorded into
@@ -298,6 +298,27 @@ lm_status lm_batch_autotune(lm_batch *batch, int *threads_out, int *ilp_out);
  */
 lm_status lm_batch_profile_enable(lm_batch *batch, int enable);
 lm_status lm_batch_profile_read(lm_batch *batch, uint64_t *out, int n, int *count);
+
+/*
+ * lm_tridiag_sqrt_e1_device -- the device form of the same tridiagonal step
+ * (Sec. 3.3) that the batched kernel runs, one GPU thread per system, exposed
+ * for testing and timing: for each of `count` systems c, out[c m .. c m + m)
+ * = sqrt(T_c) e1 with T_c = tridiag(beta_c, alpha_c, beta_c), alpha_c =
+ * alpha[c m ..] (m entries), beta_c = beta[c m ..] (m - 1 entries used).
+ * alpha, beta, out: device memory, count x m doubles each; 1 <= m <= 128.
+ * Allocates its scratch, runs on cuda_stream and waits for it.  Returns
+ * LM_ERR_CUDA if a system's QR iteration failed.
+ */
+lm_status lm_tridiag_sqrt_e1_device(int count, int m, const double *alpha, const double *beta, double *out,
+                                    void *cuda_stream);
+
+/*
+ * Tridiagonal solve requests of the last batched run (profiling): *posted
+ * receives the number of f(T_k) e1 solves the iterating CTAs requested,
+ * *solved the number the solver CTAs finished (stale requests of an earlier
+ * step included; they are dropped unsolved).
+ */
+lm_status lm_batch_solve_counts(lm_batch *batch, int64_t *posted, int64_t *solved);
 
 /*
  * lm_batch_timeout_selftest -- check of the bounded device-side waits (no

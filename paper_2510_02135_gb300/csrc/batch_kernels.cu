@@ -34,6 +34,7 @@
 
 #include "lm_internal.cuh"
 #include "tridiag.cuh"
+#include "tridiag_dev.cuh"
 
 namespace lmk {
 namespace {
@@ -50,9 +51,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// Phase end times of the first step (CTA 0, thread 0), for profiling.
+// Phase end times of the last step of the run (CTA 0, thread 0), for profiling.
 __device__ __forceinline__ void stamp(const BatchParams& P, int step, int& slot) {
-    if (P.timeline != nullptr && step == 0 && blockIdx.x == 0 && threadIdx.x == 0 && slot < P.timeline_len)
+    const int last = (P.mode == kBatchBD) ? P.nsteps - 1 : 0;
+    if (P.timeline != nullptr && step == last && blockIdx.x == 0 && threadIdx.x == 0 && slot < P.timeline_len)
         P.timeline[slot] = global_ns();
     ++slot;
 }
@@ -270,23 +272,60 @@ __device__ void pair_item(const BatchParams& P, int s, int i0, int jb, int je, c
 template <int NT>
 __device__ void chunk_dots(const BatchParams& P, int s, int e0, int e1, const double* w, int nrows,
                            double* part_out) {
+    // FP64 add latency is long (tens of cycles): each warp reduces four rows
+    // at once, so that four dependent chains overlap
+    constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int j = wid; j < nrows; j += NT / 32) {
-        const double* v = basis(P, s, j);
-        double acc = 0.0;
-        for (int e = e0 + lane; e < e1; e += 32) acc = fma(v[e], w[e], acc);
-        acc = warp_sum_d(acc);
-        if (lane == 0) part_out[j] = acc;
+    const int64_t ns = 3 * (P.off[s + 1] - P.off[s]);
+    for (int j0 = wid * 4; j0 < nrows; j0 += NW * 4) {
+        const int nr = min(4, nrows - j0);
+        const double* v = basis(P, s, 0) + j0 * ns;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        for (int e = e0 + lane; e < e1; e += 32) {
+            const double we = w[e];
+            a0 = fma(v[e], we, a0);
+            if (nr > 1) a1 = fma(v[ns + e], we, a1);
+            if (nr > 2) a2 = fma(v[2 * ns + e], we, a2);
+            if (nr > 3) a3 = fma(v[3 * ns + e], we, a3);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+            a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+        }
+        if (lane < nr) part_out[j0 + lane] = lane == 0 ? a0 : lane == 1 ? a1 : lane == 2 ? a2 : a3;
     }
 }
 
+// Deterministic warp sum of base[c * stride] for c in [cb, ce): lane-strided
+// partial sums, then a butterfly (every lane returns the same value).
+__device__ __forceinline__ double warp_range_sum(const double* base, int64_t stride, int cb, int ce) {
+    const int lane = threadIdx.x & 31;
+    double t = 0.0;
+    for (int c = cb + lane; c < ce; c += 32) t += base[(int64_t)c * stride];
+    return warp_sum_d(t);
+}
+
+// cvec[j] = sum over the chunks of system s of part[c][j], j < nrows.  With
+// few rows, G = NT / nrows threads (a power of two, at most 8) share a row
+// and combine their partial sums by a butterfly; the order depends only on
+// nrows, so every chunk of the system obtains the same coefficients.
 template <int NT>
 __device__ void chunk_sum_coeffs(const BatchParams& P, int s, const double* part, int nrows, double* cvec) {
     const int cb = P.chunk_range[2 * s], ce = P.chunk_range[2 * s + 1];
-    for (int j = threadIdx.x; j < nrows; j += NT) {
+    const int64_t M1 = P.m_max + 1;
+    int G = 1;
+    while (G < 8 && 2 * G * nrows <= NT) G *= 2;
+    const int rows_per_pass = NT / G;
+    for (int j0 = 0; j0 < nrows; j0 += rows_per_pass) {
+        const int j = j0 + threadIdx.x / G, q = threadIdx.x % G;
         double t = 0.0;
-        for (int c = cb; c < ce; ++c) t += part[(int64_t)c * (P.m_max + 1) + j];
-        cvec[j] = t;
+        if (j < nrows)
+            for (int c = cb + q; c < ce; c += G) t += part[(int64_t)c * M1 + j];
+        for (int o = 1; o < G; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (j < nrows && q == 0) cvec[j] = t;
     }
     __syncthreads();
 }
@@ -301,6 +340,9 @@ __device__ void chunk_sum_coeffs(const BatchParams& P, int s, const double* part
 // arrive.  Requests of an earlier step are dropped.  Every wait is bounded by
 // spin_limit clock cycles without progress of the other side.
 // ---------------------------------------------------------------------------
+// Requests in flight per system beyond the next pending stopping test.
+constexpr int kSpecDepth = 8;
+
 __device__ __forceinline__ unsigned long long res_tag(uint64_t gstep, int k) {
     return (unsigned long long)gstep * 128ull + (unsigned long long)k + 1ull;
 }
@@ -339,8 +381,8 @@ __device__ bool post_request(const BatchParams& P, uint64_t gstep, int s, int k)
 }
 
 // Solve the request of ticket idx (one lane).  Returns false on an error.
-__device__ bool serve_request(const BatchParams& P, unsigned long long idx, double* d, double* e, double* z, int* rk,
-                              double* rc, double* rs) {
+__device__ bool serve_request(const BatchParams& P, unsigned long long idx, df* d, df* e, df* r, double* z, int* rk,
+                              df* rc, df* rs) {
     const int slot = (int)(idx % (unsigned long long)P.q_cap);
     const long long t0 = clock64();
     while (vload(&P.q_seq[slot]) != idx + 1ull) {   // the poster is between its two writes
@@ -357,9 +399,8 @@ __device__ bool serve_request(const BatchParams& P, unsigned long long idx, doub
     bool ok = true;
     if ((long long)gstep == *(volatile long long*)P.cur_step) {
         const int m = k + 1;
-        int ncl = 0;
-        const int rcode = tridiag_sqrt_e1<32>(m, P.alpha + (size_t)s * P.m_max, P.beta + (size_t)s * P.m_max, d, e,
-                                             rk, rc, rs, P.max_rot, z, &ncl);
+        const int rcode = tridiag_sqrt_e1_df<1>(m, P.alpha + (size_t)s * P.m_max, P.beta + (size_t)s * P.m_max, d, e,
+                                               r, rk, rc, rs, P.max_rot, z);
         // a request that became stale during the solve may have read the next
         // step's coefficients: its result and status are dropped
         if ((long long)gstep == *(volatile long long*)P.cur_step) {
@@ -370,7 +411,7 @@ __device__ bool serve_request(const BatchParams& P, unsigned long long idx, doub
                 const size_t ri = res_index(P, s, gstep, k);
                 double* zr = P.zres + ri * P.m_max;
                 const double nw = __ldcg(P.normW + s);
-                for (int i = 0; i < m; ++i) zr[i] = z[32 * i] * nw;
+                for (int i = 0; i < m; ++i) zr[i] = z[i] * nw;
                 __threadfence();
                 atomicExch(&P.zdone[ri], res_tag(gstep, k));
             }
@@ -383,31 +424,36 @@ __device__ bool serve_request(const BatchParams& P, unsigned long long idx, doub
 }
 
 __device__ void solver_loop(const BatchParams& P) {
+    // lanes [0, kSolverWidth) of every solver warp each serve one request;
+    // each has contiguous scratch (the QR's working set stays in L1)
     const int lane = threadIdx.x & 31;
     const int wid = ((blockIdx.x - P.n_main) * blockDim.x + threadIdx.x) >> 5;
-    const size_t M32 = (size_t)P.m_max * 32;
-    double* d = P.sv_w + (size_t)wid * 3 * M32 + lane;
-    double* e = d + M32;
-    double* z = e + M32;
-    const size_t R32 = (size_t)P.max_rot * 32;
-    int* rk = P.trk + (size_t)wid * R32 + lane;
-    double* rc = P.trc + (size_t)wid * R32 + lane;
-    double* rs = P.trs + (size_t)wid * R32 + lane;
+    const size_t slot = (size_t)wid * kSolverWidth + (size_t)min(lane, kSolverWidth - 1);
+    df* d = reinterpret_cast<df*>(P.sv_w + slot * 4 * P.m_max);
+    df* e = d + P.m_max;
+    df* r = e + P.m_max;
+    double* z = P.sv_w + slot * 4 * P.m_max + 3 * P.m_max;
+    int* rk = P.trk + slot * P.max_rot;
+    df* rc = reinterpret_cast<df*>(P.trc + slot * P.max_rot);
+    df* rs = reinterpret_cast<df*>(P.trs + slot * P.max_rot);
     // idle wait: bounded by spin_limit cycles without any sign of progress of
     // the main CTAs (barrier generation, item tickets, posted requests)
     unsigned hb_bar = 0;
-    unsigned long long hb_ticket = 0, hb_tail = 0;
+    unsigned long long hb_ticket = 0, hb_tail = 0, last_tail = ~0ull;
     long long t0 = clock64();
     while (true) {
         unsigned long long first = 0;
         int n = 0, quit = 0;
         if (lane == 0) {
+            // take kSolverWidth requests, or fewer once posting has paused for a
+            // poll interval
             const unsigned long long h = vload(&P.q_ctr[0]);
             const unsigned long long t = vload(&P.q_ctr[1]);
-            if (t > h) {
-                const int want = (int)min(32ull, t - h);
+            if (t >= h + (unsigned long long)kSolverWidth || (t > h && t == last_tail)) {
+                const int want = (int)min((unsigned long long)kSolverWidth, t - h);
                 if (atomicCAS(&P.q_ctr[0], h, h + (unsigned long long)want) == h) { n = want; first = h; }
             }
+            last_tail = t;
             if (n == 0) {
                 if (*(volatile int*)P.main_done || *(volatile int*)P.err != kBatchOk) {
                     quit = 1;
@@ -432,7 +478,7 @@ __device__ void solver_loop(const BatchParams& P) {
             __nanosleep(256);
             continue;
         }
-        if (lane < n) serve_request(P, first + (unsigned long long)lane, d, e, z, rk, rc, rs);
+        if (lane < n) serve_request(P, first + (unsigned long long)lane, d, e, r, z, rk, rc, rs);
         __syncwarp();
         if (lane == 0) t0 = clock64();
     }
@@ -483,16 +529,28 @@ __device__ bool evaluate_results(const BatchParams& P, int s, uint64_t gstep, in
     return false;
 }
 
-// Evaluate the results of system s until it stops or fewer than `gap`
-// iterations up to `upto` remain unevaluated (gap = 0: all of them).  The wait
-// is bounded by spin_limit cycles without a finished request.  Returns false
-// on a timeout or an error.
-__device__ bool wait_results(const BatchParams& P, int s, uint64_t gstep, int upto, int gap) {
+// Post the due requests of system s: iterations after the last one posted,
+// from k0 on, up to kmax and at most kSpecDepth beyond the next iteration
+// whose stopping test is pending (bounded speculation: a system that keeps
+// iterating while its results are pending does not flood the solvers).
+__device__ bool post_due(const BatchParams& P, int s, uint64_t gstep, int kmax) {
+    const int hi = min(kmax, P.next_check[s] + kSpecDepth);
+    for (int j = max(P.posted[s] + 1, P.k0s[s]); j <= hi; ++j) {
+        if (!post_request(P, gstep, s, j)) return false;
+        P.posted[s] = j;
+    }
+    return true;
+}
+
+// Evaluate and post for system s (states 2, 3: iteration ended) until it
+// stops.  The wait is bounded by spin_limit cycles without a finished
+// request.  Returns false on a timeout or an error.
+__device__ bool drain_system(const BatchParams& P, int s, uint64_t gstep) {
     long long t0 = clock64();
     unsigned long long seen = vload(&P.q_ctr[2]);
-    while (P.state[s] != 0 && upto - P.next_check[s] >= gap) {
-        if (evaluate_results(P, s, gstep, upto)) break;
-        if (upto - P.next_check[s] < gap) break;
+    while (P.state[s] != 0) {
+        if (evaluate_results(P, s, gstep, P.last_k[s])) break;
+        if (!post_due(P, s, gstep, P.last_k[s])) return false;
         if (*(volatile int*)P.err != kBatchOk) return false;
         const unsigned long long now = vload(&P.q_ctr[2]);
         if (now != seen) { seen = now; t0 = clock64(); }
@@ -639,6 +697,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                     P.msys[s] = 0;
                     P.next_check[s] = 0;
                     P.last_k[s] = -1;
+                    P.posted[s] = -1;
                     P.k0s[s] = (P.warm_start && P.kprev[s] > 0) ? max(0, P.kprev[s] - 3) : 0;
                 }
             }
@@ -700,8 +759,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                 const int64_t o = P.off[s];
                 const int ns = 3 * (int)(P.off[s + 1] - o);
                 const int e1 = min(e0 + kBatchChunk, ns);
-                double alpha = 0.0;
-                for (int t = P.item_range[2 * s]; t < P.item_range[2 * s + 1]; ++t) alpha += P.part_item[t];
+                const double alpha = warp_range_sum(P.part_item, 1, P.item_range[2 * s], P.item_range[2 * s + 1]);
                 if (e0 == 0 && tid == 0) P.alpha[s * P.m_max + k] = alpha;
                 const double bprev = (k > 0) ? P.beta[s * P.m_max + k - 1] : 0.0;
                 const double* vk = basis(P, s, k);
@@ -742,11 +800,9 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                     const int e1 = min(e0 + kBatchChunk, ns);
                     bool apply = true;
                     if (pass == 1) {
-                        double h0 = 0.0, h1 = 0.0;
-                        for (int cc = P.chunk_range[2 * s]; cc < P.chunk_range[2 * s + 1]; ++cc) {
-                            h0 += partA[(int64_t)cc * M1 + P.m_max];
-                            h1 += partB[(int64_t)cc * M1 + P.m_max];
-                        }
+                        const int cb = P.chunk_range[2 * s], ce = P.chunk_range[2 * s + 1];
+                        const double h0 = warp_range_sum(partA + P.m_max, M1, cb, ce);
+                        const double h1 = warp_range_sum(partB + P.m_max, M1, cb, ce);
                         apply = h1 < 0.5 * h0;   // squared norms: |w1| < |w0| / sqrt(2)
                     }
                     double* w = wcur + 3 * o;
@@ -796,21 +852,15 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                 for (int i = 0; i < m; ++i) amax = fmax(amax, fabs(al[i]));
                 const bool breakdown = b <= P.brk_rel * amax;
                 const bool last = (m == P.m_max);
-                // at most R - 2 iterations ahead of the stopping test (result ring)
-                if (!wait_results(P, s, gstep, k - 1, P.R - 3)) break;
-                if (P.state[s] != 1) continue;
-                if (k >= P.k0s[s] || breakdown || last) {
-                    if (k < P.k0s[s]) P.k0s[s] = k;   // first solve forced by breakdown / max_iter
-                    if (!post_request(P, gstep, s, k)) break;
-                }
                 if (breakdown || last) {
+                    if (k < P.k0s[s]) P.k0s[s] = k;   // the last iteration is always solved
                     P.state[s] = breakdown ? 3 : 2;
                     P.last_k[s] = k;
                     P.active[s] = 0;
-                } else {
-                    evaluate_results(P, s, gstep, k);
-                    if (P.state[s] == 1) atomicAdd(&P.nact[k + 1], 1);
                 }
+                if (evaluate_results(P, s, gstep, k)) continue;
+                if (!post_due(P, s, gstep, k)) break;
+                if (P.state[s] == 1) atomicAdd(&P.nact[k + 1], 1);
             }
             if (!grid_sync(P)) return;
             stamp(P, step, slot);
@@ -819,7 +869,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
         // ---- wait for the last results of every system
         for (int s = blockIdx.x; s < P.S; s += G) {
             if (tid != 0 || P.state[s] == 0) continue;
-            if (!wait_results(P, s, gstep, P.last_k[s], 0)) break;
+            if (!drain_system(P, s, gstep)) break;
         }
         if (!grid_sync(P)) return;
         stamp(P, step, slot);
@@ -888,6 +938,19 @@ __global__ void timeout_probe_kernel(BatchParams P) {
     __syncthreads();
 }
 
+// One thread per system: out = sqrt(T) e1 with the device tridiagonal step.
+__global__ void tridiag_dev_kernel(int count, int m, const double* alpha, const double* beta, double* scratch,
+                                   int* rk, double* rc, double* rs, int max_rot, double* out, int* status) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    df* d = reinterpret_cast<df*>(scratch + (size_t)t * 3 * m);
+    const int rcode = tridiag_sqrt_e1_df<1>(m, alpha + (size_t)t * m, beta + (size_t)t * m, d, d + m, d + 2 * m,
+                                            rk + (size_t)t * max_rot, reinterpret_cast<df*>(rc + (size_t)t * max_rot),
+                                            reinterpret_cast<df*>(rs + (size_t)t * max_rot), max_rot,
+                                            out + (size_t)t * m);
+    if (rcode != 0) atomicCAS(status, 0, rcode);
+}
+
 template <int NT, int NI>
 cudaError_t launch_nt(const BatchParams& p, int grid, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
@@ -942,6 +1005,14 @@ cudaError_t launch_batch_pack(const float* pos, int64_t N, float4* pos4, double*
 
 cudaError_t launch_batch_unpack(const double* x64, int64_t N, float* out, cudaStream_t s) {
     batch_unpack_kernel<<<(unsigned)((3 * N + 255) / 256), 256, 0, s>>>(x64, 3 * N, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tridiag_dev(int count, int m, const double* alpha, const double* beta, double* scratch, int* rk,
+                               double* rc, double* rs, int max_rot, double* out, int* status, cudaStream_t s) {
+    tridiag_dev_kernel<<<(count + 127) / 128, 128, 0, s>>>(count, m, alpha, beta, scratch, rk, rc, rs, max_rot, out,
+                                                           status);
     count_launches(1);
     return cudaGetLastError();
 }

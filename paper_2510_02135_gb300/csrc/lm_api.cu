@@ -829,7 +829,8 @@ struct lm_batch {
     DBuf items, item_range, chunks, chunk_range, part_item, part_chunk, trk, trc, trs, bar, ticket, err, flag;
     DBuf in_stage, out_stage, W_stage;
     // asynchronous tridiagonal solves
-    DBuf sv_w, q_req, q_seq, q_ack, q_ctr, inflight, zres, zdone, state, next_check, last_k, k0s, main_done, cur_step;
+    DBuf sv_w, q_req, q_seq, q_ack, q_ctr, inflight, zres, zdone, state, next_check, last_k, k0s, posted, main_done,
+        cur_step;
     int solver_lanes = 0, q_cap = 0, R = 32;
     int n_items = 0, n_chunks = 0, max_rot = 0;
     int threads = 128, ilp = 1;
@@ -848,7 +849,7 @@ struct lm_batch {
                        &active, &msys, &itsum, &notconv, &nact, &items, &item_range, &chunks, &chunk_range,
                        &part_item, &part_chunk, &trk, &trc, &trs, &bar, &ticket, &err, &flag, &in_stage,
                        &out_stage, &W_stage, &sv_w, &q_req, &q_seq, &q_ack, &q_ctr, &inflight, &zres, &zdone,
-                       &state, &next_check, &last_k, &k0s, &main_done, &cur_step};
+                       &state, &next_check, &last_k, &k0s, &posted, &main_done, &cur_step};
         for (DBuf* b : all) b->release();
         if (pinned) cudaFreeHost(pinned);
         if (graph_stream) cudaStreamDestroy(graph_stream);
@@ -893,8 +894,8 @@ int batch_grid(const lm_batch* b) {
     return std::max(1, occ) * b->sms;
 }
 
-// Solver CTAs at the end of the cooperative grid (whole CTAs of solver lanes).
-int batch_solver_ctas(const lm_batch* b) { return (b->solver_lanes + b->threads - 1) / b->threads; }
+// Solver CTAs at the end of the cooperative grid: kSolverWarps warps.
+int batch_solver_ctas(const lm_batch* b) { return (lmk::kSolverWarps * 32 + b->threads - 1) / b->threads; }
 
 lmk::BatchParams batch_params(lm_batch* b, int mode) {
     lmk::BatchParams p = {};
@@ -954,6 +955,7 @@ lmk::BatchParams batch_params(lm_batch* b, int mode) {
     p.next_check = b->next_check.as<int>();
     p.last_k = b->last_k.as<int>();
     p.k0s = b->k0s.as<int>();
+    p.posted = b->posted.as<int>();
     p.main_done = b->main_done.as<int>();
     p.cur_step = b->cur_step.as<long long>();
     p.bar = b->bar.as<unsigned>();
@@ -1091,11 +1093,9 @@ lm_status lm_batch_create(lm_batch** out, int64_t S, const int64_t* offsets, dou
         wtot += ((n + lmk::kBatchJPart - 1) / lmk::kBatchJPart) * 3 * n;
     }
     b->max_rot = (int)(4 * M * M + 64);
-    // solver lanes: about four requests in flight per system, at most 1024
-    // lanes and about 512 MB of solver scratch
-    const size_t lane_bytes = 3 * M * sizeof(double) + (size_t)b->max_rot * (sizeof(int) + 2 * sizeof(double));
-    size_t lanes = std::min<size_t>(1024, std::max<size_t>(128, (4 * S_ + 127) / 128 * 128));
-    while (lanes > 128 && lanes * lane_bytes > ((size_t)512 << 20)) lanes /= 2;
+    // solver slots: kSolverWidth per solver warp (CTAs of 64 or 128 threads
+    // hold whole warps: kSolverWarps is a multiple of 4)
+    const size_t lanes = (size_t)lmk::kSolverWarps * lmk::kSolverWidth;
     b->solver_lanes = (int)lanes;
     b->q_cap = 16384;
     struct { DBuf* buf; size_t bytes; } allocs[] = {
@@ -1110,13 +1110,13 @@ lm_status lm_batch_create(lm_batch** out, int64_t S, const int64_t* offsets, dou
         {&b->nact, (M + 1) * sizeof(int)}, {&b->chunks, chunks.size() * sizeof(int)},
         {&b->chunk_range, crange.size() * sizeof(int)},
         {&b->part_chunk, 2 * (size_t)b->n_chunks * (M + 1) * sizeof(double)},
-        {&b->sv_w, lanes * 3 * M * sizeof(double)}, {&b->trk, lanes * (size_t)b->max_rot * sizeof(int)},
+        {&b->sv_w, lanes * 4 * M * sizeof(double)}, {&b->trk, lanes * (size_t)b->max_rot * sizeof(int)},
         {&b->trc, lanes * (size_t)b->max_rot * sizeof(double)}, {&b->trs, lanes * (size_t)b->max_rot * sizeof(double)},
         {&b->q_req, (size_t)b->q_cap * sizeof(long long)}, {&b->q_seq, (size_t)b->q_cap * sizeof(unsigned long long)},
         {&b->q_ack, (size_t)b->q_cap * sizeof(unsigned long long)}, {&b->q_ctr, 4 * sizeof(unsigned long long)},
         {&b->inflight, 2 * sizeof(int)}, {&b->zres, S_ * 2 * (size_t)b->R * M * sizeof(double)},
         {&b->zdone, S_ * 2 * (size_t)b->R * sizeof(unsigned long long)}, {&b->state, S_ * sizeof(int)},
-        {&b->next_check, S_ * sizeof(int)}, {&b->last_k, S_ * sizeof(int)}, {&b->k0s, S_ * sizeof(int)},
+        {&b->next_check, S_ * sizeof(int)}, {&b->last_k, S_ * sizeof(int)}, {&b->k0s, S_ * sizeof(int)}, {&b->posted, S_ * sizeof(int)},
         {&b->main_done, sizeof(int)}, {&b->cur_step, sizeof(long long)},
         {&b->bar, 4 * sizeof(unsigned)}, {&b->ticket, sizeof(unsigned long long)}, {&b->err, sizeof(int)},
         {&b->flag, sizeof(int)}, {&b->kprev, S_ * sizeof(int)}, {&b->woff, S_ * sizeof(int64_t)},
@@ -1326,6 +1326,46 @@ lm_status lm_batch_profile_read(lm_batch* b, uint64_t* out, int n, int* count) {
     while (c < (int)t.size() && t[c] != 0) ++c;
     for (int i = 0; i < std::min(c, n); ++i) out[i] = t[i];
     if (count) *count = c;
+    return LM_OK;
+}
+
+lm_status lm_tridiag_sqrt_e1_device(int count, int m, const double* alpha, const double* beta, double* out,
+                                    void* cuda_stream) {
+    g_err.clear();
+    if (count < 0 || m < 1 || m > 128) return fail(LM_ERR_INVALID_ARG, "need count >= 0 and 1 <= m <= 128");
+    if (count == 0) return LM_OK;
+    if (!alpha || !beta || !out) return fail(LM_ERR_INVALID_ARG, "alpha, beta and out are required");
+    if (!is_device_ptr(alpha) || !is_device_ptr(beta) || !is_device_ptr(out))
+        return fail(LM_ERR_INVALID_ARG, "alpha, beta and out must be device memory");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int max_rot = 4 * m * m + 64;
+    const size_t C = (size_t)count;
+    DBuf scr, rk, rc, rs, status;
+    LM_CUDA(scr.ensure(C * 3 * m * sizeof(double)), "tridiagonal scratch");
+    LM_CUDA(rk.ensure(C * max_rot * sizeof(int)), "tridiagonal scratch");
+    LM_CUDA(rc.ensure(C * max_rot * sizeof(double)), "tridiagonal scratch");
+    LM_CUDA(rs.ensure(C * max_rot * sizeof(double)), "tridiagonal scratch");
+    LM_CUDA(status.ensure(sizeof(int)), "tridiagonal scratch");
+    LM_CUDA(cudaMemsetAsync(status.p, 0, sizeof(int), st), "tridiagonal status");
+    LM_CUDA(lmk::launch_tridiag_dev(count, m, alpha, beta, scr.as<double>(), rk.as<int>(), rc.as<double>(),
+                                    rs.as<double>(), max_rot, out, status.as<int>(), st),
+            "tridiagonal kernel");
+    int h = 0;
+    LM_CUDA(cudaMemcpyAsync(&h, status.p, sizeof(int), cudaMemcpyDeviceToHost, st), "tridiagonal status");
+    LM_CUDA(cudaStreamSynchronize(st), "tridiagonal kernel");
+    if (h != 0) return fail(LM_ERR_CUDA, "device tridiagonal step failed (code %d)", h);
+    return LM_OK;
+}
+
+lm_status lm_batch_solve_counts(lm_batch* b, int64_t* posted, int64_t* solved) {
+    if (lm_status st = check_batch(b, false)) return st;
+    if (!posted || !solved) return fail(LM_ERR_INVALID_ARG, "posted and solved are required");
+    DeviceGuard g(b->device);
+    unsigned long long c[4] = {0, 0, 0, 0};
+    LM_CUDA(cudaStreamSynchronize(b->stream), "solve counts");
+    LM_CUDA(cudaMemcpy(c, b->q_ctr.p, sizeof(c), cudaMemcpyDeviceToHost), "solve counts");
+    *posted = (int64_t)c[1];
+    *solved = (int64_t)c[2];
     return LM_OK;
 }
 

@@ -162,6 +162,8 @@ enum BatchMode { kBatchBD = 0, kBatchMdot = 1, kBatchSqrt = 2 };
 enum BatchError { kBatchOk = 0, kBatchTimeout = 1, kBatchTridiag = 2 };
 constexpr int kBatchChunk = 256;       // elements per vector-phase work unit
 constexpr int kBatchJPart = 1024;      // j-range of one product work item
+constexpr int kSolverWidth = 2;        // requests a solver warp serves at once
+constexpr int kSolverWarps = 64;       // solver warps of a batched launch
 
 struct BatchParams {
     int S, m_max, mode, nsteps;
@@ -200,13 +202,13 @@ struct BatchParams {
     double* part_item;                 // n_items partial dots
     double* part_chunk;                // 2 x n_chunks x (m_max + 1) partial dots
     // Asynchronous tridiagonal solves.  CTAs [n_main, gridDim.x) are solver
-    // CTAs: each of their warps solves up to 32 requests side by side, one per
-    // lane, in lane-interleaved scratch (element i of lane l at [32 i + l]).
+    // CTAs: lanes [0, kSolverWidth) of each of their warps serve one request
+    // each (solver slot = warp * kSolverWidth + lane), with contiguous scratch.
     int n_main;                        // CTAs that run the phases and the grid barrier
-    double* sv_w;                      // per solver warp: d, e, z (3 x m_max x 32 doubles)
-    int* trk;                          // per solver warp: max_rot x 32 rotation indices
-    double* trc;                       // per solver warp: max_rot x 32 rotation cosines
-    double* trs;                       // per solver warp: max_rot x 32 rotation sines
+    double* sv_w;                      // per slot: d, e, r (double-float), z (4 x m_max doubles)
+    int* trk;                          // per slot: max_rot rotation indices
+    double* trc;                       // per slot: max_rot rotation cosines (double-float)
+    double* trs;                       // per slot: max_rot rotation sines (double-float)
     int max_rot;
     long long* q_req;                  // request ring: (step << 28) | (system << 7) | k
     unsigned long long* q_seq;         // ticket + 1 once the slot holds that ticket's request
@@ -222,6 +224,7 @@ struct BatchParams {
     int* next_check;                   // S: next iteration whose stopping test is due
     int* last_k;                       // S: last iteration (states 2, 3)
     int* k0s;                          // S: first iteration with a solve in this step
+    int* posted;                       // S: last iteration whose solve was requested
     int* main_done;                    // set when no more requests can come
     long long* cur_step;               // step the main CTAs are in (solvers drop older requests)
     unsigned* bar;                     // grid barrier: count, generation
@@ -250,6 +253,8 @@ cudaError_t launch_batch_pack(const float* pos, int64_t N, float4* pos4, double*
 cudaError_t launch_batch_unpack(const double* x64, int64_t N, float* out, cudaStream_t s);
 // A kernel whose barrier waits for one CTA more than it launches: every
 // wait runs out after spin_limit cycles and *err becomes kBatchTimeout.
+cudaError_t launch_tridiag_dev(int count, int m, const double* alpha, const double* beta, double* scratch, int* rk,
+                               double* rc, double* rs, int max_rot, double* out, int* status, cudaStream_t s);
 cudaError_t launch_batch_timeout_probe(unsigned* bar, int* err, long long spin_limit, int grid,
                                        cudaStream_t s);
 

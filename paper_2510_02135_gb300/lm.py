@@ -133,6 +133,10 @@ def lib():
         L.lm_batch_profile_enable.restype = st
         L.lm_batch_profile_read.argtypes = [_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.lm_batch_profile_read.restype = st
+        L.lm_tridiag_sqrt_e1_device.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
+        L.lm_tridiag_sqrt_e1_device.restype = st
+        L.lm_batch_solve_counts.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+        L.lm_batch_solve_counts.restype = st
         L.lm_batch_timeout_selftest.argtypes = [ctypes.c_longlong]
         L.lm_batch_timeout_selftest.restype = st
         L.lm_philox_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint64, _vp, ctypes.c_int64, _vp]
@@ -418,11 +422,35 @@ def lm_batch_profile_enable(b: Batch, enable: bool = True) -> None:
 
 
 def lm_batch_profile_read(b: Batch) -> np.ndarray:
-    """Phase end times (ns) of the first step of the last run (see include/lm.h)."""
+    """Phase end times (ns) of the last step of the last run (see include/lm.h)."""
     out = np.zeros(5 + 5 * b.max_iter, dtype=np.uint64)
     c = ctypes.c_int(0)
     _check(lib().lm_batch_profile_read(b.handle, out.ctypes.data, out.size, ctypes.byref(c)))
     return out[: c.value]
+
+
+def lm_tridiag_sqrt_e1_device(alpha, beta, out=None, stream=None):
+    """sqrt(T_c) e1 for each row c of the (count, m) float64 CUDA tensors alpha,
+    beta (beta[:, :m-1] used) with the device tridiagonal step."""
+    import torch
+
+    count, m = alpha.shape
+    if beta.shape != alpha.shape or alpha.dtype != torch.float64 or beta.dtype != torch.float64:
+        raise ValueError("alpha and beta must be float64 tensors of equal shape (count, m)")
+    alpha, beta = alpha.contiguous(), beta.contiguous()
+    if out is None:
+        out = torch.empty_like(alpha)
+    cs = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    _check(lib().lm_tridiag_sqrt_e1_device(int(count), int(m), alpha.data_ptr(), beta.data_ptr(), out.data_ptr(),
+                                           cs))
+    return out
+
+
+def lm_batch_solve_counts(b: Batch):
+    """(posted, solved) tridiagonal solve requests of the last batched run."""
+    p, q = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().lm_batch_solve_counts(b.handle, ctypes.byref(p), ctypes.byref(q)))
+    return int(p.value), int(q.value)
 
 
 def lm_batch_timeout_selftest(spin_cycles: int = 2_000_000) -> int:
