@@ -64,9 +64,13 @@ def _load():
             lib = ctypes.CDLL(_LIB_PATH)
             lib.orc_pair_blocks.argtypes = [_dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp]
             lib.orc_pair_blocks_grad.argtypes = [_dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp]
-            lib.orc_assemble.argtypes = [ctypes.c_int64, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp]
+            lib.orc_wall_blocks.argtypes = [_dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp]
+            lib.orc_wall_clamp.argtypes = [_dp, ctypes.c_double, _dp]
+            lib.orc_wall_clamp.restype = ctypes.c_double
+            lib.orc_assemble.argtypes = [ctypes.c_int64, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                         ctypes.c_int, _dp]
             lib.orc_mdot.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
-                                     ctypes.c_int, _i64p, ctypes.c_int64, _dp, _dp]
+                                     ctypes.c_int, ctypes.c_int, _i64p, ctypes.c_int64, _dp, _dp]
             lib.orc_grad.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, _dp, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_int, _i64p, ctypes.c_int64, _dp]
             lib.orc_num_threads.restype = ctypes.c_int
@@ -105,21 +109,45 @@ def pair_blocks_grad(d, a: float, eta: float):
     return tuple(out)
 
 
-def assemble(pos, a: float, eta: float, angular: bool) -> np.ndarray:
-    """Dense grand mobility, ordering [u;w] x [F;T] (Eq. block_mobility)."""
+def wall_blocks(x, y, a: float, eta: float):
+    """(uF, uT, wF, wT): the wall part of the Swan-Brady blocks (NBody with a
+    single wall, Sec. 3.5) for field particle at x and source particle at y,
+    both above the wall z = 0 (no damping); x == y gives the self term."""
+    lib = _load()
+    x = _f64(x).reshape(3)
+    y = _f64(y).reshape(3)
+    out = [np.zeros((3, 3)) for _ in range(4)]
+    lib.orc_wall_blocks(_ptr(x), _ptr(y), a, eta, *[_ptr(o) for o in out])
+    return tuple(out)
+
+
+def wall_clamp(x, a: float):
+    """(f, x_clamped): damping factor and evaluation position of a particle
+    at x (the reading of the wall damping, Sec. 3.5)."""
+    lib = _load()
+    x = _f64(x).reshape(3)
+    xc = np.zeros(3)
+    f = lib.orc_wall_clamp(_ptr(x), a, _ptr(xc))
+    return float(f), xc
+
+
+def assemble(pos, a: float, eta: float, angular: bool, wall: bool = False) -> np.ndarray:
+    """Dense grand mobility, ordering [u;w] x [F;T] (Eq. block_mobility);
+    ``wall`` adds the no-slip wall at z = 0 (Swan-Brady, with damping)."""
     lib = _load()
     pos = _f64(pos).reshape(-1, 3)
     n = pos.shape[0]
     dim = 6 * n if angular else 3 * n
     M = np.zeros((dim, dim))
-    lib.orc_assemble(n, _ptr(pos), a, eta, int(bool(angular)), _ptr(M))
+    lib.orc_assemble(n, _ptr(pos), a, eta, int(bool(angular)), int(bool(wall)), _ptr(M))
     return M
 
 
-def mdot(pos, F, T, a: float, eta: float, angular: bool, rows=None):
+def mdot(pos, F, T, a: float, eta: float, angular: bool, rows=None, wall: bool = False):
     """[u, w] = M(X) [F; T] by the direct pair sum (Sec. 3.2, Mdot).
 
     ``T`` may be None (zero torques).  ``rows`` selects output particles.
+    ``wall`` adds the no-slip wall at z = 0 (Swan-Brady, with damping).
     Returns (u, w); w is None when ``angular`` is False."""
     lib = _load()
     pos = _f64(pos).reshape(-1, 3)
@@ -133,7 +161,7 @@ def mdot(pos, F, T, a: float, eta: float, angular: bool, rows=None):
         nrows = r_arr.size
     U = np.zeros((nrows, 3))
     W = np.zeros((nrows, 3)) if angular else None
-    lib.orc_mdot(n, _ptr(pos), _ptr(F), _ptr(Tt), a, eta, int(bool(angular)),
+    lib.orc_mdot(n, _ptr(pos), _ptr(F), _ptr(Tt), a, eta, int(bool(angular)), int(bool(wall)),
                  None if r_arr is None else r_arr.ctypes.data_as(_i64p), nrows, _ptr(U), _ptr(W))
     return U, W
 
