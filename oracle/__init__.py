@@ -12,6 +12,10 @@ Contents (libMobility paper, Sec. 2 and Sec. 3.3):
   * ``mdot``          -- the matrix-free product M [F;T], optionally for a
                          subset of rows;
   * ``grad``          -- dL/dX of L = <[G;H], M(X) [F;T]> by the chain rule;
+  * ``wall_blocks``   -- the single-wall (Swan-Brady) part of the blocks
+                         (Sec. 3.5, NBody with z = "single_wall");
+  * ``div_fd``        -- the divergence of M by central differences, the
+                         reference of the thermal-drift test (Sec. 4);
   * ``sqrt_exact``    -- the principal square root M^{1/2} W from the
                          symmetric eigendecomposition (the plain definition);
   * ``lanczos_sqrt``  -- the Krylov (Lanczos) approximation of M^{1/2} W that
@@ -164,6 +168,32 @@ def mdot(pos, F, T, a: float, eta: float, angular: bool, rows=None, wall: bool =
     lib.orc_mdot(n, _ptr(pos), _ptr(F), _ptr(Tt), a, eta, int(bool(angular)), int(bool(wall)),
                  None if r_arr is None else r_arr.ctypes.data_as(_i64p), nrows, _ptr(U), _ptr(W))
     return U, W
+
+
+def div_fd(pos, a: float, eta: float, angular: bool, wall: bool, delta: float):
+    """Deterministic divergence of the mobility by central differences, the
+    reference of the thermal-drift test (Sec. 4):
+        div M = sum_k [M(q + delta e_k / 2) e_k - M(q - delta e_k / 2) e_k] / delta
+    over the 3N position coordinates q_k (e_k the unit vector of q_k; the
+    mobility of spheres does not depend on orientation).  Returns (lin, ang):
+    the rows of M_uF and, with angular blocks, of M_wF."""
+    pos = _f64(pos).reshape(-1, 3)
+    n = pos.shape[0]
+    lin = np.zeros((n, 3))
+    ang = np.zeros((n, 3)) if angular else None
+    for k in range(3 * n):
+        F = np.zeros((n, 3))
+        F.flat[k] = 1.0
+        qp = pos.copy()
+        qp.flat[k] += 0.5 * delta
+        qm = pos.copy()
+        qm.flat[k] -= 0.5 * delta
+        up, wp = mdot(qp, F, None, a, eta, angular, wall=wall)
+        um, wm = mdot(qm, F, None, a, eta, angular, wall=wall)
+        lin += (up - um) / delta
+        if angular:
+            ang += (wp - wm) / delta
+    return lin, ang
 
 
 def grad(pos, F, T, G, H, a: float, eta: float, angular: bool, rows=None) -> np.ndarray:

@@ -203,3 +203,22 @@ def test_wall_mdot_matches_assembled():
     u, w = oracle.mdot(pos, F, T, 1.1, 0.9, True, wall=True)
     y = M @ np.concatenate([F.ravel(), T.ravel()])
     np.testing.assert_allclose(np.concatenate([u.ravel(), w.ravel()]), y, rtol=1e-12, atol=1e-14)
+
+
+def test_div_fd_pins():
+    """The deterministic divergence: zero in the open geometry (Sec. 2: no
+    thermal drift in bulk), and for one sphere above the wall the derivative
+    of the normal self-mobility, d/dh [mu_0 (1 - 9/8 xi + 1/2 xi^3 - 1/8 xi^5)]
+    (the golden polynomial, differentiated by hand)."""
+    rng = np.random.default_rng(6)
+    pos = rng.uniform(-3, 3, size=(8, 3))
+    lin, ang = oracle.div_fd(pos, 1.0, 1.0, True, False, 1e-4)
+    assert np.abs(lin).max() < 1e-8 and np.abs(ang).max() < 1e-8
+    a, eta = 0.8, 1.3
+    mt = 1 / (6 * np.pi * eta * a)
+    for h in (1.05 * a, 1.7 * a, 4.0 * a):   # the damping makes z = a a kink
+        lin, ang = oracle.div_fd(np.array([[0.3, 0.1, h]]), a, eta, True, True, 1e-5)
+        xi = a / h
+        ref = mt * (9 / 8 * xi - 1.5 * xi ** 3 + 5 / 8 * xi ** 5) / h
+        assert abs(lin[0, 2] - ref) <= 1e-7 * abs(ref), (h, lin, ref)
+        assert np.abs(lin[0, :2]).max() < 1e-10 * abs(ref) and np.abs(ang).max() < 1e-10 * abs(ref)
