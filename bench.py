@@ -40,7 +40,15 @@ METRIC = "RPY pair-interactions/s (N^2 ordered pairs per application of M, incl.
 UNIT = "pair-interactions/s"
 FP32_LANES_PER_SM = 128
 RECIPE_MAX_SM_MHZ = 2070.0
-PAIR_KERNEL_SRC = os.path.join(ROOT, "paper_2510_02135_gb300", "csrc", "pair_kernels.cu")
+PAIR_KERNEL_SRCS = [os.path.join(ROOT, "paper_2510_02135_gb300", "csrc", f)
+                    for f in ("pair_kernels.cu", "pair_common.cuh")]
+
+
+def pair_kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in PAIR_KERNEL_SRCS:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
 
 
 def workload_spec(name: str):
@@ -141,7 +149,7 @@ def profile_traffic():
     path = os.path.join(ROOT, "profiles", "pair_kernel_rpy6_n32768.txt")
     if not os.path.exists(path):
         return None
-    src_hash = hashlib.sha256(open(PAIR_KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    src_hash = pair_kernel_source_hash()
     vals = {}
     for line in open(path):
         if ":" in line:
@@ -190,8 +198,11 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["rpy6", "melt", "adjoint", "bd256"], default="rpy6")
+    ap.add_argument("--workload", choices=["rpy6", "melt", "adjoint", "bd256", "wall"], default="rpy6")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default pair-kernel configuration")
+    ap.add_argument("--pair-config", default=None,
+                    help="threads,ilp,splits,packed: use this pair-kernel configuration instead of autotuning "
+                         "(profiling runs: under a profiler the autotuner's timings are not representative)")
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle CPU work for cpu_baseline")
     ap.add_argument("--ref-step-s", type=float, default=3.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -205,6 +216,8 @@ def main():
         return run_adjoint(args, ws, rank, local)
     if args.workload == "bd256":
         return run_bd(args, ws, rank, local)
+    if args.workload == "wall":
+        return run_wall(args, ws, rank, local)
 
     import torch
 
@@ -227,7 +240,10 @@ def main():
     ang2 = torch.empty_like(lin)
     solver = lm.lm_create(eta, a, True, lm.LM_FP32C, cuda_stream=torch.cuda.current_stream().cuda_stream)
     lm.lm_set_positions(solver, pos)
-    if not args.no_autotune:
+    if args.pair_config:
+        t_, i_, s_p, p_ = (int(v) for v in args.pair_config.split(","))
+        lm.lm_set_pair_config(solver, t_, i_, s_p, p_)
+    elif not args.no_autotune:
         lm.lm_autotune(solver, reps=2)
     cfg = lm.lm_get_pair_config(solver)
     iters = []
@@ -450,6 +466,96 @@ def run_adjoint(args, ws, rank, local):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "rpy_mdot_kernel (forward, translation, 35 flops/pair)"},
+            "gpu_launches": launches, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+# Algorithmic flops of one ordered pair above a single wall, translation
+# blocks (FMA = 2, counted from the formulas as the kernel evaluates them):
+# the free-space far-field pair (35) plus the wall part (96); the library's
+# profile counters use the same figure.
+WALL_FLOPS_PER_PAIR_TT = 131
+
+
+def run_wall(args, ws, rank, local):
+    """Mobility product above a single no-slip wall (the paper's "bottom
+    wall" benchmark shape): N = 32768 spheres uniform in a cube on the wall at
+    number density 0.1 / a^3, forces only, FP32.  One step = lm_set_positions
+    + lm_mdot; pairs counted N^2 per product."""
+    import torch
+
+    from paper_2510_02135_gb300 import _build, inputs as I, lm
+
+    dist = _dist_init(ws, local)
+    _build.build()
+    c = I.WALL_N32768
+    s_ = I.wall_suspension(c["seed"], c["n"], c["rho"], c["a"], angular=False, fp32=True)
+    n = c["n"]
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    pos, F = dev(s_.pos), dev(s_.F)
+    u = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    solver = lm.lm_create(c["eta"], c["a"], False, lm.LM_FP32C, periodicity=("open", "open", "single_wall"),
+                          cuda_stream=torch.cuda.current_stream().cuda_stream)
+    lm.lm_set_positions(solver, pos)
+    if args.pair_config:
+        t_, i_, s_p, p_ = (int(v) for v in args.pair_config.split(","))
+        lm.lm_set_pair_config(solver, t_, i_, s_p, p_)
+    elif not args.no_autotune:
+        lm.lm_autotune(solver, reps=2)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+
+    def step():
+        lm.lm_set_positions(solver, pos)
+        lm.lm_mdot(solver, F, None, u, None)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    lm.lm_profile_read(solver, reset=True)
+    lm.lm_profile_enable(solver, True)
+    sampler.start()
+    launches0 = lm.lm_launch_count()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    launches = lm.lm_launch_count() - launches0
+    lm.lm_profile_enable(solver, False)
+    prof = lm.lm_profile_read(solver, reset=True)
+    total = float(sum(e0.elapsed_time(e1) for e0, e1 in ev))
+    tmax, pairs = _reduce(dist, total, float(n) * n * args.steps)
+    props = torch.cuda.get_device_properties(local)
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * RECIPE_MAX_SM_MHZ * 1e6 / 1e12
+    kern_ms = prof["pair_ms"] / max(1, prof["pair_launches"])
+    achieved = prof["pair_flops"] / (prof["pair_ms"] / 1e3) / 1e12
+    line = {"metric": METRIC, "value": pairs / (tmax / 1e3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+            "config": {"workload": f"wall_n32768: N={n} spheres uniform in a cube resting on a no-slip wall, "
+                                   f"number density {c['rho']}/a^3, forces only, FP32 compensated; "
+                                   f"step = lm_set_positions + lm_mdot",
+                       "pair_config": lm.lm_get_pair_config(solver),
+                       "l2": "flushed by a 256 MB device write before every step"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": f"rpy_wall_kernel (translation, {WALL_FLOPS_PER_PAIR_TT} flops/pair)",
+                         "pair_kernel_ms_avg": kern_ms},
             "gpu_launches": launches, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))

@@ -59,10 +59,18 @@ typedef enum {
 
 /*
  * lm_create -- the solver constructor and `initialize` of Sec. 3.2.
- *   px, py, pz: periodicity strings; only "open" is accepted in all three
- *     directions (NBody, Sec. 3.5; Table tab:solver_summary).  Other valid
- *     names ("periodic", "single_wall", "two_walls") give
+ *   px, py, pz: periodicity strings (NBody, Sec. 3.5; Table
+ *     tab:solver_summary): px = py = "open"; pz = "open" (free-space RPY) or
+ *     "single_wall" (a no-slip wall at z = 0: the Swan-Brady kernel, with the
+ *     damping of particles that overlap the wall, see below).  Other valid
+ *     names ("periodic", "two_walls", or a wall in x or y) give
  *     LM_ERR_UNSUPPORTED_GEOMETRY, unknown names LM_ERR_INVALID_ARG.
+ *   Single wall: each block is the open RPY block plus the Faxen operators
+ *     applied to the image system of the Blake Green's function (Swan & Brady
+ *     2007).  A particle at height z is evaluated at height max(z, a) and its
+ *     rows and columns of M are scaled by f = clamp(z / a, 0, 1), so that M
+ *     stays symmetric positive semi-definite and the mobility of a particle
+ *     goes to zero as it reaches the wall (Sec. 3.5).
  *   viscosity (eta > 0), hydrodynamic_radius (a > 0): the parameters of the
  *     RPY kernel.
  *   include_angular: nonzero to accept torques and return angular
@@ -123,11 +131,30 @@ lm_status lm_sqrt_mdot(lm_solver *solver, const double *W, uint64_t seed, double
                        double tol, int max_iter, void *lin_out, void *ang_out, int *iters_out);
 
 /*
- * lm_div_m -- divM of Sec. 3.2.  For the open geometry the mobility is
- * translation invariant and isotropic, so the thermal drift is identically
- * zero (Sec. 2, discussion after Eq. fdt); the outputs are set to zero.
+ * lm_div_m -- divM of Sec. 3.2: lin_i = sum_j d/dx_j . M_uF(i, j),
+ * ang_i = sum_j d/dx_j . M_wF(i, j) (the thermal drift of Eq. bdhi is kT
+ * times this).  For the open geometry the mobility is translation invariant
+ * and isotropic, so it is identically zero (Sec. 2, discussion after Eq.
+ * fdt) and the outputs are set to zero.  With a single wall it is one random
+ * finite difference sample (Eq. rfd, Sec. 3.4), lm_div_m_rfd with the
+ * solver's call counter (0, 1, 2, ...) as seed and delta = 1e-4 a (LM_FP64)
+ * or 1e-2 a (LM_FP32C).
  */
 lm_status lm_div_m(lm_solver *solver, void *lin_out, void *ang_out);
+
+/*
+ * lm_div_m_rfd -- one random finite difference sample of divM, Eq. (rfd) of
+ * Sec. 3.4:
+ *   [lin; ang] = (M(X + delta W / 2) [W; 0] - M(X - delta W / 2) [W; 0]) / delta,
+ * W = 3N standard normals from Philox-4x32-10 with key seed and stream
+ * 0x524644 (element e = normal e mod 4 of counter block e / 4).  Its mean over
+ * W is divM up to O(delta^2).  Only positions are displaced: the mobility of
+ * spheres does not depend on their orientation.  delta > 0 (a length).
+ * lin_out, ang_out as in lm_mdot.  For the open geometry the result is zero.
+ * Allocates its scratch on the first call (four vectors of 3N or 6N doubles
+ * and a packed copy of the positions).
+ */
+lm_status lm_div_m_rfd(lm_solver *solver, uint64_t seed, double delta, void *lin_out, void *ang_out);
 
 /*
  * lm_mdot_backward -- adjoint of Mdot (not in the paper; the differentiable
@@ -139,7 +166,8 @@ lm_status lm_div_m(lm_solver *solver, void *lin_out, void *ang_out);
  *   required), grad_ang (H, NULL = zero, angular only).
  *   dX and dF may be NULL to skip them; dT must be NULL unless angular.
  *   The gradient of a pair term at r = 0 (coincident particles) is taken
- *   as zero.
+ *   as zero.  Open geometry only: a single-wall solver gives
+ *   LM_ERR_UNSUPPORTED_GEOMETRY.
  */
 lm_status lm_mdot_backward(lm_solver *solver, const void *forces, const void *torques,
                            const void *grad_lin, const void *grad_ang, void *dX, void *dF,
@@ -149,12 +177,16 @@ lm_status lm_mdot_backward(lm_solver *solver, const void *forces, const void *to
  * Pair-kernel launch configuration (chosen by the autotuner or set by hand).
  *   threads: CTA size (128 or 256); ilp: i-particles per thread (1, 2, 4, 8
  *   for LM_FP32C; 1, 2 for LM_FP64); splits: number of j-range splits
- *   (>= 1; 0 = automatic).
+ *   (>= 1; 0 = automatic); packed: 1 selects the packed FP32 form, which
+ *   evaluates two i-particles per f32x2 instruction (LM_FP32C with ilp 2, 4
+ *   or 8 only), 0 the scalar form.  Both give results within the FP32
+ *   tolerance of the FP64 product; they differ in rounding order only.
  */
 typedef struct {
     int threads;
     int ilp;
     int splits;
+    int packed;
 } lm_pair_config;
 
 /* lm_get_pair_config / lm_set_pair_config -- read or force the launch
@@ -193,7 +225,8 @@ typedef struct {
     int64_t pair_launches;    /* pair-kernel launches recorded */
     double pair_ms;           /* their summed device time, milliseconds */
     double pair_interactions; /* ordered pairs evaluated, N^2 per launch */
-    double pair_flops;        /* algorithmic flops: 35 per pair (forces only) or 86 (all blocks) */
+    double pair_flops;        /* algorithmic flops: 35 per pair (forces only) or 86 (all blocks);
+                                 single wall: 131 or 299 */
 } lm_profile;
 
 lm_status lm_profile_enable(lm_solver *solver, int enable);

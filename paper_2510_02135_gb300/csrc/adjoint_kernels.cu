@@ -357,6 +357,240 @@ __global__ void __launch_bounds__(NT) rpy_adjoint_kernel(const typename V4<R>::t
     }
 }
 
+// ---------------------------------------------------------------------------
+// Packed FP32 adjoint, translation blocks only: two i-particles per f32x2
+// instruction (same scheme as the packed forward kernel).  The j-tile holds
+// -x_j, F_j and G_j duplicated into both halves of a float2.  Per far-field
+// pair (units 1/(8 pi eta)):
+//   dF_i += A G_j + B (G_j.d) d
+//   dX_i += [A'/r (G_i.F_j + F_i.G_j) + B'/r ((G_i.d)(F_j.d) + (F_i.d)(G_j.d))] d
+//           + B (F_i.d) G_j + B (G_i.d) F_j
+//           + [B (F_j.d)] G_i + [B (G_j.d)] F_i        (scalars summed per tile)
+// with A'/r = -1/r^3 - 3 K1/r^5 and B'/r = -3/r^5 + 5 K2/r^7.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+
+constexpr int kAdjX2Words = 5;   // float4 words per j: (-x,-x,-y,-y) (-z,-z,Fx,Fx) (Fy,Fy,Fz,Fz) (Gx,Gx,Gy,Gy) (Gz,Gz,0,0)
+
+template <int NT, int NI>
+constexpr size_t adj_x2_smem_bytes() {
+    return (size_t)kAdjX2Words * NT * sizeof(float4) + adj_running_bytes<float, false, NT, NI>();
+}
+
+template <int NT, int NI>
+__global__ void __launch_bounds__(NT) rpy_adjoint_x2_kernel(const float4* __restrict__ pos4,
+                                                            const void* __restrict__ Fp, const void* __restrict__ Gp,
+                                                            int f64, int64_t N, int64_t jchunk, RpyConst<float> k,
+                                                            double c8, void* __restrict__ dX, void* __restrict__ dF,
+                                                            double* __restrict__ partials) {
+    static_assert(NI % 2 == 0, "packed form needs an even number of i-particles per thread");
+    constexpr int NP = NI / 2;
+    constexpr int C = 6;   // dX(3) dF(3)
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    float4* s_t = reinterpret_cast<float4*>(dyn_smem);
+    float* s_hi = reinterpret_cast<float*>(s_t + kAdjX2Words * NT);
+    float* s_lo = s_hi + C * NI * NT;
+    const int tid = threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.x * (NT * NI);
+    const int64_t jb = (int64_t)blockIdx.y * jchunk;
+    const int64_t je = (jb + jchunk < N) ? (jb + jchunk) : N;
+    const float pad = (float)kPadCoord;
+
+    float2 xi[NP], yi[NP], zi[NP], Fi[NP][3], Gi[NP][3];
+    float2 p[NP][C], sG[NP], sF[NP];
+#pragma unroll
+    for (int pp = 0; pp < NP; ++pp) {
+        float v[2][9];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t i = i0 + (int64_t)(2 * pp + h) * NT + tid;
+            if (i < N) {
+                const float4 q = pos4[i];
+                v[h][0] = q.x; v[h][1] = q.y; v[h][2] = q.z;
+            } else {
+                v[h][0] = v[h][1] = v[h][2] = -pad;
+            }
+            const int64_t ii = (i < N) ? i : 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                v[h][3 + c] = ld<float>(Fp, f64, 3 * ii + c);
+                v[h][6 + c] = ld<float>(Gp, f64, 3 * ii + c);
+            }
+        }
+        xi[pp] = make_float2(v[0][0], v[1][0]);
+        yi[pp] = make_float2(v[0][1], v[1][1]);
+        zi[pp] = make_float2(v[0][2], v[1][2]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Fi[pp][c] = make_float2(v[0][3 + c], v[1][3 + c]);
+            Gi[pp][c] = make_float2(v[0][6 + c], v[1][6 + c]);
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) p[pp][c] = bc2(0.f);
+        sG[pp] = sF[pp] = bc2(0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            s_hi[(c * NI + q) * NT + tid] = 0.f;
+            s_lo[(c * NI + q) * NT + tid] = 0.f;
+        }
+    }
+    const float2 K1 = bc2(k.K1), nK2 = bc2(-k.K2), m3K1 = bc2(-3.f * k.K1), K2x5 = bc2(5.f * k.K2);
+    const float2 m1 = bc2(-1.f), m3 = bc2(-3.f);
+
+    float4 np;
+    float3 nF, nG;
+    auto fetch = [&](int64_t j) {
+        if (j < je) {
+            np = pos4[j];
+            nF = make_float3(ld<float>(Fp, f64, 3 * j), ld<float>(Fp, f64, 3 * j + 1), ld<float>(Fp, f64, 3 * j + 2));
+            nG = make_float3(ld<float>(Gp, f64, 3 * j), ld<float>(Gp, f64, 3 * j + 1), ld<float>(Gp, f64, 3 * j + 2));
+        } else {
+            np = make_float4(pad, pad, pad, 0.f);
+            nF = nG = make_float3(0.f, 0.f, 0.f);
+        }
+    };
+    fetch(jb + tid);
+
+    for (int64_t jt = jb; jt < je; jt += NT) {
+        s_t[0 * NT + tid] = make_float4(-np.x, -np.x, -np.y, -np.y);
+        s_t[1 * NT + tid] = make_float4(-np.z, -np.z, nF.x, nF.x);
+        s_t[2 * NT + tid] = make_float4(nF.y, nF.y, nF.z, nF.z);
+        s_t[3 * NT + tid] = make_float4(nG.x, nG.x, nG.y, nG.y);
+        s_t[4 * NT + tid] = make_float4(nG.z, nG.z, 0.f, 0.f);
+        __syncthreads();
+        if (jt + NT < je) fetch(jt + NT + tid);
+#pragma unroll 1
+        for (int jj = 0; jj < NT; ++jj) {
+            const float4 w0 = s_t[0 * NT + jj], w1 = s_t[1 * NT + jj], w2 = s_t[2 * NT + jj];
+            const float4 w3 = s_t[3 * NT + jj], w4 = s_t[4 * NT + jj];
+            const float2 nx = lo2(w0), ny = hi2(w0), nz = lo2(w1);
+            const float2 Fx = hi2(w1), Fy = lo2(w2), Fz = hi2(w2);
+            const float2 Gx = lo2(w3), Gy = hi2(w3), Gz = lo2(w4);
+            float2 dx[NP], dy[NP], dz[NP], r2[NP];
+            float mn;
+#pragma unroll
+            for (int pp = 0; pp < NP; ++pp) {
+                dx[pp] = add2(xi[pp], nx);
+                dy[pp] = add2(yi[pp], ny);
+                dz[pp] = add2(zi[pp], nz);
+                r2[pp] = fma2(dx[pp], dx[pp], fma2(dy[pp], dy[pp], mul2(dz[pp], dz[pp])));
+                const float m2 = fminf(r2[pp].x, r2[pp].y);
+                mn = (pp == 0) ? m2 : fminf(mn, m2);
+            }
+            if (__any_sync(0xffffffffu, mn < k.four_a2)) {
+                const float4 Fj = make_float4(Fx.x, Fy.x, Fz.x, 0.f), Gj = make_float4(Gx.x, Gy.x, Gz.x, 0.f);
+#pragma unroll
+                for (int pp = 0; pp < NP; ++pp) {
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        IData<float, false> I;
+                        AAcc<float, false> t;
+                        I.x = I.y = I.z = 0.f;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            I.F[c] = h ? Fi[pp][c].y : Fi[pp][c].x;
+                            I.G[c] = h ? Gi[pp][c].y : Gi[pp][c].x;
+                        }
+#pragma unroll
+                        for (int c = 0; c < C; ++c) t.p[c] = 0.f;
+                        t.sG = t.sF = 0.f;
+                        Coef<float> cf;
+                        const float ddx = h ? dx[pp].y : dx[pp].x, ddy = h ? dy[pp].y : dy[pp].x;
+                        const float ddz = h ? dz[pp].y : dz[pp].x, rr = h ? r2[pp].y : r2[pp].x;
+                        const bool g = exact_coef<float, false>(rr, k, cf);
+                        adj_pair<float, false>(ddx, ddy, ddz, cf, g, Fj, Gj, Fj, Fj, I, t);
+                        if (h) {
+#pragma unroll
+                            for (int c = 0; c < C; ++c) p[pp][c].y += t.p[c];
+                            sG[pp].y += t.sG;
+                            sF[pp].y += t.sF;
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < C; ++c) p[pp][c].x += t.p[c];
+                            sG[pp].x += t.sG;
+                            sF[pp].x += t.sF;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int pp = 0; pp < NP; ++pp) {
+                    const float2 invr = make_float2(rsqrtf(r2[pp].x), rsqrtf(r2[pp].y));
+                    const float2 invr2 = mul2(invr, invr);
+                    const float2 invr3 = mul2(invr2, invr);
+                    const float2 invr5 = mul2(invr3, invr2);
+                    const float2 invr7 = mul2(invr5, invr2);
+                    const float2 A = fma2(K1, invr3, invr);
+                    const float2 B = fma2(nK2, invr5, invr3);
+                    const float2 Ap = fma2(m3K1, invr5, mul2(m1, invr3));
+                    const float2 Bp = fma2(K2x5, invr7, mul2(m3, invr5));
+                    const float2 b1 = fma2(Fx, dx[pp], fma2(Fy, dy[pp], mul2(Fz, dz[pp])));   // F_j.d
+                    const float2 b2 = fma2(Gx, dx[pp], fma2(Gy, dy[pp], mul2(Gz, dz[pp])));   // G_j.d
+                    const float2 Bb2 = mul2(B, b2);
+                    p[pp][3] = fma2(Bb2, dx[pp], fma2(A, Gx, p[pp][3]));
+                    p[pp][4] = fma2(Bb2, dy[pp], fma2(A, Gy, p[pp][4]));
+                    p[pp][5] = fma2(Bb2, dz[pp], fma2(A, Gz, p[pp][5]));
+                    const float2 a1 = fma2(Gi[pp][0], dx[pp], fma2(Gi[pp][1], dy[pp], mul2(Gi[pp][2], dz[pp])));
+                    const float2 a2 = fma2(Fi[pp][0], dx[pp], fma2(Fi[pp][1], dy[pp], mul2(Fi[pp][2], dz[pp])));
+                    const float2 S1 = fma2(Gi[pp][0], Fx, fma2(Gi[pp][1], Fy, fma2(Gi[pp][2], Fz,
+                                      fma2(Fi[pp][0], Gx, fma2(Fi[pp][1], Gy, mul2(Fi[pp][2], Gz))))));
+                    const float2 S2 = fma2(a1, b1, mul2(a2, b2));
+                    const float2 cd = fma2(Ap, S1, mul2(Bp, S2));
+                    const float2 Ba2 = mul2(B, a2), Ba1 = mul2(B, a1);
+                    sG[pp] = fma2(B, b1, sG[pp]);
+                    sF[pp] = add2(sF[pp], Bb2);
+                    p[pp][0] = fma2(cd, dx[pp], fma2(Ba2, Gx, fma2(Ba1, Fx, p[pp][0])));
+                    p[pp][1] = fma2(cd, dy[pp], fma2(Ba2, Gy, fma2(Ba1, Fy, p[pp][1])));
+                    p[pp][2] = fma2(cd, dz[pp], fma2(Ba2, Gz, fma2(Ba1, Fz, p[pp][2])));
+                }
+            }
+        }
+        // apply the tile's i-side scalars and fold into the running sums
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) p[pp][c] = fma2(sG[pp], Gi[pp][c], fma2(sF[pp], Fi[pp][c], p[pp][c]));
+            sG[pp] = sF[pp] = bc2(0.f);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const int o0 = (c * NI + 2 * pp) * NT + tid;
+                const int o1 = o0 + NT;
+                fold(&s_hi[o0], &s_lo[o0], p[pp][c].x);
+                fold(&s_hi[o1], &s_lo[o1], p[pp][c].y);
+            }
+        }
+        __syncthreads();
+    }
+    const bool direct = (gridDim.y == 1);
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+        const int64_t i = i0 + (int64_t)q * NT + tid;
+        if (i >= N) continue;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int o = (c * NI + q) * NT + tid;
+            const double v = (double)s_hi[o] + (double)s_lo[o];
+            if (direct) {
+                void* out = (c < 3) ? dX : dF;
+                if (out == nullptr) continue;
+                const int64_t idx = 3 * i + (c % 3);
+                if (f64) static_cast<double*>(out)[idx] = c8 * v;
+                else static_cast<float*>(out)[idx] = (float)(c8 * v);
+            } else {
+                partials[((int64_t)blockIdx.y * C + c) * N + i] = v;
+            }
+        }
+    }
+}
+
 __global__ void adj_reduce_kernel(const double* __restrict__ partials, int splits, int C, int64_t N, double c8,
                                   void* __restrict__ dX, void* __restrict__ dF, void* __restrict__ dT, int f64) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -414,6 +648,37 @@ cudaError_t launch_adj_t(const AdjointArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int NI>
+cudaError_t launch_adj_x2_t(const AdjointArgs& a, cudaStream_t s) {
+    constexpr int NT = 128;
+    const int64_t nblk = (a.N + NT * NI - 1) / (NT * NI);
+    int64_t jchunk = 0;
+    const int splits = (int)adj_split_plan(a.N, NT, a.splits, &jchunk);
+    if (nblk > 0x7fffffff || splits > 65535) return cudaErrorInvalidConfiguration;
+    if (splits > 1 && a.partials == nullptr) return cudaErrorInvalidValue;
+    const double c8 = 1.0 / (8.0 * 3.14159265358979323846 * a.eta);
+    const RpyConst<float> k = make_rpy_const<float>(a.a);
+    dim3 grid((unsigned)nblk, (unsigned)splits);
+    constexpr size_t dyn = adj_x2_smem_bytes<NT, NI>();
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(rpy_adjoint_x2_kernel<NT, NI>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    rpy_adjoint_x2_kernel<NT, NI><<<grid, NT, dyn, s>>>(static_cast<const float4*>(a.pos4), a.F, a.G, a.fp64, a.N,
+                                                        jchunk, k, c8, a.dX, a.dF, a.partials);
+    cudaError_t err = cudaGetLastError();
+    count_launches(1);
+    if (err != cudaSuccess || splits == 1) return err;
+    const int64_t tot = 6 * a.N;
+    adj_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a.partials, splits, 6, a.N, c8, a.dX, a.dF,
+                                                                     nullptr, a.fp64);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 int adjoint_partial_components(int angular) { return angular ? 9 : 6; }
@@ -426,7 +691,8 @@ cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s) {
     if (a.N <= 0) return cudaSuccess;
     if (a.threads != 128) return cudaErrorInvalidConfiguration;
     if (a.fp64) return a.angular ? launch_adj_t<double, true, 1>(a, s) : launch_adj_t<double, false, 1>(a, s);
-    return a.angular ? launch_adj_t<float, true, 2>(a, s) : launch_adj_t<float, false, 4>(a, s);
+    // FP32: translation blocks use the packed (f32x2) kernel
+    return a.angular ? launch_adj_t<float, true, 2>(a, s) : launch_adj_x2_t<4>(a, s);
 }
 
 int adjoint_ctas_per_sm(int fp64, int angular) {
@@ -443,7 +709,12 @@ int adjoint_ctas_per_sm(int fp64, int angular) {
     if (fp64 && angular) LM_AOCC(double, true, 1)
     else if (fp64) LM_AOCC(double, false, 1)
     else if (angular) LM_AOCC(float, true, 2)
-    else LM_AOCC(float, false, 4)
+    else {
+        constexpr size_t dyn = adj_x2_smem_bytes<128, 4>();
+        e = cudaFuncSetAttribute(rpy_adjoint_x2_kernel<128, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rpy_adjoint_x2_kernel<128, 4>, 128, dyn);
+    }
 #undef LM_AOCC
     return e == cudaSuccess ? n : 0;
 }

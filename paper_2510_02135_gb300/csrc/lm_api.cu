@@ -112,6 +112,14 @@ struct LanczosHost {
 
 }  // namespace
 
+namespace {
+// Random finite differences (Sec. 3.4): Philox stream of the noise, and the
+// default step relative to the radius (FP64 pairs / FP32 pairs).
+constexpr uint64_t kRfdStream = 0x524644ull;   // "RFD"
+constexpr double kRfdDeltaFP64 = 1e-4;
+constexpr double kRfdDeltaFP32 = 1e-2;
+}  // namespace
+
 namespace lmk {
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 void set_last_error(const char* msg) { g_err = msg; }
@@ -120,6 +128,7 @@ void set_last_error(const char* msg) { g_err = msg; }
 struct lm_solver {
     int angular = 0;
     int fp64 = 0;
+    int wall = 0;          // 1: no-slip wall at z = 0 ("single_wall" in z)
     double eta = 1.0, a = 1.0;
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -134,16 +143,19 @@ struct lm_solver {
     DBuf out_stage[3];
     DBuf flag;
     DBuf tune_in, tune_out;
+    // single wall: the caller's positions (for random finite differences) and RFD scratch
+    DBuf pos_raw, rfd_pos4, rfd_W, rfd_P, rfd_Q;
+    uint64_t rfd_calls = 0;
 
     // Lanczos state
     DBuf V, w, y, red, scal, zbuf, cbuf, Wbuf;
     double* pinned = nullptr;  // host scalar read-back
     size_t pinned_doubles = 0;
 
-    lm_pair_config cfg{128, 4, 1};
+    lm_pair_config cfg{128, 4, 1, 0};
     bool cfg_forced = false;
     int64_t cfg_N = -1;
-    lm_pair_config adj_cfg{128, 1, 1};
+    lm_pair_config adj_cfg{128, 1, 1, 0};
     int64_t adj_cfg_N = -1;
 
     lm_lanczos_stats stats{0, 0, 0.0, 0.0, 0};
@@ -161,6 +173,7 @@ struct lm_solver {
     ~lm_solver() {
         DBuf* all[] = {&pos4, &partials, &in_stage[0], &in_stage[1], &in_stage[2], &in_stage[3],
                        &out_stage[0], &out_stage[1], &out_stage[2], &flag, &tune_in, &tune_out,
+                       &pos_raw, &rfd_pos4, &rfd_W, &rfd_P, &rfd_Q,
                        &V, &w, &y, &red, &scal, &zbuf, &cbuf, &Wbuf};
         for (DBuf* b : all) b->release();
         if (pinned) cudaFreeHost(pinned);
@@ -242,11 +255,30 @@ int lmk::auto_splits(int64_t N, int threads, int ilp, int slots) {
 namespace {
 using lmk::auto_splits;
 
+bool pair_config_supported(const lm_solver* s, int threads, int ilp, int packed) {
+    return s->wall ? lmk::wall_config_supported(s->fp64, threads, ilp, packed)
+                   : lmk::mdot_config_supported(s->fp64, s->angular, threads, ilp, packed);
+}
+
+int pair_ctas_per_sm(const lm_solver* s, int threads, int ilp, int packed) {
+    return s->wall ? lmk::wall_ctas_per_sm(s->fp64, s->angular, threads, ilp)
+                   : lmk::mdot_ctas_per_sm(s->fp64, s->angular, threads, ilp, packed);
+}
+
 lm_pair_config default_config(const lm_solver* s, int64_t N) {
     lm_pair_config c;
-    c.threads = 128;
-    c.ilp = s->fp64 ? (s->angular ? 1 : 2) : 4;
-    int occ = lmk::mdot_ctas_per_sm(s->fp64, s->angular, c.threads, c.ilp);
+    // FP32: the packed form (fastest measured on GB300: 256 x 4 with angular
+    // blocks, 128 x 8 without); FP64: the scalar form.
+    c.threads = (!s->fp64 && s->angular) ? 256 : 128;
+    c.ilp = s->fp64 ? (s->angular ? 1 : 2) : (s->angular ? 4 : 8);
+    c.packed = s->fp64 ? 0 : 1;
+    if (s->wall) {
+        // single wall: scalar form, FP32 128 x 2, FP64 128 x 1
+        c.threads = 128;
+        c.ilp = s->fp64 ? 1 : 2;
+        c.packed = 0;
+    }
+    int occ = pair_ctas_per_sm(s, c.threads, c.ilp, c.packed);
     if (occ < 1) occ = 1;
     c.splits = auto_splits(N, c.threads, c.ilp, occ * s->sm_count);
     return c;
@@ -259,12 +291,12 @@ void ensure_config(lm_solver* s) {
 }
 
 lm_status run_mdot(lm_solver* s, const void* F, const void* T, int in_f64, void* lin, void* ang, int out_f64,
-                   const lm_pair_config& cfg) {
+                   const lm_pair_config& cfg, const void* pos4_override = nullptr) {
     lmk::MdotArgs a;
     a.fp64 = s->fp64;
     a.angular = s->angular;
     a.N = s->N;
-    a.pos4 = s->pos4.p;
+    a.pos4 = pos4_override ? pos4_override : s->pos4.p;
     a.F = F;
     a.T = s->angular ? T : nullptr;
     a.in_f64 = in_f64;
@@ -276,6 +308,7 @@ lm_status run_mdot(lm_solver* s, const void* F, const void* T, int in_f64, void*
     a.threads = cfg.threads;
     a.ilp = cfg.ilp;
     a.splits = cfg.splits;
+    a.packed = cfg.packed;
     a.partials = nullptr;
     const int64_t se = lmk::mdot_effective_splits(s->N, cfg.threads, cfg.splits);
     if (se > 1) {
@@ -294,7 +327,10 @@ lm_status run_mdot(lm_solver* s, const void* F, const void* T, int in_f64, void*
         s->prof_used += 1;
         s->prof_pairs += (double)s->N * (double)s->N;
     }
-    LM_CUDA(lmk::launch_mdot(a, s->stream), "mobility product kernel");
+    if (s->wall)
+        LM_CUDA(lmk::launch_wall_mdot(a, s->stream), "mobility product kernel (single wall)");
+    else
+        LM_CUDA(lmk::launch_mdot(a, s->stream), "mobility product kernel");
     return LM_OK;
 }
 
@@ -329,8 +365,9 @@ lm_status lm_create(lm_solver** out, const char* px, const char* py, const char*
     *out = nullptr;
     if (!valid_name(px) || !valid_name(py) || !valid_name(pz))
         return fail(LM_ERR_INVALID_ARG, "periodicity must be one of open, periodic, single_wall, two_walls");
-    if (strcmp(px, "open") || strcmp(py, "open") || strcmp(pz, "open"))
-        return fail(LM_ERR_UNSUPPORTED_GEOMETRY, "only open boundaries (\"open\", \"open\", \"open\") are supported");
+    if (strcmp(px, "open") || strcmp(py, "open") || (strcmp(pz, "open") && strcmp(pz, "single_wall")))
+        return fail(LM_ERR_UNSUPPORTED_GEOMETRY,
+                    "supported geometries: x and y \"open\", z \"open\" or \"single_wall\"");
     if (!(viscosity > 0.0) || !std::isfinite(viscosity)) return fail(LM_ERR_INVALID_ARG, "viscosity must be > 0");
     if (!(hydrodynamic_radius > 0.0) || !std::isfinite(hydrodynamic_radius))
         return fail(LM_ERR_INVALID_ARG, "hydrodynamic radius must be > 0");
@@ -339,6 +376,7 @@ lm_status lm_create(lm_solver** out, const char* px, const char* py, const char*
     if (!s) return fail(LM_ERR_OOM, "host allocation failed");
     s->angular = include_angular ? 1 : 0;
     s->fp64 = precision == LM_FP64 ? 1 : 0;
+    s->wall = strcmp(pz, "single_wall") == 0 ? 1 : 0;
     s->eta = viscosity;
     s->a = hydrodynamic_radius;
     s->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -384,14 +422,23 @@ lm_status lm_set_positions(lm_solver* s, const void* pos, int64_t N) {
     if (lm_status st = stage_in(s, pos, bytes, 0, &dpos)) return st;
     LM_CUDA(s->pos4.ensure((size_t)N * (s->fp64 ? sizeof(lmk::dvec4) : sizeof(float4))), "allocating positions");
     LM_CUDA(cudaMemsetAsync(s->flag.p, 0, sizeof(int), s->stream), "clearing flag");
-    LM_CUDA(lmk::launch_pack_positions(dpos, s->fp64, N, s->pos4.p, s->fp64, s->flag.as<int>(), s->stream),
-            "packing positions");
+    if (s->wall)
+        LM_CUDA(lmk::launch_pack_wall_positions(dpos, s->fp64, N, s->a, s->pos4.p, s->fp64, s->flag.as<int>(),
+                                                s->stream),
+                "packing positions");
+    else
+        LM_CUDA(lmk::launch_pack_positions(dpos, s->fp64, N, s->pos4.p, s->fp64, s->flag.as<int>(), s->stream),
+                "packing positions");
     int bad = 0;
     LM_CUDA(cudaMemcpyAsync(&s->pinned[0], s->flag.p, sizeof(int), cudaMemcpyDeviceToHost, s->stream),
             "reading flag");
     LM_CUDA(cudaStreamSynchronize(s->stream), "set_positions");
     memcpy(&bad, &s->pinned[0], sizeof(int));
     if (bad) return fail(LM_ERR_NONFINITE, "positions contain NaN/Inf or |x| > 1e15");
+    if (s->wall) {
+        LM_CUDA(s->pos_raw.ensure(bytes), "allocating positions");
+        LM_CUDA(cudaMemcpyAsync(s->pos_raw.p, dpos, bytes, cudaMemcpyDeviceToDevice, s->stream), "copying positions");
+    }
     s->N = N;
     s->has_pos = true;
     return LM_OK;
@@ -421,11 +468,56 @@ lm_status lm_mdot(lm_solver* s, const void* forces, const void* torques, void* l
     return finish_out(s, ov, 2);
 }
 
+lm_status lm_div_m_rfd(lm_solver* s, uint64_t seed, double delta, void* lin_out, void* ang_out) {
+    if (lm_status st = check_solver(s, true)) return st;
+    if (lin_out == nullptr) return fail(LM_ERR_INVALID_ARG, "lin_out is NULL");
+    if (s->angular && ang_out == nullptr) return fail(LM_ERR_INVALID_ARG, "ang_out is required with angular blocks");
+    if (!s->angular && ang_out != nullptr) return fail(LM_ERR_INVALID_ARG, "ang_out given but include_angular is 0");
+    if (!(delta > 0.0) || !std::isfinite(delta)) return fail(LM_ERR_INVALID_ARG, "delta must be > 0");
+    if (!s->wall) return lm_div_m(s, lin_out, ang_out);   // open geometry: exactly zero
+    DeviceGuard g(s->device);
+    const int64_t N = s->N;
+    const size_t bytes = (size_t)N * 3 * elem_size(s);
+    const size_t nvec = (size_t)(s->angular ? 6 : 3) * N;
+    OutView ov[2];
+    if (lm_status st = stage_out(s, lin_out, bytes, 0, &ov[0])) return st;
+    if (lm_status st = stage_out(s, ang_out, bytes, 1, &ov[1])) return st;
+    LM_CUDA(s->rfd_W.ensure(nvec * sizeof(double)), "allocating RFD scratch");
+    LM_CUDA(s->rfd_P.ensure(nvec * sizeof(double)), "allocating RFD scratch");
+    LM_CUDA(s->rfd_Q.ensure(nvec * sizeof(double)), "allocating RFD scratch");
+    LM_CUDA(s->rfd_pos4.ensure((size_t)N * (s->fp64 ? sizeof(lmk::dvec4) : sizeof(float4))), "allocating RFD scratch");
+    double* W = s->rfd_W.as<double>();
+    // W: 3N normals (translational part); the torque part stays zero, since
+    // the mobility of spheres does not depend on their orientation.
+    LM_CUDA(cudaMemsetAsync(W, 0, nvec * sizeof(double), s->stream), "RFD noise");
+    LM_CUDA(lmk::lz_philox_normals(seed, kRfdStream, W, 3 * N, s->stream), "RFD noise");
+    ensure_config(s);
+    for (int side = 0; side < 2; ++side) {
+        const double scale = side == 0 ? 0.5 * delta : -0.5 * delta;
+        LM_CUDA(lmk::launch_displace_pack_wall(s->pos_raw.p, s->fp64, W, scale, N, s->a, s->rfd_pos4.p, s->fp64,
+                                               s->stream),
+                "RFD positions");
+        double* out = side == 0 ? s->rfd_P.as<double>() : s->rfd_Q.as<double>();
+        if (lm_status st = run_mdot(s, W, s->angular ? W + 3 * N : nullptr, 1, out, s->angular ? out + 3 * N : nullptr,
+                                    1, s->cfg, s->rfd_pos4.p))
+            return st;
+    }
+    LM_CUDA(lmk::launch_rfd_difference(s->rfd_P.as<double>(), s->rfd_Q.as<double>(), 1.0 / delta, N, s->angular,
+                                       ov[0].dev, ov[1].dev, s->fp64, s->stream),
+            "RFD difference");
+    return finish_out(s, ov, 2);
+}
+
 lm_status lm_div_m(lm_solver* s, void* lin_out, void* ang_out) {
     if (lm_status st = check_solver(s, true)) return st;
     if (lin_out == nullptr) return fail(LM_ERR_INVALID_ARG, "lin_out is NULL");
     if (s->angular && ang_out == nullptr) return fail(LM_ERR_INVALID_ARG, "ang_out is required with angular blocks");
     if (!s->angular && ang_out != nullptr) return fail(LM_ERR_INVALID_ARG, "ang_out given but include_angular is 0");
+    if (s->wall) {
+        // one random-finite-difference sample per call, seeds 0, 1, 2, ... per solver
+        const double delta = (s->fp64 ? kRfdDeltaFP64 : kRfdDeltaFP32) * s->a;
+        return lm_div_m_rfd(s, s->rfd_calls++, delta, lin_out, ang_out);
+    }
     DeviceGuard g(s->device);
     const size_t bytes = (size_t)s->N * 3 * elem_size(s);
     OutView ov[2];
@@ -642,6 +734,8 @@ lm_status lm_get_lanczos_stats(lm_solver* s, lm_lanczos_stats* stats) {
 lm_status lm_mdot_backward(lm_solver* s, const void* forces, const void* torques, const void* grad_lin,
                            const void* grad_ang, void* dX, void* dF, void* dT) {
     if (lm_status st = check_solver(s, true)) return st;
+    if (s->wall)
+        return fail(LM_ERR_UNSUPPORTED_GEOMETRY, "the adjoint is implemented for the open geometry only");
     if (forces == nullptr || grad_lin == nullptr) return fail(LM_ERR_INVALID_ARG, "forces and grad_lin are required");
     if (!s->angular && (torques != nullptr || grad_ang != nullptr || dT != nullptr))
         return fail(LM_ERR_INVALID_ARG, "torque arguments given but include_angular is 0");
@@ -658,7 +752,7 @@ lm_status lm_mdot_backward(lm_solver* s, const void* forces, const void* torques
     if (lm_status st = stage_out(s, dT, bytes, 2, &ov[2])) return st;
     if (dX == nullptr && dF == nullptr && dT == nullptr) return LM_OK;
     if (s->adj_cfg_N != s->N) {
-        lm_pair_config c{128, lmk::adjoint_ilp(s->fp64, s->angular), 1};
+        lm_pair_config c{128, lmk::adjoint_ilp(s->fp64, s->angular), 1, 0};
         const int occ = std::max(1, lmk::adjoint_ctas_per_sm(s->fp64, s->angular));
         c.splits = auto_splits(s->N, c.threads, c.ilp, occ * s->sm_count);
         s->adj_cfg = c;
@@ -697,12 +791,12 @@ lm_status lm_get_pair_config(lm_solver* s, lm_pair_config* cfg) {
 lm_status lm_set_pair_config(lm_solver* s, const lm_pair_config* cfg) {
     if (lm_status st = check_solver(s, false)) return st;
     if (cfg == nullptr) return fail(LM_ERR_INVALID_ARG, "cfg is NULL");
-    if (!lmk::mdot_config_supported(s->fp64, s->angular, cfg->threads, cfg->ilp) || cfg->splits < 0)
-        return fail(LM_ERR_INVALID_ARG, "unsupported pair configuration (threads %d, ilp %d, splits %d)", cfg->threads,
-                    cfg->ilp, cfg->splits);
+    if (!pair_config_supported(s, cfg->threads, cfg->ilp, cfg->packed) || cfg->splits < 0)
+        return fail(LM_ERR_INVALID_ARG, "unsupported pair configuration (threads %d, ilp %d, splits %d, packed %d)",
+                    cfg->threads, cfg->ilp, cfg->splits, cfg->packed);
     s->cfg = *cfg;
     if (s->cfg.splits == 0) {
-        int occ = std::max(1, lmk::mdot_ctas_per_sm(s->fp64, s->angular, cfg->threads, cfg->ilp));
+        int occ = std::max(1, pair_ctas_per_sm(s, cfg->threads, cfg->ilp, cfg->packed));
         s->cfg.splits = s->has_pos ? auto_splits(s->N, cfg->threads, cfg->ilp, occ * s->sm_count) : 1;
     }
     s->cfg_forced = true;
@@ -724,17 +818,19 @@ lm_status lm_autotune(lm_solver* s, int reps, lm_pair_config* best) {
     std::vector<lm_pair_config> cands;
     const int threads_opts[2] = {128, 256};
     const int ilp_opts[4] = {1, 2, 4, 8};
-    for (int t : threads_opts) {
-        for (int il : ilp_opts) {
-            if (!lmk::mdot_config_supported(s->fp64, s->angular, t, il)) continue;
-            const int occ = lmk::mdot_ctas_per_sm(s->fp64, s->angular, t, il);
-            if (occ < 1) continue;
-            const int sa = auto_splits(N, t, il, occ * s->sm_count);
-            const int opts[4] = {sa, std::max(1, sa / 2), std::max(1, (3 * sa) / 2), sa * 2};
-            for (int k = 0; k < 4; ++k) {
-                bool dup = false;
-                for (int q = 0; q < k; ++q) dup = dup || (opts[q] == opts[k]);
-                if (!dup) cands.push_back(lm_pair_config{t, il, opts[k]});
+    for (int pk = 0; pk <= 2; ++pk) {
+        for (int t : threads_opts) {
+            for (int il : ilp_opts) {
+                if (!pair_config_supported(s, t, il, pk)) continue;
+                const int occ = pair_ctas_per_sm(s, t, il, pk);
+                if (occ < 1) continue;
+                const int sa = auto_splits(N, t, il, occ * s->sm_count);
+                const int opts[4] = {sa, std::max(1, sa / 2), std::max(1, (3 * sa) / 2), sa * 2};
+                for (int k = 0; k < 4; ++k) {
+                    bool dup = false;
+                    for (int q = 0; q < k; ++q) dup = dup || (opts[q] == opts[k]);
+                    if (!dup) cands.push_back(lm_pair_config{t, il, opts[k], pk});
+                }
             }
         }
     }
@@ -788,7 +884,8 @@ lm_status lm_profile_read(lm_solver* s, lm_profile* out, int reset) {
     out->pair_launches = (int64_t)s->prof_used;
     out->pair_ms = ms;
     out->pair_interactions = s->prof_pairs;
-    out->pair_flops = s->prof_pairs * (s->angular ? lmk::kFlopsPerPair6N : lmk::kFlopsPerPairTT);
+    out->pair_flops = s->prof_pairs * (s->wall ? (s->angular ? lmk::kFlopsPerPairWall6N : lmk::kFlopsPerPairWallTT)
+                                                : (s->angular ? lmk::kFlopsPerPair6N : lmk::kFlopsPerPairTT));
     if (reset) {
         s->prof_used = 0;
         s->prof_pairs = 0.0;

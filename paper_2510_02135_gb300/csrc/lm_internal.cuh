@@ -22,6 +22,10 @@ void set_last_error(const char* msg);
 // frozen for the roofline figures: translation only, and all four blocks.
 constexpr double kFlopsPerPairTT = 35.0;
 constexpr double kFlopsPerPair6N = 86.0;
+// Above a single wall: the free-space pair plus the wall part, counted from
+// the formulas as wall_kernels.cu evaluates them.
+constexpr double kFlopsPerPairWallTT = 131.0;
+constexpr double kFlopsPerPairWall6N = 299.0;
 
 // Constants of the RPY pair blocks for radius a, in units of 1/(8 pi eta).
 // Far field (r >= 2a), d = x_i - x_j, F the force and T the torque on j:
@@ -88,6 +92,7 @@ struct MdotArgs {
     int out_f64;           // element type of lin, ang
     double a, eta;
     int threads, ilp, splits;
+    int packed = 0;        // 1: packed f32x2 form (FP32, even ilp)
     double* partials;      // splits * (3 or 6) * N doubles when splits > 1
     cudaEvent_t ev_begin = nullptr;   // recorded right before / after the pair
     cudaEvent_t ev_end = nullptr;     // kernel when non-null (profiling)
@@ -108,14 +113,19 @@ struct AdjointArgs {
 };
 
 // Launch-configuration tables (pair_kernels.cu / adjoint_kernels.cu).
-bool mdot_config_supported(int fp64, int angular, int threads, int ilp);
-int mdot_ctas_per_sm(int fp64, int angular, int threads, int ilp);
+bool mdot_config_supported(int fp64, int angular, int threads, int ilp, int packed = 0);
+int mdot_ctas_per_sm(int fp64, int angular, int threads, int ilp, int packed = 0);
 // Default j-split count for `slots` concurrently resident CTAs (lm_api.cu).
 int auto_splits(int64_t N, int threads, int ilp, int slots);
 // Number of j-splits actually launched for a requested split count.
 int64_t mdot_effective_splits(int64_t N, int threads, int splits);
 int mdot_partial_components(int angular);
 cudaError_t launch_mdot(const MdotArgs& a, cudaStream_t s);
+// Single-wall geometry (wall_kernels.cu): the same arguments, positions packed
+// by launch_pack_wall_positions.
+bool wall_config_supported(int fp64, int threads, int ilp, int packed);
+int wall_ctas_per_sm(int fp64, int angular, int threads, int ilp);
+cudaError_t launch_wall_mdot(const MdotArgs& a, cudaStream_t s);
 cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s);
 int adjoint_partial_components(int angular);
 int adjoint_ilp(int fp64, int angular);
@@ -125,6 +135,15 @@ int adjoint_ctas_per_sm(int fp64, int angular);
 // coordinates in *bad (device int, set to 1).
 cudaError_t launch_pack_positions(const void* pos, int in_f64, int64_t N, void* pos4, int out_f64,
                                   int* bad, cudaStream_t s);
+// Wall geometry: (x, y, max(z, a), f) with the damping factor f = clamp(z / a, 0, 1).
+cudaError_t launch_pack_wall_positions(const void* pos, int in_f64, int64_t N, double a, void* pos4, int out_f64,
+                                       int* bad, cudaStream_t s);
+// Random finite differences (wall geometry): pack x + scale W (W: 3N doubles),
+// and write (P - Q) * inv_delta (FP64 grand vectors) to lin / ang.
+cudaError_t launch_displace_pack_wall(const void* pos, int in_f64, const double* W, double scale, int64_t N,
+                                      double a, void* pos4, int out_f64, cudaStream_t s);
+cudaError_t launch_rfd_difference(const double* P, const double* Q, double inv_delta, int64_t N, int angular,
+                                  void* lin, void* ang, int out_f64, cudaStream_t s);
 
 // Lanczos vector kernels (lanczos_kernels.cu).  All vectors are FP64 of
 // length n; the basis V is row-major (row j = v_j, stride n).  Reductions are

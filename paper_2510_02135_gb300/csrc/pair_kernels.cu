@@ -24,139 +24,10 @@
 #include <cstdint>
 
 #include "lm_internal.cuh"
+#include "pair_common.cuh"
 
 namespace lmk {
 namespace {
-
-template <typename R> struct V4;
-template <> struct V4<float> { using type = float4; };
-template <> struct V4<double> { using type = lmk::dvec4; };
-
-__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
-
-template <typename R>
-__device__ __forceinline__ R load_elem(const void* p, int in_f64, int64_t idx) {
-    if (p == nullptr) return R(0);
-    return in_f64 ? (R)(static_cast<const double*>(p)[idx]) : (R)(static_cast<const float*>(p)[idx]);
-}
-
-// Exact pair coefficients (both branches) for one pair.
-template <typename R>
-__device__ __forceinline__ void exact_coeffs(R r2, const RpyConst<R>& k, R& A, R& B, R& g, R& ar, R& br) {
-    if (r2 >= k.four_a2) {
-        const R invr = rsq(r2);
-        const R invr2 = invr * invr;
-        const R invr3 = invr2 * invr;
-        const R invr5 = invr3 * invr2;
-        A = invr + k.K1 * invr3;
-        B = invr3 - k.K2 * invr5;
-        g = invr3;
-        ar = R(-0.5) * invr3;
-        br = R(1.5) * invr5;
-    } else {
-        const R invr = (r2 > R(0)) ? rsq(r2) : R(0);
-        const R r = r2 * invr;
-        A = k.nA0 - k.nA1 * r;
-        B = k.nB * invr;
-        g = k.ng0 - k.ng1 * r;
-        ar = k.inv_a3 * (R(1) - k.rr1 * r + k.rr3 * r * r * r);
-        br = k.inv_a3 * (k.rrb0 * invr - k.rrb1 * r);
-    }
-}
-
-// Current-tile partial sums of one i-particle (registers).  The running
-// sums across tiles live in shared memory (FP32: a TwoSum (hi, lo) pair per
-// component; FP64: a plain sum), read and written once per tile.
-template <typename R, bool ANG>
-struct Acc {
-    R p[ANG ? 6 : 3];
-};
-
-// Far-field pair: u += A F + B (d.F) d + g (T x d) ; w += g (F x d - T/2) + br (d.T) d
-// with the tile holding h = -T/2:  T x d = -2 (h x d),  d.T = -2 d.h.
-// Written with explicit FMAs: 22 issue slots (tt) / 49 (all blocks) per pair.
-template <typename R, bool ANG>
-__device__ __forceinline__ void pair_far(R dx, R dy, R dz, R r2, const typename V4<R>::type& f,
-                                         const typename V4<R>::type& h, const RpyConst<R>& k,
-                                         Acc<R, ANG>& acc) {
-    const R invr = rsq(r2);
-    const R invr2 = invr * invr;
-    const R invr3 = invr2 * invr;
-    const R A = fma(k.K1, invr3, invr);
-    const R invr5 = invr3 * invr2;
-    const R B = fma(-k.K2, invr5, invr3);
-    const R dF = fma(dx, f.x, fma(dy, f.y, dz * f.z));
-    const R s = B * dF;
-    acc.p[0] = fma(s, dx, fma(A, f.x, acc.p[0]));
-    acc.p[1] = fma(s, dy, fma(A, f.y, acc.p[1]));
-    acc.p[2] = fma(s, dz, fma(A, f.z, acc.p[2]));
-    if constexpr (ANG) {
-        // u += g (T x d) = (-2 g) (h x d)
-        const R m2g = R(-2) * invr3;
-        const R cx = fma(h.y, dz, -(h.z * dy));
-        const R cy = fma(h.z, dx, -(h.x * dz));
-        const R cz = fma(h.x, dy, -(h.y * dx));
-        acc.p[0] = fma(m2g, cx, acc.p[0]);
-        acc.p[1] = fma(m2g, cy, acc.p[1]);
-        acc.p[2] = fma(m2g, cz, acc.p[2]);
-        // w += g (F x d + h) + (-2 br) (d.h) d
-        const R vx = fma(f.y, dz, fma(-f.z, dy, h.x));
-        const R vy = fma(f.z, dx, fma(-f.x, dz, h.y));
-        const R vz = fma(f.x, dy, fma(-f.y, dx, h.z));
-        const R t = (R(-3) * invr5) * fma(dx, h.x, fma(dy, h.y, dz * h.z));
-        acc.p[3] = fma(t, dx, fma(invr3, vx, acc.p[3]));
-        acc.p[4] = fma(t, dy, fma(invr3, vy, acc.p[4]));
-        acc.p[5] = fma(t, dz, fma(invr3, vz, acc.p[5]));
-    }
-}
-
-// Exact pair (either branch, including r = 0).
-template <typename R, bool ANG>
-__device__ __forceinline__ void pair_exact(R dx, R dy, R dz, R r2, const typename V4<R>::type& f,
-                                           const typename V4<R>::type& h, const RpyConst<R>& k,
-                                           Acc<R, ANG>& acc) {
-    R A, B, g, ar, br;
-    exact_coeffs<R>(r2, k, A, B, g, ar, br);
-    const R s = B * (dx * f.x + dy * f.y + dz * f.z);
-    acc.p[0] += A * f.x + s * dx;
-    acc.p[1] += A * f.y + s * dy;
-    acc.p[2] += A * f.z + s * dz;
-    if constexpr (ANG) {
-        const R m2g = R(-2) * g;
-        acc.p[0] += m2g * (h.y * dz - h.z * dy);
-        acc.p[1] += m2g * (h.z * dx - h.x * dz);
-        acc.p[2] += m2g * (h.x * dy - h.y * dx);
-        const R m2ar = R(-2) * ar;
-        const R t = (R(-2) * br) * (dx * h.x + dy * h.y + dz * h.z);
-        acc.p[3] += g * (f.y * dz - f.z * dy) + m2ar * h.x + t * dx;
-        acc.p[4] += g * (f.z * dx - f.x * dz) + m2ar * h.y + t * dy;
-        acc.p[5] += g * (f.x * dy - f.y * dx) + m2ar * h.z + t * dz;
-    }
-}
-
-// Knuth TwoSum fold of the tile partial p into the shared (hi, lo) pair.
-__device__ __forceinline__ void fold(float* hi, float* lo, float& p) {
-    const float h = *hi;
-    const float s = h + p;
-    const float bb = s - h;
-    const float err = (h - (s - bb)) + (p - bb);
-    *hi = s;
-    *lo += err;
-    p = 0.0f;
-}
-__device__ __forceinline__ void fold(double* hi, double* lo, double& p) {
-    *hi += p;
-    p = 0.0;
-    (void)lo;
-}
-
-// Dynamic shared memory for the running sums: C x NI x NT values of R
-// (FP32 adds the same again for the low parts).
-template <typename R, bool ANG, int NT, int NI>
-constexpr size_t running_sum_bytes() {
-    return (size_t)(ANG ? 6 : 3) * NI * NT * sizeof(R) * (sizeof(R) == 4 ? 2 : 1);
-}
 
 template <typename R, bool ANG, int NT, int NI>
 __global__ void __launch_bounds__(NT) rpy_mdot_kernel(const typename V4<R>::type* __restrict__ pos4,
@@ -283,29 +154,272 @@ __global__ void __launch_bounds__(NT) rpy_mdot_kernel(const typename V4<R>::type
     }
 }
 
-// out[3 i + c] = c8 * sum_s partials[s][c][i]
-__global__ void reduce_splits_kernel(const double* __restrict__ partials, int splits, int C, int64_t N,
-                                     double c8, void* __restrict__ lin, void* __restrict__ ang, int out_f64) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)C * N) return;
-    const int64_t i = e / C;
-    const int c = (int)(e - i * C);
-    double s = 0.0;
-    for (int k = 0; k < splits; ++k) s += partials[((int64_t)k * C + c) * N + i];
-    void* out = (c < 3) ? lin : ang;
-    const int64_t idx = 3 * i + (c % 3);
-    if (out_f64) static_cast<double*>(out)[idx] = c8 * s;
-    else static_cast<float*>(out)[idx] = (float)(c8 * s);
+// ---------------------------------------------------------------------------
+// Packed FP32 form: two i-particles per f32x2 instruction.
+//
+// sm_100-class SMs execute add / mul / fma on a pair of FP32 values held in an
+// adjacent register pair as one instruction.  The pair sum is the same for
+// every i and one j, so i-particles q = 2p and 2p + 1 of a thread share each
+// instruction: the far-field pair costs 21 (translation) / 46 (all blocks)
+// packed instructions per two pairs, plus one scalar rsqrt per pair.
+//
+// Packed operands carry no negation, so the j-tile holds every value a pair
+// needs, already duplicated into both halves of a float2 (shared-memory
+// broadcast loads land them in register pairs):
+//   slot  0.. 2  -x_j                       (d = x_i + (-x_j))
+//   slot  3.. 5  F_j
+//   slot  6.. 8  -F_j                       (F x d without negation)
+//   slot  9..11  T_j,  12..14  -T_j         (T x d)
+//   slot 15..17  -T_j / 2                   (the -T/2 term of w)
+//   slot 18..20  3 T_j / 2                  (d.T term of w: t = (d.(3T/2)) / r^5)
+// Translation-only solvers use slots 0..5.  Far field (r >= 2a), per pair:
+//   u += A F + B (d.F) d + (T x d) / r^3
+//   w += (F x d - T/2) / r^3 + (3/2) (d.T) d / r^5
+// The exact branch (some pair of the warp at r < 2a) unpacks the two lanes
+// and runs the scalar formula.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+
+// float4 words of one j in the packed tile
+template <bool ANG>
+constexpr int x2_words() { return ANG ? 11 : 3; }
+
+template <bool ANG, int NT, int NI>
+constexpr size_t x2_smem_bytes() {
+    return (size_t)x2_words<ANG>() * NT * sizeof(float4) + running_sum_bytes<float, ANG, NT, NI>();
 }
 
-// j-range split: equal chunks of whole tiles; returns the launched split count.
-int64_t split_plan(int64_t N, int NT, int splits, int64_t* jchunk) {
-    if (splits < 1) splits = 1;
-    const int64_t ntiles = (N + NT - 1) / NT;
-    if (splits > ntiles) splits = (int)ntiles;
-    const int64_t tps = (ntiles + splits - 1) / splits;
-    *jchunk = tps * NT;
-    return (N + *jchunk - 1) / *jchunk;
+template <bool ANG, int NT, int NI, int UJ>
+__global__ void __launch_bounds__(NT) rpy_mdot_x2_kernel(const float4* __restrict__ pos4,
+                                                         const void* __restrict__ Fp, const void* __restrict__ Tp,
+                                                         int in_f64, int64_t N, int64_t jchunk, RpyConst<float> k,
+                                                         double c8, void* __restrict__ lin, void* __restrict__ ang,
+                                                         int out_f64, double* __restrict__ partials) {
+    static_assert(NI % 2 == 0, "packed form needs an even number of i-particles per thread");
+    static_assert(NT % UJ == 0, "the j tile must hold whole groups of UJ");
+    constexpr int NP = NI / 2;
+    constexpr int C = ANG ? 6 : 3;
+    constexpr int W = x2_words<ANG>();
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    float4* s_t = reinterpret_cast<float4*>(dyn_smem);                 // [w][jj]
+    float* s_hi = reinterpret_cast<float*>(s_t + W * NT);              // [c][q][tid]
+    float* s_lo = s_hi + C * NI * NT;
+
+    const int tid = threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.x * (NT * NI);
+    const int64_t jb = (int64_t)blockIdx.y * jchunk;
+    const int64_t je = (jb + jchunk < N) ? (jb + jchunk) : N;
+    const float pad = (float)kPadCoord;
+
+    float2 xi[NP], yi[NP], zi[NP];
+    float2 acc[NP][C];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        float x2[2], y2[2], z2[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t i = i0 + (int64_t)(2 * p + h) * NT + tid;
+            if (i < N) {
+                const float4 v = pos4[i];
+                x2[h] = v.x; y2[h] = v.y; z2[h] = v.z;
+            } else {
+                x2[h] = -pad; y2[h] = -pad; z2[h] = -pad;
+            }
+        }
+        xi[p] = make_float2(x2[0], x2[1]);
+        yi[p] = make_float2(y2[0], y2[1]);
+        zi[p] = make_float2(z2[0], z2[1]);
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[p][c] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            s_hi[(c * NI + q) * NT + tid] = 0.f;
+            s_lo[(c * NI + q) * NT + tid] = 0.f;
+        }
+    }
+    const float2 K1 = make_float2(k.K1, k.K1);
+    const float2 nK2 = make_float2(-k.K2, -k.K2);
+
+    // register prefetch of this thread's j of the next tile (raw values)
+    float4 np;
+    float3 nf, nt;
+    auto fetch = [&](int64_t j) {
+        if (j < je) {
+            np = pos4[j];
+            nf.x = load_elem<float>(Fp, in_f64, 3 * j + 0);
+            nf.y = load_elem<float>(Fp, in_f64, 3 * j + 1);
+            nf.z = load_elem<float>(Fp, in_f64, 3 * j + 2);
+            if constexpr (ANG) {
+                nt.x = load_elem<float>(Tp, in_f64, 3 * j + 0);
+                nt.y = load_elem<float>(Tp, in_f64, 3 * j + 1);
+                nt.z = load_elem<float>(Tp, in_f64, 3 * j + 2);
+            }
+        } else {
+            np = make_float4(pad, pad, pad, 0.f);
+            nf = make_float3(0.f, 0.f, 0.f);
+            nt = make_float3(0.f, 0.f, 0.f);
+        }
+    };
+    fetch(jb + tid);
+
+    for (int64_t jt = jb; jt < je; jt += NT) {
+        // expand this thread's j into the broadcast slots
+        s_t[0 * NT + tid] = make_float4(-np.x, -np.x, -np.y, -np.y);
+        s_t[1 * NT + tid] = make_float4(-np.z, -np.z, nf.x, nf.x);
+        s_t[2 * NT + tid] = make_float4(nf.y, nf.y, nf.z, nf.z);
+        if constexpr (ANG) {
+            s_t[3 * NT + tid] = make_float4(-nf.x, -nf.x, -nf.y, -nf.y);
+            s_t[4 * NT + tid] = make_float4(-nf.z, -nf.z, nt.x, nt.x);
+            s_t[5 * NT + tid] = make_float4(nt.y, nt.y, nt.z, nt.z);
+            s_t[6 * NT + tid] = make_float4(-nt.x, -nt.x, -nt.y, -nt.y);
+            s_t[7 * NT + tid] = make_float4(-nt.z, -nt.z, -0.5f * nt.x, -0.5f * nt.x);
+            s_t[8 * NT + tid] = make_float4(-0.5f * nt.y, -0.5f * nt.y, -0.5f * nt.z, -0.5f * nt.z);
+            s_t[9 * NT + tid] = make_float4(1.5f * nt.x, 1.5f * nt.x, 1.5f * nt.y, 1.5f * nt.y);
+            s_t[10 * NT + tid] = make_float4(1.5f * nt.z, 1.5f * nt.z, 0.f, 0.f);
+        }
+        __syncthreads();
+        if (jt + NT < je) fetch(jt + NT + tid);
+
+        // UJ consecutive j share one overlap vote, so that the far-field work
+        // of UJ j-particles forms one block of independent instructions.
+#pragma unroll 1
+        for (int jj = 0; jj < NT; jj += UJ) {
+            float2 dx[UJ][NP], dy[UJ][NP], dz[UJ][NP], r2[UJ][NP];
+            float mn;
+#pragma unroll
+            for (int u = 0; u < UJ; ++u) {
+                const float4 w0 = s_t[0 * NT + jj + u];
+                const float4 w1 = s_t[1 * NT + jj + u];
+                const float2 nx = lo2(w0), ny = hi2(w0), nz = lo2(w1);
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    dx[u][p] = add2(xi[p], nx);
+                    dy[u][p] = add2(yi[p], ny);
+                    dz[u][p] = add2(zi[p], nz);
+                    r2[u][p] = fma2(dx[u][p], dx[u][p], fma2(dy[u][p], dy[u][p], mul2(dz[u][p], dz[u][p])));
+                    const float m2 = fminf(r2[u][p].x, r2[u][p].y);
+                    mn = (u == 0 && p == 0) ? m2 : fminf(mn, m2);
+                }
+            }
+            if (__any_sync(0xffffffffu, mn < k.four_a2)) {
+#pragma unroll
+                for (int u = 0; u < UJ; ++u) {
+                    const float4 w1 = s_t[1 * NT + jj + u];
+                    const float4 w2 = s_t[2 * NT + jj + u];
+                    const float4 fj = make_float4(w1.z, w2.x, w2.z, 0.f);
+                    float4 hj = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if constexpr (ANG) {
+                        const float4 w7 = s_t[7 * NT + jj + u];
+                        const float4 w8 = s_t[8 * NT + jj + u];
+                        hj = make_float4(w7.z, w8.x, w8.z, 0.f);
+                    }
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        Acc<float, ANG> t0, t1;
+#pragma unroll
+                        for (int c = 0; c < C; ++c) { t0.p[c] = 0.f; t1.p[c] = 0.f; }
+                        pair_exact<float, ANG>(dx[u][p].x, dy[u][p].x, dz[u][p].x, r2[u][p].x, fj, hj, k, t0);
+                        pair_exact<float, ANG>(dx[u][p].y, dy[u][p].y, dz[u][p].y, r2[u][p].y, fj, hj, k, t1);
+#pragma unroll
+                        for (int c = 0; c < C; ++c) acc[p][c] = add2(acc[p][c], make_float2(t0.p[c], t1.p[c]));
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < UJ; ++u) {
+                    const float4 w1 = s_t[1 * NT + jj + u];
+                    const float4 w2 = s_t[2 * NT + jj + u];
+                    const float2 fx = hi2(w1), fy = lo2(w2), fz = hi2(w2);
+                    float2 mfx, mfy, mfz, Tx, Ty, Tz, mTx, mTy, mTz, hx, hy, hz, gx, gy, gz;
+                    if constexpr (ANG) {
+                        const float4 w3 = s_t[3 * NT + jj + u];
+                        const float4 w4 = s_t[4 * NT + jj + u];
+                        const float4 w5 = s_t[5 * NT + jj + u];
+                        const float4 w6 = s_t[6 * NT + jj + u];
+                        const float4 w7 = s_t[7 * NT + jj + u];
+                        const float4 w8 = s_t[8 * NT + jj + u];
+                        const float4 w9 = s_t[9 * NT + jj + u];
+                        const float4 w10 = s_t[10 * NT + jj + u];
+                        mfx = lo2(w3); mfy = hi2(w3); mfz = lo2(w4);
+                        Tx = hi2(w4); Ty = lo2(w5); Tz = hi2(w5);
+                        mTx = lo2(w6); mTy = hi2(w6); mTz = lo2(w7);
+                        hx = hi2(w7); hy = lo2(w8); hz = hi2(w8);
+                        gx = lo2(w9); gy = hi2(w9); gz = lo2(w10);
+                    }
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        const float2 ddx = dx[u][p], ddy = dy[u][p], ddz = dz[u][p];
+                        const float2 invr = make_float2(rsqrtf(r2[u][p].x), rsqrtf(r2[u][p].y));
+                        const float2 invr2 = mul2(invr, invr);
+                        const float2 invr3 = mul2(invr2, invr);
+                        const float2 A = fma2(K1, invr3, invr);
+                        const float2 invr5 = mul2(invr3, invr2);
+                        const float2 B = fma2(nK2, invr5, invr3);
+                        const float2 dF = fma2(ddx, fx, fma2(ddy, fy, mul2(ddz, fz)));
+                        const float2 sB = mul2(B, dF);
+                        acc[p][0] = fma2(sB, ddx, fma2(A, fx, acc[p][0]));
+                        acc[p][1] = fma2(sB, ddy, fma2(A, fy, acc[p][1]));
+                        acc[p][2] = fma2(sB, ddz, fma2(A, fz, acc[p][2]));
+                        if constexpr (ANG) {
+                            // u += (T x d) / r^3
+                            const float2 cx = fma2(Ty, ddz, mul2(mTz, ddy));
+                            const float2 cy = fma2(Tz, ddx, mul2(mTx, ddz));
+                            const float2 cz = fma2(Tx, ddy, mul2(mTy, ddx));
+                            acc[p][0] = fma2(invr3, cx, acc[p][0]);
+                            acc[p][1] = fma2(invr3, cy, acc[p][1]);
+                            acc[p][2] = fma2(invr3, cz, acc[p][2]);
+                            // w += (F x d - T/2) / r^3 + (d.(3T/2)) d / r^5
+                            const float2 vx = fma2(fy, ddz, fma2(mfz, ddy, hx));
+                            const float2 vy = fma2(fz, ddx, fma2(mfx, ddz, hy));
+                            const float2 vz = fma2(fx, ddy, fma2(mfy, ddx, hz));
+                            const float2 t = mul2(invr5, fma2(ddx, gx, fma2(ddy, gy, mul2(ddz, gz))));
+                            acc[p][3] = fma2(t, ddx, fma2(invr3, vx, acc[p][3]));
+                            acc[p][4] = fma2(t, ddy, fma2(invr3, vy, acc[p][4]));
+                            acc[p][5] = fma2(t, ddz, fma2(invr3, vz, acc[p][5]));
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const int o0 = (c * NI + 2 * p) * NT + tid;
+                const int o1 = o0 + NT;
+                fold(&s_hi[o0], &s_lo[o0], acc[p][c].x);
+                fold(&s_hi[o1], &s_lo[o1], acc[p][c].y);
+            }
+        }
+        __syncthreads();
+    }
+
+    const bool direct = (gridDim.y == 1);
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+        const int64_t i = i0 + (int64_t)q * NT + tid;
+        if (i >= N) continue;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int o = (c * NI + q) * NT + tid;
+            const double v = (double)s_hi[o] + (double)s_lo[o];
+            if (direct) {
+                void* out = (c < 3) ? lin : ang;
+                const int64_t idx = 3 * i + (c % 3);
+                if (out_f64) static_cast<double*>(out)[idx] = c8 * v;
+                else static_cast<float*>(out)[idx] = (float)(c8 * v);
+            } else {
+                partials[((int64_t)blockIdx.y * C + c) * N + i] = v;
+            }
+        }
+    }
 }
 
 template <typename R, bool ANG, int NT, int NI>
@@ -341,6 +455,77 @@ cudaError_t launch_t(const MdotArgs& a, cudaStream_t s) {
                                                                         a.ang, a.out_f64);
     count_launches(1);
     return cudaGetLastError();
+}
+
+template <bool ANG, int NT, int NI, int UJ>
+cudaError_t launch_x2_t(const MdotArgs& a, cudaStream_t s) {
+    const int64_t per_cta = (int64_t)NT * NI;
+    const int64_t nblk = (a.N + per_cta - 1) / per_cta;
+    int64_t jchunk = 0;
+    const int splits = (int)split_plan(a.N, NT, a.splits, &jchunk);
+    if (nblk > 0x7fffffff || splits > 65535) return cudaErrorInvalidConfiguration;
+    const double c8 = 1.0 / (8.0 * 3.14159265358979323846 * a.eta);
+    const RpyConst<float> k = make_rpy_const<float>(a.a);
+    dim3 grid((unsigned)nblk, (unsigned)splits);
+    if (splits > 1 && a.partials == nullptr) return cudaErrorInvalidValue;
+    constexpr size_t dyn = x2_smem_bytes<ANG, NT, NI>();
+    static bool attr_set = false;  // per instantiation; the attribute is process-wide
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(rpy_mdot_x2_kernel<ANG, NT, NI, UJ>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (a.ev_begin) cudaEventRecord(a.ev_begin, s);
+    rpy_mdot_x2_kernel<ANG, NT, NI, UJ><<<grid, NT, dyn, s>>>(static_cast<const float4*>(a.pos4), a.F,
+                                                          ANG ? a.T : nullptr, a.in_f64, a.N, jchunk, k, c8,
+                                                          a.lin, a.ang, a.out_f64, a.partials);
+    cudaError_t err = cudaGetLastError();
+    if (a.ev_end) cudaEventRecord(a.ev_end, s);
+    count_launches(1);
+    if (err != cudaSuccess || splits == 1) return err;
+    constexpr int C = ANG ? 6 : 3;
+    const int64_t tot = (int64_t)C * a.N;
+    reduce_splits_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a.partials, splits, C, a.N, c8, a.lin,
+                                                                        a.ang, a.out_f64);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// Packed configurations (FP32 only): threads {128, 256} x ilp {2, 4, 8};
+// packed = 2 unrolls the j loop by two (more independent work per warp).
+template <bool ANG, int UJ>
+cudaError_t launch_x2_u(const MdotArgs& a, cudaStream_t s) {
+    if (a.threads == 128 && a.ilp == 2) return launch_x2_t<ANG, 128, 2, UJ>(a, s);
+    if (a.threads == 128 && a.ilp == 4) return launch_x2_t<ANG, 128, 4, UJ>(a, s);
+    if (a.threads == 128 && a.ilp == 8) return launch_x2_t<ANG, 128, 8, UJ>(a, s);
+    if (a.threads == 256 && a.ilp == 2) return launch_x2_t<ANG, 256, 2, UJ>(a, s);
+    if (a.threads == 256 && a.ilp == 4) return launch_x2_t<ANG, 256, 4, UJ>(a, s);
+    if (a.threads == 256 && a.ilp == 8) return launch_x2_t<ANG, 256, 8, UJ>(a, s);
+    return cudaErrorInvalidConfiguration;
+}
+
+template <bool ANG>
+cudaError_t launch_x2(const MdotArgs& a, cudaStream_t s) {
+    return a.packed == 2 ? launch_x2_u<ANG, 2>(a, s) : launch_x2_u<ANG, 1>(a, s);
+}
+
+template <bool ANG, int UJ>
+int occupancy_x2(int threads, int ilp) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidConfiguration;
+#define LM_OCC2(NT, NI)                                                                                   \
+    if (threads == NT && ilp == NI) {                                                                     \
+        constexpr size_t dyn = x2_smem_bytes<ANG, NT, NI>();                                              \
+        e = cudaFuncSetAttribute(rpy_mdot_x2_kernel<ANG, NT, NI, UJ>,                                     \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);                  \
+        if (e == cudaSuccess)                                                                             \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rpy_mdot_x2_kernel<ANG, NT, NI, UJ>, NT, \
+                                                              dyn);                                       \
+    }
+    LM_OCC2(128, 2) LM_OCC2(128, 4) LM_OCC2(128, 8) LM_OCC2(256, 2) LM_OCC2(256, 4) LM_OCC2(256, 8)
+#undef LM_OCC2
+    return e == cudaSuccess ? n : 0;
 }
 
 // Instantiated configurations: FP32 threads {128, 256} x ilp {1, 2, 4, 8};
@@ -393,13 +578,20 @@ int64_t mdot_effective_splits(int64_t N, int threads, int splits) {
     return split_plan(N, threads, splits, &jc);
 }
 
-int mdot_ctas_per_sm(int fp64, int angular, int threads, int ilp) {
+int mdot_ctas_per_sm(int fp64, int angular, int threads, int ilp, int packed) {
+    if (packed) {
+        if (fp64 || !mdot_config_supported(fp64, angular, threads, ilp, packed)) return 0;
+        if (packed == 2) return angular ? occupancy_x2<true, 2>(threads, ilp) : occupancy_x2<false, 2>(threads, ilp);
+        return angular ? occupancy_x2<true, 1>(threads, ilp) : occupancy_x2<false, 1>(threads, ilp);
+    }
     if (fp64) return angular ? occupancy_r<double, true>(threads, ilp) : occupancy_r<double, false>(threads, ilp);
     return angular ? occupancy_r<float, true>(threads, ilp) : occupancy_r<float, false>(threads, ilp);
 }
 
-bool mdot_config_supported(int fp64, int angular, int threads, int ilp) {
+bool mdot_config_supported(int fp64, int angular, int threads, int ilp, int packed) {
     (void)angular;
+    if (packed) return (packed == 1 || packed == 2) && !fp64 && (threads == 128 || threads == 256) &&
+                       (ilp == 2 || ilp == 4 || ilp == 8);
     return (threads == 128 || threads == 256) && (fp64 ? ilp_ok<double>(ilp) : ilp_ok<float>(ilp));
 }
 
@@ -407,6 +599,10 @@ int mdot_partial_components(int angular) { return angular ? 6 : 3; }
 
 cudaError_t launch_mdot(const MdotArgs& a, cudaStream_t s) {
     if (a.N <= 0) return cudaSuccess;
+    if (a.packed) {
+        if (a.fp64) return cudaErrorInvalidConfiguration;
+        return a.angular ? launch_x2<true>(a, s) : launch_x2<false>(a, s);
+    }
     if (a.fp64) return a.angular ? launch_r<double, true>(a, s) : launch_r<double, false>(a, s);
     return a.angular ? launch_r<float, true>(a, s) : launch_r<float, false>(a, s);
 }

@@ -12,6 +12,9 @@ random in a cube, overlaps allowed):
     bond length and a Gaussian bend-angle jitter), heads uniform in the cube.
   * ``batch_suspensions``-- many independent cubes with log-uniform sizes and
     uniform volume fractions.
+  * ``wall_suspension``  -- N spheres uniform in a cube resting on the wall
+    z = 0 (number density rho), for the single-wall geometry; centres below
+    z = a overlap the wall.
 
 Everything is drawn in FP64 with numpy's PCG64 (``default_rng(seed)``) and,
 for FP32 workloads, rounded once to FP32, so the oracle and the GPU see
@@ -109,6 +112,27 @@ def polymer_melt(seed: int, n_chains: int = 1024, beads: int = 512, bond: float 
                       W=W, G=G.astype(dt), H=H.astype(dt) if angular else None, L=L, a=a)
 
 
+def wall_suspension(seed: int, n: int, rho: float, a: float = 1.0, angular: bool = False,
+                    fp32: bool = True) -> Suspension:
+    """N spheres uniform in a cube of side L = (N / rho)^(1/3) on the wall:
+    x, y in [-L/2, L/2), z in [0, L).  Draw order as ``cube_suspension``
+    (positions first as three uniform columns in [0, 1), scaled)."""
+    rng = np.random.default_rng(seed)
+    L = float((n / rho) ** (1.0 / 3.0))
+    u = rng.uniform(0.0, 1.0, size=(n, 3))
+    pos = np.column_stack([(u[:, 0] - 0.5) * L, (u[:, 1] - 0.5) * L, u[:, 2] * L])
+    F = rng.standard_normal((n, 3))
+    T = rng.standard_normal((n, 3))
+    W = rng.standard_normal(6 * n)
+    G = rng.standard_normal((n, 3))
+    H = rng.standard_normal((n, 3))
+    dt = np.float32 if fp32 else np.float64
+    if not angular:
+        W = W[: 3 * n].copy()
+    return Suspension(pos=pos.astype(dt), F=F.astype(dt), T=T.astype(dt) if angular else None,
+                      W=W, G=G.astype(dt), H=H.astype(dt) if angular else None, L=L, a=a)
+
+
 @dataclass
 class Batch:
     offsets: np.ndarray   # (S+1,) int64 prefix sum of sizes
@@ -147,3 +171,6 @@ BATCH_BD_256 = dict(seed=1004, S=256, nmin=64, nmax=4096, phi_lo=0.05, phi_hi=0.
                     kT=1.0, dt=1e-3, k_trap=1.0, nsteps=100, tol=1e-4)
 MELT_N524288 = dict(seed=1005, n_chains=1024, beads=512, bond=2.2, sigma=0.3, phi=0.05, a=1.0, eta=1.0,
                     angular=True, fp32=True, tol=1e-3)
+# Single wall (the paper's "bottom wall" benchmark shape: random positions at
+# number density 0.1 / a^3, forces only).
+WALL_N32768 = dict(seed=1006, n=32768, rho=0.1, a=1.0, eta=1.0, angular=False, fp32=True)

@@ -45,7 +45,8 @@ class LmError(RuntimeError):
 
 
 class lm_pair_config(ctypes.Structure):
-    _fields_ = [("threads", ctypes.c_int), ("ilp", ctypes.c_int), ("splits", ctypes.c_int)]
+    _fields_ = [("threads", ctypes.c_int), ("ilp", ctypes.c_int), ("splits", ctypes.c_int),
+                ("packed", ctypes.c_int)]
 
 
 class lm_lanczos_stats(ctypes.Structure):
@@ -86,6 +87,8 @@ def lib():
         L.lm_sqrt_mdot.restype = st
         L.lm_div_m.argtypes = [_vp, _vp, _vp]
         L.lm_div_m.restype = st
+        L.lm_div_m_rfd.argtypes = [_vp, ctypes.c_uint64, ctypes.c_double, _vp, _vp]
+        L.lm_div_m_rfd.restype = st
         L.lm_mdot_backward.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.lm_mdot_backward.restype = st
         L.lm_get_pair_config.argtypes = [_vp, ctypes.POINTER(lm_pair_config)]
@@ -301,6 +304,17 @@ def lm_div_m(s: Solver, like):
     return lin, ang
 
 
+def lm_div_m_rfd(s: Solver, seed: int, delta: float, like):
+    """One random-finite-difference sample of div M (Sec. 3.4) with noise key ``seed``."""
+    lin = _like(like, (s.N, 3), s.f64)
+    ang = _like(like, (s.N, 3), s.f64) if s.angular else None
+    s._sync_stream(lin, ang)
+    n3 = 3 * s.N if s.N else None
+    _check(lib().lm_div_m_rfd(s.handle, int(seed), float(delta), _ptr(lin, s.f64, n3, "lin"),
+                              _ptr(ang, s.f64, n3, "ang")))
+    return lin, ang
+
+
 def lm_mdot_backward(s: Solver, forces, torques, grad_lin, grad_ang, need_dX: bool = True, need_dF: bool = True):
     """Adjoint of lm_mdot.  Returns (dX, dF, dT)."""
     dX = _like(forces, (s.N, 3), s.f64) if need_dX else None
@@ -468,18 +482,18 @@ def lm_philox_normals(seed: int, stream: int, out, cuda_stream=None) -> None:
 def lm_get_pair_config(s: Solver) -> dict:
     c = lm_pair_config()
     _check(lib().lm_get_pair_config(s.handle, ctypes.byref(c)))
-    return {"threads": c.threads, "ilp": c.ilp, "splits": c.splits}
+    return {"threads": c.threads, "ilp": c.ilp, "splits": c.splits, "packed": c.packed}
 
 
-def lm_set_pair_config(s: Solver, threads: int, ilp: int, splits: int = 0) -> None:
-    c = lm_pair_config(threads, ilp, splits)
+def lm_set_pair_config(s: Solver, threads: int, ilp: int, splits: int = 0, packed: int = 0) -> None:
+    c = lm_pair_config(threads, ilp, splits, packed)
     _check(lib().lm_set_pair_config(s.handle, ctypes.byref(c)))
 
 
 def lm_autotune(s: Solver, reps: int = 3) -> dict:
     c = lm_pair_config()
     _check(lib().lm_autotune(s.handle, int(reps), ctypes.byref(c)))
-    return {"threads": c.threads, "ilp": c.ilp, "splits": c.splits}
+    return {"threads": c.threads, "ilp": c.ilp, "splits": c.splits, "packed": c.packed}
 
 
 def lm_get_lanczos_stats(s: Solver) -> dict:
@@ -569,15 +583,18 @@ def mobility(solver: Solver, X, F, T=None):
 
 @dataclass
 class NBody:
-    """The paper's solver interface (Sec. 3.2) over the C ABI: open boundaries."""
+    """The paper's solver interface (Sec. 3.2) over the C ABI: x and y open,
+    z "open" or "single_wall" (the Swan-Brady kernel)."""
 
     viscosity: float
     hydrodynamicRadius: float
     includeAngular: bool = False
     precision: int = LM_FP32C
+    periodicityZ: str = "open"
 
     def __post_init__(self):
-        self.solver = lm_create(self.viscosity, self.hydrodynamicRadius, self.includeAngular, self.precision)
+        self.solver = lm_create(self.viscosity, self.hydrodynamicRadius, self.includeAngular, self.precision,
+                                periodicity=("open", "open", self.periodicityZ))
 
     def setPositions(self, pos):
         lm_set_positions(self.solver, pos)

@@ -49,8 +49,10 @@ def test_create_rejects_bad_arguments_without_gpu(L):
 
     h = ctypes.c_void_p()
     cases = [
-        ((b"open", b"open", b"single_wall", 1.0, 1.0, 0, 0), lm.LM_ERR_UNSUPPORTED_GEOMETRY),
+        ((b"open", b"open", b"two_walls", 1.0, 1.0, 0, 0), lm.LM_ERR_UNSUPPORTED_GEOMETRY),
+        ((b"single_wall", b"open", b"open", 1.0, 1.0, 0, 0), lm.LM_ERR_UNSUPPORTED_GEOMETRY),
         ((b"periodic", b"periodic", b"periodic", 1.0, 1.0, 0, 0), lm.LM_ERR_UNSUPPORTED_GEOMETRY),
+        ((b"open", b"open", b"single_wall", -1.0, 1.0, 0, 0), lm.LM_ERR_INVALID_ARG),
         ((b"open", b"open", b"bogus", 1.0, 1.0, 0, 0), lm.LM_ERR_INVALID_ARG),
         ((b"open", b"open", b"open", -1.0, 1.0, 0, 0), lm.LM_ERR_INVALID_ARG),
         ((b"open", b"open", b"open", 1.0, 0.0, 0, 0), lm.LM_ERR_INVALID_ARG),

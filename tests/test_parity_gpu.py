@@ -51,10 +51,13 @@ def maxabs_over_rms(y, ref):
     return np.abs(y - ref).max() / (rms if rms > 0 else 1.0)
 
 
-def make(eta, a, angular, fp64, pos):
+def make_solver(eta, a, angular, fp64, pos):
     s = lm.lm_create(eta, a, angular, lm.LM_FP64 if fp64 else lm.LM_FP32C)
     lm.lm_set_positions(s, dev(pos))
     return s
+
+
+make = make_solver
 
 
 def gpu_mdot(s, F, T):
@@ -78,12 +81,14 @@ def test_mdot_fp64_translational_n1024(orc):
     assert rel(u, ur) <= 1e-12
 
 
-@pytest.mark.parametrize("fp64", [False, True])
-def test_mdot_blocks_match_oracle(orc, fp64):
+@pytest.mark.parametrize("fp64,packed", [(False, 0), (False, 1), (False, 2), (True, 0)])
+def test_mdot_blocks_match_oracle(orc, fp64, packed):
     n = 2500  # 19 tiles of 128 and a ragged tail of 68
     a, eta = 1.0, 1.0
     s_ = I.cube_suspension(77, n, 0.2, a, angular=True, fp32=not fp64)
     s = make(eta, a, True, fp64, s_.pos)
+    if packed:
+        lm.lm_set_pair_config(s, 128, 8, 0, packed=packed)
     tol = 1e-12 if fp64 else 1e-5
     zero = np.zeros_like(s_.F)
     for name, F, T in (("F", s_.F, zero), ("T", zero, s_.T), ("FT", s_.F, s_.T)):
@@ -103,19 +108,30 @@ def test_mdot_launch_configs_agree(orc, fp64, angular):
     s = make(1.0, 1.0, angular, fp64, s_.pos)
     ur, wr = orc.mdot(s_.pos, s_.F, s_.T, 1.0, 1.0, angular)
     tol = 1e-12 if fp64 else 1e-5
-    for threads in (128, 256):
-        for ilp in ((1, 2) if fp64 else (1, 2, 4, 8)):
-            for splits in (1, 3, 9):
-                lm.lm_set_pair_config(s, threads, ilp, splits)
-                u, w = gpu_mdot(s, s_.F, s_.T)
-                assert rel(u, ur) <= tol, (threads, ilp, splits, rel(u, ur))
-                if angular:
-                    assert rel(w, wr) <= tol, (threads, ilp, splits, rel(w, wr))
+    for packed in ((0,) if fp64 else (0, 1, 2)):
+        for threads in (128, 256):
+            for ilp in ((1, 2) if fp64 else ((2, 4, 8) if packed else (1, 2, 4, 8))):
+                for splits in (1, 3, 9):
+                    lm.lm_set_pair_config(s, threads, ilp, splits, packed)
+                    u, w = gpu_mdot(s, s_.F, s_.T)
+                    cfg = (threads, ilp, splits, packed)
+                    assert rel(u, ur) <= tol, (cfg, rel(u, ur))
+                    if angular:
+                        assert rel(w, wr) <= tol, (cfg, rel(w, wr))
+                    if not fp64:
+                        assert maxabs_over_rms(u, ur) <= 1e-4, (cfg, maxabs_over_rms(u, ur))
 
 
-@pytest.mark.parametrize("fp64", [False, True])
-def test_mdot_edge_cases(orc, fp64):
+@pytest.mark.parametrize("fp64,packed", [(False, 0), (False, 1), (False, 2), (True, 0)])
+def test_mdot_edge_cases(orc, fp64, packed):
     dt = np.float64 if fp64 else np.float32
+
+    def make(eta, a, angular, fp64, pos):
+        s = make_solver(eta, a, angular, fp64, pos)
+        if packed:
+            lm.lm_set_pair_config(s, 128, 2, 0, packed=packed)
+        return s
+
     a, eta = 1.3, 0.7
     rng = np.random.default_rng(3)
     tol = 1e-12 if fp64 else 1e-6
@@ -327,6 +343,9 @@ def test_call_order_and_argument_errors():
     assert e.value.status == lm.LM_ERR_INVALID_ARG
     with pytest.raises(lm.LmError) as e:
         lm.lm_set_pair_config(s, 96, 3, 1)
+    assert e.value.status == lm.LM_ERR_INVALID_ARG
+    with pytest.raises(lm.LmError) as e:
+        lm.lm_set_pair_config(s, 128, 1, 1, packed=1)  # the packed form needs an even ilp
     assert e.value.status == lm.LM_ERR_INVALID_ARG
     z, _ = lm.lm_div_m(s, F)
     assert not z.any()
