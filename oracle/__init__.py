@@ -16,6 +16,9 @@ Contents (libMobility paper, Sec. 2 and Sec. 3.3):
                          (Sec. 3.5, NBody with z = "single_wall");
   * ``div_fd``        -- the divergence of M by central differences, the
                          reference of the thermal-drift test (Sec. 4);
+  * ``rfd_sample``    -- one random finite difference sample of div M (Eq. rfd);
+  * ``soft_repulsion``-- forces of the soft steric potential, Eq. (soft_potential);
+  * ``ab_step``       -- one stochastic Adams-Bashforth step (Sec. 5.1);
   * ``sqrt_exact``    -- the principal square root M^{1/2} W from the
                          symmetric eigendecomposition (the plain definition);
   * ``lanczos_sqrt``  -- the Krylov (Lanczos) approximation of M^{1/2} W that
@@ -393,3 +396,70 @@ def em_step(pos, a: float, eta: float, kT: float, dt: float, k_trap: float, W, t
         y, it, _ = lanczos_sqrt(lambda v: mdot(pos, v.reshape(n, 3), None, a, eta, False)[0].ravel(), W, tol,
                                 max_iter)
     return pos + dt * u + np.sqrt(2.0 * kT * dt) * y.reshape(n, 3), it
+
+
+RFD_STREAM = 0x524644   # Philox stream of the random-finite-difference noise ("RFD")
+
+
+def rfd_sample(pos, seed: int, delta: float, a: float, eta: float, angular: bool, wall: bool):
+    """One random finite difference sample of div M, Eq. (rfd) of Sec. 3.4:
+    (M(X + delta W/2) [W; 0] - M(X - delta W/2) [W; 0]) / delta with W the 3N
+    Philox normals of (seed, RFD_STREAM).  Returns (lin, ang)."""
+    pos = _f64(pos).reshape(-1, 3)
+    n = pos.shape[0]
+    W = philox_normals(seed, RFD_STREAM, 3 * n).reshape(n, 3)
+    T0 = np.zeros((n, 3)) if angular else None
+    up, wp = mdot(pos + 0.5 * delta * W, W, T0, a, eta, angular, wall=wall)
+    um, wm = mdot(pos - 0.5 * delta * W, W, T0, a, eta, angular, wall=wall)
+    return (up - um) / delta, ((wp - wm) / delta if angular else None)
+
+
+def soft_repulsion(pos, U0: float, b: float, d_pair: float, d_wall: float, wall: bool) -> np.ndarray:
+    """Forces F = -dU/dX of the soft steric potential of the roller example,
+    Eq. (soft_potential) of Sec. 5.1:
+        U(r) = U0 (1 + (d - r) / b)   for r < d,
+        U(r) = U0 exp((d - r) / b)    for r >= d,
+    over every particle pair (d = d_pair, r the centre distance) and, with a
+    wall, every particle-wall pair (d = d_wall, r the height z).  A pair at
+    r = 0 exerts no force (no direction)."""
+    pos = _f64(pos).reshape(-1, 3)
+    n = pos.shape[0]
+    F = np.zeros((n, 3))
+    for i in range(n):
+        d = pos[i] - pos
+        r = np.sqrt(np.sum(d * d, axis=1))
+        m = r > 0.0
+        # -dU/dr: U0 / b inside d, (U0 / b) exp((d - r) / b) outside
+        mag = np.where(r[m] < d_pair, U0 / b, U0 / b * np.exp((d_pair - r[m]) / b))
+        F[i] = np.sum((mag / r[m])[:, None] * d[m], axis=0)
+    if wall:
+        z = pos[:, 2]
+        F[:, 2] += np.where(z < d_wall, U0 / b, U0 / b * np.exp((d_wall - z) / b))
+    return F
+
+
+def ab_step(pos, F, T, W, prev_u, prev_d, first: bool, kT: float, dt: float, a: float, eta: float,
+            angular: bool, wall: bool, rfd_seed: int, rfd_delta: float):
+    """One step of the stochastic Adams-Bashforth scheme of Sec. 5.1 for the
+    positions X (N x 3):
+      X' = X + dt [(3/2) u^n - (1/2) u^{n-1} + kT ((3/2) d^n - (1/2) d^{n-1})]
+             + sqrt(2 kT dt) (M^n)^{1/2} W,
+    u^n = (M^n [F; T])_lin, d^n = one RFD sample of div M^n (seed rfd_seed;
+    zero in the open geometry or at kT = 0).  ``first``: the previous terms
+    equal the current ones (an Euler-Maruyama step).  W: 3N (6N with angular
+    blocks) normals; the linear part of (M^n)^{1/2} W moves X; the square root
+    is the principal one (eigendecomposition).  Returns (X', u^n, d^n)."""
+    pos = _f64(pos).reshape(-1, 3)
+    n = pos.shape[0]
+    u, _ = mdot(pos, F, T if angular else None, a, eta, angular, wall=wall)
+    if wall and kT > 0.0:
+        d, _ = rfd_sample(pos, rfd_seed, rfd_delta, a, eta, angular, wall)
+    else:
+        d = np.zeros((n, 3))
+    if first:
+        prev_u, prev_d = u, d
+    M = assemble(pos, a, eta, angular, wall=wall)
+    y = sqrt_exact(M, _f64(W).ravel())[: 3 * n].reshape(n, 3)
+    new = pos + dt * (1.5 * u - 0.5 * np.asarray(prev_u) + kT * (1.5 * d - 0.5 * np.asarray(prev_d))) \
+        + np.sqrt(2.0 * kT * dt) * y
+    return new, u, d
