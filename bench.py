@@ -462,6 +462,7 @@ def run_adjoint(args, ws, rank, local):
                        "forward_ms": fwd_ms, "backward_ms": float(np.mean(bwd)),
                        "backward_over_forward": float(np.mean(bwd)) / fwd_ms,
                        "pair_config": lm.lm_get_pair_config(solver),
+                       "adjoint_config": lm.lm_get_adjoint_config(solver),
                        "l2": "flushed by a 256 MB device write before every step"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,

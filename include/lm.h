@@ -157,6 +157,46 @@ lm_status lm_div_m(lm_solver *solver, void *lin_out, void *ang_out);
 lm_status lm_div_m_rfd(lm_solver *solver, uint64_t seed, double delta, void *lin_out, void *ang_out);
 
 /*
+ * lm_soft_repulsion -- forces of the soft steric potential of the roller
+ * example, Eq. (soft_potential) of Sec. 5.1,
+ *   U(r) = U0 (1 + (d - r)/b) for r < d,   U0 exp((d - r)/b) for r >= d,
+ * summed over every particle pair (d = d_pair, r = centre distance) and,
+ * for a single-wall solver, every particle-wall pair (d = d_wall, r = the
+ * height z of the centre).  forces_out (N x 3, overwritten) = -dU/dX at the
+ * positions last set; a coincident pair (r = 0) exerts no force.  b > 0;
+ * U0, d_pair, d_wall finite.  Direct O(N^2) sum on the GPU.
+ */
+lm_status lm_soft_repulsion(lm_solver *solver, double U0, double b, double d_pair, double d_wall,
+                            void *forces_out);
+
+/*
+ * lm_ab_step -- one step of the stochastic Adams-Bashforth scheme of
+ * Sec. 5.1 for the positions X (Eq. bdhi discretised):
+ *   X' = X + dt [(3/2) u^n - (1/2) u^{n-1} + kT ((3/2) d^n - (1/2) d^{n-1})]
+ *          + sqrt(2 kT dt) (M^{1/2} W)_lin,
+ * u^n = (M [F; T])_lin at the current positions, d^n = one random finite
+ * difference sample of divM (lm_div_m_rfd with key seed and the default
+ * delta; zero in the open geometry or at kT = 0), and the square root by
+ * the Lanczos method (lm_sqrt_mdot with tol, max_iter, seed).
+ *   forces, torques: F^n, T^n (N x 3, solver precision, host or device;
+ *     NULL = zero; torques only with angular blocks).
+ *   W: 3N (6N with angular blocks) normals, host or device, or NULL to draw
+ *     them from Philox with key seed (as lm_sqrt_mdot).
+ *   history: device array of 6N doubles, [u^{n-1} (3N); d^{n-1} (3N)], owned
+ *     by the caller; read unless first != 0, always overwritten with
+ *     (u^n, d^n).  first != 0 gives the Euler-Maruyama step (previous terms
+ *     equal to the current ones).
+ *   pos_out: N x 3 new positions (host or device); the solver's positions
+ *     are set to them as well (lm_set_positions).
+ *   iters_out: optional Lanczos iteration count.
+ * Returns the status of the Lanczos step (LM_ERR_NOT_CONVERGED with the
+ * positions updated from the last iterate).  Synchronises the stream.
+ */
+lm_status lm_ab_step(lm_solver *solver, const void *forces, const void *torques, const double *W,
+                     uint64_t seed, double kT, double dt, double tol, int max_iter, double *history,
+                     int first, void *pos_out, int *iters_out);
+
+/*
  * lm_mdot_backward -- adjoint of Mdot (not in the paper; the differentiable
  * form of the product).  For the scalar L = sum_i G_i . lin_i + H_i . ang_i
  * with [lin; ang] = M(X) [F; T] it writes
@@ -195,11 +235,22 @@ typedef struct {
 lm_status lm_get_pair_config(lm_solver *solver, lm_pair_config *cfg);
 lm_status lm_set_pair_config(lm_solver *solver, const lm_pair_config *cfg);
 
+/* lm_get_adjoint_config / lm_set_adjoint_config -- launch configuration of
+ * lm_mdot_backward for the current N.  LM_FP32C without angular blocks (the
+ * packed kernel): threads 128 or 256, ilp 2 or 4, packed = j-particles per
+ * overlap vote (1 or 2); otherwise threads 128, ilp 1 (LM_FP64) or 2
+ * (LM_FP32C with angular blocks), packed 0.  splits 0 = automatic.
+ * Unsupported combinations give LM_ERR_INVALID_ARG. */
+lm_status lm_get_adjoint_config(lm_solver *solver, lm_pair_config *cfg);
+lm_status lm_set_adjoint_config(lm_solver *solver, const lm_pair_config *cfg);
+
 /*
  * lm_autotune -- time every supported pair-kernel configuration for the
  * solver's precision, angular flag and current N (positions must be set),
  * keep the fastest, and return it in *best (nullable).  reps >= 1 timed
- * launches per candidate.  Synchronises the stream.
+ * launches per candidate.  For an LM_FP32C open solver without angular
+ * blocks it also times the configurations of the adjoint kernel and keeps
+ * the fastest (lm_get_adjoint_config).  Synchronises the stream.
  */
 lm_status lm_autotune(lm_solver *solver, int reps, lm_pair_config *best);
 

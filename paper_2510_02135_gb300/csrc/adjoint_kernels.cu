@@ -95,6 +95,21 @@ __device__ __forceinline__ bool exact_coef(R r2, const RpyConst<R>& k, Coef<R>& 
     return true;
 }
 
+// j-range split (as in the forward kernels): `splits` contiguous ranges of
+// whole tiles, as equal as possible; split k holds tiles [k T / s, (k + 1) T / s).
+inline int64_t adj_split_plan(int64_t N, int NT, int splits, int64_t* ntiles) {
+    if (splits < 1) splits = 1;
+    *ntiles = (N + NT - 1) / NT;
+    return splits < *ntiles ? splits : *ntiles;
+}
+
+__device__ __forceinline__ void split_range(int64_t N, int NT, int64_t ntiles, int64_t* jb, int64_t* je) {
+    const int64_t k = blockIdx.y, s = gridDim.y;
+    *jb = (k * ntiles / s) * NT;
+    const int64_t e = ((k + 1) * ntiles / s) * NT;
+    *je = e < N ? e : N;
+}
+
 template <typename R, bool ANG>
 struct IData {
     R x, y, z;
@@ -231,7 +246,7 @@ template <typename R, bool ANG, int NT, int NI>
 __global__ void __launch_bounds__(NT) rpy_adjoint_kernel(const typename V4<R>::type* __restrict__ pos4,
                                                          const void* __restrict__ Fp, const void* __restrict__ Tp,
                                                          const void* __restrict__ Gp, const void* __restrict__ Hp,
-                                                         int f64, int64_t N, int64_t jchunk, RpyConst<R> k, double c8,
+                                                         int f64, int64_t N, int64_t ntiles, RpyConst<R> k, double c8,
                                                          void* __restrict__ dX, void* __restrict__ dF,
                                                          void* __restrict__ dT, double* __restrict__ partials) {
     using R4 = typename V4<R>::type;
@@ -243,8 +258,8 @@ __global__ void __launch_bounds__(NT) rpy_adjoint_kernel(const typename V4<R>::t
     R* s_lo = s_hi + (sizeof(R) == 4 ? C * NI * NT : 0);
     const int tid = threadIdx.x;
     const int64_t i0 = (int64_t)blockIdx.x * (NT * NI);
-    const int64_t jb = (int64_t)blockIdx.y * jchunk;
-    const int64_t je = (jb + jchunk < N) ? (jb + jchunk) : N;
+    int64_t jb, je;
+    split_range(N, NT, ntiles, &jb, &je);
     const R pad = (R)kPadCoord;
 
     IData<R, ANG> I[NI];
@@ -366,7 +381,9 @@ __global__ void __launch_bounds__(NT) rpy_adjoint_kernel(const typename V4<R>::t
 //   dX_i += [A'/r (G_i.F_j + F_i.G_j) + B'/r ((G_i.d)(F_j.d) + (F_i.d)(G_j.d))] d
 //           + B (F_i.d) G_j + B (G_i.d) F_j
 //           + [B (F_j.d)] G_i + [B (G_j.d)] F_i        (scalars summed per tile)
-// with A'/r = -1/r^3 - 3 K1/r^5 and B'/r = -3/r^5 + 5 K2/r^7.
+// with A'/r = -1/r^3 - 3 K1/r^5 and B'/r = -3/r^5 + 5 K2/r^7.  UJ consecutive
+// j share one overlap vote, so that the far-field work of UJ j-particles is
+// one block of independent instructions.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -382,13 +399,14 @@ constexpr size_t adj_x2_smem_bytes() {
     return (size_t)kAdjX2Words * NT * sizeof(float4) + adj_running_bytes<float, false, NT, NI>();
 }
 
-template <int NT, int NI>
+template <int NT, int NI, int UJ>
 __global__ void __launch_bounds__(NT) rpy_adjoint_x2_kernel(const float4* __restrict__ pos4,
                                                             const void* __restrict__ Fp, const void* __restrict__ Gp,
-                                                            int f64, int64_t N, int64_t jchunk, RpyConst<float> k,
+                                                            int f64, int64_t N, int64_t ntiles, RpyConst<float> k,
                                                             double c8, void* __restrict__ dX, void* __restrict__ dF,
                                                             double* __restrict__ partials) {
     static_assert(NI % 2 == 0, "packed form needs an even number of i-particles per thread");
+    static_assert(NT % UJ == 0, "the j tile must hold whole groups of UJ");
     constexpr int NP = NI / 2;
     constexpr int C = 6;   // dX(3) dF(3)
     extern __shared__ __align__(16) unsigned char dyn_smem[];
@@ -397,8 +415,8 @@ __global__ void __launch_bounds__(NT) rpy_adjoint_x2_kernel(const float4* __rest
     float* s_lo = s_hi + C * NI * NT;
     const int tid = threadIdx.x;
     const int64_t i0 = (int64_t)blockIdx.x * (NT * NI);
-    const int64_t jb = (int64_t)blockIdx.y * jchunk;
-    const int64_t je = (jb + jchunk < N) ? (jb + jchunk) : N;
+    int64_t jb, je;
+    split_range(N, NT, ntiles, &jb, &je);
     const float pad = (float)kPadCoord;
 
     float2 xi[NP], yi[NP], zi[NP], Fi[NP][3], Gi[NP][3];
@@ -467,89 +485,102 @@ __global__ void __launch_bounds__(NT) rpy_adjoint_x2_kernel(const float4* __rest
         s_t[4 * NT + tid] = make_float4(nG.z, nG.z, 0.f, 0.f);
         __syncthreads();
         if (jt + NT < je) fetch(jt + NT + tid);
+        // UJ consecutive j share one overlap vote (more independent work per warp)
 #pragma unroll 1
-        for (int jj = 0; jj < NT; ++jj) {
-            const float4 w0 = s_t[0 * NT + jj], w1 = s_t[1 * NT + jj], w2 = s_t[2 * NT + jj];
-            const float4 w3 = s_t[3 * NT + jj], w4 = s_t[4 * NT + jj];
-            const float2 nx = lo2(w0), ny = hi2(w0), nz = lo2(w1);
-            const float2 Fx = hi2(w1), Fy = lo2(w2), Fz = hi2(w2);
-            const float2 Gx = lo2(w3), Gy = hi2(w3), Gz = lo2(w4);
-            float2 dx[NP], dy[NP], dz[NP], r2[NP];
+        for (int jj = 0; jj < NT; jj += UJ) {
+            float2 dx[UJ][NP], dy[UJ][NP], dz[UJ][NP], r2[UJ][NP];
             float mn;
 #pragma unroll
-            for (int pp = 0; pp < NP; ++pp) {
-                dx[pp] = add2(xi[pp], nx);
-                dy[pp] = add2(yi[pp], ny);
-                dz[pp] = add2(zi[pp], nz);
-                r2[pp] = fma2(dx[pp], dx[pp], fma2(dy[pp], dy[pp], mul2(dz[pp], dz[pp])));
-                const float m2 = fminf(r2[pp].x, r2[pp].y);
-                mn = (pp == 0) ? m2 : fminf(mn, m2);
-            }
-            if (__any_sync(0xffffffffu, mn < k.four_a2)) {
-                const float4 Fj = make_float4(Fx.x, Fy.x, Fz.x, 0.f), Gj = make_float4(Gx.x, Gy.x, Gz.x, 0.f);
+            for (int u = 0; u < UJ; ++u) {
+                const float4 w0 = s_t[0 * NT + jj + u], w1 = s_t[1 * NT + jj + u];
+                const float2 nx = lo2(w0), ny = hi2(w0), nz = lo2(w1);
 #pragma unroll
                 for (int pp = 0; pp < NP; ++pp) {
+                    dx[u][pp] = add2(xi[pp], nx);
+                    dy[u][pp] = add2(yi[pp], ny);
+                    dz[u][pp] = add2(zi[pp], nz);
+                    r2[u][pp] = fma2(dx[u][pp], dx[u][pp], fma2(dy[u][pp], dy[u][pp], mul2(dz[u][pp], dz[u][pp])));
+                    const float m2 = fminf(r2[u][pp].x, r2[u][pp].y);
+                    mn = (u == 0 && pp == 0) ? m2 : fminf(mn, m2);
+                }
+            }
+            if (__any_sync(0xffffffffu, mn < k.four_a2)) {
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        IData<float, false> I;
-                        AAcc<float, false> t;
-                        I.x = I.y = I.z = 0.f;
+                for (int u = 0; u < UJ; ++u) {
+                    const float4 w1 = s_t[1 * NT + jj + u], w2 = s_t[2 * NT + jj + u];
+                    const float4 w3 = s_t[3 * NT + jj + u], w4 = s_t[4 * NT + jj + u];
+                    const float4 Fj = make_float4(w1.z, w2.x, w2.z, 0.f), Gj = make_float4(w3.x, w3.z, w4.x, 0.f);
 #pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            I.F[c] = h ? Fi[pp][c].y : Fi[pp][c].x;
-                            I.G[c] = h ? Gi[pp][c].y : Gi[pp][c].x;
-                        }
+                    for (int pp = 0; pp < NP; ++pp) {
 #pragma unroll
-                        for (int c = 0; c < C; ++c) t.p[c] = 0.f;
-                        t.sG = t.sF = 0.f;
-                        Coef<float> cf;
-                        const float ddx = h ? dx[pp].y : dx[pp].x, ddy = h ? dy[pp].y : dy[pp].x;
-                        const float ddz = h ? dz[pp].y : dz[pp].x, rr = h ? r2[pp].y : r2[pp].x;
-                        const bool g = exact_coef<float, false>(rr, k, cf);
-                        adj_pair<float, false>(ddx, ddy, ddz, cf, g, Fj, Gj, Fj, Fj, I, t);
-                        if (h) {
+                        for (int h = 0; h < 2; ++h) {
+                            IData<float, false> I;
+                            AAcc<float, false> t;
+                            I.x = I.y = I.z = 0.f;
 #pragma unroll
-                            for (int c = 0; c < C; ++c) p[pp][c].y += t.p[c];
-                            sG[pp].y += t.sG;
-                            sF[pp].y += t.sF;
-                        } else {
+                            for (int c = 0; c < 3; ++c) {
+                                I.F[c] = h ? Fi[pp][c].y : Fi[pp][c].x;
+                                I.G[c] = h ? Gi[pp][c].y : Gi[pp][c].x;
+                            }
 #pragma unroll
-                            for (int c = 0; c < C; ++c) p[pp][c].x += t.p[c];
-                            sG[pp].x += t.sG;
-                            sF[pp].x += t.sF;
+                            for (int c = 0; c < C; ++c) t.p[c] = 0.f;
+                            t.sG = t.sF = 0.f;
+                            Coef<float> cf;
+                            const float ddx = h ? dx[u][pp].y : dx[u][pp].x, ddy = h ? dy[u][pp].y : dy[u][pp].x;
+                            const float ddz = h ? dz[u][pp].y : dz[u][pp].x, rr = h ? r2[u][pp].y : r2[u][pp].x;
+                            const bool g = exact_coef<float, false>(rr, k, cf);
+                            adj_pair<float, false>(ddx, ddy, ddz, cf, g, Fj, Gj, Fj, Fj, I, t);
+                            if (h) {
+#pragma unroll
+                                for (int c = 0; c < C; ++c) p[pp][c].y += t.p[c];
+                                sG[pp].y += t.sG;
+                                sF[pp].y += t.sF;
+                            } else {
+#pragma unroll
+                                for (int c = 0; c < C; ++c) p[pp][c].x += t.p[c];
+                                sG[pp].x += t.sG;
+                                sF[pp].x += t.sF;
+                            }
                         }
                     }
                 }
             } else {
 #pragma unroll
-                for (int pp = 0; pp < NP; ++pp) {
-                    const float2 invr = make_float2(rsqrtf(r2[pp].x), rsqrtf(r2[pp].y));
-                    const float2 invr2 = mul2(invr, invr);
-                    const float2 invr3 = mul2(invr2, invr);
-                    const float2 invr5 = mul2(invr3, invr2);
-                    const float2 invr7 = mul2(invr5, invr2);
-                    const float2 A = fma2(K1, invr3, invr);
-                    const float2 B = fma2(nK2, invr5, invr3);
-                    const float2 Ap = fma2(m3K1, invr5, mul2(m1, invr3));
-                    const float2 Bp = fma2(K2x5, invr7, mul2(m3, invr5));
-                    const float2 b1 = fma2(Fx, dx[pp], fma2(Fy, dy[pp], mul2(Fz, dz[pp])));   // F_j.d
-                    const float2 b2 = fma2(Gx, dx[pp], fma2(Gy, dy[pp], mul2(Gz, dz[pp])));   // G_j.d
-                    const float2 Bb2 = mul2(B, b2);
-                    p[pp][3] = fma2(Bb2, dx[pp], fma2(A, Gx, p[pp][3]));
-                    p[pp][4] = fma2(Bb2, dy[pp], fma2(A, Gy, p[pp][4]));
-                    p[pp][5] = fma2(Bb2, dz[pp], fma2(A, Gz, p[pp][5]));
-                    const float2 a1 = fma2(Gi[pp][0], dx[pp], fma2(Gi[pp][1], dy[pp], mul2(Gi[pp][2], dz[pp])));
-                    const float2 a2 = fma2(Fi[pp][0], dx[pp], fma2(Fi[pp][1], dy[pp], mul2(Fi[pp][2], dz[pp])));
-                    const float2 S1 = fma2(Gi[pp][0], Fx, fma2(Gi[pp][1], Fy, fma2(Gi[pp][2], Fz,
-                                      fma2(Fi[pp][0], Gx, fma2(Fi[pp][1], Gy, mul2(Fi[pp][2], Gz))))));
-                    const float2 S2 = fma2(a1, b1, mul2(a2, b2));
-                    const float2 cd = fma2(Ap, S1, mul2(Bp, S2));
-                    const float2 Ba2 = mul2(B, a2), Ba1 = mul2(B, a1);
-                    sG[pp] = fma2(B, b1, sG[pp]);
-                    sF[pp] = add2(sF[pp], Bb2);
-                    p[pp][0] = fma2(cd, dx[pp], fma2(Ba2, Gx, fma2(Ba1, Fx, p[pp][0])));
-                    p[pp][1] = fma2(cd, dy[pp], fma2(Ba2, Gy, fma2(Ba1, Fy, p[pp][1])));
-                    p[pp][2] = fma2(cd, dz[pp], fma2(Ba2, Gz, fma2(Ba1, Fz, p[pp][2])));
+                for (int u = 0; u < UJ; ++u) {
+                    const float4 w1 = s_t[1 * NT + jj + u], w2 = s_t[2 * NT + jj + u];
+                    const float4 w3 = s_t[3 * NT + jj + u], w4 = s_t[4 * NT + jj + u];
+                    const float2 Fx = hi2(w1), Fy = lo2(w2), Fz = hi2(w2);
+                    const float2 Gx = lo2(w3), Gy = hi2(w3), Gz = lo2(w4);
+#pragma unroll
+                    for (int pp = 0; pp < NP; ++pp) {
+                        const float2 ddx = dx[u][pp], ddy = dy[u][pp], ddz = dz[u][pp];
+                        const float2 invr = make_float2(rsqrtf(r2[u][pp].x), rsqrtf(r2[u][pp].y));
+                        const float2 invr2 = mul2(invr, invr);
+                        const float2 invr3 = mul2(invr2, invr);
+                        const float2 invr5 = mul2(invr3, invr2);
+                        const float2 A = fma2(K1, invr3, invr);
+                        const float2 B = fma2(nK2, invr5, invr3);
+                        const float2 Ap = mul2(invr3, fma2(m3K1, invr2, m1));    // -1/r^3 - 3 K1/r^5
+                        const float2 Bp = mul2(invr5, fma2(K2x5, invr2, m3));    // -3/r^5 + 5 K2/r^7
+                        const float2 b1 = fma2(Fx, ddx, fma2(Fy, ddy, mul2(Fz, ddz)));   // F_j.d
+                        const float2 b2 = fma2(Gx, ddx, fma2(Gy, ddy, mul2(Gz, ddz)));   // G_j.d
+                        const float2 Bb2 = mul2(B, b2);
+                        p[pp][3] = fma2(Bb2, ddx, fma2(A, Gx, p[pp][3]));
+                        p[pp][4] = fma2(Bb2, ddy, fma2(A, Gy, p[pp][4]));
+                        p[pp][5] = fma2(Bb2, ddz, fma2(A, Gz, p[pp][5]));
+                        const float2 a1 = fma2(Gi[pp][0], ddx, fma2(Gi[pp][1], ddy, mul2(Gi[pp][2], ddz)));
+                        const float2 a2 = fma2(Fi[pp][0], ddx, fma2(Fi[pp][1], ddy, mul2(Fi[pp][2], ddz)));
+                        const float2 S1 = fma2(Gi[pp][0], Fx, fma2(Gi[pp][1], Fy, fma2(Gi[pp][2], Fz,
+                                          fma2(Fi[pp][0], Gx, fma2(Fi[pp][1], Gy, mul2(Fi[pp][2], Gz))))));
+                        const float2 S2 = fma2(a1, b1, mul2(a2, b2));
+                        const float2 cd = fma2(Ap, S1, mul2(Bp, S2));
+                        const float2 Ba2 = mul2(B, a2), Ba1 = mul2(B, a1);
+                        sG[pp] = fma2(B, b1, sG[pp]);
+                        sF[pp] = add2(sF[pp], Bb2);
+                        p[pp][0] = fma2(cd, ddx, fma2(Ba2, Gx, fma2(Ba1, Fx, p[pp][0])));
+                        p[pp][1] = fma2(cd, ddy, fma2(Ba2, Gy, fma2(Ba1, Fy, p[pp][1])));
+                        p[pp][2] = fma2(cd, ddz, fma2(Ba2, Gz, fma2(Ba1, Fz, p[pp][2])));
+                    }
                 }
             }
         }
@@ -606,21 +637,13 @@ __global__ void adj_reduce_kernel(const double* __restrict__ partials, int split
     else static_cast<float*>(out)[idx] = (float)(c8 * s);
 }
 
-int64_t adj_split_plan(int64_t N, int NT, int splits, int64_t* jchunk) {
-    if (splits < 1) splits = 1;
-    const int64_t ntiles = (N + NT - 1) / NT;
-    if (splits > ntiles) splits = (int)ntiles;
-    const int64_t tps = (ntiles + splits - 1) / splits;
-    *jchunk = tps * NT;
-    return (N + *jchunk - 1) / *jchunk;
-}
 
 template <typename R, bool ANG, int NI>
 cudaError_t launch_adj_t(const AdjointArgs& a, cudaStream_t s) {
     constexpr int NT = 128;
     const int64_t nblk = (a.N + NT * NI - 1) / (NT * NI);
-    int64_t jchunk = 0;
-    const int splits = (int)adj_split_plan(a.N, NT, a.splits, &jchunk);
+    int64_t ntiles = 0;
+    const int splits = (int)adj_split_plan(a.N, NT, a.splits, &ntiles);
     if (nblk > 0x7fffffff || splits > 65535) return cudaErrorInvalidConfiguration;
     if (splits > 1 && a.partials == nullptr) return cudaErrorInvalidValue;
     const double c8 = 1.0 / (8.0 * 3.14159265358979323846 * a.eta);
@@ -636,7 +659,7 @@ cudaError_t launch_adj_t(const AdjointArgs& a, cudaStream_t s) {
     }
     rpy_adjoint_kernel<R, ANG, NT, NI><<<grid, NT, dyn, s>>>(static_cast<const typename V4<R>::type*>(a.pos4), a.F,
                                                        ANG ? a.T : nullptr, a.G, ANG ? a.H : nullptr, a.fp64, a.N,
-                                                       jchunk, k, c8, a.dX, a.dF, ANG ? a.dT : nullptr, a.partials);
+                                                       ntiles, k, c8, a.dX, a.dF, ANG ? a.dT : nullptr, a.partials);
     cudaError_t err = cudaGetLastError();
     count_launches(1);
     if (err != cudaSuccess || splits == 1) return err;
@@ -648,12 +671,11 @@ cudaError_t launch_adj_t(const AdjointArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int NI>
+template <int NT, int NI, int UJ>
 cudaError_t launch_adj_x2_t(const AdjointArgs& a, cudaStream_t s) {
-    constexpr int NT = 128;
     const int64_t nblk = (a.N + NT * NI - 1) / (NT * NI);
-    int64_t jchunk = 0;
-    const int splits = (int)adj_split_plan(a.N, NT, a.splits, &jchunk);
+    int64_t ntiles = 0;
+    const int splits = (int)adj_split_plan(a.N, NT, a.splits, &ntiles);
     if (nblk > 0x7fffffff || splits > 65535) return cudaErrorInvalidConfiguration;
     if (splits > 1 && a.partials == nullptr) return cudaErrorInvalidValue;
     const double c8 = 1.0 / (8.0 * 3.14159265358979323846 * a.eta);
@@ -662,13 +684,13 @@ cudaError_t launch_adj_x2_t(const AdjointArgs& a, cudaStream_t s) {
     constexpr size_t dyn = adj_x2_smem_bytes<NT, NI>();
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(rpy_adjoint_x2_kernel<NT, NI>,
+        cudaError_t e = cudaFuncSetAttribute(rpy_adjoint_x2_kernel<NT, NI, UJ>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    rpy_adjoint_x2_kernel<NT, NI><<<grid, NT, dyn, s>>>(static_cast<const float4*>(a.pos4), a.F, a.G, a.fp64, a.N,
-                                                        jchunk, k, c8, a.dX, a.dF, a.partials);
+    rpy_adjoint_x2_kernel<NT, NI, UJ><<<grid, NT, dyn, s>>>(static_cast<const float4*>(a.pos4), a.F, a.G, a.fp64, a.N,
+                                                        ntiles, k, c8, a.dX, a.dF, a.partials);
     cudaError_t err = cudaGetLastError();
     count_launches(1);
     if (err != cudaSuccess || splits == 1) return err;
@@ -679,25 +701,57 @@ cudaError_t launch_adj_x2_t(const AdjointArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Packed translation adjoint configurations: threads {128, 256} x ilp {2, 4}
+// x j per vote {1, 2} (AdjointArgs::uj).
+template <int NT, int NI>
+cudaError_t launch_adj_x2_u(const AdjointArgs& a, cudaStream_t s) {
+    return a.uj == 2 ? launch_adj_x2_t<NT, NI, 2>(a, s) : launch_adj_x2_t<NT, NI, 1>(a, s);
+}
+
+cudaError_t launch_adj_x2(const AdjointArgs& a, cudaStream_t s) {
+    if (a.threads == 128 && a.ilp == 2) return launch_adj_x2_u<128, 2>(a, s);
+    if (a.threads == 128 && a.ilp == 4) return launch_adj_x2_u<128, 4>(a, s);
+    if (a.threads == 256 && a.ilp == 2) return launch_adj_x2_u<256, 2>(a, s);
+    if (a.threads == 256 && a.ilp == 4) return launch_adj_x2_u<256, 4>(a, s);
+    return cudaErrorInvalidConfiguration;
+}
+
+template <int NT, int NI, int UJ>
+int adj_x2_occupancy() {
+    int n = 0;
+    constexpr size_t dyn = adj_x2_smem_bytes<NT, NI>();
+    cudaError_t e = cudaFuncSetAttribute(rpy_adjoint_x2_kernel<NT, NI, UJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dyn);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rpy_adjoint_x2_kernel<NT, NI, UJ>, NT, dyn);
+    return e == cudaSuccess ? n : 0;
+}
+
 }  // namespace
 
 int adjoint_partial_components(int angular) { return angular ? 9 : 6; }
 
-// i-particles per thread: FP32 translation 4, FP32 with angular blocks 2,
-// FP64 1 (register budget of the heavier angular and FP64 adjoints).
+// i-particles per thread: FP32 translation 4 (packed; tunable), FP32 with
+// angular blocks 2, FP64 1 (register budget of the heavier angular and FP64
+// adjoints).
 int adjoint_ilp(int fp64, int angular) { return fp64 ? 1 : (angular ? 2 : 4); }
+
+bool adjoint_config_supported(int fp64, int angular, int threads, int ilp, int uj) {
+    if (fp64 || angular) return threads == 128 && ilp == adjoint_ilp(fp64, angular) && uj <= 1;
+    return (threads == 128 || threads == 256) && (ilp == 2 || ilp == 4) && (uj == 0 || uj == 1 || uj == 2);
+}
 
 cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s) {
     if (a.N <= 0) return cudaSuccess;
-    if (a.threads != 128) return cudaErrorInvalidConfiguration;
+    if (!adjoint_config_supported(a.fp64, a.angular, a.threads, a.ilp, a.uj)) return cudaErrorInvalidConfiguration;
     if (a.fp64) return a.angular ? launch_adj_t<double, true, 1>(a, s) : launch_adj_t<double, false, 1>(a, s);
     // FP32: translation blocks use the packed (f32x2) kernel
-    return a.angular ? launch_adj_t<float, true, 2>(a, s) : launch_adj_x2_t<4>(a, s);
+    return a.angular ? launch_adj_t<float, true, 2>(a, s) : launch_adj_x2(a, s);
 }
 
-int adjoint_ctas_per_sm(int fp64, int angular) {
+int adjoint_ctas_per_sm(int fp64, int angular, int threads, int ilp, int uj) {
     int n = 0;
     cudaError_t e = cudaErrorInvalidConfiguration;
+    if (!adjoint_config_supported(fp64, angular, threads, ilp, uj)) return 0;
 #define LM_AOCC(R, ANG, NI)                                                                       \
     {                                                                                             \
         constexpr size_t dyn = adj_running_bytes<R, ANG, 128, NI>();                              \
@@ -710,10 +764,12 @@ int adjoint_ctas_per_sm(int fp64, int angular) {
     else if (fp64) LM_AOCC(double, false, 1)
     else if (angular) LM_AOCC(float, true, 2)
     else {
-        constexpr size_t dyn = adj_x2_smem_bytes<128, 4>();
-        e = cudaFuncSetAttribute(rpy_adjoint_x2_kernel<128, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rpy_adjoint_x2_kernel<128, 4>, 128, dyn);
+        const bool two = uj == 2;
+        if (threads == 128 && ilp == 2) return two ? adj_x2_occupancy<128, 2, 2>() : adj_x2_occupancy<128, 2, 1>();
+        if (threads == 128 && ilp == 4) return two ? adj_x2_occupancy<128, 4, 2>() : adj_x2_occupancy<128, 4, 1>();
+        if (threads == 256 && ilp == 2) return two ? adj_x2_occupancy<256, 2, 2>() : adj_x2_occupancy<256, 2, 1>();
+        if (threads == 256 && ilp == 4) return two ? adj_x2_occupancy<256, 4, 2>() : adj_x2_occupancy<256, 4, 1>();
+        return 0;
     }
 #undef LM_AOCC
     return e == cudaSuccess ? n : 0;

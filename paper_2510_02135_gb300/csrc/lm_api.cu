@@ -143,8 +143,10 @@ struct lm_solver {
     DBuf out_stage[3];
     DBuf flag;
     DBuf tune_in, tune_out;
-    // single wall: the caller's positions (for random finite differences) and RFD scratch
+    // the caller's positions (N x 3, solver precision) and RFD scratch
     DBuf pos_raw, rfd_pos4, rfd_W, rfd_P, rfd_Q;
+    // Adams-Bashforth step scratch: M [F; T] and the scaled square root (6N doubles / 6N values), new positions
+    DBuf ab_u, ab_d, ab_y, ab_x;
     uint64_t rfd_calls = 0;
 
     // Lanczos state
@@ -173,7 +175,7 @@ struct lm_solver {
     ~lm_solver() {
         DBuf* all[] = {&pos4, &partials, &in_stage[0], &in_stage[1], &in_stage[2], &in_stage[3],
                        &out_stage[0], &out_stage[1], &out_stage[2], &flag, &tune_in, &tune_out,
-                       &pos_raw, &rfd_pos4, &rfd_W, &rfd_P, &rfd_Q,
+                       &pos_raw, &rfd_pos4, &rfd_W, &rfd_P, &rfd_Q, &ab_u, &ab_d, &ab_y, &ab_x,
                        &V, &w, &y, &red, &scal, &zbuf, &cbuf, &Wbuf};
         for (DBuf* b : all) b->release();
         if (pinned) cudaFreeHost(pinned);
@@ -234,7 +236,8 @@ lm_status finish_out(lm_solver* s, OutView* views, int nv) {
 }  // namespace
 
 // Split count minimising (waves x tiles per CTA): keeps all SMs busy when N
-// is small and limits the tail wave when N is large.
+// is small and limits the tail wave when N is large.  Split k of s holds
+// tiles [k T / s, (k + 1) T / s), so a CTA holds at most ceil(T / s) tiles.
 int lmk::auto_splits(int64_t N, int threads, int ilp, int slots) {
     const int64_t nblk = (N + (int64_t)threads * ilp - 1) / ((int64_t)threads * ilp);
     const int64_t ntiles = (N + threads - 1) / threads;
@@ -243,11 +246,10 @@ int lmk::auto_splits(int64_t N, int threads, int ilp, int slots) {
     for (int s = 1; s <= 64 && s <= ntiles; ++s) {
         const int64_t tps = (ntiles + s - 1) / s;
         if (s > 1 && tps < 4) break;
-        const int64_t se = (ntiles + tps - 1) / tps;
-        const int64_t items = nblk * se;
+        const int64_t items = nblk * s;
         const int64_t waves = (items + slots - 1) / std::max(1, slots);
-        const double cost = (double)waves * (double)tps * (1.0 + 0.002 * (double)se);
-        if (cost < best_cost - 1e-9) { best_cost = cost; best = (int)se; }
+        const double cost = (double)waves * (double)tps * (1.0 + 0.002 * (double)s);
+        if (cost < best_cost - 1e-9) { best_cost = cost; best = s; }
     }
     return best;
 }
@@ -261,8 +263,26 @@ bool pair_config_supported(const lm_solver* s, int threads, int ilp, int packed)
 }
 
 int pair_ctas_per_sm(const lm_solver* s, int threads, int ilp, int packed) {
-    return s->wall ? lmk::wall_ctas_per_sm(s->fp64, s->angular, threads, ilp)
+    return s->wall ? lmk::wall_ctas_per_sm(s->fp64, s->angular, threads, ilp, packed)
                    : lmk::mdot_ctas_per_sm(s->fp64, s->angular, threads, ilp, packed);
+}
+
+// Split counts the autotuner times for one tiling: the model's choice, half,
+// one and a half and twice it, and the counts that make the CTA count a whole
+// number (1..4) of waves of `slots` resident CTAs.
+std::vector<int> split_candidates(int64_t N, int threads, int ilp, int slots) {
+    const int64_t nblk = (N + (int64_t)threads * ilp - 1) / ((int64_t)threads * ilp);
+    const int64_t ntiles = (N + threads - 1) / threads;
+    const int sa = auto_splits(N, threads, ilp, slots);
+    std::vector<int> c = {sa, std::max(1, sa / 2), std::max(1, (3 * sa) / 2), sa * 2};
+    for (int w = 1; w <= 4; ++w) {
+        const int64_t sp = ((int64_t)w * slots) / std::max<int64_t>(1, nblk);
+        if (sp >= 1 && sp <= ntiles && sp <= 256 && sp * nblk == (int64_t)w * slots) c.push_back((int)sp);
+    }
+    std::vector<int> out;
+    for (int v : c)
+        if (std::find(out.begin(), out.end(), v) == out.end()) out.push_back(v);
+    return out;
 }
 
 lm_pair_config default_config(const lm_solver* s, int64_t N) {
@@ -273,10 +293,10 @@ lm_pair_config default_config(const lm_solver* s, int64_t N) {
     c.ilp = s->fp64 ? (s->angular ? 1 : 2) : (s->angular ? 4 : 8);
     c.packed = s->fp64 ? 0 : 1;
     if (s->wall) {
-        // single wall: scalar form, FP32 128 x 2, FP64 128 x 1
-        c.threads = 128;
-        c.ilp = s->fp64 ? 1 : 2;
-        c.packed = 0;
+        // single wall: FP32 packed 256 x 4 (translation) / 256 x 2 (all blocks), FP64 scalar 128 x 1
+        c.threads = s->fp64 ? 128 : 256;
+        c.ilp = s->fp64 ? 1 : (s->angular ? 2 : 4);
+        c.packed = s->fp64 ? 0 : 1;
     }
     int occ = pair_ctas_per_sm(s, c.threads, c.ilp, c.packed);
     if (occ < 1) occ = 1;
@@ -340,11 +360,90 @@ lm_status check_solver(lm_solver* s, bool need_pos) {
     return LM_OK;
 }
 
+// One random finite difference sample of div M (Eq. rfd) into device
+// buffers lin / ang (element type by out_f64), wall geometry.
+lm_status rfd_sample(lm_solver* s, uint64_t seed, double delta, void* lin, void* ang, int out_f64);
+
 bool valid_name(const char* p) {
     return p && (!strcmp(p, "open") || !strcmp(p, "periodic") || !strcmp(p, "single_wall") ||
                  !strcmp(p, "two_walls"));
 }
 
+}  // namespace
+
+namespace {
+// Adjoint launch configuration: packed = 0 for the scalar FP64 / angular
+// kernels; for the packed FP32 translation kernel, packed = j-particles per
+// overlap vote (1 or 2).
+lm_pair_config default_adjoint_config(const lm_solver* s) {
+    lm_pair_config c{128, lmk::adjoint_ilp(s->fp64, s->angular), 1, (!s->fp64 && !s->angular) ? 1 : 0};
+    const int occ = std::max(1, lmk::adjoint_ctas_per_sm(s->fp64, s->angular, c.threads, c.ilp, c.packed));
+    c.splits = auto_splits(s->N, c.threads, c.ilp, occ * s->sm_count);
+    return c;
+}
+
+void ensure_adjoint_config(lm_solver* s) {
+    if (s->adj_cfg_N == s->N) return;
+    s->adj_cfg = default_adjoint_config(s);
+    s->adj_cfg_N = s->N;
+}
+
+lm_status run_adjoint(lm_solver* s, const void* F, const void* T, const void* G, const void* H, void* dX, void* dF,
+                      void* dT, const lm_pair_config& cfg) {
+    lmk::AdjointArgs a;
+    a.fp64 = s->fp64;
+    a.angular = s->angular;
+    a.N = s->N;
+    a.pos4 = s->pos4.p;
+    a.F = F; a.T = T; a.G = G; a.H = H;
+    a.dX = dX; a.dF = dF; a.dT = dT;
+    a.a = s->a;
+    a.eta = s->eta;
+    a.threads = cfg.threads;
+    a.ilp = cfg.ilp;
+    a.uj = cfg.packed > 0 ? cfg.packed : 1;
+    a.splits = cfg.splits;
+    a.partials = nullptr;
+    const int64_t se = lmk::mdot_effective_splits(s->N, a.threads, a.splits);
+    if (se > 1) {
+        const size_t pb = (size_t)se * lmk::adjoint_partial_components(s->angular) * (size_t)s->N * sizeof(double);
+        LM_CUDA(s->partials.ensure(pb), "allocating split partial sums");
+        a.partials = s->partials.as<double>();
+    }
+    LM_CUDA(lmk::launch_adjoint(a, s->stream), "adjoint kernel");
+    return LM_OK;
+}
+}  // namespace
+
+namespace {
+lm_status rfd_sample(lm_solver* s, uint64_t seed, double delta, void* lin, void* ang, int out_f64) {
+    const int64_t N = s->N;
+    const size_t nvec = (size_t)(s->angular ? 6 : 3) * N;
+    LM_CUDA(s->rfd_W.ensure(nvec * sizeof(double)), "allocating RFD scratch");
+    LM_CUDA(s->rfd_P.ensure(nvec * sizeof(double)), "allocating RFD scratch");
+    LM_CUDA(s->rfd_Q.ensure(nvec * sizeof(double)), "allocating RFD scratch");
+    LM_CUDA(s->rfd_pos4.ensure((size_t)N * (s->fp64 ? sizeof(lmk::dvec4) : sizeof(float4))), "allocating RFD scratch");
+    double* W = s->rfd_W.as<double>();
+    // W: 3N normals (translational part); the torque part stays zero, since
+    // the mobility of spheres does not depend on their orientation.
+    LM_CUDA(cudaMemsetAsync(W, 0, nvec * sizeof(double), s->stream), "RFD noise");
+    LM_CUDA(lmk::lz_philox_normals(seed, kRfdStream, W, 3 * N, s->stream), "RFD noise");
+    ensure_config(s);
+    for (int side = 0; side < 2; ++side) {
+        const double scale = side == 0 ? 0.5 * delta : -0.5 * delta;
+        LM_CUDA(lmk::launch_displace_pack_wall(s->pos_raw.p, s->fp64, W, scale, N, s->a, s->rfd_pos4.p, s->fp64,
+                                               s->stream),
+                "RFD positions");
+        double* out = side == 0 ? s->rfd_P.as<double>() : s->rfd_Q.as<double>();
+        if (lm_status st = run_mdot(s, W, s->angular ? W + 3 * N : nullptr, 1, out, s->angular ? out + 3 * N : nullptr,
+                                    1, s->cfg, s->rfd_pos4.p))
+            return st;
+    }
+    LM_CUDA(lmk::launch_rfd_difference(s->rfd_P.as<double>(), s->rfd_Q.as<double>(), 1.0 / delta, N, s->angular,
+                                       lin, ang, out_f64, s->stream),
+            "RFD difference");
+    return LM_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -435,10 +534,9 @@ lm_status lm_set_positions(lm_solver* s, const void* pos, int64_t N) {
     LM_CUDA(cudaStreamSynchronize(s->stream), "set_positions");
     memcpy(&bad, &s->pinned[0], sizeof(int));
     if (bad) return fail(LM_ERR_NONFINITE, "positions contain NaN/Inf or |x| > 1e15");
-    if (s->wall) {
-        LM_CUDA(s->pos_raw.ensure(bytes), "allocating positions");
-        LM_CUDA(cudaMemcpyAsync(s->pos_raw.p, dpos, bytes, cudaMemcpyDeviceToDevice, s->stream), "copying positions");
-    }
+    // the caller's positions as given (random finite differences, steric forces, time steps)
+    LM_CUDA(s->pos_raw.ensure(bytes), "allocating positions");
+    LM_CUDA(cudaMemcpyAsync(s->pos_raw.p, dpos, bytes, cudaMemcpyDeviceToDevice, s->stream), "copying positions");
     s->N = N;
     s->has_pos = true;
     return LM_OK;
@@ -476,35 +574,11 @@ lm_status lm_div_m_rfd(lm_solver* s, uint64_t seed, double delta, void* lin_out,
     if (!(delta > 0.0) || !std::isfinite(delta)) return fail(LM_ERR_INVALID_ARG, "delta must be > 0");
     if (!s->wall) return lm_div_m(s, lin_out, ang_out);   // open geometry: exactly zero
     DeviceGuard g(s->device);
-    const int64_t N = s->N;
-    const size_t bytes = (size_t)N * 3 * elem_size(s);
-    const size_t nvec = (size_t)(s->angular ? 6 : 3) * N;
+    const size_t bytes = (size_t)s->N * 3 * elem_size(s);
     OutView ov[2];
     if (lm_status st = stage_out(s, lin_out, bytes, 0, &ov[0])) return st;
     if (lm_status st = stage_out(s, ang_out, bytes, 1, &ov[1])) return st;
-    LM_CUDA(s->rfd_W.ensure(nvec * sizeof(double)), "allocating RFD scratch");
-    LM_CUDA(s->rfd_P.ensure(nvec * sizeof(double)), "allocating RFD scratch");
-    LM_CUDA(s->rfd_Q.ensure(nvec * sizeof(double)), "allocating RFD scratch");
-    LM_CUDA(s->rfd_pos4.ensure((size_t)N * (s->fp64 ? sizeof(lmk::dvec4) : sizeof(float4))), "allocating RFD scratch");
-    double* W = s->rfd_W.as<double>();
-    // W: 3N normals (translational part); the torque part stays zero, since
-    // the mobility of spheres does not depend on their orientation.
-    LM_CUDA(cudaMemsetAsync(W, 0, nvec * sizeof(double), s->stream), "RFD noise");
-    LM_CUDA(lmk::lz_philox_normals(seed, kRfdStream, W, 3 * N, s->stream), "RFD noise");
-    ensure_config(s);
-    for (int side = 0; side < 2; ++side) {
-        const double scale = side == 0 ? 0.5 * delta : -0.5 * delta;
-        LM_CUDA(lmk::launch_displace_pack_wall(s->pos_raw.p, s->fp64, W, scale, N, s->a, s->rfd_pos4.p, s->fp64,
-                                               s->stream),
-                "RFD positions");
-        double* out = side == 0 ? s->rfd_P.as<double>() : s->rfd_Q.as<double>();
-        if (lm_status st = run_mdot(s, W, s->angular ? W + 3 * N : nullptr, 1, out, s->angular ? out + 3 * N : nullptr,
-                                    1, s->cfg, s->rfd_pos4.p))
-            return st;
-    }
-    LM_CUDA(lmk::launch_rfd_difference(s->rfd_P.as<double>(), s->rfd_Q.as<double>(), 1.0 / delta, N, s->angular,
-                                       ov[0].dev, ov[1].dev, s->fp64, s->stream),
-            "RFD difference");
+    if (lm_status st = rfd_sample(s, seed, delta, ov[0].dev, ov[1].dev, s->fp64)) return st;
     return finish_out(s, ov, 2);
 }
 
@@ -526,6 +600,82 @@ lm_status lm_div_m(lm_solver* s, void* lin_out, void* ang_out) {
     LM_CUDA(cudaMemsetAsync(ov[0].dev, 0, bytes, s->stream), "zero output");
     if (s->angular) LM_CUDA(cudaMemsetAsync(ov[1].dev, 0, bytes, s->stream), "zero output");
     return finish_out(s, ov, 2);
+}
+
+lm_status lm_soft_repulsion(lm_solver* s, double U0, double b, double d_pair, double d_wall, void* forces_out) {
+    if (lm_status st = check_solver(s, true)) return st;
+    if (forces_out == nullptr) return fail(LM_ERR_INVALID_ARG, "forces_out is NULL");
+    if (!std::isfinite(U0) || !(b > 0.0) || !std::isfinite(b) || !std::isfinite(d_pair) || !std::isfinite(d_wall))
+        return fail(LM_ERR_INVALID_ARG, "U0, d_pair, d_wall must be finite and b > 0");
+    DeviceGuard g(s->device);
+    const size_t bytes = (size_t)s->N * 3 * elem_size(s);
+    OutView ov[1];
+    if (lm_status st = stage_out(s, forces_out, bytes, 0, &ov[0])) return st;
+    LM_CUDA(lmk::launch_soft_repulsion(s->pos_raw.p, s->fp64, s->N, U0, b, d_pair, d_wall, s->wall, ov[0].dev,
+                                       s->stream),
+            "soft repulsion kernel");
+    return finish_out(s, ov, 1);
+}
+
+lm_status lm_ab_step(lm_solver* s, const void* forces, const void* torques, const double* W, uint64_t seed,
+                     double kT, double dt, double tol, int max_iter, double* history, int first, void* pos_out,
+                     int* iters_out) {
+    if (lm_status st = check_solver(s, true)) return st;
+    if (pos_out == nullptr) return fail(LM_ERR_INVALID_ARG, "pos_out is NULL");
+    if (history == nullptr || !is_device_ptr(history))
+        return fail(LM_ERR_INVALID_ARG, "history must be a device array of 6N doubles");
+    if (!s->angular && torques != nullptr) return fail(LM_ERR_INVALID_ARG, "torques given but include_angular is 0");
+    if (!(kT >= 0.0) || !std::isfinite(kT)) return fail(LM_ERR_INVALID_ARG, "kT must be finite and >= 0");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(LM_ERR_INVALID_ARG, "dt must be > 0");
+    DeviceGuard g(s->device);
+    if (iters_out) *iters_out = 0;
+    const int64_t N = s->N;
+    const size_t n3 = (size_t)3 * N;
+    const size_t bytes = n3 * elem_size(s);
+    const void *dF = nullptr, *dT = nullptr;
+    if (lm_status st = stage_in(s, forces, bytes, 1, &dF)) return st;
+    if (lm_status st = stage_in(s, torques, bytes, 2, &dT)) return st;
+    LM_CUDA(s->ab_u.ensure(2 * n3 * sizeof(double)), "allocating step scratch");
+    LM_CUDA(s->ab_d.ensure(2 * n3 * sizeof(double)), "allocating step scratch");
+    LM_CUDA(s->ab_y.ensure(2 * n3 * sizeof(double)), "allocating step scratch");
+    LM_CUDA(s->ab_x.ensure(bytes), "allocating step scratch");
+    double* u = s->ab_u.as<double>();
+    double* d = s->ab_d.as<double>();
+    // u = (M [F; T])_lin (FP64)
+    if (dF == nullptr && dT == nullptr) {
+        LM_CUDA(cudaMemsetAsync(u, 0, 2 * n3 * sizeof(double), s->stream), "zero velocities");
+    } else {
+        ensure_config(s);
+        if (lm_status st = run_mdot(s, dF, dT, s->fp64, u, s->angular ? u + n3 : nullptr, 1, s->cfg)) return st;
+    }
+    // d = one RFD sample of div M (single wall, kT > 0; zero otherwise)
+    const bool drift = s->wall && kT > 0.0;
+    if (drift) {
+        const double delta = (s->fp64 ? kRfdDeltaFP64 : kRfdDeltaFP32) * s->a;
+        if (lm_status st = rfd_sample(s, seed, delta, d, s->angular ? d + n3 : nullptr, 1)) return st;
+    }
+    // y = sqrt(2 kT dt) (M^{1/2} W)_lin in the solver precision
+    void* y = s->ab_y.p;
+    if (kT > 0.0) {
+        int its = 0;
+        lm_status st = lm_sqrt_mdot(s, W, seed, std::sqrt(2.0 * kT * dt), tol, max_iter, y,
+                                    s->angular ? static_cast<char*>(y) + bytes : nullptr, &its);
+        if (iters_out) *iters_out = its;
+        if (st != LM_OK) return st;
+    } else {
+        LM_CUDA(cudaMemsetAsync(y, 0, bytes, s->stream), "zero noise");
+    }
+    LM_CUDA(lmk::launch_ab_update(s->pos_raw.p, s->fp64, u, drift ? d : nullptr, y, history, first ? 1 : 0, kT, dt,
+                                  N, s->ab_x.p, s->stream),
+            "Adams-Bashforth update");
+    if (lm_status st = lm_set_positions(s, s->ab_x.p, N)) return st;
+    if (is_device_ptr(pos_out)) {
+        LM_CUDA(cudaMemcpyAsync(pos_out, s->ab_x.p, bytes, cudaMemcpyDeviceToDevice, s->stream), "copying positions");
+    } else {
+        LM_CUDA(cudaMemcpyAsync(pos_out, s->ab_x.p, bytes, cudaMemcpyDeviceToHost, s->stream), "copying positions");
+        LM_CUDA(cudaStreamSynchronize(s->stream), "copying positions");
+    }
+    return LM_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -751,33 +901,34 @@ lm_status lm_mdot_backward(lm_solver* s, const void* forces, const void* torques
     if (lm_status st = stage_out(s, dF, bytes, 1, &ov[1])) return st;
     if (lm_status st = stage_out(s, dT, bytes, 2, &ov[2])) return st;
     if (dX == nullptr && dF == nullptr && dT == nullptr) return LM_OK;
-    if (s->adj_cfg_N != s->N) {
-        lm_pair_config c{128, lmk::adjoint_ilp(s->fp64, s->angular), 1, 0};
-        const int occ = std::max(1, lmk::adjoint_ctas_per_sm(s->fp64, s->angular));
-        c.splits = auto_splits(s->N, c.threads, c.ilp, occ * s->sm_count);
-        s->adj_cfg = c;
-        s->adj_cfg_N = s->N;
-    }
-    lmk::AdjointArgs a;
-    a.fp64 = s->fp64;
-    a.angular = s->angular;
-    a.N = s->N;
-    a.pos4 = s->pos4.p;
-    a.F = pF; a.T = pT; a.G = pG; a.H = pH;
-    a.dX = ov[0].dev; a.dF = ov[1].dev; a.dT = ov[2].dev;
-    a.a = s->a;
-    a.eta = s->eta;
-    a.threads = s->adj_cfg.threads;
-    a.splits = s->adj_cfg.splits;
-    a.partials = nullptr;
-    const int64_t se = lmk::mdot_effective_splits(s->N, a.threads, a.splits);
-    if (se > 1) {
-        const size_t pb = (size_t)se * lmk::adjoint_partial_components(s->angular) * (size_t)s->N * sizeof(double);
-        LM_CUDA(s->partials.ensure(pb), "allocating split partial sums");
-        a.partials = s->partials.as<double>();
-    }
-    LM_CUDA(lmk::launch_adjoint(a, s->stream), "adjoint kernel");
+    ensure_adjoint_config(s);
+    if (lm_status st = run_adjoint(s, pF, pT, pG, pH, ov[0].dev, ov[1].dev, ov[2].dev, s->adj_cfg)) return st;
     return finish_out(s, ov, 3);
+}
+
+lm_status lm_get_adjoint_config(lm_solver* s, lm_pair_config* cfg) {
+    if (lm_status st = check_solver(s, true)) return st;
+    if (cfg == nullptr) return fail(LM_ERR_INVALID_ARG, "cfg is NULL");
+    ensure_adjoint_config(s);
+    *cfg = s->adj_cfg;
+    return LM_OK;
+}
+
+lm_status lm_set_adjoint_config(lm_solver* s, const lm_pair_config* cfg) {
+    if (lm_status st = check_solver(s, true)) return st;
+    if (cfg == nullptr) return fail(LM_ERR_INVALID_ARG, "cfg is NULL");
+    if (!lmk::adjoint_config_supported(s->fp64, s->angular, cfg->threads, cfg->ilp, cfg->packed) || cfg->splits < 0 ||
+        (!s->fp64 && !s->angular && cfg->packed < 1))
+        return fail(LM_ERR_INVALID_ARG, "unsupported adjoint configuration (threads %d, ilp %d, splits %d, packed %d)",
+                    cfg->threads, cfg->ilp, cfg->splits, cfg->packed);
+    lm_pair_config c = *cfg;
+    if (c.splits == 0) {
+        const int occ = std::max(1, lmk::adjoint_ctas_per_sm(s->fp64, s->angular, c.threads, c.ilp, c.packed));
+        c.splits = auto_splits(s->N, c.threads, c.ilp, occ * s->sm_count);
+    }
+    s->adj_cfg = c;
+    s->adj_cfg_N = s->N;
+    return LM_OK;
 }
 
 lm_status lm_get_pair_config(lm_solver* s, lm_pair_config* cfg) {
@@ -824,13 +975,8 @@ lm_status lm_autotune(lm_solver* s, int reps, lm_pair_config* best) {
                 if (!pair_config_supported(s, t, il, pk)) continue;
                 const int occ = pair_ctas_per_sm(s, t, il, pk);
                 if (occ < 1) continue;
-                const int sa = auto_splits(N, t, il, occ * s->sm_count);
-                const int opts[4] = {sa, std::max(1, sa / 2), std::max(1, (3 * sa) / 2), sa * 2};
-                for (int k = 0; k < 4; ++k) {
-                    bool dup = false;
-                    for (int q = 0; q < k; ++q) dup = dup || (opts[q] == opts[k]);
-                    if (!dup) cands.push_back(lm_pair_config{t, il, opts[k], pk});
-                }
+                for (int sp : split_candidates(N, t, il, occ * s->sm_count))
+                    cands.push_back(lm_pair_config{t, il, sp, pk});
             }
         }
     }
@@ -853,6 +999,41 @@ lm_status lm_autotune(lm_solver* s, int reps, lm_pair_config* best) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms < best_ms) { best_ms = ms; best_cfg = c; }
+    }
+    // the packed translation adjoint (open geometry): threads x ilp x j per vote x splits
+    if (result == LM_OK && !s->fp64 && !s->angular && !s->wall) {
+        std::vector<lm_pair_config> acands;
+        for (int uj = 1; uj <= 2; ++uj) {
+            for (int t : threads_opts) {
+                for (int il = 2; il <= 4; il += 2) {
+                    const int occ = lmk::adjoint_ctas_per_sm(0, 0, t, il, uj);
+                    if (occ < 1) continue;
+                    for (int sp : split_candidates(N, t, il, occ * s->sm_count))
+                        acands.push_back(lm_pair_config{t, il, sp, uj});
+                }
+            }
+        }
+        // inputs F = G = 0 (the timing does not depend on the values); outputs dX, dF
+        float best_adj = 1e30f;
+        lm_pair_config best_a = default_adjoint_config(s);
+        for (const lm_pair_config& c : acands) {
+            if ((result = run_adjoint(s, fin, nullptr, fin, nullptr, fout, fout + bytes, nullptr, c)) != LM_OK) break;
+            cudaEventRecord(e0, s->stream);
+            for (int r = 0; r < reps; ++r)
+                if ((result = run_adjoint(s, fin, nullptr, fin, nullptr, fout, fout + bytes, nullptr, c)) != LM_OK)
+                    break;
+            if (result != LM_OK) break;
+            cudaEventRecord(e1, s->stream);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) { result = cuda_fail(e, "autotune"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_adj) { best_adj = ms; best_a = c; }
+        }
+        if (result == LM_OK) {
+            s->adj_cfg = best_a;
+            s->adj_cfg_N = N;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -109,6 +109,8 @@ struct AdjointArgs {
     void* dX; void* dF; void* dT;     // outputs (nullable dX / dF)
     double a, eta;
     int threads, splits;
+    int ilp = 4;                      // i-particles per thread (packed FP32 translation form: 2 or 4)
+    int uj = 1;                       // j-particles per overlap vote (packed form: 1 or 2)
     double* partials;                 // splits * (3 + 3 or 6) * N doubles when splits > 1
 };
 
@@ -124,12 +126,13 @@ cudaError_t launch_mdot(const MdotArgs& a, cudaStream_t s);
 // Single-wall geometry (wall_kernels.cu): the same arguments, positions packed
 // by launch_pack_wall_positions.
 bool wall_config_supported(int fp64, int threads, int ilp, int packed);
-int wall_ctas_per_sm(int fp64, int angular, int threads, int ilp);
+int wall_ctas_per_sm(int fp64, int angular, int threads, int ilp, int packed);
 cudaError_t launch_wall_mdot(const MdotArgs& a, cudaStream_t s);
 cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s);
 int adjoint_partial_components(int angular);
 int adjoint_ilp(int fp64, int angular);
-int adjoint_ctas_per_sm(int fp64, int angular);
+bool adjoint_config_supported(int fp64, int angular, int threads, int ilp, int uj);
+int adjoint_ctas_per_sm(int fp64, int angular, int threads, int ilp, int uj);
 
 // Pack N x 3 positions into (x, y, z, 0) and flag non-finite or too large
 // coordinates in *bad (device int, set to 1).
@@ -144,6 +147,13 @@ cudaError_t launch_displace_pack_wall(const void* pos, int in_f64, const double*
                                       double a, void* pos4, int out_f64, cudaStream_t s);
 cudaError_t launch_rfd_difference(const double* P, const double* Q, double inv_delta, int64_t N, int angular,
                                   void* lin, void* ang, int out_f64, cudaStream_t s);
+// Roller-example time stepping (integrator_kernels.cu): soft steric forces
+// (N x 3 positions in, N x 3 forces out, element type by f64) and the
+// stochastic Adams-Bashforth update of the positions.
+cudaError_t launch_soft_repulsion(const void* pos, int f64, int64_t N, double U0, double b, double d_pair,
+                                  double d_wall, int wall, void* out, cudaStream_t s);
+cudaError_t launch_ab_update(const void* pos, int f64, const double* u, const double* d, const void* y,
+                             double* hist, int first, double kT, double dt, int64_t N, void* out, cudaStream_t s);
 
 // Lanczos vector kernels (lanczos_kernels.cu).  All vectors are FP64 of
 // length n; the basis V is row-major (row j = v_j, stride n).  Reductions are

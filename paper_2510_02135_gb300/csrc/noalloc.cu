@@ -118,7 +118,7 @@ extern "C" lm_status lm_mdot_noalloc(const float* pos, const float* forces, cons
     int splits = lmk::auto_splits(N, threads, ilp, occ * sms);
     if (splits > max_splits) splits = max_splits;
     if (splits < 1) splits = 1;
-    // the launcher may merge splits (whole tiles); never more than requested
+    // the launcher never launches more splits than requested (at most one per tile)
     if (lmk::mdot_effective_splits(N, threads, splits) > max_splits)
         return noalloc_fail(LM_ERR_INVALID_ARG, "scratch too small for N = %lld", (long long)N);
 

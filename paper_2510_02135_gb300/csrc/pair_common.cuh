@@ -158,14 +158,30 @@ __global__ void reduce_splits_kernel(const double* __restrict__ partials, int sp
     else static_cast<float*>(out)[idx] = (float)(c8 * s);
 }
 
-// j-range split: equal chunks of whole tiles; returns the launched split count.
-int64_t split_plan(int64_t N, int NT, int splits, int64_t* jchunk) {
+// Packed FP32 pairs (sm_100-class f32x2 add / mul / fma on a register pair).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+
+// j-range split: `splits` contiguous ranges of whole tiles, as equal as
+// possible (split k holds tiles [k T / s, (k + 1) T / s) of the T = ceil(N /
+// NT) tiles), so that any split count is exact.  Returns the launched split
+// count s = min(splits, T) and the tile count T.
+inline int64_t split_plan(int64_t N, int NT, int splits, int64_t* ntiles) {
     if (splits < 1) splits = 1;
-    const int64_t ntiles = (N + NT - 1) / NT;
-    if (splits > ntiles) splits = (int)ntiles;
-    const int64_t tps = (ntiles + splits - 1) / splits;
-    *jchunk = tps * NT;
-    return (N + *jchunk - 1) / *jchunk;
+    *ntiles = (N + NT - 1) / NT;
+    return splits < *ntiles ? splits : *ntiles;
+}
+
+// This CTA's j-range [jb, je) for split blockIdx.y of gridDim.y.
+__device__ __forceinline__ void split_range(int64_t N, int NT, int64_t ntiles, int64_t* jb, int64_t* je) {
+    const int64_t k = blockIdx.y, s = gridDim.y;
+    *jb = (k * ntiles / s) * NT;
+    const int64_t e = ((k + 1) * ntiles / s) * NT;
+    *je = e < N ? e : N;
 }
 
 }  // namespace

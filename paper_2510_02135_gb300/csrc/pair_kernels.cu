@@ -32,7 +32,7 @@ namespace {
 template <typename R, bool ANG, int NT, int NI>
 __global__ void __launch_bounds__(NT) rpy_mdot_kernel(const typename V4<R>::type* __restrict__ pos4,
                                                       const void* __restrict__ Fp, const void* __restrict__ Tp,
-                                                      int in_f64, int64_t N, int64_t jchunk, RpyConst<R> k,
+                                                      int in_f64, int64_t N, int64_t ntiles, RpyConst<R> k,
                                                       double c8, void* __restrict__ lin, void* __restrict__ ang,
                                                       int out_f64, double* __restrict__ partials) {
     using R4 = typename V4<R>::type;
@@ -46,8 +46,8 @@ __global__ void __launch_bounds__(NT) rpy_mdot_kernel(const typename V4<R>::type
 
     const int tid = threadIdx.x;
     const int64_t i0 = (int64_t)blockIdx.x * (NT * NI);
-    const int64_t jb = (int64_t)blockIdx.y * jchunk;
-    const int64_t je = (jb + jchunk < N) ? (jb + jchunk) : N;
+    int64_t jb, je;
+    split_range(N, NT, ntiles, &jb, &je);
     const R pad = (R)kPadCoord;
 
     R xi[NI], yi[NI], zi[NI];
@@ -178,11 +178,6 @@ __global__ void __launch_bounds__(NT) rpy_mdot_kernel(const typename V4<R>::type
 // The exact branch (some pair of the warp at r < 2a) unpacks the two lanes
 // and runs the scalar formula.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
-__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
 
 // float4 words of one j in the packed tile
 template <bool ANG>
@@ -196,7 +191,7 @@ constexpr size_t x2_smem_bytes() {
 template <bool ANG, int NT, int NI, int UJ>
 __global__ void __launch_bounds__(NT) rpy_mdot_x2_kernel(const float4* __restrict__ pos4,
                                                          const void* __restrict__ Fp, const void* __restrict__ Tp,
-                                                         int in_f64, int64_t N, int64_t jchunk, RpyConst<float> k,
+                                                         int in_f64, int64_t N, int64_t ntiles, RpyConst<float> k,
                                                          double c8, void* __restrict__ lin, void* __restrict__ ang,
                                                          int out_f64, double* __restrict__ partials) {
     static_assert(NI % 2 == 0, "packed form needs an even number of i-particles per thread");
@@ -211,8 +206,8 @@ __global__ void __launch_bounds__(NT) rpy_mdot_x2_kernel(const float4* __restric
 
     const int tid = threadIdx.x;
     const int64_t i0 = (int64_t)blockIdx.x * (NT * NI);
-    const int64_t jb = (int64_t)blockIdx.y * jchunk;
-    const int64_t je = (jb + jchunk < N) ? (jb + jchunk) : N;
+    int64_t jb, je;
+    split_range(N, NT, ntiles, &jb, &je);
     const float pad = (float)kPadCoord;
 
     float2 xi[NP], yi[NP], zi[NP];
@@ -426,8 +421,8 @@ template <typename R, bool ANG, int NT, int NI>
 cudaError_t launch_t(const MdotArgs& a, cudaStream_t s) {
     const int64_t per_cta = (int64_t)NT * NI;
     const int64_t nblk = (a.N + per_cta - 1) / per_cta;
-    int64_t jchunk = 0;
-    const int splits = (int)split_plan(a.N, NT, a.splits, &jchunk);
+    int64_t ntiles = 0;
+    const int splits = (int)split_plan(a.N, NT, a.splits, &ntiles);
     if (nblk > 0x7fffffff || splits > 65535) return cudaErrorInvalidConfiguration;
     const double c8 = 1.0 / (8.0 * 3.14159265358979323846 * a.eta);
     const RpyConst<R> k = make_rpy_const<R>(a.a);
@@ -443,7 +438,7 @@ cudaError_t launch_t(const MdotArgs& a, cudaStream_t s) {
     }
     if (a.ev_begin) cudaEventRecord(a.ev_begin, s);
     rpy_mdot_kernel<R, ANG, NT, NI><<<grid, NT, dyn, s>>>(
-        static_cast<const typename V4<R>::type*>(a.pos4), a.F, ANG ? a.T : nullptr, a.in_f64, a.N, jchunk, k, c8,
+        static_cast<const typename V4<R>::type*>(a.pos4), a.F, ANG ? a.T : nullptr, a.in_f64, a.N, ntiles, k, c8,
         a.lin, a.ang, a.out_f64, a.partials);
     cudaError_t err = cudaGetLastError();
     if (a.ev_end) cudaEventRecord(a.ev_end, s);
@@ -461,8 +456,8 @@ template <bool ANG, int NT, int NI, int UJ>
 cudaError_t launch_x2_t(const MdotArgs& a, cudaStream_t s) {
     const int64_t per_cta = (int64_t)NT * NI;
     const int64_t nblk = (a.N + per_cta - 1) / per_cta;
-    int64_t jchunk = 0;
-    const int splits = (int)split_plan(a.N, NT, a.splits, &jchunk);
+    int64_t ntiles = 0;
+    const int splits = (int)split_plan(a.N, NT, a.splits, &ntiles);
     if (nblk > 0x7fffffff || splits > 65535) return cudaErrorInvalidConfiguration;
     const double c8 = 1.0 / (8.0 * 3.14159265358979323846 * a.eta);
     const RpyConst<float> k = make_rpy_const<float>(a.a);
@@ -478,7 +473,7 @@ cudaError_t launch_x2_t(const MdotArgs& a, cudaStream_t s) {
     }
     if (a.ev_begin) cudaEventRecord(a.ev_begin, s);
     rpy_mdot_x2_kernel<ANG, NT, NI, UJ><<<grid, NT, dyn, s>>>(static_cast<const float4*>(a.pos4), a.F,
-                                                          ANG ? a.T : nullptr, a.in_f64, a.N, jchunk, k, c8,
+                                                          ANG ? a.T : nullptr, a.in_f64, a.N, ntiles, k, c8,
                                                           a.lin, a.ang, a.out_f64, a.partials);
     cudaError_t err = cudaGetLastError();
     if (a.ev_end) cudaEventRecord(a.ev_end, s);
@@ -574,8 +569,8 @@ int occupancy_r(int threads, int ilp) {
 }  // namespace
 
 int64_t mdot_effective_splits(int64_t N, int threads, int splits) {
-    int64_t jc = 0;
-    return split_plan(N, threads, splits, &jc);
+    int64_t nt = 0;
+    return split_plan(N, threads, splits, &nt);
 }
 
 int mdot_ctas_per_sm(int fp64, int angular, int threads, int ilp, int packed) {

@@ -28,8 +28,8 @@
 //
 // Schedule: as the open kernel (register-blocked i, shared-memory j-tiles,
 // warp vote for the overlap branch of the free part, TwoSum fold per tile,
-// j-range splits).  The wall part needs no branch: clamped heights keep
-// rho >= 2a.
+// j-range splits), in a scalar and a packed f32x2 form.  The wall part needs
+// no branch: clamped heights keep rho >= 2a.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -97,7 +97,7 @@ __device__ __forceinline__ void wall_pair(R Rx, R Ry, R Rz, R hj, const typename
 template <typename R, bool ANG, int NT, int NI>
 __global__ void __launch_bounds__(NT) rpy_wall_kernel(const typename V4<R>::type* __restrict__ pos4,
                                                       const void* __restrict__ Fp, const void* __restrict__ Tp,
-                                                      int in_f64, int64_t N, int64_t jchunk, RpyConst<R> k, R a2,
+                                                      int in_f64, int64_t N, int64_t ntiles, RpyConst<R> k, R a2,
                                                       double c8, void* __restrict__ lin, void* __restrict__ ang,
                                                       int out_f64, double* __restrict__ partials) {
     using R4 = typename V4<R>::type;
@@ -111,8 +111,8 @@ __global__ void __launch_bounds__(NT) rpy_wall_kernel(const typename V4<R>::type
 
     const int tid = threadIdx.x;
     const int64_t i0 = (int64_t)blockIdx.x * (NT * NI);
-    const int64_t jb = (int64_t)blockIdx.y * jchunk;
-    const int64_t je = (jb + jchunk < N) ? (jb + jchunk) : N;
+    int64_t jb, je;
+    split_range(N, NT, ntiles, &jb, &je);
     const R pad = (R)kPadCoord;
 
     R xi[NI], yi[NI], zi[NI], fi[NI];
@@ -224,12 +224,384 @@ __global__ void __launch_bounds__(NT) rpy_wall_kernel(const typename V4<R>::type
     }
 }
 
+// ---------------------------------------------------------------------------
+// Packed FP32 form of the wall kernel: two i-particles per f32x2
+// instruction, as the packed open kernel.  The j-tile holds every operand
+// pre-broadcast into both halves of a float2 (packed operands carry no
+// negation): -x_j, f F_j, f T_j, their negatives, -f T_j / 2, 3 f T_j / 2 and
+// +z_j (the image height).  The wall part below is the formula of wall_pair
+// with every sign folded into a constant or a tile slot.
+// ---------------------------------------------------------------------------
+template <bool ANG>
+constexpr int wall_x2_words() { return ANG ? 11 : 4; }
+
+template <bool ANG, int NT, int NI>
+constexpr size_t wall_x2_smem_bytes() {
+    return (size_t)wall_x2_words<ANG>() * NT * sizeof(float4) + running_sum_bytes<float, ANG, NT, NI>();
+}
+
+// Wall part of two pairs (one per lane) for the source j.  Rx, Ry: x_i - x_j;
+// zi, zj: clamped heights; f*, mf*: f F_j and -f F_j; T*, mT*: f T_j and -f T_j.
+template <bool ANG>
+__device__ __forceinline__ void wall_pair2(float2 Rx, float2 Ry, float2 zi, float2 zj, float2 a2,
+                                           float2 fx, float2 fy, float2 fz, float2 mfx, float2 mfy, float2 mfz,
+                                           float2 Tx, float2 Ty, float2 Tz, float2 mTx, float2 mTy, float2 mTz,
+                                           float2* acc) {
+    const float2 Rz = add2(zi, zj);
+    const float2 r2 = fma2(Rx, Rx, fma2(Ry, Ry, mul2(Rz, Rz)));
+    const float2 u = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 ex = mul2(Rx, u), ey = mul2(Ry, u), c = mul2(Rz, u);
+    const float2 H = mul2(zj, u);
+    const float2 al = mul2(mul2(a2, u), u);
+    const float2 al2 = mul2(al, al);
+    const float2 c2 = mul2(c, c), H2 = mul2(H, H), cH = mul2(c, H);
+    const float2 alc = mul2(al, c), al2c = mul2(al2, c);
+    // A = -1 + 2H^2 - 2cH + alpha (2c^2 - 2/3) + alpha^2 (2/3 - 10c^2/3)
+    const float2 A = fma2(al2, fma2(bc2(-10.f / 3.f), c2, bc2(2.f / 3.f)),
+                          fma2(al, fma2(bc2(2.f), c2, bc2(-2.f / 3.f)),
+                               fma2(bc2(2.f), H2, fma2(bc2(-2.f), cH, bc2(-1.f)))));
+    // B = -1 - 6H^2 + 6cH + alpha (2 - 10c^2) + alpha^2 (70c^2/3 - 10/3)
+    const float2 B = fma2(al2, fma2(bc2(70.f / 3.f), c2, bc2(-10.f / 3.f)),
+                          fma2(al, fma2(bc2(-10.f), c2, bc2(2.f)),
+                               fma2(bc2(-6.f), H2, fma2(bc2(6.f), cH, bc2(-1.f)))));
+    // C = 2H + 12 cH (H - c) + alpha c (20c^2 - 4) + alpha^2 c (40/3 - 140c^2/3)
+    const float2 C = fma2(al2c, fma2(bc2(-140.f / 3.f), c2, bc2(40.f / 3.f)),
+                          fma2(alc, fma2(bc2(20.f), c2, bc2(-4.f)),
+                               fma2(mul2(bc2(12.f), cH), fma2(bc2(-1.f), c, H), mul2(bc2(2.f), H))));
+    // D = 2H - (20/3) alpha^2 c
+    const float2 D = fma2(bc2(-20.f / 3.f), al2c, mul2(bc2(2.f), H));
+    // E = -4H^2 - 4 alpha c^2 + alpha^2 (20c^2 - 8/3)
+    const float2 E = fma2(al2, fma2(bc2(20.f), c2, bc2(-8.f / 3.f)), fma2(bc2(-4.f), mul2(al, c2), mul2(bc2(-4.f), H2)));
+    const float2 eF = fma2(ex, fx, fma2(ey, fy, mul2(c, fz)));
+    const float2 pe = fma2(B, eF, mul2(C, fz));
+    const float2 pz = fma2(D, eF, mul2(E, fz));
+    acc[0] = fma2(u, fma2(A, fx, mul2(pe, ex)), acc[0]);
+    acc[1] = fma2(u, fma2(A, fy, mul2(pe, ey)), acc[1]);
+    acc[2] = fma2(u, fma2(A, fz, fma2(pe, c, pz)), acc[2]);
+    if constexpr (ANG) {
+        const float2 u2 = mul2(u, u);
+        // u += [e x T + K1 z x T + (K2 e + K3 z)(w.T)] / rho^2, with -K1 = 2 (alpha c + H)
+        const float2 K1n = mul2(bc2(2.f), add2(alc, H));
+        const float2 K2 = mul2(bc2(2.f), fma2(bc2(5.f), alc, fma2(bc2(-3.f), c, mul2(bc2(3.f), H))));
+        const float2 K3 = mul2(bc2(-2.f), al);
+        const float2 wT = fma2(ey, Tx, mul2(ex, mTy));
+        const float2 K2wT = mul2(K2, wT);
+        acc[0] = fma2(u2, fma2(ey, Tz, fma2(c, mTy, fma2(K1n, Ty, mul2(K2wT, ex)))), acc[0]);
+        acc[1] = fma2(u2, fma2(c, Tx, fma2(ex, mTz, fma2(K1n, mTx, mul2(K2wT, ey)))), acc[1]);
+        acc[2] = fma2(u2, fma2(ex, Ty, fma2(ey, mTx, mul2(fma2(K2, c, K3), wT))), acc[2]);
+        // w += [e x F + L1 z x F + (L2 (e.F) + L3 F_z) w] / rho^2
+        const float2 L1 = mul2(bc2(2.f), fma2(bc2(-1.f), H, alc));
+        const float2 L2 = mul2(bc2(2.f), fma2(bc2(5.f), alc, mul2(bc2(-3.f), H)));
+        const float2 L3 = mul2(bc2(-2.f), fma2(bc2(10.f), mul2(al, c2), fma2(bc2(-6.f), cH, mul2(bc2(-1.f), al))));
+        const float2 q = fma2(L2, eF, mul2(L3, fz));
+        const float2 qn = mul2(bc2(-1.f), q);
+        acc[3] = fma2(u2, fma2(ey, fz, fma2(c, mfy, fma2(L1, mfy, mul2(q, ey)))), acc[3]);
+        acc[4] = fma2(u2, fma2(c, fx, fma2(ex, mfz, fma2(L1, fx, mul2(qn, ex)))), acc[4]);
+        acc[5] = fma2(u2, fma2(ex, fy, mul2(ey, mfx)), acc[5]);
+        // w += [(7/2 - 6c^2) T - (9/2)(e.T) e + 3c T_z e + 6c (e.T) z - 3 T_z z] / rho^3
+        const float2 u3 = mul2(u2, u);
+        const float2 eT = fma2(ex, Tx, fma2(ey, Ty, mul2(c, Tz)));
+        const float2 Ar = fma2(bc2(-6.f), c2, bc2(3.5f));
+        const float2 pr = fma2(bc2(-4.5f), eT, mul2(mul2(bc2(3.f), c), Tz));
+        acc[3] = fma2(u3, fma2(Ar, Tx, mul2(pr, ex)), acc[3]);
+        acc[4] = fma2(u3, fma2(Ar, Ty, mul2(pr, ey)), acc[4]);
+        acc[5] = fma2(u3, fma2(Ar, Tz, fma2(pr, c, fma2(mul2(bc2(6.f), c), eT, mul2(bc2(-3.f), Tz)))), acc[5]);
+    }
+}
+
+template <bool ANG, int NT, int NI>
+__global__ void __launch_bounds__(NT) rpy_wall_x2_kernel(const float4* __restrict__ pos4,
+                                                         const void* __restrict__ Fp, const void* __restrict__ Tp,
+                                                         int in_f64, int64_t N, int64_t ntiles, RpyConst<float> k,
+                                                         float a2s, double c8, void* __restrict__ lin,
+                                                         void* __restrict__ ang, int out_f64,
+                                                         double* __restrict__ partials) {
+    static_assert(NI % 2 == 0, "packed form needs an even number of i-particles per thread");
+    constexpr int NP = NI / 2;
+    constexpr int C = ANG ? 6 : 3;
+    constexpr int W = wall_x2_words<ANG>();
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    float4* s_t = reinterpret_cast<float4*>(dyn_smem);                 // [w][jj]
+    float* s_hi = reinterpret_cast<float*>(s_t + W * NT);              // [c][q][tid]
+    float* s_lo = s_hi + C * NI * NT;
+
+    const int tid = threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.x * (NT * NI);
+    int64_t jb, je;
+    split_range(N, NT, ntiles, &jb, &je);
+    const float pad = (float)kPadCoord;
+
+    float2 xi[NP], yi[NP], zi[NP], fi[NP];
+    float2 acc[NP][C];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        float v[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t i = i0 + (int64_t)(2 * p + h) * NT + tid;
+            if (i < N) {
+                const float4 q = pos4[i];
+                v[h][0] = q.x; v[h][1] = q.y; v[h][2] = q.z; v[h][3] = q.w;
+            } else {
+                // far from every particle, above the wall
+                v[h][0] = -pad; v[h][1] = -pad; v[h][2] = pad; v[h][3] = 0.f;
+            }
+        }
+        xi[p] = make_float2(v[0][0], v[1][0]);
+        yi[p] = make_float2(v[0][1], v[1][1]);
+        zi[p] = make_float2(v[0][2], v[1][2]);
+        fi[p] = make_float2(v[0][3], v[1][3]);
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[p][c] = bc2(0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            s_hi[(c * NI + q) * NT + tid] = 0.f;
+            s_lo[(c * NI + q) * NT + tid] = 0.f;
+        }
+    }
+    const float2 K1 = bc2(k.K1);
+    const float2 nK2 = bc2(-k.K2);
+    const float2 a2 = bc2(a2s);
+
+    // register prefetch of this thread's j of the next tile: position (w = f), f F, f T
+    float4 np;
+    float3 nf, nt;
+    auto fetch = [&](int64_t j) {
+        if (j < je) {
+            np = pos4[j];
+            const float fj = np.w;
+            nf.x = fj * load_elem<float>(Fp, in_f64, 3 * j + 0);
+            nf.y = fj * load_elem<float>(Fp, in_f64, 3 * j + 1);
+            nf.z = fj * load_elem<float>(Fp, in_f64, 3 * j + 2);
+            if constexpr (ANG) {
+                nt.x = fj * load_elem<float>(Tp, in_f64, 3 * j + 0);
+                nt.y = fj * load_elem<float>(Tp, in_f64, 3 * j + 1);
+                nt.z = fj * load_elem<float>(Tp, in_f64, 3 * j + 2);
+            }
+        } else {
+            np = make_float4(pad, pad, pad, 0.f);
+            nf = make_float3(0.f, 0.f, 0.f);
+            nt = make_float3(0.f, 0.f, 0.f);
+        }
+    };
+    fetch(jb + tid);
+
+    for (int64_t jt = jb; jt < je; jt += NT) {
+        s_t[0 * NT + tid] = make_float4(-np.x, -np.x, -np.y, -np.y);
+        s_t[1 * NT + tid] = make_float4(-np.z, -np.z, nf.x, nf.x);
+        s_t[2 * NT + tid] = make_float4(nf.y, nf.y, nf.z, nf.z);
+        if constexpr (ANG) {
+            s_t[3 * NT + tid] = make_float4(-nf.x, -nf.x, -nf.y, -nf.y);
+            s_t[4 * NT + tid] = make_float4(-nf.z, -nf.z, nt.x, nt.x);
+            s_t[5 * NT + tid] = make_float4(nt.y, nt.y, nt.z, nt.z);
+            s_t[6 * NT + tid] = make_float4(-nt.x, -nt.x, -nt.y, -nt.y);
+            s_t[7 * NT + tid] = make_float4(-nt.z, -nt.z, -0.5f * nt.x, -0.5f * nt.x);
+            s_t[8 * NT + tid] = make_float4(-0.5f * nt.y, -0.5f * nt.y, -0.5f * nt.z, -0.5f * nt.z);
+            s_t[9 * NT + tid] = make_float4(1.5f * nt.x, 1.5f * nt.x, 1.5f * nt.y, 1.5f * nt.y);
+            s_t[10 * NT + tid] = make_float4(1.5f * nt.z, 1.5f * nt.z, np.z, np.z);
+        } else {
+            s_t[3 * NT + tid] = make_float4(-nf.x, -nf.x, np.z, np.z);
+        }
+        __syncthreads();
+        if (jt + NT < je) fetch(jt + NT + tid);
+
+#pragma unroll 1
+        for (int jj = 0; jj < NT; ++jj) {
+            const float4 w0 = s_t[0 * NT + jj];
+            const float4 w1 = s_t[1 * NT + jj];
+            const float4 w2 = s_t[2 * NT + jj];
+            const float2 nx = lo2(w0), ny = hi2(w0), nz = lo2(w1);
+            const float2 fx = hi2(w1), fy = lo2(w2), fz = hi2(w2);
+            float2 mfx, mfy, mfz, Tx, Ty, Tz, mTx, mTy, mTz, hx, hy, hz, gx, gy, gz, zj;
+            if constexpr (ANG) {
+                const float4 w3 = s_t[3 * NT + jj];
+                const float4 w4 = s_t[4 * NT + jj];
+                const float4 w5 = s_t[5 * NT + jj];
+                const float4 w6 = s_t[6 * NT + jj];
+                const float4 w7 = s_t[7 * NT + jj];
+                const float4 w8 = s_t[8 * NT + jj];
+                const float4 w9 = s_t[9 * NT + jj];
+                const float4 w10 = s_t[10 * NT + jj];
+                mfx = lo2(w3); mfy = hi2(w3); mfz = lo2(w4);
+                Tx = hi2(w4); Ty = lo2(w5); Tz = hi2(w5);
+                mTx = lo2(w6); mTy = hi2(w6); mTz = lo2(w7);
+                hx = hi2(w7); hy = lo2(w8); hz = hi2(w8);
+                gx = lo2(w9); gy = hi2(w9); gz = lo2(w10);
+                zj = hi2(w10);
+            } else {
+                const float4 w3 = s_t[3 * NT + jj];
+                zj = hi2(w3);
+                mfx = mfy = mfz = Tx = Ty = Tz = mTx = mTy = mTz = bc2(0.f);
+            }
+            float2 dx[NP], dy[NP], dz[NP], r2[NP];
+            float mn;
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                dx[p] = add2(xi[p], nx);
+                dy[p] = add2(yi[p], ny);
+                dz[p] = add2(zi[p], nz);
+                r2[p] = fma2(dx[p], dx[p], fma2(dy[p], dy[p], mul2(dz[p], dz[p])));
+                const float m2 = fminf(r2[p].x, r2[p].y);
+                mn = (p == 0) ? m2 : fminf(mn, m2);
+            }
+            if (__any_sync(0xffffffffu, mn < k.four_a2)) {
+                const float4 fj = make_float4(fx.x, fy.x, fz.x, 0.f);
+                float4 hj = make_float4(0.f, 0.f, 0.f, 0.f);
+                if constexpr (ANG) hj = make_float4(hx.x, hy.x, hz.x, 0.f);
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    Acc<float, ANG> t0, t1;
+#pragma unroll
+                    for (int c = 0; c < C; ++c) { t0.p[c] = 0.f; t1.p[c] = 0.f; }
+                    pair_exact<float, ANG>(dx[p].x, dy[p].x, dz[p].x, r2[p].x, fj, hj, k, t0);
+                    pair_exact<float, ANG>(dx[p].y, dy[p].y, dz[p].y, r2[p].y, fj, hj, k, t1);
+#pragma unroll
+                    for (int c = 0; c < C; ++c) acc[p][c] = add2(acc[p][c], make_float2(t0.p[c], t1.p[c]));
+                }
+            } else {
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    const float2 invr = make_float2(rsqrtf(r2[p].x), rsqrtf(r2[p].y));
+                    const float2 invr2 = mul2(invr, invr);
+                    const float2 invr3 = mul2(invr2, invr);
+                    const float2 A = fma2(K1, invr3, invr);
+                    const float2 invr5 = mul2(invr3, invr2);
+                    const float2 B = fma2(nK2, invr5, invr3);
+                    const float2 dF = fma2(dx[p], fx, fma2(dy[p], fy, mul2(dz[p], fz)));
+                    const float2 sB = mul2(B, dF);
+                    acc[p][0] = fma2(sB, dx[p], fma2(A, fx, acc[p][0]));
+                    acc[p][1] = fma2(sB, dy[p], fma2(A, fy, acc[p][1]));
+                    acc[p][2] = fma2(sB, dz[p], fma2(A, fz, acc[p][2]));
+                    if constexpr (ANG) {
+                        const float2 cx = fma2(Ty, dz[p], mul2(mTz, dy[p]));
+                        const float2 cy = fma2(Tz, dx[p], mul2(mTx, dz[p]));
+                        const float2 cz = fma2(Tx, dy[p], mul2(mTy, dx[p]));
+                        acc[p][0] = fma2(invr3, cx, acc[p][0]);
+                        acc[p][1] = fma2(invr3, cy, acc[p][1]);
+                        acc[p][2] = fma2(invr3, cz, acc[p][2]);
+                        const float2 vx = fma2(fy, dz[p], fma2(mfz, dy[p], hx));
+                        const float2 vy = fma2(fz, dx[p], fma2(mfx, dz[p], hy));
+                        const float2 vz = fma2(fx, dy[p], fma2(mfy, dx[p], hz));
+                        const float2 t = mul2(invr5, fma2(dx[p], gx, fma2(dy[p], gy, mul2(dz[p], gz))));
+                        acc[p][3] = fma2(t, dx[p], fma2(invr3, vx, acc[p][3]));
+                        acc[p][4] = fma2(t, dy[p], fma2(invr3, vy, acc[p][4]));
+                        acc[p][5] = fma2(t, dz[p], fma2(invr3, vz, acc[p][5]));
+                    }
+                }
+            }
+            // the wall part: no branch (clamped heights keep rho >= 2a)
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+                wall_pair2<ANG>(dx[p], dy[p], zi[p], zj, a2, fx, fy, fz, mfx, mfy, mfz, Tx, Ty, Tz, mTx, mTy, mTz,
+                                acc[p]);
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const int o0 = (c * NI + 2 * p) * NT + tid;
+                const int o1 = o0 + NT;
+                fold(&s_hi[o0], &s_lo[o0], acc[p][c].x);
+                fold(&s_hi[o1], &s_lo[o1], acc[p][c].y);
+            }
+        }
+        __syncthreads();
+    }
+
+    const bool direct = (gridDim.y == 1);
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+        const int64_t i = i0 + (int64_t)q * NT + tid;
+        if (i >= N) continue;
+        const float f = (q & 1) ? fi[q >> 1].y : fi[q >> 1].x;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int o = (c * NI + q) * NT + tid;
+            const double v = (double)f * ((double)s_hi[o] + (double)s_lo[o]);
+            if (direct) {
+                void* out = (c < 3) ? lin : ang;
+                const int64_t idx = 3 * i + (c % 3);
+                if (out_f64) static_cast<double*>(out)[idx] = c8 * v;
+                else static_cast<float*>(out)[idx] = (float)(c8 * v);
+            } else {
+                partials[((int64_t)blockIdx.y * C + c) * N + i] = v;
+            }
+        }
+    }
+}
+
+template <bool ANG, int NT, int NI>
+cudaError_t launch_wall_x2_t(const MdotArgs& a, cudaStream_t s) {
+    const int64_t per_cta = (int64_t)NT * NI;
+    const int64_t nblk = (a.N + per_cta - 1) / per_cta;
+    int64_t ntiles = 0;
+    const int splits = (int)split_plan(a.N, NT, a.splits, &ntiles);
+    if (nblk > 0x7fffffff || splits > 65535) return cudaErrorInvalidConfiguration;
+    if (splits > 1 && a.partials == nullptr) return cudaErrorInvalidValue;
+    const double c8 = 1.0 / (8.0 * 3.14159265358979323846 * a.eta);
+    const RpyConst<float> k = make_rpy_const<float>(a.a);
+    dim3 grid((unsigned)nblk, (unsigned)splits);
+    constexpr size_t dyn = wall_x2_smem_bytes<ANG, NT, NI>();
+    static bool attr_set = false;  // per instantiation; the attribute is process-wide
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(rpy_wall_x2_kernel<ANG, NT, NI>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (a.ev_begin) cudaEventRecord(a.ev_begin, s);
+    rpy_wall_x2_kernel<ANG, NT, NI><<<grid, NT, dyn, s>>>(static_cast<const float4*>(a.pos4), a.F,
+                                                          ANG ? a.T : nullptr, a.in_f64, a.N, ntiles, k,
+                                                          (float)(a.a * a.a), c8, a.lin, a.ang, a.out_f64,
+                                                          a.partials);
+    cudaError_t err = cudaGetLastError();
+    if (a.ev_end) cudaEventRecord(a.ev_end, s);
+    count_launches(1);
+    if (err != cudaSuccess || splits == 1) return err;
+    constexpr int C = ANG ? 6 : 3;
+    const int64_t tot = (int64_t)C * a.N;
+    reduce_splits_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a.partials, splits, C, a.N, c8, a.lin,
+                                                                        a.ang, a.out_f64);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// Packed wall configurations (FP32): threads {128, 256} x ilp {2, 4}.
+template <bool ANG>
+cudaError_t launch_wall_x2(const MdotArgs& a, cudaStream_t s) {
+    if (a.threads == 128 && a.ilp == 2) return launch_wall_x2_t<ANG, 128, 2>(a, s);
+    if (a.threads == 128 && a.ilp == 4) return launch_wall_x2_t<ANG, 128, 4>(a, s);
+    if (a.threads == 256 && a.ilp == 2) return launch_wall_x2_t<ANG, 256, 2>(a, s);
+    if (a.threads == 256 && a.ilp == 4) return launch_wall_x2_t<ANG, 256, 4>(a, s);
+    return cudaErrorInvalidConfiguration;
+}
+
+template <bool ANG>
+int wall_x2_occupancy(int threads, int ilp) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidConfiguration;
+#define LM_WOCC2(NT, NI)                                                                                 \
+    if (threads == NT && ilp == NI) {                                                                    \
+        constexpr size_t dyn = wall_x2_smem_bytes<ANG, NT, NI>();                                        \
+        e = cudaFuncSetAttribute(rpy_wall_x2_kernel<ANG, NT, NI>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)dyn);                                                              \
+        if (e == cudaSuccess)                                                                            \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rpy_wall_x2_kernel<ANG, NT, NI>, NT, dyn); \
+    }
+    LM_WOCC2(128, 2) LM_WOCC2(128, 4) LM_WOCC2(256, 2) LM_WOCC2(256, 4)
+#undef LM_WOCC2
+    return e == cudaSuccess ? n : 0;
+}
+
 template <typename R, bool ANG, int NT, int NI>
 cudaError_t launch_wall_t(const MdotArgs& a, cudaStream_t s) {
     const int64_t per_cta = (int64_t)NT * NI;
     const int64_t nblk = (a.N + per_cta - 1) / per_cta;
-    int64_t jchunk = 0;
-    const int splits = (int)split_plan(a.N, NT, a.splits, &jchunk);
+    int64_t ntiles = 0;
+    const int splits = (int)split_plan(a.N, NT, a.splits, &ntiles);
     if (nblk > 0x7fffffff || splits > 65535) return cudaErrorInvalidConfiguration;
     if (splits > 1 && a.partials == nullptr) return cudaErrorInvalidValue;
     const double c8 = 1.0 / (8.0 * 3.14159265358979323846 * a.eta);
@@ -245,7 +617,7 @@ cudaError_t launch_wall_t(const MdotArgs& a, cudaStream_t s) {
     }
     if (a.ev_begin) cudaEventRecord(a.ev_begin, s);
     rpy_wall_kernel<R, ANG, NT, NI><<<grid, NT, dyn, s>>>(
-        static_cast<const typename V4<R>::type*>(a.pos4), a.F, ANG ? a.T : nullptr, a.in_f64, a.N, jchunk, k,
+        static_cast<const typename V4<R>::type*>(a.pos4), a.F, ANG ? a.T : nullptr, a.in_f64, a.N, ntiles, k,
         (R)(a.a * a.a), c8, a.lin, a.ang, a.out_f64, a.partials);
     cudaError_t err = cudaGetLastError();
     if (a.ev_end) cudaEventRecord(a.ev_end, s);
@@ -297,19 +669,24 @@ int wall_occupancy_r(int threads, int ilp) {
 }  // namespace
 
 bool wall_config_supported(int fp64, int threads, int ilp, int packed) {
-    if (packed) return false;
     if (threads != 128 && threads != 256) return false;
+    if (packed) return packed == 1 && !fp64 && (ilp == 2 || ilp == 4);
     return fp64 ? ilp == 1 : (ilp == 1 || ilp == 2 || ilp == 4);
 }
 
-int wall_ctas_per_sm(int fp64, int angular, int threads, int ilp) {
+int wall_ctas_per_sm(int fp64, int angular, int threads, int ilp, int packed) {
+    if (!wall_config_supported(fp64, threads, ilp, packed)) return 0;
+    if (packed) return angular ? wall_x2_occupancy<true>(threads, ilp) : wall_x2_occupancy<false>(threads, ilp);
     if (fp64) return angular ? wall_occupancy_r<double, true>(threads, ilp) : wall_occupancy_r<double, false>(threads, ilp);
     return angular ? wall_occupancy_r<float, true>(threads, ilp) : wall_occupancy_r<float, false>(threads, ilp);
 }
 
 cudaError_t launch_wall_mdot(const MdotArgs& a, cudaStream_t s) {
     if (a.N <= 0) return cudaSuccess;
-    if (a.packed) return cudaErrorInvalidConfiguration;
+    if (a.packed) {
+        if (a.fp64 || a.packed != 1) return cudaErrorInvalidConfiguration;
+        return a.angular ? launch_wall_x2<true>(a, s) : launch_wall_x2<false>(a, s);
+    }
     if (a.fp64) return a.angular ? launch_wall_r<double, true>(a, s) : launch_wall_r<double, false>(a, s);
     return a.angular ? launch_wall_r<float, true>(a, s) : launch_wall_r<float, false>(a, s);
 }

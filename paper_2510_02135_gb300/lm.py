@@ -89,12 +89,21 @@ def lib():
         L.lm_div_m.restype = st
         L.lm_div_m_rfd.argtypes = [_vp, ctypes.c_uint64, ctypes.c_double, _vp, _vp]
         L.lm_div_m_rfd.restype = st
+        L.lm_soft_repulsion.argtypes = [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _vp]
+        L.lm_soft_repulsion.restype = st
+        L.lm_ab_step.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_uint64, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_int, _vp, ctypes.c_int, _vp, ctypes.POINTER(ctypes.c_int)]
+        L.lm_ab_step.restype = st
         L.lm_mdot_backward.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
         L.lm_mdot_backward.restype = st
         L.lm_get_pair_config.argtypes = [_vp, ctypes.POINTER(lm_pair_config)]
         L.lm_get_pair_config.restype = st
         L.lm_set_pair_config.argtypes = [_vp, ctypes.POINTER(lm_pair_config)]
         L.lm_set_pair_config.restype = st
+        L.lm_get_adjoint_config.argtypes = [_vp, ctypes.POINTER(lm_pair_config)]
+        L.lm_get_adjoint_config.restype = st
+        L.lm_set_adjoint_config.argtypes = [_vp, ctypes.POINTER(lm_pair_config)]
+        L.lm_set_adjoint_config.restype = st
         L.lm_autotune.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(lm_pair_config)]
         L.lm_autotune.restype = st
         L.lm_get_lanczos_stats.argtypes = [_vp, ctypes.POINTER(lm_lanczos_stats)]
@@ -315,6 +324,33 @@ def lm_div_m_rfd(s: Solver, seed: int, delta: float, like):
     return lin, ang
 
 
+def lm_soft_repulsion(s: Solver, U0: float, b: float, d_pair: float, d_wall: float, like, out=None):
+    """Soft steric forces, Eq. (soft_potential) of Sec. 5.1, at the solver's positions."""
+    out = _like(like, (s.N, 3), s.f64) if out is None else out
+    s._sync_stream(out)
+    _check(lib().lm_soft_repulsion(s.handle, float(U0), float(b), float(d_pair), float(d_wall),
+                                   _ptr(out, s.f64, 3 * s.N, "forces_out")))
+    return out
+
+
+def lm_ab_step(s: Solver, forces, torques, history, first: bool, kT: float, dt: float, W=None, seed: int = 0,
+               tol: float = 1e-5, max_iter: int = 200, pos_out=None, like=None):
+    """One stochastic Adams-Bashforth step (Sec. 5.1).  ``history``: device
+    float64 tensor of 6N values owned by the caller.  Returns (new positions,
+    Lanczos iterations)."""
+    ref = forces if forces is not None else like
+    pos_out = _like(ref, (s.N, 3), s.f64) if pos_out is None else pos_out
+    s._sync_stream(pos_out)
+    it = ctypes.c_int(0)
+    nW = (6 if s.angular else 3) * s.N
+    _check(lib().lm_ab_step(s.handle, _ptr(forces, s.f64, 3 * s.N, "forces"), _ptr(torques, s.f64, 3 * s.N, "torques"),
+                            _ptr(W, True, nW, "W"), int(seed), float(kT), float(dt), float(tol), int(max_iter),
+                            _ptr(history, True, 6 * s.N, "history"), int(bool(first)), _ptr(pos_out, s.f64, 3 * s.N,
+                                                                                             "pos_out"),
+                            ctypes.byref(it)))
+    return pos_out, it.value
+
+
 def lm_mdot_backward(s: Solver, forces, torques, grad_lin, grad_ang, need_dX: bool = True, need_dF: bool = True):
     """Adjoint of lm_mdot.  Returns (dX, dF, dT)."""
     dX = _like(forces, (s.N, 3), s.f64) if need_dX else None
@@ -488,6 +524,17 @@ def lm_get_pair_config(s: Solver) -> dict:
 def lm_set_pair_config(s: Solver, threads: int, ilp: int, splits: int = 0, packed: int = 0) -> None:
     c = lm_pair_config(threads, ilp, splits, packed)
     _check(lib().lm_set_pair_config(s.handle, ctypes.byref(c)))
+
+
+def lm_get_adjoint_config(s: Solver) -> dict:
+    c = lm_pair_config()
+    _check(lib().lm_get_adjoint_config(s.handle, ctypes.byref(c)))
+    return {"threads": c.threads, "ilp": c.ilp, "splits": c.splits, "packed": c.packed}
+
+
+def lm_set_adjoint_config(s: Solver, threads: int, ilp: int, splits: int = 0, packed: int = 1) -> None:
+    c = lm_pair_config(threads, ilp, splits, packed)
+    _check(lib().lm_set_adjoint_config(s.handle, ctypes.byref(c)))
 
 
 def lm_autotune(s: Solver, reps: int = 3) -> dict:

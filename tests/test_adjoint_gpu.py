@@ -58,6 +58,31 @@ def test_adjoint_matches_oracle_gradient(orc, fp64, angular):
         assert rel(host(dT), gT) <= tol, rel(host(dT), gT)
 
 
+def test_adjoint_launch_configs_agree(orc):
+    """Every configuration of the packed translation adjoint (threads x ilp x
+    j per vote x splits) against the oracle gradient; N = 1100 is ragged for
+    every tile size."""
+    n = 1100
+    s_ = I.cube_suspension(61, n, 0.15, 1.0, angular=False, fp32=True)
+    s = lm.lm_create(1.0, 1.0, False, lm.LM_FP32C)
+    lm.lm_set_positions(s, dev(s_.pos))
+    gX = orc.grad(s_.pos, s_.F, None, s_.G, None, 1.0, 1.0, False)
+    gF, _ = orc.mdot(s_.pos, s_.G, None, 1.0, 1.0, False)
+    for threads in (128, 256):
+        for ilp in (2, 4):
+            for uj in (1, 2):
+                for splits in (1, 3, 9):
+                    lm.lm_set_adjoint_config(s, threads, ilp, splits, uj)
+                    dX, dF, _ = lm.lm_mdot_backward(s, dev(s_.F), None, dev(s_.G), None)
+                    cfg = (threads, ilp, uj, splits)
+                    assert rel(host(dX), gX) <= 1e-5, (cfg, rel(host(dX), gX))
+                    assert rel(host(dF), gF) <= 1e-5, (cfg, rel(host(dF), gF))
+    with pytest.raises(lm.LmError):
+        lm.lm_set_adjoint_config(s, 128, 3, 1, 1)
+    with pytest.raises(lm.LmError):
+        lm.lm_set_adjoint_config(s, 128, 4, 1, 0)
+
+
 def test_adjoint_skips_outputs_and_handles_coincident(orc):
     pos = np.array([[0, 0, 0], [0, 0, 0], [0.5, 0.1, 0.0], [3.0, 0.0, 1.0]], np.float64)
     rng = np.random.default_rng(2)
@@ -77,6 +102,7 @@ def test_adjoint_n65536_finite_differences(orc):
     s_ = I.cube_suspension(c["seed"], c["n"], c["phi"], c["a"], angular=False, fp32=True)
     s = lm.lm_create(c["eta"], c["a"], False, lm.LM_FP32C)
     lm.lm_set_positions(s, dev(s_.pos))
+    lm.lm_autotune(s, reps=1)        # the launch configuration the benchmark times
     dX, dF, _ = lm.lm_mdot_backward(s, dev(s_.F), None, dev(s_.G), None)
     dX, dF = host(dX), host(dF)
     rng = np.random.default_rng(7)

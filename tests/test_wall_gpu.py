@@ -43,10 +43,13 @@ def wall_suspension(seed, n, a, fp32, zlo=-0.3, zhi=10.0, side=None):
     return pos, F, T, W
 
 
-def make(eta, a, angular, fp64, pos):
+def make_solver(eta, a, angular, fp64, pos):
     s = lm.lm_create(eta, a, angular, lm.LM_FP64 if fp64 else lm.LM_FP32C, periodicity=("open", "open", "single_wall"))
     lm.lm_set_positions(s, dev(pos))
     return s
+
+
+make = make_solver
 
 
 def gpu_mdot(s, F, T):
@@ -55,11 +58,12 @@ def gpu_mdot(s, F, T):
     return u.double().cpu().numpy(), (w.double().cpu().numpy() if w is not None else None)
 
 
-@pytest.mark.parametrize("fp64", [False, True])
-def test_wall_mdot_blocks_match_oracle(orc, fp64):
+@pytest.mark.parametrize("fp64,packed", [(False, 0), (False, 1), (True, 0)])
+def test_wall_mdot_blocks_match_oracle(orc, fp64, packed):
     n, a, eta = 1500, 1.0, 0.8        # 11 tiles of 128 and a ragged tail of 92
     pos, F, T, _ = wall_suspension(21, n, a, not fp64)
     s = make(eta, a, True, fp64, pos)
+    lm.lm_set_pair_config(s, 128, 2 if packed else 1, 0, packed)
     tol = 1e-12 if fp64 else 1e-5
     zero = np.zeros_like(F)
     for name, Fv, Tv in (("F", F, zero), ("T", zero, T), ("FT", F, T)):
@@ -69,6 +73,7 @@ def test_wall_mdot_blocks_match_oracle(orc, fp64):
         assert rel(w, wr) <= tol, (name, "w", rel(w, wr))
     # translation only
     s3 = make(eta, a, False, fp64, pos)
+    lm.lm_set_pair_config(s3, 128, 2 if packed else 1, 0, packed)
     u, _ = gpu_mdot(s3, F, None)
     ur, _ = orc.mdot(pos, F, None, a, eta, False, wall=True)
     assert rel(u, ur) <= tol, rel(u, ur)
@@ -81,22 +86,31 @@ def test_wall_launch_configs_agree(orc, fp64, angular):
     s = make(eta, a, angular, fp64, pos)
     ur, wr = orc.mdot(pos, F, T, a, eta, angular, wall=True)
     tol = 1e-12 if fp64 else 1e-5
-    for threads in (128, 256):
-        for ilp in ((1,) if fp64 else (1, 2, 4)):
-            for splits in (1, 4, 11):
-                lm.lm_set_pair_config(s, threads, ilp, splits)
-                u, w = gpu_mdot(s, F, T)
-                assert rel(u, ur) <= tol, (threads, ilp, splits, rel(u, ur))
-                if angular:
-                    assert rel(w, wr) <= tol, (threads, ilp, splits, rel(w, wr))
+    for packed in ((0,) if fp64 else (0, 1)):
+        for threads in (128, 256):
+            for ilp in ((1,) if fp64 else ((2, 4) if packed else (1, 2, 4))):
+                for splits in (1, 4, 11):
+                    lm.lm_set_pair_config(s, threads, ilp, splits, packed)
+                    u, w = gpu_mdot(s, F, T)
+                    cfg = (threads, ilp, splits, packed)
+                    assert rel(u, ur) <= tol, (cfg, rel(u, ur))
+                    if angular:
+                        assert rel(w, wr) <= tol, (cfg, rel(w, wr))
     with pytest.raises(lm.LmError) as e:
-        lm.lm_set_pair_config(s, 128, 2, 1, packed=1)   # no packed form for the wall
+        lm.lm_set_pair_config(s, 128, 1, 1, packed=1)   # the packed form needs an even ilp
     assert e.value.status == lm.LM_ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("fp64", [False, True])
-def test_wall_edge_cases(orc, fp64):
+@pytest.mark.parametrize("fp64,packed", [(False, 0), (False, 1), (True, 0)])
+def test_wall_edge_cases(orc, fp64, packed):
     dt = np.float64 if fp64 else np.float32
+
+    def make(eta, a, angular, fp64, pos):
+        s = make_solver(eta, a, angular, fp64, pos)
+        if packed:
+            lm.lm_set_pair_config(s, 128, 2, 0, packed=1)
+        return s
+
     a, eta = 1.3, 0.7
     tol = 1e-12 if fp64 else 2e-6
     rng = np.random.default_rng(9)
