@@ -137,99 +137,142 @@ __device__ void pair_item(const BatchParams& P, int s, int i0, int jb, int je, c
     const int Ns = (int)(P.off[s + 1] - o);
     const float pad = (float)kPadCoord;
     const RpyConst<float>& k = P.k;
-    float xi[NI], yi[NI], zi[NI];
-    float pA[NI][3], hA[NI][3], lA[NI][3];
-    float pB[NRHS == 2 ? NI : 1][3], hB[NRHS == 2 ? NI : 1][3], lB[NRHS == 2 ? NI : 1][3];
+    // Packed form: each f32x2 instruction evaluates one i against two
+    // consecutive j (j-paired), so any i-blocking works; the j-tile is stored
+    // as structure-of-arrays floats (x[NT], y[NT], z[NT] in the float4 arrays'
+    // memory) so that a float2 load yields the pair (x_j, x_j+1).
+    float* tx = reinterpret_cast<float*>(sp);
+    float* ty = tx + NT;
+    float* tz = ty + NT;
+    float* ax = reinterpret_cast<float*>(sa);
+    float* ay = ax + NT;
+    float* az = ay + NT;
+    float* bx = reinterpret_cast<float*>(sb);
+    float* by = bx + NT;
+    float* bz = by + NT;
+    float2 xi[NI], yi[NI], zi[NI];
+    float2 pA[NI][3], pB[NRHS == 2 ? NI : 1][3];
+    float hA[NI][3], lA[NI][3];
+    float hB[NRHS == 2 ? NI : 1][3], lB[NRHS == 2 ? NI : 1][3];
 #pragma unroll
     for (int q = 0; q < NI; ++q) {
         const int i = i0 + q * NT + tid;
+        float x = -pad, y = -pad, z = -pad;
         if (i < Ns) {
             const float4 p = P.pos4[o + i];
-            xi[q] = p.x; yi[q] = p.y; zi[q] = p.z;
-        } else {
-            xi[q] = yi[q] = zi[q] = -pad;
+            x = p.x; y = p.y; z = p.z;
         }
+        // -x_i: d = x_j - x_i is the negated separation (exact); the tt terms are even in d
+        xi[q] = make_float2(-x, -x); yi[q] = make_float2(-y, -y); zi[q] = make_float2(-z, -z);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            pA[q][c] = hA[q][c] = lA[q][c] = 0.f;
-            if (NRHS == 2) pB[q][c] = hB[q][c] = lB[q][c] = 0.f;
+            pA[q][c] = make_float2(0.f, 0.f);
+            hA[q][c] = lA[q][c] = 0.f;
+            if (NRHS == 2) { pB[q][c] = make_float2(0.f, 0.f); hB[q][c] = lB[q][c] = 0.f; }
         }
     }
+    const float2 K1 = make_float2(k.K1, k.K1), nK2 = make_float2(-k.K2, -k.K2);
     for (int jt = jb; jt < je; jt += NT) {
         const int j = jt + tid;
         __syncthreads();
         if (j < je) {
-            sp[tid] = P.pos4[o + j];
-            float4 a;
+            const float4 pj = P.pos4[o + j];
+            tx[tid] = pj.x; ty[tid] = pj.y; tz[tid] = pj.z;
             if (srcA_f) {
-                a.x = srcA_f[3 * (o + j)]; a.y = srcA_f[3 * (o + j) + 1]; a.z = srcA_f[3 * (o + j) + 2];
+                ax[tid] = srcA_f[3 * (o + j)]; ay[tid] = srcA_f[3 * (o + j) + 1]; az[tid] = srcA_f[3 * (o + j) + 2];
             } else {
-                a.x = (float)(srcA_d[3 * (o + j)] * scaleA);
-                a.y = (float)(srcA_d[3 * (o + j) + 1] * scaleA);
-                a.z = (float)(srcA_d[3 * (o + j) + 2] * scaleA);
+                ax[tid] = (float)(srcA_d[3 * (o + j)] * scaleA);
+                ay[tid] = (float)(srcA_d[3 * (o + j) + 1] * scaleA);
+                az[tid] = (float)(srcA_d[3 * (o + j) + 2] * scaleA);
             }
-            a.w = 0.f;
-            sa[tid] = a;
-            if (NRHS == 2) sb[tid] = make_float4(P.Fbuf[3 * (o + j)], P.Fbuf[3 * (o + j) + 1], P.Fbuf[3 * (o + j) + 2], 0.f);
+            if (NRHS == 2) {
+                bx[tid] = P.Fbuf[3 * (o + j)]; by[tid] = P.Fbuf[3 * (o + j) + 1]; bz[tid] = P.Fbuf[3 * (o + j) + 2];
+            }
         } else {
-            sp[tid] = make_float4(pad, pad, pad, 0.f);
-            sa[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (NRHS == 2) sb[tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+            tx[tid] = pad; ty[tid] = pad; tz[tid] = pad;
+            ax[tid] = ay[tid] = az[tid] = 0.f;
+            if (NRHS == 2) bx[tid] = by[tid] = bz[tid] = 0.f;
         }
         __syncthreads();
-        for (int jj = 0; jj < NT; ++jj) {
-            const float4 pj = sp[jj];
-            const float4 fa = sa[jj];
-            float4 fb = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (NRHS == 2) fb = sb[jj];
-            float dx[NI], dy[NI], dz[NI], r2[NI];
+        for (int jj = 0; jj < NT; jj += 2) {
+            const float2 xj = *reinterpret_cast<const float2*>(tx + jj);
+            const float2 yj = *reinterpret_cast<const float2*>(ty + jj);
+            const float2 zj = *reinterpret_cast<const float2*>(tz + jj);
+            const float2 fx = *reinterpret_cast<const float2*>(ax + jj);
+            const float2 fy = *reinterpret_cast<const float2*>(ay + jj);
+            const float2 fz = *reinterpret_cast<const float2*>(az + jj);
+            float2 gx, gy, gz;
+            if (NRHS == 2) {
+                gx = *reinterpret_cast<const float2*>(bx + jj);
+                gy = *reinterpret_cast<const float2*>(by + jj);
+                gz = *reinterpret_cast<const float2*>(bz + jj);
+            }
+            float2 dx[NI], dy[NI], dz[NI], r2[NI];
             float mn = 0.f;
 #pragma unroll
             for (int q = 0; q < NI; ++q) {
-                dx[q] = xi[q] - pj.x; dy[q] = yi[q] - pj.y; dz[q] = zi[q] - pj.z;
-                r2[q] = fmaf(dx[q], dx[q], fmaf(dy[q], dy[q], dz[q] * dz[q]));
-                mn = (q == 0) ? r2[q] : fminf(mn, r2[q]);
+                dx[q] = __fadd2_rn(xj, xi[q]); dy[q] = __fadd2_rn(yj, yi[q]); dz[q] = __fadd2_rn(zj, zi[q]);
+                r2[q] = __ffma2_rn(dx[q], dx[q], __ffma2_rn(dy[q], dy[q], __fmul2_rn(dz[q], dz[q])));
+                const float m2 = fminf(r2[q].x, r2[q].y);
+                mn = (q == 0) ? m2 : fminf(mn, m2);
             }
             const bool near = __any_sync(0xffffffffu, mn < k.four_a2);
 #pragma unroll
             for (int q = 0; q < NI; ++q) {
-                float A, B;
-                if (near && r2[q] < k.four_a2) {
-                    const float invr = (r2[q] > 0.f) ? rsqrtf(r2[q]) : 0.f;
-                    const float r = r2[q] * invr;
-                    A = k.nA0 - k.nA1 * r;
-                    B = k.nB * invr;
+                float2 A, B;
+                if (near) {
+                    float a_[2], b_[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float rr = h ? r2[q].y : r2[q].x;
+                        if (rr < k.four_a2) {
+                            const float invr = (rr > 0.f) ? rsqrtf(rr) : 0.f;
+                            const float r = rr * invr;
+                            a_[h] = k.nA0 - k.nA1 * r;
+                            b_[h] = k.nB * invr;
+                        } else {
+                            const float invr = rsqrtf(rr);
+                            const float invr2 = invr * invr;
+                            const float invr3 = invr2 * invr;
+                            a_[h] = fmaf(k.K1, invr3, invr);
+                            b_[h] = fmaf(-k.K2, invr3 * invr2, invr3);
+                        }
+                    }
+                    A = make_float2(a_[0], a_[1]);
+                    B = make_float2(b_[0], b_[1]);
                 } else {
-                    const float invr = rsqrtf(r2[q]);
-                    const float invr2 = invr * invr;
-                    const float invr3 = invr2 * invr;
-                    A = fmaf(k.K1, invr3, invr);
-                    B = fmaf(-k.K2, invr3 * invr2, invr3);
+                    const float2 invr = make_float2(rsqrtf(r2[q].x), rsqrtf(r2[q].y));
+                    const float2 invr2 = __fmul2_rn(invr, invr);
+                    const float2 invr3 = __fmul2_rn(invr2, invr);
+                    A = __ffma2_rn(K1, invr3, invr);
+                    B = __ffma2_rn(nK2, __fmul2_rn(invr3, invr2), invr3);
                 }
-                const float sa_ = B * fmaf(dx[q], fa.x, fmaf(dy[q], fa.y, dz[q] * fa.z));
-                pA[q][0] = fmaf(sa_, dx[q], fmaf(A, fa.x, pA[q][0]));
-                pA[q][1] = fmaf(sa_, dy[q], fmaf(A, fa.y, pA[q][1]));
-                pA[q][2] = fmaf(sa_, dz[q], fmaf(A, fa.z, pA[q][2]));
+                const float2 sa_ = __fmul2_rn(B, __ffma2_rn(dx[q], fx, __ffma2_rn(dy[q], fy, __fmul2_rn(dz[q], fz))));
+                pA[q][0] = __ffma2_rn(sa_, dx[q], __ffma2_rn(A, fx, pA[q][0]));
+                pA[q][1] = __ffma2_rn(sa_, dy[q], __ffma2_rn(A, fy, pA[q][1]));
+                pA[q][2] = __ffma2_rn(sa_, dz[q], __ffma2_rn(A, fz, pA[q][2]));
                 if (NRHS == 2) {
-                    const float sb_ = B * fmaf(dx[q], fb.x, fmaf(dy[q], fb.y, dz[q] * fb.z));
-                    pB[q][0] = fmaf(sb_, dx[q], fmaf(A, fb.x, pB[q][0]));
-                    pB[q][1] = fmaf(sb_, dy[q], fmaf(A, fb.y, pB[q][1]));
-                    pB[q][2] = fmaf(sb_, dz[q], fmaf(A, fb.z, pB[q][2]));
+                    const float2 sb_ = __fmul2_rn(B, __ffma2_rn(dx[q], gx, __ffma2_rn(dy[q], gy, __fmul2_rn(dz[q], gz))));
+                    pB[q][0] = __ffma2_rn(sb_, dx[q], __ffma2_rn(A, gx, pB[q][0]));
+                    pB[q][1] = __ffma2_rn(sb_, dy[q], __ffma2_rn(A, gy, pB[q][1]));
+                    pB[q][2] = __ffma2_rn(sb_, dz[q], __ffma2_rn(A, gz, pB[q][2]));
                 }
             }
         }
-        // TwoSum fold of the tile partials
+        // TwoSum fold of the tile partials (the two j-lanes first added in FP32)
 #pragma unroll
         for (int q = 0; q < NI; ++q) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                float sm = hA[q][c] + pA[q][c], bb = sm - hA[q][c];
-                lA[q][c] += (hA[q][c] - (sm - bb)) + (pA[q][c] - bb);
-                hA[q][c] = sm; pA[q][c] = 0.f;
+                float pa = pA[q][c].x + pA[q][c].y;
+                float sm = hA[q][c] + pa, bb = sm - hA[q][c];
+                lA[q][c] += (hA[q][c] - (sm - bb)) + (pa - bb);
+                hA[q][c] = sm; pA[q][c] = make_float2(0.f, 0.f);
                 if (NRHS == 2) {
-                    sm = hB[q][c] + pB[q][c]; bb = sm - hB[q][c];
-                    lB[q][c] += (hB[q][c] - (sm - bb)) + (pB[q][c] - bb);
-                    hB[q][c] = sm; pB[q][c] = 0.f;
+                    const float pb = pB[q][c].x + pB[q][c].y;
+                    sm = hB[q][c] + pb; bb = sm - hB[q][c];
+                    lB[q][c] += (hB[q][c] - (sm - bb)) + (pb - bb);
+                    hB[q][c] = sm; pB[q][c] = make_float2(0.f, 0.f);
                 }
             }
         }
