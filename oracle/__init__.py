@@ -19,6 +19,8 @@ Contents (libMobility paper, Sec. 2 and Sec. 3.3):
   * ``rfd_sample``    -- one random finite difference sample of div M (Eq. rfd);
   * ``soft_repulsion``-- forces of the soft steric potential, Eq. (soft_potential);
   * ``ab_step``       -- one stochastic Adams-Bashforth step (Sec. 5.1);
+  * ``sqrt_jacobi_exact`` -- the square root P^{-1} (P M P)^{1/2} W that the
+                         Jacobi-preconditioned Lanczos iteration approximates;
   * ``sqrt_exact``    -- the principal square root M^{1/2} W from the
                          symmetric eigendecomposition (the plain definition);
   * ``lanczos_sqrt``  -- the Krylov (Lanczos) approximation of M^{1/2} W that
@@ -463,3 +465,15 @@ def ab_step(pos, F, T, W, prev_u, prev_d, first: bool, kT: float, dt: float, a: 
     new = pos + dt * (1.5 * u - 0.5 * np.asarray(prev_u) + kT * (1.5 * d - 0.5 * np.asarray(prev_d))) \
         + np.sqrt(2.0 * kT * dt) * y
     return new, u, d
+
+
+def sqrt_jacobi_exact(M: np.ndarray, W: np.ndarray) -> np.ndarray:
+    """B W with B = P^{-1} (P M P)^{1/2}, P = diag(M)^{-1/2} (P_ii = 1 where
+    M_ii = 0): a square root of M (B B^T = M) that the Jacobi-preconditioned
+    Lanczos iteration approximates (Sec. 3.3 notes that the Krylov method can
+    be preconditioned).  The principal root of P M P is taken from its
+    symmetric eigendecomposition."""
+    d = np.diag(M).copy()
+    p = np.where(d > 0.0, 1.0 / np.sqrt(np.where(d > 0.0, d, 1.0)), 1.0)
+    Mt = p[:, None] * M * p[None, :]
+    return sqrt_exact(Mt, np.asarray(W, dtype=np.float64).ravel()) / p

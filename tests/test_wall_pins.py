@@ -222,3 +222,19 @@ def test_div_fd_pins():
         ref = mt * (9 / 8 * xi - 1.5 * xi ** 3 + 5 / 8 * xi ** 5) / h
         assert abs(lin[0, 2] - ref) <= 1e-7 * abs(ref), (h, lin, ref)
         assert np.abs(lin[0, :2]).max() < 1e-10 * abs(ref) and np.abs(ang).max() < 1e-10 * abs(ref)
+
+
+def test_jacobi_square_root_pins():
+    """B = P^{-1} (P M P)^{1/2}, P = diag(M)^{-1/2}: B B^T = M (so the
+    fluctuation-dissipation balance of Eq. fdt holds), and B is the principal
+    root when diag(M) is constant (open geometry, translation only)."""
+    rng = np.random.default_rng(12)
+    pos = np.column_stack([rng.uniform(-5, 5, (20, 2)), rng.uniform(-0.3, 4.0, 20)])   # damped and zero rows
+    M = oracle.assemble(pos, 1.0, 1.0, True, wall=True)
+    n = M.shape[0]
+    B = np.column_stack([oracle.sqrt_jacobi_exact(M, e) for e in np.eye(n)])
+    assert np.abs(B @ B.T - M).max() <= 1e-12 * np.abs(M).max()
+    posf = rng.uniform(-4, 4, (25, 3))
+    Mf = oracle.assemble(posf, 1.0, 1.0, False)
+    W = rng.standard_normal(75)
+    np.testing.assert_allclose(oracle.sqrt_jacobi_exact(Mf, W), oracle.sqrt_exact(Mf, W), rtol=1e-11, atol=1e-14)
