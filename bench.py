@@ -198,7 +198,8 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["rpy6", "melt", "adjoint", "bd256", "wall"], default="rpy6")
+    ap.add_argument("--workload", choices=["rpy6", "melt", "adjoint", "bd256", "wall", "rollers"], default="rpy6")
+    ap.add_argument("--jacobi", action="store_true", help="rollers: Jacobi-preconditioned Lanczos")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default pair-kernel configuration")
     ap.add_argument("--pair-config", default=None,
                     help="threads,ilp,splits,packed: use this pair-kernel configuration instead of autotuning "
@@ -218,6 +219,8 @@ def main():
         return run_bd(args, ws, rank, local)
     if args.workload == "wall":
         return run_wall(args, ws, rank, local)
+    if args.workload == "rollers":
+        return run_rollers(args, ws, rank, local)
 
     import torch
 
@@ -286,14 +289,7 @@ def main():
     step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
     total_ms = float(sum(step_ms))
     pairs = float(n) * float(n) * float(sum(1 + it for it in iters))
-    if dist is not None:
-        t = torch.tensor([total_ms, pairs], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_ms_max, pairs_all = float(tmax[0]), float(t[1])
-    else:
-        total_ms_max, pairs_all = total_ms, pairs
+    total_ms_max, pairs_all = _reduce(dist, total_ms, pairs)
     value = pairs_all / (total_ms_max / 1e3)
 
     # e2e: the same step through host (pinned) buffers, copies inside the timed region
@@ -320,12 +316,7 @@ def main():
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
     e2e_pairs = float(n) * float(n) * float(sum(1 + it for it in e2e_iters))
-    if dist is not None:
-        t = torch.tensor([t_e2e, e2e_pairs], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        t_e2e, e2e_pairs = float(tmax[0]), float(t[1])
+    t_e2e, e2e_pairs = _reduce(dist, t_e2e, e2e_pairs)
     e2e_value = e2e_pairs / t_e2e
     h2d = n * 3 * 4 * 3 + W_h.numel() * 8
     d2h = n * 3 * 4 * 4
@@ -382,12 +373,15 @@ def _dist_init(ws, local):
 
 
 def _reduce(dist, t_ms, units):
-    """(max time over ranks, sum of units over ranks)."""
+    """(max time over ranks, sum of units over ranks): the job's time is the
+    slowest rank's and its work is every rank's (replicas, weak scaling).
+    Runs on the GPU with NCCL and on the CPU with gloo."""
     if dist is None:
         return t_ms, units
     import torch
 
-    t = torch.tensor([t_ms, units], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([t_ms, units], dtype=torch.float64, device=dev)
     tmax = t.clone()
     dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
@@ -557,6 +551,94 @@ def run_wall(args, ws, rank, local):
                          "frac": achieved / peak, "traffic": None,
                          "kernel": f"rpy_wall_kernel (translation, {WALL_FLOPS_PER_PAIR_TT} flops/pair)",
                          "pair_kernel_ms_avg": kern_ms},
+            "gpu_launches": launches, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def run_rollers(args, ws, rank, local):
+    """The active-roller example (Sec. 5.1) as a step of the library: soft
+    steric forces (pairs and wall) + gravity, a constant torque about y, and
+    one stochastic Adams-Bashforth step (mobility product, one RFD sample of
+    the thermal drift = two products, Lanczos square root at tol 1e-3) for
+    N = 32768 spheres above a no-slip wall, FP32, all blocks.  Pairs counted:
+    N^2 per application of M (the product, the two RFD products and every
+    Lanczos iteration)."""
+    import torch
+
+    from paper_2510_02135_gb300 import _build, inputs as I, lm
+
+    dist = _dist_init(ws, local)
+    _build.build()
+    c = I.ROLLERS_N32768
+    n, a, eta, kT = c["n"], c["a"], c["eta"], c["kT"]
+    pos0 = torch.from_numpy(I.roller_monolayer(c["seed"], n, a, c["area_fraction"])).cuda()
+    solver = lm.lm_create(eta, a, True, lm.LM_FP32C, periodicity=("open", "open", "single_wall"),
+                          cuda_stream=torch.cuda.current_stream().cuda_stream)
+    lm.lm_set_positions(solver, pos0)
+    if args.pair_config:
+        t_, i_, s_p, p_ = (int(v) for v in args.pair_config.split(","))
+        lm.lm_set_pair_config(solver, t_, i_, s_p, p_)
+    elif not args.no_autotune:
+        lm.lm_autotune(solver, reps=2)
+    if args.jacobi:
+        lm.lm_set_sqrt_preconditioner(solver, 1)
+    mg = kT / ((c["h_g"] - 1.0) * a)
+    T = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    T[:, 1] = 8 * np.pi * eta * a ** 3 * c["omega"]
+    hist = torch.zeros(6 * n, dtype=torch.float64, device="cuda")
+    X = pos0.clone()
+    stream = torch.cuda.current_stream()
+    state = {"k": 0}
+    iters = []
+
+    def step(timed=False):
+        F = lm.lm_soft_repulsion(solver, 4 * kT, 0.1 * a, 2 * a, a, like=X)
+        F[:, 2] -= mg
+        Xn, it = lm.lm_ab_step(solver, F, T, hist, state["k"] == 0, kT, c["dt"], seed=state["k"], tol=c["tol"],
+                               max_iter=200, pos_out=X)
+        state["k"] += 1
+        if timed:
+            iters.append(it)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler.start()
+    launches0 = lm.lm_launch_count()
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        step(timed=True)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    launches = lm.lm_launch_count() - launches0
+    total = float(sum(e0.elapsed_time(e1) for e0, e1 in evs))
+    pairs = float(n) * n * float(sum(3 + it for it in iters))
+    tmax, pairs_all = _reduce(dist, total, pairs)
+    line = {"metric": METRIC, "value": pairs_all / (tmax / 1e3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+            "config": {"workload": f"rollers_n32768: N={n} spheres of radius {a} above a no-slip wall, soft steric "
+                                   f"repulsion + gravity + torque, one stochastic Adams-Bashforth step per bench step "
+                                   f"(product, RFD drift, Lanczos tol {c['tol']}), FP32 pairs, all blocks",
+                       "lanczos_iterations_mean": float(np.mean(iters)),
+                       "preconditioner": "jacobi" if args.jacobi else "none",
+                       "pair_config": lm.lm_get_pair_config(solver),
+                       "l2": "flushed by a 256 MB device write before every step (outside the step events)"},
             "gpu_launches": launches, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))

@@ -131,6 +131,21 @@ lm_status lm_sqrt_mdot(lm_solver *solver, const double *W, uint64_t seed, double
                        double tol, int max_iter, void *lin_out, void *ang_out, int *iters_out);
 
 /*
+ * lm_set_sqrt_preconditioner -- preconditioning of the Lanczos square root
+ * (Sec. 3.3 notes that the Krylov method can be preconditioned; the paper's
+ * release does not).  kind 0: none (the default; lm_sqrt_mdot approximates
+ * the principal root M^{1/2} W).  kind 1: Jacobi, P = diag(M)^{-1/2} from the
+ * single-sphere mobilities (Swan-Brady and the damping with a single wall):
+ * lm_sqrt_mdot then approximates B W with B = P^{-1} (P M P)^{1/2}, another
+ * square root of M (B B^T = M, so the noise has the covariance of Eq. fdt),
+ * by the Lanczos iteration on P M P, whose spectrum is better conditioned when
+ * the diagonal of M varies (particles near or touching a wall).  The stopping
+ * rule applies to the iterates of (P M P)^{1/2} W.  kind other than 0, 1
+ * gives LM_ERR_INVALID_ARG.
+ */
+lm_status lm_set_sqrt_preconditioner(lm_solver *solver, int kind);
+
+/*
  * lm_div_m -- divM of Sec. 3.2: lin_i = sum_j d/dx_j . M_uF(i, j),
  * ang_i = sum_j d/dx_j . M_wF(i, j) (the thermal drift of Eq. bdhi is kT
  * times this).  For the open geometry the mobility is translation invariant

@@ -147,6 +147,9 @@ struct lm_solver {
     DBuf pos_raw, rfd_pos4, rfd_W, rfd_P, rfd_Q;
     // Adams-Bashforth step scratch: M [F; T] and the scaled square root (6N doubles / 6N values), new positions
     DBuf ab_u, ab_d, ab_y, ab_x;
+    // Jacobi preconditioner of the Lanczos square root: p = diag(M)^{-1/2}, q = diag(M)^{1/2}, scratch
+    int precond = 0;
+    DBuf pc_p, pc_q, pc_t;
     uint64_t rfd_calls = 0;
 
     // Lanczos state
@@ -175,7 +178,7 @@ struct lm_solver {
     ~lm_solver() {
         DBuf* all[] = {&pos4, &partials, &in_stage[0], &in_stage[1], &in_stage[2], &in_stage[3],
                        &out_stage[0], &out_stage[1], &out_stage[2], &flag, &tune_in, &tune_out,
-                       &pos_raw, &rfd_pos4, &rfd_W, &rfd_P, &rfd_Q, &ab_u, &ab_d, &ab_y, &ab_x,
+                       &pos_raw, &rfd_pos4, &rfd_W, &rfd_P, &rfd_Q, &ab_u, &ab_d, &ab_y, &ab_x, &pc_p, &pc_q, &pc_t,
                        &V, &w, &y, &red, &scal, &zbuf, &cbuf, &Wbuf};
         for (DBuf* b : all) b->release();
         if (pinned) cudaFreeHost(pinned);
@@ -705,7 +708,16 @@ lm_status enqueue_lanczos_iteration(lm_solver* s, int k, int64_t n, double* V, d
     double* vk = V + (int64_t)k * n;
     double* sk = scal + kScal * k;
     if (k > 0) LM_CUDA(lmk::lz_scale(w, sk - kScal + 1, vk, n, s->stream), "next basis vector");
-    if (lm_status st = run_mdot(s, vk, vk + 3 * N, 1, w, w + 3 * N, 1, s->cfg)) return st;
+    if (s->precond) {
+        // w = P M P v_k, P = diag(M)^{-1/2}
+        double* t = s->pc_t.as<double>();
+        const double* p = s->pc_p.as<double>();
+        LM_CUDA(lmk::launch_vmul(p, vk, t, n, s->stream), "preconditioner");
+        if (lm_status st = run_mdot(s, t, t + 3 * N, 1, w, w + 3 * N, 1, s->cfg)) return st;
+        LM_CUDA(lmk::launch_vmul(p, w, w, n, s->stream), "preconditioner");
+    } else {
+        if (lm_status st = run_mdot(s, vk, vk + 3 * N, 1, w, w + 3 * N, 1, s->cfg)) return st;
+    }
     LM_CUDA(lmk::lz_dot(vk, w, n, red, sk, s->stream), "alpha");
     LM_CUDA(lmk::lz_axpy2(w, vk, sk, k > 0 ? vk - n : nullptr, k > 0 ? sk - kScal + 1 : nullptr, n, s->stream),
             "three-term update");
@@ -774,6 +786,14 @@ lm_status lm_sqrt_mdot(lm_solver* s, const double* W, uint64_t seed, double pref
     double* red = s->red.as<double>();
     double* cb = s->cbuf.as<double>();
     double* wn = scal + kScal * (m_max + 2);  // |W|, |W|^2
+    if (s->precond) {
+        LM_CUDA(s->pc_p.ensure((size_t)n * sizeof(double)), "allocating preconditioner");
+        LM_CUDA(s->pc_q.ensure((size_t)n * sizeof(double)), "allocating preconditioner");
+        LM_CUDA(s->pc_t.ensure((size_t)n * sizeof(double)), "allocating preconditioner");
+        LM_CUDA(lmk::launch_mobility_diag(s->pos4.p, s->fp64, N, s->a, s->eta, s->angular, s->wall,
+                                          s->pc_p.as<double>(), s->pc_q.as<double>(), s->stream),
+                "preconditioner");
+    }
 
     // W: user array (host or device) or Philox normals
     const double* dW = nullptr;
@@ -858,6 +878,9 @@ lm_status lm_sqrt_mdot(lm_solver* s, const double* W, uint64_t seed, double pref
     LM_CUDA(cudaMemcpyAsync(s->zbuf.p, H.z.data(), (size_t)m * sizeof(double), cudaMemcpyHostToDevice, s->stream),
             "coefficients to device");
     LM_CUDA(lmk::lz_combine(V, m, s->zbuf.as<double>(), s->y.as<double>(), n, s->stream), "combine basis");
+    if (s->precond)   // y = P^{-1} (P M P)^{1/2} W
+        LM_CUDA(lmk::launch_vmul(s->pc_q.as<double>(), s->y.as<double>(), s->y.as<double>(), n, s->stream),
+                "preconditioner");
     LM_CUDA(lmk::lz_store(s->y.as<double>(), prefactor, N, s->angular, ov[0].dev, ov[1].dev, s->fp64, s->stream),
             "store result");
     // z lives in host memory read by the copy above: wait before it changes
@@ -904,6 +927,13 @@ lm_status lm_mdot_backward(lm_solver* s, const void* forces, const void* torques
     ensure_adjoint_config(s);
     if (lm_status st = run_adjoint(s, pF, pT, pG, pH, ov[0].dev, ov[1].dev, ov[2].dev, s->adj_cfg)) return st;
     return finish_out(s, ov, 3);
+}
+
+lm_status lm_set_sqrt_preconditioner(lm_solver* s, int kind) {
+    if (lm_status st = check_solver(s, false)) return st;
+    if (kind != 0 && kind != 1) return fail(LM_ERR_INVALID_ARG, "preconditioner kind must be 0 (none) or 1 (Jacobi)");
+    s->precond = kind;
+    return LM_OK;
 }
 
 lm_status lm_get_adjoint_config(lm_solver* s, lm_pair_config* cfg) {

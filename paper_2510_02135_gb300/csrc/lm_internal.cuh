@@ -147,6 +147,12 @@ cudaError_t launch_displace_pack_wall(const void* pos, int in_f64, const double*
                                       double a, void* pos4, int out_f64, cudaStream_t s);
 cudaError_t launch_rfd_difference(const double* P, const double* Q, double inv_delta, int64_t N, int angular,
                                   void* lin, void* ang, int out_f64, cudaStream_t s);
+// Jacobi preconditioner of the Lanczos square root (wall_kernels.cu):
+// p = diag(M)^{-1/2}, q = diag(M)^{1/2} from the packed positions (3N or 6N
+// doubles each), and y = a * x elementwise.
+cudaError_t launch_mobility_diag(const void* pos4, int fp64, int64_t N, double a, double eta, int angular, int wall,
+                                 double* p, double* q, cudaStream_t s);
+cudaError_t launch_vmul(const double* a, const double* x, double* y, int64_t n, cudaStream_t s);
 // Roller-example time stepping (integrator_kernels.cu): soft steric forces
 // (N x 3 positions in, N x 3 forces out, element type by f64) and the
 // stochastic Adams-Bashforth update of the positions.

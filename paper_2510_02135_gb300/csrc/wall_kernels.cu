@@ -756,7 +756,74 @@ __global__ void rfd_difference_kernel(const double* __restrict__ P, const double
     if (out_f64) static_cast<double*>(out)[k] = v;
     else static_cast<float*>(out)[k] = (float)v;
 }
+// Diagonal of the grand mobility from the packed positions, for the Jacobi
+// preconditioner of the Lanczos square root: p = diag(M)^{-1/2} and
+// q = diag(M)^{1/2} (p = 1, q = 0 where the diagonal is 0).  Open: the
+// single-sphere drags 1/(6 pi eta a) and 1/(8 pi eta a^3).  Single wall: the
+// Swan-Brady single-sphere functions at the clamped height h (xi = a/h),
+// 1 - 9/16 xi + 1/8 xi^3 - 1/16 xi^5 (x, y) and 1 - 9/8 xi + 1/2 xi^3 - 1/8 xi^5
+// (z) for translation, 1 - 5/16 xi^3 (x, y) and 1 - 1/8 xi^3 (z) for rotation,
+// times f^2 (the damping).
+template <typename R>
+__global__ void mobility_diag_kernel(const typename V4<R>::type* __restrict__ pos4, int64_t N, double a, double eta,
+                                     int angular, int wall, double* __restrict__ p, double* __restrict__ q) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const double pi = 3.14159265358979323846;
+    const double mt = 1.0 / (6.0 * pi * eta * a), mr = 1.0 / (8.0 * pi * eta * a * a * a);
+    double t[3] = {mt, mt, mt}, r[3] = {mr, mr, mr};
+    if (wall) {
+        const typename V4<R>::type v = pos4[i];
+        const double xi = a / (double)v.z, f = (double)v.w;
+        const double x2 = xi * xi, x3 = x2 * xi, x5 = x3 * x2;
+        const double f2 = f * f;
+        const double tp = 1.0 - 0.5625 * xi + 0.125 * x3 - 0.0625 * x5;
+        const double tn = 1.0 - 1.125 * xi + 0.5 * x3 - 0.125 * x5;
+        const double rp = 1.0 - 0.3125 * x3, rn = 1.0 - 0.125 * x3;
+        t[0] = t[1] = f2 * mt * tp;
+        t[2] = f2 * mt * tn;
+        r[0] = r[1] = f2 * mr * rp;
+        r[2] = f2 * mr * rn;
+    }
+    for (int c = 0; c < 3; ++c) {
+        p[3 * i + c] = t[c] > 0.0 ? 1.0 / sqrt(t[c]) : 1.0;
+        q[3 * i + c] = t[c] > 0.0 ? sqrt(t[c]) : 0.0;
+        if (angular) {
+            p[3 * N + 3 * i + c] = r[c] > 0.0 ? 1.0 / sqrt(r[c]) : 1.0;
+            q[3 * N + 3 * i + c] = r[c] > 0.0 ? sqrt(r[c]) : 0.0;
+        }
+    }
+}
+
+// y = a * x (elementwise, FP64)
+__global__ void vmul_kernel(const double* __restrict__ a, const double* __restrict__ x, double* __restrict__ y,
+                            int64_t n) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) y[e] = a[e] * x[e];
+}
 }  // namespace
+
+cudaError_t launch_mobility_diag(const void* pos4, int fp64, int64_t N, double a, double eta, int angular, int wall,
+                                 double* p, double* q, cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((N + 255) / 256);
+    if (fp64)
+        mobility_diag_kernel<double><<<blocks, 256, 0, s>>>(static_cast<const dvec4*>(pos4), N, a, eta, angular, wall,
+                                                             p, q);
+    else
+        mobility_diag_kernel<float><<<blocks, 256, 0, s>>>(static_cast<const float4*>(pos4), N, a, eta, angular, wall,
+                                                            p, q);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vmul(const double* a, const double* x, double* y, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    vmul_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, x, y, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 
 cudaError_t launch_displace_pack_wall(const void* pos, int in_f64, const double* W, double scale, int64_t N,
                                       double a, void* pos4, int out_f64, cudaStream_t s) {

@@ -174,3 +174,20 @@ MELT_N524288 = dict(seed=1005, n_chains=1024, beads=512, bond=2.2, sigma=0.3, ph
 # Single wall (the paper's "bottom wall" benchmark shape: random positions at
 # number density 0.1 / a^3, forces only).
 WALL_N32768 = dict(seed=1006, n=32768, rho=0.1, a=1.0, eta=1.0, angular=False, fp32=True)
+# The active-roller example (Sec. 5.1): N = 2^15 spheres of radius 0.656 um
+# above a wall in water (eta = 1e-3 aJ s / um^3), kT = 4.11e-3 aJ, gravitational
+# height 1.5 a, soft repulsion U0 = 4 kT, b = 0.1 a; a torque about y drives
+# the rollers.  Initial positions: uniform in a square of area fraction 0.3,
+# heights uniform in [a, 2a].
+ROLLERS_N32768 = dict(seed=1007, n=32768, a=0.656, eta=1e-3, kT=4.11e-3, h_g=1.5, area_fraction=0.3, dt=1e-3,
+                      tol=1e-3, omega=10.0)
+
+
+def roller_monolayer(seed: int, n: int, a: float, area_fraction: float, fp32: bool = True) -> np.ndarray:
+    """N centres uniform in a square of side sqrt(N pi a^2 / area_fraction)
+    centred at the origin, heights uniform in [a, 2a]."""
+    rng = np.random.default_rng(seed)
+    L = float(np.sqrt(n * np.pi * a * a / area_fraction))
+    u = rng.uniform(0.0, 1.0, size=(n, 3))
+    pos = np.column_stack([(u[:, 0] - 0.5) * L, (u[:, 1] - 0.5) * L, a * (1.0 + u[:, 2])])
+    return pos.astype(np.float32 if fp32 else np.float64)

@@ -89,6 +89,8 @@ def lib():
         L.lm_div_m.restype = st
         L.lm_div_m_rfd.argtypes = [_vp, ctypes.c_uint64, ctypes.c_double, _vp, _vp]
         L.lm_div_m_rfd.restype = st
+        L.lm_set_sqrt_preconditioner.argtypes = [_vp, ctypes.c_int]
+        L.lm_set_sqrt_preconditioner.restype = st
         L.lm_soft_repulsion.argtypes = [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _vp]
         L.lm_soft_repulsion.restype = st
         L.lm_ab_step.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_uint64, ctypes.c_double, ctypes.c_double,
@@ -322,6 +324,11 @@ def lm_div_m_rfd(s: Solver, seed: int, delta: float, like):
     _check(lib().lm_div_m_rfd(s.handle, int(seed), float(delta), _ptr(lin, s.f64, n3, "lin"),
                               _ptr(ang, s.f64, n3, "ang")))
     return lin, ang
+
+
+def lm_set_sqrt_preconditioner(s: Solver, kind: int) -> None:
+    """0: none (principal root), 1: Jacobi (B = P^-1 (P M P)^1/2, P = diag(M)^-1/2)."""
+    _check(lib().lm_set_sqrt_preconditioner(s.handle, int(kind)))
 
 
 def lm_soft_repulsion(s: Solver, U0: float, b: float, d_pair: float, d_wall: float, like, out=None):
