@@ -19,6 +19,8 @@ Contents (libMobility paper, Sec. 2 and Sec. 3.3):
   * ``rfd_sample``    -- one random finite difference sample of div M (Eq. rfd);
   * ``soft_repulsion``-- forces of the soft steric potential, Eq. (soft_potential);
   * ``ab_step``       -- one stochastic Adams-Bashforth step (Sec. 5.1);
+  * ``langevin_velocities`` -- the terms of Eq. (bdhi) over dt (Sec. 3.2,
+                         LangevinVelocities);
   * ``sqrt_jacobi_exact`` -- the square root P^{-1} (P M P)^{1/2} W that the
                          Jacobi-preconditioned Lanczos iteration approximates;
   * ``sqrt_exact``    -- the principal square root M^{1/2} W from the
@@ -477,3 +479,25 @@ def sqrt_jacobi_exact(M: np.ndarray, W: np.ndarray) -> np.ndarray:
     p = np.where(d > 0.0, 1.0 / np.sqrt(np.where(d > 0.0, d, 1.0)), 1.0)
     Mt = p[:, None] * M * p[None, :]
     return sqrt_exact(Mt, np.asarray(W, dtype=np.float64).ravel()) / p
+
+
+def langevin_velocities(pos, F, T, W, kT: float, dt: float, a: float, eta: float, angular: bool, wall: bool,
+                        rfd_seed: int, rfd_delta: float):
+    """LangevinVelocities of Sec. 3.2 (the terms of Eq. bdhi divided by dt):
+    M [F; T] + sqrt(2 kT / dt) M^{1/2} W + kT div M, with the principal root
+    (eigendecomposition) and one RFD sample of div M (zero in the open
+    geometry or at kT = 0).  Returns (lin, ang)."""
+    pos = _f64(pos).reshape(-1, 3)
+    n = pos.shape[0]
+    u, w = mdot(pos, F, T if angular else None, a, eta, angular, wall=wall)
+    y = np.zeros((6 if angular else 3) * n)
+    if kT > 0.0:
+        y = np.sqrt(2.0 * kT / dt) * sqrt_exact(assemble(pos, a, eta, angular, wall=wall), _f64(W).ravel())
+    lin = u + y[: 3 * n].reshape(n, 3)
+    ang = (w + y[3 * n:].reshape(n, 3)) if angular else None
+    if wall and kT > 0.0:
+        dl, da = rfd_sample(pos, rfd_seed, rfd_delta, a, eta, angular, wall)
+        lin = lin + kT * dl
+        if angular:
+            ang = ang + kT * da
+    return lin, ang

@@ -104,3 +104,22 @@ def test_ab_step_noise_and_drift_terms():
     y2 = oracle.sqrt_exact(M2, W).reshape(5, 3)
     np.testing.assert_allclose(new2, new + dt * kT * (1.5 * d2 - 0.5 * d) + np.sqrt(2 * kT * dt) * y2,
                                rtol=1e-13, atol=1e-15)
+
+
+def test_langevin_velocities_are_the_euler_maruyama_step_over_dt():
+    """dt times the Langevin velocities equals the displacement of the first
+    (Euler-Maruyama) step of the Adams-Bashforth scheme, a separate oracle
+    path; at kT = 0 they are M F."""
+    a, eta, kT, dt = 1.0, 1.0, 0.8, 0.01
+    rng = np.random.default_rng(9)
+    pos = np.column_stack([rng.uniform(-3, 3, (7, 2)), rng.uniform(1.1, 4, 7)])
+    F = rng.standard_normal((7, 3))
+    T = rng.standard_normal((7, 3))
+    W = rng.standard_normal(42)
+    lin, ang = oracle.langevin_velocities(pos, F, T, W, kT, dt, a, eta, True, True, 5, 1e-5)
+    new, _, _ = oracle.ab_step(pos, F, T, W, None, None, True, kT, dt, a, eta, True, True, 5, 1e-5)
+    np.testing.assert_allclose(dt * lin, new - pos, rtol=1e-10, atol=1e-15)
+    lin0, ang0 = oracle.langevin_velocities(pos, F, T, W, 0.0, dt, a, eta, True, True, 5, 1e-5)
+    u, w = oracle.mdot(pos, F, T, a, eta, True, wall=True)
+    np.testing.assert_array_equal(lin0, u)
+    np.testing.assert_array_equal(ang0, w)
