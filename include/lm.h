@@ -172,12 +172,37 @@ lm_status lm_div_m(lm_solver *solver, void *lin_out, void *ang_out);
 lm_status lm_div_m_rfd(lm_solver *solver, uint64_t seed, double delta, void *lin_out, void *ang_out);
 
 /*
+ * lm_set_wall_height -- setParameters(wallHeight) of Sec. 3.2 for a
+ * single-wall solver: the no-slip wall lies at z = height (default 0).  All
+ * heights (wall corrections, damping, the steric wall term) are measured from
+ * it; positions already set are re-packed.  Other solvers give
+ * LM_ERR_INVALID_ARG.
+ */
+lm_status lm_set_wall_height(lm_solver *solver, double height);
+
+/*
+ * lm_langevin_velocities -- LangevinVelocities of Sec. 3.2: the three terms
+ * of Eq. (bdhi) divided by dt, i.e. the velocities of one Euler-Maruyama
+ * step,
+ *   [lin; ang] = M [F; T] + sqrt(2 kT / dt) M^{1/2} W + kT divM,
+ * with the square root by the Lanczos method (lm_sqrt_mdot with tol,
+ * max_iter, seed; W NULL draws Philox normals keyed by seed) and divM one
+ * random finite difference sample keyed by seed (zero in the open
+ * geometry).  kT = 0 gives M [F; T].  forces, torques: N x 3 (NULL = zero;
+ * torques only with angular blocks); lin_out, ang_out as in lm_mdot.
+ * Returns the status of the Lanczos step.  Synchronises the stream.
+ */
+lm_status lm_langevin_velocities(lm_solver *solver, const void *forces, const void *torques, const double *W,
+                                 uint64_t seed, double kT, double dt, double tol, int max_iter,
+                                 void *lin_out, void *ang_out, int *iters_out);
+
+/*
  * lm_soft_repulsion -- forces of the soft steric potential of the roller
  * example, Eq. (soft_potential) of Sec. 5.1,
  *   U(r) = U0 (1 + (d - r)/b) for r < d,   U0 exp((d - r)/b) for r >= d,
  * summed over every particle pair (d = d_pair, r = centre distance) and,
  * for a single-wall solver, every particle-wall pair (d = d_wall, r = the
- * height z of the centre).  forces_out (N x 3, overwritten) = -dU/dX at the
+ * height of the centre above the wall).  forces_out (N x 3, overwritten) = -dU/dX at the
  * positions last set; a coincident pair (r = 0) exerts no force.  b > 0;
  * U0, d_pair, d_wall finite.  Direct O(N^2) sum on the GPU.
  */

@@ -1,6 +1,7 @@
-// Pieces of the roller example's time stepping (Sec. 5.1 of the libMobility
-// paper): the soft steric forces of Eq. (soft_potential) and the update of
-// the stochastic Adams-Bashforth scheme.
+// Pieces of the time stepping: the soft steric forces of Eq. (soft_potential)
+// and the update of the stochastic Adams-Bashforth scheme (the roller example,
+// Sec. 5.1 of the libMobility paper), and the combination of the three terms
+// of Eq. (bdhi) into Langevin velocities (Sec. 3.2, LangevinVelocities).
 //
 // Soft repulsion, a direct O(N^2) sum in the layout of the mobility kernels
 // (one i per thread, j-tiles of positions in shared memory):
@@ -31,7 +32,7 @@ __device__ __forceinline__ double rsq(double x) { return 1.0 / sqrt(x); }
 
 template <typename R, int NT>
 __global__ void __launch_bounds__(NT) soft_repulsion_kernel(const void* __restrict__ pos, int f64, int64_t N, R U0b,
-                                                            R inv_b, R d_pair, R d_wall, int wall,
+                                                            R inv_b, R d_pair, R d_wall, int wall, R z_wall,
                                                             void* __restrict__ out) {
     using R4 = typename P4<R>::type;
     __shared__ R4 sp[NT];
@@ -69,7 +70,10 @@ __global__ void __launch_bounds__(NT) soft_repulsion_kernel(const void* __restri
         }
     }
     if (!live) return;
-    if (wall) fz += U0b * ((zi < d_wall) ? R(1) : expo((d_wall - zi) * inv_b));
+    if (wall) {
+        const R h = zi - z_wall;   // height above the wall
+        fz += U0b * ((h < d_wall) ? R(1) : expo((d_wall - h) * inv_b));
+    }
     if (f64) {
         double* o = static_cast<double*>(out);
         o[3 * i] = fx; o[3 * i + 1] = fy; o[3 * i + 2] = fz;
@@ -102,18 +106,44 @@ __global__ void ab_update_kernel(const void* __restrict__ pos, int f64, const do
     else static_cast<float*>(out)[e] = (float)xn;
 }
 
+// Langevin velocities (Eq. bdhi divided by dt): u + kT d + y over the grand
+// vector; lin gets entries [0, 3N), ang [3N, 6N).
+__global__ void langevin_combine_kernel(const double* __restrict__ u, const double* __restrict__ d,
+                                        const void* __restrict__ y, double kT, int64_t N, int angular,
+                                        void* __restrict__ lin, void* __restrict__ ang, int out_f64) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n3 = 3 * N;
+    if (e >= (angular ? 2 * n3 : n3)) return;
+    const double ye = out_f64 ? static_cast<const double*>(y)[e] : (double)static_cast<const float*>(y)[e];
+    const double v = u[e] + (d ? kT * d[e] : 0.0) + ye;
+    void* out = (e < n3) ? lin : ang;
+    const int64_t k = (e < n3) ? e : e - n3;
+    if (out_f64) static_cast<double*>(out)[k] = v;
+    else static_cast<float*>(out)[k] = (float)v;
+}
+
 }  // namespace
 
+cudaError_t launch_langevin_combine(const double* u, const double* d, const void* y, double kT, int64_t N,
+                                    int angular, void* lin, void* ang, int out_f64, cudaStream_t s) {
+    const int64_t tot = (angular ? 6 : 3) * N;
+    if (tot <= 0) return cudaSuccess;
+    langevin_combine_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(u, d, y, kT, N, angular, lin, ang, out_f64);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_soft_repulsion(const void* pos, int f64, int64_t N, double U0, double b, double d_pair,
-                                  double d_wall, int wall, void* out, cudaStream_t s) {
+                                  double d_wall, int wall, double z_wall, void* out, cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
     constexpr int NT = 256;
     const unsigned blocks = (unsigned)((N + NT - 1) / NT);
     if (f64)
-        soft_repulsion_kernel<double, NT><<<blocks, NT, 0, s>>>(pos, 1, N, U0 / b, 1.0 / b, d_pair, d_wall, wall, out);
+        soft_repulsion_kernel<double, NT><<<blocks, NT, 0, s>>>(pos, 1, N, U0 / b, 1.0 / b, d_pair, d_wall, wall,
+                                                                z_wall, out);
     else
         soft_repulsion_kernel<float, NT><<<blocks, NT, 0, s>>>(pos, 0, N, (float)(U0 / b), (float)(1.0 / b),
-                                                               (float)d_pair, (float)d_wall, wall, out);
+                                                               (float)d_pair, (float)d_wall, wall, (float)z_wall, out);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -128,7 +128,8 @@ void set_last_error(const char* msg) { g_err = msg; }
 struct lm_solver {
     int angular = 0;
     int fp64 = 0;
-    int wall = 0;          // 1: no-slip wall at z = 0 ("single_wall" in z)
+    int wall = 0;          // 1: no-slip wall at z = z_wall ("single_wall" in z)
+    double z_wall = 0.0;   // wall height (setParameters(wallHeight) of Sec. 3.2)
     double eta = 1.0, a = 1.0;
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -434,8 +435,8 @@ lm_status rfd_sample(lm_solver* s, uint64_t seed, double delta, void* lin, void*
     ensure_config(s);
     for (int side = 0; side < 2; ++side) {
         const double scale = side == 0 ? 0.5 * delta : -0.5 * delta;
-        LM_CUDA(lmk::launch_displace_pack_wall(s->pos_raw.p, s->fp64, W, scale, N, s->a, s->rfd_pos4.p, s->fp64,
-                                               s->stream),
+        LM_CUDA(lmk::launch_displace_pack_wall(s->pos_raw.p, s->fp64, W, scale, N, s->a, s->z_wall, s->rfd_pos4.p,
+                                               s->fp64, s->stream),
                 "RFD positions");
         double* out = side == 0 ? s->rfd_P.as<double>() : s->rfd_Q.as<double>();
         if (lm_status st = run_mdot(s, W, s->angular ? W + 3 * N : nullptr, 1, out, s->angular ? out + 3 * N : nullptr,
@@ -525,8 +526,8 @@ lm_status lm_set_positions(lm_solver* s, const void* pos, int64_t N) {
     LM_CUDA(s->pos4.ensure((size_t)N * (s->fp64 ? sizeof(lmk::dvec4) : sizeof(float4))), "allocating positions");
     LM_CUDA(cudaMemsetAsync(s->flag.p, 0, sizeof(int), s->stream), "clearing flag");
     if (s->wall)
-        LM_CUDA(lmk::launch_pack_wall_positions(dpos, s->fp64, N, s->a, s->pos4.p, s->fp64, s->flag.as<int>(),
-                                                s->stream),
+        LM_CUDA(lmk::launch_pack_wall_positions(dpos, s->fp64, N, s->a, s->z_wall, s->pos4.p, s->fp64,
+                                                s->flag.as<int>(), s->stream),
                 "packing positions");
     else
         LM_CUDA(lmk::launch_pack_positions(dpos, s->fp64, N, s->pos4.p, s->fp64, s->flag.as<int>(), s->stream),
@@ -614,10 +615,79 @@ lm_status lm_soft_repulsion(lm_solver* s, double U0, double b, double d_pair, do
     const size_t bytes = (size_t)s->N * 3 * elem_size(s);
     OutView ov[1];
     if (lm_status st = stage_out(s, forces_out, bytes, 0, &ov[0])) return st;
-    LM_CUDA(lmk::launch_soft_repulsion(s->pos_raw.p, s->fp64, s->N, U0, b, d_pair, d_wall, s->wall, ov[0].dev,
-                                       s->stream),
+    LM_CUDA(lmk::launch_soft_repulsion(s->pos_raw.p, s->fp64, s->N, U0, b, d_pair, d_wall, s->wall, s->z_wall,
+                                       ov[0].dev, s->stream),
             "soft repulsion kernel");
     return finish_out(s, ov, 1);
+}
+
+lm_status lm_set_wall_height(lm_solver* s, double height) {
+    if (lm_status st = check_solver(s, false)) return st;
+    if (!s->wall) return fail(LM_ERR_INVALID_ARG, "the wall height applies to single_wall solvers only");
+    if (!std::isfinite(height) || std::fabs(height) > lmk::kMaxAbsCoord)
+        return fail(LM_ERR_INVALID_ARG, "wall height must be finite");
+    s->z_wall = height;
+    if (s->has_pos) {   // re-pack the positions relative to the new wall
+        DeviceGuard g(s->device);
+        LM_CUDA(cudaMemsetAsync(s->flag.p, 0, sizeof(int), s->stream), "clearing flag");
+        LM_CUDA(lmk::launch_pack_wall_positions(s->pos_raw.p, s->fp64, s->N, s->a, s->z_wall, s->pos4.p, s->fp64,
+                                                s->flag.as<int>(), s->stream),
+                "packing positions");
+    }
+    return LM_OK;
+}
+
+lm_status lm_langevin_velocities(lm_solver* s, const void* forces, const void* torques, const double* W,
+                                 uint64_t seed, double kT, double dt, double tol, int max_iter, void* lin_out,
+                                 void* ang_out, int* iters_out) {
+    if (lm_status st = check_solver(s, true)) return st;
+    if (lin_out == nullptr) return fail(LM_ERR_INVALID_ARG, "lin_out is NULL");
+    if (s->angular && ang_out == nullptr) return fail(LM_ERR_INVALID_ARG, "ang_out is required with angular blocks");
+    if (!s->angular && (ang_out != nullptr || torques != nullptr))
+        return fail(LM_ERR_INVALID_ARG, "torques or ang_out given but include_angular is 0");
+    if (!(kT >= 0.0) || !std::isfinite(kT)) return fail(LM_ERR_INVALID_ARG, "kT must be finite and >= 0");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(LM_ERR_INVALID_ARG, "dt must be > 0");
+    DeviceGuard g(s->device);
+    if (iters_out) *iters_out = 0;
+    const int64_t N = s->N;
+    const size_t n3 = (size_t)3 * N;
+    const size_t bytes = n3 * elem_size(s);
+    const void *dF = nullptr, *dT = nullptr;
+    if (lm_status st = stage_in(s, forces, bytes, 1, &dF)) return st;
+    if (lm_status st = stage_in(s, torques, bytes, 2, &dT)) return st;
+    OutView ov[2];
+    if (lm_status st = stage_out(s, lin_out, bytes, 0, &ov[0])) return st;
+    if (lm_status st = stage_out(s, ang_out, bytes, 1, &ov[1])) return st;
+    LM_CUDA(s->ab_u.ensure(2 * n3 * sizeof(double)), "allocating scratch");
+    LM_CUDA(s->ab_d.ensure(2 * n3 * sizeof(double)), "allocating scratch");
+    LM_CUDA(s->ab_y.ensure(2 * n3 * sizeof(double)), "allocating scratch");
+    double* u = s->ab_u.as<double>();
+    double* d = s->ab_d.as<double>();
+    if (dF == nullptr && dT == nullptr) {
+        LM_CUDA(cudaMemsetAsync(u, 0, 2 * n3 * sizeof(double), s->stream), "zero velocities");
+    } else {
+        ensure_config(s);
+        if (lm_status st = run_mdot(s, dF, dT, s->fp64, u, s->angular ? u + n3 : nullptr, 1, s->cfg)) return st;
+    }
+    const bool drift = s->wall && kT > 0.0;
+    if (drift) {
+        const double delta = (s->fp64 ? kRfdDeltaFP64 : kRfdDeltaFP32) * s->a;
+        if (lm_status st = rfd_sample(s, seed, delta, d, s->angular ? d + n3 : nullptr, 1)) return st;
+    }
+    void* y = s->ab_y.p;
+    if (kT > 0.0) {
+        int its = 0;
+        lm_status st = lm_sqrt_mdot(s, W, seed, std::sqrt(2.0 * kT / dt), tol, max_iter, y,
+                                    s->angular ? static_cast<char*>(y) + bytes : nullptr, &its);
+        if (iters_out) *iters_out = its;
+        if (st != LM_OK) return st;
+    } else {
+        LM_CUDA(cudaMemsetAsync(y, 0, 2 * bytes, s->stream), "zero noise");
+    }
+    LM_CUDA(lmk::launch_langevin_combine(u, drift ? d : nullptr, y, kT, N, s->angular, ov[0].dev, ov[1].dev, s->fp64,
+                                         s->stream),
+            "Langevin velocities");
+    return finish_out(s, ov, 2);
 }
 
 lm_status lm_ab_step(lm_solver* s, const void* forces, const void* torques, const double* W, uint64_t seed,

@@ -138,13 +138,14 @@ int adjoint_ctas_per_sm(int fp64, int angular, int threads, int ilp, int uj);
 // coordinates in *bad (device int, set to 1).
 cudaError_t launch_pack_positions(const void* pos, int in_f64, int64_t N, void* pos4, int out_f64,
                                   int* bad, cudaStream_t s);
-// Wall geometry: (x, y, max(z, a), f) with the damping factor f = clamp(z / a, 0, 1).
-cudaError_t launch_pack_wall_positions(const void* pos, int in_f64, int64_t N, double a, void* pos4, int out_f64,
-                                       int* bad, cudaStream_t s);
+// Wall geometry (wall at z = z0): (x, y, max(z - z0, a), f) with the damping
+// factor f = clamp((z - z0) / a, 0, 1).
+cudaError_t launch_pack_wall_positions(const void* pos, int in_f64, int64_t N, double a, double z0, void* pos4,
+                                       int out_f64, int* bad, cudaStream_t s);
 // Random finite differences (wall geometry): pack x + scale W (W: 3N doubles),
 // and write (P - Q) * inv_delta (FP64 grand vectors) to lin / ang.
 cudaError_t launch_displace_pack_wall(const void* pos, int in_f64, const double* W, double scale, int64_t N,
-                                      double a, void* pos4, int out_f64, cudaStream_t s);
+                                      double a, double z0, void* pos4, int out_f64, cudaStream_t s);
 cudaError_t launch_rfd_difference(const double* P, const double* Q, double inv_delta, int64_t N, int angular,
                                   void* lin, void* ang, int out_f64, cudaStream_t s);
 // Jacobi preconditioner of the Lanczos square root (wall_kernels.cu):
@@ -157,7 +158,11 @@ cudaError_t launch_vmul(const double* a, const double* x, double* y, int64_t n, 
 // (N x 3 positions in, N x 3 forces out, element type by f64) and the
 // stochastic Adams-Bashforth update of the positions.
 cudaError_t launch_soft_repulsion(const void* pos, int f64, int64_t N, double U0, double b, double d_pair,
-                                  double d_wall, int wall, void* out, cudaStream_t s);
+                                  double d_wall, int wall, double z_wall, void* out, cudaStream_t s);
+// out (lin / ang, element type by out_f64) = u + kT d + y over the 3N (6N)
+// entries: u, d FP64 grand vectors (d nullable = 0), y in the out precision.
+cudaError_t launch_langevin_combine(const double* u, const double* d, const void* y, double kT, int64_t N,
+                                    int angular, void* lin, void* ang, int out_f64, cudaStream_t s);
 cudaError_t launch_ab_update(const void* pos, int f64, const double* u, const double* d, const void* y,
                              double* hist, int first, double kT, double dt, int64_t N, void* out, cudaStream_t s);
 

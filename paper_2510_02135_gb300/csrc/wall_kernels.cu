@@ -21,7 +21,7 @@
 // The same expressions hold for i = j (R = 2h z): the single-sphere wall
 // corrections.
 //
-// Damping: set_positions stores each particle at height max(z, a) and its
+// Damping: set_positions stores each particle at height max(z - z_wall, a) and its
 // factor f = clamp(z / a, 0, 1) in the fourth component of the packed
 // position.  The j-tile loader multiplies F_j, T_j by f_j and the result is
 // multiplied by f_i, which gives M = D M(clamped) D, D = diag(f).
@@ -698,7 +698,7 @@ cudaError_t launch_wall_mdot(const MdotArgs& a, cudaStream_t s) {
 // --------------------------------------------------------------------------
 namespace {
 template <typename RO>
-__global__ void pack_wall_positions_kernel(const void* __restrict__ pos, int in_f64, int64_t N, double a,
+__global__ void pack_wall_positions_kernel(const void* __restrict__ pos, int in_f64, int64_t N, double a, double z0,
                                            typename V4<RO>::type* __restrict__ out, int* __restrict__ bad) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -712,6 +712,7 @@ __global__ void pack_wall_positions_kernel(const void* __restrict__ pos, int in_
     }
     const double m = kMaxAbsCoord;
     if (!(fabs(x) <= m && fabs(y) <= m && fabs(z) <= m)) atomicExch(bad, 1);
+    z -= z0;   // height above the wall
     double f = z / a;
     f = f > 0.0 ? (f < 1.0 ? f : 1.0) : 0.0;
     typename V4<RO>::type v;
@@ -722,7 +723,8 @@ __global__ void pack_wall_positions_kernel(const void* __restrict__ pos, int in_
 // (P - Q) / delta from two FP64 products.
 template <typename RO>
 __global__ void displace_pack_wall_kernel(const void* __restrict__ pos, int in_f64, const double* __restrict__ W,
-                                          double scale, int64_t N, double a, typename V4<RO>::type* __restrict__ out) {
+                                          double scale, int64_t N, double a, double z0,
+                                          typename V4<RO>::type* __restrict__ out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     double x, y, z;
@@ -735,7 +737,7 @@ __global__ void displace_pack_wall_kernel(const void* __restrict__ pos, int in_f
     }
     x = fma(scale, W[3 * i], x);
     y = fma(scale, W[3 * i + 1], y);
-    z = fma(scale, W[3 * i + 2], z);
+    z = fma(scale, W[3 * i + 2], z) - z0;
     double f = z / a;
     f = f > 0.0 ? (f < 1.0 ? f : 1.0) : 0.0;
     typename V4<RO>::type v;
@@ -826,13 +828,15 @@ cudaError_t launch_vmul(const double* a, const double* x, double* y, int64_t n, 
 
 
 cudaError_t launch_displace_pack_wall(const void* pos, int in_f64, const double* W, double scale, int64_t N,
-                                      double a, void* pos4, int out_f64, cudaStream_t s) {
+                                      double a, double z0, void* pos4, int out_f64, cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((N + 255) / 256);
     if (out_f64)
-        displace_pack_wall_kernel<double><<<blocks, 256, 0, s>>>(pos, in_f64, W, scale, N, a, static_cast<dvec4*>(pos4));
+        displace_pack_wall_kernel<double><<<blocks, 256, 0, s>>>(pos, in_f64, W, scale, N, a, z0,
+                                                                  static_cast<dvec4*>(pos4));
     else
-        displace_pack_wall_kernel<float><<<blocks, 256, 0, s>>>(pos, in_f64, W, scale, N, a, static_cast<float4*>(pos4));
+        displace_pack_wall_kernel<float><<<blocks, 256, 0, s>>>(pos, in_f64, W, scale, N, a, z0,
+                                                                 static_cast<float4*>(pos4));
     count_launches(1);
     return cudaGetLastError();
 }
@@ -846,14 +850,16 @@ cudaError_t launch_rfd_difference(const double* P, const double* Q, double inv_d
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_wall_positions(const void* pos, int in_f64, int64_t N, double a, void* pos4, int out_f64,
-                                       int* bad, cudaStream_t s) {
+cudaError_t launch_pack_wall_positions(const void* pos, int in_f64, int64_t N, double a, double z0, void* pos4,
+                                       int out_f64, int* bad, cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((N + 255) / 256);
     if (out_f64)
-        pack_wall_positions_kernel<double><<<blocks, 256, 0, s>>>(pos, in_f64, N, a, static_cast<dvec4*>(pos4), bad);
+        pack_wall_positions_kernel<double><<<blocks, 256, 0, s>>>(pos, in_f64, N, a, z0, static_cast<dvec4*>(pos4),
+                                                                   bad);
     else
-        pack_wall_positions_kernel<float><<<blocks, 256, 0, s>>>(pos, in_f64, N, a, static_cast<float4*>(pos4), bad);
+        pack_wall_positions_kernel<float><<<blocks, 256, 0, s>>>(pos, in_f64, N, a, z0, static_cast<float4*>(pos4),
+                                                                  bad);
     count_launches(1);
     return cudaGetLastError();
 }

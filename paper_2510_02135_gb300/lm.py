@@ -89,6 +89,11 @@ def lib():
         L.lm_div_m.restype = st
         L.lm_div_m_rfd.argtypes = [_vp, ctypes.c_uint64, ctypes.c_double, _vp, _vp]
         L.lm_div_m_rfd.restype = st
+        L.lm_set_wall_height.argtypes = [_vp, ctypes.c_double]
+        L.lm_set_wall_height.restype = st
+        L.lm_langevin_velocities.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_uint64, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_int, _vp, _vp, ctypes.POINTER(ctypes.c_int)]
+        L.lm_langevin_velocities.restype = st
         L.lm_set_sqrt_preconditioner.argtypes = [_vp, ctypes.c_int]
         L.lm_set_sqrt_preconditioner.restype = st
         L.lm_soft_repulsion.argtypes = [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _vp]
@@ -324,6 +329,29 @@ def lm_div_m_rfd(s: Solver, seed: int, delta: float, like):
     _check(lib().lm_div_m_rfd(s.handle, int(seed), float(delta), _ptr(lin, s.f64, n3, "lin"),
                               _ptr(ang, s.f64, n3, "ang")))
     return lin, ang
+
+
+def lm_set_wall_height(s: Solver, height: float) -> None:
+    """setParameters(wallHeight): the no-slip wall lies at z = height."""
+    _check(lib().lm_set_wall_height(s.handle, float(height)))
+
+
+def lm_langevin_velocities(s: Solver, forces, torques, kT: float, dt: float, W=None, seed: int = 0,
+                           tol: float = 1e-5, max_iter: int = 200, like=None):
+    """LangevinVelocities (Sec. 3.2): M [F; T] + sqrt(2 kT / dt) M^{1/2} W + kT divM.
+    Returns (lin, ang, Lanczos iterations)."""
+    ref = forces if forces is not None else like
+    lin = _like(ref, (s.N, 3), s.f64)
+    ang = _like(ref, (s.N, 3), s.f64) if s.angular else None
+    s._sync_stream(lin, ang)
+    it = ctypes.c_int(0)
+    nW = (6 if s.angular else 3) * s.N
+    _check(lib().lm_langevin_velocities(s.handle, _ptr(forces, s.f64, 3 * s.N, "forces"),
+                                        _ptr(torques, s.f64, 3 * s.N, "torques"), _ptr(W, True, nW, "W"), int(seed),
+                                        float(kT), float(dt), float(tol), int(max_iter),
+                                        _ptr(lin, s.f64, 3 * s.N, "lin"), _ptr(ang, s.f64, 3 * s.N, "ang"),
+                                        ctypes.byref(it)))
+    return lin, ang, it.value
 
 
 def lm_set_sqrt_preconditioner(s: Solver, kind: int) -> None:
@@ -662,3 +690,12 @@ class NBody:
 
     def divM(self, like):
         return lm_div_m(self.solver, like)
+
+    def setParameters(self, wallHeight: float = 0.0):
+        if self.periodicityZ == "single_wall":
+            lm_set_wall_height(self.solver, wallHeight)
+
+    def LangevinVelocities(self, dt, kbt, forces=None, torques=None, seed=0, tol=1e-5, max_iter=200, like=None):
+        lin, ang, _ = lm_langevin_velocities(self.solver, forces, torques, kbt, dt, seed=seed, tol=tol,
+                                             max_iter=max_iter, like=like)
+        return lin, ang

@@ -126,3 +126,52 @@ def test_roller_like_trajectory_stays_finite():
     assert np.isfinite(Xh).all()
     assert Xh[:, 2].min() > -a and Xh[:, 2].mean() > 0.5 * a
     assert np.abs(Xh[:, 0] - pos[:, 0]).mean() > 0.0
+
+
+@pytest.mark.parametrize("fp64,wall,angular", [(True, True, True), (False, True, False), (True, False, True)])
+def test_langevin_velocities_match_oracle(orc, fp64, wall, angular):
+    """LangevinVelocities (Sec. 3.2): M [F; T] + sqrt(2 kT/dt) M^{1/2} W +
+    kT divM against the oracle with the same W and RFD seed."""
+    a, eta, kT, dt = 1.0, 1.0, 0.6, 1e-3
+    n = 140
+    pos, rng = slab(35, n, a, 0.6 * a, 5 * a, 18 * a)
+    dt_ = np.float64 if fp64 else np.float32
+    pos = pos.astype(dt_)
+    F = rng.standard_normal((n, 3)).astype(dt_)
+    T = rng.standard_normal((n, 3)).astype(dt_) if angular else None
+    W = rng.standard_normal((6 if angular else 3) * n)
+    geo = ("open", "open", "single_wall" if wall else "open")
+    s = lm.lm_create(eta, a, angular, lm.LM_FP64 if fp64 else lm.LM_FP32C, periodicity=geo)
+    lm.lm_set_positions(s, dev(pos))
+    tol = 1e-11 if fp64 else 1e-6
+    lin, ang, it = lm.lm_langevin_velocities(s, dev(F), dev(T) if angular else None, kT, dt, W=dev(W), seed=17,
+                                             tol=tol, max_iter=400)
+    torch.cuda.synchronize()
+    rl, ra = orc.langevin_velocities(pos, F, T, W, kT, dt, a, eta, angular, wall, 17, 1e-4 if fp64 else 1e-2)
+    got = lin.double().cpu().numpy() if not angular else np.concatenate([lin.double().cpu().numpy(),
+                                                                          ang.double().cpu().numpy()])
+    ref = rl if not angular else np.concatenate([rl, ra])
+    # FP32: the RFD difference amplifies the 1e-7 rounding of the FP32 products by 1/delta, and the
+    # displaced positions are rounded to FP32 (ulp(|x|) against displacements of delta/2 = 5e-3 a)
+    assert rel(got, ref) <= (1e-8 if fp64 else 1e-3), (rel(got, ref), it)
+
+
+def test_wall_height_shifts_the_geometry(orc):
+    """setParameters(wallHeight): positions lifted by h above a wall at z = h
+    give the mobility of the unlifted positions above a wall at z = 0."""
+    a, eta, h = 1.0, 1.0, 3.25
+    pos, rng = slab(36, 300, a, -0.2 * a, 6 * a, 20 * a)
+    F = rng.standard_normal((300, 3))
+    T = rng.standard_normal((300, 3))
+    s = lm.lm_create(eta, a, True, lm.LM_FP64, periodicity=("open", "open", "single_wall"))
+    lm.lm_set_positions(s, dev(pos + np.array([0.0, 0.0, h])))
+    lm.lm_set_wall_height(s, h)
+    u, w = lm.lm_mdot(s, dev(F), dev(T))
+    ur, wr = orc.mdot(pos, F, T, a, eta, True, wall=True)
+    assert rel(u.cpu().numpy(), ur) <= 1e-12 and rel(w.cpu().numpy(), wr) <= 1e-12
+    Fs = lm.lm_soft_repulsion(s, 1.0, 0.1, 2.0, 1.0, like=dev(F))
+    Fr = orc.soft_repulsion(pos, 1.0, 0.1, 2.0, 1.0, True)
+    assert rel(Fs.cpu().numpy(), Fr) <= 1e-12
+    so = lm.lm_create(eta, a, True, lm.LM_FP64)
+    with pytest.raises(lm.LmError):
+        lm.lm_set_wall_height(so, 1.0)

@@ -247,3 +247,24 @@ def test_jacobi_preconditioned_sqrt_matches_oracle(orc, fp64, wall):
         assert it_pre < it_plain, (it_pre, it_plain)
     with pytest.raises(lm.LmError):
         lm.lm_set_sqrt_preconditioner(pre, 2)
+
+
+def test_wall_n32768_sampled_rows_bench_configuration(orc):
+    """The single-wall benchmark workload at full size (N = 32768 on the wall
+    at number density 0.1/a^3, forces only) in the autotuned launch
+    configuration the benchmark times; 256 sampled rows against the oracle,
+    and all blocks on the same positions."""
+    from paper_2510_02135_gb300 import inputs as I
+
+    c = I.WALL_N32768
+    s_ = I.wall_suspension(c["seed"], c["n"], c["rho"], c["a"], angular=True, fp32=True)
+    rows = np.random.default_rng(3).choice(c["n"], 256, replace=False)
+    for angular in (False, True):
+        s = make(c["eta"], c["a"], angular, False, s_.pos)
+        lm.lm_autotune(s, reps=1)
+        u, w = gpu_mdot(s, s_.F, s_.T if angular else None)
+        ur, wr = orc.mdot(s_.pos, s_.F, s_.T if angular else None, c["a"], c["eta"], angular, rows=rows, wall=True)
+        assert rel(u[rows], ur) <= 1e-5, (angular, rel(u[rows], ur))
+        if angular:
+            assert rel(w[rows], wr) <= 1e-5, rel(w[rows], wr)
+        assert np.isfinite(u).all()
