@@ -829,10 +829,28 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
             }
             if (!grid_sync(P)) return;
             stamp(P, step, slot);
-            // C3: first Gram-Schmidt pass; dots for a second pass and |w|^2 after.
+            // C3: first Gram-Schmidt pass and |w|^2 after it.
             // C4: second pass only if |w| dropped below |w_before| / sqrt(2)
-            //     (DGKS criterion); |w|^2 partials for beta.
+            //     (DGKS criterion): its dots, computed only for the systems that
+            //     need them (C4a), then the subtraction and the |w|^2 partials
+            //     for beta (C4b).
             for (int pass = 0; pass < 2; ++pass) {
+                if (pass == 1) {
+                    for (int c = blockIdx.x; c < P.n_chunks; c += G) {
+                        const int s = P.chunks[2 * c], e0 = P.chunks[2 * c + 1];
+                        if (!P.active[s]) continue;
+                        const int cb = P.chunk_range[2 * s], ce = P.chunk_range[2 * s + 1];
+                        const double h0 = warp_range_sum(partA + P.m_max, M1, cb, ce);
+                        const double h1 = warp_range_sum(partB + P.m_max, M1, cb, ce);
+                        if (!(h1 < 0.5 * h0)) continue;
+                        const int64_t o = P.off[s];
+                        const int ns = 3 * (int)(P.off[s + 1] - o);
+                        const int e1 = min(e0 + kBatchChunk, ns);
+                        chunk_dots<NT>(P, s, e0, e1, wcur + 3 * o, k + 1, partB + (int64_t)c * M1);
+                        __syncthreads();
+                    }
+                    if (!grid_sync(P)) return;
+                }
                 const double* pin = pass == 0 ? partA : partB;
                 double* pout = pass == 0 ? partB : partA;
                 for (int c = blockIdx.x; c < P.n_chunks; c += G) {
@@ -868,7 +886,6 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                         for (int ww = 0; ww < NT / 32; ++ww) t += sred[ww];
                         pout[(int64_t)c * M1 + (pass == 0 ? P.m_max : 0)] = t;
                     }
-                    if (pass == 0) chunk_dots<NT>(P, s, e0, e1, w, k + 1, pout + (int64_t)c * M1);
                     __syncthreads();
                 }
                 if (!grid_sync(P)) return;
