@@ -75,6 +75,17 @@ def test_null_solver_and_null_pointers(L):
     assert L.lm_sqrt_mdot(None, None, 0, 1.0, 1e-5, 10, None, None, None) == lm.LM_ERR_INVALID_ARG
     assert L.lm_mdot_backward(None, None, None, None, None, None, None, None) == lm.LM_ERR_INVALID_ARG
     assert L.lm_create(None, b"open", b"open", b"open", 1.0, 1.0, 0, 0, None) == lm.LM_ERR_INVALID_ARG
+    # entry points added for the single wall, the drift, the time stepping and the tuning
+    assert L.lm_div_m_rfd(None, 0, 1e-3, None, None) == lm.LM_ERR_INVALID_ARG
+    assert L.lm_set_wall_height(None, 0.0) == lm.LM_ERR_INVALID_ARG
+    assert L.lm_set_sqrt_preconditioner(None, 1) == lm.LM_ERR_INVALID_ARG
+    assert L.lm_soft_repulsion(None, 1.0, 0.1, 2.0, 1.0, None) == lm.LM_ERR_INVALID_ARG
+    assert L.lm_ab_step(None, None, None, None, 0, 1.0, 1e-3, 1e-5, 10, None, 1, None, None) == lm.LM_ERR_INVALID_ARG
+    assert L.lm_langevin_velocities(None, None, None, None, 0, 1.0, 1e-3, 1e-5, 10, None, None,
+                                    None) == lm.LM_ERR_INVALID_ARG
+    cfg = lm.lm_pair_config(128, 4, 0, 1)
+    assert L.lm_get_adjoint_config(None, ctypes.byref(cfg)) == lm.LM_ERR_INVALID_ARG
+    assert L.lm_set_adjoint_config(None, ctypes.byref(cfg)) == lm.LM_ERR_INVALID_ARG
 
 
 def test_create_without_gpu_reports_cuda_error(L):
