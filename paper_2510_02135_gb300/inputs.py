@@ -15,6 +15,8 @@ random in a cube, overlaps allowed):
   * ``wall_suspension``  -- N spheres uniform in a cube resting on the wall
     z = 0 (number density rho), for the single-wall geometry; centres below
     z = a overlap the wall.
+  * ``roller_monolayer`` -- the active-roller setting of Sec. 5.1: centres
+    uniform in a square at a given area fraction, heights uniform in [a, 2a].
 
 Everything is drawn in FP64 with numpy's PCG64 (``default_rng(seed)``) and,
 for FP32 workloads, rounded once to FP32, so the oracle and the GPU see
