@@ -200,6 +200,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["rpy6", "melt", "adjoint", "bd256", "wall", "rollers"], default="rpy6")
     ap.add_argument("--jacobi", action="store_true", help="rollers: Jacobi-preconditioned Lanczos")
+    ap.add_argument("--adjoint-config", default=None,
+                    help="adjoint workload: threads,ilp,splits,packed of the adjoint kernel instead of autotuning")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default pair-kernel configuration")
     ap.add_argument("--pair-config", default=None,
                     help="threads,ilp,splits,packed: use this pair-kernel configuration instead of autotuning "
@@ -406,8 +408,14 @@ def run_adjoint(args, ws, rank, local):
     u = torch.empty((n, 3), dtype=torch.float32, device="cuda")
     solver = lm.lm_create(c["eta"], c["a"], False, lm.LM_FP32C, cuda_stream=torch.cuda.current_stream().cuda_stream)
     lm.lm_set_positions(solver, pos)
-    if not args.no_autotune:
+    if args.pair_config:
+        t_, i_, s_p, p_ = (int(v) for v in args.pair_config.split(","))
+        lm.lm_set_pair_config(solver, t_, i_, s_p, p_)
+    elif not args.no_autotune:
         lm.lm_autotune(solver, reps=2)
+    if args.adjoint_config:
+        t_, i_, s_p, p_ = (int(v) for v in args.adjoint_config.split(","))
+        lm.lm_set_adjoint_config(solver, t_, i_, s_p, p_)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
