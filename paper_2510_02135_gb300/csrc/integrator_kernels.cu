@@ -19,7 +19,7 @@ namespace {
 
 template <typename R> struct P4;
 template <> struct P4<float> { using type = float4; };
-template <> struct P4<double> { using type = double4; };
+template <> struct P4<double> { using type = lmk::dvec4; };
 
 template <typename R>
 __device__ __forceinline__ R ld3(const void* p, int f64, int64_t idx) {
