@@ -242,14 +242,14 @@ lm_status finish_out(lm_solver* s, OutView* views, int nv) {
 // Split count minimising (waves x tiles per CTA): keeps all SMs busy when N
 // is small and limits the tail wave when N is large.  Split k of s holds
 // tiles [k T / s, (k + 1) T / s), so a CTA holds at most ceil(T / s) tiles.
-int lmk::auto_splits(int64_t N, int threads, int ilp, int slots) {
+int lmk::auto_splits(int64_t N, int threads, int ilp, int slots, int min_tps) {
     const int64_t nblk = (N + (int64_t)threads * ilp - 1) / ((int64_t)threads * ilp);
     const int64_t ntiles = (N + threads - 1) / threads;
     int best = 1;
     double best_cost = 1e300;
     for (int s = 1; s <= 64 && s <= ntiles; ++s) {
         const int64_t tps = (ntiles + s - 1) / s;
-        if (s > 1 && tps < 4) break;
+        if (s > 1 && tps < min_tps) break;
         const int64_t items = nblk * s;
         const int64_t waves = (items + slots - 1) / std::max(1, slots);
         const double cost = (double)waves * (double)tps * (1.0 + 0.002 * (double)s);
@@ -278,7 +278,7 @@ std::vector<int> split_candidates(int64_t N, int threads, int ilp, int slots) {
     const int64_t nblk = (N + (int64_t)threads * ilp - 1) / ((int64_t)threads * ilp);
     const int64_t ntiles = (N + threads - 1) / threads;
     const int sa = auto_splits(N, threads, ilp, slots);
-    std::vector<int> c = {sa, std::max(1, sa / 2), std::max(1, (3 * sa) / 2), sa * 2};
+    std::vector<int> c = {sa, std::max(1, sa / 2), std::max(1, (3 * sa) / 2), sa * 2, auto_splits(N, threads, ilp, slots, 1)};
     for (int w = 1; w <= 4; ++w) {
         const int64_t sp = ((int64_t)w * slots) / std::max<int64_t>(1, nblk);
         if (sp >= 1 && sp <= ntiles && sp <= 256 && sp * nblk == (int64_t)w * slots) c.push_back((int)sp);
@@ -302,9 +302,18 @@ lm_pair_config default_config(const lm_solver* s, int64_t N) {
         c.ilp = s->fp64 ? 1 : (s->angular ? 2 : 4);
         c.packed = s->fp64 ? 0 : 1;
     }
-    int occ = pair_ctas_per_sm(s, c.threads, c.ilp, c.packed);
-    if (occ < 1) occ = 1;
+    int occ = std::max(1, pair_ctas_per_sm(s, c.threads, c.ilp, c.packed));
     c.splits = auto_splits(N, c.threads, c.ilp, occ * s->sm_count);
+    const int64_t nblk = (N + (int64_t)c.threads * c.ilp - 1) / ((int64_t)c.threads * c.ilp);
+    if (nblk * lmk::mdot_effective_splits(N, c.threads, c.splits) < (int64_t)occ * s->sm_count) {
+        // too few CTAs to fill the GPU: the smallest i-blocks, and splits of down
+        // to one j-tile each
+        c.threads = 128;
+        c.ilp = s->fp64 ? 1 : 2;
+        c.packed = s->fp64 ? 0 : 1;
+        occ = std::max(1, pair_ctas_per_sm(s, c.threads, c.ilp, c.packed));
+        c.splits = auto_splits(N, c.threads, c.ilp, occ * s->sm_count, 1);
+    }
     return c;
 }
 
@@ -381,8 +390,18 @@ namespace {
 // overlap vote (1 or 2).
 lm_pair_config default_adjoint_config(const lm_solver* s) {
     lm_pair_config c{128, lmk::adjoint_ilp(s->fp64, s->angular), 1, (!s->fp64 && !s->angular) ? 1 : 0};
-    const int occ = std::max(1, lmk::adjoint_ctas_per_sm(s->fp64, s->angular, c.threads, c.ilp, c.packed));
+    int occ = std::max(1, lmk::adjoint_ctas_per_sm(s->fp64, s->angular, c.threads, c.ilp, c.packed));
     c.splits = auto_splits(s->N, c.threads, c.ilp, occ * s->sm_count);
+    const int64_t nblk = (s->N + (int64_t)c.threads * c.ilp - 1) / ((int64_t)c.threads * c.ilp);
+    if (nblk * lmk::mdot_effective_splits(s->N, c.threads, c.splits) < (int64_t)occ * s->sm_count) {
+        // too few CTAs to fill the GPU: splits of down to one j-tile, and for the
+        // packed kernel the smaller i-blocks
+        if (!s->fp64 && !s->angular) {
+            c.ilp = 2;
+            occ = std::max(1, lmk::adjoint_ctas_per_sm(s->fp64, s->angular, c.threads, c.ilp, c.packed));
+        }
+        c.splits = auto_splits(s->N, c.threads, c.ilp, occ * s->sm_count, 1);
+    }
     return c;
 }
 

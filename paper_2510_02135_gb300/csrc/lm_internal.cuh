@@ -117,8 +117,9 @@ struct AdjointArgs {
 // Launch-configuration tables (pair_kernels.cu / adjoint_kernels.cu).
 bool mdot_config_supported(int fp64, int angular, int threads, int ilp, int packed = 0);
 int mdot_ctas_per_sm(int fp64, int angular, int threads, int ilp, int packed = 0);
-// Default j-split count for `slots` concurrently resident CTAs (lm_api.cu).
-int auto_splits(int64_t N, int threads, int ilp, int slots);
+// Default j-split count for `slots` concurrently resident CTAs (lm_api.cu);
+// every split holds at least min_tps j-tiles.
+int auto_splits(int64_t N, int threads, int ilp, int slots, int min_tps = 4);
 // Number of j-splits actually launched for a requested split count.
 int64_t mdot_effective_splits(int64_t N, int threads, int splits);
 int mdot_partial_components(int angular);
