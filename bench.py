@@ -329,7 +329,8 @@ def main():
     achieved = prof["pair_flops"] / (prof["pair_ms"] / 1e3) / 1e12 if prof["pair_ms"] > 0 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": profile_traffic(),
-                "kernel": "rpy_mdot_kernel (forward pair kernel, FP32, all four blocks)",
+                "kernel": ("rpy_mdot_x2_kernel (forward pair kernel, packed FP32, all four blocks)" if cfg["packed"]
+                           else "rpy_mdot_kernel (forward pair kernel, scalar FP32, all four blocks)"),
                 "flops_per_pair": 86, "pair_launches": prof["pair_launches"],
                 "pair_kernel_ms_avg": prof["pair_ms"] / max(1, prof["pair_launches"]),
                 "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {RECIPE_MAX_SM_MHZ:.0f} MHz "
@@ -468,7 +469,8 @@ def run_adjoint(args, ws, rank, local):
                        "l2": "flushed by a 256 MB device write before every step"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "rpy_mdot_kernel (forward, translation, 35 flops/pair)"},
+                         "kernel": "forward pair kernel (%s, translation, 35 flops/pair)"
+                                   % ("packed" if lm.lm_get_pair_config(solver)["packed"] else "scalar")},
             "gpu_launches": launches, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))
@@ -557,7 +559,9 @@ def run_wall(args, ws, rank, local):
                        "l2": "flushed by a 256 MB device write before every step"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": f"rpy_wall_kernel (translation, {WALL_FLOPS_PER_PAIR_TT} flops/pair)",
+                         "kernel": "single-wall pair kernel (%s, translation, %d flops/pair)"
+                                   % ("packed" if lm.lm_get_pair_config(solver)["packed"] else "scalar",
+                                      WALL_FLOPS_PER_PAIR_TT),
                          "pair_kernel_ms_avg": kern_ms},
             "gpu_launches": launches, "clocks": clocks}
     if rank == 0:
