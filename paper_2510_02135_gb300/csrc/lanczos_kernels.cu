@@ -185,6 +185,128 @@ __global__ void philox_normals_kernel(uint64_t seed, uint64_t stream, double* __
     }
 }
 
+// ---------------------------------------------------------------------------
+// Single-launch forms: every block writes its partial result, and the last
+// block to finish (a device counter, reset by that block) adds the partials
+// in block order, so the results are deterministic and equal to the
+// two-launch forms'.  They halve the launches of a Lanczos iteration, which
+// bound its time at small N.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool last_block_done(unsigned* ctr) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(ctr, 1u) == gridDim.x - 1);
+    __syncthreads();
+    return last;
+}
+
+// Sum of red[0, nb) in the order of sum_stage2; called by the last block.
+__device__ __forceinline__ double final_sum(const double* red, int nb) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += kThreads) acc += __ldcg(red + b);
+    return block_sum(acc);
+}
+
+// mode 0: out[0] = x.y ; mode 1: out[0] = sqrt(x.x), out[1] = x.x
+__global__ void dot_fused(const double* __restrict__ x, const double* __restrict__ y, int64_t n, double* red,
+                          unsigned* ctr, double* __restrict__ out, int mode) {
+    double acc = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kThreads)
+        acc = fma(x[e], y[e], acc);
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) red[blockIdx.x] = acc;
+    if (!last_block_done(ctr)) return;
+    const double t = final_sum(red, gridDim.x);
+    if (threadIdx.x == 0) {
+        if (mode == 0) out[0] = t;
+        else { out[0] = sqrt(t); out[1] = t; }
+        *ctr = 0u;
+    }
+}
+
+// w -= alpha vk + beta vkm1, then out = (|w|, |w|^2)
+__global__ void axpy2_norm_kernel(double* __restrict__ w, const double* __restrict__ vk,
+                                  const double* __restrict__ alpha, const double* __restrict__ vkm1,
+                                  const double* __restrict__ beta, int64_t n, double* red, unsigned* ctr,
+                                  double* __restrict__ out) {
+    const double a = alpha[0];
+    const double b = (vkm1 != nullptr) ? beta[0] : 0.0;
+    double acc = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kThreads) {
+        double v = w[e] - a * vk[e];
+        if (vkm1 != nullptr) v -= b * vkm1[e];
+        w[e] = v;
+        acc = fma(v, v, acc);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) red[blockIdx.x] = acc;
+    if (!last_block_done(ctr)) return;
+    const double t = final_sum(red, gridDim.x);
+    if (threadIdx.x == 0) { out[0] = sqrt(t); out[1] = t; *ctr = 0u; }
+}
+
+// multidot_stage1, then the last block forms c[j] = sum_b red[j nb + b]
+// (the order of multidot_stage2).
+__global__ void multidot_fused(const double* __restrict__ V, int m, const double* __restrict__ w, int64_t n,
+                               int64_t cs, double* red, unsigned* ctr, double* __restrict__ c,
+                               const double* __restrict__ cond) {
+    if (!second_pass_needed(cond)) return;
+    const int64_t e0 = (int64_t)blockIdx.x * cs;
+    const int64_t e1 = (e0 + cs < n) ? (e0 + cs) : n;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int j = wid; j < m; j += kThreads / 32) {
+        const double* __restrict__ v = V + (int64_t)j * n;
+        double acc = 0.0;
+        for (int64_t e = e0 + lane; e < e1; e += 32) acc = fma(v[e], w[e], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) red[(int64_t)j * gridDim.x + blockIdx.x] = acc;
+    }
+    if (!last_block_done(ctr)) return;
+    const int nb = gridDim.x;
+    for (int j = wid; j < m; j += kThreads / 32) {
+        double acc = 0.0;
+        for (int b = lane; b < nb; b += 32) acc += __ldcg(red + (int64_t)j * nb + b);
+        acc = warp_sum(acc);
+        if (lane == 0) c[j] = acc;
+    }
+    if (threadIdx.x == 0) *ctr = 0u;
+}
+
+// w -= sum_j c[j] V[j] (skipped unless the DGKS test asks for it), then
+// out = (|w|, |w|^2) in any case.
+__global__ void sub_vc_norm_kernel(const double* __restrict__ V, int m, const double* __restrict__ c,
+                                   double* __restrict__ w, int64_t n, const double* __restrict__ cond, double* red,
+                                   unsigned* ctr, double* __restrict__ out) {
+    const bool apply = second_pass_needed(cond);
+    __shared__ double csh[256];
+    double nrm = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e - threadIdx.x < n;
+         e += (int64_t)gridDim.x * kThreads) {
+        double acc = 0.0;
+        if (apply) {
+            for (int j0 = 0; j0 < m; j0 += 256) {
+                const int mm = (m - j0 < 256) ? (m - j0) : 256;
+                __syncthreads();
+                if (threadIdx.x < mm) csh[threadIdx.x] = c[j0 + threadIdx.x];
+                __syncthreads();
+                if (e < n)
+                    for (int j = 0; j < mm; ++j) acc = fma(csh[j], V[(int64_t)(j0 + j) * n + e], acc);
+            }
+        }
+        if (e < n) {
+            const double v = apply ? fma(-1.0, acc, w[e]) : w[e];
+            w[e] = v;
+            nrm = fma(v, v, nrm);
+        }
+    }
+    nrm = block_sum(nrm);
+    if (threadIdx.x == 0) red[blockIdx.x] = nrm;
+    if (!last_block_done(ctr)) return;
+    const double t = final_sum(red, gridDim.x);
+    if (threadIdx.x == 0) { out[0] = sqrt(t); out[1] = t; *ctr = 0u; }
+}
+
 inline int64_t md_chunk(int64_t n, int* nb) {
     int64_t cs = (n + kMaxBlocks - 1) / kMaxBlocks;
     cs = (cs + 31) / 32 * 32;
@@ -240,6 +362,38 @@ cudaError_t lz_multidot(const double* V, int m, const double* w, int64_t n, doub
 cudaError_t lz_sub_vc(const double* V, int m, const double* c, double* w, int64_t n, cudaStream_t s,
                       const double* cond) {
     combine_kernel<<<blocks_for(n, 1), kThreads, 0, s>>>(V, m, c, w, n, 1, -1.0, cond);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t lz_dot1(const double* x, const double* y, int64_t n, double* red, unsigned* ctr, double* out,
+                    int mode, cudaStream_t s) {
+    dot_fused<<<blocks_for(n), kThreads, 0, s>>>(x, y, n, red, ctr, out, mode);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t lz_axpy2_norm(double* w, const double* vk, const double* alpha, const double* vkm1, const double* beta,
+                          int64_t n, double* red, unsigned* ctr, double* out, cudaStream_t s) {
+    axpy2_norm_kernel<<<blocks_for(n), kThreads, 0, s>>>(w, vk, alpha, vkm1, beta, n, red, ctr, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t lz_multidot1(const double* V, int m, const double* w, int64_t n, double* red, unsigned* ctr, double* c,
+                         cudaStream_t s, const double* cond) {
+    int nb = 0;
+    const int64_t cs = md_chunk(n, &nb);
+    // one block adds the partials: worth it while they are few
+    if ((int64_t)nb * m > 8192) return lz_multidot(V, m, w, n, red, c, s, cond);
+    multidot_fused<<<nb, kThreads, 0, s>>>(V, m, w, n, cs, red, ctr, c, cond);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t lz_sub_vc_norm(const double* V, int m, const double* c, double* w, int64_t n, double* red,
+                           unsigned* ctr, double* out, cudaStream_t s, const double* cond) {
+    sub_vc_norm_kernel<<<blocks_for(n, 1), kThreads, 0, s>>>(V, m, c, w, n, cond, red, ctr, out);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -151,6 +151,8 @@ struct lm_solver {
     // Jacobi preconditioner of the Lanczos square root: p = diag(M)^{-1/2}, q = diag(M)^{1/2}, scratch
     int precond = 0;
     DBuf pc_p, pc_q, pc_t;
+    // device counter of the single-launch reductions (zero between launches)
+    DBuf lzctr;
     uint64_t rfd_calls = 0;
 
     // Lanczos state
@@ -179,7 +181,7 @@ struct lm_solver {
     ~lm_solver() {
         DBuf* all[] = {&pos4, &partials, &in_stage[0], &in_stage[1], &in_stage[2], &in_stage[3],
                        &out_stage[0], &out_stage[1], &out_stage[2], &flag, &tune_in, &tune_out,
-                       &pos_raw, &rfd_pos4, &rfd_W, &rfd_P, &rfd_Q, &ab_u, &ab_d, &ab_y, &ab_x, &pc_p, &pc_q, &pc_t,
+                       &pos_raw, &rfd_pos4, &rfd_W, &rfd_P, &rfd_Q, &ab_u, &ab_d, &ab_y, &ab_x, &pc_p, &pc_q, &pc_t, &lzctr,
                        &V, &w, &y, &red, &scal, &zbuf, &cbuf, &Wbuf};
         for (DBuf* b : all) b->release();
         if (pinned) cudaFreeHost(pinned);
@@ -807,17 +809,18 @@ lm_status enqueue_lanczos_iteration(lm_solver* s, int k, int64_t n, double* V, d
     } else {
         if (lm_status st = run_mdot(s, vk, vk + 3 * N, 1, w, w + 3 * N, 1, s->cfg)) return st;
     }
-    LM_CUDA(lmk::lz_dot(vk, w, n, red, sk, s->stream), "alpha");
-    LM_CUDA(lmk::lz_axpy2(w, vk, sk, k > 0 ? vk - n : nullptr, k > 0 ? sk - kScal + 1 : nullptr, n, s->stream),
+    unsigned* ctr = s->lzctr.as<unsigned>();
+    LM_CUDA(lmk::lz_dot1(vk, w, n, red, ctr, sk, 0, s->stream), "alpha");
+    // three-term update and |w| before the Gram-Schmidt pass
+    LM_CUDA(lmk::lz_axpy2_norm(w, vk, sk, k > 0 ? vk - n : nullptr, k > 0 ? sk - kScal + 1 : nullptr, n, red, ctr,
+                               sk + 4, s->stream),
             "three-term update");
-    // full reorthogonalisation: one Gram-Schmidt pass, a second one only after cancellation (DGKS)
-    LM_CUDA(lmk::lz_norm(w, n, red, sk + 4, s->stream), "reorthogonalisation");
-    LM_CUDA(lmk::lz_multidot(V, k + 1, w, n, red, cb, s->stream), "reorthogonalisation");
-    LM_CUDA(lmk::lz_sub_vc(V, k + 1, cb, w, n, s->stream), "reorthogonalisation");
-    LM_CUDA(lmk::lz_norm(w, n, red, sk + 6, s->stream), "reorthogonalisation");
-    LM_CUDA(lmk::lz_multidot(V, k + 1, w, n, red, cb, s->stream, sk + 4), "reorthogonalisation");
-    LM_CUDA(lmk::lz_sub_vc(V, k + 1, cb, w, n, s->stream, sk + 4), "reorthogonalisation");
-    LM_CUDA(lmk::lz_norm(w, n, red, sk + 1, s->stream), "beta");
+    // full reorthogonalisation: one Gram-Schmidt pass (|w| after it), a second
+    // one only after cancellation (DGKS); beta = |w| at the end
+    LM_CUDA(lmk::lz_multidot1(V, k + 1, w, n, red, ctr, cb, s->stream), "reorthogonalisation");
+    LM_CUDA(lmk::lz_sub_vc_norm(V, k + 1, cb, w, n, red, ctr, sk + 6, s->stream), "reorthogonalisation");
+    LM_CUDA(lmk::lz_multidot1(V, k + 1, w, n, red, ctr, cb, s->stream, sk + 4), "reorthogonalisation");
+    LM_CUDA(lmk::lz_sub_vc_norm(V, k + 1, cb, w, n, red, ctr, sk + 1, s->stream, sk + 4), "beta");
     LM_CUDA(cudaMemcpyAsync(s->pinned + kScal * k, sk, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream),
             "read alpha, beta");
     LM_CUDA(cudaEventRecord(ev, s->stream), "iteration event");
@@ -856,6 +859,10 @@ lm_status lm_sqrt_mdot(lm_solver* s, const double* W, uint64_t seed, double pref
     LM_CUDA(s->scal.ensure((size_t)(kScal * (m_max + 3)) * sizeof(double)), "allocating scalars");
     LM_CUDA(s->zbuf.ensure((size_t)m_max * sizeof(double)), "allocating coefficients");
     LM_CUDA(s->cbuf.ensure((size_t)(m_max + 1) * sizeof(double)), "allocating coefficients");
+    if (s->lzctr.p == nullptr) {
+        LM_CUDA(s->lzctr.ensure(64), "allocating counters");
+        LM_CUDA(cudaMemsetAsync(s->lzctr.p, 0, 64, s->stream), "allocating counters");
+    }
     if (s->pinned_doubles < (size_t)(kScal * (m_max + 3))) {
         cudaFreeHost(s->pinned);
         s->pinned = nullptr;

@@ -184,6 +184,19 @@ cudaError_t lz_multidot(const double* V, int m, const double* w, int64_t n, doub
 // w -= sum_j c[j] v_j  (same optional condition)
 cudaError_t lz_sub_vc(const double* V, int m, const double* c, double* w, int64_t n, cudaStream_t s,
                       const double* cond = nullptr);
+// Single-launch forms (the last block adds the partials in block order and
+// resets *ctr, a device counter that must start at 0): lz_dot1 (mode 0: x.y,
+// mode 1: |x|, |x|^2), lz_axpy2_norm (lz_axpy2, then |w|, |w|^2 into out),
+// lz_multidot1 (lz_multidot), lz_sub_vc_norm (the conditional lz_sub_vc,
+// then |w|, |w|^2 into out).  `red` is scratch of lz_red_doubles(n, m).
+cudaError_t lz_dot1(const double* x, const double* y, int64_t n, double* red, unsigned* ctr, double* out,
+                    int mode, cudaStream_t s);
+cudaError_t lz_axpy2_norm(double* w, const double* vk, const double* alpha, const double* vkm1, const double* beta,
+                          int64_t n, double* red, unsigned* ctr, double* out, cudaStream_t s);
+cudaError_t lz_multidot1(const double* V, int m, const double* w, int64_t n, double* red, unsigned* ctr, double* c,
+                         cudaStream_t s, const double* cond = nullptr);
+cudaError_t lz_sub_vc_norm(const double* V, int m, const double* c, double* w, int64_t n, double* red,
+                           unsigned* ctr, double* out, cudaStream_t s, const double* cond = nullptr);
 // y = x / nrm[0]
 cudaError_t lz_scale(const double* x, const double* nrm, double* y, int64_t n, cudaStream_t s);
 // y = sum_j z[j] v_j
