@@ -712,23 +712,40 @@ def run_bd(args, ws, rank, local):
     clocks = sampler.stop()
     launches = lm.lm_launch_count() - launches0
     tmax, pairs_all = _reduce(dist, t, pairs)
-    # one BD step with per-system calls (same noise streams and tolerance)
+    # one BD step with per-system calls (same noise streams and tolerance): one
+    # solver per system with its buffers created beforehand and warmed up by
+    # one untimed step, so the timed step holds only the per-system calls
     t_loop = None
     if rank == 0:
         x = lm.lm_batch_get_positions(b, like=dev(b_.pos))
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
         sq = float(np.sqrt(2 * c["kT"] * c["dt"]))
+        solvers, bufs = [], []
         for s in range(b.S):
             o0, o1 = int(b_.offsets[s]), int(b_.offsets[s + 1])
-            sv = lm.lm_create(c["eta"], c["a"], False, lm.LM_FP32C)
-            xs = x[o0:o1].contiguous()
-            lm.lm_set_positions(sv, xs)
-            uu, _ = lm.lm_mdot(sv, (-c["k_trap"]) * xs, None)
-            W = torch.empty(3 * (o1 - o0), dtype=torch.float64, device="cuda")
-            lm.lm_philox_normals(c["seed"], (step_no[0] << 32) | s, W)
-            y, _, _ = lm.lm_sqrt_mdot(sv, W, tol=c["tol"], max_iter=64, prefactor=sq)
-            x[o0:o1] = xs + c["dt"] * uu + y
+            solvers.append(lm.lm_create(c["eta"], c["a"], False, lm.LM_FP32C))
+            ns = o1 - o0
+            bufs.append((torch.empty(3 * ns, dtype=torch.float64, device="cuda"),
+                         torch.empty((ns, 3), dtype=torch.float32, device="cuda"),
+                         torch.empty((ns, 3), dtype=torch.float32, device="cuda"),
+                         torch.empty((ns, 3), dtype=torch.float32, device="cuda")))
+
+        def per_system_step(xx, step):
+            for s in range(b.S):
+                o0, o1 = int(b_.offsets[s]), int(b_.offsets[s + 1])
+                sv = solvers[s]
+                W, Fs, uu, y = bufs[s]
+                xs = xx[o0:o1]
+                lm.lm_set_positions(sv, xs)
+                torch.mul(xs, -c["k_trap"], out=Fs)
+                lm.lm_mdot(sv, Fs, None, uu, None)
+                lm.lm_philox_normals(c["seed"], (step << 32) | s, W)
+                lm.lm_sqrt_mdot(sv, W, tol=c["tol"], max_iter=64, prefactor=sq, lin_out=y)
+                xx[o0:o1] = xs + c["dt"] * uu + y
+
+        per_system_step(x.clone(), step_no[0])      # warm-up: allocations, autotuning-free defaults
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        per_system_step(x, step_no[0])
         torch.cuda.synchronize()
         t_loop = time.perf_counter() - t1
     ms_bd_step = tmax / (args.steps * nsub)
