@@ -158,8 +158,8 @@ def profile_traffic():
     if vals.get("kernel_source_sha256_16") != src_hash:
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
+        return float(vals["dram_bytes_per_launch"].split()[0])
+    except (KeyError, ValueError, IndexError):
         return None
 
 

@@ -54,3 +54,18 @@ def test_reference_arm_runs_on_rank_zero_only(tmp_path):
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                         "--warmup", "3"], env=env, capture_output=True, text=True, timeout=120, cwd=str(tmp_path))
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_profile_traffic_read_from_the_committed_summary():
+    """The roofline's traffic figure comes from the committed ncu summary of
+    the pair kernel, and only while that summary's source hash is current."""
+    import bench
+
+    path = os.path.join(ROOT, "profiles", "pair_kernel_rpy6_n32768.txt")
+    vals = dict(line.split(":", 1) for line in open(path) if ":" in line)
+    current = vals["kernel_source_sha256_16"].strip() == bench.pair_kernel_source_hash()
+    t = bench.profile_traffic()
+    if current:
+        assert t == float(vals["dram_bytes_per_launch"].split()[0]) and t > 0
+    else:
+        assert t is None
