@@ -143,6 +143,15 @@ def oracle_pairs_per_s(pos, F, T, a, eta, budget_s: float):
     return nrows * n / t, nrows, t, oracle.num_threads()
 
 
+def measured_hbm_gbs():
+    """Copy bandwidth measured on this GPU pool (generated file), else the
+    recipe's fallback figure."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
 def profile_traffic():
     """DRAM bytes per pair-kernel launch from the committed ncu summary, if it
     was taken on the current kernel source (else None)."""
@@ -337,6 +346,20 @@ def main():
                               f"(recipe max SM clock; FP32 FMA peak)"}
     if clocks and achieved:
         roofline["frac_at_sampled_clock"] = achieved / (peak * clocks["sm_mhz"] / RECIPE_MAX_SM_MHZ)
+    # the Lanczos vector kernels of every timed iteration (HBM-bound FP64 streams)
+    hbm = measured_hbm_gbs()
+    vec_gbs = prof["vector_bytes"] / (prof["vector_ms"] / 1e3) / 1e9 if prof["vector_ms"] > 0 else None
+    vec_bytes_it = prof["vector_bytes"] / max(1, prof["vector_iterations"])
+    lanczos_vectors = {
+        "bound": "hbm", "achieved": vec_gbs, "peak": hbm, "unit": "GB/s",
+        "frac": (vec_gbs / hbm) if (vec_gbs and hbm) else None,
+        "iterations": prof["vector_iterations"], "ms_per_iteration": prof["vector_ms"] / max(1, prof["vector_iterations"]),
+        "share_of_step": prof["vector_ms"] / max(1e-9, total_ms),
+        "bytes_per_iteration_mean": vec_bytes_it,
+        "bytes_rule": "FP64 vectors of n=6N: alpha 2, three-term update 4, each Gram-Schmidt pass 2k+5 at iteration k",
+        "note": (f"basis of {n * 6 * 8 / 2**20:.1f} MB per vector; it stays in the 129 MB L2 for the first "
+                 f"{int(126e6 // (n * 6 * 8))} iterations of a step, so early iterations can read faster than HBM"),
+        "peak_basis": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -346,7 +369,7 @@ def main():
                        "sqrt_per_s": args.steps / (total_ms_max / 1e3),
                        "l2": "flushed by a 256 MB device write before every step (outside the step events)",
                        "pair_config": cfg, "parallelism": f"replicas x{ws}", "wall_s_timed": t_wall},
-            "roofline": roofline,
+            "roofline": roofline, "lanczos_vectors": lanczos_vectors,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps, "api": "lm_set_positions/lm_mdot/lm_sqrt_mdot with pinned host buffers"},
             "gpu_launches": launches, "clocks": clocks}

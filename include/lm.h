@@ -310,11 +310,17 @@ typedef struct {
 lm_status lm_get_lanczos_stats(lm_solver *solver, lm_lanczos_stats *stats);
 
 /*
- * Device-time profile of the forward pair kernel.  While enabled, the solver
- * records a CUDA event pair on its stream around every pair-kernel launch
- * (the split reduction is not included).  lm_profile_read synchronises the
- * stream, returns the totals since the last reset, and resets them if reset
- * is nonzero.
+ * Device-time profile of the forward pair kernel and of the Lanczos vector
+ * kernels.  While enabled, the solver records a CUDA event pair on its stream
+ * around every pair-kernel launch (the split reduction is not included) and
+ * around the vector kernels of every Lanczos iteration that follow its
+ * product (alpha, the three-term update, the Gram-Schmidt passes and beta).
+ * The bytes of an iteration are the algorithmic FP64 vector traffic, in
+ * vectors of n = 3N or 6N doubles: 2 + 4 (3 at k = 0) + (2k + 5) per
+ * Gram-Schmidt pass at 0-based iteration k, the second pass counted only
+ * where it ran.  Iterations of an lm_sqrt_mdot call that returned an error
+ * are left out.  lm_profile_read synchronises the stream, returns the totals
+ * since the last reset, and resets them if reset is nonzero.
  */
 typedef struct {
     int64_t pair_launches;    /* pair-kernel launches recorded */
@@ -322,6 +328,9 @@ typedef struct {
     double pair_interactions; /* ordered pairs evaluated, N^2 per launch */
     double pair_flops;        /* algorithmic flops: 35 per pair (forces only) or 86 (all blocks);
                                  single wall: 131 or 299 */
+    int64_t vector_iterations; /* Lanczos iterations whose vector kernels were timed */
+    double vector_ms;          /* their summed device time, milliseconds */
+    double vector_bytes;       /* their algorithmic bytes (see above) */
 } lm_profile;
 
 lm_status lm_profile_enable(lm_solver *solver, int enable);

@@ -177,6 +177,14 @@ struct lm_solver {
     std::vector<cudaEvent_t> prof_ev;   // pairs (begin, end)
     size_t prof_used = 0;               // event pairs in use
     double prof_pairs = 0.0;
+    // profiling of the Lanczos vector kernels: one event pair per iteration
+    // around the kernels that follow the product (alpha, three-term update,
+    // Gram-Schmidt passes, beta); bytes are counted once the iteration's
+    // scalars (and so whether the second pass ran) are on the host
+    std::vector<cudaEvent_t> vprof_ev;
+    std::vector<double> vprof_bytes;    // per event pair; < 0 while unknown
+    std::vector<std::pair<size_t, int>> vprof_pending;   // (event pair, iteration) of the running call
+    size_t vprof_used = 0;
 
     ~lm_solver() {
         DBuf* all[] = {&pos4, &partials, &in_stage[0], &in_stage[1], &in_stage[2], &in_stage[3],
@@ -186,6 +194,7 @@ struct lm_solver {
         for (DBuf* b : all) b->release();
         if (pinned) cudaFreeHost(pinned);
         for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
+        for (cudaEvent_t e : vprof_ev) cudaEventDestroy(e);
         for (cudaEvent_t e : lz_ev) cudaEventDestroy(e);
     }
 };
@@ -810,6 +819,20 @@ lm_status enqueue_lanczos_iteration(lm_solver* s, int k, int64_t n, double* V, d
         if (lm_status st = run_mdot(s, vk, vk + 3 * N, 1, w, w + 3 * N, 1, s->cfg)) return st;
     }
     unsigned* ctr = s->lzctr.as<unsigned>();
+    cudaEvent_t vend = nullptr;
+    if (s->prof_on) {
+        while (s->vprof_ev.size() < 2 * (s->vprof_used + 1)) {
+            cudaEvent_t e;
+            LM_CUDA(cudaEventCreate(&e), "profiling event");
+            s->vprof_ev.push_back(e);
+        }
+        s->vprof_bytes.resize(s->vprof_used + 1);
+        s->vprof_bytes[s->vprof_used] = -1.0;
+        s->vprof_pending.emplace_back(s->vprof_used, k);
+        LM_CUDA(cudaEventRecord(s->vprof_ev[2 * s->vprof_used], s->stream), "profiling event");
+        vend = s->vprof_ev[2 * s->vprof_used + 1];
+        s->vprof_used += 1;
+    }
     LM_CUDA(lmk::lz_dot1(vk, w, n, red, ctr, sk, 0, s->stream), "alpha");
     // three-term update and |w| before the Gram-Schmidt pass
     LM_CUDA(lmk::lz_axpy2_norm(w, vk, sk, k > 0 ? vk - n : nullptr, k > 0 ? sk - kScal + 1 : nullptr, n, red, ctr,
@@ -821,10 +844,33 @@ lm_status enqueue_lanczos_iteration(lm_solver* s, int k, int64_t n, double* V, d
     LM_CUDA(lmk::lz_sub_vc_norm(V, k + 1, cb, w, n, red, ctr, sk + 6, s->stream), "reorthogonalisation");
     LM_CUDA(lmk::lz_multidot1(V, k + 1, w, n, red, ctr, cb, s->stream, sk + 4), "reorthogonalisation");
     LM_CUDA(lmk::lz_sub_vc_norm(V, k + 1, cb, w, n, red, ctr, sk + 1, s->stream, sk + 4), "beta");
-    LM_CUDA(cudaMemcpyAsync(s->pinned + kScal * k, sk, 3 * sizeof(double), cudaMemcpyDeviceToHost, s->stream),
+    if (vend) LM_CUDA(cudaEventRecord(vend, s->stream), "profiling event");
+    LM_CUDA(cudaMemcpyAsync(s->pinned + kScal * k, sk, kScal * sizeof(double), cudaMemcpyDeviceToHost, s->stream),
             "read alpha, beta");
     LM_CUDA(cudaEventRecord(ev, s->stream), "iteration event");
     return LM_OK;
+}
+
+// Algorithmic bytes of the vector kernels of iteration k (those inside the
+// profiling events), in units of one FP64 vector of length n: alpha reads v_k
+// and w (2); the three-term update reads w, v_k, v_{k-1} and writes w (4, or
+// 3 at k = 0); a Gram-Schmidt pass reads the k + 1 basis vectors and w for
+// the dots (k + 2), then the basis, w and writes w (k + 3).
+double lanczos_vector_bytes(int k, int64_t n, bool second_pass) {
+    const double pass = (double)(k + 2) + (double)(k + 3);
+    const double units = 2.0 + (k > 0 ? 4.0 : 3.0) + pass * (second_pass ? 2.0 : 1.0);
+    return units * 8.0 * (double)n;
+}
+
+// Counts the bytes of the profiled iterations of the finished lm_sqrt_mdot
+// call (its scalars are on the host after the final synchronisation).
+void settle_vector_profile(lm_solver* s, int64_t n) {
+    for (const auto& pk : s->vprof_pending) {
+        const double* sc = s->pinned + kScal * pk.second;
+        const bool second = sc[6] < sc[4] * 0.70710678118654752440;   // the DGKS test the kernels apply
+        if (pk.first < s->vprof_bytes.size()) s->vprof_bytes[pk.first] = lanczos_vector_bytes(pk.second, n, second);
+    }
+    s->vprof_pending.clear();
 }
 
 }  // namespace
@@ -841,6 +887,7 @@ lm_status lm_sqrt_mdot(lm_solver* s, const double* W, uint64_t seed, double pref
     DeviceGuard g(s->device);
     if (iters_out) *iters_out = 0;
     s->stats = lm_lanczos_stats{0, 0, 0.0, 0.0, 0};
+    s->vprof_pending.clear();
 
     const int64_t N = s->N;
     const int64_t n = (s->angular ? 6 : 3) * N;
@@ -981,6 +1028,7 @@ lm_status lm_sqrt_mdot(lm_solver* s, const double* W, uint64_t seed, double pref
             "store result");
     // z lives in host memory read by the copy above: wait before it changes
     LM_CUDA(cudaStreamSynchronize(s->stream), "lanczos result");
+    settle_vector_profile(s, n);
     s->stats.iterations = m;
     s->stats.converged = converged ? 1 : 0;
     s->stats.rel_change = rel;
@@ -1193,9 +1241,23 @@ lm_status lm_profile_read(lm_solver* s, lm_profile* out, int reset) {
     out->pair_interactions = s->prof_pairs;
     out->pair_flops = s->prof_pairs * (s->wall ? (s->angular ? lmk::kFlopsPerPairWall6N : lmk::kFlopsPerPairWallTT)
                                                 : (s->angular ? lmk::kFlopsPerPair6N : lmk::kFlopsPerPairTT));
+    out->vector_iterations = 0;
+    out->vector_ms = 0.0;
+    out->vector_bytes = 0.0;
+    for (size_t k = 0; k < s->vprof_used && k < s->vprof_bytes.size(); ++k) {
+        if (s->vprof_bytes[k] < 0.0) continue;   // iteration of a call that did not finish
+        float t = 0.f;
+        LM_CUDA(cudaEventElapsedTime(&t, s->vprof_ev[2 * k], s->vprof_ev[2 * k + 1]), "profile read");
+        out->vector_iterations += 1;
+        out->vector_ms += t;
+        out->vector_bytes += s->vprof_bytes[k];
+    }
     if (reset) {
         s->prof_used = 0;
         s->prof_pairs = 0.0;
+        s->vprof_used = 0;
+        s->vprof_bytes.clear();
+        s->vprof_pending.clear();
     }
     return LM_OK;
 }

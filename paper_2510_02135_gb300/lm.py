@@ -56,7 +56,9 @@ class lm_lanczos_stats(ctypes.Structure):
 
 class lm_profile(ctypes.Structure):
     _fields_ = [("pair_launches", ctypes.c_int64), ("pair_ms", ctypes.c_double),
-                ("pair_interactions", ctypes.c_double), ("pair_flops", ctypes.c_double)]
+                ("pair_interactions", ctypes.c_double), ("pair_flops", ctypes.c_double),
+                ("vector_iterations", ctypes.c_int64), ("vector_ms", ctypes.c_double),
+                ("vector_bytes", ctypes.c_double)]
 
 
 _lib = None
@@ -593,7 +595,8 @@ def lm_profile_read(s: Solver, reset: bool = True) -> dict:
     p = lm_profile()
     _check(lib().lm_profile_read(s.handle, ctypes.byref(p), int(bool(reset))))
     return {"pair_launches": p.pair_launches, "pair_ms": p.pair_ms, "pair_interactions": p.pair_interactions,
-            "pair_flops": p.pair_flops}
+            "pair_flops": p.pair_flops, "vector_iterations": p.vector_iterations, "vector_ms": p.vector_ms,
+            "vector_bytes": p.vector_bytes}
 
 
 def lm_launch_count() -> int:

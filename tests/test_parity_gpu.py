@@ -297,6 +297,37 @@ def test_sqrt_rpy6_n32768_norm_identity(orc):
     assert st["converged"] and 2 <= it < 200
 
 
+def test_profile_counts_pairs_and_lanczos_vector_bytes():
+    """The device-time profile: one pair launch and N^2 pairs per product
+    (86 flops each with all blocks); one vector-kernel record per Lanczos
+    iteration enqueued (the speculative one included), with the algorithmic
+    bytes of the rule stated in the header, between the one-pass and the
+    two-pass counts."""
+    n = 2000
+    s_ = I.cube_suspension(5, n, 0.2, 1.0, angular=True, fp32=True)
+    s = make(1.0, 1.0, True, False, s_.pos)
+    lm.lm_sqrt_mdot(s, dev(s_.W), tol=1e-5, max_iter=200)   # warm-up, not profiled
+    lm.lm_profile_read(s, reset=True)
+    lm.lm_profile_enable(s, True)
+    lm.lm_mdot(s, dev(s_.F), dev(s_.T))
+    _, _, it = lm.lm_sqrt_mdot(s, dev(s_.W), tol=1e-5, max_iter=200)
+    lm.lm_profile_enable(s, False)
+    p = lm.lm_profile_read(s, reset=True)
+    nv = p["vector_iterations"]
+    assert it <= nv <= it + 1, (it, nv)
+    assert p["pair_launches"] == 1 + nv
+    assert p["pair_interactions"] == float(n) * n * (1 + nv)
+    assert p["pair_flops"] == 86.0 * p["pair_interactions"]
+    assert p["pair_ms"] > 0 and p["vector_ms"] > 0
+    vec = 8.0 * 6 * n
+    one = sum(2 + (4 if k else 3) + (2 * k + 5) for k in range(nv)) * vec
+    two = sum(2 + (4 if k else 3) + 2 * (2 * k + 5) for k in range(nv)) * vec
+    assert one <= p["vector_bytes"] <= two, (one, p["vector_bytes"], two)
+    # reset cleared everything
+    p2 = lm.lm_profile_read(s, reset=False)
+    assert p2["pair_launches"] == 0 and p2["vector_iterations"] == 0 and p2["vector_bytes"] == 0.0
+
+
 def test_sqrt_error_paths(orc):
     n = 200
     s_ = I.cube_suspension(4, n, 0.2, 1.0, angular=False, fp32=False)
