@@ -315,30 +315,47 @@ __device__ void pair_item(const BatchParams& P, int s, int i0, int jb, int je, c
 template <int NT>
 __device__ void chunk_dots(const BatchParams& P, int s, int e0, int e1, const double* w, int nrows,
                            double* part_out) {
-    // FP64 add latency is long (tens of cycles): each warp reduces four rows
-    // at once, so that four dependent chains overlap
+    // Each warp takes eight rows at a time: every lane runs eight independent
+    // FP64 chains over its elements (w read once per element, nine loads in
+    // flight; a deeper unroll costs the persistent kernel registers), then a transposing butterfly reduces the eight sums
+    // (after the offsets 16, 8 and 4 lane l holds row l >> 2; 9 shuffles and
+    // adds instead of 40).
     constexpr int NW = NT / 32;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t ns = 3 * (P.off[s + 1] - P.off[s]);
-    for (int j0 = wid * 4; j0 < nrows; j0 += NW * 4) {
-        const int nr = min(4, nrows - j0);
+    for (int j0 = wid * 8; j0 < nrows; j0 += NW * 8) {
+        const int nr = min(8, nrows - j0);
         const double* v = basis(P, s, 0) + j0 * ns;
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        double acc[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) acc[r] = 0.0;
+#pragma unroll 1
         for (int e = e0 + lane; e < e1; e += 32) {
             const double we = w[e];
-            a0 = fma(v[e], we, a0);
-            if (nr > 1) a1 = fma(v[ns + e], we, a1);
-            if (nr > 2) a2 = fma(v[2 * ns + e], we, a2);
-            if (nr > 3) a3 = fma(v[3 * ns + e], we, a3);
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+                if (r < nr) acc[r] = fma(v[r * ns + e], we, acc[r]);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-            a3 += __shfl_xor_sync(0xffffffffu, a3, o);
+        for (int r = 0; r < 4; ++r) {
+            const bool up = lane & 16;
+            const double keep = up ? acc[r + 4] : acc[r], send = up ? acc[r] : acc[r + 4];
+            acc[r] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
         }
-        if (lane < nr) part_out[j0 + lane] = lane == 0 ? a0 : lane == 1 ? a1 : lane == 2 ? a2 : a3;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const bool up = lane & 8;
+            const double keep = up ? acc[r + 2] : acc[r], send = up ? acc[r] : acc[r + 2];
+            acc[r] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+        {
+            const bool up = lane & 4;
+            const double keep = up ? acc[1] : acc[0], send = up ? acc[0] : acc[1];
+            acc[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        }
+        acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 2);
+        acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+        if ((lane & 3) == 0 && (lane >> 2) < nr) part_out[j0 + (lane >> 2)] = acc[0];
     }
 }
 
@@ -870,12 +887,35 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                     const double* V0 = basis(P, s, 0);
                     double nrm = 0.0;
                     if (apply) chunk_sum_coeffs<NT>(P, s, pin, k + 1, cvec);
-                    for (int e = e0 + tid; e < e1; e += NT) {
-                        double acc = w[e];
-                        if (apply)
-                            for (int j = 0; j <= k; ++j) acc -= cvec[j] * V0[(int64_t)j * ns + e];
-                        w[e] = acc;
-                        nrm = fma(acc, acc, nrm);
+                    // the thread's kBatchChunk / NT elements advance together:
+                    // independent FP64 chains and loads in flight per row
+                    static_assert(kBatchChunk % NT == 0, "a chunk is a whole number of elements per thread");
+                    constexpr int EPT = kBatchChunk / NT;
+                    double acc[EPT];
+#pragma unroll
+                    for (int q = 0; q < EPT; ++q) {
+                        const int e = e0 + tid + q * NT;
+                        acc[q] = (e < e1) ? w[e] : 0.0;
+                    }
+                    if (apply) {
+#pragma unroll 2
+                        for (int j = 0; j <= k; ++j) {
+                            const double cj = cvec[j];
+                            const double* vj = V0 + (int64_t)j * ns;
+#pragma unroll
+                            for (int q = 0; q < EPT; ++q) {
+                                const int e = e0 + tid + q * NT;
+                                if (e < e1) acc[q] = fma(-cj, vj[e], acc[q]);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < EPT; ++q) {
+                        const int e = e0 + tid + q * NT;
+                        if (e < e1) {
+                            w[e] = acc[q];
+                            nrm = fma(acc[q], acc[q], nrm);
+                        }
                     }
                     __syncthreads();
                     nrm = warp_sum_d(nrm);

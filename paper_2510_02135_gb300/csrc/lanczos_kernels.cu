@@ -13,7 +13,7 @@ namespace lmk {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kMaxBlocks = 608;   // 4 x 152 SMs
+constexpr int kMaxBlocks = 1216;   // 8 x 152 SMs: one wave of 256-thread blocks
 
 inline int blocks_for(int64_t n, int per_thread = 4) {
     int64_t b = (n + (int64_t)kThreads * per_thread - 1) / ((int64_t)kThreads * per_thread);
@@ -60,69 +60,49 @@ __global__ void sum_stage2(const double* __restrict__ red, int nb, double* __res
     }
 }
 
-__global__ void axpy2_kernel(double* __restrict__ w, const double* __restrict__ vk, const double* __restrict__ alpha,
-                             const double* __restrict__ vkm1, const double* __restrict__ beta, int64_t n) {
-    const double a = alpha[0];
-    const double b = (vkm1 != nullptr) ? beta[0] : 0.0;
-    for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kThreads) {
-        double v = w[e] - a * vk[e];
-        if (vkm1 != nullptr) v -= b * vkm1[e];
-        w[e] = v;
-    }
-}
-
-// Multi-dot: block b owns the chunk [b*cs, min(n, (b+1)*cs)); warp q handles
-// rows j = q, q + 8, ...; red[j * nb + b] = partial dot.
 // DGKS test for the second Gram-Schmidt pass: h = [h0, h0^2, h1, h1^2], the
 // norms before and after the first pass; the pass runs only if h1 < h0 / sqrt(2).
 __device__ __forceinline__ bool second_pass_needed(const double* h) {
     return h == nullptr || h[2] < h[0] * 0.70710678118654752440;
 }
 
-__global__ void multidot_stage1(const double* __restrict__ V, int m, const double* __restrict__ w, int64_t n,
-                                int64_t cs, double* __restrict__ red, const double* __restrict__ cond) {
-    if (!second_pass_needed(cond)) return;
-    const int64_t e0 = (int64_t)blockIdx.x * cs;
-    const int64_t e1 = (e0 + cs < n) ? (e0 + cs) : n;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int j = wid; j < m; j += kThreads / 32) {
-        const double* __restrict__ v = V + (int64_t)j * n;
-        double acc = 0.0;
-        for (int64_t e = e0 + lane; e < e1; e += 32) acc = fma(v[e], w[e], acc);
-        acc = warp_sum(acc);
-        if (lane == 0) red[(int64_t)j * gridDim.x + blockIdx.x] = acc;
+// Basis combination for one element e: sum_j c[j] V[j][e], j < m, with c
+// staged in shared memory 256 rows at a time.  Eight loads are issued before
+// their FMAs and two accumulators alternate, so that a thread keeps eight
+// HBM reads and two FP64 FMA chains (64-cycle latency on this GPU) in flight.
+__device__ __forceinline__ double basis_combination(const double* __restrict__ V, int m, const double* __restrict__ c,
+                                                    int64_t n, int64_t e, double* csh) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int j0 = 0; j0 < m; j0 += 256) {
+        const int mm = (m - j0 < 256) ? (m - j0) : 256;
+        __syncthreads();
+        if (threadIdx.x < mm) csh[threadIdx.x] = c[j0 + threadIdx.x];
+        __syncthreads();
+        if (e >= n) continue;
+        const double* __restrict__ v = V + (int64_t)j0 * n + e;
+        int j = 0;
+        for (; j + 8 <= mm; j += 8) {
+            double x[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) x[q] = v[(int64_t)(j + q) * n];
+#pragma unroll
+            for (int q = 0; q < 8; q += 2) {
+                a0 = fma(csh[j + q], x[q], a0);
+                a1 = fma(csh[j + q + 1], x[q + 1], a1);
+            }
+        }
+        for (; j < mm; ++j) a0 = fma(csh[j], v[(int64_t)j * n], a0);
     }
-}
-
-__global__ void multidot_stage2(const double* __restrict__ red, int m, int nb, double* __restrict__ c,
-                                const double* __restrict__ cond) {
-    if (!second_pass_needed(cond)) return;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int j = blockIdx.x * (kThreads / 32) + wid; j < m; j += gridDim.x * (kThreads / 32)) {
-        double acc = 0.0;
-        for (int b = lane; b < nb; b += 32) acc += red[(int64_t)j * nb + b];
-        acc = warp_sum(acc);
-        if (lane == 0) c[j] = acc;
-    }
+    return a0 + a1;
 }
 
 // w[e] (+)= sign * sum_j c[j] V[j][e]; accumulate = 0 overwrites (y = V^T z).
 __global__ void combine_kernel(const double* __restrict__ V, int m, const double* __restrict__ c,
-                               double* __restrict__ w, int64_t n, int accumulate, double sign,
-                               const double* __restrict__ cond) {
-    if (!second_pass_needed(cond)) return;
-    __shared__ double cs[256];
+                               double* __restrict__ w, int64_t n, int accumulate, double sign) {
+    __shared__ double csh[256];
     for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e - threadIdx.x < n;
          e += (int64_t)gridDim.x * kThreads) {
-        double acc = 0.0;
-        for (int j0 = 0; j0 < m; j0 += 256) {
-            const int mm = (m - j0 < 256) ? (m - j0) : 256;
-            __syncthreads();
-            if (threadIdx.x < mm) cs[threadIdx.x] = c[j0 + threadIdx.x];
-            __syncthreads();
-            if (e < n)
-                for (int j = 0; j < mm; ++j) acc = fma(cs[j], V[(int64_t)(j0 + j) * n + e], acc);
-        }
+        const double acc = basis_combination(V, m, c, n, e, csh);
         if (e < n) w[e] = accumulate ? fma(sign, acc, w[e]) : sign * acc;
     }
 }
@@ -246,56 +226,108 @@ __global__ void axpy2_norm_kernel(double* __restrict__ w, const double* __restri
     if (threadIdx.x == 0) { out[0] = sqrt(t); out[1] = t; *ctr = 0u; }
 }
 
-// multidot_stage1, then the last block forms c[j] = sum_b red[j nb + b]
-// (the order of multidot_stage2).
-__global__ void multidot_fused(const double* __restrict__ V, int m, const double* __restrict__ w, int64_t n,
-                               int64_t cs, double* red, unsigned* ctr, double* __restrict__ c,
-                               const double* __restrict__ cond) {
+// Multi-dot c[j] = v_j . w, j < m.  Block (b, g) takes the rows
+// [8g, 8g + 8) over the element chunk [b*kMdChunk, (b+1)*kMdChunk): each
+// thread accumulates the eight rows over its kMdElems elements (eight
+// independent FP64 chains, w read once per element), the warp reduces the
+// eight sums by a transposing butterfly (9 shuffles and adds instead of 40),
+// the block adds its four warps and writes red[j * nb + b].  The last block
+// of row group g (counter ctr[g]) forms c[j] = sum_b red[j * nb + b] in
+// lane-strided order followed by a butterfly, so the result is deterministic.
+constexpr int kMdThreads = 128;
+constexpr int kMdElems = 8;
+constexpr int kMdRows = 8;
+constexpr int64_t kMdChunk = (int64_t)kMdThreads * kMdElems;
+
+__global__ void __launch_bounds__(kMdThreads) multidot_rows(const double* __restrict__ V, int m,
+                                                            const double* __restrict__ w, int64_t n, double* red,
+                                                            unsigned* ctr, double* __restrict__ c,
+                                                            const double* __restrict__ cond) {
     if (!second_pass_needed(cond)) return;
-    const int64_t e0 = (int64_t)blockIdx.x * cs;
-    const int64_t e1 = (e0 + cs < n) ? (e0 + cs) : n;
+    const int nb = gridDim.x, g = blockIdx.y;
+    const int j0 = g * kMdRows;
+    const int rows = (m - j0 < kMdRows) ? (m - j0) : kMdRows;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int j = wid; j < m; j += kThreads / 32) {
-        const double* __restrict__ v = V + (int64_t)j * n;
-        double acc = 0.0;
-        for (int64_t e = e0 + lane; e < e1; e += 32) acc = fma(v[e], w[e], acc);
-        acc = warp_sum(acc);
-        if (lane == 0) red[(int64_t)j * gridDim.x + blockIdx.x] = acc;
+    const int64_t eb = (int64_t)blockIdx.x * kMdChunk + threadIdx.x;
+    double acc[kMdRows];
+#pragma unroll
+    for (int r = 0; r < kMdRows; ++r) acc[r] = 0.0;
+#pragma unroll 2
+    for (int q = 0; q < kMdElems; ++q) {
+        const int64_t e = eb + (int64_t)q * kMdThreads;
+        if (e < n) {
+            const double we = w[e];
+            const double* __restrict__ v = V + (int64_t)j0 * n + e;
+#pragma unroll
+            for (int r = 0; r < kMdRows; ++r)
+                if (r < rows) acc[r] = fma(v[(int64_t)r * n], we, acc[r]);
+        }
     }
-    if (!last_block_done(ctr)) return;
-    const int nb = gridDim.x;
-    for (int j = wid; j < m; j += kThreads / 32) {
-        double acc = 0.0;
-        for (int b = lane; b < nb; b += 32) acc += __ldcg(red + (int64_t)j * nb + b);
-        acc = warp_sum(acc);
-        if (lane == 0) c[j] = acc;
+    // transposing butterfly: after the offsets 16, 8 and 4 lane l holds the
+    // partial of row l >> 2 (bits 4, 3, 2 of l), completed by offsets 2 and 1
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const bool up = lane & 16;
+        const double keep = up ? acc[r + 4] : acc[r], send = up ? acc[r] : acc[r + 4];
+        acc[r] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
     }
-    if (threadIdx.x == 0) *ctr = 0u;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const bool up = lane & 8;
+        const double keep = up ? acc[r + 2] : acc[r], send = up ? acc[r] : acc[r + 2];
+        acc[r] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    {
+        const bool up = lane & 4;
+        const double keep = up ? acc[1] : acc[0], send = up ? acc[0] : acc[1];
+        acc[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 2);
+    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+    __shared__ double wsum[kMdThreads / 32][kMdRows];
+    if ((lane & 3) == 0) wsum[wid][lane >> 2] = acc[0];
+    __syncthreads();
+    if (threadIdx.x < rows) {
+        double t = wsum[0][threadIdx.x];
+#pragma unroll
+        for (int q = 1; q < kMdThreads / 32; ++q) t += wsum[q][threadIdx.x];
+        red[(int64_t)(j0 + threadIdx.x) * nb + blockIdx.x] = t;
+    }
+    // the last block of this row group adds the chunks
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(&ctr[g], 1u) == (unsigned)nb - 1u);
+    __syncthreads();
+    if (!last) return;
+    for (int r = wid; r < rows; r += kMdThreads / 32) {
+        const double* pr = red + (int64_t)(j0 + r) * nb;
+        double t = 0.0;
+        for (int b = lane; b < nb; b += 32) t += __ldcg(pr + b);
+        t = warp_sum(t);
+        if (lane == 0) c[j0 + r] = t;
+    }
+    if (threadIdx.x == 0) ctr[g] = 0u;
 }
 
-// w -= sum_j c[j] V[j] (skipped unless the DGKS test asks for it), then
-// out = (|w|, |w|^2) in any case.
+// w -= sum_j c[j] V[j], then out = (|w|, |w|^2).  When the DGKS test skips
+// the pass, w is unchanged and its norm is the one the first pass left in
+// cond[2], cond[3] (the same kernel over the same w would recompute it bit
+// for bit), so one thread copies it.
 __global__ void sub_vc_norm_kernel(const double* __restrict__ V, int m, const double* __restrict__ c,
                                    double* __restrict__ w, int64_t n, const double* __restrict__ cond, double* red,
                                    unsigned* ctr, double* __restrict__ out) {
-    const bool apply = second_pass_needed(cond);
+    if (!second_pass_needed(cond)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) { out[0] = cond[2]; out[1] = cond[3]; }
+        return;
+    }
     __shared__ double csh[256];
     double nrm = 0.0;
     for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e - threadIdx.x < n;
          e += (int64_t)gridDim.x * kThreads) {
-        double acc = 0.0;
-        if (apply) {
-            for (int j0 = 0; j0 < m; j0 += 256) {
-                const int mm = (m - j0 < 256) ? (m - j0) : 256;
-                __syncthreads();
-                if (threadIdx.x < mm) csh[threadIdx.x] = c[j0 + threadIdx.x];
-                __syncthreads();
-                if (e < n)
-                    for (int j = 0; j < mm; ++j) acc = fma(csh[j], V[(int64_t)(j0 + j) * n + e], acc);
-            }
-        }
+        const double acc = basis_combination(V, m, c, n, e, csh);
         if (e < n) {
-            const double v = apply ? fma(-1.0, acc, w[e]) : w[e];
+            const double v = w[e] - acc;
             w[e] = v;
             nrm = fma(v, v, nrm);
         }
@@ -307,62 +339,22 @@ __global__ void sub_vc_norm_kernel(const double* __restrict__ V, int m, const do
     if (threadIdx.x == 0) { out[0] = sqrt(t); out[1] = t; *ctr = 0u; }
 }
 
-inline int64_t md_chunk(int64_t n, int* nb) {
-    int64_t cs = (n + kMaxBlocks - 1) / kMaxBlocks;
-    cs = (cs + 31) / 32 * 32;
-    if (cs < 256) cs = 256;
-    *nb = (int)((n + cs - 1) / cs);
-    if (*nb < 1) *nb = 1;
-    return cs;
-}
+inline int md_blocks(int64_t n) { return (int)((n + kMdChunk - 1) / kMdChunk); }
 
 }  // namespace
 
 size_t lz_red_doubles(int64_t n, int m) {
-    int nb = 0;
-    md_chunk(n, &nb);
-    size_t a = (size_t)nb * (size_t)(m < 1 ? 1 : m);
+    const size_t a = (size_t)md_blocks(n) * (size_t)(m < 1 ? 1 : m);
     return a > (size_t)kMaxBlocks ? a : (size_t)kMaxBlocks;
 }
 
-cudaError_t lz_dot(const double* x, const double* y, int64_t n, double* red, double* out, cudaStream_t s) {
-    const int nb = blocks_for(n);
-    dot_stage1<<<nb, kThreads, 0, s>>>(x, y, n, red);
-    sum_stage2<<<1, kThreads, 0, s>>>(red, nb, out, 0);
-    count_launches(2);
-    return cudaGetLastError();
-}
+size_t lz_ctr_count(int m) { return 1 + (size_t)((m < 1 ? 1 : m) + kMdRows - 1) / kMdRows; }
 
 cudaError_t lz_norm(const double* x, int64_t n, double* red, double* out, cudaStream_t s) {
     const int nb = blocks_for(n);
     dot_stage1<<<nb, kThreads, 0, s>>>(x, x, n, red);
     sum_stage2<<<1, kThreads, 0, s>>>(red, nb, out, 1);
     count_launches(2);
-    return cudaGetLastError();
-}
-
-cudaError_t lz_axpy2(double* w, const double* vk, const double* alpha, const double* vkm1, const double* beta,
-                     int64_t n, cudaStream_t s) {
-    axpy2_kernel<<<blocks_for(n), kThreads, 0, s>>>(w, vk, alpha, vkm1, beta, n);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t lz_multidot(const double* V, int m, const double* w, int64_t n, double* red, double* c,
-                        cudaStream_t s, const double* cond) {
-    int nb = 0;
-    const int64_t cs = md_chunk(n, &nb);
-    multidot_stage1<<<nb, kThreads, 0, s>>>(V, m, w, n, cs, red, cond);
-    const int g2 = (m + (kThreads / 32) - 1) / (kThreads / 32);
-    multidot_stage2<<<g2, kThreads, 0, s>>>(red, m, nb, c, cond);
-    count_launches(2);
-    return cudaGetLastError();
-}
-
-cudaError_t lz_sub_vc(const double* V, int m, const double* c, double* w, int64_t n, cudaStream_t s,
-                      const double* cond) {
-    combine_kernel<<<blocks_for(n, 1), kThreads, 0, s>>>(V, m, c, w, n, 1, -1.0, cond);
-    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -382,11 +374,10 @@ cudaError_t lz_axpy2_norm(double* w, const double* vk, const double* alpha, cons
 
 cudaError_t lz_multidot1(const double* V, int m, const double* w, int64_t n, double* red, unsigned* ctr, double* c,
                          cudaStream_t s, const double* cond) {
-    int nb = 0;
-    const int64_t cs = md_chunk(n, &nb);
-    // one block adds the partials: worth it while they are few
-    if ((int64_t)nb * m > 8192) return lz_multidot(V, m, w, n, red, c, s, cond);
-    multidot_fused<<<nb, kThreads, 0, s>>>(V, m, w, n, cs, red, ctr, c, cond);
+    if (m < 1) return cudaSuccess;
+    const int nb = md_blocks(n), ng = (m + kMdRows - 1) / kMdRows;
+    if (nb < 1 || ng > 65535) return cudaErrorInvalidConfiguration;
+    multidot_rows<<<dim3((unsigned)nb, (unsigned)ng), kMdThreads, 0, s>>>(V, m, w, n, red, ctr + 1, c, cond);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -405,7 +396,7 @@ cudaError_t lz_scale(const double* x, const double* nrm, double* y, int64_t n, c
 }
 
 cudaError_t lz_combine(const double* V, int m, const double* z, double* y, int64_t n, cudaStream_t s) {
-    combine_kernel<<<blocks_for(n, 1), kThreads, 0, s>>>(V, m, z, y, n, 0, 1.0, nullptr);
+    combine_kernel<<<blocks_for(n, 1), kThreads, 0, s>>>(V, m, z, y, n, 0, 1.0);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -906,9 +906,11 @@ lm_status lm_sqrt_mdot(lm_solver* s, const double* W, uint64_t seed, double pref
     LM_CUDA(s->scal.ensure((size_t)(kScal * (m_max + 3)) * sizeof(double)), "allocating scalars");
     LM_CUDA(s->zbuf.ensure((size_t)m_max * sizeof(double)), "allocating coefficients");
     LM_CUDA(s->cbuf.ensure((size_t)(m_max + 1) * sizeof(double)), "allocating coefficients");
-    if (s->lzctr.p == nullptr) {
-        LM_CUDA(s->lzctr.ensure(64), "allocating counters");
-        LM_CUDA(cudaMemsetAsync(s->lzctr.p, 0, 64, s->stream), "allocating counters");
+    const size_t ctr_bytes = std::max<size_t>(64, lmk::lz_ctr_count(m_max + 1) * sizeof(unsigned));
+    if (s->lzctr.p == nullptr || s->lzctr.cap < ctr_bytes) {
+        // the counters must start at zero; the kernels reset them after use
+        LM_CUDA(s->lzctr.ensure(ctr_bytes), "allocating counters");
+        LM_CUDA(cudaMemsetAsync(s->lzctr.p, 0, s->lzctr.cap, s->stream), "allocating counters");
     }
     if (s->pinned_doubles < (size_t)(kScal * (m_max + 3))) {
         cudaFreeHost(s->pinned);

@@ -169,32 +169,26 @@ cudaError_t launch_ab_update(const void* pos, int f64, const double* u, const do
 
 // Lanczos vector kernels (lanczos_kernels.cu).  All vectors are FP64 of
 // length n; the basis V is row-major (row j = v_j, stride n).  Reductions are
-// two-stage and deterministic; `red` is scratch of lz_red_doubles(n, m).
+// deterministic: blocks write partials and the last block to finish (a device
+// counter that must start at 0 and is reset by that block) adds them in a
+// fixed order.  `red` is scratch of lz_red_doubles(n, m) doubles and `ctr`
+// holds lz_ctr_count(m) counters for bases of up to m rows.
 size_t lz_red_doubles(int64_t n, int m);
-cudaError_t lz_dot(const double* x, const double* y, int64_t n, double* red, double* out, cudaStream_t s);
-// out[0] = |x|, out[1] = |x|^2
+size_t lz_ctr_count(int m);
+// out[0] = |x|, out[1] = |x|^2 (two launches, no counter)
 cudaError_t lz_norm(const double* x, int64_t n, double* red, double* out, cudaStream_t s);
-// w -= alpha[0] vk + beta[0] vkm1   (vkm1 / beta nullable)
-cudaError_t lz_axpy2(double* w, const double* vk, const double* alpha, const double* vkm1,
-                     const double* beta, int64_t n, cudaStream_t s);
-// c[j] = v_j . w for j < m.  With cond = [h0, h0^2, h1, h1^2] (device) the
-// kernels do nothing unless h1 < h0 / sqrt(2) (DGKS second-pass test).
-cudaError_t lz_multidot(const double* V, int m, const double* w, int64_t n, double* red, double* c,
-                        cudaStream_t s, const double* cond = nullptr);
-// w -= sum_j c[j] v_j  (same optional condition)
-cudaError_t lz_sub_vc(const double* V, int m, const double* c, double* w, int64_t n, cudaStream_t s,
-                      const double* cond = nullptr);
-// Single-launch forms (the last block adds the partials in block order and
-// resets *ctr, a device counter that must start at 0): lz_dot1 (mode 0: x.y,
-// mode 1: |x|, |x|^2), lz_axpy2_norm (lz_axpy2, then |w|, |w|^2 into out),
-// lz_multidot1 (lz_multidot), lz_sub_vc_norm (the conditional lz_sub_vc,
-// then |w|, |w|^2 into out).  `red` is scratch of lz_red_doubles(n, m).
+// mode 0: out[0] = x.y; mode 1: out[0] = |x|, out[1] = |x|^2
 cudaError_t lz_dot1(const double* x, const double* y, int64_t n, double* red, unsigned* ctr, double* out,
                     int mode, cudaStream_t s);
+// w -= alpha[0] vk + beta[0] vkm1 (vkm1 / beta nullable), then out = (|w|, |w|^2)
 cudaError_t lz_axpy2_norm(double* w, const double* vk, const double* alpha, const double* vkm1, const double* beta,
                           int64_t n, double* red, unsigned* ctr, double* out, cudaStream_t s);
+// c[j] = v_j . w for j < m.  With cond = [h0, h0^2, h1, h1^2] (device) the
+// kernel does nothing unless h1 < h0 / sqrt(2) (DGKS second-pass test).
 cudaError_t lz_multidot1(const double* V, int m, const double* w, int64_t n, double* red, unsigned* ctr, double* c,
                          cudaStream_t s, const double* cond = nullptr);
+// w -= sum_j c[j] v_j (same optional condition), then out = (|w|, |w|^2);
+// a skipped pass copies (cond[2], cond[3]) into out.
 cudaError_t lz_sub_vc_norm(const double* V, int m, const double* c, double* w, int64_t n, double* red,
                            unsigned* ctr, double* out, cudaStream_t s, const double* cond = nullptr);
 // y = x / nrm[0]
