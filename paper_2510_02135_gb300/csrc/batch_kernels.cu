@@ -60,18 +60,36 @@ __device__ __forceinline__ void stamp(const BatchParams& P, int step, int& slot)
 }
 
 // Grid barrier with a bounded wait.  Returns false if the run must stop.
+// Two levels: a CTA adds itself to its group's counter; the last CTA of a
+// group resets that counter and adds the group to bar[0]; the last group's
+// CTA resets bar[0] and advances the generation, which every other CTA waits
+// for.  Same-address atomics are what a one-counter barrier pays for (one
+// per CTA, serialised in one L2 slice); here each counter takes at most
+// kBarGroup of them and the group counters sit in separate lines.
 __device__ bool grid_sync(const BatchParams& P) {
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned* gen = P.bar + 1;
         const unsigned g = *gen;
         __threadfence();
-        const unsigned arrived = atomicAdd(P.bar, 1u);
-        if (arrived == (unsigned)P.n_main - 1) {
-            atomicExch(P.bar, 0u);
+        const int grp = blockIdx.x / kBarGroup;
+        const int ngrp = (P.n_main + kBarGroup - 1) / kBarGroup;
+        const unsigned gsize = (unsigned)min(kBarGroup, P.n_main - grp * kBarGroup);
+        unsigned* gc = P.bar + kBarStride * (1 + grp);
+        bool release = false;
+        if (atomicAdd(gc, 1u) == gsize - 1u) {
+            // every CTA of the group has arrived: none can arrive again before
+            // the generation advances, so the counter can be reset now
+            atomicExch(gc, 0u);
             __threadfence();
-            atomicAdd(P.bar + 1, 1u);
-        } else {
+            if (atomicAdd(P.bar, 1u) == (unsigned)ngrp - 1u) {
+                atomicExch(P.bar, 0u);
+                __threadfence();
+                atomicAdd(P.bar + 1, 1u);
+                release = true;
+            }
+        }
+        if (!release) {
             const long long t0 = clock64();
             while (*gen == g) {
                 if (*(volatile int*)P.err != kBatchOk) break;
@@ -882,6 +900,11 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                         const double h0 = warp_range_sum(partA + P.m_max, M1, cb, ce);
                         const double h1 = warp_range_sum(partB + P.m_max, M1, cb, ce);
                         apply = h1 < 0.5 * h0;   // squared norms: |w1| < |w0| / sqrt(2)
+                        if (!apply) {
+                            // w unchanged: its norm partial is the first pass's, bit for bit
+                            if (tid == 0) pout[(int64_t)c * M1] = pin[(int64_t)c * M1 + P.m_max];
+                            continue;
+                        }
                     }
                     double* w = wcur + 3 * o;
                     const double* V0 = basis(P, s, 0);

@@ -1454,7 +1454,11 @@ lm_status batch_run(lm_batch* b, const lmk::BatchParams& p, bool use_graph) {
         LM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "batch graph capture");
     }
     if (p.n_main < 1) return fail(LM_ERR_CUDA, "cooperative grid of %d CTAs leaves no main CTA", grid);
-    cudaError_t e = cudaMemsetAsync(b->bar.p, 0, 2 * sizeof(unsigned), st);
+    if (p.n_main > lmk::kBarGroup * lmk::kBarMaxGroups)
+        return fail(LM_ERR_CUDA, "cooperative grid of %d CTAs exceeds the grid barrier's capacity", grid);
+    // every level of the grid barrier starts at zero (a run that ended on an
+    // error may have left counts behind)
+    cudaError_t e = cudaMemsetAsync(b->bar.p, 0, lmk::kBarWords * sizeof(unsigned), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->ticket.p, 0, sizeof(unsigned long long), st);
     // request ring, counters and result tags start empty in every launch
     const size_t S_ = (size_t)b->S;
@@ -1586,7 +1590,7 @@ lm_status lm_batch_create(lm_batch** out, int64_t S, const int64_t* offsets, dou
         {&b->zdone, S_ * 2 * (size_t)b->R * sizeof(unsigned long long)}, {&b->state, S_ * sizeof(int)},
         {&b->next_check, S_ * sizeof(int)}, {&b->last_k, S_ * sizeof(int)}, {&b->k0s, S_ * sizeof(int)}, {&b->posted, S_ * sizeof(int)},
         {&b->main_done, sizeof(int)}, {&b->cur_step, sizeof(long long)},
-        {&b->bar, 4 * sizeof(unsigned)}, {&b->ticket, sizeof(unsigned long long)}, {&b->err, sizeof(int)},
+        {&b->bar, lmk::kBarWords * sizeof(unsigned)}, {&b->ticket, sizeof(unsigned long long)}, {&b->err, sizeof(int)},
         {&b->flag, sizeof(int)}, {&b->kprev, S_ * sizeof(int)}, {&b->woff, S_ * sizeof(int64_t)},
         {&b->wsplit, (size_t)wtot * sizeof(double)}, {&b->usplit, (size_t)wtot * sizeof(double)}};
     for (auto& al : allocs) LM_CUDA(al.buf->ensure(al.bytes), "allocating batch buffers");
@@ -1594,7 +1598,7 @@ lm_status lm_batch_create(lm_batch** out, int64_t S, const int64_t* offsets, dou
     LM_CUDA(cudaMemcpy(b->chunks.p, chunks.data(), chunks.size() * sizeof(int), cudaMemcpyHostToDevice), "chunks");
     LM_CUDA(cudaMemcpy(b->chunk_range.p, crange.data(), crange.size() * sizeof(int), cudaMemcpyHostToDevice),
             "chunks");
-    LM_CUDA(cudaMemset(b->bar.p, 0, 4 * sizeof(unsigned)), "batch barrier");
+    LM_CUDA(cudaMemset(b->bar.p, 0, lmk::kBarWords * sizeof(unsigned)), "batch barrier");
     LM_CUDA(cudaMemset(b->kprev.p, 0, S_ * sizeof(int)), "batch history");
     LM_CUDA(cudaMemcpy(b->woff.p, woff.data(), S_ * sizeof(int64_t), cudaMemcpyHostToDevice), "batch offsets");
     if (lm_status st = batch_build_items(b)) return st;

@@ -210,6 +210,13 @@ enum BatchMode { kBatchBD = 0, kBatchMdot = 1, kBatchSqrt = 2 };
 enum BatchError { kBatchOk = 0, kBatchTimeout = 1, kBatchTridiag = 2 };
 constexpr int kBatchChunk = 256;       // elements per vector-phase work unit
 constexpr int kBatchJPart = 1024;      // j-range of one product work item
+// Grid barrier of the persistent kernel: bar[0] counts arrived groups,
+// bar[1] is the generation, and group g of kBarGroup consecutive main CTAs
+// counts its arrivals at bar[kBarStride * (1 + g)] (one 128-byte line each).
+constexpr int kBarGroup = 32;
+constexpr int kBarStride = 32;
+constexpr int kBarMaxGroups = 256;
+constexpr size_t kBarWords = (size_t)kBarStride * (1 + kBarMaxGroups);
 constexpr int kSolverWidth = 2;        // requests a solver warp serves at once
 constexpr int kSolverWarps = 64;       // solver warps of a batched launch
 
