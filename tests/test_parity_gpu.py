@@ -240,6 +240,23 @@ def test_sqrt_fp64_n1024_matches_eigen_root(orc):
     np.testing.assert_allclose(host(y2).ravel(), -0.25 * y, rtol=1e-14, atol=1e-300)
 
 
+def test_sqrt_long_basis_matches_eigen_root(orc):
+    """tol = 0 runs up to max_iter = 200 iterations (NOT_CONVERGED by design):
+    a basis of more than 128 rows takes more than 16 row groups of the
+    Gram-Schmidt multi-dot and its counters; the result stays the exact root
+    (converged long before), and a second call reuses the counters."""
+    n = 300
+    s_ = I.cube_suspension(31, n, 0.3, 1.0, angular=True, fp32=False)
+    s = make(1.0, 1.0, True, True, s_.pos)
+    M = orc.assemble(s_.pos, 1.0, 1.0, True)
+    exact = orc.sqrt_exact(M, s_.W)
+    for _ in range(2):
+        lin, ang, it = lm.lm_sqrt_mdot(s, dev(s_.W), tol=0.0, max_iter=200, raise_not_converged=False)
+        y = np.concatenate([host(lin).ravel(), host(ang).ravel()])
+        assert it >= 130, it   # (a breakdown, |beta| ~ 0, may end it before 200)
+        assert rel(y, exact) <= 1e-10, rel(y, exact)
+
+
 @pytest.mark.parametrize("fp64", [False, True])
 def test_sqrt_rpy6_small_matches_oracle(orc, fp64):
     n = 600
