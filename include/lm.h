@@ -146,6 +146,19 @@ lm_status lm_sqrt_mdot(lm_solver *solver, const double *W, uint64_t seed, double
 lm_status lm_set_sqrt_preconditioner(lm_solver *solver, int kind);
 
 /*
+ * lm_set_reorthogonalization -- the Gram-Schmidt passes of the Lanczos
+ * square root (full reorthogonalisation against the stored basis, reading 6
+ * of the Lanczos details).  mode 0 (the default): one classical pass, and a
+ * second only when the first removed more than 1 - 1/sqrt(2) of the norm of
+ * w (the DGKS criterion, Daniel, Gragg, Kaufman & Stewart 1976).  mode 1:
+ * always two passes (costs one more pass over the basis per iteration; the
+ * iterates agree with mode 0 to rounding).  Other modes give
+ * LM_ERR_INVALID_ARG.  lm_batch_set_reorthogonalization does the same for a
+ * batch.
+ */
+lm_status lm_set_reorthogonalization(lm_solver *solver, int mode);
+
+/*
  * lm_div_m -- divM of Sec. 3.2: lin_i = sum_j d/dx_j . M_uF(i, j),
  * ang_i = sum_j d/dx_j . M_wF(i, j) (the thermal drift of Eq. bdhi is kT
  * times this).  For the open geometry the mobility is translation invariant
@@ -422,6 +435,7 @@ lm_status lm_batch_bd_run(lm_batch *batch, double kT, double dt, double k_trap, 
  * product over all systems) or set by hand.
  */
 lm_status lm_batch_set_tiling(lm_batch *batch, int threads, int ilp);
+lm_status lm_batch_set_reorthogonalization(lm_batch *batch, int mode);
 lm_status lm_batch_autotune(lm_batch *batch, int *threads_out, int *ilp_out);
 
 /*

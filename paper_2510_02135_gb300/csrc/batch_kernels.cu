@@ -877,7 +877,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                         const int cb = P.chunk_range[2 * s], ce = P.chunk_range[2 * s + 1];
                         const double h0 = warp_range_sum(partA + P.m_max, M1, cb, ce);
                         const double h1 = warp_range_sum(partB + P.m_max, M1, cb, ce);
-                        if (!(h1 < 0.5 * h0)) continue;
+                        if (!(P.reorth || h1 < 0.5 * h0)) continue;
                         const int64_t o = P.off[s];
                         const int ns = 3 * (int)(P.off[s + 1] - o);
                         const int e1 = min(e0 + kBatchChunk, ns);
@@ -899,7 +899,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                         const int cb = P.chunk_range[2 * s], ce = P.chunk_range[2 * s + 1];
                         const double h0 = warp_range_sum(partA + P.m_max, M1, cb, ce);
                         const double h1 = warp_range_sum(partB + P.m_max, M1, cb, ce);
-                        apply = h1 < 0.5 * h0;   // squared norms: |w1| < |w0| / sqrt(2)
+                        apply = P.reorth || h1 < 0.5 * h0;   // squared norms: |w1| < |w0| / sqrt(2)
                         if (!apply) {
                             // w unchanged: its norm partial is the first pass's, bit for bit
                             if (tid == 0) pout[(int64_t)c * M1] = pin[(int64_t)c * M1 + P.m_max];

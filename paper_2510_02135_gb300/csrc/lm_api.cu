@@ -168,6 +168,7 @@ struct lm_solver {
 
     lm_lanczos_stats stats{0, 0, 0.0, 0.0, 0};
 
+    int reorth = 0;   // 0: DGKS-adaptive second Gram-Schmidt pass, 1: always two passes
     // Lanczos host state and per-iteration events
     LanczosHost lz_host;
     std::vector<cudaEvent_t> lz_ev;
@@ -842,8 +843,9 @@ lm_status enqueue_lanczos_iteration(lm_solver* s, int k, int64_t n, double* V, d
     // one only after cancellation (DGKS); beta = |w| at the end
     LM_CUDA(lmk::lz_multidot1(V, k + 1, w, n, red, ctr, cb, s->stream), "reorthogonalisation");
     LM_CUDA(lmk::lz_sub_vc_norm(V, k + 1, cb, w, n, red, ctr, sk + 6, s->stream), "reorthogonalisation");
-    LM_CUDA(lmk::lz_multidot1(V, k + 1, w, n, red, ctr, cb, s->stream, sk + 4), "reorthogonalisation");
-    LM_CUDA(lmk::lz_sub_vc_norm(V, k + 1, cb, w, n, red, ctr, sk + 1, s->stream, sk + 4), "beta");
+    const double* cond = s->reorth ? nullptr : sk + 4;   // nullptr: the second pass always runs
+    LM_CUDA(lmk::lz_multidot1(V, k + 1, w, n, red, ctr, cb, s->stream, cond), "reorthogonalisation");
+    LM_CUDA(lmk::lz_sub_vc_norm(V, k + 1, cb, w, n, red, ctr, sk + 1, s->stream, cond), "beta");
     if (vend) LM_CUDA(cudaEventRecord(vend, s->stream), "profiling event");
     LM_CUDA(cudaMemcpyAsync(s->pinned + kScal * k, sk, kScal * sizeof(double), cudaMemcpyDeviceToHost, s->stream),
             "read alpha, beta");
@@ -867,7 +869,7 @@ double lanczos_vector_bytes(int k, int64_t n, bool second_pass) {
 void settle_vector_profile(lm_solver* s, int64_t n) {
     for (const auto& pk : s->vprof_pending) {
         const double* sc = s->pinned + kScal * pk.second;
-        const bool second = sc[6] < sc[4] * 0.70710678118654752440;   // the DGKS test the kernels apply
+        const bool second = s->reorth != 0 || sc[6] < sc[4] * 0.70710678118654752440;   // the kernels' DGKS test
         if (pk.first < s->vprof_bytes.size()) s->vprof_bytes[pk.first] = lanczos_vector_bytes(pk.second, n, second);
     }
     s->vprof_pending.clear();
@@ -1079,6 +1081,13 @@ lm_status lm_set_sqrt_preconditioner(lm_solver* s, int kind) {
     if (lm_status st = check_solver(s, false)) return st;
     if (kind != 0 && kind != 1) return fail(LM_ERR_INVALID_ARG, "preconditioner kind must be 0 (none) or 1 (Jacobi)");
     s->precond = kind;
+    return LM_OK;
+}
+
+lm_status lm_set_reorthogonalization(lm_solver* s, int mode) {
+    if (lm_status st = check_solver(s, false)) return st;
+    if (mode != 0 && mode != 1) return fail(LM_ERR_INVALID_ARG, "reorthogonalization mode must be 0 (DGKS) or 1 (two passes)");
+    s->reorth = mode;
     return LM_OK;
 }
 
@@ -1302,6 +1311,7 @@ struct lm_batch {
     int solver_lanes = 0, q_cap = 0, R = 32;
     int n_items = 0, n_chunks = 0, max_rot = 0;
     int threads = 128, ilp = 1;
+    int reorth = 0;   // as lm_solver::reorth
     bool has_pos = false;
     int* pinned = nullptr;
     bool prof_on = false;
@@ -1395,6 +1405,7 @@ lmk::BatchParams batch_params(lm_batch* b, int mode) {
     p.usplit = b->usplit.as<double>();
     p.woff = b->woff.as<int64_t>();
     p.warm_start = (mode == lmk::kBatchBD) ? 1 : 0;
+    p.reorth = b->reorth;
     p.nact = b->nact.as<int>();
     p.items = b->items.as<int>();
     p.n_items = b->n_items;
@@ -1724,6 +1735,13 @@ lm_status lm_batch_bd_run(lm_batch* b, double kT, double dt, double k_trap, int 
     LM_CUDA(cudaMemcpy(nc.data(), b->notconv.p, b->S * sizeof(int), cudaMemcpyDeviceToHost), "iterations");
     for (int v : nc)
         if (v) return fail(LM_ERR_NOT_CONVERGED, "some systems reached max_iter before tol %.3g", tol);
+    return LM_OK;
+}
+
+lm_status lm_batch_set_reorthogonalization(lm_batch* b, int mode) {
+    if (lm_status st = check_batch(b, false)) return st;
+    if (mode != 0 && mode != 1) return fail(LM_ERR_INVALID_ARG, "reorthogonalization mode must be 0 (DGKS) or 1 (two passes)");
+    b->reorth = mode;
     return LM_OK;
 }
 

@@ -244,6 +244,7 @@ struct BatchParams {
     int* notconv;                      // S: 1 if max_iter was reached in some step
     int* kprev;                        // S: iterations of the previous BD step (0 = none)
     int warm_start;                    // 1: start the stopping test near kprev (BD mode)
+    int reorth;                        // 1: always run the second Gram-Schmidt pass
     int* nact;                         // m_max + 1 counters of systems still active
     double* wsplit;                    // per-system j-part partial products of w (or F for mdot)
     double* usplit;                    // per-system j-part partial products of u = M F

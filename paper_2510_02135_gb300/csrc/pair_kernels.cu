@@ -303,83 +303,89 @@ __global__ void __launch_bounds__(NT) rpy_mdot_x2_kernel(const float4* __restric
                     mn = (u == 0 && p == 0) ? m2 : fminf(mn, m2);
                 }
             }
+            // far-field pair of slot (u, p): two i-particles against j = jj + u
+            auto far_slot = [&](int u, int p) {
+                const float4 w1 = s_t[1 * NT + jj + u];
+                const float4 w2 = s_t[2 * NT + jj + u];
+                const float2 fx = hi2(w1), fy = lo2(w2), fz = hi2(w2);
+                const float2 ddx = dx[u][p], ddy = dy[u][p], ddz = dz[u][p];
+                const float2 invr = make_float2(rsqrtf(r2[u][p].x), rsqrtf(r2[u][p].y));
+                const float2 invr2 = mul2(invr, invr);
+                const float2 invr3 = mul2(invr2, invr);
+                const float2 A = fma2(K1, invr3, invr);
+                const float2 invr5 = mul2(invr3, invr2);
+                const float2 B = fma2(nK2, invr5, invr3);
+                const float2 dF = fma2(ddx, fx, fma2(ddy, fy, mul2(ddz, fz)));
+                const float2 sB = mul2(B, dF);
+                acc[p][0] = fma2(sB, ddx, fma2(A, fx, acc[p][0]));
+                acc[p][1] = fma2(sB, ddy, fma2(A, fy, acc[p][1]));
+                acc[p][2] = fma2(sB, ddz, fma2(A, fz, acc[p][2]));
+                if constexpr (ANG) {
+                    const float4 w3 = s_t[3 * NT + jj + u];
+                    const float4 w4 = s_t[4 * NT + jj + u];
+                    const float4 w5 = s_t[5 * NT + jj + u];
+                    const float4 w6 = s_t[6 * NT + jj + u];
+                    const float4 w7 = s_t[7 * NT + jj + u];
+                    const float4 w8 = s_t[8 * NT + jj + u];
+                    const float4 w9 = s_t[9 * NT + jj + u];
+                    const float4 w10 = s_t[10 * NT + jj + u];
+                    const float2 mfx = lo2(w3), mfy = hi2(w3), mfz = lo2(w4);
+                    const float2 Tx = hi2(w4), Ty = lo2(w5), Tz = hi2(w5);
+                    const float2 mTx = lo2(w6), mTy = hi2(w6), mTz = lo2(w7);
+                    const float2 hx = hi2(w7), hy = lo2(w8), hz = hi2(w8);
+                    const float2 gx = lo2(w9), gy = hi2(w9), gz = lo2(w10);
+                    // u += (T x d) / r^3
+                    const float2 cx = fma2(Ty, ddz, mul2(mTz, ddy));
+                    const float2 cy = fma2(Tz, ddx, mul2(mTx, ddz));
+                    const float2 cz = fma2(Tx, ddy, mul2(mTy, ddx));
+                    acc[p][0] = fma2(invr3, cx, acc[p][0]);
+                    acc[p][1] = fma2(invr3, cy, acc[p][1]);
+                    acc[p][2] = fma2(invr3, cz, acc[p][2]);
+                    // w += (F x d - T/2) / r^3 + (d.(3T/2)) d / r^5
+                    const float2 vx = fma2(fy, ddz, fma2(mfz, ddy, hx));
+                    const float2 vy = fma2(fz, ddx, fma2(mfx, ddz, hy));
+                    const float2 vz = fma2(fx, ddy, fma2(mfy, ddx, hz));
+                    const float2 t = mul2(invr5, fma2(ddx, gx, fma2(ddy, gy, mul2(ddz, gz))));
+                    acc[p][3] = fma2(t, ddx, fma2(invr3, vx, acc[p][3]));
+                    acc[p][4] = fma2(t, ddy, fma2(invr3, vy, acc[p][4]));
+                    acc[p][5] = fma2(t, ddz, fma2(invr3, vz, acc[p][5]));
+                }
+            };
             if (__any_sync(0xffffffffu, mn < k.four_a2)) {
+                // some pair of the warp overlaps (or is the self pair): the exact
+                // scalar form only for the slots that hold one, the packed far
+                // field for the others
 #pragma unroll
                 for (int u = 0; u < UJ; ++u) {
-                    const float4 w1 = s_t[1 * NT + jj + u];
-                    const float4 w2 = s_t[2 * NT + jj + u];
-                    const float4 fj = make_float4(w1.z, w2.x, w2.z, 0.f);
-                    float4 hj = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if constexpr (ANG) {
-                        const float4 w7 = s_t[7 * NT + jj + u];
-                        const float4 w8 = s_t[8 * NT + jj + u];
-                        hj = make_float4(w7.z, w8.x, w8.z, 0.f);
-                    }
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
-                        Acc<float, ANG> t0, t1;
+                        if (__any_sync(0xffffffffu, fminf(r2[u][p].x, r2[u][p].y) < k.four_a2)) {
+                            const float4 w1 = s_t[1 * NT + jj + u];
+                            const float4 w2 = s_t[2 * NT + jj + u];
+                            const float4 fj = make_float4(w1.z, w2.x, w2.z, 0.f);
+                            float4 hj = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if constexpr (ANG) {
+                                const float4 w7 = s_t[7 * NT + jj + u];
+                                const float4 w8 = s_t[8 * NT + jj + u];
+                                hj = make_float4(w7.z, w8.x, w8.z, 0.f);
+                            }
+                            Acc<float, ANG> t0, t1;
 #pragma unroll
-                        for (int c = 0; c < C; ++c) { t0.p[c] = 0.f; t1.p[c] = 0.f; }
-                        pair_exact<float, ANG>(dx[u][p].x, dy[u][p].x, dz[u][p].x, r2[u][p].x, fj, hj, k, t0);
-                        pair_exact<float, ANG>(dx[u][p].y, dy[u][p].y, dz[u][p].y, r2[u][p].y, fj, hj, k, t1);
+                            for (int c = 0; c < C; ++c) { t0.p[c] = 0.f; t1.p[c] = 0.f; }
+                            pair_exact<float, ANG>(dx[u][p].x, dy[u][p].x, dz[u][p].x, r2[u][p].x, fj, hj, k, t0);
+                            pair_exact<float, ANG>(dx[u][p].y, dy[u][p].y, dz[u][p].y, r2[u][p].y, fj, hj, k, t1);
 #pragma unroll
-                        for (int c = 0; c < C; ++c) acc[p][c] = add2(acc[p][c], make_float2(t0.p[c], t1.p[c]));
+                            for (int c = 0; c < C; ++c) acc[p][c] = add2(acc[p][c], make_float2(t0.p[c], t1.p[c]));
+                        } else {
+                            far_slot(u, p);
+                        }
                     }
                 }
             } else {
 #pragma unroll
                 for (int u = 0; u < UJ; ++u) {
-                    const float4 w1 = s_t[1 * NT + jj + u];
-                    const float4 w2 = s_t[2 * NT + jj + u];
-                    const float2 fx = hi2(w1), fy = lo2(w2), fz = hi2(w2);
-                    float2 mfx, mfy, mfz, Tx, Ty, Tz, mTx, mTy, mTz, hx, hy, hz, gx, gy, gz;
-                    if constexpr (ANG) {
-                        const float4 w3 = s_t[3 * NT + jj + u];
-                        const float4 w4 = s_t[4 * NT + jj + u];
-                        const float4 w5 = s_t[5 * NT + jj + u];
-                        const float4 w6 = s_t[6 * NT + jj + u];
-                        const float4 w7 = s_t[7 * NT + jj + u];
-                        const float4 w8 = s_t[8 * NT + jj + u];
-                        const float4 w9 = s_t[9 * NT + jj + u];
-                        const float4 w10 = s_t[10 * NT + jj + u];
-                        mfx = lo2(w3); mfy = hi2(w3); mfz = lo2(w4);
-                        Tx = hi2(w4); Ty = lo2(w5); Tz = hi2(w5);
-                        mTx = lo2(w6); mTy = hi2(w6); mTz = lo2(w7);
-                        hx = hi2(w7); hy = lo2(w8); hz = hi2(w8);
-                        gx = lo2(w9); gy = hi2(w9); gz = lo2(w10);
-                    }
 #pragma unroll
-                    for (int p = 0; p < NP; ++p) {
-                        const float2 ddx = dx[u][p], ddy = dy[u][p], ddz = dz[u][p];
-                        const float2 invr = make_float2(rsqrtf(r2[u][p].x), rsqrtf(r2[u][p].y));
-                        const float2 invr2 = mul2(invr, invr);
-                        const float2 invr3 = mul2(invr2, invr);
-                        const float2 A = fma2(K1, invr3, invr);
-                        const float2 invr5 = mul2(invr3, invr2);
-                        const float2 B = fma2(nK2, invr5, invr3);
-                        const float2 dF = fma2(ddx, fx, fma2(ddy, fy, mul2(ddz, fz)));
-                        const float2 sB = mul2(B, dF);
-                        acc[p][0] = fma2(sB, ddx, fma2(A, fx, acc[p][0]));
-                        acc[p][1] = fma2(sB, ddy, fma2(A, fy, acc[p][1]));
-                        acc[p][2] = fma2(sB, ddz, fma2(A, fz, acc[p][2]));
-                        if constexpr (ANG) {
-                            // u += (T x d) / r^3
-                            const float2 cx = fma2(Ty, ddz, mul2(mTz, ddy));
-                            const float2 cy = fma2(Tz, ddx, mul2(mTx, ddz));
-                            const float2 cz = fma2(Tx, ddy, mul2(mTy, ddx));
-                            acc[p][0] = fma2(invr3, cx, acc[p][0]);
-                            acc[p][1] = fma2(invr3, cy, acc[p][1]);
-                            acc[p][2] = fma2(invr3, cz, acc[p][2]);
-                            // w += (F x d - T/2) / r^3 + (d.(3T/2)) d / r^5
-                            const float2 vx = fma2(fy, ddz, fma2(mfz, ddy, hx));
-                            const float2 vy = fma2(fz, ddx, fma2(mfx, ddz, hy));
-                            const float2 vz = fma2(fx, ddy, fma2(mfy, ddx, hz));
-                            const float2 t = mul2(invr5, fma2(ddx, gx, fma2(ddy, gy, mul2(ddz, gz))));
-                            acc[p][3] = fma2(t, ddx, fma2(invr3, vx, acc[p][3]));
-                            acc[p][4] = fma2(t, ddy, fma2(invr3, vy, acc[p][4]));
-                            acc[p][5] = fma2(t, ddz, fma2(invr3, vz, acc[p][5]));
-                        }
-                    }
+                    for (int p = 0; p < NP; ++p) far_slot(u, p);
                 }
             }
         }

@@ -98,6 +98,10 @@ def lib():
         L.lm_langevin_velocities.restype = st
         L.lm_set_sqrt_preconditioner.argtypes = [_vp, ctypes.c_int]
         L.lm_set_sqrt_preconditioner.restype = st
+        L.lm_set_reorthogonalization.argtypes = [_vp, ctypes.c_int]
+        L.lm_set_reorthogonalization.restype = st
+        L.lm_batch_set_reorthogonalization.argtypes = [_vp, ctypes.c_int]
+        L.lm_batch_set_reorthogonalization.restype = st
         L.lm_soft_repulsion.argtypes = [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _vp]
         L.lm_soft_repulsion.restype = st
         L.lm_ab_step.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_uint64, ctypes.c_double, ctypes.c_double,
@@ -361,6 +365,11 @@ def lm_set_sqrt_preconditioner(s: Solver, kind: int) -> None:
     _check(lib().lm_set_sqrt_preconditioner(s.handle, int(kind)))
 
 
+def lm_set_reorthogonalization(s: Solver, mode: int) -> None:
+    """Gram-Schmidt passes of the Lanczos root: 0 DGKS-adaptive (default), 1 always two."""
+    _check(lib().lm_set_reorthogonalization(s.handle, int(mode)))
+
+
 def lm_soft_repulsion(s: Solver, U0: float, b: float, d_pair: float, d_wall: float, like, out=None):
     """Soft steric forces, Eq. (soft_potential) of Sec. 5.1, at the solver's positions."""
     out = _like(like, (s.N, 3), s.f64) if out is None else out
@@ -496,6 +505,10 @@ def lm_batch_bd_run(b: Batch, kT: float, dt: float, k_trap: float, nsteps: int, 
 
 def lm_batch_set_tiling(b: Batch, threads: int, ilp: int) -> None:
     _check(lib().lm_batch_set_tiling(b.handle, int(threads), int(ilp)))
+
+
+def lm_batch_set_reorthogonalization(b: Batch, mode: int) -> None:
+    _check(lib().lm_batch_set_reorthogonalization(b.handle, int(mode)))
 
 
 def lm_batch_autotune(b: Batch) -> dict:

@@ -95,6 +95,30 @@ def test_batch_sqrt_philox_equals_explicit_noise(orc):
     assert rel(y1.cpu().numpy(), y2.cpu().numpy()) <= 1e-12
 
 
+def test_batch_forced_second_gram_schmidt_pass(orc):
+    """Two Gram-Schmidt passes at every iteration (the DGKS pass that the
+    adaptive test rarely asks for) give the same iterates to rounding, and the
+    results stay within the stopping tolerance of the exact root."""
+    b_ = small_batch(seed=17, S=5)
+    n = b_.pos.shape[0]
+    W = np.random.default_rng(5).standard_normal(3 * n)
+    b = lm.lm_batch_create(b_.offsets, 1.0, 1.0)
+    lm.lm_batch_set_positions(b, dev(b_.pos))
+    y0, it0 = lm.lm_batch_sqrt_mdot(b, dev(W), tol=1e-6)
+    lm.lm_batch_set_reorthogonalization(b, 1)
+    y1, it1 = lm.lm_batch_sqrt_mdot(b, dev(W), tol=1e-6)
+    y0, y1 = y0.cpu().numpy(), y1.cpu().numpy()
+    for s in range(b.S):
+        o0, o1 = b_.offsets[s], b_.offsets[s + 1]
+        assert abs(int(it0[s]) - int(it1[s])) <= 1
+        assert rel(y1[o0:o1], y0[o0:o1]) <= 1e-5, s
+        M = orc.assemble(b_.pos[o0:o1], 1.0, 1.0, False)
+        exact = orc.sqrt_exact(M, W[3 * o0:3 * o1])
+        assert rel(y1[o0:o1], exact) <= 20 * 1e-6, (s, rel(y1[o0:o1], exact))
+    with pytest.raises(lm.LmError):
+        lm.lm_batch_set_reorthogonalization(b, 2)
+
+
 def test_batch_sqrt_matches_single_system_api(orc):
     b_ = small_batch(seed=13, S=4)
     n = b_.pos.shape[0]

@@ -258,6 +258,36 @@ def test_sqrt_long_basis_matches_eigen_root(orc):
 
 
 @pytest.mark.parametrize("fp64", [False, True])
+def test_sqrt_forced_second_gram_schmidt_pass(orc, fp64):
+    """Mode 1 runs the second Gram-Schmidt pass at every iteration (the DGKS
+    pass that mode 0 skips unless the first pass cancelled): the same
+    iterates to rounding, the exact root within the stopping rule, and the
+    profile counts two passes at every iteration."""
+    n = 300
+    s_ = I.cube_suspension(41, n, 0.2, 1.0, angular=True, fp32=not fp64)
+    s = make(1.0, 1.0, True, fp64, s_.pos)
+    tol = 1e-8 if fp64 else 1e-5
+    lin0, ang0, it0 = lm.lm_sqrt_mdot(s, dev(s_.W), tol=tol, max_iter=300)
+    lm.lm_set_reorthogonalization(s, 1)
+    lm.lm_profile_read(s, reset=True)
+    lm.lm_profile_enable(s, True)
+    lin1, ang1, it1 = lm.lm_sqrt_mdot(s, dev(s_.W), tol=tol, max_iter=300)
+    lm.lm_profile_enable(s, False)
+    p = lm.lm_profile_read(s, reset=True)
+    y0 = np.concatenate([host(lin0).ravel(), host(ang0).ravel()])
+    y1 = np.concatenate([host(lin1).ravel(), host(ang1).ravel()])
+    assert abs(it1 - it0) <= 1
+    assert rel(y1, y0) <= (1e-12 if fp64 else 1e-5), rel(y1, y0)
+    M = orc.assemble(s_.pos, 1.0, 1.0, True)
+    assert rel(y1, orc.sqrt_exact(M, s_.W)) <= 20 * tol
+    nv = p["vector_iterations"]
+    two = sum(2 + (4 if k else 3) + 2 * (2 * k + 5) for k in range(nv)) * 8.0 * 6 * n
+    assert it1 <= nv <= it1 + 1 and p["vector_bytes"] == two
+    with pytest.raises(lm.LmError):
+        lm.lm_set_reorthogonalization(s, 3)
+
+
+@pytest.mark.parametrize("fp64", [False, True])
 def test_sqrt_rpy6_small_matches_oracle(orc, fp64):
     n = 600
     a, eta = 1.0, 1.0
