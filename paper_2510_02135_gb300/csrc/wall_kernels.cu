@@ -447,50 +447,58 @@ __global__ void __launch_bounds__(NT) rpy_wall_x2_kernel(const float4* __restric
                 const float m2 = fminf(r2[p].x, r2[p].y);
                 mn = (p == 0) ? m2 : fminf(mn, m2);
             }
+            // open-space far-field pair of slot p (two i-particles against j)
+            auto far_slot = [&](int p) {
+                const float2 invr = make_float2(rsqrtf(r2[p].x), rsqrtf(r2[p].y));
+                const float2 invr2 = mul2(invr, invr);
+                const float2 invr3 = mul2(invr2, invr);
+                const float2 A = fma2(K1, invr3, invr);
+                const float2 invr5 = mul2(invr3, invr2);
+                const float2 B = fma2(nK2, invr5, invr3);
+                const float2 dF = fma2(dx[p], fx, fma2(dy[p], fy, mul2(dz[p], fz)));
+                const float2 sB = mul2(B, dF);
+                acc[p][0] = fma2(sB, dx[p], fma2(A, fx, acc[p][0]));
+                acc[p][1] = fma2(sB, dy[p], fma2(A, fy, acc[p][1]));
+                acc[p][2] = fma2(sB, dz[p], fma2(A, fz, acc[p][2]));
+                if constexpr (ANG) {
+                    const float2 cx = fma2(Ty, dz[p], mul2(mTz, dy[p]));
+                    const float2 cy = fma2(Tz, dx[p], mul2(mTx, dz[p]));
+                    const float2 cz = fma2(Tx, dy[p], mul2(mTy, dx[p]));
+                    acc[p][0] = fma2(invr3, cx, acc[p][0]);
+                    acc[p][1] = fma2(invr3, cy, acc[p][1]);
+                    acc[p][2] = fma2(invr3, cz, acc[p][2]);
+                    const float2 vx = fma2(fy, dz[p], fma2(mfz, dy[p], hx));
+                    const float2 vy = fma2(fz, dx[p], fma2(mfx, dz[p], hy));
+                    const float2 vz = fma2(fx, dy[p], fma2(mfy, dx[p], hz));
+                    const float2 t = mul2(invr5, fma2(dx[p], gx, fma2(dy[p], gy, mul2(dz[p], gz))));
+                    acc[p][3] = fma2(t, dx[p], fma2(invr3, vx, acc[p][3]));
+                    acc[p][4] = fma2(t, dy[p], fma2(invr3, vy, acc[p][4]));
+                    acc[p][5] = fma2(t, dz[p], fma2(invr3, vz, acc[p][5]));
+                }
+            };
             if (__any_sync(0xffffffffu, mn < k.four_a2)) {
+                // the exact scalar form only for the slots that hold an
+                // overlapping (or self) pair somewhere in the warp
                 const float4 fj = make_float4(fx.x, fy.x, fz.x, 0.f);
                 float4 hj = make_float4(0.f, 0.f, 0.f, 0.f);
                 if constexpr (ANG) hj = make_float4(hx.x, hy.x, hz.x, 0.f);
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
-                    Acc<float, ANG> t0, t1;
+                    if (__any_sync(0xffffffffu, fminf(r2[p].x, r2[p].y) < k.four_a2)) {
+                        Acc<float, ANG> t0, t1;
 #pragma unroll
-                    for (int c = 0; c < C; ++c) { t0.p[c] = 0.f; t1.p[c] = 0.f; }
-                    pair_exact<float, ANG>(dx[p].x, dy[p].x, dz[p].x, r2[p].x, fj, hj, k, t0);
-                    pair_exact<float, ANG>(dx[p].y, dy[p].y, dz[p].y, r2[p].y, fj, hj, k, t1);
+                        for (int c = 0; c < C; ++c) { t0.p[c] = 0.f; t1.p[c] = 0.f; }
+                        pair_exact<float, ANG>(dx[p].x, dy[p].x, dz[p].x, r2[p].x, fj, hj, k, t0);
+                        pair_exact<float, ANG>(dx[p].y, dy[p].y, dz[p].y, r2[p].y, fj, hj, k, t1);
 #pragma unroll
-                    for (int c = 0; c < C; ++c) acc[p][c] = add2(acc[p][c], make_float2(t0.p[c], t1.p[c]));
+                        for (int c = 0; c < C; ++c) acc[p][c] = add2(acc[p][c], make_float2(t0.p[c], t1.p[c]));
+                    } else {
+                        far_slot(p);
+                    }
                 }
             } else {
 #pragma unroll
-                for (int p = 0; p < NP; ++p) {
-                    const float2 invr = make_float2(rsqrtf(r2[p].x), rsqrtf(r2[p].y));
-                    const float2 invr2 = mul2(invr, invr);
-                    const float2 invr3 = mul2(invr2, invr);
-                    const float2 A = fma2(K1, invr3, invr);
-                    const float2 invr5 = mul2(invr3, invr2);
-                    const float2 B = fma2(nK2, invr5, invr3);
-                    const float2 dF = fma2(dx[p], fx, fma2(dy[p], fy, mul2(dz[p], fz)));
-                    const float2 sB = mul2(B, dF);
-                    acc[p][0] = fma2(sB, dx[p], fma2(A, fx, acc[p][0]));
-                    acc[p][1] = fma2(sB, dy[p], fma2(A, fy, acc[p][1]));
-                    acc[p][2] = fma2(sB, dz[p], fma2(A, fz, acc[p][2]));
-                    if constexpr (ANG) {
-                        const float2 cx = fma2(Ty, dz[p], mul2(mTz, dy[p]));
-                        const float2 cy = fma2(Tz, dx[p], mul2(mTx, dz[p]));
-                        const float2 cz = fma2(Tx, dy[p], mul2(mTy, dx[p]));
-                        acc[p][0] = fma2(invr3, cx, acc[p][0]);
-                        acc[p][1] = fma2(invr3, cy, acc[p][1]);
-                        acc[p][2] = fma2(invr3, cz, acc[p][2]);
-                        const float2 vx = fma2(fy, dz[p], fma2(mfz, dy[p], hx));
-                        const float2 vy = fma2(fz, dx[p], fma2(mfx, dz[p], hy));
-                        const float2 vz = fma2(fx, dy[p], fma2(mfy, dx[p], hz));
-                        const float2 t = mul2(invr5, fma2(dx[p], gx, fma2(dy[p], gy, mul2(dz[p], gz))));
-                        acc[p][3] = fma2(t, dx[p], fma2(invr3, vx, acc[p][3]));
-                        acc[p][4] = fma2(t, dy[p], fma2(invr3, vy, acc[p][4]));
-                        acc[p][5] = fma2(t, dz[p], fma2(invr3, vz, acc[p][5]));
-                    }
-                }
+                for (int p = 0; p < NP; ++p) far_slot(p);
             }
             // the wall part: no branch (clamped heights keep rho >= 2a)
 #pragma unroll
