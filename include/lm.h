@@ -305,9 +305,11 @@ lm_status lm_set_adjoint_config(lm_solver *solver, const lm_pair_config *cfg);
  * lm_autotune -- time every supported pair-kernel configuration for the
  * solver's precision, angular flag and current N (positions must be set),
  * keep the fastest, and return it in *best (nullable).  reps >= 1 timed
- * launches per candidate.  For an LM_FP32C open solver without angular
- * blocks it also times the configurations of the adjoint kernel and keeps
- * the fastest (lm_get_adjoint_config).  Synchronises the stream.
+ * launches per candidate (after one warm-up launch); the three fastest are
+ * then timed three more times each, interleaved, and the best of their four
+ * timings decides.  For an LM_FP32C open solver without angular blocks it
+ * also times the configurations of the adjoint kernel the same way and
+ * keeps the fastest (lm_get_adjoint_config).  Synchronises the stream.
  */
 lm_status lm_autotune(lm_solver *solver, int reps, lm_pair_config *best);
 
