@@ -309,7 +309,11 @@ lm_status lm_set_adjoint_config(lm_solver *solver, const lm_pair_config *cfg);
  * then timed three more times each, interleaved, and the best of their four
  * timings decides.  For an LM_FP32C open solver without angular blocks it
  * also times the configurations of the adjoint kernel the same way and
- * keeps the fastest (lm_get_adjoint_config).  Synchronises the stream.
+ * keeps the fastest (lm_get_adjoint_config).  The choice is also recorded
+ * for the process under (device, precision, angular flag, geometry,
+ * floor(log2 N)): a solver without a configuration of its own (none set or
+ * tuned) whose N falls in a recorded bucket starts from that choice, with
+ * the split count recomputed for its N.  Synchronises the stream.
  */
 lm_status lm_autotune(lm_solver *solver, int reps, lm_pair_config *best);
 

@@ -4,13 +4,16 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <vector>
 
 #include "../../include/lm.h"
@@ -329,9 +332,47 @@ lm_pair_config default_config(const lm_solver* s, int64_t N) {
     return c;
 }
 
+// Tuned launch configurations shared by the solvers of this process:
+// lm_autotune records its choice under (device, precision, angular blocks,
+// geometry, N bucket = floor(log2 N)), and a solver without a configuration
+// of its own takes the one recorded for its bucket, with the split count
+// recomputed when its N is not the tuned N.
+struct TunedEntry {
+    lm_pair_config cfg;
+    lm_pair_config adj;
+    bool has_adj = false;
+    int64_t N = 0;
+};
+std::mutex g_tuned_mu;
+std::map<std::array<int, 5>, TunedEntry> g_tuned;
+
+std::array<int, 5> tuned_key(const lm_solver* s, int64_t N) {
+    int b = 0;
+    while (b < 62 && ((int64_t)1 << (b + 1)) <= N) ++b;
+    return {s->device, s->fp64 ? 1 : 0, s->angular ? 1 : 0, s->wall ? 1 : 0, b};
+}
+
+bool lookup_tuned(const lm_solver* s, int64_t N, TunedEntry* e) {
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    auto it = g_tuned.find(tuned_key(s, N));
+    if (it == g_tuned.end()) return false;
+    *e = it->second;
+    return true;
+}
+
 void ensure_config(lm_solver* s) {
     if (s->cfg_N == s->N) return;
-    if (!s->cfg_forced) s->cfg = default_config(s, s->N);
+    if (!s->cfg_forced) {
+        s->cfg = default_config(s, s->N);
+        TunedEntry e;
+        if (lookup_tuned(s, s->N, &e)) {
+            s->cfg = e.cfg;
+            if (e.N != s->N) {
+                const int occ = std::max(1, pair_ctas_per_sm(s, e.cfg.threads, e.cfg.ilp, e.cfg.packed));
+                s->cfg.splits = auto_splits(s->N, e.cfg.threads, e.cfg.ilp, occ * s->sm_count);
+            }
+        }
+    }
     s->cfg_N = s->N;
 }
 
@@ -420,6 +461,15 @@ lm_pair_config default_adjoint_config(const lm_solver* s) {
 void ensure_adjoint_config(lm_solver* s) {
     if (s->adj_cfg_N == s->N) return;
     s->adj_cfg = default_adjoint_config(s);
+    TunedEntry e;
+    if (lookup_tuned(s, s->N, &e) && e.has_adj) {
+        s->adj_cfg = e.adj;
+        if (e.N != s->N) {
+            const int occ = std::max(1, lmk::adjoint_ctas_per_sm(s->fp64, s->angular, e.adj.threads, e.adj.ilp,
+                                                                  e.adj.packed));
+            s->adj_cfg.splits = auto_splits(s->N, e.adj.threads, e.adj.ilp, occ * s->sm_count);
+        }
+    }
     s->adj_cfg_N = s->N;
 }
 
@@ -1241,6 +1291,15 @@ lm_status lm_autotune(lm_solver* s, int reps, lm_pair_config* best) {
     s->cfg = best_cfg;
     s->cfg_forced = true;
     s->cfg_N = N;
+    {
+        TunedEntry e;
+        e.cfg = best_cfg;
+        e.N = N;
+        e.has_adj = (s->adj_cfg_N == N) && !s->fp64 && !s->angular && !s->wall;
+        if (e.has_adj) e.adj = s->adj_cfg;
+        std::lock_guard<std::mutex> lk(g_tuned_mu);
+        g_tuned[tuned_key(s, N)] = e;
+    }
     if (best) *best = best_cfg;
     return LM_OK;
 }

@@ -328,6 +328,30 @@ def test_sqrt_philox_noise_matches_oracle_generator(orc):
     assert rel(y, orc.sqrt_exact(M, W)) <= 1e-8
 
 
+def test_fdt_whitening_of_library_noise(orc):
+    """The FDT test of Sec. 4 on the library's own output: samples
+    y = M^{1/2} W with W from the library's Philox generator (one seed per
+    sample), whitened by the oracle's SVD inverse root, are N(0, I):
+    component-wise Kolmogorov-Smirnov p-values and the sample covariance."""
+    from scipy.stats import kstest
+
+    n = 6
+    s_ = I.cube_suspension(53, n, 0.3, 1.0, angular=True, fp32=False)
+    s = make(1.0, 1.0, True, True, s_.pos)
+    M = orc.assemble(s_.pos, 1.0, 1.0, True)
+    U, sv, Vt = np.linalg.svd(M)
+    Minvsqrt = U @ np.diag(1.0 / np.sqrt(sv)) @ Vt
+    ns = 3000
+    like = dev(s_.F)
+    Z = np.empty((6 * n, ns))
+    for q in range(ns):
+        lin, ang, _ = lm.lm_sqrt_mdot(s, None, seed=1000 + q, tol=1e-10, max_iter=6 * n, like=like)
+        Z[:, q] = Minvsqrt @ np.concatenate([host(lin).ravel(), host(ang).ravel()])
+    pvals = [kstest(Z[c], "norm").pvalue for c in range(6 * n)]
+    assert min(pvals) > 1e-4, min(pvals)
+    np.testing.assert_allclose(np.cov(Z), np.eye(6 * n), atol=0.12)
+
+
 def test_sqrt_rpy6_n32768_norm_identity(orc):
     """Full-size Lanczos (N = 32768, 6N, FP32, tol 1e-5): |M^1/2 W|^2 = W^T M W,
     with W^T M W from the oracle's direct sum."""
@@ -439,3 +463,26 @@ def test_autotune_keeps_results(orc):
     u, _ = gpu_mdot(s, s_.F, None)
     ur, _ = orc.mdot(s_.pos, s_.F, None, 1.0, 1.0, False)
     assert rel(u, ur) <= 1e-5
+
+
+def test_autotune_choice_shared_within_n_bucket(orc):
+    """lm_autotune records its choice per (precision, angular, geometry,
+    floor(log2 N)): a new solver of the same kind whose N falls in the same
+    bucket starts from it (pair and adjoint kernels); other precisions keep
+    their own defaults; results stay exact."""
+    s_a = I.cube_suspension(61, 2600, 0.1, 1.0, angular=False, fp32=True)
+    a = make(1.0, 1.0, False, False, s_a.pos)
+    tuned = lm.lm_autotune(a, reps=2)
+    tuned_adj = lm.lm_get_adjoint_config(a)
+    n_b = 3900                                    # same bucket [2048, 4096)
+    s_b = I.cube_suspension(62, n_b, 0.1, 1.0, angular=False, fp32=True)
+    b = make(1.0, 1.0, False, False, s_b.pos)
+    cb = lm.lm_get_pair_config(b)
+    assert (cb["threads"], cb["ilp"], cb["packed"]) == (tuned["threads"], tuned["ilp"], tuned["packed"])
+    ab = lm.lm_get_adjoint_config(b)
+    assert (ab["threads"], ab["ilp"], ab["packed"]) == (tuned_adj["threads"], tuned_adj["ilp"], tuned_adj["packed"])
+    u, _ = gpu_mdot(b, s_b.F, None)
+    ur, _ = orc.mdot(s_b.pos, s_b.F, None, 1.0, 1.0, False)
+    assert rel(u, ur) <= 1e-5
+    c64 = lm.lm_get_pair_config(make(1.0, 1.0, False, True, s_b.pos.astype(np.float64)))
+    assert c64["packed"] == 0
