@@ -377,6 +377,22 @@ __device__ void chunk_dots(const BatchParams& P, int s, int e0, int e1, const do
     }
 }
 
+// Sum of base[c * stride] over c = c0, c0 + step, ... < ce with four
+// independent accumulators (four loads in flight; the order depends only on
+// c0, step and ce, so every caller with the same range gets the same bits).
+__device__ __forceinline__ double strided_sum4(const double* base, int64_t stride, int c0, int step, int ce) {
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    int c = c0;
+    for (; c + 3 * step < ce; c += 4 * step) {
+        t0 += base[(int64_t)c * stride];
+        t1 += base[(int64_t)(c + step) * stride];
+        t2 += base[(int64_t)(c + 2 * step) * stride];
+        t3 += base[(int64_t)(c + 3 * step) * stride];
+    }
+    for (; c < ce; c += step) t0 += base[(int64_t)c * stride];
+    return (t0 + t1) + (t2 + t3);
+}
+
 // Deterministic warp sum of base[c * stride] for c in [cb, ce): lane-strided
 // partial sums, then a butterfly (every lane returns the same value).
 __device__ __forceinline__ double warp_range_sum(const double* base, int64_t stride, int cb, int ce) {
@@ -400,8 +416,7 @@ __device__ void chunk_sum_coeffs(const BatchParams& P, int s, const double* part
     for (int j0 = 0; j0 < nrows; j0 += rows_per_pass) {
         const int j = j0 + threadIdx.x / G, q = threadIdx.x % G;
         double t = 0.0;
-        if (j < nrows)
-            for (int c = cb + q; c < ce; c += G) t += part[(int64_t)c * M1 + j];
+        if (j < nrows) t = strided_sum4(part + j, M1, cb + q, G, ce);
         for (int o = 1; o < G; o <<= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (j < nrows && q == 0) cvec[j] = t;
     }
@@ -770,6 +785,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                 for (int w = 0; w < NT / 32; ++w) t += sred[w];
                 partA[(int64_t)c * M1] = t;
                 if (e0 == 0) {
+                    P.amax[s] = 0.0;
                     P.active[s] = 1;
                     P.state[s] = 1;
                     P.msys[s] = 0;
@@ -838,7 +854,10 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                 const int ns = 3 * (int)(P.off[s + 1] - o);
                 const int e1 = min(e0 + kBatchChunk, ns);
                 const double alpha = warp_range_sum(P.part_item, 1, P.item_range[2 * s], P.item_range[2 * s + 1]);
-                if (e0 == 0 && tid == 0) P.alpha[s * P.m_max + k] = alpha;
+                if (e0 == 0 && tid == 0) {
+                    P.alpha[s * P.m_max + k] = alpha;
+                    P.amax[s] = fmax(P.amax[s], fabs(alpha));
+                }
                 const double bprev = (k > 0) ? P.beta[s * P.m_max + k - 1] : 0.0;
                 const double* vk = basis(P, s, k);
                 const double* vkm1 = (k > 0) ? basis(P, s, k - 1) : vk;
@@ -964,16 +983,14 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
             // at once.  A system keeps iterating while its results are pending;
             // iterations past its stopping point are discarded.
             for (int s = blockIdx.x; s < P.S; s += G) {
-                if (tid != 0 || P.state[s] != 1) continue;
-                double b2 = 0.0;
-                for (int c = P.chunk_range[2 * s]; c < P.chunk_range[2 * s + 1]; ++c) b2 += partA[(int64_t)c * M1];
+                // warp 0 adds the system's norm partials, then its lane 0 goes on alone
+                if (tid >= 32 || P.state[s] != 1) continue;
+                const double b2 = warp_range_sum(partA, M1, P.chunk_range[2 * s], P.chunk_range[2 * s + 1]);
+                if (tid != 0) continue;
                 const double b = sqrt(b2);
-                const double* al = P.alpha + s * P.m_max;
                 P.beta[s * P.m_max + k] = b;
                 const int m = k + 1;
-                double amax = 0.0;
-                for (int i = 0; i < m; ++i) amax = fmax(amax, fabs(al[i]));
-                const bool breakdown = b <= P.brk_rel * amax;
+                const bool breakdown = b <= P.brk_rel * P.amax[s];
                 const bool last = (m == P.m_max);
                 if (breakdown || last) {
                     if (k < P.k0s[s]) P.k0s[s] = k;   // the last iteration is always solved

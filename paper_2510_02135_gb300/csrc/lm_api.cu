@@ -1375,7 +1375,7 @@ struct lm_batch {
     int device = 0, sms = 1;
     double eta = 1.0, a = 1.0;
     std::vector<int64_t> off_h;
-    DBuf off, pos4, x64, Fbuf, u, w0, w1, V, alpha, beta, z, zprev, normW, rel, active, msys, itsum, notconv, nact;
+    DBuf off, pos4, x64, Fbuf, u, w0, w1, V, alpha, amax, beta, z, zprev, normW, rel, active, msys, itsum, notconv, nact;
     DBuf kprev, wsplit, usplit, woff;
     DBuf items, item_range, chunks, chunk_range, part_item, part_chunk, trk, trc, trs, bar, ticket, err, flag;
     DBuf in_stage, out_stage, W_stage;
@@ -1397,7 +1397,7 @@ struct lm_batch {
         wsplit.release();
         usplit.release();
         woff.release();
-        DBuf* all[] = {&off, &pos4, &x64, &Fbuf, &u, &w0, &w1, &V, &alpha, &beta, &z, &zprev, &normW, &rel,
+        DBuf* all[] = {&off, &pos4, &x64, &Fbuf, &u, &w0, &w1, &V, &alpha, &amax, &beta, &z, &zprev, &normW, &rel,
                        &active, &msys, &itsum, &notconv, &nact, &items, &item_range, &chunks, &chunk_range,
                        &part_item, &part_chunk, &trk, &trc, &trs, &bar, &ticket, &err, &flag, &in_stage,
                        &out_stage, &W_stage, &sv_w, &q_req, &q_seq, &q_ack, &q_ctr, &inflight, &zres, &zdone,
@@ -1465,6 +1465,7 @@ lmk::BatchParams batch_params(lm_batch* b, int mode) {
     p.w1 = b->w1.as<double>();
     p.V = b->V.as<double>();
     p.alpha = b->alpha.as<double>();
+    p.amax = b->amax.as<double>();
     p.beta = b->beta.as<double>();
     p.z = b->z.as<double>();
     p.zprev = b->zprev.as<double>();
@@ -1660,7 +1661,7 @@ lm_status lm_batch_create(lm_batch** out, int64_t S, const int64_t* offsets, dou
         {&b->x64, (size_t)n3 * sizeof(double)}, {&b->Fbuf, (size_t)n3 * sizeof(float)},
         {&b->u, (size_t)n3 * sizeof(double)}, {&b->w0, (size_t)n3 * sizeof(double)},
         {&b->w1, (size_t)n3 * sizeof(double)}, {&b->V, M * (size_t)n3 * sizeof(double)},
-        {&b->alpha, S_ * M * sizeof(double)}, {&b->beta, S_ * M * sizeof(double)},
+        {&b->alpha, S_ * M * sizeof(double)}, {&b->amax, S_ * sizeof(double)}, {&b->beta, S_ * M * sizeof(double)},
         {&b->z, S_ * M * sizeof(double)}, {&b->zprev, S_ * M * sizeof(double)},
         {&b->normW, S_ * sizeof(double)}, {&b->rel, S_ * sizeof(double)}, {&b->active, S_ * sizeof(int)},
         {&b->msys, S_ * sizeof(int)}, {&b->itsum, S_ * sizeof(int)}, {&b->notconv, S_ * sizeof(int)},

@@ -233,6 +233,7 @@ struct BatchParams {
     double* w1;                        // 3 Ntot Lanczos residual, odd iterations
     double* V;                         // Krylov bases: system s at V + m_max * 3 off[s], row j stride 3 N_s
     double* alpha;                     // S x m_max
+    double* amax;                      // S: max |alpha_i| so far in the step (breakdown test)
     double* beta;                      // S x m_max
     double* z;                         // S x m_max: |W| f(T_k) e1 of the latest iteration
     double* zprev;                     // S x m_max
