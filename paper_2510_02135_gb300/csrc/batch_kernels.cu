@@ -190,28 +190,37 @@ __device__ void pair_item(const BatchParams& P, int s, int i0, int jb, int je, c
         }
     }
     const float2 K1 = make_float2(k.K1, k.K1), nK2 = make_float2(-k.K2, -k.K2);
-    for (int jt = jb; jt < je; jt += NT) {
-        const int j = jt + tid;
-        __syncthreads();
+    // this thread's j of the next tile, loaded into registers one tile ahead so
+    // that the global-load latency hides behind the current tile's pairs
+    float nj[NRHS == 2 ? 9 : 6];
+    auto fetch = [&](int j) {
         if (j < je) {
             const float4 pj = P.pos4[o + j];
-            tx[tid] = pj.x; ty[tid] = pj.y; tz[tid] = pj.z;
+            nj[0] = pj.x; nj[1] = pj.y; nj[2] = pj.z;
             if (srcA_f) {
-                ax[tid] = srcA_f[3 * (o + j)]; ay[tid] = srcA_f[3 * (o + j) + 1]; az[tid] = srcA_f[3 * (o + j) + 2];
+                nj[3] = srcA_f[3 * (o + j)]; nj[4] = srcA_f[3 * (o + j) + 1]; nj[5] = srcA_f[3 * (o + j) + 2];
             } else {
-                ax[tid] = (float)(srcA_d[3 * (o + j)] * scaleA);
-                ay[tid] = (float)(srcA_d[3 * (o + j) + 1] * scaleA);
-                az[tid] = (float)(srcA_d[3 * (o + j) + 2] * scaleA);
+                nj[3] = (float)(srcA_d[3 * (o + j)] * scaleA);
+                nj[4] = (float)(srcA_d[3 * (o + j) + 1] * scaleA);
+                nj[5] = (float)(srcA_d[3 * (o + j) + 2] * scaleA);
             }
-            if (NRHS == 2) {
-                bx[tid] = P.Fbuf[3 * (o + j)]; by[tid] = P.Fbuf[3 * (o + j) + 1]; bz[tid] = P.Fbuf[3 * (o + j) + 2];
+            if constexpr (NRHS == 2) {
+                nj[6] = P.Fbuf[3 * (o + j)]; nj[7] = P.Fbuf[3 * (o + j) + 1]; nj[8] = P.Fbuf[3 * (o + j) + 2];
             }
         } else {
-            tx[tid] = pad; ty[tid] = pad; tz[tid] = pad;
-            ax[tid] = ay[tid] = az[tid] = 0.f;
-            if (NRHS == 2) bx[tid] = by[tid] = bz[tid] = 0.f;
+            nj[0] = nj[1] = nj[2] = pad;
+            nj[3] = nj[4] = nj[5] = 0.f;
+            if constexpr (NRHS == 2) nj[6] = nj[7] = nj[8] = 0.f;
         }
+    };
+    fetch(jb + tid);
+    for (int jt = jb; jt < je; jt += NT) {
         __syncthreads();
+        tx[tid] = nj[0]; ty[tid] = nj[1]; tz[tid] = nj[2];
+        ax[tid] = nj[3]; ay[tid] = nj[4]; az[tid] = nj[5];
+        if constexpr (NRHS == 2) { bx[tid] = nj[6]; by[tid] = nj[7]; bz[tid] = nj[8]; }
+        __syncthreads();
+        if (jt + NT < je) fetch(jt + NT + tid);
         for (int jj = 0; jj < NT; jj += 2) {
             const float2 xj = *reinterpret_cast<const float2*>(tx + jj);
             const float2 yj = *reinterpret_cast<const float2*>(ty + jj);
