@@ -451,10 +451,14 @@ lm_status lm_batch_autotune(lm_batch *batch, int *threads_out, int *ilp_out);
  * Lanczos iteration B, C2, C3, C4, C5, then the wait for the last
  * tridiagonal results, then D].  lm_batch_profile_read copies
  * up to n stamps of the last run into out and the number recorded into
- * *count.
+ * *count.  lm_batch_profile_pairs gives the pair evaluations of the last
+ * profiled run, all steps and systems: the particle pairs of every product
+ * work item, including the iterations a system runs past its stopping point
+ * while its tridiagonal results are pending (synchronises the stream).
  */
 lm_status lm_batch_profile_enable(lm_batch *batch, int enable);
 lm_status lm_batch_profile_read(lm_batch *batch, uint64_t *out, int n, int *count);
+lm_status lm_batch_profile_pairs(lm_batch *batch, uint64_t *pairs);
 
 /*
  * lm_tridiag_sqrt_e1_device -- the device form of the same tridiagonal step

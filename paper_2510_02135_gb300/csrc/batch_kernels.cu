@@ -304,6 +304,8 @@ __device__ void pair_item(const BatchParams& P, int s, int i0, int jb, int je, c
             }
         }
     }
+    if (P.pair_count != nullptr && tid == 0)
+        atomicAdd(P.pair_count, (unsigned long long)min(NT * NI, Ns - i0) * (unsigned long long)(je - jb));
     // outputs and the partial v_k . w of this item
     double dot = 0.0;
 #pragma unroll

@@ -1389,10 +1389,11 @@ struct lm_batch {
     bool has_pos = false;
     int* pinned = nullptr;
     bool prof_on = false;
-    DBuf timeline;
+    DBuf timeline, pcount;
     int timeline_len = 0;
     ~lm_batch() {
         timeline.release();
+        pcount.release();
         kprev.release();
         wsplit.release();
         usplit.release();
@@ -1523,6 +1524,7 @@ lmk::BatchParams batch_params(lm_batch* b, int mode) {
     if (b->prof_on && b->timeline.p) {
         p.timeline = b->timeline.as<unsigned long long>();
         p.timeline_len = b->timeline_len;
+        p.pair_count = b->pcount.as<unsigned long long>();
     }
     return p;
 }
@@ -1546,6 +1548,7 @@ lm_status batch_run(lm_batch* b, const lmk::BatchParams& p, bool use_graph) {
     // error may have left counts behind)
     cudaError_t e = cudaMemsetAsync(b->bar.p, 0, lmk::kBarWords * sizeof(unsigned), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->ticket.p, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess && p.pair_count) e = cudaMemsetAsync(p.pair_count, 0, sizeof(unsigned long long), st);
     // request ring, counters and result tags start empty in every launch
     const size_t S_ = (size_t)b->S;
     if (e == cudaSuccess) e = cudaMemsetAsync(b->q_seq.p, 0, (size_t)b->q_cap * sizeof(unsigned long long), st);
@@ -1875,7 +1878,22 @@ lm_status lm_batch_profile_enable(lm_batch* b, int enable) {
         b->timeline_len = 5 + 5 * b->m_max;
         LM_CUDA(b->timeline.ensure((size_t)b->timeline_len * sizeof(unsigned long long)), "batch timeline");
         LM_CUDA(cudaMemset(b->timeline.p, 0, (size_t)b->timeline_len * sizeof(unsigned long long)), "timeline");
+        LM_CUDA(b->pcount.ensure(sizeof(unsigned long long)), "batch pair counter");
+        LM_CUDA(cudaMemset(b->pcount.p, 0, sizeof(unsigned long long)), "batch pair counter");
     }
+    return LM_OK;
+}
+
+lm_status lm_batch_profile_pairs(lm_batch* b, uint64_t* pairs) {
+    if (lm_status st = check_batch(b, false)) return st;
+    if (pairs == nullptr) return fail(LM_ERR_INVALID_ARG, "pairs is NULL");
+    DeviceGuard g(b->device);
+    *pairs = 0;
+    if (b->pcount.p == nullptr) return LM_OK;
+    LM_CUDA(cudaStreamSynchronize(b->stream), "batch pair counter");
+    unsigned long long v = 0;
+    LM_CUDA(cudaMemcpy(&v, b->pcount.p, sizeof(v), cudaMemcpyDeviceToHost), "batch pair counter");
+    *pairs = (uint64_t)v;
     return LM_OK;
 }
 

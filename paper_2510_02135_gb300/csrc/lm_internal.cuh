@@ -295,6 +295,7 @@ struct BatchParams {
     const float* F_in;                 // kBatchMdot input
     float* lin_out;                    // kBatchMdot / kBatchSqrt output
     const double* W_in;                // kBatchSqrt noise (nullable: Philox)
+    unsigned long long* pair_count;    // nullable: pair evaluations of the run (profiling)
     unsigned long long* timeline;      // nullable: phase end times (ns) of the first step
     int timeline_len;
 };

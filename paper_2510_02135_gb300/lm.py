@@ -158,6 +158,8 @@ def lib():
         L.lm_batch_profile_enable.restype = st
         L.lm_batch_profile_read.argtypes = [_vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.lm_batch_profile_read.restype = st
+        L.lm_batch_profile_pairs.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.lm_batch_profile_pairs.restype = st
         L.lm_tridiag_sqrt_e1_device.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.lm_tridiag_sqrt_e1_device.restype = st
         L.lm_batch_solve_counts.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
@@ -519,6 +521,13 @@ def lm_batch_autotune(b: Batch) -> dict:
 
 def lm_batch_profile_enable(b: Batch, enable: bool = True) -> None:
     _check(lib().lm_batch_profile_enable(b.handle, int(bool(enable))))
+
+
+def lm_batch_profile_pairs(b: Batch) -> int:
+    """Pair evaluations of the last profiled run (all steps and systems)."""
+    v = ctypes.c_uint64(0)
+    _check(lib().lm_batch_profile_pairs(b.handle, ctypes.byref(v)))
+    return int(v.value)
 
 
 def lm_batch_profile_read(b: Batch) -> np.ndarray:

@@ -81,6 +81,7 @@ def test_null_solver_and_null_pointers(L):
     assert L.lm_set_sqrt_preconditioner(None, 1) == lm.LM_ERR_INVALID_ARG
     assert L.lm_set_reorthogonalization(None, 1) == lm.LM_ERR_INVALID_ARG
     assert L.lm_batch_set_reorthogonalization(None, 1) == lm.LM_ERR_INVALID_ARG
+    assert L.lm_batch_profile_pairs(None, None) == lm.LM_ERR_INVALID_ARG
     assert L.lm_soft_repulsion(None, 1.0, 0.1, 2.0, 1.0, None) == lm.LM_ERR_INVALID_ARG
     assert L.lm_ab_step(None, None, None, None, 0, 1.0, 1e-3, 1e-5, 10, None, 1, None, None) == lm.LM_ERR_INVALID_ARG
     assert L.lm_langevin_velocities(None, None, None, None, 0, 1.0, 1e-3, 1e-5, 10, None, None,

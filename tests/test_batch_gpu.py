@@ -82,6 +82,25 @@ def test_batch_sqrt_matches_oracle(orc):
         assert abs(int(its[s]) - ito) <= 1, (s, its[s], ito)
 
 
+def test_batch_profile_counts_pair_evaluations():
+    """The profiling pair counter: one batched product evaluates exactly
+    sum_s N_s^2 pairs; a batched square root at least sum_s N_s^2 per
+    Lanczos iteration of system s (speculative iterations on top)."""
+    b_ = small_batch(seed=23, S=5)
+    sizes = np.diff(b_.offsets)
+    F = np.random.default_rng(2).standard_normal((b_.pos.shape[0], 3)).astype(np.float32)
+    b = lm.lm_batch_create(b_.offsets, 1.0, 1.0)
+    lm.lm_batch_set_positions(b, dev(b_.pos))
+    lm.lm_batch_profile_enable(b, True)
+    for threads, ilp in ((64, 1), (128, 2)):
+        lm.lm_batch_set_tiling(b, threads, ilp)
+        lm.lm_batch_mdot(b, dev(F))
+        assert lm.lm_batch_profile_pairs(b) == int(np.sum(sizes.astype(np.int64) ** 2))
+    W = np.random.default_rng(3).standard_normal(3 * b_.pos.shape[0])
+    _, its = lm.lm_batch_sqrt_mdot(b, dev(W), tol=1e-6)
+    assert lm.lm_batch_profile_pairs(b) >= int(np.sum(sizes.astype(np.int64) ** 2 * np.asarray(its)))
+
+
 def test_batch_sqrt_philox_equals_explicit_noise(orc):
     b_ = small_batch(seed=11)
     n = b_.pos.shape[0]
