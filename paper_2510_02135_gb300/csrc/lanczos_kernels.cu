@@ -96,14 +96,14 @@ __device__ __forceinline__ double basis_combination(const double* __restrict__ V
     return a0 + a1;
 }
 
-// w[e] (+)= sign * sum_j c[j] V[j][e]; accumulate = 0 overwrites (y = V^T z).
-__global__ void combine_kernel(const double* __restrict__ V, int m, const double* __restrict__ c,
-                               double* __restrict__ w, int64_t n, int accumulate, double sign) {
+// y[e] = sum_j z[j] V[j][e] (the Lanczos iterate y = V z).
+__global__ void combine_kernel(const double* __restrict__ V, int m, const double* __restrict__ z,
+                               double* __restrict__ y, int64_t n) {
     __shared__ double csh[256];
     for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e - threadIdx.x < n;
          e += (int64_t)gridDim.x * kThreads) {
-        const double acc = basis_combination(V, m, c, n, e, csh);
-        if (e < n) w[e] = accumulate ? fma(sign, acc, w[e]) : sign * acc;
+        const double acc = basis_combination(V, m, z, n, e, csh);
+        if (e < n) y[e] = acc;
     }
 }
 
@@ -396,7 +396,7 @@ cudaError_t lz_scale(const double* x, const double* nrm, double* y, int64_t n, c
 }
 
 cudaError_t lz_combine(const double* V, int m, const double* z, double* y, int64_t n, cudaStream_t s) {
-    combine_kernel<<<blocks_for(n, 1), kThreads, 0, s>>>(V, m, z, y, n, 0, 1.0);
+    combine_kernel<<<blocks_for(n, 1), kThreads, 0, s>>>(V, m, z, y, n);
     count_launches(1);
     return cudaGetLastError();
 }
