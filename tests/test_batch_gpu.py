@@ -175,6 +175,35 @@ def test_batch_bd_one_step_matches_oracle(orc):
         assert abs(int(its[s]) - itr) <= 1
 
 
+def test_batch_bd_full_size_step_on_sampled_systems(orc):
+    """The benchmark's batch (256 systems, N log-uniform in [64, 4096]) in
+    its launch configuration (autotuned tiling, max_iter 64, tol 1e-4): one
+    Euler-Maruyama step against the oracle's step with the same Philox noise,
+    on the smallest systems and a few of a few hundred particles."""
+    c = I.BATCH_BD_256
+    b_ = I.batch_suspensions(c["seed"], c["S"], c["nmin"], c["nmax"], c["phi_lo"], c["phi_hi"], c["a"])
+    b = lm.lm_batch_create(b_.offsets, c["eta"], c["a"], max_iter=64)
+    lm.lm_batch_set_positions(b, dev(b_.pos))
+    lm.lm_batch_autotune(b)
+    its = lm.lm_batch_bd_run(b, c["kT"], c["dt"], c["k_trap"], 1, step0=0, seed=c["seed"], tol=c["tol"],
+                             use_graph=True)
+    x1 = lm.lm_batch_get_positions(b, like=dev(b_.pos)).cpu().numpy()
+    order = np.argsort(b_.sizes)
+    mid = [s for s in order if 300 <= b_.sizes[s] <= 700][:3]
+    for s in list(order[:3]) + mid:
+        o0, o1 = b_.offsets[s], b_.offsets[s + 1]
+        x0 = b_.pos[o0:o1].astype(np.float64)
+        W = orc.philox_normals(c["seed"], orc.bd_noise_stream(s, 0), 3 * (o1 - o0))
+        xr, itr = orc.em_step(x0, c["a"], c["eta"], c["kT"], c["dt"], c["k_trap"], W, c["tol"])
+        d_gpu, d_ref = x1[o0:o1] - x0, xr - x0
+        atol = 2 * np.abs(x0).max() * 2 ** -24
+        # iteration counts may differ by one near the stopping rule: then the
+        # iterates differ by about tol
+        assert abs(int(its[s]) - itr) <= 1, (s, its[s], itr)
+        lim = (1e-5 if int(its[s]) == itr else 20 * c["tol"]) * np.abs(d_ref).max() + atol
+        assert np.abs(d_gpu - d_ref).max() <= lim, (s, int(b_.sizes[s]))
+
+
 def test_batch_bd_graph_direct_and_resume_agree():
     b_ = small_batch(seed=19, S=7, nmin=16, nmax=300)
     args = dict(kT=1.0, dt=1e-3, k_trap=1.0, seed=5, tol=1e-4)

@@ -188,16 +188,35 @@ def test_mdot_rpy6_n32768_sampled_rows(orc):
 
 
 def test_mdot_melt_n524288_sampled_rows(orc):
-    """Largest workload: 1024 chains x 512 beads, 6N, FP32; 48 sampled rows."""
+    """Largest workload: 1024 chains x 512 beads, 6N, FP32; 48 sampled rows,
+    in the default launch configuration and in the one the autotuner picks
+    there (256 threads x 8 i-particles, two j per vote)."""
     c = I.MELT_N524288
     m = I.polymer_melt(c["seed"], c["n_chains"], c["beads"], c["bond"], c["sigma"], c["phi"], c["a"])
     s = make(c["eta"], c["a"], True, False, m.pos)
-    u, w = gpu_mdot(s, m.F, m.T)
     rows = np.random.default_rng(1).choice(m.pos.shape[0], 48, replace=False)
     ur, wr = orc.mdot(m.pos, m.F, m.T, c["a"], c["eta"], True, rows=rows)
+    for cfg in (None, (256, 8, 20, 2)):
+        if cfg is not None:
+            lm.lm_set_pair_config(s, *cfg)
+        u, w = gpu_mdot(s, m.F, m.T)
+        assert rel(u[rows], ur) <= 1e-5, (cfg, rel(u[rows], ur))
+        assert rel(w[rows], wr) <= 1e-5, (cfg, rel(w[rows], wr))
+        assert np.isfinite(u).all() and np.isfinite(w).all()
+
+
+def test_mdot_tt_n65536_sampled_rows(orc):
+    """Full-size translation workload of the adjoint benchmark (N = 65536,
+    phi = 0.1) in the autotuned forward configuration; 256 sampled rows."""
+    c = I.ADJOINT_N65536
+    s_ = I.cube_suspension(c["seed"], c["n"], c["phi"], c["a"], angular=False, fp32=True)
+    s = make(c["eta"], c["a"], False, False, s_.pos)
+    lm.lm_autotune(s, reps=2)
+    rows = np.random.default_rng(2).choice(c["n"], 256, replace=False)
+    u, _ = gpu_mdot(s, s_.F, None)
+    ur, _ = orc.mdot(s_.pos, s_.F, None, c["a"], c["eta"], False, rows=rows)
     assert rel(u[rows], ur) <= 1e-5, rel(u[rows], ur)
-    assert rel(w[rows], wr) <= 1e-5, rel(w[rows], wr)
-    assert np.isfinite(u).all() and np.isfinite(w).all()
+    assert np.isfinite(u).all()
 
 
 def test_host_arrays_are_copied_by_the_library(orc):
