@@ -1,8 +1,10 @@
 // FP64 vector kernels of the Krylov (Lanczos) square root, M^{1/2} W
-// (libMobility paper, Sec. 3.3).  They are HBM-bound: dot products, the
-// three-term update, classical Gram-Schmidt against the stored basis
-// (full reorthogonalisation), the final combination y = V z and the
-// Philox-4x32-10 normal generator for W.
+// (libMobility paper, Sec. 3.3): dot products, the three-term update,
+// classical Gram-Schmidt against the stored basis (full reorthogonalisation),
+// the final combination y = V z and the Philox-4x32-10 normal generator for
+// W.  They stream FP64 vectors from HBM; the Gram-Schmidt pair does one FP64
+// FMA per 8-byte basis element, so on GB300 (FP64 at 1/64 of the FP32 rate)
+// the FP64 pipe, not HBM, bounds it once the basis is long.
 #include <cuda_runtime.h>
 
 #include <cstdint>
