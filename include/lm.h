@@ -147,8 +147,9 @@ lm_status lm_set_sqrt_preconditioner(lm_solver *solver, int kind);
 
 /*
  * lm_set_reorthogonalization -- the Gram-Schmidt passes of the Lanczos
- * square root (full reorthogonalisation against the stored basis, reading 6
- * of the Lanczos details).  mode 0 (the default): one classical pass, and a
+ * square root (full reorthogonalisation of each new Krylov vector against the
+ * stored basis, as in the Krylov square-root method of Ando, Chow, Saad &
+ * Skolnick 2012 that Sec. 3.3 cites).  mode 0 (the default): one classical pass, and a
  * second only when the first removed more than 1 - 1/sqrt(2) of the norm of
  * w (the DGKS criterion, Daniel, Gragg, Kaufman & Stewart 1976).  mode 1:
  * always two passes (costs one more pass over the basis per iteration; the
@@ -313,7 +314,12 @@ lm_status lm_set_adjoint_config(lm_solver *solver, const lm_pair_config *cfg);
  * for the process under (device, precision, angular flag, geometry,
  * floor(log2 N)): a solver without a configuration of its own (none set or
  * tuned) whose N falls in a recorded bucket starts from that choice, with
- * the split count recomputed for its N.  Synchronises the stream.
+ * the split count recomputed for its N.  For FP32 products large enough
+ * that one launch takes more than about 20 ms (N^2 x flops per pair above
+ * 1e12), the sweep keeps only the packed forms with at least 512 particles
+ * per i-block and the split counts of the model and of whole waves, and
+ * candidates after the first are timed without a warm-up launch of their
+ * own.  Synchronises the stream.
  */
 lm_status lm_autotune(lm_solver *solver, int reps, lm_pair_config *best);
 
@@ -496,6 +502,21 @@ lm_status lm_batch_timeout_selftest(long long spin_cycles);
  * seed high), Box-Muller in FP64.  out: n doubles, device memory.
  */
 lm_status lm_philox_normals(uint64_t seed, uint64_t stream, double *out, int64_t n, void *cuda_stream);
+
+/*
+ * lm_philox4x32_10 -- the raw words of the device generator behind
+ * lm_philox_normals, the Lanczos noise, the RFD displacements and the
+ * batched Brownian noise: Philox-4x32 with 10 rounds (Salmon, Moraes, Dror &
+ * Shaw, SC'11), so that it can be checked against the generator's published
+ * known-answer vectors.  The paper has no counterpart (it only requires
+ * Gaussian W, Eq. fdt).
+ *   counters: count x 4 uint32 (c0..c3), keys: count x 2 uint32 (k0, k1),
+ *   out: count x 4 uint32; all device memory, owned by the caller.
+ *   count >= 0; host pointers give LM_ERR_INVALID_ARG.  Stream-ordered on
+ *   cuda_stream (NULL = legacy default stream).
+ */
+lm_status lm_philox4x32_10(const uint32_t *counters, const uint32_t *keys, uint32_t *out, int64_t count,
+                           void *cuda_stream);
 
 /*
  * lm_mdot_noalloc -- the FP32 (compensated) mobility product for callers that

@@ -650,13 +650,8 @@ cudaError_t launch_adj_t(const AdjointArgs& a, cudaStream_t s) {
     const RpyConst<R> k = make_rpy_const<R>(a.a);
     dim3 grid((unsigned)nblk, (unsigned)splits);
     constexpr size_t dyn = adj_running_bytes<R, ANG, NT, NI>();
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(rpy_adjoint_kernel<R, ANG, NT, NI>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr_devs{0};  // devices whose limit is raised
+    if (cudaError_t e = smem_attr_once(attr_devs, rpy_adjoint_kernel<R, ANG, NT, NI>, dyn)) return e;
     rpy_adjoint_kernel<R, ANG, NT, NI><<<grid, NT, dyn, s>>>(static_cast<const typename V4<R>::type*>(a.pos4), a.F,
                                                        ANG ? a.T : nullptr, a.G, ANG ? a.H : nullptr, a.fp64, a.N,
                                                        ntiles, k, c8, a.dX, a.dF, ANG ? a.dT : nullptr, a.partials);
@@ -682,13 +677,8 @@ cudaError_t launch_adj_x2_t(const AdjointArgs& a, cudaStream_t s) {
     const RpyConst<float> k = make_rpy_const<float>(a.a);
     dim3 grid((unsigned)nblk, (unsigned)splits);
     constexpr size_t dyn = adj_x2_smem_bytes<NT, NI>();
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(rpy_adjoint_x2_kernel<NT, NI, UJ>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr_devs{0};  // devices whose limit is raised
+    if (cudaError_t e = smem_attr_once(attr_devs, rpy_adjoint_x2_kernel<NT, NI, UJ>, dyn)) return e;
     rpy_adjoint_x2_kernel<NT, NI, UJ><<<grid, NT, dyn, s>>>(static_cast<const float4*>(a.pos4), a.F, a.G, a.fp64, a.N,
                                                         ntiles, k, c8, a.dX, a.dF, a.partials);
     cudaError_t err = cudaGetLastError();

@@ -33,6 +33,7 @@
 #include <cstdint>
 
 #include "lm_internal.cuh"
+#include "philox.cuh"
 #include "tridiag.cuh"
 #include "tridiag_dev.cuh"
 
@@ -104,36 +105,6 @@ __device__ bool grid_sync(const BatchParams& P) {
     }
     __syncthreads();
     return *(volatile int*)P.err == kBatchOk;
-}
-
-// Philox-4x32-10 (Salmon et al., SC'11) and FP64 Box-Muller, as in the
-// single-system generator.
-__device__ __forceinline__ void philox(uint32_t c[4], uint32_t k0, uint32_t k1) {
-    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
-        const uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
-        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
-        if (r < 9) { k0 += W0; k1 += W1; }
-    }
-}
-
-__device__ __forceinline__ void normals4(uint64_t seed, uint64_t stream, uint64_t q, double z[4]) {
-    uint32_t c[4] = {(uint32_t)(q & 0xffffffffu), (uint32_t)(q >> 32), (uint32_t)(stream & 0xffffffffu),
-                     (uint32_t)(stream >> 32)};
-    philox(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        const double u1 = ((double)c[2 * p] + 1.0) * (1.0 / 4294967296.0);
-        const double u2 = (double)c[2 * p + 1] * (1.0 / 4294967296.0);
-        const double rad = sqrt(-2.0 * log(u1));
-        double sn, cs;
-        sincospi(2.0 * u2, &sn, &cs);
-        z[2 * p] = rad * cs;
-        z[2 * p + 1] = rad * sn;
-    }
 }
 
 __device__ __forceinline__ double* basis(const BatchParams& P, int s, int j) {
@@ -778,7 +749,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                 const uint64_t stream = (P.mode == kBatchBD) ? ((gstep << 32) | (uint64_t)s) : (uint64_t)s;
                 for (int q = e0 / 4 + tid; 4 * q < e1; q += NT) {
                     double zz[4];
-                    normals4(P.seed, stream, (uint64_t)q, zz);
+                    philox_normals4(P.seed, stream, (uint64_t)q, zz);
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
                         const int e = 4 * q + t;

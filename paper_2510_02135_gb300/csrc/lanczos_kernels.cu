@@ -10,6 +10,7 @@
 #include <cstdint>
 
 #include "lm_internal.cuh"
+#include "philox.cuh"
 
 namespace lmk {
 namespace {
@@ -129,41 +130,25 @@ __global__ void store_kernel(const double* __restrict__ y, double scale, int64_t
     }
 }
 
-// Philox-4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): 10 rounds of the
-// multiply/xor round on four 32-bit words, the key bumped by the Weyl
-// constants after every round but the last.
-__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
-    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
-        const uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
-        const uint32_t n0 = hi1 ^ c[1] ^ k0, n1 = lo1, n2 = hi0 ^ c[3] ^ k1, n3 = lo0;
-        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
-        if (r < 9) { k0 += W0; k1 += W1; }
-    }
-}
-
 __global__ void philox_normals_kernel(uint64_t seed, uint64_t stream, double* __restrict__ W, int64_t n) {
     const int64_t nq = (n + 3) / 4;
     for (int64_t q = (int64_t)blockIdx.x * kThreads + threadIdx.x; q < nq; q += (int64_t)gridDim.x * kThreads) {
-        uint32_t c[4] = {(uint32_t)(q & 0xffffffffu), (uint32_t)((uint64_t)q >> 32),
-                         (uint32_t)(stream & 0xffffffffu), (uint32_t)(stream >> 32)};
-        philox4x32_10(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
         double z[4];
-#pragma unroll
-        for (int p = 0; p < 2; ++p) {
-            const double u1 = ((double)c[2 * p] + 1.0) * (1.0 / 4294967296.0);
-            const double u2 = (double)c[2 * p + 1] * (1.0 / 4294967296.0);
-            const double rad = sqrt(-2.0 * log(u1));
-            double sn, cs;
-            sincospi(2.0 * u2, &sn, &cs);
-            z[2 * p] = rad * cs;
-            z[2 * p + 1] = rad * sn;
-        }
+        philox_normals4(seed, stream, (uint64_t)q, z);
 #pragma unroll
         for (int t = 0; t < 4; ++t)
             if (4 * q + t < n) W[4 * q + t] = z[t];
+    }
+}
+
+// Raw Philox-4x32-10 words: out[4 e + t] = word t of philox(ctr[4 e ..], key[2 e ..]).
+__global__ void philox_words_kernel(const uint32_t* __restrict__ ctr, const uint32_t* __restrict__ key,
+                                    uint32_t* __restrict__ out, int64_t count) {
+    for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < count; e += (int64_t)gridDim.x * kThreads) {
+        uint32_t c[4] = {ctr[4 * e], ctr[4 * e + 1], ctr[4 * e + 2], ctr[4 * e + 3]};
+        philox4x32_10(c, key[2 * e], key[2 * e + 1]);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) out[4 * e + t] = c[t];
     }
 }
 
@@ -413,6 +398,14 @@ cudaError_t lz_store(const double* y, double scale, int64_t N, int angular, void
 
 cudaError_t lz_philox_normals(uint64_t seed, uint64_t stream, double* W, int64_t n, cudaStream_t s) {
     philox_normals_kernel<<<blocks_for((n + 3) / 4), kThreads, 0, s>>>(seed, stream, W, n);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t lz_philox_words(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t count,
+                            cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    philox_words_kernel<<<blocks_for(count), kThreads, 0, s>>>(ctr, key, out, count);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -288,12 +288,19 @@ int pair_ctas_per_sm(const lm_solver* s, int threads, int ilp, int packed) {
 
 // Split counts the autotuner times for one tiling: the model's choice, half,
 // one and a half and twice it, and the counts that make the CTA count a whole
-// number (1..4) of waves of `slots` resident CTAs.
-std::vector<int> split_candidates(int64_t N, int threads, int ilp, int slots) {
+// number (1..4) of waves of `slots` resident CTAs.  `model_and_waves` keeps
+// only the model's choice and the whole-wave counts.
+std::vector<int> split_candidates(int64_t N, int threads, int ilp, int slots, bool model_and_waves = false) {
     const int64_t nblk = (N + (int64_t)threads * ilp - 1) / ((int64_t)threads * ilp);
     const int64_t ntiles = (N + threads - 1) / threads;
     const int sa = auto_splits(N, threads, ilp, slots);
-    std::vector<int> c = {sa, std::max(1, sa / 2), std::max(1, (3 * sa) / 2), sa * 2, auto_splits(N, threads, ilp, slots, 1)};
+    std::vector<int> c = {sa};
+    if (!model_and_waves) {
+        c.push_back(std::max(1, sa / 2));
+        c.push_back(std::max(1, (3 * sa) / 2));
+        c.push_back(sa * 2);
+        c.push_back(auto_splits(N, threads, ilp, slots, 1));
+    }
     for (int w = 1; w <= 4; ++w) {
         const int64_t sp = ((int64_t)w * slots) / std::max<int64_t>(1, nblk);
         if (sp >= 1 && sp <= ntiles && sp <= 256 && sp * nblk == (int64_t)w * slots) c.push_back((int)sp);
@@ -1204,13 +1211,24 @@ lm_status lm_autotune(lm_solver* s, int reps, lm_pair_config* best) {
     std::vector<lm_pair_config> cands;
     const int threads_opts[2] = {128, 256};
     const int ilp_opts[4] = {1, 2, 4, 8};
+    // Large products (an FP32 launch of more than about 20 ms at the measured
+    // 50 TFLOP/s): the sweep keeps the packed FP32 forms with i-blocks of at
+    // least 512 particles and the split counts of whole waves, and times each
+    // candidate without its own warm-up launch.  The scalar form and small
+    // i-blocks lost at every size above 2^17 where they were timed, and a full
+    // sweep would take minutes there.
+    const double flops_pp = s->wall ? (s->angular ? lmk::kFlopsPerPairWall6N : lmk::kFlopsPerPairWallTT)
+                                    : (s->angular ? lmk::kFlopsPerPair6N : lmk::kFlopsPerPairTT);
+    const bool large = !s->fp64 && (double)N * (double)N * flops_pp > 20e-3 * 50e12;
     for (int pk = 0; pk <= 2; ++pk) {
+        if (large && pk == 0) continue;
         for (int t : threads_opts) {
             for (int il : ilp_opts) {
+                if (large && t * il < 512) continue;
                 if (!pair_config_supported(s, t, il, pk)) continue;
                 const int occ = pair_ctas_per_sm(s, t, il, pk);
                 if (occ < 1) continue;
-                for (int sp : split_candidates(N, t, il, occ * s->sm_count))
+                for (int sp : split_candidates(N, t, il, occ * s->sm_count, large))
                     cands.push_back(lm_pair_config{t, il, sp, pk});
             }
         }
@@ -1219,8 +1237,12 @@ lm_status lm_autotune(lm_solver* s, int reps, lm_pair_config* best) {
     LM_CUDA(cudaEventCreate(&e0), "autotune events");
     LM_CUDA(cudaEventCreate(&e1), "autotune events");
     // Times `reps` launches of one candidate (after one warm-up launch).
+    bool warm = false;
     auto time_one = [&](auto&& launch, const lm_pair_config& c, float* ms) -> lm_status {
-        if (lm_status st = launch(c)) return st;
+        if (!large || !warm) {
+            if (lm_status st = launch(c)) return st;
+            warm = true;
+        }
         cudaEventRecord(e0, s->stream);
         for (int r = 0; r < reps; ++r)
             if (lm_status st = launch(c)) return st;
@@ -1957,6 +1979,18 @@ lm_status lm_philox_normals(uint64_t seed, uint64_t stream, double* out, int64_t
     if (!is_device_ptr(out)) return fail(LM_ERR_INVALID_ARG, "out must be device memory");
     if (n == 0) return LM_OK;
     LM_CUDA(lmk::lz_philox_normals(seed, stream, out, n, static_cast<cudaStream_t>(cuda_stream)), "noise generator");
+    return LM_OK;
+}
+
+lm_status lm_philox4x32_10(const uint32_t* counters, const uint32_t* keys, uint32_t* out, int64_t count,
+                           void* cuda_stream) {
+    if (count < 0) return fail(LM_ERR_INVALID_ARG, "count must be >= 0");
+    if (count == 0) return LM_OK;
+    if (!counters || !keys || !out) return fail(LM_ERR_INVALID_ARG, "counters, keys and out are required");
+    if (!is_device_ptr(counters) || !is_device_ptr(keys) || !is_device_ptr(out))
+        return fail(LM_ERR_INVALID_ARG, "counters, keys and out must be device memory");
+    LM_CUDA(lmk::lz_philox_words(counters, keys, out, count, static_cast<cudaStream_t>(cuda_stream)),
+            "Philox words");
     return LM_OK;
 }
 

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 
 namespace lmk {
@@ -15,6 +16,23 @@ struct __align__(32) dvec4 {
 
 // Kernel launches issued by the library (all solvers, all threads).
 void count_launches(int n);
+
+// Raises the dynamic shared-memory limit of kernel `fn` to `bytes` on the
+// current device, once per device.  The attribute belongs to the device
+// context, so a process that drives several GPUs sets it on each of them;
+// `devs` (one per kernel instantiation) records the devices done, bit d for
+// device d (devices 64 and above set it on every launch).
+template <typename K>
+inline cudaError_t smem_attr_once(std::atomic<unsigned long long>& devs, K fn, size_t bytes) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+    if (bit && (devs.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && bit) devs.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
 // Message returned by lm_last_error() on the calling thread.
 void set_last_error(const char* msg);
 
@@ -202,6 +220,8 @@ cudaError_t lz_store(const double* y, double scale, int64_t N, int angular, void
 // counter (q low, q high, stream low, stream high), key (seed low, seed high),
 // two Box-Muller pairs from the words (0, 1) and (2, 3).
 cudaError_t lz_philox_normals(uint64_t seed, uint64_t stream, double* W, int64_t n, cudaStream_t s);
+cudaError_t lz_philox_words(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t count,
+                            cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // Batched persistent kernel (batch_kernels.cu) over S concatenated systems.

@@ -435,13 +435,8 @@ cudaError_t launch_t(const MdotArgs& a, cudaStream_t s) {
     dim3 grid((unsigned)nblk, (unsigned)splits);
     if (splits > 1 && a.partials == nullptr) return cudaErrorInvalidValue;
     constexpr size_t dyn = running_sum_bytes<R, ANG, NT, NI>();
-    static bool attr_set = false;  // per instantiation; the attribute is process-wide
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(rpy_mdot_kernel<R, ANG, NT, NI>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr_devs{0};  // devices whose limit is raised
+    if (cudaError_t e = smem_attr_once(attr_devs, rpy_mdot_kernel<R, ANG, NT, NI>, dyn)) return e;
     if (a.ev_begin) cudaEventRecord(a.ev_begin, s);
     rpy_mdot_kernel<R, ANG, NT, NI><<<grid, NT, dyn, s>>>(
         static_cast<const typename V4<R>::type*>(a.pos4), a.F, ANG ? a.T : nullptr, a.in_f64, a.N, ntiles, k, c8,
@@ -470,13 +465,8 @@ cudaError_t launch_x2_t(const MdotArgs& a, cudaStream_t s) {
     dim3 grid((unsigned)nblk, (unsigned)splits);
     if (splits > 1 && a.partials == nullptr) return cudaErrorInvalidValue;
     constexpr size_t dyn = x2_smem_bytes<ANG, NT, NI>();
-    static bool attr_set = false;  // per instantiation; the attribute is process-wide
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(rpy_mdot_x2_kernel<ANG, NT, NI, UJ>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr_devs{0};  // devices whose limit is raised
+    if (cudaError_t e = smem_attr_once(attr_devs, rpy_mdot_x2_kernel<ANG, NT, NI, UJ>, dyn)) return e;
     if (a.ev_begin) cudaEventRecord(a.ev_begin, s);
     rpy_mdot_x2_kernel<ANG, NT, NI, UJ><<<grid, NT, dyn, s>>>(static_cast<const float4*>(a.pos4), a.F,
                                                           ANG ? a.T : nullptr, a.in_f64, a.N, ntiles, k, c8,

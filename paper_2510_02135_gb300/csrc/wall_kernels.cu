@@ -553,13 +553,8 @@ cudaError_t launch_wall_x2_t(const MdotArgs& a, cudaStream_t s) {
     const RpyConst<float> k = make_rpy_const<float>(a.a);
     dim3 grid((unsigned)nblk, (unsigned)splits);
     constexpr size_t dyn = wall_x2_smem_bytes<ANG, NT, NI>();
-    static bool attr_set = false;  // per instantiation; the attribute is process-wide
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(rpy_wall_x2_kernel<ANG, NT, NI>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr_devs{0};  // devices whose limit is raised
+    if (cudaError_t e = smem_attr_once(attr_devs, rpy_wall_x2_kernel<ANG, NT, NI>, dyn)) return e;
     if (a.ev_begin) cudaEventRecord(a.ev_begin, s);
     rpy_wall_x2_kernel<ANG, NT, NI><<<grid, NT, dyn, s>>>(static_cast<const float4*>(a.pos4), a.F,
                                                           ANG ? a.T : nullptr, a.in_f64, a.N, ntiles, k,
@@ -616,13 +611,8 @@ cudaError_t launch_wall_t(const MdotArgs& a, cudaStream_t s) {
     const RpyConst<R> k = make_rpy_const<R>(a.a);
     dim3 grid((unsigned)nblk, (unsigned)splits);
     constexpr size_t dyn = running_sum_bytes<R, ANG, NT, NI>();
-    static bool attr_set = false;  // per instantiation; the attribute is process-wide
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(rpy_wall_kernel<R, ANG, NT, NI>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr_devs{0};  // devices whose limit is raised
+    if (cudaError_t e = smem_attr_once(attr_devs, rpy_wall_kernel<R, ANG, NT, NI>, dyn)) return e;
     if (a.ev_begin) cudaEventRecord(a.ev_begin, s);
     rpy_wall_kernel<R, ANG, NT, NI><<<grid, NT, dyn, s>>>(
         static_cast<const typename V4<R>::type*>(a.pos4), a.F, ANG ? a.T : nullptr, a.in_f64, a.N, ntiles, k,

@@ -168,6 +168,8 @@ def lib():
         L.lm_batch_timeout_selftest.restype = st
         L.lm_philox_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint64, _vp, ctypes.c_int64, _vp]
         L.lm_philox_normals.restype = st
+        L.lm_philox4x32_10.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp]
+        L.lm_philox4x32_10.restype = st
         L.lm_tridiag_sqrt_e1.argtypes = [ctypes.c_int, _vp, _vp, _vp]
         L.lm_tridiag_sqrt_e1.restype = ctypes.c_int
         _lib = L
@@ -572,6 +574,17 @@ def lm_philox_normals(seed: int, stream: int, out, cuda_stream=None) -> None:
     if cuda_stream is None:
         cuda_stream = _current_stream(out)
     _check(lib().lm_philox_normals(int(seed), int(stream), _ptr(out, True, None, "out"), out.numel(), cuda_stream))
+
+
+def lm_philox4x32_10(counters, keys, out, cuda_stream=None) -> None:
+    """Raw Philox-4x32-10 words on the device: counters (count, 4), keys
+    (count, 2) and out (count, 4) are CUDA int32/uint32 tensors."""
+    count = counters.numel() // 4
+    if keys.numel() != 2 * count or out.numel() != 4 * count:
+        raise ValueError("counters (count, 4), keys (count, 2) and out (count, 4) must agree")
+    if cuda_stream is None:
+        cuda_stream = _current_stream(out)
+    _check(lib().lm_philox4x32_10(counters.data_ptr(), keys.data_ptr(), out.data_ptr(), count, cuda_stream))
 
 
 def lm_get_pair_config(s: Solver) -> dict:

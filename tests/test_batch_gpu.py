@@ -48,6 +48,25 @@ def test_philox_normals_match_oracle(orc):
         np.testing.assert_allclose(out.cpu().numpy(), ref, rtol=0, atol=1e-13)
 
 
+def test_device_philox_known_answer_vectors():
+    """The device generator (the one source of the library's noise) against
+    the published Philox-4x32-10 known-answer vectors, read from
+    tests/golden/philox4x32_10_kat.txt, bitwise."""
+    import os
+
+    rows = []
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")):
+        if line.strip() and not line.startswith("#"):
+            rows.append([int(w, 16) for w in line.split()])
+    a = np.array(rows, dtype=np.uint64).astype(np.uint32).view(np.int32)
+    ctr = torch.from_numpy(np.ascontiguousarray(a[:, 0:4])).cuda()
+    key = torch.from_numpy(np.ascontiguousarray(a[:, 4:6])).cuda()
+    out = torch.zeros_like(ctr)
+    lm.lm_philox4x32_10(ctr, key, out)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), a[:, 6:10].view(np.uint32))
+
+
 def test_batch_mdot_matches_oracle(orc):
     b_ = small_batch()
     rng = np.random.default_rng(1)
