@@ -222,7 +222,7 @@ def _pair_config_arg(text):
 # The hot-path step: set_positions + M [F; T] + Lanczos M^{1/2} W
 # ---------------------------------------------------------------------------
 def hotpath_leg(workload, steps, warmup, dist, local, *, pair_config=None, autotune=True, e2e_steps=0,
-                sample_clocks=True):
+                sample_clocks=True, probe=False):
     """Times `steps` hot-path steps of `workload` after `warmup` untimed ones.
     Returns a dict of results; the solver and the device tensors of the last
     step stay in it (keys starting with "_") for the checks that follow."""
@@ -336,6 +336,16 @@ def hotpath_leg(workload, steps, warmup, dist, local, *, pair_config=None, autot
                               f"(nominal FP32 FMA peak at the recipe's maximum SM clock)"}
     if clocks and achieved:
         roofline["frac_at_sampled_clock"] = achieved / (peak * clocks["sm_mhz"] / RECIPE_MAX_SM_MHZ)
+    if probe and achieved:
+        # measured FP32 FMA ceilings of this GPU (library probe, after the timed region)
+        pr = {"ffma": lm.lm_fp32_probe(0), "ffma2": lm.lm_fp32_probe(1), "ffma2_distinct_operands": lm.lm_fp32_probe(2),
+              "ffma2_dependent_chains": lm.lm_fp32_probe(3)}
+        roofline["probe_tflops"] = pr
+        roofline["frac_of_probe_ffma2"] = achieved / pr["ffma2"]
+        roofline["probe_note"] = ("lm_fp32_probe on this GPU after the timed region: FMA streams on every SM; "
+                                  "ffma2 = packed f32x2 FMA (the pair kernels' instruction form) with reused "
+                                  "operands; distinct = three distinct register pairs per instruction; dependent "
+                                  "chains = operands produced a few instructions earlier")
     hbm = measured_hbm_gbs()
     vec_gbs = prof["vector_bytes"] / (prof["vector_ms"] / 1e3) / 1e9 if prof["vector_ms"] > 0 else None
     lanczos_vectors = {
@@ -673,7 +683,7 @@ def main():
     _build.build()
     t_job0 = time.perf_counter()
     leg = hotpath_leg(args.workload, args.steps, args.warmup, dist, local, pair_config=pcfg,
-                      autotune=not args.no_autotune, e2e_steps=max(1, args.e2e_steps))
+                      autotune=not args.no_autotune, e2e_steps=max(1, args.e2e_steps), probe=True)
     cfg = leg["cfg"]
     line = {"metric": METRIC, "value": leg["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": leg["ms_per_step"], "higher_is_better": True,

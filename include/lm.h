@@ -551,6 +551,27 @@ lm_status lm_mdot_noalloc(const float *pos, const float *forces, const float *to
                           double viscosity, double hydrodynamic_radius, int include_angular,
                           float *lin_out, float *ang_out, void *cuda_stream);
 
+/*
+ * lm_fp32_probe -- measured FP32 FMA throughput of the current GPU, the
+ * ceiling of the pair kernels (no paper counterpart: a calibration of the
+ * roofline the pair kernels are reported against).  Runs `iters` outer
+ * iterations of independent FMA chains on every SM (one full wave of CTAs)
+ * on cuda_stream (NULL = legacy default stream), twice, and returns the
+ * second launch's rate in *tflops (2 flops per FMA lane).
+ *   mode 0: scalar FMA chains x = x a + b;
+ *   mode 1: packed f32x2 FMA chains of the same form (the instruction form of
+ *           the packed pair kernels);
+ *   mode 2: packed f32x2 FMAs on 12 independent accumulators, each reading
+ *           two loop-invariant register pairs of its own (three distinct
+ *           register pairs per instruction);
+ *   mode 3: packed f32x2 FMAs in rotating dependent chains whose operands are
+ *           values produced a few instructions earlier (the data flow of the
+ *           pair formulas).
+ *   1 <= iters <= 2^24 (about 2^14 gives a launch of tens of milliseconds).
+ * Allocates and frees a small output buffer; synchronises the stream.
+ */
+lm_status lm_fp32_probe(int mode, int64_t iters, double *tflops, void *cuda_stream);
+
 /* Thread-local message for the last non-OK status ("" if none). */
 const char *lm_last_error(void);
 

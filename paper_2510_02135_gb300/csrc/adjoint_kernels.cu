@@ -399,8 +399,8 @@ constexpr size_t adj_x2_smem_bytes() {
     return (size_t)kAdjX2Words * NT * sizeof(float4) + adj_running_bytes<float, false, NT, NI>();
 }
 
-template <int NT, int NI, int UJ>
-__global__ void __launch_bounds__(NT) rpy_adjoint_x2_kernel(const float4* __restrict__ pos4,
+template <int NT, int NI, int UJ, int MINB = 1>
+__global__ void __launch_bounds__(NT, MINB) rpy_adjoint_x2_kernel(const float4* __restrict__ pos4,
                                                             const void* __restrict__ Fp, const void* __restrict__ Gp,
                                                             int f64, int64_t N, int64_t ntiles, RpyConst<float> k,
                                                             double c8, void* __restrict__ dX, void* __restrict__ dF,

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <numeric>
 #include <array>
 #include <atomic>
 #include <cmath>
@@ -305,6 +306,14 @@ std::vector<int> split_candidates(int64_t N, int threads, int ilp, int slots, bo
         const int64_t sp = ((int64_t)w * slots) / std::max<int64_t>(1, nblk);
         if (sp >= 1 && sp <= ntiles && sp <= 256 && sp * nblk == (int64_t)w * slots) c.push_back((int)sp);
     }
+    // many i-blocks: the smallest split count of at least the model's choice
+    // that makes the CTA count a whole number of waves (nblk x s a multiple of
+    // slots), e.g. 19 splits of 256 i-blocks on 152 slots
+    if (nblk > 0 && slots > 0) {
+        const int64_t step = slots / std::gcd<int64_t>(nblk, slots);
+        const int64_t sp = ((std::max<int64_t>(sa, 1) + step - 1) / step) * step;
+        if (sp <= ntiles && sp <= 64) c.push_back((int)sp);
+    }
     std::vector<int> out;
     for (int v : c)
         if (std::find(out.begin(), out.end(), v) == out.end()) out.push_back(v);
@@ -405,7 +414,8 @@ lm_status run_mdot(lm_solver* s, const void* F, const void* T, int in_f64, void*
     a.partials = nullptr;
     const int64_t se = lmk::mdot_effective_splits(s->N, cfg.threads, cfg.splits);
     if (se > 1) {
-        const size_t bytes = (size_t)se * lmk::mdot_partial_components(s->angular) * (size_t)s->N * sizeof(double);
+        const size_t bytes =
+            (size_t)se * lmk::mdot_partial_components(s->angular) * (size_t)s->N * sizeof(double);
         LM_CUDA(s->partials.ensure(bytes), "allocating split partial sums");
         a.partials = s->partials.as<double>();
     }

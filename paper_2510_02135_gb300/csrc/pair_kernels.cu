@@ -29,25 +29,29 @@
 namespace lmk {
 namespace {
 
+// Shared memory of the scalar kernels: the j-tile (static) and the running
+// sums (dynamic, [c][q][tid]; FP32 adds the low parts).
+template <typename R, bool ANG, int NT>
+struct ScalarTile {
+    typename V4<R>::type p[NT];
+    typename V4<R>::type f[NT];
+    typename V4<R>::type h[ANG ? NT : 1];
+};
+
+// Sums of the i-block starting at i0 against j in [jb, je) into s_hi / s_lo
+// (zeroed here); every thread leaves its own entries.
 template <typename R, bool ANG, int NT, int NI>
-__global__ void __launch_bounds__(NT) rpy_mdot_kernel(const typename V4<R>::type* __restrict__ pos4,
-                                                      const void* __restrict__ Fp, const void* __restrict__ Tp,
-                                                      int in_f64, int64_t N, int64_t ntiles, RpyConst<R> k,
-                                                      double c8, void* __restrict__ lin, void* __restrict__ ang,
-                                                      int out_f64, double* __restrict__ partials) {
+__device__ __forceinline__ void scalar_segment(const typename V4<R>::type* __restrict__ pos4,
+                                               const void* __restrict__ Fp, const void* __restrict__ Tp,
+                                               int in_f64, int64_t N, int64_t i0, int64_t jb, int64_t je,
+                                               const RpyConst<R>& k, ScalarTile<R, ANG, NT>& tile, R* s_hi,
+                                               R* s_lo) {
     using R4 = typename V4<R>::type;
     constexpr int C = ANG ? 6 : 3;
-    __shared__ R4 sp[NT];
-    __shared__ R4 sf[NT];
-    __shared__ R4 sh[ANG ? NT : 1];
-    extern __shared__ __align__(16) unsigned char dyn_smem[];
-    R* s_hi = reinterpret_cast<R*>(dyn_smem);              // [c][q][tid]
-    R* s_lo = s_hi + (sizeof(R) == 4 ? C * NI * NT : 0);     // FP32 only
-
+    R4* sp = tile.p;
+    R4* sf = tile.f;
+    R4* sh = tile.h;
     const int tid = threadIdx.x;
-    const int64_t i0 = (int64_t)blockIdx.x * (NT * NI);
-    int64_t jb, je;
-    split_range(N, NT, ntiles, &jb, &je);
     const R pad = (R)kPadCoord;
 
     R xi[NI], yi[NI], zi[NI];
@@ -133,6 +137,24 @@ __global__ void __launch_bounds__(NT) rpy_mdot_kernel(const typename V4<R>::type
         __syncthreads();
     }
 
+}
+
+template <typename R, bool ANG, int NT, int NI>
+__global__ void __launch_bounds__(NT) rpy_mdot_kernel(const typename V4<R>::type* __restrict__ pos4,
+                                                      const void* __restrict__ Fp, const void* __restrict__ Tp,
+                                                      int in_f64, int64_t N, int64_t ntiles, RpyConst<R> k,
+                                                      double c8, void* __restrict__ lin, void* __restrict__ ang,
+                                                      int out_f64, double* __restrict__ partials) {
+    constexpr int C = ANG ? 6 : 3;
+    __shared__ ScalarTile<R, ANG, NT> tile;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    R* s_hi = reinterpret_cast<R*>(dyn_smem);              // [c][q][tid]
+    R* s_lo = s_hi + (sizeof(R) == 4 ? C * NI * NT : 0);     // FP32 only
+    const int tid = threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.x * (NT * NI);
+    int64_t jb, je;
+    split_range(N, NT, ntiles, &jb, &je);
+    scalar_segment<R, ANG, NT, NI>(pos4, Fp, Tp, in_f64, N, i0, jb, je, k, tile, s_hi, s_lo);
     const bool direct = (gridDim.y == 1);
 #pragma unroll
     for (int q = 0; q < NI; ++q) {
@@ -188,26 +210,18 @@ constexpr size_t x2_smem_bytes() {
     return (size_t)x2_words<ANG>() * NT * sizeof(float4) + running_sum_bytes<float, ANG, NT, NI>();
 }
 
+// Sums of the i-block starting at i0 against j in [jb, je) into the running
+// sums s_hi / s_lo (zeroed here); every thread leaves its own entries.
 template <bool ANG, int NT, int NI, int UJ>
-__global__ void __launch_bounds__(NT) rpy_mdot_x2_kernel(const float4* __restrict__ pos4,
-                                                         const void* __restrict__ Fp, const void* __restrict__ Tp,
-                                                         int in_f64, int64_t N, int64_t ntiles, RpyConst<float> k,
-                                                         double c8, void* __restrict__ lin, void* __restrict__ ang,
-                                                         int out_f64, double* __restrict__ partials) {
+__device__ __forceinline__ void x2_segment(const float4* __restrict__ pos4, const void* __restrict__ Fp,
+                                           const void* __restrict__ Tp, int in_f64, int64_t N, int64_t i0,
+                                           int64_t jb, int64_t je, const RpyConst<float>& k, float4* s_t,
+                                           float* s_hi, float* s_lo) {
     static_assert(NI % 2 == 0, "packed form needs an even number of i-particles per thread");
     static_assert(NT % UJ == 0, "the j tile must hold whole groups of UJ");
     constexpr int NP = NI / 2;
     constexpr int C = ANG ? 6 : 3;
-    constexpr int W = x2_words<ANG>();
-    extern __shared__ __align__(16) unsigned char dyn_smem[];
-    float4* s_t = reinterpret_cast<float4*>(dyn_smem);                 // [w][jj]
-    float* s_hi = reinterpret_cast<float*>(s_t + W * NT);              // [c][q][tid]
-    float* s_lo = s_hi + C * NI * NT;
-
     const int tid = threadIdx.x;
-    const int64_t i0 = (int64_t)blockIdx.x * (NT * NI);
-    int64_t jb, je;
-    split_range(N, NT, ntiles, &jb, &je);
     const float pad = (float)kPadCoord;
 
     float2 xi[NP], yi[NP], zi[NP];
@@ -402,6 +416,39 @@ __global__ void __launch_bounds__(NT) rpy_mdot_x2_kernel(const float4* __restric
         __syncthreads();
     }
 
+}
+
+// Dynamic shared memory of the packed kernels: [w][jj] tile words, then the
+// running sums [c][q][tid] (hi, then lo).
+template <bool ANG, int NT, int NI>
+struct X2Smem {
+    float4* t;
+    float* hi;
+    float* lo;
+    __device__ explicit X2Smem(unsigned char* base) {
+        t = reinterpret_cast<float4*>(base);
+        hi = reinterpret_cast<float*>(t + x2_words<ANG>() * NT);
+        lo = hi + (ANG ? 6 : 3) * NI * NT;
+    }
+};
+
+// Split schedule: CTA (blockIdx.x, blockIdx.y) takes i-block blockIdx.x and
+// j-split blockIdx.y; several splits write FP64 partials that a second kernel
+// adds.
+template <bool ANG, int NT, int NI, int UJ>
+__global__ void __launch_bounds__(NT) rpy_mdot_x2_kernel(const float4* __restrict__ pos4,
+                                                         const void* __restrict__ Fp, const void* __restrict__ Tp,
+                                                         int in_f64, int64_t N, int64_t ntiles, RpyConst<float> k,
+                                                         double c8, void* __restrict__ lin, void* __restrict__ ang,
+                                                         int out_f64, double* __restrict__ partials) {
+    constexpr int C = ANG ? 6 : 3;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    X2Smem<ANG, NT, NI> sm(dyn_smem);
+    const int tid = threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.x * (NT * NI);
+    int64_t jb, je;
+    split_range(N, NT, ntiles, &jb, &je);
+    x2_segment<ANG, NT, NI, UJ>(pos4, Fp, Tp, in_f64, N, i0, jb, je, k, sm.t, sm.hi, sm.lo);
     const bool direct = (gridDim.y == 1);
 #pragma unroll
     for (int q = 0; q < NI; ++q) {
@@ -410,7 +457,7 @@ __global__ void __launch_bounds__(NT) rpy_mdot_x2_kernel(const float4* __restric
 #pragma unroll
         for (int c = 0; c < C; ++c) {
             const int o = (c * NI + q) * NT + tid;
-            const double v = (double)s_hi[o] + (double)s_lo[o];
+            const double v = (double)sm.hi[o] + (double)sm.lo[o];
             if (direct) {
                 void* out = (c < 3) ? lin : ang;
                 const int64_t idx = 3 * i + (c % 3);
@@ -501,22 +548,21 @@ cudaError_t launch_x2(const MdotArgs& a, cudaStream_t s) {
     return a.packed == 2 ? launch_x2_u<ANG, 2>(a, s) : launch_x2_u<ANG, 1>(a, s);
 }
 
+template <typename K>
+int occupancy_of(K kernel, int threads, size_t dyn) {
+    int n = 0;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, dyn);
+    return e == cudaSuccess ? n : 0;
+}
+
 template <bool ANG, int UJ>
 int occupancy_x2(int threads, int ilp) {
-    int n = 0;
-    cudaError_t e = cudaErrorInvalidConfiguration;
-#define LM_OCC2(NT, NI)                                                                                   \
-    if (threads == NT && ilp == NI) {                                                                     \
-        constexpr size_t dyn = x2_smem_bytes<ANG, NT, NI>();                                              \
-        e = cudaFuncSetAttribute(rpy_mdot_x2_kernel<ANG, NT, NI, UJ>,                                     \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);                  \
-        if (e == cudaSuccess)                                                                             \
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rpy_mdot_x2_kernel<ANG, NT, NI, UJ>, NT, \
-                                                              dyn);                                       \
-    }
+#define LM_OCC2(NT, NI) \
+    if (threads == NT && ilp == NI) return occupancy_of(rpy_mdot_x2_kernel<ANG, NT, NI, UJ>, NT, x2_smem_bytes<ANG, NT, NI>());
     LM_OCC2(128, 2) LM_OCC2(128, 4) LM_OCC2(128, 8) LM_OCC2(256, 2) LM_OCC2(256, 4) LM_OCC2(256, 8)
 #undef LM_OCC2
-    return e == cudaSuccess ? n : 0;
+    return 0;
 }
 
 // Instantiated configurations: FP32 threads {128, 256} x ilp {1, 2, 4, 8};
@@ -543,23 +589,14 @@ cudaError_t launch_r(const MdotArgs& a, cudaStream_t s) {
 
 template <typename R, bool ANG>
 int occupancy_r(int threads, int ilp) {
-    int n = 0;
-    cudaError_t e = cudaErrorInvalidConfiguration;
-#define LM_OCC(NT, NI)                                                                             \
-    if (threads == NT && ilp == NI) {                                                              \
-        constexpr size_t dyn = running_sum_bytes<R, ANG, NT, NI>();                                \
-        e = cudaFuncSetAttribute(rpy_mdot_kernel<R, ANG, NT, NI>,                                  \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);           \
-        if (e == cudaSuccess)                                                                      \
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rpy_mdot_kernel<R, ANG, NT, NI>, \
-                                                              NT, dyn);                            \
-    }
+#define LM_OCC(NT, NI) \
+    if (threads == NT && ilp == NI) return occupancy_of(rpy_mdot_kernel<R, ANG, NT, NI>, NT, running_sum_bytes<R, ANG, NT, NI>());
     LM_OCC(128, 1) LM_OCC(128, 2) LM_OCC(256, 1) LM_OCC(256, 2)
     if constexpr (sizeof(R) == 4) {
         LM_OCC(128, 4) LM_OCC(128, 8) LM_OCC(256, 4) LM_OCC(256, 8)
     }
 #undef LM_OCC
-    return e == cudaSuccess ? n : 0;
+    return 0;
 }
 
 }  // namespace

@@ -170,6 +170,8 @@ def lib():
         L.lm_philox_normals.restype = st
         L.lm_philox4x32_10.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp]
         L.lm_philox4x32_10.restype = st
+        L.lm_fp32_probe.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), _vp]
+        L.lm_fp32_probe.restype = st
         L.lm_tridiag_sqrt_e1.argtypes = [ctypes.c_int, _vp, _vp, _vp]
         L.lm_tridiag_sqrt_e1.restype = ctypes.c_int
         _lib = L
@@ -632,6 +634,15 @@ def lm_profile_read(s: Solver, reset: bool = True) -> dict:
     return {"pair_launches": p.pair_launches, "pair_ms": p.pair_ms, "pair_interactions": p.pair_interactions,
             "pair_flops": p.pair_flops, "vector_iterations": p.vector_iterations, "vector_ms": p.vector_ms,
             "vector_bytes": p.vector_bytes}
+
+
+def lm_fp32_probe(mode: int, iters: int = 1 << 14, cuda_stream=None) -> float:
+    """Measured FP32 FMA rate of the current GPU in TFLOP/s (mode 0 scalar,
+    1 packed f32x2, 2 packed with three distinct operand pairs, 3 packed in
+    dependent chains of fresh operands)."""
+    t = ctypes.c_double(0.0)
+    _check(lib().lm_fp32_probe(int(mode), int(iters), ctypes.byref(t), cuda_stream))
+    return t.value
 
 
 def lm_launch_count() -> int:

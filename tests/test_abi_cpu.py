@@ -134,3 +134,15 @@ def test_tridiagonal_root_clamps_negative(orc, L):
     alpha = np.array([-1e-18, 1.0])
     beta = np.array([0.0])
     np.testing.assert_allclose(lm.lm_tridiag_sqrt_e1(alpha, beta), [0.0, 0.0], atol=1e-15)
+
+
+def test_fp32_probe_rejects_bad_arguments_without_gpu(L):
+    """The FP32 throughput probe checks its arguments before touching the GPU."""
+    import ctypes as C
+
+    from paper_2510_02135_gb300 import lm
+
+    t = C.c_double(0.0)
+    for mode, iters in ((4, 100), (-1, 100), (1, 0), (1, (1 << 24) + 1)):
+        assert L.lm_fp32_probe(mode, iters, C.byref(t), None) == lm.LM_ERR_INVALID_ARG
+    assert L.lm_fp32_probe(1, 100, None, None) == lm.LM_ERR_INVALID_ARG
