@@ -388,11 +388,11 @@ __global__ void __launch_bounds__(NT) rpy_adjoint_kernel(const typename V4<R>::t
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
-__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
 
-constexpr int kAdjX2Words = 5;   // float4 words per j: (-x,-x,-y,-y) (-z,-z,Fx,Fx) (Fy,Fy,Fz,Fz) (Gx,Gx,Gy,Gy) (Gz,Gz,0,0)
+// float4 words per j, plain scalars (a j-value enters a packed instruction as
+// the same scalar in both lanes): (-x,-y,-z,Fx) (Fy,Fz,Gx,Gy) (Gz,0,0,0)
+constexpr int kAdjX2Words = 3;
 
 template <int NT, int NI>
 constexpr size_t adj_x2_smem_bytes() {
@@ -478,11 +478,9 @@ __global__ void __launch_bounds__(NT, MINB) rpy_adjoint_x2_kernel(const float4* 
     fetch(jb + tid);
 
     for (int64_t jt = jb; jt < je; jt += NT) {
-        s_t[0 * NT + tid] = make_float4(-np.x, -np.x, -np.y, -np.y);
-        s_t[1 * NT + tid] = make_float4(-np.z, -np.z, nF.x, nF.x);
-        s_t[2 * NT + tid] = make_float4(nF.y, nF.y, nF.z, nF.z);
-        s_t[3 * NT + tid] = make_float4(nG.x, nG.x, nG.y, nG.y);
-        s_t[4 * NT + tid] = make_float4(nG.z, nG.z, 0.f, 0.f);
+        s_t[0 * NT + tid] = make_float4(-np.x, -np.y, -np.z, nF.x);
+        s_t[1 * NT + tid] = make_float4(nF.y, nF.z, nG.x, nG.y);
+        s_t[2 * NT + tid] = make_float4(nG.z, 0.f, 0.f, 0.f);
         __syncthreads();
         if (jt + NT < je) fetch(jt + NT + tid);
         // UJ consecutive j share one overlap vote (more independent work per warp)
@@ -492,8 +490,8 @@ __global__ void __launch_bounds__(NT, MINB) rpy_adjoint_x2_kernel(const float4* 
             float mn;
 #pragma unroll
             for (int u = 0; u < UJ; ++u) {
-                const float4 w0 = s_t[0 * NT + jj + u], w1 = s_t[1 * NT + jj + u];
-                const float2 nx = lo2(w0), ny = hi2(w0), nz = lo2(w1);
+                const float4 w0 = s_t[0 * NT + jj + u];
+                const float2 nx = bc2(w0.x), ny = bc2(w0.y), nz = bc2(w0.z);
 #pragma unroll
                 for (int pp = 0; pp < NP; ++pp) {
                     dx[u][pp] = add2(xi[pp], nx);
@@ -507,9 +505,9 @@ __global__ void __launch_bounds__(NT, MINB) rpy_adjoint_x2_kernel(const float4* 
             if (__any_sync(0xffffffffu, mn < k.four_a2)) {
 #pragma unroll
                 for (int u = 0; u < UJ; ++u) {
-                    const float4 w1 = s_t[1 * NT + jj + u], w2 = s_t[2 * NT + jj + u];
-                    const float4 w3 = s_t[3 * NT + jj + u], w4 = s_t[4 * NT + jj + u];
-                    const float4 Fj = make_float4(w1.z, w2.x, w2.z, 0.f), Gj = make_float4(w3.x, w3.z, w4.x, 0.f);
+                    const float4 w0 = s_t[0 * NT + jj + u], w1 = s_t[1 * NT + jj + u];
+                    const float4 w2 = s_t[2 * NT + jj + u];
+                    const float4 Fj = make_float4(w0.w, w1.x, w1.y, 0.f), Gj = make_float4(w1.z, w1.w, w2.x, 0.f);
 #pragma unroll
                     for (int pp = 0; pp < NP; ++pp) {
 #pragma unroll
@@ -547,10 +545,10 @@ __global__ void __launch_bounds__(NT, MINB) rpy_adjoint_x2_kernel(const float4* 
             } else {
 #pragma unroll
                 for (int u = 0; u < UJ; ++u) {
-                    const float4 w1 = s_t[1 * NT + jj + u], w2 = s_t[2 * NT + jj + u];
-                    const float4 w3 = s_t[3 * NT + jj + u], w4 = s_t[4 * NT + jj + u];
-                    const float2 Fx = hi2(w1), Fy = lo2(w2), Fz = hi2(w2);
-                    const float2 Gx = lo2(w3), Gy = hi2(w3), Gz = lo2(w4);
+                    const float4 w0 = s_t[0 * NT + jj + u], w1 = s_t[1 * NT + jj + u];
+                    const float4 w2 = s_t[2 * NT + jj + u];
+                    const float2 Fx = bc2(w0.w), Fy = bc2(w1.x), Fz = bc2(w1.y);
+                    const float2 Gx = bc2(w1.z), Gy = bc2(w1.w), Gz = bc2(w2.x);
 #pragma unroll
                     for (int pp = 0; pp < NP; ++pp) {
                         const float2 ddx = dx[u][pp], ddy = dy[u][pp], ddz = dz[u][pp];

@@ -185,16 +185,21 @@ __global__ void __launch_bounds__(NT) rpy_mdot_kernel(const typename V4<R>::type
 // instruction: the far-field pair costs 21 (translation) / 46 (all blocks)
 // packed instructions per two pairs, plus one scalar rsqrt per pair.
 //
-// Packed operands carry no negation, so the j-tile holds every value a pair
-// needs, already duplicated into both halves of a float2 (shared-memory
-// broadcast loads land them in register pairs):
-//   slot  0.. 2  -x_j                       (d = x_i + (-x_j))
-//   slot  3.. 5  F_j
-//   slot  6.. 8  -F_j                       (F x d without negation)
-//   slot  9..11  T_j,  12..14  -T_j         (T x d)
-//   slot 15..17  -T_j / 2                   (the -T/2 term of w)
-//   slot 18..20  3 T_j / 2                  (d.T term of w: t = (d.(3T/2)) / r^5)
-// Translation-only solvers use slots 0..5.  Far field (r >= 2a), per pair:
+// Packed operands carry no negation, so the j-tile holds every signed and
+// scaled value a pair needs, as plain scalars (21 per j, 6 float4 words):
+//   word 0  (-x_j, -y_j, -z_j, Fx)          (d = x_i + (-x_j))
+//   word 1  (Fy, Fz, -Fx, -Fy)              (F x d without negation)
+//   word 2  (-Fz, Tx, Ty, Tz)
+//   word 3  (-Tx, -Ty, -Tz, -Tx/2)          (T x d; the -T/2 term of w)
+//   word 4  (-Ty/2, -Tz/2, 3Tx/2, 3Ty/2)    (d.T term of w: t = (d.(3T/2)) / r^5)
+//   word 5  (3Tz/2, 0, 0, 0)
+// A j-value enters a packed instruction as the same scalar in both lanes
+// (make_float2(v, v)); the compiler feeds it to both halves without a
+// duplicated register pair.  On GB300 this beat a tile of pre-duplicated
+// float2 values (11 words per j) by 2-5% at equal results: half the shared
+// loads and fewer register operands per packed instruction, which is what
+// bounds packed FMA streams there (lm_fp32_probe).
+// Translation-only solvers use words 0..1.  Far field (r >= 2a), per pair:
 //   u += A F + B (d.F) d + (T x d) / r^3
 //   w += (F x d - T/2) / r^3 + (3/2) (d.T) d / r^5
 // The exact branch (some pair of the warp at r < 2a) unpacks the two lanes
@@ -203,7 +208,7 @@ __global__ void __launch_bounds__(NT) rpy_mdot_kernel(const typename V4<R>::type
 
 // float4 words of one j in the packed tile
 template <bool ANG>
-constexpr int x2_words() { return ANG ? 11 : 3; }
+constexpr int x2_words() { return ANG ? 6 : 2; }
 
 template <bool ANG, int NT, int NI>
 constexpr size_t x2_smem_bytes() {
@@ -279,19 +284,15 @@ __device__ __forceinline__ void x2_segment(const float4* __restrict__ pos4, cons
     fetch(jb + tid);
 
     for (int64_t jt = jb; jt < je; jt += NT) {
-        // expand this thread's j into the broadcast slots
-        s_t[0 * NT + tid] = make_float4(-np.x, -np.x, -np.y, -np.y);
-        s_t[1 * NT + tid] = make_float4(-np.z, -np.z, nf.x, nf.x);
-        s_t[2 * NT + tid] = make_float4(nf.y, nf.y, nf.z, nf.z);
+        // scalar tile words: (-x,-y,-z,Fx) (Fy,Fz,-Fx,-Fy) (-Fz,Tx,Ty,Tz) (-Tx,-Ty,-Tz,-Tx/2)
+        //                    (-Ty/2,-Tz/2,1.5Tx,1.5Ty) (1.5Tz,0,0,0)
+        s_t[0 * NT + tid] = make_float4(-np.x, -np.y, -np.z, nf.x);
+        s_t[1 * NT + tid] = make_float4(nf.y, nf.z, -nf.x, -nf.y);
         if constexpr (ANG) {
-            s_t[3 * NT + tid] = make_float4(-nf.x, -nf.x, -nf.y, -nf.y);
-            s_t[4 * NT + tid] = make_float4(-nf.z, -nf.z, nt.x, nt.x);
-            s_t[5 * NT + tid] = make_float4(nt.y, nt.y, nt.z, nt.z);
-            s_t[6 * NT + tid] = make_float4(-nt.x, -nt.x, -nt.y, -nt.y);
-            s_t[7 * NT + tid] = make_float4(-nt.z, -nt.z, -0.5f * nt.x, -0.5f * nt.x);
-            s_t[8 * NT + tid] = make_float4(-0.5f * nt.y, -0.5f * nt.y, -0.5f * nt.z, -0.5f * nt.z);
-            s_t[9 * NT + tid] = make_float4(1.5f * nt.x, 1.5f * nt.x, 1.5f * nt.y, 1.5f * nt.y);
-            s_t[10 * NT + tid] = make_float4(1.5f * nt.z, 1.5f * nt.z, 0.f, 0.f);
+            s_t[2 * NT + tid] = make_float4(-nf.z, nt.x, nt.y, nt.z);
+            s_t[3 * NT + tid] = make_float4(-nt.x, -nt.y, -nt.z, -0.5f * nt.x);
+            s_t[4 * NT + tid] = make_float4(-0.5f * nt.y, -0.5f * nt.z, 1.5f * nt.x, 1.5f * nt.y);
+            s_t[5 * NT + tid] = make_float4(1.5f * nt.z, 0.f, 0.f, 0.f);
         }
         __syncthreads();
         if (jt + NT < je) fetch(jt + NT + tid);
@@ -305,8 +306,7 @@ __device__ __forceinline__ void x2_segment(const float4* __restrict__ pos4, cons
 #pragma unroll
             for (int u = 0; u < UJ; ++u) {
                 const float4 w0 = s_t[0 * NT + jj + u];
-                const float4 w1 = s_t[1 * NT + jj + u];
-                const float2 nx = lo2(w0), ny = hi2(w0), nz = lo2(w1);
+                const float2 nx = bc2(w0.x), ny = bc2(w0.y), nz = bc2(w0.z);
 #pragma unroll
                 for (int p = 0; p < NP; ++p) {
                     dx[u][p] = add2(xi[p], nx);
@@ -319,9 +319,9 @@ __device__ __forceinline__ void x2_segment(const float4* __restrict__ pos4, cons
             }
             // far-field pair of slot (u, p): two i-particles against j = jj + u
             auto far_slot = [&](int u, int p) {
+                const float4 w0 = s_t[0 * NT + jj + u];
                 const float4 w1 = s_t[1 * NT + jj + u];
-                const float4 w2 = s_t[2 * NT + jj + u];
-                const float2 fx = hi2(w1), fy = lo2(w2), fz = hi2(w2);
+                const float2 fx = bc2(w0.w), fy = bc2(w1.x), fz = bc2(w1.y);
                 const float2 ddx = dx[u][p], ddy = dy[u][p], ddz = dz[u][p];
                 const float2 invr = make_float2(rsqrtf(r2[u][p].x), rsqrtf(r2[u][p].y));
                 const float2 invr2 = mul2(invr, invr);
@@ -335,19 +335,15 @@ __device__ __forceinline__ void x2_segment(const float4* __restrict__ pos4, cons
                 acc[p][1] = fma2(sB, ddy, fma2(A, fy, acc[p][1]));
                 acc[p][2] = fma2(sB, ddz, fma2(A, fz, acc[p][2]));
                 if constexpr (ANG) {
+                    const float4 w2 = s_t[2 * NT + jj + u];
                     const float4 w3 = s_t[3 * NT + jj + u];
                     const float4 w4 = s_t[4 * NT + jj + u];
                     const float4 w5 = s_t[5 * NT + jj + u];
-                    const float4 w6 = s_t[6 * NT + jj + u];
-                    const float4 w7 = s_t[7 * NT + jj + u];
-                    const float4 w8 = s_t[8 * NT + jj + u];
-                    const float4 w9 = s_t[9 * NT + jj + u];
-                    const float4 w10 = s_t[10 * NT + jj + u];
-                    const float2 mfx = lo2(w3), mfy = hi2(w3), mfz = lo2(w4);
-                    const float2 Tx = hi2(w4), Ty = lo2(w5), Tz = hi2(w5);
-                    const float2 mTx = lo2(w6), mTy = hi2(w6), mTz = lo2(w7);
-                    const float2 hx = hi2(w7), hy = lo2(w8), hz = hi2(w8);
-                    const float2 gx = lo2(w9), gy = hi2(w9), gz = lo2(w10);
+                    const float2 mfx = bc2(w1.z), mfy = bc2(w1.w), mfz = bc2(w2.x);
+                    const float2 Tx = bc2(w2.y), Ty = bc2(w2.z), Tz = bc2(w2.w);
+                    const float2 mTx = bc2(w3.x), mTy = bc2(w3.y), mTz = bc2(w3.z);
+                    const float2 hx = bc2(w3.w), hy = bc2(w4.x), hz = bc2(w4.y);
+                    const float2 gx = bc2(w4.z), gy = bc2(w4.w), gz = bc2(w5.x);
                     // u += (T x d) / r^3
                     const float2 cx = fma2(Ty, ddz, mul2(mTz, ddy));
                     const float2 cy = fma2(Tz, ddx, mul2(mTx, ddz));
@@ -374,14 +370,14 @@ __device__ __forceinline__ void x2_segment(const float4* __restrict__ pos4, cons
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
                         if (__any_sync(0xffffffffu, fminf(r2[u][p].x, r2[u][p].y) < k.four_a2)) {
+                            const float4 w0 = s_t[0 * NT + jj + u];
                             const float4 w1 = s_t[1 * NT + jj + u];
-                            const float4 w2 = s_t[2 * NT + jj + u];
-                            const float4 fj = make_float4(w1.z, w2.x, w2.z, 0.f);
+                            const float4 fj = make_float4(w0.w, w1.x, w1.y, 0.f);
                             float4 hj = make_float4(0.f, 0.f, 0.f, 0.f);
                             if constexpr (ANG) {
-                                const float4 w7 = s_t[7 * NT + jj + u];
-                                const float4 w8 = s_t[8 * NT + jj + u];
-                                hj = make_float4(w7.z, w8.x, w8.z, 0.f);
+                                const float4 w3 = s_t[3 * NT + jj + u];
+                                const float4 w4 = s_t[4 * NT + jj + u];
+                                hj = make_float4(w3.w, w4.x, w4.y, 0.f);
                             }
                             Acc<float, ANG> t0, t1;
 #pragma unroll

@@ -226,14 +226,16 @@ __global__ void __launch_bounds__(NT) rpy_wall_kernel(const typename V4<R>::type
 
 // ---------------------------------------------------------------------------
 // Packed FP32 form of the wall kernel: two i-particles per f32x2
-// instruction, as the packed open kernel.  The j-tile holds every operand
-// pre-broadcast into both halves of a float2 (packed operands carry no
-// negation): -x_j, f F_j, f T_j, their negatives, -f T_j / 2, 3 f T_j / 2 and
-// +z_j (the image height).  The wall part below is the formula of wall_pair
-// with every sign folded into a constant or a tile slot.
+// instruction, as the packed open kernel.  The j-tile holds every operand as
+// a plain scalar that enters packed instructions in both lanes (packed
+// operands carry no negation): -x_j, f F_j, f T_j, their negatives,
+// -f T_j / 2, 3 f T_j / 2 and +z_j (the image height), in the word layout of
+// the open kernel with z_j after 3 f Tz / 2 (translation only: (-x, -y, -z,
+// f Fx) (f Fy, f Fz, z_j, 0)).  The wall part below is the formula of
+// wall_pair with every sign folded into a constant or a tile slot.
 // ---------------------------------------------------------------------------
 template <bool ANG>
-constexpr int wall_x2_words() { return ANG ? 11 : 4; }
+constexpr int wall_x2_words() { return ANG ? 6 : 2; }
 
 template <bool ANG, int NT, int NI>
 constexpr size_t wall_x2_smem_bytes() {
@@ -390,20 +392,15 @@ __global__ void __launch_bounds__(NT) rpy_wall_x2_kernel(const float4* __restric
     fetch(jb + tid);
 
     for (int64_t jt = jb; jt < je; jt += NT) {
-        s_t[0 * NT + tid] = make_float4(-np.x, -np.x, -np.y, -np.y);
-        s_t[1 * NT + tid] = make_float4(-np.z, -np.z, nf.x, nf.x);
-        s_t[2 * NT + tid] = make_float4(nf.y, nf.y, nf.z, nf.z);
+        s_t[0 * NT + tid] = make_float4(-np.x, -np.y, -np.z, nf.x);
         if constexpr (ANG) {
-            s_t[3 * NT + tid] = make_float4(-nf.x, -nf.x, -nf.y, -nf.y);
-            s_t[4 * NT + tid] = make_float4(-nf.z, -nf.z, nt.x, nt.x);
-            s_t[5 * NT + tid] = make_float4(nt.y, nt.y, nt.z, nt.z);
-            s_t[6 * NT + tid] = make_float4(-nt.x, -nt.x, -nt.y, -nt.y);
-            s_t[7 * NT + tid] = make_float4(-nt.z, -nt.z, -0.5f * nt.x, -0.5f * nt.x);
-            s_t[8 * NT + tid] = make_float4(-0.5f * nt.y, -0.5f * nt.y, -0.5f * nt.z, -0.5f * nt.z);
-            s_t[9 * NT + tid] = make_float4(1.5f * nt.x, 1.5f * nt.x, 1.5f * nt.y, 1.5f * nt.y);
-            s_t[10 * NT + tid] = make_float4(1.5f * nt.z, 1.5f * nt.z, np.z, np.z);
+            s_t[1 * NT + tid] = make_float4(nf.y, nf.z, -nf.x, -nf.y);
+            s_t[2 * NT + tid] = make_float4(-nf.z, nt.x, nt.y, nt.z);
+            s_t[3 * NT + tid] = make_float4(-nt.x, -nt.y, -nt.z, -0.5f * nt.x);
+            s_t[4 * NT + tid] = make_float4(-0.5f * nt.y, -0.5f * nt.z, 1.5f * nt.x, 1.5f * nt.y);
+            s_t[5 * NT + tid] = make_float4(1.5f * nt.z, np.z, 0.f, 0.f);
         } else {
-            s_t[3 * NT + tid] = make_float4(-nf.x, -nf.x, np.z, np.z);
+            s_t[1 * NT + tid] = make_float4(nf.y, nf.z, np.z, 0.f);
         }
         __syncthreads();
         if (jt + NT < je) fetch(jt + NT + tid);
@@ -412,28 +409,22 @@ __global__ void __launch_bounds__(NT) rpy_wall_x2_kernel(const float4* __restric
         for (int jj = 0; jj < NT; ++jj) {
             const float4 w0 = s_t[0 * NT + jj];
             const float4 w1 = s_t[1 * NT + jj];
-            const float4 w2 = s_t[2 * NT + jj];
-            const float2 nx = lo2(w0), ny = hi2(w0), nz = lo2(w1);
-            const float2 fx = hi2(w1), fy = lo2(w2), fz = hi2(w2);
+            const float2 nx = bc2(w0.x), ny = bc2(w0.y), nz = bc2(w0.z);
+            const float2 fx = bc2(w0.w), fy = bc2(w1.x), fz = bc2(w1.y);
             float2 mfx, mfy, mfz, Tx, Ty, Tz, mTx, mTy, mTz, hx, hy, hz, gx, gy, gz, zj;
             if constexpr (ANG) {
+                const float4 w2 = s_t[2 * NT + jj];
                 const float4 w3 = s_t[3 * NT + jj];
                 const float4 w4 = s_t[4 * NT + jj];
                 const float4 w5 = s_t[5 * NT + jj];
-                const float4 w6 = s_t[6 * NT + jj];
-                const float4 w7 = s_t[7 * NT + jj];
-                const float4 w8 = s_t[8 * NT + jj];
-                const float4 w9 = s_t[9 * NT + jj];
-                const float4 w10 = s_t[10 * NT + jj];
-                mfx = lo2(w3); mfy = hi2(w3); mfz = lo2(w4);
-                Tx = hi2(w4); Ty = lo2(w5); Tz = hi2(w5);
-                mTx = lo2(w6); mTy = hi2(w6); mTz = lo2(w7);
-                hx = hi2(w7); hy = lo2(w8); hz = hi2(w8);
-                gx = lo2(w9); gy = hi2(w9); gz = lo2(w10);
-                zj = hi2(w10);
+                mfx = bc2(w1.z); mfy = bc2(w1.w); mfz = bc2(w2.x);
+                Tx = bc2(w2.y); Ty = bc2(w2.z); Tz = bc2(w2.w);
+                mTx = bc2(w3.x); mTy = bc2(w3.y); mTz = bc2(w3.z);
+                hx = bc2(w3.w); hy = bc2(w4.x); hz = bc2(w4.y);
+                gx = bc2(w4.z); gy = bc2(w4.w); gz = bc2(w5.x);
+                zj = bc2(w5.y);
             } else {
-                const float4 w3 = s_t[3 * NT + jj];
-                zj = hi2(w3);
+                zj = bc2(w1.z);
                 mfx = mfy = mfz = Tx = Ty = Tz = mTx = mTy = mTz = bc2(0.f);
             }
             float2 dx[NP], dy[NP], dz[NP], r2[NP];
