@@ -572,6 +572,39 @@ lm_status lm_mdot_noalloc(const float *pos, const float *forces, const float *to
  */
 lm_status lm_fp32_probe(int mode, int64_t iters, double *tflops, void *cuda_stream);
 
+/*
+ * Debug bounds checks (no paper counterpart; the stand-in for a memory
+ * sanitizer).  A build with -DLM_DEBUG_BOUNDS checks the indices of the
+ * kernels' main loads and stores against their buffers (j < N in every pair
+ * tile, partial-sum and output indices, basis rows < m in the Lanczos
+ * passes, particle indices < N_total in the batched kernel).  A failed check
+ * records its code and index in a device word, the first failure wins, and
+ * the access is skipped: a check never faults the GPU.
+ * lm_debug_bounds returns 1 for such a build, else 0.
+ * lm_debug_check synchronises the current device, reads and clears every
+ * check word and returns LM_OK if no check failed, LM_ERR_CUDA with the check
+ * and index in lm_last_error otherwise.  In other builds it returns LM_OK
+ * without touching the GPU.
+ */
+int lm_debug_bounds(void);
+lm_status lm_debug_check(void);
+
+/*
+ * Environment switches read by the library (no paper counterpart):
+ *   LM_METRICS_JSONL=<path>  lm_mdot, lm_sqrt_mdot, lm_mdot_backward and the
+ *     batch calls synchronise their stream at the end and append one JSON
+ *     object per call to <path>: call, status, milliseconds, N, precision,
+ *     blocks, geometry, products, pair interactions, flops per pair,
+ *     iterations and relative change (square roots), GPU name, SM count and
+ *     its nominal FP32 peak.  Every call records an NVTX range either way.
+ *   LM_AUTOTUNE_CACHE=<path>  lm_autotune appends its choice to <path> (JSON
+ *     lines keyed by GPU name, SM count, precision, angular flag, geometry and
+ *     floor(log2 N)); a solver without a configuration of its own starts from
+ *     the last entry for its key, in this or a later process.
+ *   LM_AUTOTUNE=1  such a solver with no recorded entry runs lm_autotune the
+ *     first time it needs a configuration at a new N bucket.
+ */
+
 /* Thread-local message for the last non-OK status ("" if none). */
 const char *lm_last_error(void);
 

@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(NT, MINB) rpy_adjoint_x2_kernel(const float4* 
     float4 np;
     float3 nF, nG;
     auto fetch = [&](int64_t j) {
-        if (j < je) {
+        if (j < je && LM_INBOUNDS(j >= 0 && j < N, 8, j)) {
             np = pos4[j];
             nF = make_float3(ld<float>(Fp, f64, 3 * j), ld<float>(Fp, f64, 3 * j + 1), ld<float>(Fp, f64, 3 * j + 2));
             nG = make_float3(ld<float>(Gp, f64, 3 * j), ld<float>(Gp, f64, 3 * j + 1), ld<float>(Gp, f64, 3 * j + 2));

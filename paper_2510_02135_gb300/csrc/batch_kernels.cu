@@ -165,7 +165,7 @@ __device__ void pair_item(const BatchParams& P, int s, int i0, int jb, int je, c
     // that the global-load latency hides behind the current tile's pairs
     float nj[NRHS == 2 ? 9 : 6];
     auto fetch = [&](int j) {
-        if (j < je) {
+        if (j < je && LM_INBOUNDS(o + j >= 0 && o + j < P.Ntot, 9, o + j)) {
             const float4 pj = P.pos4[o + j];
             nj[0] = pj.x; nj[1] = pj.y; nj[2] = pj.z;
             if (srcA_f) {

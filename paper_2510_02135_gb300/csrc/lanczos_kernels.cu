@@ -81,7 +81,7 @@ __device__ __forceinline__ double basis_combination(const double* __restrict__ V
         __syncthreads();
         if (threadIdx.x < mm) csh[threadIdx.x] = c[j0 + threadIdx.x];
         __syncthreads();
-        if (e >= n) continue;
+        if (e >= n || !LM_INBOUNDS(j0 + mm <= m, 11, j0 + mm)) continue;
         const double* __restrict__ v = V + (int64_t)j0 * n + e;
         int j = 0;
         for (; j + 8 <= mm; j += 8) {
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kMdThreads) multidot_rows(const double* __rest
             const double* __restrict__ v = V + (int64_t)j0 * n + e;
 #pragma unroll
             for (int r = 0; r < kMdRows; ++r)
-                if (r < rows) acc[r] = fma(v[(int64_t)r * n], we, acc[r]);
+                if (r < rows && LM_INBOUNDS(j0 + r < m, 10, j0 + r)) acc[r] = fma(v[(int64_t)r * n], we, acc[r]);
         }
     }
     // transposing butterfly: after the offsets 16, 8 and 4 lane l holds the

@@ -7,6 +7,7 @@
 #include <numeric>
 #include <array>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -19,6 +20,7 @@
 
 #include "../../include/lm.h"
 #include "lm_internal.cuh"
+#include "lm_runtime.cuh"
 #include "tridiag.cuh"
 
 namespace {
@@ -368,20 +370,47 @@ std::array<int, 5> tuned_key(const lm_solver* s, int64_t N) {
     return {s->device, s->fp64 ? 1 : 0, s->angular ? 1 : 0, s->wall ? 1 : 0, b};
 }
 
+// The process's record, else the persistent cache (LM_AUTOTUNE_CACHE).
 bool lookup_tuned(const lm_solver* s, int64_t N, TunedEntry* e) {
+    const std::array<int, 5> key = tuned_key(s, N);
+    {
+        std::lock_guard<std::mutex> lk(g_tuned_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            *e = it->second;
+            return true;
+        }
+    }
+    lmk::TuneCacheKey ck;
+    long long n = 0;
+    bool has_adj = false;
+    if (!lmk::tune_cache_key(s->device, key[1], key[2], key[3], key[4], &ck) ||
+        !lmk::tune_cache_lookup(ck, &n, &e->cfg, &e->adj, &has_adj))
+        return false;
+    if (!pair_config_supported(s, e->cfg.threads, e->cfg.ilp, e->cfg.packed) || e->cfg.splits < 1) return false;
+    e->N = n;
+    e->has_adj = has_adj && lmk::adjoint_config_supported(s->fp64, s->angular, e->adj.threads, e->adj.ilp,
+                                                          e->adj.packed);
     std::lock_guard<std::mutex> lk(g_tuned_mu);
-    auto it = g_tuned.find(tuned_key(s, N));
-    if (it == g_tuned.end()) return false;
-    *e = it->second;
+    g_tuned[key] = *e;
     return true;
 }
+
+lm_status autotune_impl(lm_solver* s, int reps, lm_pair_config* best);
 
 void ensure_config(lm_solver* s) {
     if (s->cfg_N == s->N) return;
     if (!s->cfg_forced) {
         s->cfg = default_config(s, s->N);
         TunedEntry e;
-        if (lookup_tuned(s, s->N, &e)) {
+        bool found = lookup_tuned(s, s->N, &e);
+        if (!found && lmk::autotune_on_first_use()) {
+            // LM_AUTOTUNE=1: tune this N bucket now (recorded for the process and
+            // in the persistent cache); on failure keep the model's choice
+            lm_pair_config best;
+            if (autotune_impl(s, 2, &best) == LM_OK) return;
+        }
+        if (found) {
             s->cfg = e.cfg;
             if (e.N != s->N) {
                 const int occ = std::max(1, pair_ctas_per_sm(s, e.cfg.threads, e.cfg.ilp, e.cfg.packed));
@@ -548,6 +577,51 @@ lm_status rfd_sample(lm_solver* s, uint64_t seed, double delta, void* lin, void*
 }
 }  // namespace
 
+namespace {
+// One ABI call: an NVTX range for its duration and, with LM_METRICS_JSONL
+// set, one JSON line written after the call's stream has been synchronised
+// (the metrics mode makes every logged call synchronous).
+struct CallScope {
+    lmk::TraceRange range;
+    const char* name;
+    std::chrono::steady_clock::time_point t0;
+    explicit CallScope(const char* n) : range(n), name(n), t0(std::chrono::steady_clock::now()) {}
+};
+
+lm_status log_call(const CallScope& c, cudaStream_t stream, int device, lm_status st, const char* fields) {
+    if (!lmk::metrics_enabled()) return st;
+    {
+        DeviceGuard g(device);
+        cudaStreamSynchronize(stream);
+    }
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - c.t0).count();
+    char buf[1024];
+    std::snprintf(buf, sizeof(buf), "\"call\":\"%s\",\"status\":%d,\"ms\":%.6f,%s,%s", c.name, (int)st, ms, fields,
+                  lmk::metrics_device_fields(device).c_str());
+    lmk::metrics_write(buf);
+    return st;
+}
+
+double solver_flops_per_pair(const lm_solver* s) {
+    return s->wall ? (s->angular ? lmk::kFlopsPerPairWall6N : lmk::kFlopsPerPairWallTT)
+                   : (s->angular ? lmk::kFlopsPerPair6N : lmk::kFlopsPerPairTT);
+}
+
+// Fields of a solver call: N, precision, blocks, geometry and the pair
+// interactions of its products (N^2 per product); extra starts with a comma.
+lm_status log_solver_call(const CallScope& c, lm_solver* s, lm_status st, double products, double flops_per_pair,
+                          const char* extra = "") {
+    if (!lmk::metrics_enabled() || s == nullptr) return st;
+    char buf[512];
+    std::snprintf(buf, sizeof(buf),
+                  "\"N\":%lld,\"precision\":\"%s\",\"angular\":%d,\"geometry\":\"%s\",\"products\":%.0f,"
+                  "\"pair_interactions\":%.6e,\"flops_per_pair\":%.0f%s",
+                  (long long)s->N, s->fp64 ? "fp64" : "fp32c", s->angular, s->wall ? "single_wall" : "open", products,
+                  products * (double)s->N * (double)s->N, flops_per_pair, extra);
+    return log_call(c, s->stream, s->device, st, buf);
+}
+}  // namespace
+
 extern "C" {
 
 const char* lm_last_error(void) { return g_err.c_str(); }
@@ -561,6 +635,7 @@ int64_t lm_launch_count(lm_solver* solver) {
 
 lm_status lm_create(lm_solver** out, const char* px, const char* py, const char* pz, double viscosity,
                     double hydrodynamic_radius, int include_angular, lm_precision precision, void* cuda_stream) {
+    lmk::TraceRange trace_("lm_create");
     g_err.clear();
     if (out == nullptr) return fail(LM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -598,6 +673,7 @@ lm_status lm_create(lm_solver** out, const char* px, const char* py, const char*
 }
 
 lm_status lm_destroy(lm_solver* solver) {
+    lmk::TraceRange trace_("lm_destroy");
     if (solver == nullptr) return LM_OK;
     DeviceGuard g(solver->device);
     cudaStreamSynchronize(solver->stream);
@@ -612,6 +688,7 @@ lm_status lm_set_stream(lm_solver* solver, void* cuda_stream) {
 }
 
 lm_status lm_set_positions(lm_solver* s, const void* pos, int64_t N) {
+    lmk::TraceRange trace_("lm_set_positions");
     if (lm_status st = check_solver(s, false)) return st;
     if (pos == nullptr) return fail(LM_ERR_INVALID_ARG, "pos is NULL");
     if (N < 1) return fail(LM_ERR_INVALID_ARG, "N must be >= 1 (got %lld)", (long long)N);
@@ -644,7 +721,7 @@ lm_status lm_set_positions(lm_solver* s, const void* pos, int64_t N) {
     return LM_OK;
 }
 
-lm_status lm_mdot(lm_solver* s, const void* forces, const void* torques, void* lin_out, void* ang_out) {
+static lm_status mdot_body(lm_solver* s, const void* forces, const void* torques, void* lin_out, void* ang_out) {
     if (lm_status st = check_solver(s, true)) return st;
     if (lin_out == nullptr) return fail(LM_ERR_INVALID_ARG, "lin_out is NULL");
     if (s->angular && ang_out == nullptr) return fail(LM_ERR_INVALID_ARG, "ang_out is required with angular blocks");
@@ -667,8 +744,14 @@ lm_status lm_mdot(lm_solver* s, const void* forces, const void* torques, void* l
     }
     return finish_out(s, ov, 2);
 }
+lm_status lm_mdot(lm_solver* s, const void* forces, const void* torques, void* lin_out, void* ang_out) {
+    CallScope cs("lm_mdot");
+    const lm_status st = mdot_body(s, forces, torques, lin_out, ang_out);
+    return log_solver_call(cs, s, st, (forces || torques) ? 1.0 : 0.0, s ? solver_flops_per_pair(s) : 0.0);
+}
 
 lm_status lm_div_m_rfd(lm_solver* s, uint64_t seed, double delta, void* lin_out, void* ang_out) {
+    lmk::TraceRange trace_("lm_div_m_rfd");
     if (lm_status st = check_solver(s, true)) return st;
     if (lin_out == nullptr) return fail(LM_ERR_INVALID_ARG, "lin_out is NULL");
     if (s->angular && ang_out == nullptr) return fail(LM_ERR_INVALID_ARG, "ang_out is required with angular blocks");
@@ -685,6 +768,7 @@ lm_status lm_div_m_rfd(lm_solver* s, uint64_t seed, double delta, void* lin_out,
 }
 
 lm_status lm_div_m(lm_solver* s, void* lin_out, void* ang_out) {
+    lmk::TraceRange trace_("lm_div_m");
     if (lm_status st = check_solver(s, true)) return st;
     if (lin_out == nullptr) return fail(LM_ERR_INVALID_ARG, "lin_out is NULL");
     if (s->angular && ang_out == nullptr) return fail(LM_ERR_INVALID_ARG, "ang_out is required with angular blocks");
@@ -705,6 +789,7 @@ lm_status lm_div_m(lm_solver* s, void* lin_out, void* ang_out) {
 }
 
 lm_status lm_soft_repulsion(lm_solver* s, double U0, double b, double d_pair, double d_wall, void* forces_out) {
+    lmk::TraceRange trace_("lm_soft_repulsion");
     if (lm_status st = check_solver(s, true)) return st;
     if (forces_out == nullptr) return fail(LM_ERR_INVALID_ARG, "forces_out is NULL");
     if (!std::isfinite(U0) || !(b > 0.0) || !std::isfinite(b) || !std::isfinite(d_pair) || !std::isfinite(d_wall))
@@ -738,6 +823,7 @@ lm_status lm_set_wall_height(lm_solver* s, double height) {
 lm_status lm_langevin_velocities(lm_solver* s, const void* forces, const void* torques, const double* W,
                                  uint64_t seed, double kT, double dt, double tol, int max_iter, void* lin_out,
                                  void* ang_out, int* iters_out) {
+    lmk::TraceRange trace_("lm_langevin_velocities");
     if (lm_status st = check_solver(s, true)) return st;
     if (lin_out == nullptr) return fail(LM_ERR_INVALID_ARG, "lin_out is NULL");
     if (s->angular && ang_out == nullptr) return fail(LM_ERR_INVALID_ARG, "ang_out is required with angular blocks");
@@ -791,6 +877,7 @@ lm_status lm_langevin_velocities(lm_solver* s, const void* forces, const void* t
 lm_status lm_ab_step(lm_solver* s, const void* forces, const void* torques, const double* W, uint64_t seed,
                      double kT, double dt, double tol, int max_iter, double* history, int first, void* pos_out,
                      int* iters_out) {
+    lmk::TraceRange trace_("lm_ab_step");
     if (lm_status st = check_solver(s, true)) return st;
     if (pos_out == nullptr) return fail(LM_ERR_INVALID_ARG, "pos_out is NULL");
     if (history == nullptr || !is_device_ptr(history))
@@ -944,7 +1031,7 @@ void settle_vector_profile(lm_solver* s, int64_t n) {
 
 }  // namespace
 
-lm_status lm_sqrt_mdot(lm_solver* s, const double* W, uint64_t seed, double prefactor, double tol, int max_iter,
+static lm_status sqrt_mdot_body(lm_solver* s, const double* W, uint64_t seed, double prefactor, double tol, int max_iter,
                        void* lin_out, void* ang_out, int* iters_out) {
     if (lm_status st = check_solver(s, true)) return st;
     if (lin_out == nullptr) return fail(LM_ERR_INVALID_ARG, "lin_out is NULL");
@@ -1111,6 +1198,18 @@ lm_status lm_sqrt_mdot(lm_solver* s, const double* W, uint64_t seed, double pref
                     m, rel);
     return LM_OK;
 }
+lm_status lm_sqrt_mdot(lm_solver* s, const double* W, uint64_t seed, double prefactor, double tol, int max_iter,
+                       void* lin_out, void* ang_out, int* iters_out) {
+    CallScope cs("lm_sqrt_mdot");
+    int it = 0;
+    const lm_status st = sqrt_mdot_body(s, W, seed, prefactor, tol, max_iter, lin_out, ang_out, &it);
+    if (iters_out) *iters_out = it;
+    if (!lmk::metrics_enabled() || s == nullptr) return st;
+    char extra[160];
+    std::snprintf(extra, sizeof(extra), ",\"iterations\":%d,\"tol\":%.3e,\"rel_change\":%.6e,\"converged\":%d", it,
+                  tol, s->stats.rel_change, s->stats.converged);
+    return log_solver_call(cs, s, st, (double)it, solver_flops_per_pair(s), extra);
+}
 
 lm_status lm_get_lanczos_stats(lm_solver* s, lm_lanczos_stats* stats) {
     if (lm_status st = check_solver(s, false)) return st;
@@ -1119,7 +1218,7 @@ lm_status lm_get_lanczos_stats(lm_solver* s, lm_lanczos_stats* stats) {
     return LM_OK;
 }
 
-lm_status lm_mdot_backward(lm_solver* s, const void* forces, const void* torques, const void* grad_lin,
+static lm_status mdot_backward_body(lm_solver* s, const void* forces, const void* torques, const void* grad_lin,
                            const void* grad_ang, void* dX, void* dF, void* dT) {
     if (lm_status st = check_solver(s, true)) return st;
     if (s->wall)
@@ -1142,6 +1241,13 @@ lm_status lm_mdot_backward(lm_solver* s, const void* forces, const void* torques
     ensure_adjoint_config(s);
     if (lm_status st = run_adjoint(s, pF, pT, pG, pH, ov[0].dev, ov[1].dev, ov[2].dev, s->adj_cfg)) return st;
     return finish_out(s, ov, 3);
+}
+
+lm_status lm_mdot_backward(lm_solver* s, const void* forces, const void* torques, const void* grad_lin,
+                           const void* grad_ang, void* dX, void* dF, void* dT) {
+    CallScope cs("lm_mdot_backward");
+    const lm_status st = mdot_backward_body(s, forces, torques, grad_lin, grad_ang, dX, dF, dT);
+    return log_solver_call(cs, s, st, 1.0, 0.0, ",\"note\":\"fused dL/dX and dL/dF pass\"");
 }
 
 lm_status lm_set_sqrt_preconditioner(lm_solver* s, int kind) {
@@ -1207,7 +1313,10 @@ lm_status lm_set_pair_config(lm_solver* s, const lm_pair_config* cfg) {
     return LM_OK;
 }
 
-lm_status lm_autotune(lm_solver* s, int reps, lm_pair_config* best) {
+}  // extern "C"
+
+namespace {
+lm_status autotune_impl(lm_solver* s, int reps, lm_pair_config* best) {
     if (lm_status st = check_solver(s, true)) return st;
     if (reps < 1) return fail(LM_ERR_INVALID_ARG, "reps must be >= 1");
     DeviceGuard g(s->device);
@@ -1329,11 +1438,25 @@ lm_status lm_autotune(lm_solver* s, int reps, lm_pair_config* best) {
         e.N = N;
         e.has_adj = (s->adj_cfg_N == N) && !s->fp64 && !s->angular && !s->wall;
         if (e.has_adj) e.adj = s->adj_cfg;
-        std::lock_guard<std::mutex> lk(g_tuned_mu);
-        g_tuned[tuned_key(s, N)] = e;
+        const std::array<int, 5> key = tuned_key(s, N);
+        {
+            std::lock_guard<std::mutex> lk(g_tuned_mu);
+            g_tuned[key] = e;
+        }
+        lmk::TuneCacheKey ck;
+        if (lmk::tune_cache_key(s->device, key[1], key[2], key[3], key[4], &ck))
+            lmk::tune_cache_store(ck, N, best_cfg, e.has_adj ? &e.adj : nullptr);
     }
     if (best) *best = best_cfg;
     return LM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+lm_status lm_autotune(lm_solver* s, int reps, lm_pair_config* best) {
+    lmk::TraceRange tr("lm_autotune");
+    return autotune_impl(s, reps, best);
 }
 
 lm_status lm_profile_enable(lm_solver* s, int enable) {
@@ -1638,6 +1761,7 @@ extern "C" {
 
 lm_status lm_batch_create(lm_batch** out, int64_t S, const int64_t* offsets, double viscosity,
                           double hydrodynamic_radius, int max_iter, void* cuda_stream) {
+    lmk::TraceRange trace_("lm_batch_create");
     g_err.clear();
     if (!out) return fail(LM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -1737,6 +1861,7 @@ lm_status lm_batch_destroy(lm_batch* b) {
 }
 
 lm_status lm_batch_set_positions(lm_batch* b, const float* pos) {
+    lmk::TraceRange trace_("lm_batch_set_positions");
     if (lm_status st = check_batch(b, false)) return st;
     if (!pos) return fail(LM_ERR_INVALID_ARG, "pos is NULL");
     DeviceGuard g(b->device);
@@ -1771,7 +1896,7 @@ lm_status lm_batch_get_positions(lm_batch* b, float* pos_out) {
     return LM_OK;
 }
 
-lm_status lm_batch_mdot(lm_batch* b, const float* forces, float* lin_out) {
+static lm_status batch_mdot_body(lm_batch* b, const float* forces, float* lin_out) {
     if (lm_status st = check_batch(b, true)) return st;
     if (!forces || !lin_out) return fail(LM_ERR_INVALID_ARG, "forces and lin_out are required");
     DeviceGuard g(b->device);
@@ -1792,7 +1917,16 @@ lm_status lm_batch_mdot(lm_batch* b, const float* forces, float* lin_out) {
     return LM_OK;
 }
 
-lm_status lm_batch_sqrt_mdot(lm_batch* b, const double* W, uint64_t seed, double prefactor, double tol,
+lm_status lm_batch_mdot(lm_batch* b, const float* forces, float* lin_out) {
+    CallScope cs("lm_batch_mdot");
+    const lm_status st = batch_mdot_body(b, forces, lin_out);
+    if (!lmk::metrics_enabled() || b == nullptr) return st;
+    char f[128];
+    std::snprintf(f, sizeof(f), "\"systems\":%d,\"N_total\":%lld", b->S, (long long)b->Ntot);
+    return log_call(cs, b->stream, b->device, st, f);
+}
+
+static lm_status batch_sqrt_mdot_body(lm_batch* b, const double* W, uint64_t seed, double prefactor, double tol,
                              float* lin_out, int* iters_out) {
     if (lm_status st = check_batch(b, true)) return st;
     if (!lin_out) return fail(LM_ERR_INVALID_ARG, "lin_out is NULL");
@@ -1824,7 +1958,17 @@ lm_status lm_batch_sqrt_mdot(lm_batch* b, const double* W, uint64_t seed, double
     return LM_OK;
 }
 
-lm_status lm_batch_bd_run(lm_batch* b, double kT, double dt, double k_trap, int nsteps, int64_t step0,
+lm_status lm_batch_sqrt_mdot(lm_batch* b, const double* W, uint64_t seed, double prefactor, double tol,
+                             float* lin_out, int* iters_out) {
+    CallScope cs("lm_batch_sqrt_mdot");
+    const lm_status st = batch_sqrt_mdot_body(b, W, seed, prefactor, tol, lin_out, iters_out);
+    if (!lmk::metrics_enabled() || b == nullptr) return st;
+    char f[256];
+    std::snprintf(f, sizeof(f), "\"systems\":%d,\"N_total\":%lld,\"tol\":%.3e", b->S, (long long)b->Ntot, tol);
+    return log_call(cs, b->stream, b->device, st, f);
+}
+
+static lm_status batch_bd_run_body(lm_batch* b, double kT, double dt, double k_trap, int nsteps, int64_t step0,
                           uint64_t seed, double tol, int use_graph, int* iters_out) {
     if (lm_status st = check_batch(b, true)) return st;
     if (nsteps < 1 || !(kT >= 0.0) || !(dt >= 0.0) || !std::isfinite(k_trap) || !(tol >= 0.0) || step0 < 0)
@@ -1848,6 +1992,17 @@ lm_status lm_batch_bd_run(lm_batch* b, double kT, double dt, double k_trap, int 
     return LM_OK;
 }
 
+lm_status lm_batch_bd_run(lm_batch* b, double kT, double dt, double k_trap, int nsteps, int64_t step0,
+                          uint64_t seed, double tol, int use_graph, int* iters_out) {
+    CallScope cs("lm_batch_bd_run");
+    const lm_status st = batch_bd_run_body(b, kT, dt, k_trap, nsteps, step0, seed, tol, use_graph, iters_out);
+    if (!lmk::metrics_enabled() || b == nullptr) return st;
+    char f[256];
+    std::snprintf(f, sizeof(f), "\"systems\":%d,\"N_total\":%lld,\"steps\":%d,\"tol\":%.3e,\"graph\":%d", b->S,
+                  (long long)b->Ntot, nsteps, tol, use_graph);
+    return log_call(cs, b->stream, b->device, st, f);
+}
+
 lm_status lm_batch_set_reorthogonalization(lm_batch* b, int mode) {
     if (lm_status st = check_batch(b, false)) return st;
     if (mode != 0 && mode != 1) return fail(LM_ERR_INVALID_ARG, "reorthogonalization mode must be 0 (DGKS) or 1 (two passes)");
@@ -1866,6 +2021,7 @@ lm_status lm_batch_set_tiling(lm_batch* b, int threads, int ilp) {
 }
 
 lm_status lm_batch_autotune(lm_batch* b, int* threads_out, int* ilp_out) {
+    lmk::TraceRange trace_("lm_batch_autotune");
     if (lm_status st = check_batch(b, true)) return st;
     DeviceGuard g(b->device);
     const size_t bytes = (size_t)b->Ntot * 3 * sizeof(float);

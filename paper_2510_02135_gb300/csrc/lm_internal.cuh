@@ -17,6 +17,49 @@ struct __align__(32) dvec4 {
 // Kernel launches issued by the library (all solvers, all threads).
 void count_launches(int n);
 
+// ---------------------------------------------------------------------------
+// Device bounds checks (a build with -DLM_DEBUG_BOUNDS; the stand-in for a
+// memory sanitizer).  LM_INBOUNDS(cond, code, index) is true in other builds;
+// in a checked build a false condition records (code, index) in the
+// translation unit's check word (the first failure wins) and the caller skips
+// the access, so a failed check never faults the GPU.  lm_debug_check reads
+// and clears the words of every unit.
+// ---------------------------------------------------------------------------
+using BoundsReadFn = cudaError_t (*)(unsigned long long*);
+void register_bounds_reader(BoundsReadFn fn, const char* unit);
+
+}  // namespace lmk
+
+#ifdef LM_DEBUG_BOUNDS
+namespace {
+__device__ unsigned long long g_lm_bounds_word;
+
+__device__ __forceinline__ bool lm_bounds_ok(bool ok, unsigned code, long long idx) {
+    if (!ok)
+        atomicCAS(&g_lm_bounds_word, 0ull,
+                  ((unsigned long long)code << 48) | ((unsigned long long)idx & 0xffffffffffffull));
+    return ok;
+}
+
+cudaError_t lm_bounds_read_and_clear(unsigned long long* w) {
+    cudaError_t e = cudaMemcpyFromSymbol(w, g_lm_bounds_word, sizeof(*w));
+    const unsigned long long zero = 0;
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_lm_bounds_word, &zero, sizeof(zero));
+    return e;
+}
+
+struct LmBoundsRegistrar {
+    explicit LmBoundsRegistrar(const char* unit) { lmk::register_bounds_reader(&lm_bounds_read_and_clear, unit); }
+};
+const LmBoundsRegistrar g_lm_bounds_registrar(__FILE__);
+}  // namespace
+#define LM_INBOUNDS(cond, code, idx) lm_bounds_ok((cond), (unsigned)(code), (long long)(idx))
+#else
+#define LM_INBOUNDS(cond, code, idx) (true)
+#endif
+
+namespace lmk {
+
 // Raises the dynamic shared-memory limit of kernel `fn` to `bytes` on the
 // current device, once per device.  The attribute belongs to the device
 // context, so a process that drives several GPUs sets it on each of them;

@@ -151,9 +151,13 @@ __global__ void reduce_splits_kernel(const double* __restrict__ partials, int sp
     const int64_t i = e / C;
     const int c = (int)(e - i * C);
     double s = 0.0;
-    for (int k = 0; k < splits; ++k) s += partials[((int64_t)k * C + c) * N + i];
+    for (int k = 0; k < splits; ++k) {
+        const int64_t pidx = ((int64_t)k * C + c) * N + i;
+        if (LM_INBOUNDS(pidx < (int64_t)splits * C * N, 5, pidx)) s += partials[pidx];
+    }
     void* out = (c < 3) ? lin : ang;
     const int64_t idx = 3 * i + (c % 3);
+    if (!LM_INBOUNDS(idx < 3 * N, 6, idx)) return;
     if (out_f64) static_cast<double*>(out)[idx] = c8 * s;
     else static_cast<float*>(out)[idx] = (float)(c8 * s);
 }

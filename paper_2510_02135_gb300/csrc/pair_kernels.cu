@@ -76,7 +76,7 @@ __device__ __forceinline__ void scalar_segment(const typename V4<R>::type* __res
     // register prefetch of this thread's j in the first tile
     R4 np, nf, nh;
     auto fetch = [&](int64_t j) {
-        if (j < je) {
+        if (j < je && LM_INBOUNDS(j >= 0 && j < N, 1, j)) {
             np = pos4[j];
             nf.x = load_elem<R>(Fp, in_f64, 3 * j + 0);
             nf.y = load_elem<R>(Fp, in_f64, 3 * j + 1);
@@ -170,7 +170,8 @@ __global__ void __launch_bounds__(NT) rpy_mdot_kernel(const typename V4<R>::type
                 if (out_f64) static_cast<double*>(out)[idx] = c8 * v;
                 else static_cast<float*>(out)[idx] = (float)(c8 * v);
             } else {
-                partials[((int64_t)blockIdx.y * C + c) * N + i] = v;
+                const int64_t pidx = ((int64_t)blockIdx.y * C + c) * N + i;
+                if (LM_INBOUNDS(pidx < (int64_t)gridDim.y * C * N, 3, pidx)) partials[pidx] = v;
             }
         }
     }
@@ -265,7 +266,7 @@ __device__ __forceinline__ void x2_segment(const float4* __restrict__ pos4, cons
     float4 np;
     float3 nf, nt;
     auto fetch = [&](int64_t j) {
-        if (j < je) {
+        if (j < je && LM_INBOUNDS(j >= 0 && j < N, 1, j)) {
             np = pos4[j];
             nf.x = load_elem<float>(Fp, in_f64, 3 * j + 0);
             nf.y = load_elem<float>(Fp, in_f64, 3 * j + 1);
@@ -460,7 +461,8 @@ __global__ void __launch_bounds__(NT) rpy_mdot_x2_kernel(const float4* __restric
                 if (out_f64) static_cast<double*>(out)[idx] = c8 * v;
                 else static_cast<float*>(out)[idx] = (float)(c8 * v);
             } else {
-                partials[((int64_t)blockIdx.y * C + c) * N + i] = v;
+                const int64_t pidx = ((int64_t)blockIdx.y * C + c) * N + i;
+                if (LM_INBOUNDS(pidx < (int64_t)gridDim.y * C * N, 3, pidx)) partials[pidx] = v;
             }
         }
     }

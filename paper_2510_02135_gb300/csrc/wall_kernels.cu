@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(NT) rpy_wall_kernel(const typename V4<R>::type
     // register prefetch of this thread's j in the next tile: position, f F, -f T / 2
     R4 np, nf, nh;
     auto fetch = [&](int64_t j) {
-        if (j < je) {
+        if (j < je && LM_INBOUNDS(j >= 0 && j < N, 7, j)) {
             np = pos4[j];
             const R fj = np.w;
             nf.x = fj * load_elem<R>(Fp, in_f64, 3 * j + 0);
@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(NT) rpy_wall_x2_kernel(const float4* __restric
     float4 np;
     float3 nf, nt;
     auto fetch = [&](int64_t j) {
-        if (j < je) {
+        if (j < je && LM_INBOUNDS(j >= 0 && j < N, 7, j)) {
             np = pos4[j];
             const float fj = np.w;
             nf.x = fj * load_elem<float>(Fp, in_f64, 3 * j + 0);

@@ -19,7 +19,9 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "liblm_gb300.so")
+# LM_DEBUG_BOUNDS=1 selects the bounds-checked build (``_build.build(debug_bounds=True)``)
+LIB_PATH = os.path.join(_HERE, "_lib", "liblm_gb300_debug.so" if os.environ.get("LM_DEBUG_BOUNDS") == "1"
+                        else "liblm_gb300.so")
 
 LM_OK = 0
 LM_ERR_INVALID_ARG = 1
@@ -172,6 +174,10 @@ def lib():
         L.lm_philox4x32_10.restype = st
         L.lm_fp32_probe.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), _vp]
         L.lm_fp32_probe.restype = st
+        L.lm_debug_bounds.argtypes = []
+        L.lm_debug_bounds.restype = ctypes.c_int
+        L.lm_debug_check.argtypes = []
+        L.lm_debug_check.restype = st
         L.lm_tridiag_sqrt_e1.argtypes = [ctypes.c_int, _vp, _vp, _vp]
         L.lm_tridiag_sqrt_e1.restype = ctypes.c_int
         _lib = L
@@ -643,6 +649,16 @@ def lm_fp32_probe(mode: int, iters: int = 1 << 14, cuda_stream=None) -> float:
     t = ctypes.c_double(0.0)
     _check(lib().lm_fp32_probe(int(mode), int(iters), ctypes.byref(t), cuda_stream))
     return t.value
+
+
+def lm_debug_bounds() -> bool:
+    """True if the loaded library is the bounds-checked build."""
+    return bool(lib().lm_debug_bounds())
+
+
+def lm_debug_check() -> None:
+    """Raise LmError if a device bounds check failed since the last call (bounds-checked build)."""
+    _check(lib().lm_debug_check())
 
 
 def lm_launch_count() -> int:

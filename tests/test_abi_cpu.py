@@ -146,3 +146,12 @@ def test_fp32_probe_rejects_bad_arguments_without_gpu(L):
     for mode, iters in ((4, 100), (-1, 100), (1, 0), (1, (1 << 24) + 1)):
         assert L.lm_fp32_probe(mode, iters, C.byref(t), None) == lm.LM_ERR_INVALID_ARG
     assert L.lm_fp32_probe(1, 100, None, None) == lm.LM_ERR_INVALID_ARG
+
+
+def test_release_build_has_no_bounds_checks_and_debug_check_is_free(L):
+    """The release library reports no device bounds checks, and lm_debug_check
+    returns LM_OK there without touching a GPU."""
+    from paper_2510_02135_gb300 import lm
+
+    assert L.lm_debug_bounds() == 0
+    assert L.lm_debug_check() == lm.LM_OK
