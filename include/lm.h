@@ -280,6 +280,15 @@ lm_status lm_mdot_backward(lm_solver *solver, const void *forces, const void *to
  *   (packed = 1); FP64 ilp 1.  All forms give results within the FP32
  *   tolerance of the FP64 product; they differ in rounding order only.
  */
+/* Launch configuration of the pair kernels (no paper counterpart):
+ *   threads: CTA size and j-tile length (128 or 256);
+ *   ilp: i-particles per thread (FP32: 1, 2, 4, 8; FP64: 1, 2);
+ *   splits: j-range chunks per i-block, >= 1 (0 in lm_set_pair_config: the
+ *     library's model chooses); several splits add FP64 partial sums in a
+ *     second kernel;
+ *   packed: 0 the scalar kernel; FP32 only, with even ilp: 1, 2 or 4 the
+ *     packed f32x2 kernel evaluating 1, 2 or 4 j-particles per overlap vote
+ *     (4 needs ilp >= 4). */
 typedef struct {
     int threads;
     int ilp;

@@ -1339,7 +1339,7 @@ lm_status autotune_impl(lm_solver* s, int reps, lm_pair_config* best) {
     const double flops_pp = s->wall ? (s->angular ? lmk::kFlopsPerPairWall6N : lmk::kFlopsPerPairWallTT)
                                     : (s->angular ? lmk::kFlopsPerPair6N : lmk::kFlopsPerPairTT);
     const bool large = !s->fp64 && (double)N * (double)N * flops_pp > 20e-3 * 50e12;
-    for (int pk = 0; pk <= 2; ++pk) {
+    for (int pk : {0, 1, 2, 4}) {
         if (large && pk == 0) continue;
         for (int t : threads_opts) {
             for (int il : ilp_opts) {

@@ -529,13 +529,16 @@ cudaError_t launch_x2_t(const MdotArgs& a, cudaStream_t s) {
 }
 
 // Packed configurations (FP32 only): threads {128, 256} x ilp {2, 4, 8};
-// packed = 2 unrolls the j loop by two (more independent work per warp).
+// packed = UJ, the j-particles per overlap vote: 1, 2, or 4 (ilp 4 and 8
+// only; more independent work per warp where a CTA of 8 warps fills an SM).
 template <bool ANG, int UJ>
 cudaError_t launch_x2_u(const MdotArgs& a, cudaStream_t s) {
-    if (a.threads == 128 && a.ilp == 2) return launch_x2_t<ANG, 128, 2, UJ>(a, s);
+    if constexpr (UJ != 4) {
+        if (a.threads == 128 && a.ilp == 2) return launch_x2_t<ANG, 128, 2, UJ>(a, s);
+        if (a.threads == 256 && a.ilp == 2) return launch_x2_t<ANG, 256, 2, UJ>(a, s);
+    }
     if (a.threads == 128 && a.ilp == 4) return launch_x2_t<ANG, 128, 4, UJ>(a, s);
     if (a.threads == 128 && a.ilp == 8) return launch_x2_t<ANG, 128, 8, UJ>(a, s);
-    if (a.threads == 256 && a.ilp == 2) return launch_x2_t<ANG, 256, 2, UJ>(a, s);
     if (a.threads == 256 && a.ilp == 4) return launch_x2_t<ANG, 256, 4, UJ>(a, s);
     if (a.threads == 256 && a.ilp == 8) return launch_x2_t<ANG, 256, 8, UJ>(a, s);
     return cudaErrorInvalidConfiguration;
@@ -543,6 +546,7 @@ cudaError_t launch_x2_u(const MdotArgs& a, cudaStream_t s) {
 
 template <bool ANG>
 cudaError_t launch_x2(const MdotArgs& a, cudaStream_t s) {
+    if (a.packed == 4) return launch_x2_u<ANG, 4>(a, s);
     return a.packed == 2 ? launch_x2_u<ANG, 2>(a, s) : launch_x2_u<ANG, 1>(a, s);
 }
 
@@ -558,7 +562,8 @@ template <bool ANG, int UJ>
 int occupancy_x2(int threads, int ilp) {
 #define LM_OCC2(NT, NI) \
     if (threads == NT && ilp == NI) return occupancy_of(rpy_mdot_x2_kernel<ANG, NT, NI, UJ>, NT, x2_smem_bytes<ANG, NT, NI>());
-    LM_OCC2(128, 2) LM_OCC2(128, 4) LM_OCC2(128, 8) LM_OCC2(256, 2) LM_OCC2(256, 4) LM_OCC2(256, 8)
+    if constexpr (UJ != 4) { LM_OCC2(128, 2) LM_OCC2(256, 2) }
+    LM_OCC2(128, 4) LM_OCC2(128, 8) LM_OCC2(256, 4) LM_OCC2(256, 8)
 #undef LM_OCC2
     return 0;
 }
@@ -607,6 +612,7 @@ int64_t mdot_effective_splits(int64_t N, int threads, int splits) {
 int mdot_ctas_per_sm(int fp64, int angular, int threads, int ilp, int packed) {
     if (packed) {
         if (fp64 || !mdot_config_supported(fp64, angular, threads, ilp, packed)) return 0;
+        if (packed == 4) return angular ? occupancy_x2<true, 4>(threads, ilp) : occupancy_x2<false, 4>(threads, ilp);
         if (packed == 2) return angular ? occupancy_x2<true, 2>(threads, ilp) : occupancy_x2<false, 2>(threads, ilp);
         return angular ? occupancy_x2<true, 1>(threads, ilp) : occupancy_x2<false, 1>(threads, ilp);
     }
@@ -616,8 +622,8 @@ int mdot_ctas_per_sm(int fp64, int angular, int threads, int ilp, int packed) {
 
 bool mdot_config_supported(int fp64, int angular, int threads, int ilp, int packed) {
     (void)angular;
-    if (packed) return (packed == 1 || packed == 2) && !fp64 && (threads == 128 || threads == 256) &&
-                       (ilp == 2 || ilp == 4 || ilp == 8);
+    if (packed) return (packed == 1 || packed == 2 || (packed == 4 && ilp >= 4)) && !fp64 &&
+                       (threads == 128 || threads == 256) && (ilp == 2 || ilp == 4 || ilp == 8);
     return (threads == 128 || threads == 256) && (fp64 ? ilp_ok<double>(ilp) : ilp_ok<float>(ilp));
 }
 

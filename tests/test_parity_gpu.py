@@ -108,9 +108,9 @@ def test_mdot_launch_configs_agree(orc, fp64, angular):
     s = make(1.0, 1.0, angular, fp64, s_.pos)
     ur, wr = orc.mdot(s_.pos, s_.F, s_.T, 1.0, 1.0, angular)
     tol = 1e-12 if fp64 else 1e-5
-    for packed in ((0,) if fp64 else (0, 1, 2)):
+    for packed in ((0,) if fp64 else (0, 1, 2, 4)):
         for threads in (128, 256):
-            for ilp in ((1, 2) if fp64 else ((2, 4, 8) if packed else (1, 2, 4, 8))):
+            for ilp in ((1, 2) if fp64 else ((4, 8) if packed == 4 else ((2, 4, 8) if packed else (1, 2, 4, 8)))):
                 for splits in (1, 3, 9):
                     lm.lm_set_pair_config(s, threads, ilp, splits, packed)
                     u, w = gpu_mdot(s, s_.F, s_.T)
@@ -122,14 +122,14 @@ def test_mdot_launch_configs_agree(orc, fp64, angular):
                         assert maxabs_over_rms(u, ur) <= 1e-4, (cfg, maxabs_over_rms(u, ur))
 
 
-@pytest.mark.parametrize("fp64,packed", [(False, 0), (False, 1), (False, 2), (True, 0)])
+@pytest.mark.parametrize("fp64,packed", [(False, 0), (False, 1), (False, 2), (False, 4), (True, 0)])
 def test_mdot_edge_cases(orc, fp64, packed):
     dt = np.float64 if fp64 else np.float32
 
     def make(eta, a, angular, fp64, pos):
         s = make_solver(eta, a, angular, fp64, pos)
         if packed:
-            lm.lm_set_pair_config(s, 128, 2, 0, packed=packed)
+            lm.lm_set_pair_config(s, 128, 4 if packed == 4 else 2, 0, packed=packed)
         return s
 
     a, eta = 1.3, 0.7
