@@ -304,10 +304,18 @@ lm_status lm_set_pair_config(lm_solver *solver, const lm_pair_config *cfg);
 
 /* lm_get_adjoint_config / lm_set_adjoint_config -- launch configuration of
  * lm_mdot_backward for the current N.  LM_FP32C without angular blocks (the
- * packed kernel): threads 128 or 256, ilp 2 or 4, packed = j-particles per
- * overlap vote (1 or 2); otherwise threads 128, ilp 1 (LM_FP64) or 2
- * (LM_FP32C with angular blocks), packed 0.  splits 0 = automatic.
- * Unsupported combinations give LM_ERR_INVALID_ARG. */
+ * packed kernels): threads 128 or 256, ilp 2 or 4, and packed
+ *   1 or 2: the one-sided kernel, j-particles per overlap vote; splits =
+ *     j-range chunks per i-block;
+ *   3: the symmetric kernel: each unordered pair is evaluated once and added
+ *     to both particles (the gradient of a pair term is odd in x_i - x_j and
+ *     the tt block even), about 18% faster at N = 65536; splits = tiles per
+ *     work item (0: chosen from N).  Its two sides meet in FP64 atomic adds,
+ *     so the last bits of an FP64 sum, and rarely the last bit of an FP32
+ *     output, can differ from run to run;
+ * otherwise threads 128, ilp 1 (LM_FP64) or 2 (LM_FP32C with angular
+ * blocks), packed 0.  splits 0 = automatic.  Unsupported combinations give
+ * LM_ERR_INVALID_ARG. */
 lm_status lm_get_adjoint_config(lm_solver *solver, lm_pair_config *cfg);
 lm_status lm_set_adjoint_config(lm_solver *solver, const lm_pair_config *cfg);
 

@@ -689,6 +689,336 @@ cudaError_t launch_adj_x2_t(const AdjointArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Symmetric form of the packed translation adjoint (AdjointArgs::uj == 3).
+//
+// The pair term is symmetric: with d = x_i - x_j and g_ij its gradient,
+// dL/dx_j receives -g_ij, and dL/dF_j receives M(d) G_i = A G_i + B (G_i.d) d
+// (M is even in d).  So each unordered pair is evaluated once and added to
+// both particles: 57 + 18 packed instructions per two pairs for both
+// directions against 2 x 57 for the one-sided kernel.  The j-side terms are
+//   dX_j -= cd d + B (F_j.d) G_i + B (G_j.d) F_i   (summed as a vector)
+//          + [B (F_i.d)] G_j + [B (G_i.d)] F_j     (scalars, applied per tile)
+//   dF_j += A G_i + B (G_i.d) d.
+// Work item (i-block b, tiles [t0, t1)): the tiles of the block's own range
+// [b NI, (b + 1) NI) are diagonal and run one-sided (all ordered pairs,
+// self pairs included); every later tile runs symmetric, and no i-block
+// visits tiles before its own.  Per j, the eight j-side sums of a warp are
+// added across its lanes by a transposing butterfly (9 shuffles) and into
+// the tile's shared sums with one atomic per value; at the end of a tile and
+// of the item, both sides go to FP64 accumulators acc[particle][dX 3, dF 3]
+// by atomic adds, so the summation order of those FP64 adds (not of any
+// FP32 sum) varies from run to run.  A final kernel scales acc into the
+// outputs.
+// ---------------------------------------------------------------------------
+constexpr int kAdjSymVals = 8;   // j-side sums per j: dX vector (3), dF (3), scalars of G_j and F_j
+
+template <int NT, int NI>
+constexpr size_t adj_sym_smem_bytes() {
+    return (size_t)kAdjX2Words * NT * sizeof(float4) + (size_t)kAdjSymVals * NT * sizeof(float) +
+           adj_running_bytes<float, false, NT, NI>();
+}
+
+// Eight per-lane values reduced over the warp: on return lane l holds the
+// sum of value (l >> 2) over all 32 lanes.
+__device__ __forceinline__ float warp_transpose_sum8(float v[8], int lane) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const bool up = lane & 16;
+        const float keep = up ? v[r + 4] : v[r], send = up ? v[r] : v[r + 4];
+        v[r] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const bool up = lane & 8;
+        const float keep = up ? v[r + 2] : v[r], send = up ? v[r] : v[r + 2];
+        v[r] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    {
+        const bool up = lane & 4;
+        const float keep = up ? v[1] : v[0], send = up ? v[0] : v[1];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    return v[0];
+}
+
+template <int NT, int NI>
+__global__ void __launch_bounds__(NT) rpy_adjoint_sym_kernel(const float4* __restrict__ pos4,
+                                                             const void* __restrict__ Fp, const void* __restrict__ Gp,
+                                                             int f64, int64_t N, const int4* __restrict__ items,
+                                                             RpyConst<float> k, double* __restrict__ acc) {
+    static_assert(NI % 2 == 0, "packed form needs an even number of i-particles per thread");
+    constexpr int NP = NI / 2;
+    constexpr int C = 6;   // dX(3) dF(3)
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    float4* s_t = reinterpret_cast<float4*>(dyn_smem);
+    float* s_j = reinterpret_cast<float*>(s_t + kAdjX2Words * NT);   // [v][jj]
+    float* s_hi = s_j + kAdjSymVals * NT;
+    float* s_lo = s_hi + C * NI * NT;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int4 item = items[blockIdx.x];
+    const int64_t b = item.x, t_begin = item.y, t_end = item.z;
+    const int64_t i0 = b * (NT * NI);
+    const int64_t diag_end = (b + 1) * NI;   // first tile after the block's own range
+    const float pad = (float)kPadCoord;
+
+    float2 xi[NP], yi[NP], zi[NP], Fi[NP][3], Gi[NP][3];
+    float2 p[NP][C], sG[NP], sF[NP];
+#pragma unroll
+    for (int pp = 0; pp < NP; ++pp) {
+        float v[2][9];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t i = i0 + (int64_t)(2 * pp + h) * NT + tid;
+            if (i < N && LM_INBOUNDS(i >= 0, 12, i)) {
+                const float4 q = pos4[i];
+                v[h][0] = q.x; v[h][1] = q.y; v[h][2] = q.z;
+            } else {
+                v[h][0] = v[h][1] = v[h][2] = -pad;
+            }
+            const int64_t ii = (i < N) ? i : 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                v[h][3 + c] = (i < N) ? ld<float>(Fp, f64, 3 * ii + c) : 0.f;
+                v[h][6 + c] = (i < N) ? ld<float>(Gp, f64, 3 * ii + c) : 0.f;
+            }
+        }
+        xi[pp] = make_float2(v[0][0], v[1][0]);
+        yi[pp] = make_float2(v[0][1], v[1][1]);
+        zi[pp] = make_float2(v[0][2], v[1][2]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Fi[pp][c] = make_float2(v[0][3 + c], v[1][3 + c]);
+            Gi[pp][c] = make_float2(v[0][6 + c], v[1][6 + c]);
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) p[pp][c] = bc2(0.f);
+        sG[pp] = sF[pp] = bc2(0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            s_hi[(c * NI + q) * NT + tid] = 0.f;
+            s_lo[(c * NI + q) * NT + tid] = 0.f;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < kAdjSymVals; ++v) s_j[v * NT + tid] = 0.f;
+    const float2 K1 = bc2(k.K1), nK2 = bc2(-k.K2), m3K1 = bc2(-3.f * k.K1), K2x5 = bc2(5.f * k.K2);
+    const float2 m1 = bc2(-1.f), m3 = bc2(-3.f);
+
+    const int64_t jlo = t_begin * NT;
+    const int64_t jhi = (t_end * NT < N) ? t_end * NT : N;
+    float4 np;
+    float3 nF, nG;
+    auto fetch = [&](int64_t j) {
+        if (j < jhi && LM_INBOUNDS(j >= 0 && j < N, 13, j)) {
+            np = pos4[j];
+            nF = make_float3(ld<float>(Fp, f64, 3 * j), ld<float>(Fp, f64, 3 * j + 1), ld<float>(Fp, f64, 3 * j + 2));
+            nG = make_float3(ld<float>(Gp, f64, 3 * j), ld<float>(Gp, f64, 3 * j + 1), ld<float>(Gp, f64, 3 * j + 2));
+        } else {
+            np = make_float4(pad, pad, pad, 0.f);
+            nF = nG = make_float3(0.f, 0.f, 0.f);
+        }
+    };
+    fetch(jlo + tid);
+
+    for (int64_t t = t_begin; t < t_end; ++t) {
+        const int64_t jt = t * NT;
+        const bool sym = t >= diag_end;
+        s_t[0 * NT + tid] = make_float4(-np.x, -np.y, -np.z, nF.x);
+        s_t[1 * NT + tid] = make_float4(nF.y, nF.z, nG.x, nG.y);
+        s_t[2 * NT + tid] = make_float4(nG.z, 0.f, 0.f, 0.f);
+        __syncthreads();
+        if (jt + NT < jhi) fetch(jt + NT + tid);
+#pragma unroll 1
+        for (int jj = 0; jj < NT; ++jj) {
+            const float4 w0 = s_t[0 * NT + jj], w1 = s_t[1 * NT + jj], w2 = s_t[2 * NT + jj];
+            const float2 nx = bc2(w0.x), ny = bc2(w0.y), nz = bc2(w0.z);
+            const float2 Fx = bc2(w0.w), Fy = bc2(w1.x), Fz = bc2(w1.y);
+            const float2 Gx = bc2(w1.z), Gy = bc2(w1.w), Gz = bc2(w2.x);
+            float2 dx[NP], dy[NP], dz[NP], r2[NP];
+            float mn;
+#pragma unroll
+            for (int pp = 0; pp < NP; ++pp) {
+                dx[pp] = add2(xi[pp], nx);
+                dy[pp] = add2(yi[pp], ny);
+                dz[pp] = add2(zi[pp], nz);
+                r2[pp] = fma2(dx[pp], dx[pp], fma2(dy[pp], dy[pp], mul2(dz[pp], dz[pp])));
+                const float m2 = fminf(r2[pp].x, r2[pp].y);
+                mn = (pp == 0) ? m2 : fminf(mn, m2);
+            }
+            const bool near = __any_sync(0xffffffffu, mn < k.four_a2);
+            // j-side sums of this lane for j (packed over the lane's i pairs)
+            float2 jX[3], jF[3], jSG, jSF;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) jX[c] = jF[c] = bc2(0.f);
+            jSG = jSF = bc2(0.f);
+#pragma unroll
+            for (int pp = 0; pp < NP; ++pp) {
+                const float2 ddx = dx[pp], ddy = dy[pp], ddz = dz[pp];
+                float2 A, B, Ap, Bp;
+                if (!near) {
+                    const float2 invr = make_float2(rsqrtf(r2[pp].x), rsqrtf(r2[pp].y));
+                    const float2 invr2 = mul2(invr, invr);
+                    const float2 invr3 = mul2(invr2, invr);
+                    const float2 invr5 = mul2(invr3, invr2);
+                    A = fma2(K1, invr3, invr);
+                    B = fma2(nK2, invr5, invr3);
+                    Ap = mul2(invr3, fma2(m3K1, invr2, m1));    // -1/r^3 - 3 K1/r^5
+                    Bp = mul2(invr5, fma2(K2x5, invr2, m3));    // -3/r^5 + 5 K2/r^7
+                } else {
+                    // exact coefficients of either branch per lane; at r = 0
+                    // (self or coincident pairs) A is the self mobility and
+                    // B = A' = B' = 0, so the pair adds only A G_j to dF
+                    Coef<float> c0, c1;
+                    exact_coef<float, false>(r2[pp].x, k, c0);
+                    exact_coef<float, false>(r2[pp].y, k, c1);
+                    A = make_float2(c0.A, c1.A);
+                    B = make_float2(c0.B, c1.B);
+                    Ap = make_float2(c0.Ap, c1.Ap);
+                    Bp = make_float2(c0.Bp, c1.Bp);
+                }
+                const float2 b1 = fma2(Fx, ddx, fma2(Fy, ddy, mul2(Fz, ddz)));   // F_j.d
+                const float2 b2 = fma2(Gx, ddx, fma2(Gy, ddy, mul2(Gz, ddz)));   // G_j.d
+                const float2 Bb2 = mul2(B, b2);
+                p[pp][3] = fma2(Bb2, ddx, fma2(A, Gx, p[pp][3]));
+                p[pp][4] = fma2(Bb2, ddy, fma2(A, Gy, p[pp][4]));
+                p[pp][5] = fma2(Bb2, ddz, fma2(A, Gz, p[pp][5]));
+                const float2 a1 = fma2(Gi[pp][0], ddx, fma2(Gi[pp][1], ddy, mul2(Gi[pp][2], ddz)));
+                const float2 a2 = fma2(Fi[pp][0], ddx, fma2(Fi[pp][1], ddy, mul2(Fi[pp][2], ddz)));
+                const float2 S1 = fma2(Gi[pp][0], Fx, fma2(Gi[pp][1], Fy, fma2(Gi[pp][2], Fz,
+                                  fma2(Fi[pp][0], Gx, fma2(Fi[pp][1], Gy, mul2(Fi[pp][2], Gz))))));
+                const float2 S2 = fma2(a1, b1, mul2(a2, b2));
+                const float2 cd = fma2(Ap, S1, mul2(Bp, S2));
+                const float2 Ba2 = mul2(B, a2), Ba1 = mul2(B, a1), Bb1 = mul2(B, b1);
+                sG[pp] = add2(sG[pp], Bb1);
+                sF[pp] = add2(sF[pp], Bb2);
+                p[pp][0] = fma2(cd, ddx, fma2(Ba2, Gx, fma2(Ba1, Fx, p[pp][0])));
+                p[pp][1] = fma2(cd, ddy, fma2(Ba2, Gy, fma2(Ba1, Fy, p[pp][1])));
+                p[pp][2] = fma2(cd, ddz, fma2(Ba2, Gz, fma2(Ba1, Fz, p[pp][2])));
+                if (sym) {
+                    jX[0] = fma2(cd, ddx, fma2(Bb1, Gi[pp][0], fma2(Bb2, Fi[pp][0], jX[0])));
+                    jX[1] = fma2(cd, ddy, fma2(Bb1, Gi[pp][1], fma2(Bb2, Fi[pp][1], jX[1])));
+                    jX[2] = fma2(cd, ddz, fma2(Bb1, Gi[pp][2], fma2(Bb2, Fi[pp][2], jX[2])));
+                    jSG = add2(jSG, Ba2);
+                    jSF = add2(jSF, Ba1);
+                    jF[0] = fma2(Ba1, ddx, fma2(A, Gi[pp][0], jF[0]));
+                    jF[1] = fma2(Ba1, ddy, fma2(A, Gi[pp][1], jF[1]));
+                    jF[2] = fma2(Ba1, ddz, fma2(A, Gi[pp][2], jF[2]));
+                }
+            }
+            if (sym) {
+                float v[kAdjSymVals] = {jX[0].x + jX[0].y, jX[1].x + jX[1].y, jX[2].x + jX[2].y,
+                                        jF[0].x + jF[0].y, jF[1].x + jF[1].y, jF[2].x + jF[2].y,
+                                        jSG.x + jSG.y, jSF.x + jSF.y};
+                const float tot = warp_transpose_sum8(v, lane);
+                if ((lane & 3) == 0) atomicAdd(&s_j[(lane >> 2) * NT + jj], tot);
+            }
+        }
+        // apply the tile's i-side scalars and fold into the running sums
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) p[pp][c] = fma2(sG[pp], Gi[pp][c], fma2(sF[pp], Fi[pp][c], p[pp][c]));
+            sG[pp] = sF[pp] = bc2(0.f);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const int o0 = (c * NI + 2 * pp) * NT + tid;
+                const int o1 = o0 + NT;
+                fold(&s_hi[o0], &s_lo[o0], p[pp][c].x);
+                fold(&s_hi[o1], &s_lo[o1], p[pp][c].y);
+            }
+        }
+        __syncthreads();
+        if (sym) {
+            // this tile's j-side sums of the CTA: dX_j -= vector + sG_j G_j + sF_j F_j, dF_j += sums
+            const int64_t j = jt + tid;
+            if (j < N && LM_INBOUNDS(j >= 0, 14, j)) {
+                const float4 w0 = s_t[0 * NT + tid], w1 = s_t[1 * NT + tid], w2 = s_t[2 * NT + tid];
+                const float Fj[3] = {w0.w, w1.x, w1.y}, Gj[3] = {w1.z, w1.w, w2.x};
+                const float sgj = s_j[6 * NT + tid], sfj = s_j[7 * NT + tid];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float dxj = s_j[c * NT + tid] + sgj * Gj[c] + sfj * Fj[c];
+                    atomicAdd(&acc[6 * j + c], -(double)dxj);
+                    atomicAdd(&acc[6 * j + 3 + c], (double)s_j[(3 + c) * NT + tid]);
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < kAdjSymVals; ++v) s_j[v * NT + tid] = 0.f;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+        const int64_t i = i0 + (int64_t)q * NT + tid;
+        if (i >= N) continue;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int o = (c * NI + q) * NT + tid;
+            atomicAdd(&acc[6 * i + c], (double)s_hi[o] + (double)s_lo[o]);
+        }
+    }
+}
+
+// out = c8 * acc (dX from components 0..2, dF from 3..5), nullable outputs.
+__global__ void adj_sym_store_kernel(const double* __restrict__ acc, int64_t N, double c8, void* __restrict__ dX,
+                                     void* __restrict__ dF, int out_f64) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 6 * N) return;
+    const int64_t i = e / 6;
+    const int c = (int)(e - 6 * i);
+    void* out = (c < 3) ? dX : dF;
+    if (out == nullptr) return;
+    const int64_t idx = 3 * i + (c % 3);
+    if (out_f64) static_cast<double*>(out)[idx] = c8 * acc[e];
+    else static_cast<float*>(out)[idx] = (float)(c8 * acc[e]);
+}
+
+template <int NT, int NI>
+cudaError_t launch_adj_sym_t(const AdjointArgs& a, cudaStream_t s) {
+    if (a.sym_items == nullptr || a.sym_acc == nullptr || a.n_sym_items < 1) return cudaErrorInvalidValue;
+    if (a.n_sym_items > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    const double c8 = 1.0 / (8.0 * 3.14159265358979323846 * a.eta);
+    const RpyConst<float> k = make_rpy_const<float>(a.a);
+    constexpr size_t dyn = adj_sym_smem_bytes<NT, NI>();
+    static std::atomic<unsigned long long> attr_devs{0};  // devices whose limit is raised
+    if (cudaError_t e = smem_attr_once(attr_devs, rpy_adjoint_sym_kernel<NT, NI>, dyn)) return e;
+    cudaError_t e = cudaMemsetAsync(a.sym_acc, 0, (size_t)6 * a.N * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    rpy_adjoint_sym_kernel<NT, NI><<<(unsigned)a.n_sym_items, NT, dyn, s>>>(
+        static_cast<const float4*>(a.pos4), a.F, a.G, a.fp64, a.N, static_cast<const int4*>(a.sym_items), k,
+        a.sym_acc);
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    adj_sym_store_kernel<<<(unsigned)((6 * a.N + 255) / 256), 256, 0, s>>>(a.sym_acc, a.N, c8, a.dX, a.dF, a.fp64);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_sym(const AdjointArgs& a, cudaStream_t s) {
+    if (a.threads == 128 && a.ilp == 2) return launch_adj_sym_t<128, 2>(a, s);
+    if (a.threads == 128 && a.ilp == 4) return launch_adj_sym_t<128, 4>(a, s);
+    if (a.threads == 256 && a.ilp == 2) return launch_adj_sym_t<256, 2>(a, s);
+    if (a.threads == 256 && a.ilp == 4) return launch_adj_sym_t<256, 4>(a, s);
+    return cudaErrorInvalidConfiguration;
+}
+
+template <int NT, int NI>
+int adj_sym_occupancy() {
+    int n = 0;
+    constexpr size_t dyn = adj_sym_smem_bytes<NT, NI>();
+    cudaError_t e = cudaFuncSetAttribute(rpy_adjoint_sym_kernel<NT, NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dyn);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rpy_adjoint_sym_kernel<NT, NI>, NT, dyn);
+    return e == cudaSuccess ? n : 0;
+}
+
 // Packed translation adjoint configurations: threads {128, 256} x ilp {2, 4}
 // x j per vote {1, 2} (AdjointArgs::uj).
 template <int NT, int NI>
@@ -725,15 +1055,16 @@ int adjoint_ilp(int fp64, int angular) { return fp64 ? 1 : (angular ? 2 : 4); }
 
 bool adjoint_config_supported(int fp64, int angular, int threads, int ilp, int uj) {
     if (fp64 || angular) return threads == 128 && ilp == adjoint_ilp(fp64, angular) && uj <= 1;
-    return (threads == 128 || threads == 256) && (ilp == 2 || ilp == 4) && (uj == 0 || uj == 1 || uj == 2);
+    return (threads == 128 || threads == 256) && (ilp == 2 || ilp == 4) && uj >= 0 && uj <= 3;
 }
 
 cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s) {
     if (a.N <= 0) return cudaSuccess;
     if (!adjoint_config_supported(a.fp64, a.angular, a.threads, a.ilp, a.uj)) return cudaErrorInvalidConfiguration;
     if (a.fp64) return a.angular ? launch_adj_t<double, true, 1>(a, s) : launch_adj_t<double, false, 1>(a, s);
-    // FP32: translation blocks use the packed (f32x2) kernel
-    return a.angular ? launch_adj_t<float, true, 2>(a, s) : launch_adj_x2(a, s);
+    // FP32: translation blocks use the packed (f32x2) kernels, one-sided or symmetric
+    if (a.angular) return launch_adj_t<float, true, 2>(a, s);
+    return a.uj == 3 ? launch_adj_sym(a, s) : launch_adj_x2(a, s);
 }
 
 int adjoint_ctas_per_sm(int fp64, int angular, int threads, int ilp, int uj) {
@@ -751,7 +1082,13 @@ int adjoint_ctas_per_sm(int fp64, int angular, int threads, int ilp, int uj) {
     if (fp64 && angular) LM_AOCC(double, true, 1)
     else if (fp64) LM_AOCC(double, false, 1)
     else if (angular) LM_AOCC(float, true, 2)
-    else {
+    else if (uj == 3) {
+        if (threads == 128 && ilp == 2) return adj_sym_occupancy<128, 2>();
+        if (threads == 128 && ilp == 4) return adj_sym_occupancy<128, 4>();
+        if (threads == 256 && ilp == 2) return adj_sym_occupancy<256, 2>();
+        if (threads == 256 && ilp == 4) return adj_sym_occupancy<256, 4>();
+        return 0;
+    } else {
         const bool two = uj == 2;
         if (threads == 128 && ilp == 2) return two ? adj_x2_occupancy<128, 2, 2>() : adj_x2_occupancy<128, 2, 1>();
         if (threads == 128 && ilp == 4) return two ? adj_x2_occupancy<128, 4, 2>() : adj_x2_occupancy<128, 4, 1>();

@@ -163,6 +163,10 @@ struct lm_solver {
 
     // Lanczos state
     DBuf V, w, y, red, scal, zbuf, cbuf, Wbuf;
+    // symmetric adjoint: work-item table (for sym_key) and FP64 accumulators
+    DBuf sym_items, sym_acc;
+    std::array<int64_t, 4> sym_key{{-1, 0, 0, 0}};
+    int64_t sym_n_items = 0;
     double* pinned = nullptr;  // host scalar read-back
     size_t pinned_doubles = 0;
 
@@ -197,7 +201,7 @@ struct lm_solver {
         DBuf* all[] = {&pos4, &partials, &in_stage[0], &in_stage[1], &in_stage[2], &in_stage[3],
                        &out_stage[0], &out_stage[1], &out_stage[2], &flag, &tune_in, &tune_out,
                        &pos_raw, &rfd_pos4, &rfd_W, &rfd_P, &rfd_Q, &ab_u, &ab_d, &ab_y, &ab_x, &pc_p, &pc_q, &pc_t, &lzctr,
-                       &V, &w, &y, &red, &scal, &zbuf, &cbuf, &Wbuf};
+                       &V, &w, &y, &red, &scal, &zbuf, &cbuf, &Wbuf, &sym_items, &sym_acc};
         for (DBuf* b : all) b->release();
         if (pinned) cudaFreeHost(pinned);
         for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
@@ -510,13 +514,27 @@ void ensure_adjoint_config(lm_solver* s) {
     TunedEntry e;
     if (lookup_tuned(s, s->N, &e) && e.has_adj) {
         s->adj_cfg = e.adj;
-        if (e.N != s->N) {
+        if (e.N != s->N && e.adj.packed == 3) {
+            s->adj_cfg.splits = 0;   // item size recomputed for this N
+        } else if (e.N != s->N) {
             const int occ = std::max(1, lmk::adjoint_ctas_per_sm(s->fp64, s->angular, e.adj.threads, e.adj.ilp,
                                                                   e.adj.packed));
             s->adj_cfg.splits = auto_splits(s->N, e.adj.threads, e.adj.ilp, occ * s->sm_count);
         }
     }
     s->adj_cfg_N = s->N;
+}
+
+// Tiles per work item of the symmetric adjoint when the configuration leaves
+// it open: about six items per resident CTA slot over the block-triangle of
+// (i-block, tile) units.
+int64_t sym_auto_chunk(const lm_solver* s, int threads, int ilp) {
+    const int64_t BI = (int64_t)threads * ilp;
+    const int64_t nblk = (s->N + BI - 1) / BI;
+    const int64_t T = (s->N + threads - 1) / threads;
+    const int occ = std::max(1, lmk::adjoint_ctas_per_sm(0, 0, threads, ilp, 3));
+    const double total = (double)nblk * (double)T - (double)ilp * (double)nblk * (double)(nblk - 1) / 2.0;
+    return std::max<int64_t>(1, (int64_t)std::ceil(total / (6.0 * occ * s->sm_count)));
 }
 
 lm_status run_adjoint(lm_solver* s, const void* F, const void* T, const void* G, const void* H, void* dX, void* dF,
@@ -535,6 +553,36 @@ lm_status run_adjoint(lm_solver* s, const void* F, const void* T, const void* G,
     a.uj = cfg.packed > 0 ? cfg.packed : 1;
     a.splits = cfg.splits;
     a.partials = nullptr;
+    if (a.uj == 3) {
+        // symmetric form: items (i-block b, tiles [t0, t1)) over each block's
+        // tiles from its own range onward, at most `chunk` tiles each, longest first
+        const int64_t BI = (int64_t)cfg.threads * cfg.ilp;
+        const int64_t nblk = (s->N + BI - 1) / BI;
+        const int64_t T = (s->N + cfg.threads - 1) / cfg.threads;
+        const int64_t chunk = cfg.splits >= 1 ? cfg.splits : sym_auto_chunk(s, cfg.threads, cfg.ilp);
+        const std::array<int64_t, 4> key{{s->N, cfg.threads, cfg.ilp, chunk}};
+        if (s->sym_key != key) {
+            std::vector<int4> items;
+            for (int64_t b = 0; b < nblk; ++b)
+                for (int64_t t0 = b * cfg.ilp; t0 < T; t0 += chunk)
+                    items.push_back(make_int4((int)b, (int)t0, (int)std::min(T, t0 + chunk), 0));
+            std::stable_sort(items.begin(), items.end(),
+                             [](const int4& x, const int4& y) { return (x.z - x.y) > (y.z - y.y); });
+            LM_CUDA(s->sym_items.ensure(items.size() * sizeof(int4)), "allocating adjoint work items");
+            LM_CUDA(cudaMemcpyAsync(s->sym_items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                    s->stream),
+                    "adjoint work items");
+            LM_CUDA(cudaStreamSynchronize(s->stream), "adjoint work items");
+            s->sym_key = key;
+            s->sym_n_items = (int64_t)items.size();
+        }
+        LM_CUDA(s->sym_acc.ensure((size_t)6 * s->N * sizeof(double)), "allocating adjoint accumulators");
+        a.sym_items = s->sym_items.p;
+        a.n_sym_items = s->sym_n_items;
+        a.sym_acc = s->sym_acc.as<double>();
+        LM_CUDA(lmk::launch_adjoint(a, s->stream), "adjoint kernel");
+        return LM_OK;
+    }
     const int64_t se = lmk::mdot_effective_splits(s->N, a.threads, a.splits);
     if (se > 1) {
         const size_t pb = (size_t)se * lmk::adjoint_partial_components(s->angular) * (size_t)s->N * sizeof(double);
@@ -1280,7 +1328,7 @@ lm_status lm_set_adjoint_config(lm_solver* s, const lm_pair_config* cfg) {
         return fail(LM_ERR_INVALID_ARG, "unsupported adjoint configuration (threads %d, ilp %d, splits %d, packed %d)",
                     cfg->threads, cfg->ilp, cfg->splits, cfg->packed);
     lm_pair_config c = *cfg;
-    if (c.splits == 0) {
+    if (c.splits == 0 && c.packed != 3) {   // the symmetric form chooses its item size at launch
         const int occ = std::max(1, lmk::adjoint_ctas_per_sm(s->fp64, s->angular, c.threads, c.ilp, c.packed));
         c.splits = auto_splits(s->N, c.threads, c.ilp, occ * s->sm_count);
     }
@@ -1404,11 +1452,18 @@ lm_status autotune_impl(lm_solver* s, int reps, lm_pair_config* best) {
     // the packed translation adjoint (open geometry): threads x ilp x j per vote x splits
     if (result == LM_OK && !s->fp64 && !s->angular && !s->wall) {
         std::vector<lm_pair_config> acands;
-        for (int uj = 1; uj <= 2; ++uj) {
+        for (int uj = 1; uj <= 3; ++uj) {
             for (int t : threads_opts) {
                 for (int il = 2; il <= 4; il += 2) {
                     const int occ = lmk::adjoint_ctas_per_sm(0, 0, t, il, uj);
                     if (occ < 1) continue;
+                    if (uj == 3) {
+                        // symmetric form: the item size (tiles) of the model, half and twice it
+                        const int64_t ch = sym_auto_chunk(s, t, il);
+                        for (int64_t c : {ch, std::max<int64_t>(1, ch / 2), 2 * ch})
+                            acands.push_back(lm_pair_config{t, il, (int)std::min<int64_t>(c, 1 << 20), 3});
+                        continue;
+                    }
                     for (int sp : split_candidates(N, t, il, occ * s->sm_count))
                         acands.push_back(lm_pair_config{t, il, sp, uj});
                 }

@@ -70,7 +70,7 @@ def test_adjoint_launch_configs_agree(orc):
     gF, _ = orc.mdot(s_.pos, s_.G, None, 1.0, 1.0, False)
     for threads in (128, 256):
         for ilp in (2, 4):
-            for uj in (1, 2):
+            for uj in (1, 2, 3):
                 for splits in (1, 3, 9):
                     lm.lm_set_adjoint_config(s, threads, ilp, splits, uj)
                     dX, dF, _ = lm.lm_mdot_backward(s, dev(s_.F), None, dev(s_.G), None)
@@ -81,6 +81,31 @@ def test_adjoint_launch_configs_agree(orc):
         lm.lm_set_adjoint_config(s, 128, 3, 1, 1)
     with pytest.raises(lm.LmError):
         lm.lm_set_adjoint_config(s, 128, 4, 1, 0)
+
+
+def test_adjoint_symmetric_form_overlaps_across_blocks(orc):
+    """The symmetric form (each unordered pair once, added to both particles)
+    where the exact branch falls in symmetric tiles: a coincident pair and an
+    overlapping pair whose particles lie in different i-blocks, N ragged for
+    every tile; dF alone and dX alone."""
+    n = 700
+    s_ = I.cube_suspension(62, n, 0.15, 1.0, angular=False, fp32=True)
+    pos = s_.pos.copy()
+    pos[500] = pos[10]                                           # coincident, blocks 0 and 1
+    pos[600] = pos[20] + np.array([0.5, 0.1, 0.0], np.float32)  # overlapping, blocks 0 and 2
+    s = lm.lm_create(1.0, 1.0, False, lm.LM_FP32C)
+    lm.lm_set_positions(s, dev(pos))
+    gX = orc.grad(pos, s_.F, None, s_.G, None, 1.0, 1.0, False)
+    gF, _ = orc.mdot(pos, s_.G, None, 1.0, 1.0, False)
+    for threads, ilp, chunk in ((128, 2, 1), (128, 2, 0), (256, 4, 2), (128, 4, 5)):
+        lm.lm_set_adjoint_config(s, threads, ilp, chunk, 3)
+        dX, dF, _ = lm.lm_mdot_backward(s, dev(s_.F), None, dev(s_.G), None)
+        assert rel(host(dX), gX) <= 1e-5, (threads, ilp, chunk, rel(host(dX), gX))
+        assert rel(host(dF), gF) <= 1e-5, (threads, ilp, chunk, rel(host(dF), gF))
+        dX2, dF2, _ = lm.lm_mdot_backward(s, dev(s_.F), None, dev(s_.G), None, need_dF=False)
+        assert dF2 is None and rel(host(dX2), gX) <= 1e-5
+        _, dF3, _ = lm.lm_mdot_backward(s, dev(s_.F), None, dev(s_.G), None, need_dX=False)
+        assert rel(host(dF3), gF) <= 1e-5
 
 
 def test_adjoint_skips_outputs_and_handles_coincident(orc):
