@@ -647,8 +647,8 @@ def run_reference(args, ws, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["melt", "rpy6", "adjoint", "bd256", "wall", "rollers"], default="melt")
     ap.add_argument("--jacobi", action="store_true", help="rollers: Jacobi-preconditioned Lanczos")

@@ -715,7 +715,7 @@ constexpr int kAdjSymVals = 8;   // j-side sums per j: dX vector (3), dF (3), sc
 
 template <int NT, int NI>
 constexpr size_t adj_sym_smem_bytes() {
-    return (size_t)kAdjX2Words * NT * sizeof(float4) + (size_t)kAdjSymVals * NT * sizeof(float) +
+    return (size_t)kAdjX2Words * NT * sizeof(float4) + (size_t)kAdjSymVals * (NT + 1) * sizeof(float) +
            adj_running_bytes<float, false, NT, NI>();
 }
 
@@ -754,8 +754,11 @@ __global__ void __launch_bounds__(NT) rpy_adjoint_sym_kernel(const float4* __res
     constexpr int C = 6;   // dX(3) dF(3)
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     float4* s_t = reinterpret_cast<float4*>(dyn_smem);
-    float* s_j = reinterpret_cast<float*>(s_t + kAdjX2Words * NT);   // [v][jj]
-    float* s_hi = s_j + kAdjSymVals * NT;
+    // j-side sums [v][jj], rows NT + 1 apart so that the eight lanes adding
+    // values 0..7 of one j hit eight different banks
+    constexpr int SJ = NT + 1;
+    float* s_j = reinterpret_cast<float*>(s_t + kAdjX2Words * NT);
+    float* s_hi = s_j + kAdjSymVals * SJ;
     float* s_lo = s_hi + C * NI * NT;
     const int tid = threadIdx.x, lane = tid & 31;
     const int4 item = items[blockIdx.x];
@@ -806,7 +809,7 @@ __global__ void __launch_bounds__(NT) rpy_adjoint_sym_kernel(const float4* __res
         }
     }
 #pragma unroll
-    for (int v = 0; v < kAdjSymVals; ++v) s_j[v * NT + tid] = 0.f;
+    for (int v = 0; v < kAdjSymVals; ++v) s_j[v * SJ + tid] = 0.f;
     const float2 K1 = bc2(k.K1), nK2 = bc2(-k.K2), m3K1 = bc2(-3.f * k.K1), K2x5 = bc2(5.f * k.K2);
     const float2 m1 = bc2(-1.f), m3 = bc2(-3.f);
 
@@ -916,7 +919,7 @@ __global__ void __launch_bounds__(NT) rpy_adjoint_sym_kernel(const float4* __res
                                         jF[0].x + jF[0].y, jF[1].x + jF[1].y, jF[2].x + jF[2].y,
                                         jSG.x + jSG.y, jSF.x + jSF.y};
                 const float tot = warp_transpose_sum8(v, lane);
-                if ((lane & 3) == 0) atomicAdd(&s_j[(lane >> 2) * NT + jj], tot);
+                if ((lane & 3) == 0) atomicAdd(&s_j[(lane >> 2) * SJ + jj], tot);
             }
         }
         // apply the tile's i-side scalars and fold into the running sums
@@ -940,16 +943,16 @@ __global__ void __launch_bounds__(NT) rpy_adjoint_sym_kernel(const float4* __res
             if (j < N && LM_INBOUNDS(j >= 0, 14, j)) {
                 const float4 w0 = s_t[0 * NT + tid], w1 = s_t[1 * NT + tid], w2 = s_t[2 * NT + tid];
                 const float Fj[3] = {w0.w, w1.x, w1.y}, Gj[3] = {w1.z, w1.w, w2.x};
-                const float sgj = s_j[6 * NT + tid], sfj = s_j[7 * NT + tid];
+                const float sgj = s_j[6 * SJ + tid], sfj = s_j[7 * SJ + tid];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float dxj = s_j[c * NT + tid] + sgj * Gj[c] + sfj * Fj[c];
+                    const float dxj = s_j[c * SJ + tid] + sgj * Gj[c] + sfj * Fj[c];
                     atomicAdd(&acc[6 * j + c], -(double)dxj);
-                    atomicAdd(&acc[6 * j + 3 + c], (double)s_j[(3 + c) * NT + tid]);
+                    atomicAdd(&acc[6 * j + 3 + c], (double)s_j[(3 + c) * SJ + tid]);
                 }
             }
 #pragma unroll
-            for (int v = 0; v < kAdjSymVals; ++v) s_j[v * NT + tid] = 0.f;
+            for (int v = 0; v < kAdjSymVals; ++v) s_j[v * SJ + tid] = 0.f;
         }
         __syncthreads();
     }
