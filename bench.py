@@ -162,7 +162,7 @@ def profile_traffic(workload: str):
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_sha256_16") != pair_kernel_source_hash():
+    if (vals.get("kernel_source_sha256_16", "").split() or [""])[0] != pair_kernel_source_hash():
         return None
     try:
         return float(vals["dram_bytes_per_launch"].split()[0])

@@ -484,17 +484,28 @@ lm_status lm_batch_profile_read(lm_batch *batch, uint64_t *out, int n, int *coun
 lm_status lm_batch_profile_pairs(lm_batch *batch, uint64_t *pairs);
 
 /*
- * lm_tridiag_sqrt_e1_device -- the device form of the same tridiagonal step
- * (Sec. 3.3) that the batched kernel runs, one GPU thread per system, exposed
- * for testing and timing: for each of `count` systems c, out[c m .. c m + m)
- * = sqrt(T_c) e1 with T_c = tridiag(beta_c, alpha_c, beta_c), alpha_c =
+ * lm_tridiag_sqrt_e1_device -- the device form of the tridiagonal step
+ * (Sec. 3.3) that the batched kernel runs, one warp per system, exposed for
+ * testing and timing: for each of `count` systems c, out[c m .. c m + m) =
+ * sqrt(T_c) e1 with T_c = tridiag(beta_c, alpha_c, beta_c), alpha_c =
  * alpha[c m ..] (m entries), beta_c = beta[c m ..] (m - 1 entries used).
  * alpha, beta, out: device memory, count x m doubles each; 1 <= m <= 128.
- * Allocates its scratch, runs on cuda_stream and waits for it.  Returns
- * LM_ERR_CUDA if a system's QR iteration failed.
+ * A T that FP32 Sturm counts certify positive definite (smallest eigenvalue
+ * above about 1e-5 of its largest entry) is solved by a trapezoid-rule
+ * quadrature of (2/pi) int_0^inf T (T + t^2 I)^{-1} e1 dt over log t (about
+ * 200 nodes, relative error about 1e-13, one tridiagonal solve per node, the
+ * nodes shared among the warp's lanes); any other T by the implicit QR
+ * iteration in double-float on one lane, which clamps negative eigenvalues to
+ * zero.  Allocates its scratch, runs on cuda_stream and waits for it.
+ * Returns LM_ERR_CUDA if a system's QR iteration failed or T has a
+ * non-finite entry.  lm_tridiag_sqrt_e1_device_paths also writes, when
+ * paths (host memory, count ints) is not NULL, 0 for each system the
+ * quadrature solved and 1 for each the QR form solved.
  */
 lm_status lm_tridiag_sqrt_e1_device(int count, int m, const double *alpha, const double *beta, double *out,
                                     void *cuda_stream);
+lm_status lm_tridiag_sqrt_e1_device_paths(int count, int m, const double *alpha, const double *beta, double *out,
+                                          int *paths, void *cuda_stream);
 
 /*
  * Tridiagonal solve requests of the last batched run (profiling): *posted

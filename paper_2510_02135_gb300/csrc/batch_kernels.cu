@@ -455,80 +455,104 @@ __device__ bool post_request(const BatchParams& P, uint64_t gstep, int s, int k)
     return true;
 }
 
-// Solve the request of ticket idx (one lane).  Returns false on an error.
-__device__ bool serve_request(const BatchParams& P, unsigned long long idx, df* d, df* e, df* r, double* z, int* rk,
-                              df* rc, df* rs) {
+// Solve the request of ticket idx with the whole warp (every lane calls it
+// with the same idx; scr is the warp's scratch, wid its solver-warp index).
+// Returns false on an error (the same value on every lane).
+__device__ bool serve_request(const BatchParams& P, unsigned long long idx, int lane, int wid, double* scr) {
     const int slot = (int)(idx % (unsigned long long)P.q_cap);
-    const long long t0 = clock64();
-    while (vload(&P.q_seq[slot]) != idx + 1ull) {   // the poster is between its two writes
-        if (clock64() - t0 > P.spin_limit) { atomicCAS(P.err, kBatchOk, kBatchTimeout); return false; }
-        __nanosleep(100);
+    unsigned long long req = 0;
+    int got = 1;
+    if (lane == 0) {
+        const long long t0 = clock64();
+        while (vload(&P.q_seq[slot]) != idx + 1ull) {   // the poster is between its two writes
+            if (clock64() - t0 > P.spin_limit) {
+                atomicCAS(P.err, kBatchOk, kBatchTimeout);
+                got = 0;
+                break;
+            }
+            __nanosleep(100);
+        }
+        if (got) {
+            __threadfence();
+            req = (unsigned long long)*(volatile long long*)&P.q_req[slot];
+            __threadfence();
+            atomicExch(&P.q_ack[slot], idx + 1ull);
+        }
     }
-    __threadfence();
-    const uint64_t req = (uint64_t)*(volatile long long*)&P.q_req[slot];
-    __threadfence();
-    atomicExch(&P.q_ack[slot], idx + 1ull);
+    if (!__shfl_sync(0xffffffffu, got, 0)) return false;
+    req = __shfl_sync(0xffffffffu, req, 0);
     const uint64_t gstep = req >> 28;
     const int s = (int)((req >> 7) & ((1u << 21) - 1));
     const int k = (int)(req & 127);
     bool ok = true;
-    if ((long long)gstep == *(volatile long long*)P.cur_step) {
+    int current = 0;
+    if (lane == 0) current = (long long)gstep == *(volatile long long*)P.cur_step;
+    if (__shfl_sync(0xffffffffu, current, 0)) {
         const int m = k + 1;
-        const int rcode = tridiag_sqrt_e1_df<1>(m, P.alpha + (size_t)s * P.m_max, P.beta + (size_t)s * P.m_max, d, e,
-                                               r, rk, rc, rs, P.max_rot, z);
+        const double* al = P.alpha + (size_t)s * P.m_max;
+        const double* be = P.beta + (size_t)s * P.m_max;
+        double* z = scr + 4 * (size_t)P.m_max;
+        int rcode = tridiag_sqrt_e1_warp(m, P.m_max, al, be, scr, z, lane);
+        if (rcode == 1) {
+            // not certified positive definite: the QR form on lane 0
+            if (lane == 0) {
+                df* d = reinterpret_cast<df*>(scr + 5 * (size_t)P.m_max);
+                rcode = tridiag_sqrt_e1_df<1>(m, al, be, d, d + P.m_max, d + 2 * P.m_max,
+                                              P.trk + (size_t)wid * P.max_rot,
+                                              reinterpret_cast<df*>(P.trc + (size_t)wid * P.max_rot),
+                                              reinterpret_cast<df*>(P.trs + (size_t)wid * P.max_rot), P.max_rot, z);
+            }
+            rcode = __shfl_sync(0xffffffffu, rcode, 0);
+            __syncwarp();
+        }
         // a request that became stale during the solve may have read the next
         // step's coefficients: its result and status are dropped
-        if ((long long)gstep == *(volatile long long*)P.cur_step) {
+        int still = 0;
+        if (lane == 0) still = (long long)gstep == *(volatile long long*)P.cur_step;
+        if (__shfl_sync(0xffffffffu, still, 0)) {
             if (rcode != 0) {
-                atomicCAS(P.err, kBatchOk, kBatchTridiag);
+                if (lane == 0) atomicCAS(P.err, kBatchOk, kBatchTridiag);
                 ok = false;
             } else {
                 const size_t ri = res_index(P, s, gstep, k);
                 double* zr = P.zres + ri * P.m_max;
                 const double nw = __ldcg(P.normW + s);
-                for (int i = 0; i < m; ++i) zr[i] = z[i] * nw;
+                for (int i = lane; i < m; i += 32) zr[i] = z[i] * nw;
                 __threadfence();
-                atomicExch(&P.zdone[ri], res_tag(gstep, k));
+                __syncwarp();
+                if (lane == 0) atomicExch(&P.zdone[ri], res_tag(gstep, k));
             }
         }
     }
-    __threadfence();
-    atomicSub(&P.inflight[gstep & 1], 1);
-    atomicAdd(&P.q_ctr[2], 1ull);
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence();
+        atomicSub(&P.inflight[gstep & 1], 1);
+        atomicAdd(&P.q_ctr[2], 1ull);
+    }
     return ok;
 }
 
 __device__ void solver_loop(const BatchParams& P) {
-    // lanes [0, kSolverWidth) of every solver warp each serve one request;
-    // each has contiguous scratch (the QR's working set stays in L1)
+    // every solver warp serves one request at a time with all its lanes
     const int lane = threadIdx.x & 31;
     const int wid = ((blockIdx.x - P.n_main) * blockDim.x + threadIdx.x) >> 5;
-    const size_t slot = (size_t)wid * kSolverWidth + (size_t)min(lane, kSolverWidth - 1);
-    df* d = reinterpret_cast<df*>(P.sv_w + slot * 4 * P.m_max);
-    df* e = d + P.m_max;
-    df* r = e + P.m_max;
-    double* z = P.sv_w + slot * 4 * P.m_max + 3 * P.m_max;
-    int* rk = P.trk + slot * P.max_rot;
-    df* rc = reinterpret_cast<df*>(P.trc + slot * P.max_rot);
-    df* rs = reinterpret_cast<df*>(P.trs + slot * P.max_rot);
+    double* scr = P.sv_w + (size_t)wid * tridiag_warp_scratch_doubles(P.m_max);
     // idle wait: bounded by spin_limit cycles without any sign of progress of
     // the main CTAs (barrier generation, item tickets, posted requests)
     unsigned hb_bar = 0;
-    unsigned long long hb_ticket = 0, hb_tail = 0, last_tail = ~0ull;
+    unsigned long long hb_ticket = 0, hb_tail = 0;
     long long t0 = clock64();
     while (true) {
         unsigned long long first = 0;
         int n = 0, quit = 0;
         if (lane == 0) {
-            // take kSolverWidth requests, or fewer once posting has paused for a
-            // poll interval
             const unsigned long long h = vload(&P.q_ctr[0]);
             const unsigned long long t = vload(&P.q_ctr[1]);
-            if (t >= h + (unsigned long long)kSolverWidth || (t > h && t == last_tail)) {
-                const int want = (int)min((unsigned long long)kSolverWidth, t - h);
-                if (atomicCAS(&P.q_ctr[0], h, h + (unsigned long long)want) == h) { n = want; first = h; }
+            if (t > h && atomicCAS(&P.q_ctr[0], h, h + 1ull) == h) {
+                n = 1;
+                first = h;
             }
-            last_tail = t;
             if (n == 0) {
                 if (*(volatile int*)P.main_done || *(volatile int*)P.err != kBatchOk) {
                     quit = 1;
@@ -553,8 +577,7 @@ __device__ void solver_loop(const BatchParams& P) {
             __nanosleep(256);
             continue;
         }
-        if (lane < n) serve_request(P, first + (unsigned long long)lane, d, e, r, z, rk, rc, rs);
-        __syncwarp();
+        serve_request(P, first, lane, wid, scr);
         if (lane == 0) t0 = clock64();
     }
 }
@@ -1061,16 +1084,34 @@ __global__ void timeout_probe_kernel(BatchParams P) {
 }
 
 // One thread per system: out = sqrt(T) e1 with the device tridiagonal step.
-__global__ void tridiag_dev_kernel(int count, int m, const double* alpha, const double* beta, double* scratch,
-                                   int* rk, double* rc, double* rs, int max_rot, double* out, int* status) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= count) return;
-    df* d = reinterpret_cast<df*>(scratch + (size_t)t * 3 * m);
-    const int rcode = tridiag_sqrt_e1_df<1>(m, alpha + (size_t)t * m, beta + (size_t)t * m, d, d + m, d + 2 * m,
-                                            rk + (size_t)t * max_rot, reinterpret_cast<df*>(rc + (size_t)t * max_rot),
-                                            reinterpret_cast<df*>(rs + (size_t)t * max_rot), max_rot,
-                                            out + (size_t)t * m);
-    if (rcode != 0) atomicCAS(status, 0, rcode);
+// One warp per system: the warp form of the tridiagonal step, the QR form on
+// lane 0 where it declines (path[c] = 1), exactly as the solver warps of the
+// batched kernel run it.
+__global__ void tridiag_warp_kernel(int count, int m, const double* alpha, const double* beta, double* scratch,
+                                    int* rk, double* rc, double* rs, int max_rot, double* out, int* status,
+                                    int* path) {
+    const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= count) return;   // whole warps
+    double* scr = scratch + (size_t)w * tridiag_warp_scratch_doubles(m);
+    const double* al = alpha + (size_t)w * m;
+    const double* be = beta + (size_t)w * m;
+    double* o = out + (size_t)w * m;
+    int rcode = tridiag_sqrt_e1_warp(m, m, al, be, scr, o, lane);
+    const int qr = rcode == 1;
+    if (qr) {
+        if (lane == 0) {
+            df* d = reinterpret_cast<df*>(scr + 5 * (size_t)m);
+            rcode = tridiag_sqrt_e1_df<1>(m, al, be, d, d + m, d + 2 * m, rk + (size_t)w * max_rot,
+                                          reinterpret_cast<df*>(rc + (size_t)w * max_rot),
+                                          reinterpret_cast<df*>(rs + (size_t)w * max_rot), max_rot, o);
+        }
+        rcode = __shfl_sync(0xffffffffu, rcode, 0);
+    }
+    if (lane == 0) {
+        if (rcode != 0) atomicCAS(status, 0, rcode);
+        if (path != nullptr) path[w] = qr;
+    }
 }
 
 template <int NT, int NI>
@@ -1132,9 +1173,10 @@ cudaError_t launch_batch_unpack(const double* x64, int64_t N, float* out, cudaSt
 }
 
 cudaError_t launch_tridiag_dev(int count, int m, const double* alpha, const double* beta, double* scratch, int* rk,
-                               double* rc, double* rs, int max_rot, double* out, int* status, cudaStream_t s) {
-    tridiag_dev_kernel<<<(count + 127) / 128, 128, 0, s>>>(count, m, alpha, beta, scratch, rk, rc, rs, max_rot, out,
-                                                           status);
+                               double* rc, double* rs, int max_rot, double* out, int* status, int* path,
+                               cudaStream_t s) {
+    tridiag_warp_kernel<<<(count + 3) / 4, 128, 0, s>>>(count, m, alpha, beta, scratch, rk, rc, rs, max_rot, out,
+                                                        status, path);
     count_launches(1);
     return cudaGetLastError();
 }

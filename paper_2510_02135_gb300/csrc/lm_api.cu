@@ -1865,9 +1865,9 @@ lm_status lm_batch_create(lm_batch** out, int64_t S, const int64_t* offsets, dou
         wtot += ((n + lmk::kBatchJPart - 1) / lmk::kBatchJPart) * 3 * n;
     }
     b->max_rot = (int)(4 * M * M + 64);
-    // solver slots: kSolverWidth per solver warp (CTAs of 64 or 128 threads
-    // hold whole warps: kSolverWarps is a multiple of 4)
-    const size_t lanes = (size_t)lmk::kSolverWarps * lmk::kSolverWidth;
+    // one solver slot per solver warp (CTAs of 64 or 128 threads hold whole
+    // warps: kSolverWarps is a multiple of 4)
+    const size_t lanes = (size_t)lmk::kSolverWarps;
     b->solver_lanes = (int)lanes;
     b->q_cap = 16384;
     struct { DBuf* buf; size_t bytes; } allocs[] = {
@@ -1882,7 +1882,7 @@ lm_status lm_batch_create(lm_batch** out, int64_t S, const int64_t* offsets, dou
         {&b->nact, (M + 1) * sizeof(int)}, {&b->chunks, chunks.size() * sizeof(int)},
         {&b->chunk_range, crange.size() * sizeof(int)},
         {&b->part_chunk, 2 * (size_t)b->n_chunks * (M + 1) * sizeof(double)},
-        {&b->sv_w, lanes * 4 * M * sizeof(double)}, {&b->trk, lanes * (size_t)b->max_rot * sizeof(int)},
+        {&b->sv_w, lanes * lmk::tridiag_warp_scratch_doubles((int)M) * sizeof(double)}, {&b->trk, lanes * (size_t)b->max_rot * sizeof(int)},
         {&b->trc, lanes * (size_t)b->max_rot * sizeof(double)}, {&b->trs, lanes * (size_t)b->max_rot * sizeof(double)},
         {&b->q_req, (size_t)b->q_cap * sizeof(long long)}, {&b->q_seq, (size_t)b->q_cap * sizeof(unsigned long long)},
         {&b->q_ack, (size_t)b->q_cap * sizeof(unsigned long long)}, {&b->q_ctr, 4 * sizeof(unsigned long long)},
@@ -2155,8 +2155,8 @@ lm_status lm_batch_profile_read(lm_batch* b, uint64_t* out, int n, int* count) {
     return LM_OK;
 }
 
-lm_status lm_tridiag_sqrt_e1_device(int count, int m, const double* alpha, const double* beta, double* out,
-                                    void* cuda_stream) {
+lm_status lm_tridiag_sqrt_e1_device_paths(int count, int m, const double* alpha, const double* beta, double* out,
+                                          int* paths, void* cuda_stream) {
     g_err.clear();
     if (count < 0 || m < 1 || m > 128) return fail(LM_ERR_INVALID_ARG, "need count >= 0 and 1 <= m <= 128");
     if (count == 0) return LM_OK;
@@ -2166,21 +2166,29 @@ lm_status lm_tridiag_sqrt_e1_device(int count, int m, const double* alpha, const
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const int max_rot = 4 * m * m + 64;
     const size_t C = (size_t)count;
-    DBuf scr, rk, rc, rs, status;
-    LM_CUDA(scr.ensure(C * 3 * m * sizeof(double)), "tridiagonal scratch");
+    DBuf scr, rk, rc, rs, status, path;
+    LM_CUDA(scr.ensure(C * lmk::tridiag_warp_scratch_doubles(m) * sizeof(double)), "tridiagonal scratch");
     LM_CUDA(rk.ensure(C * max_rot * sizeof(int)), "tridiagonal scratch");
     LM_CUDA(rc.ensure(C * max_rot * sizeof(double)), "tridiagonal scratch");
     LM_CUDA(rs.ensure(C * max_rot * sizeof(double)), "tridiagonal scratch");
     LM_CUDA(status.ensure(sizeof(int)), "tridiagonal scratch");
+    if (paths) LM_CUDA(path.ensure(C * sizeof(int)), "tridiagonal scratch");
     LM_CUDA(cudaMemsetAsync(status.p, 0, sizeof(int), st), "tridiagonal status");
     LM_CUDA(lmk::launch_tridiag_dev(count, m, alpha, beta, scr.as<double>(), rk.as<int>(), rc.as<double>(),
-                                    rs.as<double>(), max_rot, out, status.as<int>(), st),
+                                    rs.as<double>(), max_rot, out, status.as<int>(),
+                                    paths ? path.as<int>() : nullptr, st),
             "tridiagonal kernel");
     int h = 0;
     LM_CUDA(cudaMemcpyAsync(&h, status.p, sizeof(int), cudaMemcpyDeviceToHost, st), "tridiagonal status");
+    if (paths) LM_CUDA(cudaMemcpyAsync(paths, path.p, C * sizeof(int), cudaMemcpyDeviceToHost, st), "tridiagonal paths");
     LM_CUDA(cudaStreamSynchronize(st), "tridiagonal kernel");
     if (h != 0) return fail(LM_ERR_CUDA, "device tridiagonal step failed (code %d)", h);
     return LM_OK;
+}
+
+lm_status lm_tridiag_sqrt_e1_device(int count, int m, const double* alpha, const double* beta, double* out,
+                                    void* cuda_stream) {
+    return lm_tridiag_sqrt_e1_device_paths(count, m, alpha, beta, out, nullptr, cuda_stream);
 }
 
 lm_status lm_batch_solve_counts(lm_batch* b, int64_t* posted, int64_t* solved) {

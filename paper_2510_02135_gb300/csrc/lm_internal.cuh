@@ -285,8 +285,15 @@ constexpr int kBarGroup = 32;
 constexpr int kBarStride = 32;
 constexpr int kBarMaxGroups = 256;
 constexpr size_t kBarWords = (size_t)kBarStride * (1 + kBarMaxGroups);
-constexpr int kSolverWidth = 2;        // requests a solver warp serves at once
-constexpr int kSolverWarps = 64;       // solver warps of a batched launch
+constexpr int kSolverWarps = 64;       // solver warps of a batched launch (one request each at a time)
+
+// Scratch of the warp form of the tridiagonal step f(T) e1 in doubles, for
+// T of at most m_max rows: d, b, b^2, u as double-float (4 m_max), z (m_max),
+// the lanes' reciprocal pivots and partial sums (2 x 32 m_max double-float,
+// lane-interleaved).  The QR fallback uses the pivot region for its d, e, r.
+__host__ __device__ constexpr size_t tridiag_warp_scratch_doubles(int m_max) {
+    return (size_t)69 * (size_t)m_max;
+}
 
 struct BatchParams {
     int S, m_max, mode, nsteps;
@@ -327,13 +334,13 @@ struct BatchParams {
     double* part_item;                 // n_items partial dots
     double* part_chunk;                // 2 x n_chunks x (m_max + 1) partial dots
     // Asynchronous tridiagonal solves.  CTAs [n_main, gridDim.x) are solver
-    // CTAs: lanes [0, kSolverWidth) of each of their warps serve one request
-    // each (solver slot = warp * kSolverWidth + lane), with contiguous scratch.
+    // CTAs: each of their warps serves one request at a time with all its
+    // lanes (tridiag_sqrt_e1_warp; the QR form on lane 0 where that declines).
     int n_main;                        // CTAs that run the phases and the grid barrier
-    double* sv_w;                      // per slot: d, e, r (double-float), z (4 x m_max doubles)
-    int* trk;                          // per slot: max_rot rotation indices
-    double* trc;                       // per slot: max_rot rotation cosines (double-float)
-    double* trs;                       // per slot: max_rot rotation sines (double-float)
+    double* sv_w;                      // per solver warp: tridiag_warp_scratch_doubles(m_max) doubles
+    int* trk;                          // per solver warp: max_rot rotation indices (QR fallback)
+    double* trc;                       // per solver warp: max_rot rotation cosines (double-float)
+    double* trs;                       // per solver warp: max_rot rotation sines (double-float)
     int max_rot;
     long long* q_req;                  // request ring: (step << 28) | (system << 7) | k
     unsigned long long* q_seq;         // ticket + 1 once the slot holds that ticket's request
@@ -380,7 +387,8 @@ cudaError_t launch_batch_unpack(const double* x64, int64_t N, float* out, cudaSt
 // A kernel whose barrier waits for one CTA more than it launches: every
 // wait runs out after spin_limit cycles and *err becomes kBatchTimeout.
 cudaError_t launch_tridiag_dev(int count, int m, const double* alpha, const double* beta, double* scratch, int* rk,
-                               double* rc, double* rs, int max_rot, double* out, int* status, cudaStream_t s);
+                               double* rc, double* rs, int max_rot, double* out, int* status, int* path,
+                               cudaStream_t s);
 cudaError_t launch_batch_timeout_probe(unsigned* bar, int* err, long long spin_limit, int grid,
                                        cudaStream_t s);
 

@@ -164,6 +164,8 @@ def lib():
         L.lm_batch_profile_pairs.restype = st
         L.lm_tridiag_sqrt_e1_device.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]
         L.lm_tridiag_sqrt_e1_device.restype = st
+        L.lm_tridiag_sqrt_e1_device_paths.argtypes = [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]
+        L.lm_tridiag_sqrt_e1_device_paths.restype = st
         L.lm_batch_solve_counts.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
         L.lm_batch_solve_counts.restype = st
         L.lm_batch_timeout_selftest.argtypes = [ctypes.c_longlong]
@@ -548,9 +550,11 @@ def lm_batch_profile_read(b: Batch) -> np.ndarray:
     return out[: c.value]
 
 
-def lm_tridiag_sqrt_e1_device(alpha, beta, out=None, stream=None):
+def lm_tridiag_sqrt_e1_device(alpha, beta, out=None, stream=None, paths=False):
     """sqrt(T_c) e1 for each row c of the (count, m) float64 CUDA tensors alpha,
-    beta (beta[:, :m-1] used) with the device tridiagonal step."""
+    beta (beta[:, :m-1] used) with the device tridiagonal step.  With
+    paths=True also returns an int array: 0 where the quadrature solved T_c,
+    1 where the QR form did."""
     import torch
 
     count, m = alpha.shape
@@ -560,9 +564,10 @@ def lm_tridiag_sqrt_e1_device(alpha, beta, out=None, stream=None):
     if out is None:
         out = torch.empty_like(alpha)
     cs = stream if stream is not None else torch.cuda.current_stream().cuda_stream
-    _check(lib().lm_tridiag_sqrt_e1_device(int(count), int(m), alpha.data_ptr(), beta.data_ptr(), out.data_ptr(),
-                                           cs))
-    return out
+    pth = np.zeros(max(int(count), 1), dtype=np.int32) if paths else None
+    _check(lib().lm_tridiag_sqrt_e1_device_paths(int(count), int(m), alpha.data_ptr(), beta.data_ptr(),
+                                                 out.data_ptr(), pth.ctypes.data if paths else None, cs))
+    return (out, pth[: int(count)]) if paths else out
 
 
 def lm_batch_solve_counts(b: Batch):
