@@ -461,7 +461,9 @@ lm_status lm_batch_bd_run(lm_batch *batch, double kT, double dt, double k_trap, 
 /*
  * Pair tiling of the batched launches: threads per CTA (64 or 128) and
  * i-particles per thread (1 or 2); picked by lm_batch_autotune (timing a
- * product over all systems) or set by hand.
+ * batched square root, Philox noise at tol 1e-4, over all systems: the
+ * products, vector phases and tridiagonal solves of a Brownian step; the
+ * systems' warm-start iteration counts are kept) or set by hand.
  */
 lm_status lm_batch_set_tiling(lm_batch *batch, int threads, int ilp);
 lm_status lm_batch_set_reorthogonalization(lm_batch *batch, int mode);

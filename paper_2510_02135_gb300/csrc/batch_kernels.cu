@@ -192,37 +192,35 @@ __device__ void pair_item(const BatchParams& P, int s, int i0, int jb, int je, c
         if constexpr (NRHS == 2) { bx[tid] = nj[6]; by[tid] = nj[7]; bz[tid] = nj[8]; }
         __syncthreads();
         if (jt + NT < je) fetch(jt + NT + tid);
-        for (int jj = 0; jj < NT; jj += 2) {
-            const float2 xj = *reinterpret_cast<const float2*>(tx + jj);
-            const float2 yj = *reinterpret_cast<const float2*>(ty + jj);
-            const float2 zj = *reinterpret_cast<const float2*>(tz + jj);
-            const float2 fx = *reinterpret_cast<const float2*>(ax + jj);
-            const float2 fy = *reinterpret_cast<const float2*>(ay + jj);
-            const float2 fz = *reinterpret_cast<const float2*>(az + jj);
-            float2 gx, gy, gz;
-            if (NRHS == 2) {
-                gx = *reinterpret_cast<const float2*>(bx + jj);
-                gy = *reinterpret_cast<const float2*>(by + jj);
-                gz = *reinterpret_cast<const float2*>(bz + jj);
-            }
-            float2 dx[NI], dy[NI], dz[NI], r2[NI];
+        static_assert(NT % 4 == 0, "the j tile holds whole groups of four");
+        // two j-pairs (four j) per overlap vote: two independent packed chains
+        // per i-particle; a slot (one i against one j-pair) that holds an
+        // overlapping or self pair takes the exact scalar coefficients
+        for (int jj = 0; jj < NT; jj += 4) {
+            float2 dx[2][NI], dy[2][NI], dz[2][NI], r2[2][NI];
             float mn = 0.f;
 #pragma unroll
-            for (int q = 0; q < NI; ++q) {
-                dx[q] = __fadd2_rn(xj, xi[q]); dy[q] = __fadd2_rn(yj, yi[q]); dz[q] = __fadd2_rn(zj, zi[q]);
-                r2[q] = __ffma2_rn(dx[q], dx[q], __ffma2_rn(dy[q], dy[q], __fmul2_rn(dz[q], dz[q])));
-                const float m2 = fminf(r2[q].x, r2[q].y);
-                mn = (q == 0) ? m2 : fminf(mn, m2);
-            }
-            const bool near = __any_sync(0xffffffffu, mn < k.four_a2);
+            for (int u = 0; u < 2; ++u) {
+                const int j2 = jj + 2 * u;
+                const float2 xj = *reinterpret_cast<const float2*>(tx + j2);
+                const float2 yj = *reinterpret_cast<const float2*>(ty + j2);
+                const float2 zj = *reinterpret_cast<const float2*>(tz + j2);
 #pragma unroll
-            for (int q = 0; q < NI; ++q) {
+                for (int q = 0; q < NI; ++q) {
+                    dx[u][q] = __fadd2_rn(xj, xi[q]); dy[u][q] = __fadd2_rn(yj, yi[q]); dz[u][q] = __fadd2_rn(zj, zi[q]);
+                    r2[u][q] = __ffma2_rn(dx[u][q], dx[u][q], __ffma2_rn(dy[u][q], dy[u][q], __fmul2_rn(dz[u][q], dz[u][q])));
+                    const float m2 = fminf(r2[u][q].x, r2[u][q].y);
+                    mn = (u == 0 && q == 0) ? m2 : fminf(mn, m2);
+                }
+            }
+            auto slot = [&](int u, int q, bool exact) {
+                const int j2 = jj + 2 * u;
                 float2 A, B;
-                if (near) {
+                if (exact) {
                     float a_[2], b_[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const float rr = h ? r2[q].y : r2[q].x;
+                        const float rr = h ? r2[u][q].y : r2[u][q].x;
                         if (rr < k.four_a2) {
                             const float invr = (rr > 0.f) ? rsqrtf(rr) : 0.f;
                             const float r = rr * invr;
@@ -239,21 +237,42 @@ __device__ void pair_item(const BatchParams& P, int s, int i0, int jb, int je, c
                     A = make_float2(a_[0], a_[1]);
                     B = make_float2(b_[0], b_[1]);
                 } else {
-                    const float2 invr = make_float2(rsqrtf(r2[q].x), rsqrtf(r2[q].y));
+                    const float2 invr = make_float2(rsqrtf(r2[u][q].x), rsqrtf(r2[u][q].y));
                     const float2 invr2 = __fmul2_rn(invr, invr);
                     const float2 invr3 = __fmul2_rn(invr2, invr);
                     A = __ffma2_rn(K1, invr3, invr);
                     B = __ffma2_rn(nK2, __fmul2_rn(invr3, invr2), invr3);
                 }
-                const float2 sa_ = __fmul2_rn(B, __ffma2_rn(dx[q], fx, __ffma2_rn(dy[q], fy, __fmul2_rn(dz[q], fz))));
-                pA[q][0] = __ffma2_rn(sa_, dx[q], __ffma2_rn(A, fx, pA[q][0]));
-                pA[q][1] = __ffma2_rn(sa_, dy[q], __ffma2_rn(A, fy, pA[q][1]));
-                pA[q][2] = __ffma2_rn(sa_, dz[q], __ffma2_rn(A, fz, pA[q][2]));
-                if (NRHS == 2) {
-                    const float2 sb_ = __fmul2_rn(B, __ffma2_rn(dx[q], gx, __ffma2_rn(dy[q], gy, __fmul2_rn(dz[q], gz))));
-                    pB[q][0] = __ffma2_rn(sb_, dx[q], __ffma2_rn(A, gx, pB[q][0]));
-                    pB[q][1] = __ffma2_rn(sb_, dy[q], __ffma2_rn(A, gy, pB[q][1]));
-                    pB[q][2] = __ffma2_rn(sb_, dz[q], __ffma2_rn(A, gz, pB[q][2]));
+                const float2 fx = *reinterpret_cast<const float2*>(ax + j2);
+                const float2 fy = *reinterpret_cast<const float2*>(ay + j2);
+                const float2 fz = *reinterpret_cast<const float2*>(az + j2);
+                const float2 ddx = dx[u][q], ddy = dy[u][q], ddz = dz[u][q];
+                const float2 sa_ = __fmul2_rn(B, __ffma2_rn(ddx, fx, __ffma2_rn(ddy, fy, __fmul2_rn(ddz, fz))));
+                pA[q][0] = __ffma2_rn(sa_, ddx, __ffma2_rn(A, fx, pA[q][0]));
+                pA[q][1] = __ffma2_rn(sa_, ddy, __ffma2_rn(A, fy, pA[q][1]));
+                pA[q][2] = __ffma2_rn(sa_, ddz, __ffma2_rn(A, fz, pA[q][2]));
+                if constexpr (NRHS == 2) {
+                    const float2 gx = *reinterpret_cast<const float2*>(bx + j2);
+                    const float2 gy = *reinterpret_cast<const float2*>(by + j2);
+                    const float2 gz = *reinterpret_cast<const float2*>(bz + j2);
+                    const float2 sb_ = __fmul2_rn(B, __ffma2_rn(ddx, gx, __ffma2_rn(ddy, gy, __fmul2_rn(ddz, gz))));
+                    pB[q][0] = __ffma2_rn(sb_, ddx, __ffma2_rn(A, gx, pB[q][0]));
+                    pB[q][1] = __ffma2_rn(sb_, ddy, __ffma2_rn(A, gy, pB[q][1]));
+                    pB[q][2] = __ffma2_rn(sb_, ddz, __ffma2_rn(A, gz, pB[q][2]));
+                }
+            };
+            if (__any_sync(0xffffffffu, mn < k.four_a2)) {
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+#pragma unroll
+                    for (int q = 0; q < NI; ++q)
+                        slot(u, q, __any_sync(0xffffffffu, fminf(r2[u][q].x, r2[u][q].y) < k.four_a2));
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+#pragma unroll
+                    for (int q = 0; q < NI; ++q) slot(u, q, false);
                 }
             }
         }

@@ -2080,9 +2080,7 @@ lm_status lm_batch_autotune(lm_batch* b, int* threads_out, int* ilp_out) {
     if (lm_status st = check_batch(b, true)) return st;
     DeviceGuard g(b->device);
     const size_t bytes = (size_t)b->Ntot * 3 * sizeof(float);
-    LM_CUDA(b->in_stage.ensure(bytes), "autotune buffers");
     LM_CUDA(b->out_stage.ensure(bytes), "autotune buffers");
-    LM_CUDA(cudaMemsetAsync(b->in_stage.p, 0, bytes, b->stream), "autotune buffers");
     const int opts[4][2] = {{64, 1}, {64, 2}, {128, 1}, {128, 2}};
     float best = 1e30f;
     int bt = b->threads, bi = b->ilp;
@@ -2090,10 +2088,22 @@ lm_status lm_batch_autotune(lm_batch* b, int* threads_out, int* ilp_out) {
     LM_CUDA(cudaEventCreate(&e0), "autotune");
     LM_CUDA(cudaEventCreate(&e1), "autotune");
     lm_status result = LM_OK;
+    // each tiling times a batched square root (Philox noise, tol 1e-4): the
+    // products, the vector phases and the solves of a Brownian step, whose
+    // best tilings differ (the vector phases favour more, smaller CTAs).  The
+    // solves overwrite the systems' warm-start counts: kept and put back.
+    DBuf kprev_keep;
+    LM_CUDA(kprev_keep.ensure((size_t)b->S * sizeof(int)), "autotune buffers");
+    LM_CUDA(cudaMemcpyAsync(kprev_keep.p, b->kprev.p, (size_t)b->S * sizeof(int), cudaMemcpyDeviceToDevice,
+                            b->stream),
+            "autotune buffers");
     for (auto& o : opts) {
         if ((result = lm_batch_set_tiling(b, o[0], o[1])) != LM_OK) break;
-        lmk::BatchParams p = batch_params(b, lmk::kBatchMdot);
-        p.F_in = b->in_stage.as<float>();
+        lmk::BatchParams p = batch_params(b, lmk::kBatchSqrt);
+        p.W_in = nullptr;
+        p.seed = 0x5eedull;
+        p.tol = 1e-4;
+        p.prefactor = 1.0;
         p.lin_out = b->out_stage.as<float>();
         if ((result = batch_run(b, p, false)) != LM_OK) break;  // warm-up
         cudaEventRecord(e0, b->stream);
@@ -2106,6 +2116,10 @@ lm_status lm_batch_autotune(lm_batch* b, int* threads_out, int* ilp_out) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    LM_CUDA(cudaMemcpyAsync(b->kprev.p, kprev_keep.p, (size_t)b->S * sizeof(int), cudaMemcpyDeviceToDevice,
+                            b->stream),
+            "autotune buffers");
+    LM_CUDA(cudaStreamSynchronize(b->stream), "autotune");
     if (result != LM_OK) return result;
     if (lm_status st = lm_batch_set_tiling(b, bt, bi)) return st;
     if (threads_out) *threads_out = bt;
