@@ -13,12 +13,17 @@
 //                  loading (and stored for the own rows); partial v_k . w
 //     C2  chunks   w = sum of the j-parts; alpha_k = sum of the item partials;
 //                  w -= alpha_k v_k + beta_{k-1} v_{k-1}; dots V_s^T w
-//     C3  chunks   w -= V_s c; dots V_s^T w; |w|^2 before and after the pass
-//     C4  chunks   w -= V_s c' only if |w| fell below 1/sqrt(2) of its value
-//                  before C3 (DGKS); |w|^2 partials
-//     C5  systems  beta_k; z_k = |W| f(T_k) e1 (implicit QR, FP64); stopping rule
-//                  (in BD runs the relative-change test is first made one
-//                  iteration before the count of the system's previous step)
+//     C3  chunks   w -= V_s c; |w|^2 after the pass.  The system's last chunk
+//                  makes the DGKS test (|w| below 1/sqrt(2) of its value
+//                  before C3) and, without a second pass, ends the iteration:
+//                  beta_k, a solve request for z_k = |W| f(T_k) e1 (served by
+//                  the solver warps), the stopping rule on the results that
+//                  have arrived (in BD runs the relative-change test is first
+//                  made one iteration before the count of the system's
+//                  previous step)
+//     C4  chunks   only if some system needs it: dots V_s^T w, then
+//                  w -= V_s c', |w|^2, and the end of the iteration by the
+//                  last chunk of each such system
 //   D   chunks   y = V_s z; x += dt u + sqrt(2 kT dt) y
 // Phases are separated by a grid barrier whose waits are bounded in clock
 // cycles: an expired wait sets an error flag and every CTA returns.
@@ -403,6 +408,15 @@ __device__ __forceinline__ double warp_range_sum(const double* base, int64_t str
     return warp_sum_d(t);
 }
 
+// The same sum through L2 (partials that other CTAs wrote since the last
+// grid barrier).
+__device__ __forceinline__ double warp_range_sum_cg(const double* base, int64_t stride, int cb, int ce) {
+    const int lane = threadIdx.x & 31;
+    double t = 0.0;
+    for (int c = cb + lane; c < ce; c += 32) t += __ldcg(base + (int64_t)c * stride);
+    return warp_sum_d(t);
+}
+
 // cvec[j] = sum over the chunks of system s of part[c][j], j < nrows.  With
 // few rows, G = NT / nrows threads (a power of two, at most 8) share a row
 // and combine their partial sums by a butterfly; the order depends only on
@@ -659,6 +673,34 @@ __device__ bool post_due(const BatchParams& P, int s, uint64_t gstep, int kmax) 
     return true;
 }
 
+// End of Lanczos iteration k of system s (one thread, once per iteration:
+// the thread that closed the system's last chunk), with b2 = |w|^2 after the
+// reorthogonalisation: beta_k, breakdown and max_iter, the stopping rule on
+// the results that have arrived, the due solve requests, and the count of
+// systems that iterate on.  Warm start (BD mode): with kprev the iteration
+// count of the system's previous step, solves begin at (0-based) iteration
+// k0 = kprev - 3 and the relative-change test one iteration later, at the
+// count kprev - 1 (one below the previous count, so that counts can also
+// fall), since counts change little from one step to the next; breakdown and
+// max_iter end the iteration at once.  A system keeps iterating while its
+// results are pending; iterations past its stopping point are discarded.
+__device__ void end_iteration(const BatchParams& P, int s, int k, uint64_t gstep, double b2) {
+    const double b = sqrt(b2);
+    P.beta[s * P.m_max + k] = b;
+    const int m = k + 1;
+    const bool breakdown = b <= P.brk_rel * __ldcg(P.amax + s);
+    const bool last = (m == P.m_max);
+    if (breakdown || last) {
+        if (k < P.k0s[s]) P.k0s[s] = k;   // the last iteration is always solved
+        P.state[s] = breakdown ? 3 : 2;
+        P.last_k[s] = k;
+        P.active[s] = 0;
+    }
+    if (evaluate_results(P, s, gstep, k)) return;
+    if (!post_due(P, s, gstep, k)) return;   // a timeout: the error flag is set
+    if (P.state[s] == 1) atomicAdd(&P.nact[k + 1], 1);
+}
+
 // Evaluate and post for system s (states 2, 3: iteration ended) until it
 // stops.  The wait is bounded by spin_limit cycles without a finished
 // request.  Returns false on a timeout or an error.
@@ -687,6 +729,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
     __shared__ double sred[NT / 32];
     __shared__ double cvec[129];
     __shared__ unsigned long long s_ticket;
+    __shared__ int s_last;
     const int tid = threadIdx.x;
     const int G = P.n_main;
     const int per_item = NT * NI;
@@ -759,7 +802,10 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
         stamp(P, step, slot);
         // ---- A1: noise, forces, |W|^2 partials
         if (blockIdx.x == 0) {
-            for (int k = tid; k <= P.m_max; k += NT) P.nact[k] = 0;
+            for (int k = tid; k <= P.m_max; k += NT) {
+                P.nact[k] = 0;
+                P.pass2[k] = 0;
+            }
             if (tid == 0) {
                 atomicExch((unsigned long long*)P.cur_step, (unsigned long long)gstep);
                 // requests of two steps ago (same result-ring parity) all finished:
@@ -809,6 +855,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                 for (int w = 0; w < NT / 32; ++w) t += sred[w];
                 partA[(int64_t)c * M1] = t;
                 if (e0 == 0) {
+                    P.sys_cnt[s] = 0;
                     P.amax[s] = 0.0;
                     P.active[s] = 1;
                     P.state[s] = 1;
@@ -907,13 +954,20 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
             }
             if (!grid_sync(P)) return;
             stamp(P, step, slot);
-            // C3: first Gram-Schmidt pass and |w|^2 after it.
-            // C4: second pass only if |w| dropped below |w_before| / sqrt(2)
-            //     (DGKS criterion): its dots, computed only for the systems that
-            //     need them (C4a), then the subtraction and the |w|^2 partials
-            //     for beta (C4b).
+            // C3: first Gram-Schmidt pass and |w|^2 after it.  The CTA that
+            // finishes a system's last chunk makes the system's DGKS test: a
+            // system that needs no second pass (the usual case) ends its
+            // iteration there (end_iteration), the others raise pass2[k].
+            // C4, only when pass2[k] is set: the second pass of the systems whose
+            // |w| dropped below |w_before| / sqrt(2): its dots (C4a), then the
+            // subtraction and the |w|^2 partials, and the end of the iteration by
+            // each such system's last chunk (C4b).
             for (int pass = 0; pass < 2; ++pass) {
                 if (pass == 1) {
+                    if (*(volatile int*)&P.pass2[k] == 0) {
+                        stamp(P, step, slot);
+                        break;
+                    }
                     for (int c = blockIdx.x; c < P.n_chunks; c += G) {
                         const int s = P.chunks[2 * c], e0 = P.chunks[2 * c + 1];
                         if (!P.active[s]) continue;
@@ -937,22 +991,16 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                     const int64_t o = P.off[s];
                     const int ns = 3 * (int)(P.off[s + 1] - o);
                     const int e1 = min(e0 + kBatchChunk, ns);
-                    bool apply = true;
+                    const int cb = P.chunk_range[2 * s], ce = P.chunk_range[2 * s + 1];
                     if (pass == 1) {
-                        const int cb = P.chunk_range[2 * s], ce = P.chunk_range[2 * s + 1];
                         const double h0 = warp_range_sum(partA + P.m_max, M1, cb, ce);
                         const double h1 = warp_range_sum(partB + P.m_max, M1, cb, ce);
-                        apply = P.reorth || h1 < 0.5 * h0;   // squared norms: |w1| < |w0| / sqrt(2)
-                        if (!apply) {
-                            // w unchanged: its norm partial is the first pass's, bit for bit
-                            if (tid == 0) pout[(int64_t)c * M1] = pin[(int64_t)c * M1 + P.m_max];
-                            continue;
-                        }
+                        if (!(P.reorth || h1 < 0.5 * h0)) continue;   // squared norms: |w1| < |w0| / sqrt(2)
                     }
                     double* w = wcur + 3 * o;
                     const double* V0 = basis(P, s, 0);
                     double nrm = 0.0;
-                    if (apply) chunk_sum_coeffs<NT>(P, s, pin, k + 1, cvec);
+                    chunk_sum_coeffs<NT>(P, s, pin, k + 1, cvec);
                     // the thread's kBatchChunk / NT elements advance together:
                     // independent FP64 chains and loads in flight per row
                     static_assert(kBatchChunk % NT == 0, "a chunk is a whole number of elements per thread");
@@ -963,16 +1011,14 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                         const int e = e0 + tid + q * NT;
                         acc[q] = (e < e1) ? w[e] : 0.0;
                     }
-                    if (apply) {
 #pragma unroll 2
-                        for (int j = 0; j <= k; ++j) {
-                            const double cj = cvec[j];
-                            const double* vj = V0 + (int64_t)j * ns;
+                    for (int j = 0; j <= k; ++j) {
+                        const double cj = cvec[j];
+                        const double* vj = V0 + (int64_t)j * ns;
 #pragma unroll
-                            for (int q = 0; q < EPT; ++q) {
-                                const int e = e0 + tid + q * NT;
-                                if (e < e1) acc[q] = fma(-cj, vj[e], acc[q]);
-                            }
+                        for (int q = 0; q < EPT; ++q) {
+                            const int e = e0 + tid + q * NT;
+                            if (e < e1) acc[q] = fma(-cj, vj[e], acc[q]);
                         }
                     }
 #pragma unroll
@@ -991,43 +1037,32 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                         double t = 0.0;
                         for (int ww = 0; ww < NT / 32; ++ww) t += sred[ww];
                         pout[(int64_t)c * M1 + (pass == 0 ? P.m_max : 0)] = t;
+                        // the system's last chunk of this pass (its partials are all written)
+                        __threadfence();
+                        s_last = atomicAdd(&P.sys_cnt[s], 1) == ce - cb - 1;
+                        if (s_last) P.sys_cnt[s] = 0;
+                    }
+                    __syncthreads();
+                    if (s_last && tid < 32) {
+                        __threadfence();
+                        if (pass == 0) {
+                            const double h0 = warp_range_sum_cg(partA + P.m_max, M1, cb, ce);
+                            const double h1 = warp_range_sum_cg(partB + P.m_max, M1, cb, ce);
+                            if (tid == 0) {
+                                if (P.reorth || h1 < 0.5 * h0) atomicExch(&P.pass2[k], 1);
+                                else end_iteration(P, s, k, gstep, h1);   // w unchanged: beta from the first pass
+                            }
+                        } else {
+                            const double b2 = warp_range_sum_cg(partA, M1, cb, ce);
+                            if (tid == 0) end_iteration(P, s, k, gstep, b2);
+                        }
                     }
                     __syncthreads();
                 }
                 if (!grid_sync(P)) return;
                 stamp(P, step, slot);
             }
-            // C5: beta_k, solve request, stopping rule on the results that have
-            // arrived (one thread per system).  Warm start (BD mode): with kprev
-            // the iteration count of the system's previous step, solves begin at
-            // (0-based) iteration k0 = kprev - 3 and the relative-change test one
-            // iteration later, at the count kprev - 1 (one below the previous
-            // count, so that counts can also fall), since counts change little
-            // from one step to the next; breakdown and max_iter end the iteration
-            // at once.  A system keeps iterating while its results are pending;
-            // iterations past its stopping point are discarded.
-            for (int s = blockIdx.x; s < P.S; s += G) {
-                // warp 0 adds the system's norm partials, then its lane 0 goes on alone
-                if (tid >= 32 || P.state[s] != 1) continue;
-                const double b2 = warp_range_sum(partA, M1, P.chunk_range[2 * s], P.chunk_range[2 * s + 1]);
-                if (tid != 0) continue;
-                const double b = sqrt(b2);
-                P.beta[s * P.m_max + k] = b;
-                const int m = k + 1;
-                const bool breakdown = b <= P.brk_rel * P.amax[s];
-                const bool last = (m == P.m_max);
-                if (breakdown || last) {
-                    if (k < P.k0s[s]) P.k0s[s] = k;   // the last iteration is always solved
-                    P.state[s] = breakdown ? 3 : 2;
-                    P.last_k[s] = k;
-                    P.active[s] = 0;
-                }
-                if (evaluate_results(P, s, gstep, k)) continue;
-                if (!post_due(P, s, gstep, k)) break;
-                if (P.state[s] == 1) atomicAdd(&P.nact[k + 1], 1);
-            }
-            if (!grid_sync(P)) return;
-            stamp(P, step, slot);
+            stamp(P, step, slot);   // the end-of-iteration work ran inside C3 / C4
             if (*(volatile int*)&P.nact[k + 1] == 0) break;
         }
         // ---- wait for the last results of every system

@@ -1590,6 +1590,7 @@ struct lm_batch {
     DBuf items, item_range, chunks, chunk_range, part_item, part_chunk, trk, trc, trs, bar, ticket, err, flag;
     DBuf in_stage, out_stage, W_stage;
     // asynchronous tridiagonal solves
+    DBuf pass2, sys_cnt;
     DBuf sv_w, q_req, q_seq, q_ack, q_ctr, inflight, zres, zdone, state, next_check, last_k, k0s, posted, main_done,
         cur_step;
     int solver_lanes = 0, q_cap = 0, R = 32;
@@ -1611,7 +1612,7 @@ struct lm_batch {
         DBuf* all[] = {&off, &pos4, &x64, &Fbuf, &u, &w0, &w1, &V, &alpha, &amax, &beta, &z, &zprev, &normW, &rel,
                        &active, &msys, &itsum, &notconv, &nact, &items, &item_range, &chunks, &chunk_range,
                        &part_item, &part_chunk, &trk, &trc, &trs, &bar, &ticket, &err, &flag, &in_stage,
-                       &out_stage, &W_stage, &sv_w, &q_req, &q_seq, &q_ack, &q_ctr, &inflight, &zres, &zdone,
+                       &out_stage, &W_stage, &pass2, &sys_cnt, &sv_w, &q_req, &q_seq, &q_ack, &q_ctr, &inflight, &zres, &zdone,
                        &state, &next_check, &last_k, &k0s, &posted, &main_done, &cur_step};
         for (DBuf* b : all) b->release();
         if (pinned) cudaFreeHost(pinned);
@@ -1693,6 +1694,8 @@ lmk::BatchParams batch_params(lm_batch* b, int mode) {
     p.warm_start = (mode == lmk::kBatchBD) ? 1 : 0;
     p.reorth = b->reorth;
     p.nact = b->nact.as<int>();
+    p.pass2 = b->pass2.as<int>();
+    p.sys_cnt = b->sys_cnt.as<int>();
     p.items = b->items.as<int>();
     p.n_items = b->n_items;
     p.item_range = b->item_range.as<int>();
@@ -1879,7 +1882,8 @@ lm_status lm_batch_create(lm_batch** out, int64_t S, const int64_t* offsets, dou
         {&b->z, S_ * M * sizeof(double)}, {&b->zprev, S_ * M * sizeof(double)},
         {&b->normW, S_ * sizeof(double)}, {&b->rel, S_ * sizeof(double)}, {&b->active, S_ * sizeof(int)},
         {&b->msys, S_ * sizeof(int)}, {&b->itsum, S_ * sizeof(int)}, {&b->notconv, S_ * sizeof(int)},
-        {&b->nact, (M + 1) * sizeof(int)}, {&b->chunks, chunks.size() * sizeof(int)},
+        {&b->nact, (M + 1) * sizeof(int)}, {&b->pass2, (M + 1) * sizeof(int)}, {&b->sys_cnt, S_ * sizeof(int)},
+        {&b->chunks, chunks.size() * sizeof(int)},
         {&b->chunk_range, crange.size() * sizeof(int)},
         {&b->part_chunk, 2 * (size_t)b->n_chunks * (M + 1) * sizeof(double)},
         {&b->sv_w, lanes * lmk::tridiag_warp_scratch_doubles((int)M) * sizeof(double)}, {&b->trk, lanes * (size_t)b->max_rot * sizeof(int)},
@@ -1900,6 +1904,8 @@ lm_status lm_batch_create(lm_batch** out, int64_t S, const int64_t* offsets, dou
             "chunks");
     LM_CUDA(cudaMemset(b->bar.p, 0, lmk::kBarWords * sizeof(unsigned)), "batch barrier");
     LM_CUDA(cudaMemset(b->kprev.p, 0, S_ * sizeof(int)), "batch history");
+    LM_CUDA(cudaMemset(b->sys_cnt.p, 0, S_ * sizeof(int)), "batch counters");
+    LM_CUDA(cudaMemset(b->pass2.p, 0, (M + 1) * sizeof(int)), "batch counters");
     LM_CUDA(cudaMemcpy(b->woff.p, woff.data(), S_ * sizeof(int64_t), cudaMemcpyHostToDevice), "batch offsets");
     if (lm_status st = batch_build_items(b)) return st;
     LM_CUDA(cudaMallocHost(reinterpret_cast<void**>(&b->pinned), 2 * S_ * sizeof(int)), "batch pinned");

@@ -322,6 +322,8 @@ struct BatchParams {
     int warm_start;                    // 1: start the stopping test near kprev (BD mode)
     int reorth;                        // 1: always run the second Gram-Schmidt pass
     int* nact;                         // m_max + 1 counters of systems still active
+    int* pass2;                        // m_max + 1 flags: some system needs the second Gram-Schmidt pass at k
+    int* sys_cnt;                      // S arrival counters of the chunks of the current pass
     double* wsplit;                    // per-system j-part partial products of w (or F for mdot)
     double* usplit;                    // per-system j-part partial products of u = M F
     const int64_t* woff;               // S: offset of system s in wsplit / usplit (parts x 3 N_s)
