@@ -16,7 +16,7 @@ also reports, at one GPU:
   * "error": the relative L2 error of the timed step's M [F; T] per block
     (u from F, u from T, w from F, w from T) against the FP64 oracle on
     sampled rows (the rows of the CPU-baseline sample);
-  * "c2": the 6N step at N = 32768 (tol 1e-5) with its own roofline and
+  * "rpy6_n32768": the 6N step at N = 32768 (tol 1e-5) with its own roofline and
     per-block errors;
   * "adjoint": forward and backward (dL/dX, dL/dF) times at N = 65536 and
     their ratio;
@@ -662,7 +662,7 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=3.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="headline leg only (no c2 / adjoint / bd256 entries)")
+                    help="headline leg only (no rpy6_n32768 / adjoint / bd256 entries)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -707,16 +707,16 @@ def main():
         del leg[k]
     torch.cuda.empty_cache()
     if ws == 1 and not args.no_extras and args.workload == "melt":
-        c2 = hotpath_leg("rpy6", min(args.steps, 10), 3, None, local, autotune=not args.no_autotune)
+        step2 = hotpath_leg("rpy6", min(args.steps, 10), 3, None, local, autotune=not args.no_autotune)
         if rank == 0 and not args.no_cpu_baseline:
-            _, err2 = cpu_baseline_and_error(c2, 1.0, block_rows=256)
-            c2_sum = _leg_summary(c2)
-            c2_sum["error"] = err2
+            _, err2 = cpu_baseline_and_error(step2, 1.0, block_rows=256)
+            step2_sum = _leg_summary(step2)
+            step2_sum["error"] = err2
         else:
-            c2_sum = _leg_summary(c2)
-        c2_sum["roofline"]["traffic"] = profile_traffic("rpy6")
-        line["c2"] = c2_sum
-        del c2
+            step2_sum = _leg_summary(step2)
+        step2_sum["roofline"]["traffic"] = profile_traffic("rpy6")
+        line["rpy6_n32768"] = step2_sum
+        del step2
         torch.cuda.empty_cache()
         line["adjoint"] = adjoint_leg(10, 3, None, local, autotune=not args.no_autotune)
         torch.cuda.empty_cache()

@@ -157,6 +157,43 @@ def test_batch_forced_second_gram_schmidt_pass(orc):
         lm.lm_batch_set_reorthogonalization(b, 2)
 
 
+def test_batch_sqrt_mixed_breakdown_and_large_systems(orc):
+    """Systems that end almost at once (one particle: W is an eigenvector of M),
+    after a few iterations with round-off residuals (two far-apart particles,
+    three touching ones), next to two suspensions: in one iteration some
+    systems end in the first Gram-Schmidt pass and others may take the DGKS
+    pass, all in the same launch.  Every system matches the exact root and the
+    oracle's iteration count; the forced second pass agrees to rounding."""
+    rng = np.random.default_rng(31)
+    parts = [np.array([[0.3, -0.2, 0.1]]),
+             np.array([[0.0, 0.0, 0.0], [40.0, 5.0, -3.0]]),
+             np.array([[0.0, 0.0, 0.0], [2.0, 0.0, 0.0], [1.0, 1.7, 0.0]]),
+             I.batch_suspensions(3, S=1, nmin=150, nmax=150).pos,
+             I.batch_suspensions(4, S=1, nmin=400, nmax=400).pos]
+    offsets = np.cumsum([0] + [p_.shape[0] for p_ in parts]).astype(np.int64)
+    pos = np.concatenate(parts).astype(np.float32)
+    n = pos.shape[0]
+    W = rng.standard_normal(3 * n)
+    b = lm.lm_batch_create(offsets, 1.0, 1.0, max_iter=100)
+    lm.lm_batch_set_positions(b, dev(pos))
+    tol = 1e-6
+    y0, it0 = lm.lm_batch_sqrt_mdot(b, dev(W), tol=tol)
+    lm.lm_batch_set_reorthogonalization(b, 1)
+    y1, it1 = lm.lm_batch_sqrt_mdot(b, dev(W), tol=tol)
+    y0, y1 = y0.cpu().numpy(), y1.cpu().numpy()
+    for s in range(b.S):
+        o0, o1 = offsets[s], offsets[s + 1]
+        M = orc.assemble(pos[o0:o1].astype(np.float64), 1.0, 1.0, False)
+        ws = W[3 * o0:3 * o1]
+        exact = orc.sqrt_exact(M, ws)
+        # FP32 pairs: the product itself carries about 1e-7 relative error
+        assert rel(y0[o0:o1], exact) <= 20 * tol + 1e-6, (s, rel(y0[o0:o1], exact), it0[s])
+        assert rel(y1[o0:o1], y0[o0:o1]) <= 1e-6, (s, rel(y1[o0:o1], y0[o0:o1]))
+        assert abs(int(it1[s]) - int(it0[s])) <= 1, (s, it0[s], it1[s])
+        _, ito, _ = orc.lanczos_sqrt(lambda v: M @ v, ws, tol=tol, max_iter=100)
+        assert abs(int(it0[s]) - ito) <= 2, (s, it0[s], ito)
+
+
 def test_batch_sqrt_matches_single_system_api(orc):
     b_ = small_batch(seed=13, S=4)
     n = b_.pos.shape[0]
