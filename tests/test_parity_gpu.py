@@ -205,6 +205,29 @@ def test_mdot_melt_n524288_sampled_rows(orc):
         assert np.isfinite(u).all() and np.isfinite(w).all()
 
 
+@pytest.mark.parametrize("n,angular", [(1 << 20, True), (1 << 21, False)])
+def test_mdot_beyond_the_benchmark_sizes_sampled_rows(orc, n, angular):
+    """Sizes above the largest benchmark workload (2^20 particles with all four
+    blocks, 2^21 translation only; random cube at phi = 0.1): 48 sampled rows
+    against the oracle, in the default launch configuration (and, with the
+    angular blocks, in the headline tiling of 256 threads x 8 i-particles with
+    four j per vote).  Indices, split counts and grids are all far from the
+    sizes the smaller tests reach."""
+    s_ = I.cube_suspension(77 + angular, n, 0.1, 1.0, angular=angular, fp32=True)
+    s = make(1.0, 1.0, angular, False, s_.pos)
+    rows = np.random.default_rng(3).choice(n, 48, replace=False)
+    ur, wr = orc.mdot(s_.pos, s_.F, s_.T if angular else None, 1.0, 1.0, angular, rows=rows)
+    for cfg in (None, (256, 8, 19, 4)) if angular else (None,):
+        if cfg is not None:
+            lm.lm_set_pair_config(s, *cfg)
+        u, w = gpu_mdot(s, s_.F, s_.T if angular else None)
+        assert rel(u[rows], ur) <= 1e-5, (cfg, rel(u[rows], ur))
+        assert np.isfinite(u).all()
+        if angular:
+            assert rel(w[rows], wr) <= 1e-5, (cfg, rel(w[rows], wr))
+            assert np.isfinite(w).all()
+
+
 def test_mdot_tt_n65536_sampled_rows(orc):
     """Full-size translation workload of the adjoint benchmark (N = 65536,
     phi = 0.1) in the autotuned forward configuration; 256 sampled rows."""
