@@ -276,7 +276,12 @@ cudaError_t lz_philox_words(const uint32_t* ctr, const uint32_t* key, uint32_t* 
 // ---------------------------------------------------------------------------
 enum BatchMode { kBatchBD = 0, kBatchMdot = 1, kBatchSqrt = 2 };
 enum BatchError { kBatchOk = 0, kBatchTimeout = 1, kBatchTridiag = 2 };
-constexpr int kBatchChunk = 256;       // elements per vector-phase work unit
+// Elements per vector-phase work unit.  A unit's time is set by the basis
+// rows it walks (serialised DRAM rounds), not by its length, and the phase
+// lasts as many units as the busiest CTA holds: 384 leaves two units per CTA
+// for the benchmark batch (256 left a third one for a few CTAs; 512 lengthens
+// the dot loop of every unit).  A multiple of both CTA widths (64, 128).
+constexpr int kBatchChunk = 384;
 constexpr int kBatchJPart = 1024;      // j-range of one product work item
 // Grid barrier of the persistent kernel: bar[0] counts arrived groups,
 // bar[1] is the generation, and group g of kBarGroup consecutive main CTAs
