@@ -125,7 +125,7 @@ __device__ __forceinline__ double* basis(const BatchParams& P, int s, int j) {
 template <int NT, int NI, int NRHS>
 __device__ void pair_item(const BatchParams& P, int s, int i0, int jb, int je, const float* srcA_f,
                           const double* srcA_d, double scaleA, double* outA_d, double* outB, double* Vrow_store,
-                          double* part_slot, float4* sp, float4* sa, float4* sb, double* sred) {
+                          double* part_slot, float* st, double* sred) {
     const int tid = threadIdx.x;
     const int64_t o = P.off[s];
     const int Ns = (int)(P.off[s + 1] - o);
@@ -135,15 +135,16 @@ __device__ void pair_item(const BatchParams& P, int s, int i0, int jb, int je, c
     // consecutive j (j-paired), so any i-blocking works; the j-tile is stored
     // as structure-of-arrays floats (x[NT], y[NT], z[NT] in the float4 arrays'
     // memory) so that a float2 load yields the pair (x_j, x_j+1).
-    float* tx = reinterpret_cast<float*>(sp);
-    float* ty = tx + NT;
-    float* tz = ty + NT;
-    float* ax = reinterpret_cast<float*>(sa);
-    float* ay = ax + NT;
-    float* az = ay + NT;
-    float* bx = reinterpret_cast<float*>(sb);
-    float* by = bx + NT;
-    float* bz = by + NT;
+    // two tile buffers of nine NT-float arrays (x, y, z, A, B), used in turn:
+    // the next tile is written into the idle buffer after the current one is
+    // computed, so one barrier per tile separates its writes from the reads of
+    // both neighbours
+    float *tx, *ty, *tz, *ax, *ay, *az, *bx, *by, *bz;
+    auto use_buffer = [&](int b) {
+        tx = st + b * 9 * NT; ty = tx + NT; tz = ty + NT;
+        ax = tz + NT; ay = ax + NT; az = ay + NT;
+        bx = az + NT; by = bx + NT; bz = by + NT;
+    };
     float2 xi[NI], yi[NI], zi[NI];
     float2 pA[NI][3], pB[NRHS == 2 ? NI : 1][3];
     float hA[NI][3], lA[NI][3];
@@ -189,14 +190,21 @@ __device__ void pair_item(const BatchParams& P, int s, int i0, int jb, int je, c
             if constexpr (NRHS == 2) nj[6] = nj[7] = nj[8] = 0.f;
         }
     };
+    auto store_tile = [&](int b) {
+        float* t = st + b * 9 * NT;
+        t[0 * NT + tid] = nj[0]; t[1 * NT + tid] = nj[1]; t[2 * NT + tid] = nj[2];
+        t[3 * NT + tid] = nj[3]; t[4 * NT + tid] = nj[4]; t[5 * NT + tid] = nj[5];
+        if constexpr (NRHS == 2) { t[6 * NT + tid] = nj[6]; t[7 * NT + tid] = nj[7]; t[8 * NT + tid] = nj[8]; }
+    };
     fetch(jb + tid);
+    __syncthreads();   // the previous item's last reads of buffer 0 are done
+    store_tile(0);
+    __syncthreads();
+    int buf = 0;
     for (int jt = jb; jt < je; jt += NT) {
-        __syncthreads();
-        tx[tid] = nj[0]; ty[tid] = nj[1]; tz[tid] = nj[2];
-        ax[tid] = nj[3]; ay[tid] = nj[4]; az[tid] = nj[5];
-        if constexpr (NRHS == 2) { bx[tid] = nj[6]; by[tid] = nj[7]; bz[tid] = nj[8]; }
-        __syncthreads();
-        if (jt + NT < je) fetch(jt + NT + tid);
+        const bool more = jt + NT < je;
+        if (more) fetch(jt + NT + tid);
+        use_buffer(buf);
         static_assert(NT % 4 == 0, "the j tile holds whole groups of four");
         // two j-pairs (four j) per overlap vote: two independent packed chains
         // per i-particle; a slot (one i against one j-pair) that holds an
@@ -298,6 +306,9 @@ __device__ void pair_item(const BatchParams& P, int s, int i0, int jb, int je, c
                 }
             }
         }
+        if (more) store_tile(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
     }
     if (P.pair_count != nullptr && tid == 0)
         atomicAdd(P.pair_count, (unsigned long long)min(NT * NI, Ns - i0) * (unsigned long long)(je - jb));
@@ -726,7 +737,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
         solver_loop(P);
         return;
     }
-    __shared__ float4 sp[NT], sa[NT], sb[NT];
+    __shared__ float s_tile[2 * 9 * NT];
     __shared__ double sred[NT / 32];
     __shared__ double cvec[129];
     __shared__ unsigned long long s_ticket;
@@ -775,8 +786,7 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
             int s, i0, jp, jb, je;
             double *wout, *uout;
             item_args(t, s, i0, jp, jb, je, wout, uout);
-            pair_item<NT, NI, 1>(P, s, i0, jb, je, P.F_in, nullptr, 1.0, wout, nullptr, nullptr, nullptr, sp, sa, sb,
-                                 sred);
+            pair_item<NT, NI, 1>(P, s, i0, jb, je, P.F_in, nullptr, 1.0, wout, nullptr, nullptr, nullptr, s_tile, sred);
         });
         if (!grid_sync(P)) return;
         if (blockIdx.x == 0 && tid == 0) atomicExch(P.main_done, 1);
@@ -906,14 +916,14 @@ __global__ void __launch_bounds__(NT) batch_kernel(BatchParams P) {
                     const double* v0 = basis(P, s, 0) - 3 * o;  // indexed by global element
                     if (P.mode == kBatchBD)
                         pair_item<NT, NI, 2>(P, s, i0, jb, je, nullptr, v0, 1.0, wout, uout, nullptr,
-                                             &P.part_item[t], sp, sa, sb, sred);
+                                             &P.part_item[t], s_tile, sred);
                     else
                         pair_item<NT, NI, 1>(P, s, i0, jb, je, nullptr, v0, 1.0, wout, nullptr, nullptr,
-                                             &P.part_item[t], sp, sa, sb, sred);
+                                             &P.part_item[t], s_tile, sred);
                 } else {
                     const double invb = 1.0 / P.beta[s * P.m_max + k - 1];
                     pair_item<NT, NI, 1>(P, s, i0, jb, je, nullptr, wprev, invb, wout, nullptr,
-                                         jp == 0 ? basis(P, s, k) : nullptr, &P.part_item[t], sp, sa, sb, sred);
+                                         jp == 0 ? basis(P, s, k) : nullptr, &P.part_item[t], s_tile, sred);
                 }
             });
             if (!grid_sync(P)) return;
