@@ -349,6 +349,7 @@ __device__ int tridiag_sqrt_e1_warp(int m, int m_max, const double* alpha, const
     df* u = b2 + m_max;
     df* inv = reinterpret_cast<df*>(scr + 5 * (size_t)m_max);   // [row][lane]
     df* acc = inv + 32 * (size_t)m_max;                          // [row][lane]
+    if (!LM_INBOUNDS(m >= 1 && m <= m_max, 15, m)) return -3;   // the scratch holds m_max rows
 
     // scale by 4^-k as the QR form does (largest |entry| in [1/4, 1))
     float amax = 0.f;

@@ -73,6 +73,10 @@ for n in (1, 2, 3, 31, 33, 129, 700):
     g = oracle.grad(s_.pos, s_.F, None, s_.G, None, 1.0, 1.0, False)
     if n > 1:
         assert rel(dX.cpu(), g) < 1e-4, (n, rel(dX.cpu(), g))
+    lm.lm_set_adjoint_config(s, 128, 2, 0, 3)   # the symmetric form
+    dX, dF, _ = lm.lm_mdot_backward(s, dev(s_.F), None, dev(s_.G), None)
+    if n > 1:
+        assert rel(dX.cpu(), g) < 1e-4, (n, "symmetric", rel(dX.cpu(), g))
     pw = s_.pos.copy(); pw[:, 2] -= pw[:, 2].min() - 0.5
     sw = lm.lm_create(1.0, 1.0, False, lm.LM_FP32C, periodicity=("open", "open", "single_wall"))
     lm.lm_set_positions(sw, dev(pw))
@@ -84,6 +88,18 @@ b_ = I.batch_suspensions(7, S=5, nmin=20, nmax=300)
 b = lm.lm_batch_create(b_.offsets, 1.0, 1.0)
 lm.lm_batch_set_positions(b, dev(b_.pos))
 lm.lm_batch_bd_run(b, 1.0, 1e-3, 1.0, 2, step0=0, seed=3, tol=1e-4, use_graph=False)
+# the device tridiagonal step: the warp quadrature and its QR fallback (graded T)
+rng = np.random.default_rng(4)
+for m in (1, 7, 40, 128):
+    al = rng.uniform(0.5, 3.0, (3, m)); be = rng.uniform(0.05, 0.8, (3, m))
+    al[0] = rng.uniform(2.0, 3.0, m); be[0] = rng.uniform(0.05, 0.5, m)   # diagonally dominant: certified
+    al[2] = np.linspace(1e-7, 1.0, m); be[2] = 1e-9                          # graded: the QR form
+    out, paths = lm.lm_tridiag_sqrt_e1_device(torch.from_numpy(al).cuda(), torch.from_numpy(be).cuda(), paths=True)
+    for c in range(3):
+        want = oracle.tridiag_sqrt_e1(al[c], be[c, : m - 1])
+        got = out[c].cpu().numpy()
+        assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max()), (m, c)
+    assert paths[0] == 0 and (m == 1 or paths[2] == 1), (m, list(paths))
 torch.cuda.synchronize()
 lm.lm_debug_check()
 print("bounds-checked parity ok, worst M[F;T] error %.2e" % worst)
