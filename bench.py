@@ -357,6 +357,33 @@ def hotpath_leg(workload, steps, warmup, dist, local, *, pair_config=None, autot
         "bytes_per_iteration_mean": prof["vector_bytes"] / max(1, prof["vector_iterations"]),
         "bytes_rule": "FP64 vectors of n=6N: alpha 2, three-term update 4, each Gram-Schmidt pass 2k+5 at iteration k",
         "peak_basis": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth), of measured"}
+    # The Gram-Schmidt kernels do one FP64 FMA per 8-byte basis element: their
+    # ceiling is min(HBM, 8 B x the FP64 FMA rate), measured here after the
+    # timed region.  The bound time sums, per enqueued iteration k, the HBM
+    # time of alpha and the three-term update and, for the dots and the
+    # subtraction, the larger of their HBM time and their FP64 FMA time.
+    fp64 = lm.lm_fp32_probe(4, 1 << 8)
+    if hbm and fp64 > 0 and prof["vector_ms"] > 0:
+        ks = []
+        extra = max(0, int(prof["vector_iterations"]) - int(sum(iters)))
+        for c, m in enumerate(iters):
+            ks.extend(range(int(m) + (1 if c < extra else 0)))
+        vec = 8.0 * (6 * n)
+        bw = hbm * 1e9
+        fma_rate = fp64 * 1e12 / 2.0
+        bound_s = 0.0
+        for k in ks:
+            bound_s += (2 + (4 if k else 3)) * vec / bw
+            for rows in (k + 2, k + 3):
+                bound_s += max(rows * vec / bw, (k + 1) * (6 * n) / fma_rate)
+        lanczos_vectors.update({
+            "fp64_probe_tflops": fp64,
+            "bound_ms_per_iteration": 1e3 * bound_s / max(1, len(ks)),
+            "frac_of_fp64_hbm_bound": 1e3 * bound_s / prof["vector_ms"],
+            "bound_rule": "per enqueued iteration k: alpha and the three-term update at the HBM copy peak; the "
+                          "Gram-Schmidt dots ((k+2) vectors, (k+1) n FP64 FMAs) and subtraction ((k+3) vectors, "
+                          "(k+1) n FMAs) each at max(HBM time, FMA time at the measured FP64 rate); the DGKS second "
+                          "pass, rarely taken, not counted"})
     return {"workload": workload, "desc": desc, "n": n, "value": value, "ms_per_step": total_ms_max / steps,
             "steps": steps, "warmup": warmup, "iters": list(iters), "cfg": cfg, "autotune_s": t_tune,
             "roofline": roofline, "lanczos_vectors": lanczos_vectors, "e2e": e2e, "launches": launches,

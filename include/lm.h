@@ -596,8 +596,13 @@ lm_status lm_mdot_noalloc(const float *pos, const float *forces, const float *to
  *           register pairs per instruction);
  *   mode 3: packed f32x2 FMAs in rotating dependent chains whose operands are
  *           values produced a few instructions earlier (the data flow of the
- *           pair formulas).
- *   1 <= iters <= 2^24 (about 2^14 gives a launch of tens of milliseconds).
+ *           pair formulas);
+ *   mode 4: FP64 FMA chains x = x a + b (the ceiling of the Lanczos
+ *           Gram-Schmidt kernels, one FP64 FMA per basis element; the FP64
+ *           pipe runs at a small fraction of the FP32 rate, so about 2^8
+ *           iterations give a launch of tens of milliseconds).
+ *   1 <= iters <= 2^24 (about 2^14 gives an FP32 launch of tens of
+ *   milliseconds).
  * Allocates and frees a small output buffer; synchronises the stream.
  */
 lm_status lm_fp32_probe(int mode, int64_t iters, double *tflops, void *cuda_stream);

@@ -25,6 +25,34 @@ inline int blocks_for(int64_t n, int per_thread = 4) {
     return (int)b;
 }
 
+// Programmatic dependent launch: the per-iteration vector kernels are
+// launched with cudaLaunchAttributeProgrammaticStreamSerialization, so that
+// each can be scheduled while its predecessor in the stream drains.  Every
+// such kernel first waits for its predecessors to complete (griddepcontrol.
+// wait: their memory operations are then visible), so the order of all
+// memory accesses is that of plain stream order; only the launch latency
+// overlaps.  It then allows its own dependent to be scheduled.  In a launch
+// without the attribute both instructions return at once.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -112,6 +140,7 @@ __global__ void combine_kernel(const double* __restrict__ V, int m, const double
 
 __global__ void scale_kernel(const double* __restrict__ x, const double* __restrict__ nrm, double* __restrict__ y,
                              int64_t n) {
+    pdl_enter();
     const double inv = 1.0 / nrm[0];
     for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kThreads)
         y[e] = x[e] * inv;
@@ -178,6 +207,7 @@ __device__ __forceinline__ double final_sum(const double* red, int nb) {
 // mode 0: out[0] = x.y ; mode 1: out[0] = sqrt(x.x), out[1] = x.x
 __global__ void dot_fused(const double* __restrict__ x, const double* __restrict__ y, int64_t n, double* red,
                           unsigned* ctr, double* __restrict__ out, int mode) {
+    pdl_enter();
     double acc = 0.0;
     for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < n; e += (int64_t)gridDim.x * kThreads)
         acc = fma(x[e], y[e], acc);
@@ -197,6 +227,7 @@ __global__ void axpy2_norm_kernel(double* __restrict__ w, const double* __restri
                                   const double* __restrict__ alpha, const double* __restrict__ vkm1,
                                   const double* __restrict__ beta, int64_t n, double* red, unsigned* ctr,
                                   double* __restrict__ out) {
+    pdl_enter();
     const double a = alpha[0];
     const double b = (vkm1 != nullptr) ? beta[0] : 0.0;
     double acc = 0.0;
@@ -230,6 +261,7 @@ __global__ void __launch_bounds__(kMdThreads) multidot_rows(const double* __rest
                                                             const double* __restrict__ w, int64_t n, double* red,
                                                             unsigned* ctr, double* __restrict__ c,
                                                             const double* __restrict__ cond) {
+    pdl_enter();
     if (!second_pass_needed(cond)) return;
     const int nb = gridDim.x, g = blockIdx.y;
     const int j0 = g * kMdRows;
@@ -304,6 +336,7 @@ __global__ void __launch_bounds__(kMdThreads) multidot_rows(const double* __rest
 __global__ void sub_vc_norm_kernel(const double* __restrict__ V, int m, const double* __restrict__ c,
                                    double* __restrict__ w, int64_t n, const double* __restrict__ cond, double* red,
                                    unsigned* ctr, double* __restrict__ out) {
+    pdl_enter();
     if (!second_pass_needed(cond)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) { out[0] = cond[2]; out[1] = cond[3]; }
         return;
@@ -347,16 +380,15 @@ cudaError_t lz_norm(const double* x, int64_t n, double* red, double* out, cudaSt
 
 cudaError_t lz_dot1(const double* x, const double* y, int64_t n, double* red, unsigned* ctr, double* out,
                     int mode, cudaStream_t s) {
-    dot_fused<<<blocks_for(n), kThreads, 0, s>>>(x, y, n, red, ctr, out, mode);
     count_launches(1);
-    return cudaGetLastError();
+    return launch_pdl(dot_fused, dim3(blocks_for(n)), dim3(kThreads), s, x, y, n, red, ctr, out, mode);
 }
 
 cudaError_t lz_axpy2_norm(double* w, const double* vk, const double* alpha, const double* vkm1, const double* beta,
                           int64_t n, double* red, unsigned* ctr, double* out, cudaStream_t s) {
-    axpy2_norm_kernel<<<blocks_for(n), kThreads, 0, s>>>(w, vk, alpha, vkm1, beta, n, red, ctr, out);
     count_launches(1);
-    return cudaGetLastError();
+    return launch_pdl(axpy2_norm_kernel, dim3(blocks_for(n)), dim3(kThreads), s, w, vk, alpha, vkm1, beta, n, red,
+                      ctr, out);
 }
 
 cudaError_t lz_multidot1(const double* V, int m, const double* w, int64_t n, double* red, unsigned* ctr, double* c,
@@ -364,22 +396,21 @@ cudaError_t lz_multidot1(const double* V, int m, const double* w, int64_t n, dou
     if (m < 1) return cudaSuccess;
     const int nb = md_blocks(n), ng = (m + kMdRows - 1) / kMdRows;
     if (nb < 1 || ng > 65535) return cudaErrorInvalidConfiguration;
-    multidot_rows<<<dim3((unsigned)nb, (unsigned)ng), kMdThreads, 0, s>>>(V, m, w, n, red, ctr + 1, c, cond);
     count_launches(1);
-    return cudaGetLastError();
+    return launch_pdl(multidot_rows, dim3((unsigned)nb, (unsigned)ng), dim3(kMdThreads), s, V, m, w, n, red, ctr + 1, c,
+                      cond);
 }
 
 cudaError_t lz_sub_vc_norm(const double* V, int m, const double* c, double* w, int64_t n, double* red,
                            unsigned* ctr, double* out, cudaStream_t s, const double* cond) {
-    sub_vc_norm_kernel<<<blocks_for(n, 1), kThreads, 0, s>>>(V, m, c, w, n, cond, red, ctr, out);
     count_launches(1);
-    return cudaGetLastError();
+    return launch_pdl(sub_vc_norm_kernel, dim3(blocks_for(n, 1)), dim3(kThreads), s, V, m, c, w, n, cond, red, ctr,
+                      out);
 }
 
 cudaError_t lz_scale(const double* x, const double* nrm, double* y, int64_t n, cudaStream_t s) {
-    scale_kernel<<<blocks_for(n), kThreads, 0, s>>>(x, nrm, y, n);
     count_launches(1);
-    return cudaGetLastError();
+    return launch_pdl(scale_kernel, dim3(blocks_for(n)), dim3(kThreads), s, x, nrm, y, n);
 }
 
 cudaError_t lz_combine(const double* V, int m, const double* z, double* y, int64_t n, cudaStream_t s) {

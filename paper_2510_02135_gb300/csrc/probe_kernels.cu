@@ -14,7 +14,10 @@
 //           within 12 instructions);
 //   mode 3  packed f32x2 FMA in rotating dependent chains, every operand a
 //           value produced a few instructions earlier (the data flow of the
-//           pair formulas, where most operands are fresh intermediates).
+//           pair formulas, where most operands are fresh intermediates);
+//   mode 4  FP64 FMA, x = x a + b on 8 independent chains per thread: the
+//           ceiling of the Lanczos Gram-Schmidt kernels, which do one FP64
+//           FMA per 8-byte basis element.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -63,6 +66,24 @@ __global__ void __launch_bounds__(kProbeThreads) probe_ffma2_kernel(int64_t iter
 #pragma unroll
     for (int c = 0; c < kChains; ++c) s += x[c].x + x[c].y;
     out[(int64_t)blockIdx.x * kProbeThreads + threadIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kProbeThreads) probe_dfma_kernel(int64_t iters, double a, double b,
+                                                                   float* __restrict__ out) {
+    double x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = 1.0 + 1e-3 * (double)(threadIdx.x + c);
+    for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) x[c] = fma(x[c], a, b);
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) s += x[c];
+    out[(int64_t)blockIdx.x * kProbeThreads + threadIdx.x] = (float)s;
 }
 
 // Twelve accumulators, each with its own pair of loop-invariant operands.
@@ -130,21 +151,22 @@ __global__ void __launch_bounds__(kProbeThreads) probe_ffma2_chain_kernel(int64_
 
 extern "C" lm_status lm_fp32_probe(int mode, int64_t iters, double* tflops, void* cuda_stream) {
     lmk::set_last_error("");
-    if (tflops == nullptr || mode < 0 || mode > 3 || iters < 1 || iters > (int64_t)1 << 24) {
-        lmk::set_last_error("lm_fp32_probe: mode in 0..3, 1 <= iters <= 2^24 and tflops are required");
+    if (tflops == nullptr || mode < 0 || mode > 4 || iters < 1 || iters > (int64_t)1 << 24) {
+        lmk::set_last_error("lm_fp32_probe: mode in 0..4, 1 <= iters <= 2^24 and tflops are required");
         return LM_ERR_INVALID_ARG;
     }
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     int dev = 0, sms = 0, occ = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &occ,
-            mode == 0 ? lmk::probe_ffma_kernel
-                      : (mode == 1 ? lmk::probe_ffma2_kernel
-                                   : (mode == 2 ? lmk::probe_ffma2_wide_kernel : lmk::probe_ffma2_chain_kernel)),
-            lmk::kProbeThreads, 0);
+    if (e == cudaSuccess) {
+        const int nt = lmk::kProbeThreads;
+        if (mode == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lmk::probe_ffma_kernel, nt, 0);
+        else if (mode == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lmk::probe_ffma2_kernel, nt, 0);
+        else if (mode == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lmk::probe_ffma2_wide_kernel, nt, 0);
+        else if (mode == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lmk::probe_ffma2_chain_kernel, nt, 0);
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lmk::probe_dfma_kernel, nt, 0);
+    }
     if (e != cudaSuccess) {
         lmk::set_last_error(cudaGetErrorString(e));
         return LM_ERR_CUDA;
@@ -155,16 +177,17 @@ extern "C" lm_status lm_fp32_probe(int mode, int64_t iters, double* tflops, void
     e = cudaMalloc(&out, (size_t)blocks * lmk::kProbeThreads * sizeof(float));
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
-    // flops per thread per outer iteration: FFMA 16 x 8 x 2; FFMA2 16 x 8 x 4;
-    // wide 8 x 12 x 4; chains 4 x 8 x 4 packed FMAs x 4
-    const double per_it = mode == 0 ? 256.0 : (mode == 2 ? 384.0 : 512.0);
+    // flops per thread per outer iteration: FFMA and DFMA 16 x 8 x 2; FFMA2
+    // 16 x 8 x 4; wide 8 x 12 x 4; chains 4 x 8 x 4 packed FMAs x 4
+    const double per_it = (mode == 0 || mode == 4) ? 256.0 : (mode == 2 ? 384.0 : 512.0);
     float ms = 0.f;
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first launch warms up
         cudaEventRecord(e0, s);
         if (mode == 0) lmk::probe_ffma_kernel<<<blocks, lmk::kProbeThreads, 0, s>>>(iters, 0.9999f, 1e-4f, out);
         else if (mode == 1) lmk::probe_ffma2_kernel<<<blocks, lmk::kProbeThreads, 0, s>>>(iters, 0.9999f, 1e-4f, out);
         else if (mode == 2) lmk::probe_ffma2_wide_kernel<<<blocks, lmk::kProbeThreads, 0, s>>>(iters, 0.9999f, 1e-4f, out);
-        else lmk::probe_ffma2_chain_kernel<<<blocks, lmk::kProbeThreads, 0, s>>>(iters, 0.9999f, 1e-4f, out);
+        else if (mode == 3) lmk::probe_ffma2_chain_kernel<<<blocks, lmk::kProbeThreads, 0, s>>>(iters, 0.9999f, 1e-4f, out);
+        else lmk::probe_dfma_kernel<<<blocks, lmk::kProbeThreads, 0, s>>>(iters, 0.9999, 1e-4, out);
         lmk::count_launches(1);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaEventRecord(e1, s);

@@ -648,9 +648,10 @@ def lm_profile_read(s: Solver, reset: bool = True) -> dict:
 
 
 def lm_fp32_probe(mode: int, iters: int = 1 << 14, cuda_stream=None) -> float:
-    """Measured FP32 FMA rate of the current GPU in TFLOP/s (mode 0 scalar,
+    """Measured FMA rate of the current GPU in TFLOP/s (mode 0 scalar FP32,
     1 packed f32x2, 2 packed with three distinct operand pairs, 3 packed in
-    dependent chains of fresh operands)."""
+    dependent chains of fresh operands, 4 FP64; for mode 4 pass about 2^8
+    iterations)."""
     t = ctypes.c_double(0.0)
     _check(lib().lm_fp32_probe(int(mode), int(iters), ctypes.byref(t), cuda_stream))
     return t.value

@@ -143,7 +143,7 @@ def test_fp32_probe_rejects_bad_arguments_without_gpu(L):
     from paper_2510_02135_gb300 import lm
 
     t = C.c_double(0.0)
-    for mode, iters in ((4, 100), (-1, 100), (1, 0), (1, (1 << 24) + 1)):
+    for mode, iters in ((5, 100), (-1, 100), (1, 0), (1, (1 << 24) + 1)):
         assert L.lm_fp32_probe(mode, iters, C.byref(t), None) == lm.LM_ERR_INVALID_ARG
     assert L.lm_fp32_probe(1, 100, None, None) == lm.LM_ERR_INVALID_ARG
 

@@ -496,6 +496,9 @@ def test_fp32_probe_rates_are_plausible():
     rates = [lm.lm_fp32_probe(m, 1 << 10) for m in range(4)]
     assert all(0 < r < 2 * nominal for r in rates), rates
     assert rates[1] > 0.5 * nominal, rates
+    # FP64 (mode 4): well below the FP32 rate on this GPU, and above a 1/256 floor
+    fp64 = lm.lm_fp32_probe(4, 1 << 6)
+    assert nominal / 256 < fp64 < 0.25 * nominal, (fp64, nominal)
 
 
 def test_profile_counts_pairs_and_lanczos_vector_bytes():
