@@ -33,9 +33,11 @@ Contents (libMobility paper, Sec. 2 and Sec. 3.3):
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (closed forms, a quadrature of Eq. (stokestomob), invariants, library
-routines).  Lanczos at sizes where the eigendecomposition is infeasible is
-pinned only through its agreement with ``sqrt_exact`` at small sizes and by
-self-convergence; at those sizes exact parity is unpinned.
+routines).  Lanczos is pinned against ``sqrt_exact`` at small sizes and, with
+no eigendecomposition, by the identity M^{1/2} (M^{1/2} W) = M W and the norm
+identity |M^{1/2} W|^2 = W . M W at n = 7200; at the benchmark sizes
+(n >= 196608) its results are compared with the same code at a tighter
+tolerance, not with an independent definition.
 """
 from __future__ import annotations
 

@@ -287,6 +287,32 @@ def test_lanczos_tolerance_controls_error(orc):
         assert err < 20 * tol, (tol, err, it)
 
 
+def test_lanczos_root_applied_twice_is_the_product(orc):
+    """A pin that needs no eigendecomposition, so it holds at sizes where the
+    dense root is out of reach: the Lanczos root applied to its own result
+    gives M W, since M^{1/2} M^{1/2} = M.  N = 1200 spheres with all four
+    blocks (n = 7200), the products by the oracle's direct sum."""
+    rng = np.random.default_rng(41)
+    n = 1200
+    L = (n * (4.0 / 3.0) * np.pi / 0.1) ** (1.0 / 3.0)
+    pos = rng.uniform(-L / 2, L / 2, size=(n, 3))
+    F = rng.standard_normal((n, 3))
+    T = rng.standard_normal((n, 3))
+
+    def matvec(v):
+        u, w = orc.mdot(pos, v[: 3 * n].reshape(n, 3), v[3 * n:].reshape(n, 3), 1.0, 1.0, True)
+        return np.concatenate([u.ravel(), w.ravel()])
+
+    W = np.concatenate([F.ravel(), T.ravel()])
+    y, it1, c1 = orc.lanczos_sqrt(matvec, W, tol=1e-11, max_iter=400)
+    y2, it2, c2 = orc.lanczos_sqrt(matvec, y, tol=1e-11, max_iter=400)
+    assert c1 and c2, (it1, it2)
+    MW = matvec(W)
+    assert np.linalg.norm(y2 - MW) / np.linalg.norm(MW) < 1e-8
+    # and the norm identity |M^{1/2} W|^2 = W . M W
+    assert abs(y @ y - W @ MW) / (W @ MW) < 1e-9
+
+
 def test_fluctuation_dissipation_covariance(orc):
     """<(M^1/2 W)(M^1/2 W)^T> = M for W ~ N(0, I) (Eq. fdt with 2kT dt = 1)."""
     rng = np.random.default_rng(37)
