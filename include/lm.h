@@ -474,7 +474,9 @@ lm_status lm_batch_autotune(lm_batch *batch, int *threads_out, int *ilp_out);
  * persistent kernel records the device global timer (ns) at the start of the
  * last step of the run and after every phase of that step: [start, A1, A2, then per
  * Lanczos iteration B, C2, C3, C4, C5, then the wait for the last
- * tridiagonal results, then D].  lm_batch_profile_read copies
+ * tridiagonal results, then D].  C3 includes each system's end of iteration
+ * (beta, solve request, stopping rule); C4 is empty unless some system takes
+ * the second Gram-Schmidt pass; C5 is an empty stamp kept for the layout.  lm_batch_profile_read copies
  * up to n stamps of the last run into out and the number recorded into
  * *count.  lm_batch_profile_pairs gives the pair evaluations of the last
  * profiled run, all steps and systems: the particle pairs of every product

@@ -452,12 +452,12 @@ __device__ void chunk_sum_coeffs(const BatchParams& P, int s, const double* part
 
 // ---------------------------------------------------------------------------
 // Asynchronous tridiagonal solves.  The main CTAs post a request (step,
-// system, k) once beta_k is known and keep iterating; the warps of the solver
-// CTAs take the posted requests, up to 32 at a time (one per lane), compute
-// |W| f(T_{k+1}) e1 with T_{k+1} = tridiag(beta_0..k-1, alpha_0..k,
-// beta_0..k-1) in FP64 and publish it in the system's result ring under a
-// tag; the main CTAs apply the stopping rule in iteration order as results
-// arrive.  Requests of an earlier step are dropped.  Every wait is bounded by
+// system, k) once beta_k is known and keep iterating; each warp of the solver
+// CTAs takes one posted request at a time, computes |W| f(T_{k+1}) e1 with
+// T_{k+1} = tridiag(beta_0..k-1, alpha_0..k, beta_0..k-1) with all its lanes
+// (tridiag_sqrt_e1_warp; the QR form on lane 0 where the quadrature declines)
+// and publishes it in the system's result ring under a tag; the main CTAs
+// apply the stopping rule in iteration order as results arrive.  Requests of an earlier step are dropped.  Every wait is bounded by
 // spin_limit clock cycles without progress of the other side.
 // ---------------------------------------------------------------------------
 // Requests in flight per system beyond the next pending stopping test.

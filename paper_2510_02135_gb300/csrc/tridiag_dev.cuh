@@ -1,6 +1,7 @@
-// Device form of the tridiagonal step f(T) e1, f = sqrt (the last step of the
+// Device forms of the tridiagonal step f(T) e1, f = sqrt (the last step of the
 // Krylov square root M^{1/2} W ~ |W| V_m T_m^{1/2} e1, libMobility paper,
-// Sec. 3.3), one thread per system.  Same algorithm as tridiag.cuh (implicit
+// Sec. 3.3): the warp-parallel quadrature at the end of this file, and, for a
+// T that it declines, the QR form on one thread.  The QR form is the algorithm of tridiag.cuh (implicit
 // symmetric QR with Wilkinson shifts, Golub & Van Loan Sec. 8.3; the
 // rotations' product Q applied to e1 during the sweeps and, in reverse, to
 // f(Lambda) Q^T e1 afterwards), in double-float arithmetic.
