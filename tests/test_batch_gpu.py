@@ -194,6 +194,31 @@ def test_batch_sqrt_mixed_breakdown_and_large_systems(orc):
         assert abs(int(it0[s]) - ito) <= 2, (s, it0[s], ito)
 
 
+def test_batch_sqrt_runs_to_the_largest_basis(orc):
+    """max_iter = 128 (the largest basis a batch holds) with a tolerance that
+    FP32 products cannot reach: the systems iterate until the FP32 breakdown
+    test (beta below 1e-7 of the largest alpha) or m = 128, so the solver
+    warps solve tridiagonal matrices up to their scratch limit; the call
+    reports non-convergence for the systems that hit the cap, and all results
+    match the exact root to the accuracy of the FP32 products."""
+    b_ = small_batch(seed=43, S=4, nmin=300, nmax=600)
+    n = b_.pos.shape[0]
+    W = np.random.default_rng(8).standard_normal(3 * n)
+    b = lm.lm_batch_create(b_.offsets, 1.0, 1.0, max_iter=128)
+    lm.lm_batch_set_positions(b, dev(b_.pos))
+    with pytest.raises(lm.LmError) as e:
+        lm.lm_batch_sqrt_mdot(b, dev(W), tol=1e-15)
+    assert e.value.status == lm.LM_ERR_NOT_CONVERGED
+    y, its = lm.lm_batch_sqrt_mdot(b, dev(W), tol=1e-15, raise_not_converged=False)
+    y = y.cpu().numpy()
+    its = np.asarray(its)
+    assert (its >= 100).all() and (its <= 128).all() and (its == 128).any(), its
+    for s in range(b.S):
+        o0, o1 = b_.offsets[s], b_.offsets[s + 1]
+        M = orc.assemble(b_.pos[o0:o1], 1.0, 1.0, False)
+        assert rel(y[o0:o1], orc.sqrt_exact(M, W[3 * o0:3 * o1])) <= 1e-5, s
+
+
 def test_batch_sqrt_matches_single_system_api(orc):
     b_ = small_batch(seed=13, S=4)
     n = b_.pos.shape[0]
