@@ -51,6 +51,7 @@ UNIT = "pair-interactions/s"
 FP32_LANES_PER_SM = 128
 RECIPE_MAX_SM_MHZ = 2070.0
 FLOPS_PER_PAIR_6N = 86
+FLOPS_PER_PAIR_TT = 35   # translation-only far-field pair (the batched and adjoint workloads)
 PAIR_KERNEL_SRCS = [os.path.join(ROOT, "paper_2510_02135_gb300", "csrc", f)
                     for f in ("pair_kernels.cu", "pair_common.cuh")]
 # ncu summaries of the forward pair kernel, per workload (DRAM bytes per launch)
@@ -510,7 +511,7 @@ def adjoint_leg(steps, warmup, dist, local, *, pair_config=None, adjoint_config=
     peak, _ = fp32_peak(local)
     fwd_ms = float(np.median(fwd))
     bwd_ms = float(np.median(bwd))
-    achieved = 35.0 * n * n / (fwd_ms / 1e3) / 1e12
+    achieved = FLOPS_PER_PAIR_TT * float(n) * n / (fwd_ms / 1e3) / 1e12
     return {"value": pairs / (tmax / 1e3), "unit": UNIT, "ms_per_step": tmax / steps, "steps": steps,
             "warmup": warmup,
             "desc": f"adjoint_n65536: N={n}, phi={c['phi']}, translation only, FP32 compensated; "
@@ -615,6 +616,37 @@ def bd_leg(steps, warmup, dist, local, rank, *, autotune=True, per_system=True):
         torch.cuda.synchronize()
         t_loop = time.perf_counter() - t1
     ms_bd_step = tmax / (steps * nsub)
+    # one more EM step with the phase timeline on (after the timed region):
+    # where a BD step's time goes, the product phases' FP32 fraction and the
+    # share of pair evaluations in iterations that the systems keep
+    profiled = None
+    if rank == 0:
+        lm.lm_batch_profile_enable(b, True)
+        its1 = lm.lm_batch_bd_run(b, c["kT"], c["dt"], c["k_trap"], 1, step0=step_no[0], seed=c["seed"],
+                                  tol=c["tol"], use_graph=False)
+        torch.cuda.synchronize()
+        st = lm.lm_batch_profile_read(b).astype(np.int64)
+        pairs_ev = float(lm.lm_batch_profile_pairs(b))
+        lm.lm_batch_profile_enable(b, False)
+        d = np.diff(st) / 1e6   # ms
+        nit = (len(st) - 5) // 5
+        ph = d[2:2 + 5 * nit].reshape(nit, 5) if nit > 0 else np.zeros((0, 5))
+        prod_ms = float(ph[:, 0].sum())
+        peak, _ = fp32_peak(local)
+        kept = float((sizes2 * np.asarray(its1)).sum())
+        profiled = {"iterations_run": int(nit), "step_ms": float(d.sum()),
+                    "phases_ms": {"noise_forces_normalise": float(d[0] + d[1]), "products": prod_ms,
+                                  "gram_schmidt": float(ph[:, 1:4].sum()), "end_of_iteration": float(ph[:, 4].sum()),
+                                  "final_wait_and_update": float(d[2 + 5 * nit:].sum())},
+                    "pair_evaluations": pairs_ev,
+                    "product_phase_pairs_per_s": pairs_ev / (prod_ms / 1e3) if prod_ms > 0 else None,
+                    "product_phase_frac_fp32": (pairs_ev / (prod_ms / 1e3) * FLOPS_PER_PAIR_TT / 1e12 / peak
+                                                if prod_ms > 0 else None),
+                    "kept_pair_fraction": kept / pairs_ev if pairs_ev > 0 else None,
+                    "note": "lm_batch_profile_* timeline of one further EM step (direct launch); products = phase B "
+                            "of every Lanczos iteration, gram_schmidt = C2 + C3 + C4, end_of_iteration = C5; FP32 "
+                            "fraction at 35 flops/pair of the nominal peak; kept = pairs of the iterations the "
+                            "systems keep (sum N_s^2 x iterations)"}
     return {"value": pairs_all / (tmax / 1e3), "unit": UNIT, "ms_per_step": tmax / steps, "steps": steps,
             "warmup": warmup,
             "desc": "bd256: 256 systems, N log-uniform [64, 4096], phi U(0.05, 0.3), a=1, eta=1, kT=1, dt=1e-3, "
@@ -623,7 +655,7 @@ def bd_leg(steps, warmup, dist, local, rank, *, autotune=True, per_system=True):
             "lanczos_iterations_mean": float(np.mean(iters)), "tiling": tiling,
             "per_system_calls_ms_per_bd_step": None if t_loop is None else 1e3 * t_loop,
             "speedup_vs_per_system_calls": None if t_loop is None else 1e3 * t_loop / ms_bd_step,
-            "gpu_launches": launches, "clocks": clocks}
+            "gpu_launches": launches, "clocks": clocks, "profiled_step": profiled}
 
 
 # ---------------------------------------------------------------------------
@@ -777,7 +809,8 @@ def run_single(args, ws, rank, local, pcfg, acfg):
         extra = {"N_total": r["N_total"], "ms_per_bd_step": r["ms_per_bd_step"],
                  "lanczos_iterations_mean": r["lanczos_iterations_mean"], "tiling": r["tiling"],
                  "per_system_calls_ms_per_bd_step": r["per_system_calls_ms_per_bd_step"],
-                 "speedup_vs_per_system_calls": r["speedup_vs_per_system_calls"]}
+                 "speedup_vs_per_system_calls": r["speedup_vs_per_system_calls"],
+                 "profiled_step": r["profiled_step"]}
     line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
