@@ -406,7 +406,8 @@ int lm_tridiag_sqrt_e1(int m, const double *alpha, const double *beta, double *o
 typedef struct lm_batch lm_batch;
 
 /*
- * lm_batch_create -- S >= 1 systems; offsets: host array of S+1 int64 with
+ * lm_batch_create -- 1 <= S <= 2^20 systems (the solve requests encode the
+ * system in 21 bits); offsets: host array of S+1 int64 with
  * offsets[0] = 0 and offsets[s+1] - offsets[s] in [1, 65536].
  * max_iter (1..128): Lanczos iteration cap per system and step; it sizes the
  * Krylov storage, max_iter x 3 N_total doubles.
