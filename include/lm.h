@@ -274,8 +274,9 @@ lm_status lm_mdot_backward(lm_solver *solver, const void *forces, const void *to
  *   (>= 1; 0 = automatic; split k of s holds j-tiles [k T/s, (k+1) T/s) of
  *   the T tiles of `threads` particles, at most T splits are launched);
  *   packed: 0 the scalar form; 1 the packed FP32 form, which evaluates two
- *   i-particles per f32x2 instruction (LM_FP32C with ilp 2, 4 or 8); 2 the
- *   packed form with two j-particles per overlap vote (open geometry only).
+ *   i-particles per f32x2 instruction (LM_FP32C with ilp 2, 4 or 8); 2 and 4
+ *   the packed form with two or four j-particles per overlap vote (open
+ *   geometry only; 4 needs ilp >= 4).
  *   Single-wall solvers: threads 128 or 256, ilp 1, 2, 4 (scalar) or 2, 4
  *   (packed = 1); FP64 ilp 1.  All forms give results within the FP32
  *   tolerance of the FP64 product; they differ in rounding order only.
