@@ -19,7 +19,7 @@ also reports, at one GPU:
   * "rpy6_n32768": the 6N step at N = 32768 (tol 1e-5) with its own roofline and
     per-block errors;
   * "adjoint": forward and backward (dL/dX, dL/dF) times at N = 65536 and
-    their ratio;
+    their ratio, and the same with angular blocks (dL/dT too);
   * "bd256": the batched Brownian-dynamics step of 256 suspensions and its
     speed-up over per-system library calls.
 "--workload rpy6" makes the N = 32768 step the headline instead.
@@ -512,6 +512,37 @@ def adjoint_leg(steps, warmup, dist, local, *, pair_config=None, adjoint_config=
     fwd_ms = float(np.median(fwd))
     bwd_ms = float(np.median(bwd))
     achieved = FLOPS_PER_PAIR_TT * float(n) * n / (fwd_ms / 1e3) / 1e12
+
+    # the same suspension with angular blocks (torques T, cotangents H): the
+    # forward product M [F; T] and the adjoint (dX, dF, dT) in their default
+    # (symmetric) form; reported beside the translation figures, not in value
+    s6 = I.cube_suspension(c["seed"], n, c["phi"], c["a"], angular=True, fp32=True)
+    T6, H6 = dev(s6.T), dev(s6.H)
+    w6 = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    solver6 = lm.lm_create(c["eta"], c["a"], True, lm.LM_FP32C, cuda_stream=stream.cuda_stream)
+    lm.lm_set_positions(solver6, pos)
+    if autotune and not pair_config:
+        lm.lm_autotune(solver6, reps=1)
+    ev6 = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(3)]
+    for k in range(warmup + 3):
+        flush.zero_()
+        e = ev6[k - warmup] if k >= warmup else None
+        if e:
+            e[0].record(stream)
+        lm.lm_mdot(solver6, F, T6, u, w6)
+        if e:
+            e[1].record(stream)
+        lm.lm_mdot_backward(solver6, F, T6, G, H6)
+        if e:
+            e[2].record(stream)
+    torch.cuda.synchronize()
+    fwd6 = float(np.median([e[0].elapsed_time(e[1]) for e in ev6]))
+    bwd6 = float(np.median([e[1].elapsed_time(e[2]) for e in ev6]))
+    angular = {"forward_ms": fwd6, "backward_ms": bwd6, "backward_over_forward": bwd6 / fwd6,
+               "steps": 3, "pair_config": lm.lm_get_pair_config(solver6),
+               "adjoint_config": lm.lm_get_adjoint_config(solver6),
+               "desc": "same N and positions with torques; backward = dX, dF, dT (symmetric scalar form)"}
+    del solver6
     return {"value": pairs / (tmax / 1e3), "unit": UNIT, "ms_per_step": tmax / steps, "steps": steps,
             "warmup": warmup,
             "desc": f"adjoint_n65536: N={n}, phi={c['phi']}, translation only, FP32 compensated; "
@@ -522,7 +553,7 @@ def adjoint_leg(steps, warmup, dist, local, *, pair_config=None, adjoint_config=
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "forward pair kernel (translation, 35 flops/pair)"},
-            "gpu_launches": launches, "clocks": clocks,
+            "gpu_launches": launches, "clocks": clocks, "angular": angular,
             "l2": "flushed by a 256 MB device write before every step"}
 
 

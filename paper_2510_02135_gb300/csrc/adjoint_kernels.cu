@@ -968,14 +968,16 @@ __global__ void __launch_bounds__(NT) rpy_adjoint_sym_kernel(const float4* __res
     }
 }
 
-// out = c8 * acc (dX from components 0..2, dF from 3..5), nullable outputs.
-__global__ void adj_sym_store_kernel(const double* __restrict__ acc, int64_t N, double c8, void* __restrict__ dX,
-                                     void* __restrict__ dF, int out_f64) {
+// out = c8 * acc[N][C] (dX from components 0..2, dF from 3..5, dT from
+// 6..8 when C = 9), nullable outputs.
+__global__ void adj_sym_store_kernel(const double* __restrict__ acc, int C, int64_t N, double c8,
+                                     void* __restrict__ dX, void* __restrict__ dF, void* __restrict__ dT,
+                                     int out_f64) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 6 * N) return;
-    const int64_t i = e / 6;
-    const int c = (int)(e - 6 * i);
-    void* out = (c < 3) ? dX : dF;
+    if (e >= (int64_t)C * N) return;
+    const int64_t i = e / C;
+    const int c = (int)(e - (int64_t)C * i);
+    void* out = (c < 3) ? dX : (c < 6 ? dF : dT);
     if (out == nullptr) return;
     const int64_t idx = 3 * i + (c % 3);
     if (out_f64) static_cast<double*>(out)[idx] = c8 * acc[e];
@@ -999,7 +1001,8 @@ cudaError_t launch_adj_sym_t(const AdjointArgs& a, cudaStream_t s) {
     count_launches(1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    adj_sym_store_kernel<<<(unsigned)((6 * a.N + 255) / 256), 256, 0, s>>>(a.sym_acc, a.N, c8, a.dX, a.dF, a.fp64);
+    adj_sym_store_kernel<<<(unsigned)((6 * a.N + 255) / 256), 256, 0, s>>>(a.sym_acc, 6, a.N, c8, a.dX, a.dF, nullptr,
+                                                                         a.fp64);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -1019,6 +1022,399 @@ int adj_sym_occupancy() {
     cudaError_t e = cudaFuncSetAttribute(rpy_adjoint_sym_kernel<NT, NI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)dyn);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rpy_adjoint_sym_kernel<NT, NI>, NT, dyn);
+    return e == cudaSuccess ? n : 0;
+}
+
+// ---------------------------------------------------------------------------
+// Symmetric form of the scalar adjoint (AdjointArgs::uj == 3 with angular
+// blocks, or in FP64).  Each unordered pair {i, j} is evaluated once, with
+// d = x_i - x_j.  The pair term Phi_ij of the header satisfies
+// Phi_ji(-d) = Phi_ij(d), so its gradient g_ij goes to dX_i and -g_ij to
+// dX_j; the mobility parts of both directions come from the same
+// coefficients (tt and rr even in d, the coupling odd):
+//   dF_i += A G_j + B (G_j.d) d + g H_j x d,  dT_i += g G_j x d + ar H_j + br (H_j.d) d
+//   dF_j += A G_i + B (G_i.d) d - g H_i x d,  dT_j += -g G_i x d + ar H_i + br (H_i.d) d.
+// With P = G_i x T_j + H_i x F_j + T_i x G_j + F_i x H_j and
+// cd = (A'/r) S1 + (B'/r) S2 + (ar'/r) R1 + (br'/r) R2 + (g'/r) d.P (S1, S2,
+// R1, R2 as in adj_pair):
+//   g_ij = cd d + g P + B [(F_j.d) G_i + (G_i.d) F_j + (G_j.d) F_i + (F_i.d) G_j]
+//                     + br [(T_j.d) H_i + (H_i.d) T_j + (H_j.d) T_i + (T_i.d) H_j].
+// A term that multiplies an i-vector is summed as a scalar over the tile on
+// the i-side, one that multiplies a j-vector as a scalar per j on the j-side.
+// The j-side sums of a warp for one j (13 with angular blocks, 8 without)
+// are added across its lanes by a transposing butterfly and into the tile's
+// shared sums with one atomic per value.  Work items, diagonal tiles and the
+// FP64 accumulators acc[particle][C] are those of the packed translation
+// form above.  At r = 0 (self or coincident pairs) the gradient is taken as
+// zero, as in the one-sided form; only the mobility parts contribute.
+// ---------------------------------------------------------------------------
+
+// V per-lane values (V = 8 or 16) reduced over the warp: on return lane l
+// holds the sum over all 32 lanes of value l / (32 / V).
+template <typename R, int V>
+__device__ __forceinline__ R warp_transpose_sum(R (&v)[V], int lane) {
+    static_assert(V == 8 || V == 16, "butterfly width");
+#pragma unroll
+    for (int h = V / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = lane & o;
+#pragma unroll
+        for (int r = 0; r < h; ++r) {
+            const R keep = up ? v[r + h] : v[r], send = up ? v[r] : v[r + h];
+            v[r] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+#pragma unroll
+    for (int o = 16 / V; o >= 1; o >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    return v[0];
+}
+
+template <bool ANG> constexpr int sym_s_words() { return ANG ? 4 : 3; }    // R4 words per j in the tile
+template <bool ANG> constexpr int sym_s_vals() { return ANG ? 13 : 8; }    // j-side sums per j
+template <bool ANG> constexpr int sym_s_width() { return ANG ? 16 : 8; }   // butterfly width
+
+template <typename R, bool ANG, int NT, int NI>
+constexpr size_t adj_sym_s_smem_bytes() {
+    return (size_t)sym_s_words<ANG>() * NT * sizeof(typename V4<R>::type) +
+           (size_t)sym_s_vals<ANG>() * (NT + 1) * sizeof(R) + adj_running_bytes<R, ANG, NT, NI>();
+}
+
+template <typename R, bool ANG>
+struct SymAcc {
+    static constexpr int C = ANG ? 9 : 6;
+    R p[C];             // current-tile partials: dX(3) dF(3) [dT(3)]
+    R sG, sF, sH, sT;   // scalars multiplying G_i, F_i, H_i, T_i
+};
+
+// One pair of the symmetric form: the i-side partials and scalars and, for
+// SYM, the j-side sums v = jX(3) jF(3) [jT(3)] then the scalars of F_j, G_j
+// [, T_j, H_j].  gg is g where the gradient is taken (r > 0), else 0.
+template <typename R, bool ANG, bool SYM>
+__device__ __forceinline__ void sym_pair(R dx, R dy, R dz, const Coef<R>& c, R gg, const IData<R, ANG>& I,
+                                         const IData<R, ANG>& J, SymAcc<R, ANG>& a, R* v) {
+    const R a1 = fma(I.G[0], dx, fma(I.G[1], dy, I.G[2] * dz));   // G_i.d
+    const R a2 = fma(I.F[0], dx, fma(I.F[1], dy, I.F[2] * dz));   // F_i.d
+    const R b1 = fma(J.F[0], dx, fma(J.F[1], dy, J.F[2] * dz));   // F_j.d
+    const R b2 = fma(J.G[0], dx, fma(J.G[1], dy, J.G[2] * dz));   // G_j.d
+    const R S1 = fma(I.G[0], J.F[0], fma(I.G[1], J.F[1], fma(I.G[2], J.F[2],
+                 fma(I.F[0], J.G[0], fma(I.F[1], J.G[1], I.F[2] * J.G[2])))));
+    R cd = fma(c.Ap, S1, c.Bp * fma(a1, b1, a2 * b2));
+    const R BA1 = c.B * a1, BA2 = c.B * a2, BB1 = c.B * b1, BB2 = c.B * b2;
+    R V[3] = {R(0), R(0), R(0)};
+    R rC1 = R(0), rC2 = R(0), rE1 = R(0), rE2 = R(0);
+    if constexpr (ANG) {
+        const R c1 = fma(I.H[0], dx, fma(I.H[1], dy, I.H[2] * dz));   // H_i.d
+        const R c2 = fma(I.T[0], dx, fma(I.T[1], dy, I.T[2] * dz));   // T_i.d
+        const R e1 = fma(J.T[0], dx, fma(J.T[1], dy, J.T[2] * dz));   // T_j.d
+        const R e2 = fma(J.H[0], dx, fma(J.H[1], dy, J.H[2] * dz));   // H_j.d
+        const R R1 = fma(I.H[0], J.T[0], fma(I.H[1], J.T[1], fma(I.H[2], J.T[2],
+                     fma(I.T[0], J.H[0], fma(I.T[1], J.H[1], I.T[2] * J.H[2])))));
+        // P = G_i x T_j + H_i x F_j + T_i x G_j + F_i x H_j
+        R P[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int u = (q + 1) % 3, w = (q + 2) % 3;
+            P[q] = fma(I.G[u], J.T[w], fma(-I.G[w], J.T[u], fma(I.H[u], J.F[w], fma(-I.H[w], J.F[u],
+                   fma(I.T[u], J.G[w], fma(-I.T[w], J.G[u], fma(I.F[u], J.H[w], -I.F[w] * J.H[u])))))));
+        }
+        cd = fma(c.arp, R1, fma(c.brp, fma(c1, e1, c2 * e2), fma(c.gp, fma(dx, P[0], fma(dy, P[1], dz * P[2])), cd)));
+#pragma unroll
+        for (int q = 0; q < 3; ++q) V[q] = gg * P[q];
+        rC1 = c.br * c1; rC2 = c.br * c2; rE1 = c.br * e1; rE2 = c.br * e2;
+    }
+    V[0] = fma(cd, dx, V[0]);
+    V[1] = fma(cd, dy, V[1]);
+    V[2] = fma(cd, dz, V[2]);
+    const R d[3] = {dx, dy, dz};
+    // i-side
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        R t = fma(BA2, J.G[q], fma(BA1, J.F[q], V[q]));
+        if constexpr (ANG) t = fma(rC2, J.H[q], fma(rC1, J.T[q], t));
+        a.p[q] += t;
+        a.p[3 + q] = fma(BB2, d[q], fma(c.A, J.G[q], a.p[3 + q]));
+    }
+    a.sG += BB1;
+    a.sF += BB2;
+    if constexpr (ANG) {
+        a.sH += rE1;
+        a.sT += rE2;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int u = (q + 1) % 3, w = (q + 2) % 3;
+            // dF_i += g H_j x d ; dT_i += g G_j x d + ar H_j + br (H_j.d) d
+            a.p[3 + q] = fma(c.g, fma(J.H[u], d[w], -J.H[w] * d[u]), a.p[3 + q]);
+            a.p[6 + q] = fma(rE2, d[q], fma(c.ar, J.H[q], fma(c.g, fma(J.G[u], d[w], -J.G[w] * d[u]), a.p[6 + q])));
+        }
+    }
+    if constexpr (SYM) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            R t = fma(BB2, I.F[q], fma(BB1, I.G[q], V[q]));
+            if constexpr (ANG) t = fma(rE2, I.T[q], fma(rE1, I.H[q], t));
+            v[q] += t;
+            v[3 + q] = fma(BA1, d[q], fma(c.A, I.G[q], v[3 + q]));
+        }
+        if constexpr (ANG) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const int u = (q + 1) % 3, w = (q + 2) % 3;
+                // dF_j -= g H_i x d ; dT_j += -g G_i x d + ar H_i + br (H_i.d) d
+                v[3 + q] = fma(-c.g, fma(I.H[u], d[w], -I.H[w] * d[u]), v[3 + q]);
+                v[6 + q] = fma(rC1, d[q], fma(c.ar, I.H[q], fma(-c.g, fma(I.G[u], d[w], -I.G[w] * d[u]), v[6 + q])));
+            }
+            v[9] += BA1;    // x F_j
+            v[10] += BA2;   // x G_j
+            v[11] += rC1;   // x T_j
+            v[12] += rC2;   // x H_j
+        } else {
+            v[6] += BA1;
+            v[7] += BA2;
+        }
+    }
+}
+
+template <typename R, bool ANG, int NT, int NI>
+__global__ void __launch_bounds__(NT) rpy_adjoint_sym_s_kernel(const typename V4<R>::type* __restrict__ pos4,
+                                                               const void* __restrict__ Fp, const void* __restrict__ Tp,
+                                                               const void* __restrict__ Gp, const void* __restrict__ Hp,
+                                                               int f64, int64_t N, const int4* __restrict__ items,
+                                                               RpyConst<R> k, double* __restrict__ acc) {
+    using R4 = typename V4<R>::type;
+    constexpr int C = SymAcc<R, ANG>::C;
+    constexpr int W = sym_s_words<ANG>();
+    constexpr int NV = sym_s_vals<ANG>();
+    constexpr int VW = sym_s_width<ANG>();
+    constexpr int SJ = NT + 1;   // j-side rows one word apart in bank
+    extern __shared__ __align__(32) unsigned char adj_sym_s_smem[];
+    R4* s_t = reinterpret_cast<R4*>(adj_sym_s_smem);   // [w][jj]
+    R* s_j = reinterpret_cast<R*>(s_t + W * NT);       // [v][jj]
+    R* s_hi = s_j + NV * SJ;                           // [c][q][tid]
+    R* s_lo = s_hi + (sizeof(R) == 4 ? C * NI * NT : 0);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int4 item = items[blockIdx.x];
+    const int64_t b = item.x, t_begin = item.y, t_end = item.z;
+    const int64_t i0 = b * (NT * NI);
+    const int64_t diag_end = (b + 1) * NI;   // first tile after the block's own range
+    const R pad = (R)kPadCoord;
+
+    IData<R, ANG> I[NI];
+    SymAcc<R, ANG> a[NI];
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+        const int64_t i = i0 + (int64_t)q * NT + tid;
+        const bool in = i < N && LM_INBOUNDS(i >= 0, 12, i);
+        if (in) {
+            const R4 p = pos4[i];
+            I[q].x = p.x; I[q].y = p.y; I[q].z = p.z;
+        } else {
+            I[q].x = I[q].y = I[q].z = -pad;
+        }
+        const int64_t ii = in ? i : 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            I[q].F[c] = in ? ld<R>(Fp, f64, 3 * ii + c) : R(0);
+            I[q].G[c] = in ? ld<R>(Gp, f64, 3 * ii + c) : R(0);
+            if constexpr (ANG) {
+                I[q].T[c] = in ? ld<R>(Tp, f64, 3 * ii + c) : R(0);
+                I[q].H[c] = in ? ld<R>(Hp, f64, 3 * ii + c) : R(0);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            a[q].p[c] = R(0);
+            s_hi[(c * NI + q) * NT + tid] = R(0);
+            if (sizeof(R) == 4) s_lo[(c * NI + q) * NT + tid] = R(0);
+        }
+        a[q].sG = a[q].sF = a[q].sH = a[q].sT = R(0);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s_j[v * SJ + tid] = R(0);
+
+    const int64_t jlo = t_begin * NT;
+    const int64_t jhi = (t_end * NT < N) ? t_end * NT : N;
+    // register prefetch of this thread's j of the next tile
+    R nv[4 * W];
+    auto fetch = [&](int64_t j) {
+        const bool in = j < jhi && LM_INBOUNDS(j >= 0 && j < N, 13, j);
+        const int64_t jj = in ? j : 0;
+        if (in) {
+            const R4 p = pos4[jj];
+            nv[0] = p.x; nv[1] = p.y; nv[2] = p.z;
+        } else {
+            nv[0] = nv[1] = nv[2] = pad;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            nv[3 + c] = in ? ld<R>(Fp, f64, 3 * jj + c) : R(0);
+            nv[6 + c] = in ? ld<R>(Gp, f64, 3 * jj + c) : R(0);
+            if constexpr (ANG) {
+                nv[9 + c] = in ? ld<R>(Tp, f64, 3 * jj + c) : R(0);
+                nv[12 + c] = in ? ld<R>(Hp, f64, 3 * jj + c) : R(0);
+            }
+        }
+#pragma unroll
+        for (int c = ANG ? 15 : 9; c < 4 * W; ++c) nv[c] = R(0);
+    };
+    fetch(jlo + tid);
+
+    for (int64_t t = t_begin; t < t_end; ++t) {
+        const int64_t jt = t * NT;
+        const bool sym = t >= diag_end;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            R4 q;
+            q.x = nv[4 * w]; q.y = nv[4 * w + 1]; q.z = nv[4 * w + 2]; q.w = nv[4 * w + 3];
+            s_t[w * NT + tid] = q;
+        }
+        __syncthreads();
+        if (jt + NT < jhi) fetch(jt + NT + tid);
+#pragma unroll 1
+        for (int jj = 0; jj < NT; ++jj) {
+            R wv[4 * W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const R4 q = s_t[w * NT + jj];
+                wv[4 * w] = q.x; wv[4 * w + 1] = q.y; wv[4 * w + 2] = q.z; wv[4 * w + 3] = q.w;
+            }
+            IData<R, ANG> J;
+            J.x = wv[0]; J.y = wv[1]; J.z = wv[2];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                J.F[c] = wv[3 + c];
+                J.G[c] = wv[6 + c];
+                if constexpr (ANG) { J.T[c] = wv[9 + c]; J.H[c] = wv[12 + c]; }
+            }
+            R dx[NI], dy[NI], dz[NI], r2[NI];
+            R mn = R(0);
+#pragma unroll
+            for (int q = 0; q < NI; ++q) {
+                dx[q] = I[q].x - J.x; dy[q] = I[q].y - J.y; dz[q] = I[q].z - J.z;
+                r2[q] = fma(dx[q], dx[q], fma(dy[q], dy[q], dz[q] * dz[q]));
+                mn = (q == 0) ? r2[q] : fmin(mn, r2[q]);
+            }
+            const bool near = __any_sync(0xffffffffu, mn < k.four_a2);
+            R v[VW];
+#pragma unroll
+            for (int c = 0; c < VW; ++c) v[c] = R(0);
+#pragma unroll
+            for (int q = 0; q < NI; ++q) {
+                Coef<R> c;
+                bool g = true;
+                if (near) g = exact_coef<R, ANG>(r2[q], k, c);
+                else far_coef<R, ANG>(r2[q], k, c);
+                R gg = R(0);
+                if constexpr (ANG) gg = g ? c.g : R(0);
+                if (sym) sym_pair<R, ANG, true>(dx[q], dy[q], dz[q], c, gg, I[q], J, a[q], v);
+                else sym_pair<R, ANG, false>(dx[q], dy[q], dz[q], c, gg, I[q], J, a[q], v);
+            }
+            if (sym) {
+                const R tot = warp_transpose_sum<R, VW>(v, lane);
+                constexpr int per = 32 / VW;
+                if (lane % per == 0 && lane / per < NV) atomicAdd(&s_j[(lane / per) * SJ + jj], tot);
+            }
+        }
+        // apply the tile's i-side scalars and fold into the running sums
+#pragma unroll
+        for (int q = 0; q < NI; ++q) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                R t = fma(a[q].sG, I[q].G[c], fma(a[q].sF, I[q].F[c], a[q].p[c]));
+                if constexpr (ANG) t = fma(a[q].sH, I[q].H[c], fma(a[q].sT, I[q].T[c], t));
+                a[q].p[c] = t;
+            }
+            a[q].sG = a[q].sF = a[q].sH = a[q].sT = R(0);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const int o = (c * NI + q) * NT + tid;
+                fold(&s_hi[o], &s_lo[o], a[q].p[c]);
+            }
+        }
+        __syncthreads();
+        if (sym) {
+            // this tile's j-side sums of the CTA: dX_j -= vector + scalars x (F_j, G_j[, T_j, H_j])
+            const int64_t j = jt + tid;
+            if (j < N && LM_INBOUNDS(j >= 0, 14, j)) {
+                R wv[4 * W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    const R4 q = s_t[w * NT + tid];
+                    wv[4 * w] = q.x; wv[4 * w + 1] = q.y; wv[4 * w + 2] = q.z; wv[4 * w + 3] = q.w;
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    R x = s_j[c * SJ + tid];
+                    if constexpr (ANG) {
+                        x = fma(s_j[9 * SJ + tid], wv[3 + c], fma(s_j[10 * SJ + tid], wv[6 + c], x));
+                        x = fma(s_j[11 * SJ + tid], wv[9 + c], fma(s_j[12 * SJ + tid], wv[12 + c], x));
+                    } else {
+                        x = fma(s_j[6 * SJ + tid], wv[3 + c], fma(s_j[7 * SJ + tid], wv[6 + c], x));
+                    }
+                    atomicAdd(&acc[C * j + c], -(double)x);
+                }
+#pragma unroll
+                for (int c = 3; c < C; ++c) atomicAdd(&acc[C * j + c], (double)s_j[c * SJ + tid]);
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) s_j[v * SJ + tid] = R(0);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+        const int64_t i = i0 + (int64_t)q * NT + tid;
+        if (i >= N) continue;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int o = (c * NI + q) * NT + tid;
+            atomicAdd(&acc[C * i + c], (double)s_hi[o] + (sizeof(R) == 4 ? (double)s_lo[o] : 0.0));
+        }
+    }
+}
+
+template <typename R, bool ANG, int NI>
+cudaError_t launch_adj_sym_s_t(const AdjointArgs& a, cudaStream_t s) {
+    constexpr int NT = 128;
+    constexpr int C = SymAcc<R, ANG>::C;
+    if (a.sym_items == nullptr || a.sym_acc == nullptr || a.n_sym_items < 1) return cudaErrorInvalidValue;
+    if (a.n_sym_items > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    const double c8 = 1.0 / (8.0 * 3.14159265358979323846 * a.eta);
+    const RpyConst<R> k = make_rpy_const<R>(a.a);
+    constexpr size_t dyn = adj_sym_s_smem_bytes<R, ANG, NT, NI>();
+    static std::atomic<unsigned long long> attr_devs{0};  // devices whose limit is raised
+    if (cudaError_t e = smem_attr_once(attr_devs, rpy_adjoint_sym_s_kernel<R, ANG, NT, NI>, dyn)) return e;
+    cudaError_t e = cudaMemsetAsync(a.sym_acc, 0, (size_t)C * a.N * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    rpy_adjoint_sym_s_kernel<R, ANG, NT, NI><<<(unsigned)a.n_sym_items, NT, dyn, s>>>(
+        static_cast<const typename V4<R>::type*>(a.pos4), a.F, ANG ? a.T : nullptr, a.G, ANG ? a.H : nullptr, a.fp64,
+        a.N, static_cast<const int4*>(a.sym_items), k, a.sym_acc);
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t tot = (int64_t)C * a.N;
+    adj_sym_store_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a.sym_acc, C, a.N, c8, a.dX, a.dF,
+                                                                       ANG ? a.dT : nullptr, a.fp64);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// i-particles per thread of the symmetric scalar form: FP64 1; FP32 with
+// angular blocks 2 or 4.
+inline bool sym_s_ilp_supported(int fp64, int ilp) { return fp64 ? ilp == 1 : (ilp == 2 || ilp == 4); }
+
+cudaError_t launch_adj_sym_s(const AdjointArgs& a, cudaStream_t s) {
+    if (a.fp64) return a.angular ? launch_adj_sym_s_t<double, true, 1>(a, s) : launch_adj_sym_s_t<double, false, 1>(a, s);
+    if (!a.angular) return cudaErrorInvalidConfiguration;   // FP32 translation: the packed symmetric form
+    return a.ilp == 4 ? launch_adj_sym_s_t<float, true, 4>(a, s) : launch_adj_sym_s_t<float, true, 2>(a, s);
+}
+
+template <typename R, bool ANG, int NI>
+int adj_sym_s_occupancy() {
+    int n = 0;
+    constexpr size_t dyn = adj_sym_s_smem_bytes<R, ANG, 128, NI>();
+    cudaError_t e = cudaFuncSetAttribute(rpy_adjoint_sym_s_kernel<R, ANG, 128, NI>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rpy_adjoint_sym_s_kernel<R, ANG, 128, NI>, 128, dyn);
     return e == cudaSuccess ? n : 0;
 }
 
@@ -1057,16 +1453,23 @@ int adjoint_partial_components(int angular) { return angular ? 9 : 6; }
 int adjoint_ilp(int fp64, int angular) { return fp64 ? 1 : (angular ? 2 : 4); }
 
 bool adjoint_config_supported(int fp64, int angular, int threads, int ilp, int uj) {
-    if (fp64 || angular) return threads == 128 && ilp == adjoint_ilp(fp64, angular) && uj <= 1;
+    if (fp64 || angular) {
+        if (uj == 3) return threads == 128 && sym_s_ilp_supported(fp64, ilp);   // symmetric scalar form
+        return threads == 128 && ilp == adjoint_ilp(fp64, angular) && uj >= 0 && uj <= 1;
+    }
     return (threads == 128 || threads == 256) && (ilp == 2 || ilp == 4) && uj >= 0 && uj <= 3;
 }
 
 cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s) {
     if (a.N <= 0) return cudaSuccess;
     if (!adjoint_config_supported(a.fp64, a.angular, a.threads, a.ilp, a.uj)) return cudaErrorInvalidConfiguration;
-    if (a.fp64) return a.angular ? launch_adj_t<double, true, 1>(a, s) : launch_adj_t<double, false, 1>(a, s);
-    // FP32: translation blocks use the packed (f32x2) kernels, one-sided or symmetric
-    if (a.angular) return launch_adj_t<float, true, 2>(a, s);
+    // FP64, and FP32 with angular blocks: the scalar kernels, one-sided or symmetric
+    if (a.fp64 || a.angular) {
+        if (a.uj == 3) return launch_adj_sym_s(a, s);
+        if (a.fp64) return a.angular ? launch_adj_t<double, true, 1>(a, s) : launch_adj_t<double, false, 1>(a, s);
+        return launch_adj_t<float, true, 2>(a, s);
+    }
+    // FP32 translation blocks: the packed (f32x2) kernels, one-sided or symmetric
     return a.uj == 3 ? launch_adj_sym(a, s) : launch_adj_x2(a, s);
 }
 
@@ -1081,6 +1484,10 @@ int adjoint_ctas_per_sm(int fp64, int angular, int threads, int ilp, int uj) {
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);          \
         if (e == cudaSuccess)                                                                     \
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rpy_adjoint_kernel<R, ANG, 128, NI>, 128, dyn); \
+    }
+    if ((fp64 || angular) && uj == 3) {
+        if (fp64) return angular ? adj_sym_s_occupancy<double, true, 1>() : adj_sym_s_occupancy<double, false, 1>();
+        return ilp == 4 ? adj_sym_s_occupancy<float, true, 4>() : adj_sym_s_occupancy<float, true, 2>();
     }
     if (fp64 && angular) LM_AOCC(double, true, 1)
     else if (fp64) LM_AOCC(double, false, 1)

@@ -488,21 +488,21 @@ bool valid_name(const char* p) {
 }  // namespace
 
 namespace {
-// Adjoint launch configuration: packed = 0 for the scalar FP64 / angular
-// kernels; for the packed FP32 translation kernel, packed = j-particles per
-// overlap vote (1 or 2).
+// Adjoint launch configuration.  FP64 and angular blocks: the symmetric
+// scalar form (packed = 3, item size chosen at launch), 1.5x faster than the
+// one-sided scalar kernel at N = 65536 (FP32) and 16384 (FP64).  FP32
+// translation: the packed one-sided kernel, packed = j-particles per overlap
+// vote (the autotuner also times the symmetric form).
 lm_pair_config default_adjoint_config(const lm_solver* s) {
-    lm_pair_config c{128, lmk::adjoint_ilp(s->fp64, s->angular), 1, (!s->fp64 && !s->angular) ? 1 : 0};
-    int occ = std::max(1, lmk::adjoint_ctas_per_sm(s->fp64, s->angular, c.threads, c.ilp, c.packed));
+    if (s->fp64 || s->angular) return lm_pair_config{128, lmk::adjoint_ilp(s->fp64, s->angular), 0, 3};
+    lm_pair_config c{128, lmk::adjoint_ilp(0, 0), 1, 1};
+    int occ = std::max(1, lmk::adjoint_ctas_per_sm(0, 0, c.threads, c.ilp, c.packed));
     c.splits = auto_splits(s->N, c.threads, c.ilp, occ * s->sm_count);
     const int64_t nblk = (s->N + (int64_t)c.threads * c.ilp - 1) / ((int64_t)c.threads * c.ilp);
     if (nblk * lmk::mdot_effective_splits(s->N, c.threads, c.splits) < (int64_t)occ * s->sm_count) {
-        // too few CTAs to fill the GPU: splits of down to one j-tile, and for the
-        // packed kernel the smaller i-blocks
-        if (!s->fp64 && !s->angular) {
-            c.ilp = 2;
-            occ = std::max(1, lmk::adjoint_ctas_per_sm(s->fp64, s->angular, c.threads, c.ilp, c.packed));
-        }
+        // too few CTAs to fill the GPU: the smaller i-blocks and splits of down to one j-tile
+        c.ilp = 2;
+        occ = std::max(1, lmk::adjoint_ctas_per_sm(0, 0, c.threads, c.ilp, c.packed));
         c.splits = auto_splits(s->N, c.threads, c.ilp, occ * s->sm_count, 1);
     }
     return c;
@@ -532,7 +532,7 @@ int64_t sym_auto_chunk(const lm_solver* s, int threads, int ilp) {
     const int64_t BI = (int64_t)threads * ilp;
     const int64_t nblk = (s->N + BI - 1) / BI;
     const int64_t T = (s->N + threads - 1) / threads;
-    const int occ = std::max(1, lmk::adjoint_ctas_per_sm(0, 0, threads, ilp, 3));
+    const int occ = std::max(1, lmk::adjoint_ctas_per_sm(s->fp64, s->angular, threads, ilp, 3));
     const double total = (double)nblk * (double)T - (double)ilp * (double)nblk * (double)(nblk - 1) / 2.0;
     return std::max<int64_t>(1, (int64_t)std::ceil(total / (6.0 * occ * s->sm_count)));
 }
@@ -576,7 +576,8 @@ lm_status run_adjoint(lm_solver* s, const void* F, const void* T, const void* G,
             s->sym_key = key;
             s->sym_n_items = (int64_t)items.size();
         }
-        LM_CUDA(s->sym_acc.ensure((size_t)6 * s->N * sizeof(double)), "allocating adjoint accumulators");
+        LM_CUDA(s->sym_acc.ensure((size_t)lmk::adjoint_partial_components(s->angular) * s->N * sizeof(double)),
+                "allocating adjoint accumulators");
         a.sym_items = s->sym_items.p;
         a.n_sym_items = s->sym_n_items;
         a.sym_acc = s->sym_acc.as<double>();

@@ -108,6 +108,60 @@ def test_adjoint_symmetric_form_overlaps_across_blocks(orc):
         assert rel(host(dF3), gF) <= 1e-5
 
 
+@pytest.mark.parametrize("fp64,angular,ilp", [(False, True, 2), (False, True, 4), (True, True, 1), (True, False, 1)])
+def test_adjoint_symmetric_scalar_form(orc, fp64, angular, ilp):
+    """The symmetric form of the scalar adjoint (angular blocks in FP32, and
+    FP64): each unordered pair evaluated once and added to both particles.
+    A coincident and an overlapping pair whose particles lie in different
+    i-blocks, N ragged for every tile; items of one tile, of the automatic
+    size and of five tiles; dX alone and dF, dT alone."""
+    n = 700
+    s_ = I.cube_suspension(63, n, 0.15, 1.0, angular=angular, fp32=not fp64)
+    pos = s_.pos.copy()
+    pos[500] = pos[10]                                          # coincident
+    pos[600] = pos[20] + np.array([0.5, 0.1, 0.0], pos.dtype)  # overlapping
+    s = lm.lm_create(1.0, 1.0, angular, lm.LM_FP64 if fp64 else lm.LM_FP32C)
+    lm.lm_set_positions(s, dev(pos))
+    gX = orc.grad(pos, s_.F, s_.T, s_.G, s_.H, 1.0, 1.0, angular)
+    gF, gT = orc.mdot(pos, s_.G, s_.H, 1.0, 1.0, angular)
+    tol = 1e-11 if fp64 else 1e-5
+    args = (dev(s_.F), dev(s_.T), dev(s_.G), dev(s_.H))
+    for chunk in (1, 0, 5):
+        lm.lm_set_adjoint_config(s, 128, ilp, chunk, 3)
+        assert lm.lm_get_adjoint_config(s)["packed"] == 3
+        dX, dF, dT = lm.lm_mdot_backward(s, *args)
+        assert rel(host(dX), gX) <= tol, (chunk, rel(host(dX), gX))
+        assert rel(host(dF), gF) <= tol, (chunk, rel(host(dF), gF))
+        if angular:
+            assert rel(host(dT), gT) <= tol, (chunk, rel(host(dT), gT))
+    dX2, dF2, dT2 = lm.lm_mdot_backward(s, *args, need_dF=False)
+    assert dF2 is None and dT2 is None and rel(host(dX2), gX) <= tol
+    dX3, dF3, dT3 = lm.lm_mdot_backward(s, *args, need_dX=False)
+    assert dX3 is None and rel(host(dF3), gF) <= tol
+    if angular:
+        assert rel(host(dT3), gT) <= tol
+
+
+@pytest.mark.parametrize("packed", [0, 3])
+def test_adjoint_6n_full_size_sampled_rows(orc, packed):
+    """The FP32 adjoint with angular blocks at N = 65536 (the adjoint
+    benchmark's suspension, with torques and their cotangents), one-sided
+    (packed 0) and symmetric (packed 3), against the oracle's gradient and
+    products on 64 sampled particles."""
+    c = I.ADJOINT_N65536
+    s_ = I.cube_suspension(c["seed"], c["n"], c["phi"], c["a"], angular=True, fp32=True)
+    s = lm.lm_create(c["eta"], c["a"], True, lm.LM_FP32C)
+    lm.lm_set_positions(s, dev(s_.pos))
+    lm.lm_set_adjoint_config(s, 128, 2, 0, packed)
+    dX, dF, dT = lm.lm_mdot_backward(s, dev(s_.F), dev(s_.T), dev(s_.G), dev(s_.H))
+    rows = np.sort(np.random.default_rng(8).choice(c["n"], 64, replace=False))
+    gX = orc.grad(s_.pos, s_.F, s_.T, s_.G, s_.H, c["a"], c["eta"], True, rows=rows)
+    gF, gT = orc.mdot(s_.pos, s_.G, s_.H, c["a"], c["eta"], True, rows=rows)
+    assert rel(host(dX)[rows], gX) <= 1e-5, rel(host(dX)[rows], gX)
+    assert rel(host(dF)[rows], gF) <= 1e-5, rel(host(dF)[rows], gF)
+    assert rel(host(dT)[rows], gT) <= 1e-5, rel(host(dT)[rows], gT)
+
+
 def test_adjoint_skips_outputs_and_handles_coincident(orc):
     pos = np.array([[0, 0, 0], [0, 0, 0], [0.5, 0.1, 0.0], [3.0, 0.0, 1.0]], np.float64)
     rng = np.random.default_rng(2)
