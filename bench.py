@@ -834,7 +834,7 @@ def run_single(args, ws, rank, local, pcfg, acfg):
                         autotune=not args.no_autotune)
         extra = {"forward_ms": r["forward_ms"], "backward_ms": r["backward_ms"],
                  "backward_over_forward": r["backward_over_forward"], "pair_config": r["pair_config"],
-                 "adjoint_config": r["adjoint_config"], "l2": r["l2"]}
+                 "adjoint_config": r["adjoint_config"], "angular": r["angular"], "l2": r["l2"]}
     else:
         r = bd_leg(args.steps, args.warmup, dist, local, rank, autotune=not args.no_autotune)
         extra = {"N_total": r["N_total"], "ms_per_bd_step": r["ms_per_bd_step"],
