@@ -541,7 +541,7 @@ def adjoint_leg(steps, warmup, dist, local, *, pair_config=None, adjoint_config=
     angular = {"forward_ms": fwd6, "backward_ms": bwd6, "backward_over_forward": bwd6 / fwd6,
                "steps": 3, "pair_config": lm.lm_get_pair_config(solver6),
                "adjoint_config": lm.lm_get_adjoint_config(solver6),
-               "desc": "same N and positions with torques; backward = dX, dF, dT (symmetric scalar form)"}
+               "desc": "same N and positions with torques; backward = dX, dF, dT (the default symmetric form)"}
     del solver6
     return {"value": pairs / (tmax / 1e3), "unit": UNIT, "ms_per_step": tmax / steps, "steps": steps,
             "warmup": warmup,

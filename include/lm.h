@@ -262,7 +262,7 @@ lm_status lm_ab_step(lm_solver *solver, const void *forces, const void *torques,
  *   The gradient of a pair term at r = 0 (coincident particles) is taken
  *   as zero.  Open geometry only: a single-wall solver gives
  *   LM_ERR_UNSUPPORTED_GEOMETRY.
- *   For LM_FP64 and for angular blocks the default kernel is the symmetric
+ *   For LM_FP64 and for angular blocks the default kernel is a symmetric
  *   one, whose two sides meet in FP64 atomic adds: the last bits of the
  *   results can vary from run to run.  lm_set_adjoint_config with packed 0
  *   selects the one-sided kernel, which is bitwise reproducible.
@@ -319,13 +319,17 @@ lm_status lm_set_pair_config(lm_solver *solver, const lm_pair_config *cfg);
  *     so the last bits of an FP64 sum, and rarely the last bit of an FP32
  *     output, can differ from run to run;
  * otherwise (LM_FP64, or angular blocks) threads 128 and packed
- *   3: the symmetric scalar kernel (the default): each unordered pair once,
- *     its gradient added to one particle and subtracted from the other, the
- *     mobility parts of both directions from the same coefficients; ilp 1
- *     (LM_FP64) or 2, 4 (LM_FP32C); splits = tiles per work item (0: chosen
- *     from N).  1.5x faster than packed 0 at N = 65536 (FP32, angular) and
- *     N = 16384 (FP64, angular).  Its FP64 atomic adds make the last bits of
- *     the results vary from run to run, as above;
+ *   3: the symmetric scalar kernel (the LM_FP64 default): each unordered
+ *     pair once, its gradient added to one particle and subtracted from the
+ *     other, the mobility parts of both directions from the same
+ *     coefficients; ilp 1 (LM_FP64) or 2, 4 (LM_FP32C); 1.5x faster than
+ *     packed 0 at N = 16384 (FP64, angular);
+ *   4: the same in packed f32x2 form, two i-particles per instruction
+ *     (LM_FP32C with angular blocks, ilp 2 or 4; the default there with
+ *     ilp 4): 1.7x faster than packed 0 at N = 65536;
+ *     for 3 and 4, splits = tiles per work item (0: chosen from N), and the
+ *     FP64 atomic adds make the last bits of the results vary from run to
+ *     run, as above;
  *   0: the one-sided scalar kernel, ilp 1 (LM_FP64) or 2 (LM_FP32C);
  *     splits = j-range chunks per i-block.
  * splits 0 = automatic.  Unsupported combinations give LM_ERR_INVALID_ARG. */

@@ -1418,6 +1418,369 @@ int adj_sym_s_occupancy() {
     return e == cudaSuccess ? n : 0;
 }
 
+// ---------------------------------------------------------------------------
+// Packed (f32x2) form of the symmetric adjoint with angular blocks
+// (AdjointArgs::uj == 4, FP32): the pair of rpy_adjoint_sym_s_kernel with
+// two i-particles per packed instruction; the j-words enter as the same
+// scalar in both lanes.  Packed operands take no negation, so the cross
+// products with d use g d and -g d, and P is formed as the difference of
+// its two halves.  Same work items, j-side butterfly and FP64 accumulators.
+// ---------------------------------------------------------------------------
+struct PCoef2 {
+    float2 A, B, Ap, Bp, g, gp, ar, arp, br, brp;
+};
+
+struct Sym6Acc2 {
+    float2 p[9];             // dX(3) dF(3) dT(3) of the tile, two i-particles
+    float2 sG, sF, sH, sT;   // scalars multiplying G_i, F_i, H_i, T_i
+};
+
+// j-side sums v (SYM): jX(3) jF(3) jT(3), then the scalars of F_j, G_j, T_j, H_j.
+template <bool SYM>
+__device__ __forceinline__ void sym6_pair2(const float2 (&d)[3], const PCoef2& c, float2 gg, const float2 (&Fi)[3],
+                                           const float2 (&Gi)[3], const float2 (&Ti)[3], const float2 (&Hi)[3],
+                                           const float (&jw)[16], Sym6Acc2& a, float2 (&v)[13]) {
+    // j-words: (-x, -y, -z, Fx) (Fy, Fz, Gx, Gy) (Gz, Tx, Ty, Tz) (Hx, Hy, Hz, 0)
+    const float* Fj = jw + 3;
+    const float* Gj = jw + 6;
+    const float* Tj = jw + 9;
+    const float* Hj = jw + 12;
+    auto doti = [&](const float2 (&w)[3]) { return fma2(w[0], d[0], fma2(w[1], d[1], mul2(w[2], d[2]))); };
+    auto dotj = [&](const float* w) { return fma2(bc2(w[0]), d[0], fma2(bc2(w[1]), d[1], mul2(bc2(w[2]), d[2]))); };
+    const float2 a1 = doti(Gi), a2 = doti(Fi), c1 = doti(Hi), c2 = doti(Ti);
+    const float2 b1 = dotj(Fj), b2 = dotj(Gj), e1 = dotj(Tj), e2 = dotj(Hj);
+    const float2 S1 = fma2(Gi[0], bc2(Fj[0]), fma2(Gi[1], bc2(Fj[1]), fma2(Gi[2], bc2(Fj[2]),
+                      fma2(Fi[0], bc2(Gj[0]), fma2(Fi[1], bc2(Gj[1]), mul2(Fi[2], bc2(Gj[2])))))));
+    const float2 R1 = fma2(Hi[0], bc2(Tj[0]), fma2(Hi[1], bc2(Tj[1]), fma2(Hi[2], bc2(Tj[2]),
+                      fma2(Ti[0], bc2(Hj[0]), fma2(Ti[1], bc2(Hj[1]), mul2(Ti[2], bc2(Hj[2])))))));
+    // P = G_i x T_j + H_i x F_j + T_i x G_j + F_i x H_j = X - Y
+    float2 P[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int u = (q + 1) % 3, w = (q + 2) % 3;
+        const float2 X = fma2(Gi[u], bc2(Tj[w]), fma2(Hi[u], bc2(Fj[w]), fma2(Ti[u], bc2(Gj[w]), mul2(Fi[u], bc2(Hj[w])))));
+        const float2 Y = fma2(Gi[w], bc2(Tj[u]), fma2(Hi[w], bc2(Fj[u]), fma2(Ti[w], bc2(Gj[u]), mul2(Fi[w], bc2(Hj[u])))));
+        P[q] = fma2(bc2(-1.f), Y, X);
+    }
+    const float2 dP = fma2(d[0], P[0], fma2(d[1], P[1], mul2(d[2], P[2])));
+    const float2 cd = fma2(c.Ap, S1, fma2(c.Bp, fma2(a1, b1, mul2(a2, b2)),
+                      fma2(c.arp, R1, fma2(c.brp, fma2(c1, e1, mul2(c2, e2)), mul2(c.gp, dP)))));
+    const float2 BA1 = mul2(c.B, a1), BA2 = mul2(c.B, a2), BB1 = mul2(c.B, b1), BB2 = mul2(c.B, b2);
+    const float2 rC1 = mul2(c.br, c1), rC2 = mul2(c.br, c2), rE1 = mul2(c.br, e1), rE2 = mul2(c.br, e2);
+    const float2 ng = mul2(bc2(-1.f), c.g);
+    float2 V[3], gd[3], ngd[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        V[q] = fma2(cd, d[q], mul2(gg, P[q]));
+        gd[q] = mul2(c.g, d[q]);
+        ngd[q] = mul2(ng, d[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int u = (q + 1) % 3, w = (q + 2) % 3;
+        a.p[q] = fma2(BA2, bc2(Gj[q]), fma2(BA1, bc2(Fj[q]), fma2(rC2, bc2(Hj[q]), fma2(rC1, bc2(Tj[q]),
+                 add2(a.p[q], V[q])))));
+        // dF_i += A G_j + B (G_j.d) d + g H_j x d ;  dT_i += g G_j x d + ar H_j + br (H_j.d) d
+        a.p[3 + q] = fma2(BB2, d[q], fma2(c.A, bc2(Gj[q]), fma2(bc2(Hj[u]), gd[w], fma2(bc2(Hj[w]), ngd[u],
+                     a.p[3 + q]))));
+        a.p[6 + q] = fma2(rE2, d[q], fma2(c.ar, bc2(Hj[q]), fma2(bc2(Gj[u]), gd[w], fma2(bc2(Gj[w]), ngd[u],
+                     a.p[6 + q]))));
+    }
+    a.sG = add2(a.sG, BB1);
+    a.sF = add2(a.sF, BB2);
+    a.sH = add2(a.sH, rE1);
+    a.sT = add2(a.sT, rE2);
+    if constexpr (SYM) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int u = (q + 1) % 3, w = (q + 2) % 3;
+            v[q] = fma2(BB2, Fi[q], fma2(BB1, Gi[q], fma2(rE2, Ti[q], fma2(rE1, Hi[q], add2(v[q], V[q])))));
+            // dF_j += A G_i + B (G_i.d) d - g H_i x d ;  dT_j += -g G_i x d + ar H_i + br (H_i.d) d
+            v[3 + q] = fma2(BA1, d[q], fma2(c.A, Gi[q], fma2(Hi[u], ngd[w], fma2(Hi[w], gd[u], v[3 + q]))));
+            v[6 + q] = fma2(rC1, d[q], fma2(c.ar, Hi[q], fma2(Gi[u], ngd[w], fma2(Gi[w], gd[u], v[6 + q]))));
+        }
+        v[9] = add2(v[9], BA1);     // x F_j
+        v[10] = add2(v[10], BA2);   // x G_j
+        v[11] = add2(v[11], rC1);   // x T_j
+        v[12] = add2(v[12], rC2);   // x H_j
+    }
+}
+
+template <int NT, int NI>
+constexpr size_t adj_sym6_x2_smem_bytes() { return adj_sym_s_smem_bytes<float, true, NT, NI>(); }
+
+template <int NT, int NI>
+__global__ void __launch_bounds__(NT) rpy_adjoint_sym6_x2_kernel(const float4* __restrict__ pos4,
+                                                                 const void* __restrict__ Fp, const void* __restrict__ Tp,
+                                                                 const void* __restrict__ Gp, const void* __restrict__ Hp,
+                                                                 int f64, int64_t N, const int4* __restrict__ items,
+                                                                 RpyConst<float> k, double* __restrict__ acc) {
+    static_assert(NI % 2 == 0, "packed form needs an even number of i-particles per thread");
+    constexpr int NP = NI / 2;
+    constexpr int C = 9;
+    constexpr int W = 4;
+    constexpr int NV = 13;
+    constexpr int SJ = NT + 1;
+    extern __shared__ __align__(16) unsigned char adj_sym6_smem[];
+    float4* s_t = reinterpret_cast<float4*>(adj_sym6_smem);   // [w][jj]
+    float* s_j = reinterpret_cast<float*>(s_t + W * NT);      // [v][jj]
+    float* s_hi = s_j + NV * SJ;                              // [c][q][tid]
+    float* s_lo = s_hi + C * NI * NT;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int4 item = items[blockIdx.x];
+    const int64_t b = item.x, t_begin = item.y, t_end = item.z;
+    const int64_t i0 = b * (NT * NI);
+    const int64_t diag_end = (b + 1) * NI;
+    const float pad = (float)kPadCoord;
+
+    float2 xi[NP][3], Fi[NP][3], Gi[NP][3], Ti[NP][3], Hi[NP][3];
+    Sym6Acc2 a[NP];
+#pragma unroll
+    for (int pp = 0; pp < NP; ++pp) {
+        float v[2][15];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t i = i0 + (int64_t)(2 * pp + h) * NT + tid;
+            const bool in = i < N && LM_INBOUNDS(i >= 0, 12, i);
+            if (in) {
+                const float4 q = pos4[i];
+                v[h][0] = q.x; v[h][1] = q.y; v[h][2] = q.z;
+            } else {
+                v[h][0] = v[h][1] = v[h][2] = -pad;
+            }
+            const int64_t ii = in ? i : 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                v[h][3 + c] = in ? ld<float>(Fp, f64, 3 * ii + c) : 0.f;
+                v[h][6 + c] = in ? ld<float>(Gp, f64, 3 * ii + c) : 0.f;
+                v[h][9 + c] = in ? ld<float>(Tp, f64, 3 * ii + c) : 0.f;
+                v[h][12 + c] = in ? ld<float>(Hp, f64, 3 * ii + c) : 0.f;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            xi[pp][c] = make_float2(v[0][c], v[1][c]);
+            Fi[pp][c] = make_float2(v[0][3 + c], v[1][3 + c]);
+            Gi[pp][c] = make_float2(v[0][6 + c], v[1][6 + c]);
+            Ti[pp][c] = make_float2(v[0][9 + c], v[1][9 + c]);
+            Hi[pp][c] = make_float2(v[0][12 + c], v[1][12 + c]);
+        }
+#pragma unroll
+        for (int c = 0; c < C; ++c) a[pp].p[c] = bc2(0.f);
+        a[pp].sG = a[pp].sF = a[pp].sH = a[pp].sT = bc2(0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            s_hi[(c * NI + q) * NT + tid] = 0.f;
+            s_lo[(c * NI + q) * NT + tid] = 0.f;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s_j[v * SJ + tid] = 0.f;
+    const float2 K1 = bc2(k.K1), nK2 = bc2(-k.K2), m3K1 = bc2(-3.f * k.K1), K2x5 = bc2(5.f * k.K2);
+    const float2 m1 = bc2(-1.f), m3 = bc2(-3.f), mhalf = bc2(-0.5f), p15 = bc2(1.5f), m75 = bc2(-7.5f);
+
+    const int64_t jlo = t_begin * NT;
+    const int64_t jhi = (t_end * NT < N) ? t_end * NT : N;
+    float nv[16];
+    auto fetch = [&](int64_t j) {
+        const bool in = j < jhi && LM_INBOUNDS(j >= 0 && j < N, 13, j);
+        const int64_t jj = in ? j : 0;
+        if (in) {
+            const float4 p = pos4[jj];
+            nv[0] = -p.x; nv[1] = -p.y; nv[2] = -p.z;
+        } else {
+            nv[0] = nv[1] = nv[2] = -pad;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            nv[3 + c] = in ? ld<float>(Fp, f64, 3 * jj + c) : 0.f;
+            nv[6 + c] = in ? ld<float>(Gp, f64, 3 * jj + c) : 0.f;
+            nv[9 + c] = in ? ld<float>(Tp, f64, 3 * jj + c) : 0.f;
+            nv[12 + c] = in ? ld<float>(Hp, f64, 3 * jj + c) : 0.f;
+        }
+        nv[15] = 0.f;
+    };
+    fetch(jlo + tid);
+
+    for (int64_t t = t_begin; t < t_end; ++t) {
+        const int64_t jt = t * NT;
+        const bool sym = t >= diag_end;
+#pragma unroll
+        for (int w = 0; w < W; ++w) s_t[w * NT + tid] = make_float4(nv[4 * w], nv[4 * w + 1], nv[4 * w + 2], nv[4 * w + 3]);
+        __syncthreads();
+        if (jt + NT < jhi) fetch(jt + NT + tid);
+#pragma unroll 1
+        for (int jj = 0; jj < NT; ++jj) {
+            float jw[16];
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const float4 q = s_t[w * NT + jj];
+                jw[4 * w] = q.x; jw[4 * w + 1] = q.y; jw[4 * w + 2] = q.z; jw[4 * w + 3] = q.w;
+            }
+            float2 d[NP][3], r2[NP];
+            float mn = 0.f;
+#pragma unroll
+            for (int pp = 0; pp < NP; ++pp) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) d[pp][c] = add2(xi[pp][c], bc2(jw[c]));
+                r2[pp] = fma2(d[pp][0], d[pp][0], fma2(d[pp][1], d[pp][1], mul2(d[pp][2], d[pp][2])));
+                const float m2 = fminf(r2[pp].x, r2[pp].y);
+                mn = (pp == 0) ? m2 : fminf(mn, m2);
+            }
+            const bool near = __any_sync(0xffffffffu, mn < k.four_a2);
+            float2 v[NV];
+#pragma unroll
+            for (int c = 0; c < NV; ++c) v[c] = bc2(0.f);
+#pragma unroll
+            for (int pp = 0; pp < NP; ++pp) {
+                PCoef2 c;
+                float2 gg;
+                if (!near) {
+                    const float2 invr = make_float2(rsqrtf(r2[pp].x), rsqrtf(r2[pp].y));
+                    const float2 invr2 = mul2(invr, invr);
+                    const float2 invr3 = mul2(invr2, invr);
+                    const float2 invr5 = mul2(invr3, invr2);
+                    const float2 invr7 = mul2(invr5, invr2);
+                    c.A = fma2(K1, invr3, invr);
+                    c.B = fma2(nK2, invr5, invr3);
+                    c.Ap = mul2(invr3, fma2(m3K1, invr2, m1));   // -1/r^3 - 3 K1/r^5
+                    c.Bp = mul2(invr5, fma2(K2x5, invr2, m3));   // -3/r^5 + 5 K2/r^7
+                    c.g = invr3;
+                    c.gp = mul2(m3, invr5);
+                    c.ar = mul2(mhalf, invr3);
+                    c.arp = mul2(p15, invr5);
+                    c.br = c.arp;
+                    c.brp = mul2(m75, invr7);
+                    gg = c.g;
+                } else {
+                    // exact coefficients of either branch per lane; at r = 0 the
+                    // gradient is taken as zero (gg = 0, the derivatives vanish)
+                    Coef<float> c0, c1;
+                    const bool g0 = exact_coef<float, true>(r2[pp].x, k, c0);
+                    const bool g1 = exact_coef<float, true>(r2[pp].y, k, c1);
+                    c.A = make_float2(c0.A, c1.A);
+                    c.B = make_float2(c0.B, c1.B);
+                    c.Ap = make_float2(c0.Ap, c1.Ap);
+                    c.Bp = make_float2(c0.Bp, c1.Bp);
+                    c.g = make_float2(c0.g, c1.g);
+                    c.gp = make_float2(c0.gp, c1.gp);
+                    c.ar = make_float2(c0.ar, c1.ar);
+                    c.arp = make_float2(c0.arp, c1.arp);
+                    c.br = make_float2(c0.br, c1.br);
+                    c.brp = make_float2(c0.brp, c1.brp);
+                    gg = make_float2(g0 ? c0.g : 0.f, g1 ? c1.g : 0.f);
+                }
+                if (sym) sym6_pair2<true>(d[pp], c, gg, Fi[pp], Gi[pp], Ti[pp], Hi[pp], jw, a[pp], v);
+                else sym6_pair2<false>(d[pp], c, gg, Fi[pp], Gi[pp], Ti[pp], Hi[pp], jw, a[pp], v);
+            }
+            if (sym) {
+                float s[16];
+#pragma unroll
+                for (int c = 0; c < NV; ++c) s[c] = v[c].x + v[c].y;
+#pragma unroll
+                for (int c = NV; c < 16; ++c) s[c] = 0.f;
+                const float tot = warp_transpose_sum<float, 16>(s, lane);
+                if ((lane & 1) == 0 && (lane >> 1) < NV) atomicAdd(&s_j[(lane >> 1) * SJ + jj], tot);
+            }
+        }
+        // apply the tile's i-side scalars and fold into the running sums
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                a[pp].p[c] = fma2(a[pp].sG, Gi[pp][c], fma2(a[pp].sF, Fi[pp][c], fma2(a[pp].sH, Hi[pp][c],
+                             fma2(a[pp].sT, Ti[pp][c], a[pp].p[c]))));
+            a[pp].sG = a[pp].sF = a[pp].sH = a[pp].sT = bc2(0.f);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const int o0 = (c * NI + 2 * pp) * NT + tid;
+                const int o1 = o0 + NT;
+                fold(&s_hi[o0], &s_lo[o0], a[pp].p[c].x);
+                fold(&s_hi[o1], &s_lo[o1], a[pp].p[c].y);
+            }
+        }
+        __syncthreads();
+        if (sym) {
+            const int64_t j = jt + tid;
+            if (j < N && LM_INBOUNDS(j >= 0, 14, j)) {
+                float wv[16];
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    const float4 q = s_t[w * NT + tid];
+                    wv[4 * w] = q.x; wv[4 * w + 1] = q.y; wv[4 * w + 2] = q.z; wv[4 * w + 3] = q.w;
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float x = s_j[c * SJ + tid];
+                    x = fmaf(s_j[9 * SJ + tid], wv[3 + c], fmaf(s_j[10 * SJ + tid], wv[6 + c], x));
+                    x = fmaf(s_j[11 * SJ + tid], wv[9 + c], fmaf(s_j[12 * SJ + tid], wv[12 + c], x));
+                    atomicAdd(&acc[C * j + c], -(double)x);
+                }
+#pragma unroll
+                for (int c = 3; c < C; ++c) atomicAdd(&acc[C * j + c], (double)s_j[c * SJ + tid]);
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) s_j[v * SJ + tid] = 0.f;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < NI; ++q) {
+        const int64_t i = i0 + (int64_t)q * NT + tid;
+        if (i >= N) continue;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const int o = (c * NI + q) * NT + tid;
+            atomicAdd(&acc[C * i + c], (double)s_hi[o] + (double)s_lo[o]);
+        }
+    }
+}
+
+template <int NI>
+cudaError_t launch_adj_sym6_x2_t(const AdjointArgs& a, cudaStream_t s) {
+    constexpr int NT = 128;
+    constexpr int C = 9;
+    if (a.sym_items == nullptr || a.sym_acc == nullptr || a.n_sym_items < 1) return cudaErrorInvalidValue;
+    if (a.n_sym_items > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    const double c8 = 1.0 / (8.0 * 3.14159265358979323846 * a.eta);
+    const RpyConst<float> k = make_rpy_const<float>(a.a);
+    constexpr size_t dyn = adj_sym6_x2_smem_bytes<NT, NI>();
+    static std::atomic<unsigned long long> attr_devs{0};  // devices whose limit is raised
+    if (cudaError_t e = smem_attr_once(attr_devs, rpy_adjoint_sym6_x2_kernel<NT, NI>, dyn)) return e;
+    cudaError_t e = cudaMemsetAsync(a.sym_acc, 0, (size_t)C * a.N * sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    rpy_adjoint_sym6_x2_kernel<NT, NI><<<(unsigned)a.n_sym_items, NT, dyn, s>>>(
+        static_cast<const float4*>(a.pos4), a.F, a.T, a.G, a.H, a.fp64, a.N, static_cast<const int4*>(a.sym_items), k,
+        a.sym_acc);
+    count_launches(1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t tot = (int64_t)C * a.N;
+    adj_sym_store_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a.sym_acc, C, a.N, c8, a.dX, a.dF, a.dT,
+                                                                       a.fp64);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_sym6_x2(const AdjointArgs& a, cudaStream_t s) {
+    if (a.fp64 || !a.angular) return cudaErrorInvalidConfiguration;
+    return a.ilp == 4 ? launch_adj_sym6_x2_t<4>(a, s) : launch_adj_sym6_x2_t<2>(a, s);
+}
+
+template <int NI>
+int adj_sym6_x2_occupancy() {
+    int n = 0;
+    constexpr size_t dyn = adj_sym6_x2_smem_bytes<128, NI>();
+    cudaError_t e = cudaFuncSetAttribute(rpy_adjoint_sym6_x2_kernel<128, NI>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rpy_adjoint_sym6_x2_kernel<128, NI>, 128, dyn);
+    return e == cudaSuccess ? n : 0;
+}
+
 // Packed translation adjoint configurations: threads {128, 256} x ilp {2, 4}
 // x j per vote {1, 2} (AdjointArgs::uj).
 template <int NT, int NI>
@@ -1455,6 +1818,7 @@ int adjoint_ilp(int fp64, int angular) { return fp64 ? 1 : (angular ? 2 : 4); }
 bool adjoint_config_supported(int fp64, int angular, int threads, int ilp, int uj) {
     if (fp64 || angular) {
         if (uj == 3) return threads == 128 && sym_s_ilp_supported(fp64, ilp);   // symmetric scalar form
+        if (uj == 4) return !fp64 && threads == 128 && (ilp == 2 || ilp == 4);   // symmetric packed form
         return threads == 128 && ilp == adjoint_ilp(fp64, angular) && uj >= 0 && uj <= 1;
     }
     return (threads == 128 || threads == 256) && (ilp == 2 || ilp == 4) && uj >= 0 && uj <= 3;
@@ -1466,6 +1830,7 @@ cudaError_t launch_adjoint(const AdjointArgs& a, cudaStream_t s) {
     // FP64, and FP32 with angular blocks: the scalar kernels, one-sided or symmetric
     if (a.fp64 || a.angular) {
         if (a.uj == 3) return launch_adj_sym_s(a, s);
+        if (a.uj == 4) return launch_adj_sym6_x2(a, s);
         if (a.fp64) return a.angular ? launch_adj_t<double, true, 1>(a, s) : launch_adj_t<double, false, 1>(a, s);
         return launch_adj_t<float, true, 2>(a, s);
     }
@@ -1485,6 +1850,7 @@ int adjoint_ctas_per_sm(int fp64, int angular, int threads, int ilp, int uj) {
         if (e == cudaSuccess)                                                                     \
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rpy_adjoint_kernel<R, ANG, 128, NI>, 128, dyn); \
     }
+    if (angular && !fp64 && uj == 4) return ilp == 4 ? adj_sym6_x2_occupancy<4>() : adj_sym6_x2_occupancy<2>();
     if ((fp64 || angular) && uj == 3) {
         if (fp64) return angular ? adj_sym_s_occupancy<double, true, 1>() : adj_sym_s_occupancy<double, false, 1>();
         return ilp == 4 ? adj_sym_s_occupancy<float, true, 4>() : adj_sym_s_occupancy<float, true, 2>();

@@ -488,13 +488,15 @@ bool valid_name(const char* p) {
 }  // namespace
 
 namespace {
-// Adjoint launch configuration.  FP64 and angular blocks: the symmetric
-// scalar form (packed = 3, item size chosen at launch), 1.5x faster than the
-// one-sided scalar kernel at N = 65536 (FP32) and 16384 (FP64).  FP32
-// translation: the packed one-sided kernel, packed = j-particles per overlap
-// vote (the autotuner also times the symmetric form).
+// Adjoint launch configuration (item sizes chosen at launch).  FP32 with
+// angular blocks: the symmetric packed form (packed = 4, ilp 4), 1.7x faster
+// than the one-sided scalar kernel at N = 65536; FP64: the symmetric scalar
+// form (packed = 3), 1.5x faster at N = 16384.  FP32 translation: the packed
+// one-sided kernel, packed = j-particles per overlap vote (the autotuner also
+// times the symmetric form).
 lm_pair_config default_adjoint_config(const lm_solver* s) {
-    if (s->fp64 || s->angular) return lm_pair_config{128, lmk::adjoint_ilp(s->fp64, s->angular), 0, 3};
+    if (s->fp64) return lm_pair_config{128, 1, 0, 3};
+    if (s->angular) return lm_pair_config{128, 4, 0, 4};
     lm_pair_config c{128, lmk::adjoint_ilp(0, 0), 1, 1};
     int occ = std::max(1, lmk::adjoint_ctas_per_sm(0, 0, c.threads, c.ilp, c.packed));
     c.splits = auto_splits(s->N, c.threads, c.ilp, occ * s->sm_count);
@@ -514,7 +516,7 @@ void ensure_adjoint_config(lm_solver* s) {
     TunedEntry e;
     if (lookup_tuned(s, s->N, &e) && e.has_adj) {
         s->adj_cfg = e.adj;
-        if (e.N != s->N && e.adj.packed == 3) {
+        if (e.N != s->N && e.adj.packed >= 3) {
             s->adj_cfg.splits = 0;   // item size recomputed for this N
         } else if (e.N != s->N) {
             const int occ = std::max(1, lmk::adjoint_ctas_per_sm(s->fp64, s->angular, e.adj.threads, e.adj.ilp,
@@ -527,14 +529,16 @@ void ensure_adjoint_config(lm_solver* s) {
 
 // Tiles per work item of the symmetric adjoint when the configuration leaves
 // it open: about six items per resident CTA slot over the block-triangle of
-// (i-block, tile) units.
-int64_t sym_auto_chunk(const lm_solver* s, int threads, int ilp) {
+// (i-block, tile) units, and for the heavier angular and FP64 pairs at most
+// four tiles (4 against 8-19 was 2-3% faster at N = 65536 and 16384).
+int64_t sym_auto_chunk(const lm_solver* s, int threads, int ilp, int packed) {
     const int64_t BI = (int64_t)threads * ilp;
     const int64_t nblk = (s->N + BI - 1) / BI;
     const int64_t T = (s->N + threads - 1) / threads;
-    const int occ = std::max(1, lmk::adjoint_ctas_per_sm(s->fp64, s->angular, threads, ilp, 3));
+    const int occ = std::max(1, lmk::adjoint_ctas_per_sm(s->fp64, s->angular, threads, ilp, packed));
     const double total = (double)nblk * (double)T - (double)ilp * (double)nblk * (double)(nblk - 1) / 2.0;
-    return std::max<int64_t>(1, (int64_t)std::ceil(total / (6.0 * occ * s->sm_count)));
+    const int64_t chunk = std::max<int64_t>(1, (int64_t)std::ceil(total / (6.0 * occ * s->sm_count)));
+    return (s->fp64 || s->angular) ? std::min<int64_t>(chunk, 4) : chunk;
 }
 
 lm_status run_adjoint(lm_solver* s, const void* F, const void* T, const void* G, const void* H, void* dX, void* dF,
@@ -553,13 +557,13 @@ lm_status run_adjoint(lm_solver* s, const void* F, const void* T, const void* G,
     a.uj = cfg.packed > 0 ? cfg.packed : 1;
     a.splits = cfg.splits;
     a.partials = nullptr;
-    if (a.uj == 3) {
+    if (a.uj >= 3) {
         // symmetric form: items (i-block b, tiles [t0, t1)) over each block's
         // tiles from its own range onward, at most `chunk` tiles each, longest first
         const int64_t BI = (int64_t)cfg.threads * cfg.ilp;
         const int64_t nblk = (s->N + BI - 1) / BI;
         const int64_t T = (s->N + cfg.threads - 1) / cfg.threads;
-        const int64_t chunk = cfg.splits >= 1 ? cfg.splits : sym_auto_chunk(s, cfg.threads, cfg.ilp);
+        const int64_t chunk = cfg.splits >= 1 ? cfg.splits : sym_auto_chunk(s, cfg.threads, cfg.ilp, a.uj);
         const std::array<int64_t, 4> key{{s->N, cfg.threads, cfg.ilp, chunk}};
         if (s->sym_key != key) {
             std::vector<int4> items;
@@ -1329,7 +1333,7 @@ lm_status lm_set_adjoint_config(lm_solver* s, const lm_pair_config* cfg) {
         return fail(LM_ERR_INVALID_ARG, "unsupported adjoint configuration (threads %d, ilp %d, splits %d, packed %d)",
                     cfg->threads, cfg->ilp, cfg->splits, cfg->packed);
     lm_pair_config c = *cfg;
-    if (c.splits == 0 && c.packed != 3) {   // the symmetric form chooses its item size at launch
+    if (c.splits == 0 && c.packed < 3) {   // the symmetric forms choose their item size at launch
         const int occ = std::max(1, lmk::adjoint_ctas_per_sm(s->fp64, s->angular, c.threads, c.ilp, c.packed));
         c.splits = auto_splits(s->N, c.threads, c.ilp, occ * s->sm_count);
     }
@@ -1460,7 +1464,7 @@ lm_status autotune_impl(lm_solver* s, int reps, lm_pair_config* best) {
                     if (occ < 1) continue;
                     if (uj == 3) {
                         // symmetric form: the item size (tiles) of the model, half and twice it
-                        const int64_t ch = sym_auto_chunk(s, t, il);
+                        const int64_t ch = sym_auto_chunk(s, t, il, 3);
                         for (int64_t c : {ch, std::max<int64_t>(1, ch / 2), 2 * ch})
                             acands.push_back(lm_pair_config{t, il, (int)std::min<int64_t>(c, 1 << 20), 3});
                         continue;

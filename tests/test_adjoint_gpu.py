@@ -108,10 +108,12 @@ def test_adjoint_symmetric_form_overlaps_across_blocks(orc):
         assert rel(host(dF3), gF) <= 1e-5
 
 
-@pytest.mark.parametrize("fp64,angular,ilp", [(False, True, 2), (False, True, 4), (True, True, 1), (True, False, 1)])
-def test_adjoint_symmetric_scalar_form(orc, fp64, angular, ilp):
-    """The symmetric form of the scalar adjoint (angular blocks in FP32, and
-    FP64): each unordered pair evaluated once and added to both particles.
+@pytest.mark.parametrize("fp64,angular,ilp,packed", [(False, True, 2, 3), (False, True, 4, 3), (True, True, 1, 3),
+                                                     (True, False, 1, 3), (False, True, 2, 4), (False, True, 4, 4)])
+def test_adjoint_symmetric_6n_and_fp64_forms(orc, fp64, angular, ilp, packed):
+    """The symmetric forms of the adjoint with angular blocks (FP32 scalar,
+    packed = 3, and packed f32x2, packed = 4) and in FP64 (scalar): each
+    unordered pair evaluated once and added to both particles.
     A coincident and an overlapping pair whose particles lie in different
     i-blocks, N ragged for every tile; items of one tile, of the automatic
     size and of five tiles; dX alone and dF, dT alone."""
@@ -127,8 +129,8 @@ def test_adjoint_symmetric_scalar_form(orc, fp64, angular, ilp):
     tol = 1e-11 if fp64 else 1e-5
     args = (dev(s_.F), dev(s_.T), dev(s_.G), dev(s_.H))
     for chunk in (1, 0, 5):
-        lm.lm_set_adjoint_config(s, 128, ilp, chunk, 3)
-        assert lm.lm_get_adjoint_config(s)["packed"] == 3
+        lm.lm_set_adjoint_config(s, 128, ilp, chunk, packed)
+        assert lm.lm_get_adjoint_config(s)["packed"] == packed
         dX, dF, dT = lm.lm_mdot_backward(s, *args)
         assert rel(host(dX), gX) <= tol, (chunk, rel(host(dX), gX))
         assert rel(host(dF), gF) <= tol, (chunk, rel(host(dF), gF))
@@ -142,12 +144,12 @@ def test_adjoint_symmetric_scalar_form(orc, fp64, angular, ilp):
         assert rel(host(dT3), gT) <= tol
 
 
-@pytest.mark.parametrize("packed", [0, 3])
+@pytest.mark.parametrize("packed", [0, 3, 4])
 def test_adjoint_6n_full_size_sampled_rows(orc, packed):
     """The FP32 adjoint with angular blocks at N = 65536 (the adjoint
     benchmark's suspension, with torques and their cotangents), one-sided
-    (packed 0) and symmetric (packed 3), against the oracle's gradient and
-    products on 64 sampled particles."""
+    (packed 0), symmetric scalar (3) and symmetric packed (4), against the
+    oracle's gradient and products on 64 sampled particles."""
     c = I.ADJOINT_N65536
     s_ = I.cube_suspension(c["seed"], c["n"], c["phi"], c["a"], angular=True, fp32=True)
     s = lm.lm_create(c["eta"], c["a"], True, lm.LM_FP32C)

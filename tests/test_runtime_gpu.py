@@ -77,18 +77,18 @@ for n in (1, 2, 3, 31, 33, 129, 700):
     dX, dF, _ = lm.lm_mdot_backward(s, dev(s_.F), None, dev(s_.G), None)
     if n > 1:
         assert rel(dX.cpu(), g) < 1e-4, (n, "symmetric", rel(dX.cpu(), g))
-    # the symmetric scalar adjoint: angular blocks in FP32 (ilp 2 and 4) and FP64
-    for fp64, ilp in ((False, 2), (False, 4), (True, 1)):
+    # the symmetric adjoint with angular blocks: FP32 scalar (ilp 2, 4), FP32 packed, FP64
+    for fp64, ilp, packed in ((False, 2, 3), (False, 4, 3), (False, 2, 4), (False, 4, 4), (True, 1, 3)):
         sa = I.cube_suspension(300 + n, n, 0.15, 1.0, angular=True, fp32=not fp64)
         s = lm.lm_create(1.0, 1.0, True, lm.LM_FP64 if fp64 else lm.LM_FP32C)
         lm.lm_set_positions(s, dev(sa.pos))
-        lm.lm_set_adjoint_config(s, 128, ilp, 0, 3)
+        lm.lm_set_adjoint_config(s, 128, ilp, 0, packed)
         dX, dF, dT = lm.lm_mdot_backward(s, dev(sa.F), dev(sa.T), dev(sa.G), dev(sa.H))
         g = oracle.grad(sa.pos, sa.F, sa.T, sa.G, sa.H, 1.0, 1.0, True)
         gt = oracle.mdot(sa.pos, sa.G, sa.H, 1.0, 1.0, True)[1]
         if n > 1:
-            assert rel(dX.cpu(), g) < 1e-4, (n, fp64, ilp, "symmetric 6N", rel(dX.cpu(), g))
-        assert rel(dT.cpu(), gt) < 1e-4, (n, fp64, ilp, "symmetric 6N dT", rel(dT.cpu(), gt))
+            assert rel(dX.cpu(), g) < 1e-4, (n, fp64, ilp, packed, "symmetric 6N", rel(dX.cpu(), g))
+        assert rel(dT.cpu(), gt) < 1e-4, (n, fp64, ilp, packed, "symmetric 6N dT", rel(dT.cpu(), gt))
     pw = s_.pos.copy(); pw[:, 2] -= pw[:, 2].min() - 0.5
     sw = lm.lm_create(1.0, 1.0, False, lm.LM_FP32C, periodicity=("open", "open", "single_wall"))
     lm.lm_set_positions(sw, dev(pw))
