@@ -376,6 +376,26 @@ def test_gradient_matches_central_differences(orc, angular):
     np.testing.assert_array_equal(orc.grad(pos, F, T, G, H, a, eta, angular, rows=rows), dX[rows])
 
 
+@pytest.mark.parametrize("angular", [False, True])
+def test_gradient_invariants(orc, angular):
+    """L depends on the positions only through the differences x_i - x_j, so
+    dL/dX sums to zero over the particles; and L = <[G;H], M [F;T]> =
+    <[F;T], M [G;H]> because M is symmetric, so exchanging (F, T) with
+    (G, H) leaves dL/dX unchanged.  A dropped or mis-signed cross term
+    between the two sides of a pair (the terms the symmetric adjoint kernels
+    split between i and j) breaks one of them.  Overlapping pairs and a
+    coincident pair included."""
+    rng = np.random.default_rng(53 + angular)
+    n = 40
+    pos = _overlapping(rng, n, 6.0)
+    pos[7] = pos[30]
+    F, T, G, H = (rng.standard_normal((n, 3)) for _ in range(4))
+    dX = orc.grad(pos, F, T, G, H, 1.0, 1.0, angular)
+    scale = np.abs(dX).max()
+    np.testing.assert_allclose(dX.sum(axis=0), 0.0, atol=1e-13 * n * scale)
+    np.testing.assert_allclose(orc.grad(pos, G, H, F, T, 1.0, 1.0, angular), dX, atol=1e-13 * scale)
+
+
 def test_force_gradient_is_mobility_product(orc):
     """dL/dF = (M [G;H])_u and dL/dT = (M [G;H])_w because M is symmetric."""
     rng = np.random.default_rng(47)
