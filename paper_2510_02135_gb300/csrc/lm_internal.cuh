@@ -171,10 +171,12 @@ struct AdjointArgs {
     double a, eta;
     int threads, splits;
     int ilp = 4;                      // i-particles per thread (packed FP32 translation form: 2 or 4)
-    int uj = 1;                       // j-particles per overlap vote (packed form: 1 or 2); 3: symmetric form
+    int uj = 1;                       // j-particles per overlap vote (packed form: 1 or 2); 3: symmetric
+                                      // form (packed for FP32 translation, scalar otherwise); 4: symmetric
+                                      // packed form with angular blocks (FP32)
     double* partials;                 // splits * (3 + 3 or 6) * N doubles when splits > 1
-    // symmetric form (uj == 3): work items (int4: i-block, first tile, end tile, 0) and the
-    // FP64 accumulators acc[N][6] (zeroed by the launcher)
+    // symmetric forms (uj >= 3): work items (int4: i-block, first tile, end tile, 0) and the
+    // FP64 accumulators acc[N][C], C = 6 or 9 with angular blocks (zeroed by the launcher)
     const void* sym_items = nullptr;
     int64_t n_sym_items = 0;
     double* sym_acc = nullptr;
