@@ -164,6 +164,27 @@ def test_adjoint_6n_full_size_sampled_rows(orc, packed):
     assert rel(host(dT)[rows], gT) <= 1e-5, rel(host(dT)[rows], gT)
 
 
+def test_adjoint_6n_beyond_the_benchmark_size_sampled_rows(orc):
+    """The default adjoint with angular blocks (the packed symmetric form) at
+    N = 2^20, sixteen times the adjoint benchmark's N (random cube at
+    phi = 0.1): dX, dF and dT on 32 sampled particles against the oracle.
+    Work-item counts, accumulator indices and grids are far from the sizes
+    the smaller tests reach."""
+    n = 1 << 20
+    s_ = I.cube_suspension(79, n, 0.1, 1.0, angular=True, fp32=True)
+    s = lm.lm_create(1.0, 1.0, True, lm.LM_FP32C)
+    lm.lm_set_positions(s, dev(s_.pos))
+    assert lm.lm_get_adjoint_config(s)["packed"] == 4
+    dX, dF, dT = (host(t) for t in lm.lm_mdot_backward(s, dev(s_.F), dev(s_.T), dev(s_.G), dev(s_.H)))
+    rows = np.sort(np.random.default_rng(9).choice(n, 32, replace=False))
+    gX = orc.grad(s_.pos, s_.F, s_.T, s_.G, s_.H, 1.0, 1.0, True, rows=rows)
+    gF, gT = orc.mdot(s_.pos, s_.G, s_.H, 1.0, 1.0, True, rows=rows)
+    assert rel(dX[rows], gX) <= 1e-5, rel(dX[rows], gX)
+    assert rel(dF[rows], gF) <= 1e-5, rel(dF[rows], gF)
+    assert rel(dT[rows], gT) <= 1e-5, rel(dT[rows], gT)
+    assert np.isfinite(dX).all() and np.isfinite(dF).all() and np.isfinite(dT).all()
+
+
 def test_adjoint_skips_outputs_and_handles_coincident(orc):
     pos = np.array([[0, 0, 0], [0, 0, 0], [0.5, 0.1, 0.0], [3.0, 0.0, 1.0]], np.float64)
     rng = np.random.default_rng(2)
