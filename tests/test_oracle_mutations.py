@@ -1,0 +1,148 @@
+"""The oracle's pins reject plausible mistakes.
+
+Each case compiles a copy of the C oracle (``oracle/rpy_oracle.c``) with one
+planted change -- a flipped sign, a dropped term, a transposed block -- on the
+CPU, in a temporary directory, and checks that the pin aimed at that kind of
+mistake fails on the mutant while it passes on an unchanged copy.  The oracle
+source itself is never modified and no GPU is involved."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+
+SRC = os.path.join(os.path.dirname(os.path.abspath(oracle.__file__)), "rpy_oracle.c")
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+pytestmark = pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+
+
+def _compile(tmp_path, name, old=None, new=None):
+    """Build a copy of the oracle, with `old` replaced by `new` (exactly one
+    occurrence), and return its ctypes handle."""
+    src = open(SRC).read()
+    if old is not None:
+        assert src.count(old) == 1, old
+        src = src.replace(old, new)
+    c = tmp_path / (name + ".c")
+    so = tmp_path / (name + ".so")
+    c.write_text(src)
+    subprocess.run(["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+                    str(c), "-o", str(so), "-lm"], check=True)
+    lib = ctypes.CDLL(str(so))
+    lib.orc_grad.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                             ctypes.c_int, _i64p, ctypes.c_int64, _dp]
+    lib.orc_mdot.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                             ctypes.c_int, _i64p, ctypes.c_int64, _dp, _dp]
+    lib.orc_assemble.argtypes = [ctypes.c_int64, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                 ctypes.c_int, _dp]
+    return lib
+
+
+def _p(x):
+    return None if x is None else x.ctypes.data_as(_dp)
+
+
+def _grad(lib, pos, F, T, G, H, angular):
+    n = pos.shape[0]
+    dX = np.zeros((n, 3))
+    lib.orc_grad(n, _p(pos), _p(F), _p(T), _p(G), _p(H), 1.0, 1.0, int(angular), None, n, _p(dX))
+    return dX
+
+
+def _mdot(lib, pos, F, T, angular):
+    n = pos.shape[0]
+    U = np.zeros((n, 3))
+    W = np.zeros((n, 3))
+    lib.orc_mdot(n, _p(pos), _p(F), _p(T), 1.0, 1.0, int(angular), 0, None, n, _p(U), _p(W))
+    return U, W
+
+
+def _assemble(lib, pos, angular):
+    n = pos.shape[0]
+    dim = (6 if angular else 3) * n
+    M = np.zeros((dim, dim))
+    lib.orc_assemble(n, _p(pos), 1.0, 1.0, int(angular), 0, _p(M))
+    return M
+
+
+def _case(seed, n=24, L=5.0):
+    rng = np.random.default_rng(seed)
+    pos = rng.uniform(-L / 2, L / 2, size=(n, 3))   # overlapping pairs included
+    F, T, G, H = (np.ascontiguousarray(rng.standard_normal((n, 3))) for _ in range(4))
+    return np.ascontiguousarray(pos), F, T, G, H
+
+
+def _pins(lib, angular, seed=3):
+    """The gradient and product pins of the oracle (as in test_oracle_pins),
+    evaluated on `lib`: True where the pin holds."""
+    pos, F, T, G, H = _case(seed)
+    n = pos.shape[0]
+    if not angular:
+        T = H = None
+    dX = _grad(lib, pos, F, T, G, H, angular)
+
+    def L(p):
+        U, W = _mdot(lib, p, F, T, angular)
+        return np.sum(G * U) + (np.sum(H * W) if angular else 0.0)
+
+    h = 1e-6
+    fd = np.zeros_like(pos)
+    for i in range(n):
+        for k in range(3):
+            pp = pos.copy()
+            pp[i, k] += h
+            pm = pos.copy()
+            pm[i, k] -= h
+            fd[i, k] = (L(pp) - L(pm)) / (2 * h)
+    scale = np.abs(fd).max()
+    M = _assemble(lib, pos, angular)
+    U, W = _mdot(lib, pos, F, T, angular)
+    y = M @ (np.concatenate([F.ravel(), T.ravel()]) if angular else F.ravel())
+    direct = np.concatenate([U.ravel(), W.ravel()]) if angular else U.ravel()
+    pins = {
+        "central_differences": np.abs(dX - fd).max() <= 2e-7 * scale,
+        "sum_zero": np.abs(dX.sum(axis=0)).max() <= 1e-13 * n * np.abs(dX).max(),
+        "dense_equals_direct": np.abs(direct - y).max() <= 1e-13 * np.abs(y).max(),
+    }
+    if angular:
+        dX2 = _grad(lib, pos, G, H, F, T, angular)
+        pins["exchange"] = np.abs(dX2 - dX).max() <= 1e-13 * np.abs(dX).max()
+    return pins
+
+
+@pytest.mark.parametrize("angular", [False, True])
+def test_unchanged_copy_passes_every_pin(tmp_path, angular):
+    pins = _pins(_compile(tmp_path, "same"), angular)
+    assert all(pins.values()), pins
+
+
+MUTATIONS = [
+    # the source-role term of the chain rule added with the wrong sign
+    ("sign_of_source_term", "acc[c] += sgn * s;", "acc[c] += s;", False,
+     {"central_differences", "sum_zero"}),
+    # the H.wF.F coupling term of the gradient dropped
+    ("dropped_coupling_term", "if (H) s += H[3 * k + p] * dwF[9 * c + 3 * p + q] * F[3 * l + q];", "", True,
+     {"central_differences", "exchange"}),
+    # the derivative of the u-from-T block transposed
+    ("transposed_coupling_derivative", "duT[9 * c + 3 * p + q]", "duT[9 * c + 3 * q + p]", True,
+     {"central_differences", "exchange"}),
+    # the u-from-T block transposed in the direct sum only
+    ("transposed_block_in_direct_sum", "if (T) u[p] += uT[3 * p + q] * T[3 * j + q];",
+     "if (T) u[p] += uT[3 * q + p] * T[3 * j + q];", True, {"central_differences", "dense_equals_direct"}),
+    # the column particle of the source-role term taken from the wrong index
+    ("wrong_column_particle", "const int64_t l = side == 0 ? j : i;", "const int64_t l = j;", False,
+     {"central_differences"}),
+]
+
+
+@pytest.mark.parametrize("name,old,new,angular,caught_by", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_fails_its_pins(tmp_path, name, old, new, angular, caught_by):
+    pins = _pins(_compile(tmp_path, name, old, new), angular)
+    failed = {k for k, ok in pins.items() if not ok}
+    assert caught_by <= failed, (name, pins)
