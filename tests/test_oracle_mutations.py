@@ -146,3 +146,68 @@ def test_planted_mistake_fails_its_pins(tmp_path, name, old, new, angular, caugh
     pins = _pins(_compile(tmp_path, name, old, new), angular)
     failed = {k for k, ok in pins.items() if not ok}
     assert caught_by <= failed, (name, pins)
+
+
+# --------------------------------------------------------------------------
+# Pair-block mistakes, caught by the pins of test_oracle_pins run unchanged
+# against the mutant (the oracle module pointed at the mutant's library).
+# --------------------------------------------------------------------------
+import test_oracle_pins as P  # noqa: E402
+
+BLOCK_PINS = {
+    "quadrature": lambda o: [P.test_pair_blocks_match_envelope_quadrature(o, s)
+                             for s in (0.3, 1.2, 1.9, 2.05, 2.15, 3.0, 6.0)],
+    "contact_golden": P.test_contact_values_golden,
+    "continuous_at_contact": P.test_blocks_continuous_at_contact,
+    "oseen_limit": P.test_oseen_limit,
+    "half_vorticity": P.test_far_field_rotation_is_half_vorticity,
+    "symmetric_positive_definite": lambda o: P.test_grand_mobility_symmetric_positive_definite(o, 40, 6.0),
+    "gradient_central_differences": lambda o: P.test_gradient_matches_central_differences(o, True),
+}
+
+
+def _block_pins(monkeypatch, lib_path):
+    monkeypatch.setattr(oracle, "_LIB_PATH", str(lib_path))
+    monkeypatch.setattr(oracle, "_lib", None)
+    oracle._load()
+    held = {}
+    for name, pin in BLOCK_PINS.items():
+        try:
+            pin(oracle)
+            held[name] = True
+        except AssertionError:
+            held[name] = False
+    return held
+
+
+def test_unchanged_copy_passes_every_block_pin(tmp_path, monkeypatch):
+    _compile(tmp_path, "same")
+    held = _block_pins(monkeypatch, tmp_path / "same.so")
+    assert all(held.values()), held
+
+
+BLOCK_MUTATIONS = [
+    # the a^2 / (3 r^3) term of the far-field tt identity coefficient without its 1/3
+    ("far_field_a2_term", "c[0] = k8 * (1.0 / r + 2.0 * a * a / (3.0 * r3));", "c[0] = k8 * (1.0 / r + 2.0 * a * a / r3);",
+     {"quadrature", "continuous_at_contact"}),
+    # a wrong constant in the overlapping rr coefficient (the golden contact
+    # values sit at r = 2a, on the far-field branch, so they cannot see it)
+    ("overlap_rr_constant", "c[3] = kr * (1.0 - 27.0 * s / 32.0 + 5.0 * s * s * s / 64.0);",
+     "c[3] = kr * (1.0 - 9.0 * s / 32.0 + 5.0 * s * s * s / 64.0);", {"quadrature", "continuous_at_contact"}),
+    # the far-field translation-rotation coupling with the wrong sign
+    ("coupling_sign", "c[2] = -k8 / r2;", "c[2] = k8 / r2;", {"half_vorticity", "continuous_at_contact"}),
+    # omega-from-F block with the opposite sign of u-from-T (M no longer symmetric)
+    ("rt_block_sign", "wF[3 * p + q] = c[2] * ex[3 * p + q];", "wF[3 * p + q] = -c[2] * ex[3 * p + q];",
+     {"symmetric_positive_definite"}),
+    # a wrong constant in the derivative of the far-field tt dd coefficient
+    ("far_field_derivative", "dc[1] = k8 * (-1.0 / r2 + 6.0 * a * a / r4);", "dc[1] = k8 * (-1.0 / r2 + 2.0 * a * a / r4);",
+     {"gradient_central_differences"}),
+]
+
+
+@pytest.mark.parametrize("name,old,new,caught_by", BLOCK_MUTATIONS, ids=[m[0] for m in BLOCK_MUTATIONS])
+def test_planted_block_mistake_fails_its_pins(tmp_path, monkeypatch, name, old, new, caught_by):
+    _compile(tmp_path, name, old, new)
+    held = _block_pins(monkeypatch, tmp_path / (name + ".so"))
+    failed = {k for k, ok in held.items() if not ok}
+    assert caught_by <= failed, (name, held)
