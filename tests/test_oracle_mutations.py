@@ -211,3 +211,62 @@ def test_planted_block_mistake_fails_its_pins(tmp_path, monkeypatch, name, old, 
     held = _block_pins(monkeypatch, tmp_path / (name + ".so"))
     failed = {k for k, ok in held.items() if not ok}
     assert caught_by <= failed, (name, held)
+
+
+# --------------------------------------------------------------------------
+# Single-wall mistakes, caught by the wall pins (the sympy derivation of the
+# blocks from the Blake image system, the Swan-Brady self mobilities).
+# --------------------------------------------------------------------------
+import functools  # noqa: E402
+
+import test_wall_pins as WP  # noqa: E402
+
+_blake = functools.lru_cache(maxsize=None)(WP._blake_blocks)   # independent of the oracle
+
+WALL_PINS = {
+    "blake_definition": WP.test_wall_blocks_match_blake_definition,
+    "swan_brady_self": lambda: WP.test_wall_self_mobility_matches_swan_brady(1.0, 1.0),
+    "symmetric_positive_definite": lambda: WP.test_wall_matrix_symmetric_positive_definite(True),
+}
+
+
+def _wall_pins(monkeypatch, lib_path):
+    monkeypatch.setattr(oracle, "_LIB_PATH", str(lib_path))
+    monkeypatch.setattr(oracle, "_lib", None)
+    monkeypatch.setattr(WP, "_blake_blocks", _blake)
+    oracle._load()
+    held = {}
+    for name, pin in WALL_PINS.items():
+        try:
+            pin()
+            held[name] = True
+        except AssertionError:
+            held[name] = False
+    return held
+
+
+def test_unchanged_copy_passes_every_wall_pin(tmp_path, monkeypatch):
+    pytest.importorskip("sympy")
+    _compile(tmp_path, "same")
+    held = _wall_pins(monkeypatch, tmp_path / "same.so")
+    assert all(held.values()), held
+
+
+WALL_MUTATIONS = [
+    # a wrong constant in the a^4 term of the tangential uF entry
+    ("uF_a4_constant", "a4 * (-70.0 * c4 / 3.0 + 70.0 * c2 / 3.0 - 8.0 / 3.0) * r5",
+     "a4 * (-70.0 * c4 / 3.0 + 70.0 * c2 / 3.0 - 4.0 / 3.0) * r5", {"blake_definition"}),
+    # a wrong constant in the normal-normal wT entry
+    ("wT_constant", "LwT[4] = (3.5 - 6.0 * c2) * r3;", "LwT[4] = (3.5 - 4.5 * c2) * r3;", {"blake_definition"}),
+    # a flipped sign in the uT block
+    ("uT_sign", "LuT[5] = -s * r2;", "LuT[5] = s * r2;", {"blake_definition"}),
+]
+
+
+@pytest.mark.parametrize("name,old,new,caught_by", WALL_MUTATIONS, ids=[m[0] for m in WALL_MUTATIONS])
+def test_planted_wall_mistake_fails_its_pins(tmp_path, monkeypatch, name, old, new, caught_by):
+    pytest.importorskip("sympy")
+    _compile(tmp_path, name, old, new)
+    held = _wall_pins(monkeypatch, tmp_path / (name + ".so"))
+    failed = {k for k, ok in held.items() if not ok}
+    assert caught_by <= failed, (name, held)
