@@ -270,3 +270,80 @@ def test_planted_wall_mistake_fails_its_pins(tmp_path, monkeypatch, name, old, n
     held = _wall_pins(monkeypatch, tmp_path / (name + ".so"))
     failed = {k for k, ok in held.items() if not ok}
     assert caught_by <= failed, (name, held)
+
+
+# --------------------------------------------------------------------------
+# Mistakes in the Python half of the oracle (square roots, Lanczos, Philox,
+# the roller-example integrator): a changed copy of oracle/__init__.py is
+# executed as a separate module (same C library) and the pins run against it.
+# --------------------------------------------------------------------------
+import types  # noqa: E402
+
+import test_integrator_pins as IP  # noqa: E402
+
+PY_SRC = os.path.join(os.path.dirname(os.path.abspath(oracle.__file__)), "__init__.py")
+
+
+def _py_mutant(old=None, new=None):
+    src = open(PY_SRC).read()
+    if old is not None:
+        assert src.count(old) == 1, old
+        src = src.replace(old, new)
+    mod = types.ModuleType("oracle_mutant")
+    mod.__file__ = oracle.__file__
+    exec(compile(src, "oracle_mutant", "exec"), mod.__dict__)
+    return mod
+
+
+PY_PINS = {
+    "sqrt_schur": P.test_sqrt_exact_matches_schur_sqrtm,
+    "tridiag_dense": P.test_tridiagonal_root_matches_dense,
+    "lanczos_full_dimension": P.test_lanczos_full_dimension_is_exact,
+    "lanczos_eigenvector": P.test_lanczos_eigenvector_converges_in_one_step,
+    "lanczos_tolerance": P.test_lanczos_tolerance_controls_error,
+    "philox_kat": P.test_philox_known_answer_vectors,
+    "soft_gradient": lambda o: IP.test_soft_repulsion_is_minus_energy_gradient(),
+    "ab_euler_second_order": lambda o: IP.test_ab_step_first_step_is_euler_and_second_order(),
+}
+
+
+def _py_pins(monkeypatch, mod):
+    monkeypatch.setattr(IP, "oracle", mod)
+    held = {}
+    for name, pin in PY_PINS.items():
+        try:
+            pin(mod)
+            held[name] = True
+        except AssertionError:
+            held[name] = False
+    return held
+
+
+def test_unchanged_python_copy_passes_every_pin(monkeypatch):
+    held = _py_pins(monkeypatch, _py_mutant())
+    assert all(held.values()), held
+
+
+PY_MUTATIONS = [
+    ("tridiagonal_root_without_sqrt", "return Q @ (np.sqrt(lam) * Q[0, :])", "return Q @ (lam * Q[0, :])",
+     {"tridiag_dense", "lanczos_full_dimension"}),
+    ("lanczos_without_norm_of_W", "z = normW * tridiag_sqrt_e1(alpha, beta)", "z = tridiag_sqrt_e1(alpha, beta)",
+     {"lanczos_full_dimension", "lanczos_eigenvector"}),
+    ("square_root_transposed_operand", "return Q @ (root * (Q.T @ W))", "return Q.T @ (root * (Q @ W))",
+     {"sqrt_schur"}),
+    ("philox_weyl_constant", "_PHILOX_W1 = 0xBB67AE85", "_PHILOX_W1 = 0xBB67AE86", {"philox_kat"}),
+    ("philox_round_word_order", "c0, c1, c2, c3 = (hi1 ^ c1 ^ k0), lo1, (hi0 ^ c3 ^ k1), lo0",
+     "c0, c1, c2, c3 = (hi0 ^ c1 ^ k0), lo1, (hi1 ^ c3 ^ k1), lo0", {"philox_kat"}),
+    ("philox_key_schedule", "if rnd < 9:", "if rnd < 8:", {"philox_kat"}),
+    ("soft_force_without_1_over_b", "U0 / b * np.exp((d_pair - r[m]) / b)", "U0 * np.exp((d_pair - r[m]) / b)",
+     {"soft_gradient"}),
+    ("adams_bashforth_history_sign", "1.5 * u - 0.5 * np.asarray(prev_u)", "1.5 * u + 0.5 * np.asarray(prev_u)",
+     {"ab_euler_second_order"}),
+]
+
+
+@pytest.mark.parametrize("name,old,new,caught_by", PY_MUTATIONS, ids=[m[0] for m in PY_MUTATIONS])
+def test_planted_python_mistake_fails_its_pins(monkeypatch, name, old, new, caught_by):
+    held = _py_pins(monkeypatch, _py_mutant(old, new))
+    failed = {k for k, ok in held.items() if not ok}
+    assert caught_by <= failed, (name, held)
