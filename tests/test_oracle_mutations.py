@@ -1,10 +1,20 @@
 """The oracle's pins reject plausible mistakes.
 
-Each case compiles a copy of the C oracle (``oracle/rpy_oracle.c``) with one
-planted change -- a flipped sign, a dropped term, a transposed block -- on the
-CPU, in a temporary directory, and checks that the pin aimed at that kind of
-mistake fails on the mutant while it passes on an unchanged copy.  The oracle
-source itself is never modified and no GPU is involved."""
+Each case plants one change -- a flipped sign, a dropped term, a transposed
+operand, a wrong constant or index -- in a copy of the oracle on the CPU and
+checks that the pins aimed at that kind of mistake fail on the mutant while
+they pass on an unchanged copy:
+  * the gradient and the direct sum of the C oracle (``oracle/rpy_oracle.c``,
+    compiled in a temporary directory) against central differences, the
+    gradient invariants and the dense matrix;
+  * the RPY pair blocks against the pins of ``test_oracle_pins.py`` (the
+    quadrature of the defining integral, contact values, continuity, the
+    Oseen limit, half the vorticity, symmetry and positive definiteness);
+  * the single-wall blocks against the sympy derivation of ``test_wall_pins.py``;
+  * the Python half (square roots, Lanczos, Philox, the roller-example
+    integrator), a changed copy of ``oracle/__init__.py`` executed as a
+    separate module, against the pins of both files.
+The oracle's own sources are never modified and no GPU is involved."""
 import ctypes
 import os
 import shutil
